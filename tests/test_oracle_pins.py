@@ -1,0 +1,344 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+Nothing here retypes the oracle's formulas: each check is a brute-force count
+on a tiny image, a library routine standing in for a textbook special case
+(numpy cumsum / var / bincount), a closed form, an invariant the paper states,
+or a finite difference. Each is chosen so that a plausible slip in the oracle
+(swapped weight, wrong corner index, dropped term, wrong sign) fails here.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _grey(vals):
+    v = np.asarray(vals, np.float32)
+    return np.repeat(v[..., None], 3, axis=-1)
+
+
+# ---------------------------------------------------------------- Eq. 11 --
+def test_luminance_weights_match_eq11(orc):
+    g = json.load(open(os.path.join(GOLDEN, "paper_constants.json")))
+    wr, wg, wb = g["luminance_weights"]["value"]
+    assert orc.luminance(1.0, 0.0, 0.0) == np.float32(wr)
+    assert orc.luminance(0.0, 1.0, 0.0) == np.float32(wg)
+    assert orc.luminance(0.0, 0.0, 1.0) == np.float32(wb)
+    # weights sum to one (up to float rounding), so grey in -> same luminance
+    assert abs(orc.luminance(3.0, 3.0, 3.0) - 3.0) < 3.0 * 2e-7
+
+
+def test_luminance_float_order_and_floor(orc):
+    rng = np.random.default_rng(1)
+    f = np.float32
+    for r, g, b in rng.uniform(0, 1e4, size=(200, 3)).astype(np.float32):
+        expect = (f(0.2126) * r + f(0.7152) * g) + f(0.0722) * b  # numpy float32 ops
+        assert orc.luminance(r, g, b) == expect
+    assert orc.luminance(0.0, 0.0, 0.0) == np.float32(1e-30)
+
+
+# ------------------------------------------------ Section II-A binning --
+@pytest.mark.parametrize("n", [1, 2, 5, 32, 64, 256])
+def test_bins_equal_width_in_log(orc, n):
+    img = synth.wdr_image(37, 53, seed=n)
+    d = orc.prepare(img, n)
+    lum = d["lum"].astype(np.float64)
+    lo, hi = math.log(d["imin"]), math.log(d["imax"])
+    u = n * (np.log(lum) - lo) / (hi - lo)
+    expect = np.minimum(np.floor(u), n - 1).astype(np.int64)
+    near_edge = np.abs(u - np.round(u)) < 1e-9
+    assert np.array_equal(d["bins"][~near_edge], expect[~near_edge])
+    assert d["bins"].min() == 0 and d["bins"].max() == n - 1
+    assert d["bins"].ravel()[np.argmin(lum)] == 0
+    assert d["bins"].ravel()[np.argmax(lum)] == n - 1
+    thr = d["thr"]
+    assert thr.shape == (n - 1,)
+    assert np.all(np.diff(thr.astype(np.float64)) > 0)
+    # edges round up: the float just below each edge lies below the exact edge
+    for k in range(1, n):
+        exact_u = k  # edge k sits at u == k
+        below = np.nextafter(thr[k - 1], np.float32(0))
+        assert n * (math.log(float(below)) - lo) / (hi - lo) < exact_u + 1e-9
+
+
+def test_degenerate_range_all_bin_zero(orc):
+    d = orc.prepare(_grey(np.full((4, 6), 7.0)), 16)
+    assert np.all(d["bins"] == 0) and np.all(d["lhat"] == 0)
+
+
+def test_lhat_normalised_log(orc):
+    img = _grey([[1.0, 10.0, 100.0, 1000.0]])
+    d = orc.prepare(img, 4)
+    lum = d["lum"].astype(np.float64).ravel()
+    lh = d["lhat"].ravel()
+    assert lh[0] == 0.0 and abs(lh[-1] - 1.0) < 1e-15
+    # log base does not matter: compare with log10 ratio
+    ref = (np.log10(lum) - np.log10(lum[0])) / (np.log10(lum[-1]) - np.log10(lum[0]))
+    assert np.allclose(lh, ref, atol=1e-14)
+
+
+# ------------------------------------------------------------- Eq. 5 ----
+def test_integral_image_matches_cumsum(orc):
+    rng = np.random.default_rng(0)
+    v = rng.integers(-(2 ** 40), 2 ** 40, size=(19, 23))
+    S = orc.integral_i64(v)
+    ref = np.zeros((20, 24), np.uint64)
+    ref[1:, 1:] = np.cumsum(np.cumsum(v.astype(np.uint64), 0), 1)  # wraps mod 2^64
+    assert np.array_equal(S, ref)
+    vf = rng.standard_normal((7, 9))
+    Sf = orc.integral_f64(vf)
+    assert np.allclose(Sf[1:, 1:], np.cumsum(np.cumsum(vf, 0), 1), atol=1e-12)
+    assert np.all(Sf[0] == 0) and np.all(Sf[:, 0] == 0)
+
+
+def test_integral_image_wraps_mod_2_64(orc):
+    v = np.full((3, 3), 2 ** 62, np.int64)
+    S = orc.integral_i64(v)
+    assert int(S[3, 3]) == (9 * 2 ** 62) % (2 ** 64)
+
+
+# --------------------------------------------------------- Eq. 7-9 ------
+def test_integral_histogram_matches_onehot_cumsum(orc):
+    rng = np.random.default_rng(3)
+    n = 7
+    b = rng.integers(0, n, size=(11, 13)).astype(np.uint8)
+    Hk = orc.integral_histogram(b, n)
+    for k in range(n):
+        ref = np.zeros((12, 14), np.int64)
+        ref[1:, 1:] = np.cumsum(np.cumsum((b == k).astype(np.int64), 0), 1)
+        assert np.array_equal(Hk[k].astype(np.int64), ref)
+    # Eq. 9 with Algorithm 1's corners (x - r - 1, x + r) on interior windows
+    r, x, y = 2, 6, 5
+    for k in range(n):
+        box = (int(Hk[k, y + r + 1, x + r + 1]) - int(Hk[k, y + r + 1, x - r])
+               - int(Hk[k, y - r, x + r + 1]) + int(Hk[k, y - r, x - r]))
+        assert box == int(np.sum(b[y - r:y + r + 1, x - r:x + r + 1] == k))
+    # histogram counts of every window sum to the window area (Eq. 1's T)
+    tot = sum(int(Hk[k, -1, -1]) for k in range(n))
+    assert tot == b.size
+
+
+# -------------------------------------------- Eq. 1, 2, 4, 10 by brute force
+RADII_SETS = [
+    [0],
+    [1],
+    [(2, 1), (0, 3)],
+    [1, 3, 40],  # last window larger than the image
+]
+
+
+@pytest.mark.parametrize("radii", RADII_SETS)
+def test_forward_fields_against_brute_force(orc, radii):
+    img = synth.wdr_image(9, 12, seed=len(radii) + 5)
+    n = 6
+    p = orc.make_params(n, radii, eps=[0.1, 0.02, 0.3, 0.05][: len(radii)])
+    out, fl = orc.forward(img, p)
+    d = orc.prepare(img, n)
+    b, lh = d["bins"].astype(np.int64), d["lhat"]
+    H, W = b.shape
+    for f, r in enumerate(radii):
+        rx, ry = (r, r) if np.isscalar(r) else r
+        for y in range(H):
+            for x in range(W):
+                ys = slice(max(y - ry, 0), min(y + ry, H - 1) + 1)
+                xs = slice(max(x - rx, 0), min(x + rx, W - 1) + 1)
+                win_b, win_l = b[ys, xs], lh[ys, xs]
+                assert fl.area[f, y, x] == win_b.size
+                assert fl.cnt[f, y, x] == int(np.sum(win_b < b[y, x]))  # strict (Eq. 1)
+                v = float(np.var(win_l))
+                assert abs(fl.sigma2[f, y, x] - v) <= 1e-12 + 1e-9 * v
+                assert abs(fl.mu[f, y, x] - float(np.mean(win_l))) <= 1e-12
+    # convex combination (Eq. 3) and weight range (Eq. 4)
+    lo = fl.lf.min(axis=0) - 1e-12
+    hi = fl.lf.max(axis=0) + 1e-12
+    assert np.all((fl.l >= lo) & (fl.l <= hi))
+    alpha = np.array([p.alpha[f] for f in range(len(radii))])[:, None, None]
+    assert np.all(fl.weight >= 0) and np.all(fl.weight < alpha)
+
+
+def test_forward_matches_direct_pixel_path(orc):
+    img = synth.wdr_image(23, 31, seed=11)
+    p = orc.make_params(16, [1, 4, 12])
+    out, fl = orc.forward(img, p)
+    yy, xx = np.meshgrid(np.arange(23), np.arange(31), indexing="ij")
+    o2, d = orc.forward_pixels(img, p, xx.ravel(), yy.ravel())
+    assert np.array_equal(d["cnt"].T.reshape(3, 23, 31), fl.cnt)
+    assert np.allclose(o2, out.reshape(-1, 3), rtol=1e-12, atol=1e-15)
+
+
+# ------------------------------------------------------ special cases ----
+def test_constant_image_maps_to_ld_min(orc):
+    img = _grey(np.full((6, 8), 3.5))
+    p = orc.make_params(8, [1, 2], ld_min=0.25, ld_max=0.9)
+    out, fl = orc.forward(img, p)
+    assert np.all(fl.sigma2 == 0) and np.all(fl.weight == 0)
+    assert np.allclose(out, 0.25, atol=1e-15)  # grey: (C/i)^sat == 1 up to rounding
+
+
+def test_zero_radius_maps_to_ld_min(orc):
+    img = synth.wdr_image(8, 8, seed=2)
+    p = orc.make_params(8, [0], ld_min=0.1)
+    out, fl = orc.forward(img, p)
+    assert np.all(fl.cnt == 0) and np.all(fl.sigma2 == 0)
+    assert np.allclose(fl.l, 0.1)
+
+
+def test_single_global_field_is_histogram_equalisation(orc):
+    """s = 1 with a window covering the image: P is the global strict-below
+    histogram CDF (Section II-B: the mapping becomes global and monotone)."""
+    img = synth.wdr_image(14, 17, seed=4)
+    n = 10
+    p = orc.make_params(n, [100], ld_min=0.0, ld_max=1.0)
+    out, fl = orc.forward(img, p)
+    b = orc.prepare(img, n)["bins"]
+    hist = np.bincount(b.ravel(), minlength=n)
+    cdf_below = np.concatenate([[0], np.cumsum(hist)[:-1]]) / b.size
+    assert np.allclose(fl.lf[0], cdf_below[b], atol=1e-15)
+    assert np.allclose(fl.l, cdf_below[b], atol=1e-15)
+    lum = orc.prepare(img, n)["lum"].ravel()
+    order = np.argsort(lum, kind="stable")
+    assert np.all(np.diff(fl.l.ravel()[order]) >= -1e-15)  # monotone in luminance
+
+
+def test_two_level_step_counts_closed_form(orc):
+    img, (y0, y1, x0, x1) = synth.box_image(20, 24, seed=5)
+    r = 3
+    p = orc.make_params(4, [r])
+    out, fl = orc.forward(img, p)
+    H, W = 20, 24
+
+    def overlap(a0, a1, b0, b1):  # |[a0,a1] cap [b0,b1-1]|
+        return max(0, min(a1, b1 - 1) - max(a0, b0) + 1)
+
+    for y in range(H):
+        for x in range(W):
+            wy0, wy1 = max(y - r, 0), min(y + r, H - 1)
+            wx0, wx1 = max(x - r, 0), min(x + r, W - 1)
+            area = (wy1 - wy0 + 1) * (wx1 - wx0 + 1)
+            bright = overlap(wy0, wy1, y0, y1) * overlap(wx0, wx1, x0, x1)
+            inside = (y0 <= y < y1) and (x0 <= x < x1)
+            assert fl.cnt[0, y, x] == (area - bright if inside else 0)
+
+
+def test_colour_restoration_closed_form(orc):
+    # one pixel with C/i = 2 in red: out_r / L = 2^0.6 (Eq. 12, sat = 0.6)
+    img = synth.wdr_image(6, 6, seed=9)
+    p = orc.make_params(8, [1, 2])
+    out, fl = orc.forward(img, p)
+    lum = orc.prepare(img, 8)["lum"].astype(np.float64)
+    ratio = img.astype(np.float64) / lum[..., None]
+    assert np.allclose(out, ratio ** 0.6 * fl.l[..., None], rtol=1e-13)
+    assert abs(2.0 ** 0.6 - 1.5157165665103982) < 1e-15
+    grey = _grey(synth.wdr_image(5, 5, seed=1)[..., 1])
+    og, fg = orc.forward(grey, p)
+    assert np.allclose(og[..., 0], og[..., 2]) and np.allclose(og[..., 0], fg.l, rtol=1e-6)
+
+
+# ------------------------------------------------------------ invariants --
+def test_scale_invariance(orc):
+    img = synth.wdr_image(16, 21, seed=8)
+    p = orc.make_params(12, [1, 5])
+    out, fl = orc.forward(img, p)
+    out2, fl2 = orc.forward(img * np.float32(8.0), p)
+    assert np.array_equal(orc.prepare(img, 12)["bins"], orc.prepare(img * np.float32(8.0), 12)["bins"])
+    assert np.array_equal(fl.cnt, fl2.cnt)
+    assert np.allclose(out2, out, rtol=1e-12, atol=1e-15)
+
+
+def test_power_law_invariance_of_tone_mapped_luminance(orc):
+    # lhat and the bins only see ln i up to an affine map: i -> i^gamma leaves L
+    base = synth.wdr_image(12, 12, seed=3)[..., 0].astype(np.float64)
+    img1 = _grey(base)
+    img2 = _grey(base ** 1.7)
+    p = orc.make_params(6, [1, 3])
+    _, f1 = orc.forward(img1, p)
+    _, f2 = orc.forward(img2, p)
+    b1, b2 = orc.prepare(img1, 6)["bins"], orc.prepare(img2, 6)["bins"]
+    if not np.array_equal(b1, b2):
+        pytest.skip("a pixel sits within float rounding of a bin edge")
+    assert np.allclose(f1.l, f2.l, rtol=1e-5, atol=1e-9)
+
+
+def test_tone_curve_monotone_in_centre_bin(orc):
+    # raising only the centre pixel (same window otherwise) never lowers L_w
+    base = _grey(np.full((7, 7), 1.0))
+    base[0, 0] = 0.01
+    base[6, 6] = 1000.0
+    p = orc.make_params(8, [3])
+    vals = np.geomspace(0.02, 900, 25)
+    lfs = []
+    for v in vals:
+        im = base.copy()
+        im[3, 3] = v
+        _, fl = orc.forward(im, p)
+        lfs.append(fl.lf[0, 3, 3])
+    assert np.all(np.diff(lfs) >= 0) and lfs[-1] > lfs[0]
+
+
+def test_weight_limits(orc):
+    # W -> alpha when sigma^2 >> eps, W -> 0 when sigma^2 << eps (Section II-B)
+    img = synth.wdr_image(20, 20, seed=12)
+    _, big = orc.forward(img, orc.make_params(8, [4], eps=1e-9, alpha=0.7))
+    _, small = orc.forward(img, orc.make_params(8, [4], eps=1e9))
+    m = big.sigma2[0] > 1e-4
+    assert np.allclose(big.weight[0][m], 0.7, rtol=1e-3)
+    assert np.all(small.weight < 1e-9)
+
+
+# --------------------------------------------------------------- adjoint --
+def _fd_setup(orc, seed=0, H=6, W=7, radii=(1, 2, 9)):
+    rng = np.random.default_rng(seed)
+    img = synth.wdr_image(H, W, seed=seed).astype(np.float64)
+    p = orc.make_params(5, list(radii), eps=[0.05, 0.1, 0.2][: len(radii)],
+                        alpha=[1.0, 0.8, 1.2][: len(radii)], ld_min=0.05, ld_max=0.95, sat=0.6)
+    bins = orc.prepare(img.astype(np.float32), 5)["bins"]
+    g = rng.standard_normal(img.shape)
+    return img, p, bins, g
+
+
+def test_adjoint_matches_central_differences_input(orc):
+    img, p, bins, g = _fd_setup(orc)
+    gin, _ = orc.backward(img, p, g, lum_f64=True, bins=bins)
+    rng = np.random.default_rng(1)
+    idx = [tuple(rng.integers(0, s) for s in img.shape) for _ in range(12)]
+    lum = img @ np.array([0.2126, 0.7152, 0.0722])
+    idx += [np.unravel_index(np.argmin(lum), lum.shape) + (1,),
+            np.unravel_index(np.argmax(lum), lum.shape) + (0,)]  # range terms
+    for ix in idx:
+        h = 1e-6 * max(abs(img[ix]), 1e-3)
+        ip, im = img.copy(), img.copy()
+        ip[ix] += h
+        im[ix] -= h
+        fd = (np.sum(g * orc.forward_fixed_bins(ip, p, bins))
+              - np.sum(g * orc.forward_fixed_bins(im, p, bins))) / (2 * h)
+        assert abs(fd - gin[ix]) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(gin).max()), (ix, fd, gin[ix])
+
+
+def test_adjoint_matches_central_differences_params(orc):
+    img, p, bins, g = _fd_setup(orc, seed=3)
+    _, gp = orc.backward(img, p, g, lum_f64=True, bins=bins)
+
+    def loss(q):
+        return float(np.sum(g * orc.forward_fixed_bins(img, q, bins)))
+
+    def bumped(attr, f, delta):
+        q = orc.Params.from_buffer_copy(p)
+        if f is None:
+            setattr(q, attr, getattr(q, attr) + delta)
+        else:
+            getattr(q, attr)[f] += delta
+        return q
+
+    h = 1e-6
+    checks = [("ld_min", None, gp["ld_min"]), ("ld_max", None, gp["ld_max"]), ("sat", None, gp["sat"])]
+    checks += [("eps", f, gp["eps"][f]) for f in range(p.n_fields)]
+    checks += [("alpha", f, gp["alpha"][f]) for f in range(p.n_fields)]
+    for attr, f, an in checks:
+        fd = (loss(bumped(attr, f, h)) - loss(bumped(attr, f, -h))) / (2 * h)
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(fd)), (attr, f, fd, an)
