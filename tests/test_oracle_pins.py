@@ -342,3 +342,25 @@ def test_adjoint_matches_central_differences_params(orc):
     for attr, f, an in checks:
         fd = (loss(bumped(attr, f, h)) - loss(bumped(attr, f, -h))) / (2 * h)
         assert abs(fd - an) <= 1e-6 * max(1.0, abs(fd)), (attr, f, fd, an)
+
+
+def test_value_on_bin_edge_goes_to_upper_bin(orc):
+    """Reading R3: a luminance equal to an edge belongs to the upper bin."""
+    n = 8
+    img = _grey(np.geomspace(0.01, 100.0, 40).reshape(5, 8))
+    d = orc.prepare(img, n)
+    k = 3
+    edge = d["thr"][k - 1]
+    hit = None
+    for v in (edge, np.nextafter(edge, np.float32(0)), np.nextafter(edge, np.float32(np.inf))):
+        for w in np.float32(v) * (1 + np.arange(-8, 9, dtype=np.float32) * np.float32(6e-8)):
+            if orc.luminance(w, w, w) == edge:
+                hit = w
+                break
+        if hit is not None:
+            break
+    assert hit is not None
+    img[2, 3] = hit
+    d2 = orc.prepare(img, n)
+    assert d2["imin"] == d["imin"] and d2["imax"] == d["imax"]
+    assert d2["lum"][2, 3] == edge and d2["bins"][2, 3] == k
