@@ -1,0 +1,609 @@
+// tm_api.cu -- the C ABI declared in include/tm.h: parameter validation,
+// context and workspace management, and the launch sequences of the forward
+// path. Every entry point validates on the host before issuing GPU work.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "tm.h"
+#include "tm_kernels.cuh"
+
+using namespace tmk;
+
+struct tm_ctx {
+  tm_params p;
+  std::string err;
+  int debug = 0;
+  int hist_path = 0;
+  int64_t launches = 0;
+  // device workspace (grown on demand)
+  void *ws = nullptr;
+  size_t ws_bytes = 0;
+  Stats *stats = nullptr;
+  // staging for tm_forward_host
+  void *stage = nullptr;
+  size_t stage_bytes = 0;
+  // layout of the last forward (for debug exports)
+  int last_W = 0, last_H = 0, last_q = 0;
+  uint8_t *bins = nullptr;
+  int32_t *q = nullptr;
+  DebugPlanes dbg{};
+  // stage timing: events recorded on the call's stream after each stage
+  int stage_timing = 0;
+  std::vector<std::vector<std::pair<cudaEvent_t, int>>> marks;
+  std::vector<cudaEvent_t> event_pool;
+  double stage_ms[16] = {};
+};
+
+namespace {
+
+std::mutex g_create_mu;
+std::string g_create_err;
+
+tm_status fail(tm_ctx *c, tm_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  else {
+    std::lock_guard<std::mutex> g(g_create_mu);
+    g_create_err = buf;
+  }
+  return s;
+}
+
+tm_status cuda_fail(tm_ctx *c, cudaError_t e, const char *what) {
+  return fail(c, TM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define TM_CUDA(c, call)                                   \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail((c), e_, #call); \
+  } while (0)
+
+bool finite_pos(float v) { return std::isfinite(v) && v > 0.f; }
+
+tm_status validate_params(const tm_params *p, std::string &why) {
+  char b[256];
+  if (!p) { why = "params is NULL"; return TM_EINVAL; }
+  if (p->n_bins < 1 || p->n_bins > TM_MAX_BINS) {
+    snprintf(b, sizeof b, "n_bins %d outside 1..%d", p->n_bins, TM_MAX_BINS); why = b; return TM_EINVAL;
+  }
+  if (p->n_fields < 1 || p->n_fields > TM_MAX_FIELDS) {
+    snprintf(b, sizeof b, "n_fields %d outside 1..%d", p->n_fields, TM_MAX_FIELDS); why = b; return TM_EINVAL;
+  }
+  for (int f = 0; f < p->n_fields; ++f) {
+    if (p->rx[f] < 0 || p->ry[f] < 0 || p->rx[f] > TM_MAX_RADIUS || p->ry[f] > TM_MAX_RADIUS) {
+      snprintf(b, sizeof b, "field %d radius (%d, %d) outside 0..%d", f, p->rx[f], p->ry[f], TM_MAX_RADIUS);
+      why = b; return TM_EINVAL;
+    }
+    if (!finite_pos(p->eps[f])) { snprintf(b, sizeof b, "field %d eps must be finite and > 0", f); why = b; return TM_EINVAL; }
+    if (!std::isfinite(p->alpha[f]) || p->alpha[f] < 0.f) {
+      snprintf(b, sizeof b, "field %d alpha must be finite and >= 0", f); why = b; return TM_EINVAL;
+    }
+  }
+  if (!std::isfinite(p->ld_min) || !std::isfinite(p->ld_max) || p->ld_max < p->ld_min) {
+    why = "need finite ld_min <= ld_max"; return TM_EINVAL;
+  }
+  if (!std::isfinite(p->sat) || p->sat < 0.f) { why = "sat must be finite and >= 0"; return TM_EINVAL; }
+  if (p->flags != 0) { why = "flags must be 0"; return TM_EINVAL; }
+  return TM_OK;
+}
+
+enum Stage { ST_RANGE, ST_PREP, ST_INTEGRAL, ST_HIST, ST_LOOKUP, ST_SWEEP, ST_BATCH,
+             ST_BWD_PIXEL, ST_BWD_ADJOINT, ST_BWD_INPUT, ST_COUNT };
+const char *const kStageNames[ST_COUNT] = {"range", "prep", "integral_image", "integral_histogram",
+                                          "lookup", "fused_sweep", "batch", "bwd_pixel",
+                                          "bwd_adjoint", "bwd_input"};
+
+// Record a stage boundary on stream s (stage < 0 opens a new call).
+void mark(tm_ctx *c, cudaStream_t s, int stage) {
+  if (!c->stage_timing) return;
+  cudaEvent_t e;
+  if (!c->event_pool.empty()) {
+    e = c->event_pool.back();
+    c->event_pool.pop_back();
+  } else if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  if (stage < 0) c->marks.emplace_back();
+  if (c->marks.empty()) c->marks.emplace_back();
+  cudaEventRecord(e, s);
+  c->marks.back().emplace_back(e, stage);
+}
+
+size_t elem_size(int dt) { return dt == TM_F32 ? 4 : dt == TM_F16 ? 2 : 1; }
+
+tm_status validate_image(tm_ctx *c, const tm_image *im, const char *name, bool is_input) {
+  if (!im) return fail(c, TM_EINVAL, "%s descriptor is NULL", name);
+  if (!im->data) return fail(c, TM_EINVAL, "%s.data is NULL", name);
+  if (im->width < 1 || im->height < 1)
+    return fail(c, TM_EINVAL, "%s size %dx%d must be positive", name, im->width, im->height);
+  if ((long long)im->width * im->height > (1LL << 31) - 1)
+    return fail(c, TM_EINVAL, "%s has more than 2^31-1 pixels", name);
+  if (im->pitch < 3LL * im->width)
+    return fail(c, TM_EINVAL, "%s.pitch %lld < 3*width", name, (long long)im->pitch);
+  if (im->dtype != TM_F32 && im->dtype != TM_F16 && im->dtype != TM_U8)
+    return fail(c, TM_EINVAL, "%s.dtype %d unknown", name, im->dtype);
+  if (is_input && im->dtype == TM_U8)
+    return fail(c, TM_EUNSUPPORTED, "%s: uint8 input is not supported (use F32 or F16)", name);
+  if (((uintptr_t)im->data) % elem_size(im->dtype))
+    return fail(c, TM_EINVAL, "%s.data is not aligned to its element size", name);
+  return TM_OK;
+}
+
+size_t image_bytes(const tm_image *im) {
+  return ((size_t)(im->height - 1) * im->pitch + 3 * (size_t)im->width) * elem_size(im->dtype);
+}
+
+bool overlap(const tm_image *a, const tm_image *b) {
+  uintptr_t a0 = (uintptr_t)a->data, a1 = a0 + image_bytes(a);
+  uintptr_t b0 = (uintptr_t)b->data, b1 = b0 + image_bytes(b);
+  return a0 < b1 && b0 < a1;
+}
+
+// Q for the quantised log: the largest Q <= 24 with every window sum of q^2
+// below 2^63 (|q| <= 2^(Q-1), windows of at most n_max pixels).
+int choose_qbits(const tm_params &p, int W, int H) {
+  unsigned long long n_max = 1;
+  for (int f = 0; f < p.n_fields; ++f) {
+    unsigned long long wx = std::min<long long>(2LL * p.rx[f] + 1, W);
+    unsigned long long wy = std::min<long long>(2LL * p.ry[f] + 1, H);
+    n_max = std::max(n_max, wx * wy);
+  }
+  int Q = 24;
+  while (Q > 2 && ((unsigned __int128)n_max << (2 * Q - 2)) >= ((unsigned __int128)1 << 63)) --Q;
+  return Q;
+}
+
+DevParams dev_params(const tm_params &p, int qbits) {
+  DevParams d{};
+  d.n_bins = p.n_bins;
+  d.n_fields = p.n_fields;
+  for (int f = 0; f < TM_MAX_FIELDS; ++f) {
+    d.rx[f] = p.rx[f];
+    d.ry[f] = p.ry[f];
+    d.eps[f] = p.eps[f];
+    d.alpha[f] = p.alpha[f];
+  }
+  d.ld_min = p.ld_min;
+  d.ld_max = p.ld_max;
+  d.sat = p.sat;
+  d.qbits = qbits;
+  return d;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct Layout {
+  size_t bins, q, s1, s2, iscr, cpl, hscr, dcnt, dvar, dw, dlf, dl, total;
+};
+
+Layout plan(const tm_params &p, int W, int H, bool debug, bool materialised) {
+  Layout L{};
+  const size_t N = (size_t)W * H;
+  const size_t plane = (size_t)(W + 1) * (H + 1);
+  const int s = p.n_fields;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
+  L.bins = take(N);
+  L.q = take(4 * N);
+  L.s1 = take(8 * plane);
+  L.s2 = take(8 * plane);
+  L.iscr = take(8 * integral_scratch_elems(W, H));
+  if (materialised && p.n_bins > 1) {
+    L.cpl = take(4 * plane * (size_t)(p.n_bins - 1));
+    L.hscr = take(4 * hist_scratch_elems(W, H, p.n_bins - 1));
+  }
+  if (debug) {
+    L.dcnt = take(4 * N * s);
+    L.dvar = take(4 * N * s);
+    L.dw = take(4 * N * s);
+    L.dlf = take(4 * N * s);
+    L.dl = take(4 * N);
+  }
+  L.total = off;
+  return L;
+}
+
+tm_status ensure_stats(tm_ctx *c) {
+  if (c->stats) return TM_OK;
+  Stats h{};
+  h.min_bits = 0x7f800000u;
+  h.max_bits = 0u;
+  h.blocks_done = 0u;
+  TM_CUDA(c, cudaMalloc(&c->stats, sizeof(Stats)));
+  TM_CUDA(c, cudaMemcpy(c->stats, &h, sizeof(Stats), cudaMemcpyHostToDevice));
+  return TM_OK;
+}
+
+tm_status ensure_ws(tm_ctx *c, size_t bytes) {
+  if (c->ws_bytes >= bytes) return TM_OK;
+  if (c->ws) {
+    TM_CUDA(c, cudaDeviceSynchronize());
+    cudaFree(c->ws);
+    c->ws = nullptr;
+    c->ws_bytes = 0;
+  }
+  cudaError_t e = cudaMalloc(&c->ws, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, TM_ENOMEM, "workspace of %zu bytes: %s", bytes, cudaGetErrorString(e));
+  }
+  c->ws_bytes = bytes;
+  return TM_OK;
+}
+
+Image to_image(const tm_image *im) {
+  Image r;
+  r.p = im->data;
+  r.W = im->width;
+  r.H = im->height;
+  r.pitch = im->pitch;
+  r.dtype = im->dtype;
+  return r;
+}
+
+tm_status check_launch(tm_ctx *c, const char *what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, what);
+  return TM_OK;
+}
+
+// The forward launch sequence on one image (device buffers already checked).
+tm_status forward_device(tm_ctx *c, const tm_image *in, const tm_image *out, cudaStream_t s) {
+  const int W = in->width, H = in->height;
+  const bool materialised = true;
+  tm_status st = ensure_stats(c);
+  if (st) return st;
+  Layout L = plan(c->p, W, H, c->debug != 0, materialised);
+  if ((st = ensure_ws(c, L.total))) return st;
+  char *ws = static_cast<char *>(c->ws);
+  const int qbits = choose_qbits(c->p, W, H);
+  const DevParams P = dev_params(c->p, qbits);
+  const Image iin = to_image(in), iout = to_image(out);
+  uint8_t *bins = reinterpret_cast<uint8_t *>(ws + L.bins);
+  int32_t *q = reinterpret_cast<int32_t *>(ws + L.q);
+  int64_t *s1 = reinterpret_cast<int64_t *>(ws + L.s1);
+  int64_t *s2 = reinterpret_cast<int64_t *>(ws + L.s2);
+  DebugPlanes dbg{};
+  if (c->debug) {
+    dbg.cnt = reinterpret_cast<unsigned *>(ws + L.dcnt);
+    dbg.sigma2 = reinterpret_cast<float *>(ws + L.dvar);
+    dbg.weight = reinterpret_cast<float *>(ws + L.dw);
+    dbg.lf = reinterpret_cast<float *>(ws + L.dlf);
+    dbg.l = reinterpret_cast<float *>(ws + L.dl);
+  }
+  int64_t n = 0;
+  mark(c, s, -1);
+  launch_range(iin, c->stats, c->p.n_bins, qbits, s);
+  n += 1;
+  mark(c, s, ST_RANGE);
+  launch_prep(iin, c->stats, c->p.n_bins, qbits, bins, q, s);
+  n += 1;
+  mark(c, s, ST_PREP);
+  n += launch_integral_image(q, W, H, s1, s2, reinterpret_cast<int64_t *>(ws + L.iscr), s);
+  mark(c, s, ST_INTEGRAL);
+  uint32_t *cpl = nullptr;
+  if (c->p.n_bins > 1) {
+    cpl = reinterpret_cast<uint32_t *>(ws + L.cpl);
+    n += launch_integral_histogram(bins, W, H, c->p.n_bins, true, cpl,
+                                   reinterpret_cast<uint32_t *>(ws + L.hscr), s);
+  }
+  mark(c, s, ST_HIST);
+  n += launch_lookup_materialised(iin, iout, P, bins, cpl, s1, s2, dbg, s);
+  mark(c, s, ST_LOOKUP);
+  if ((st = check_launch(c, "forward launch"))) return st;
+  c->launches = n;
+  c->last_W = W;
+  c->last_H = H;
+  c->last_q = qbits;
+  c->bins = bins;
+  c->q = q;
+  c->dbg = dbg;
+  return TM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void tm_params_default(tm_params *p) {
+  if (!p) return;
+  memset(p, 0, sizeof *p);
+  p->n_bins = 5;
+  p->n_fields = 5;
+  const int half[5] = {1024, 512, 256, 128, 64};
+  for (int f = 0; f < TM_MAX_FIELDS; ++f) {
+    p->rx[f] = p->ry[f] = f < 5 ? half[f] : 0;
+    p->eps[f] = 0.1f;
+    p->alpha[f] = 1.0f;
+  }
+  p->ld_min = 0.f;
+  p->ld_max = 1.f;
+  p->sat = 0.6f;
+  p->flags = 0;
+}
+
+tm_status tm_params_pyramid(tm_params *p, int32_t width, int32_t height, int32_t n_fields,
+                            int32_t n_bins) {
+  if (!p || width < 1 || height < 1 || n_fields < 1 || n_fields > TM_MAX_FIELDS || n_bins < 1 ||
+      n_bins > TM_MAX_BINS)
+    return fail(nullptr, TM_EINVAL, "tm_params_pyramid: bad argument");
+  tm_params_default(p);
+  p->n_fields = n_fields;
+  p->n_bins = n_bins;
+  for (int f = 0; f < TM_MAX_FIELDS; ++f) {
+    p->rx[f] = f < n_fields ? std::min(width >> (f + 1), TM_MAX_RADIUS) : 0;
+    p->ry[f] = f < n_fields ? std::min(height >> (f + 1), TM_MAX_RADIUS) : 0;
+  }
+  return TM_OK;
+}
+
+tm_status tm_create(const tm_params *params, tm_ctx **out) {
+  if (!out) return fail(nullptr, TM_EINVAL, "tm_create: out is NULL");
+  *out = nullptr;
+  std::string why;
+  tm_status s = validate_params(params, why);
+  if (s) return fail(nullptr, s, "tm_create: %s", why.c_str());
+  tm_ctx *c = new (std::nothrow) tm_ctx();
+  if (!c) return fail(nullptr, TM_ENOMEM, "tm_create: out of host memory");
+  c->p = *params;
+  *out = c;
+  return TM_OK;
+}
+
+void tm_destroy(tm_ctx *c) {
+  if (!c) return;
+  if (c->ws || c->stats || c->stage) cudaDeviceSynchronize();
+  for (auto &call : c->marks)
+    for (auto &m : call) cudaEventDestroy(m.first);
+  for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
+  if (c->ws) cudaFree(c->ws);
+  if (c->stats) cudaFree(c->stats);
+  if (c->stage) cudaFree(c->stage);
+  delete c;
+}
+
+const char *tm_last_error(const tm_ctx *c) {
+  if (c) return c->err.c_str();
+  std::lock_guard<std::mutex> g(g_create_mu);
+  return g_create_err.c_str();
+}
+
+const char *tm_status_string(tm_status s) {
+  switch (s) {
+    case TM_OK: return "TM_OK";
+    case TM_EINVAL: return "TM_EINVAL";
+    case TM_ENOMEM: return "TM_ENOMEM";
+    case TM_ECUDA: return "TM_ECUDA";
+    case TM_EUNSUPPORTED: return "TM_EUNSUPPORTED";
+    case TM_ETIMEOUT: return "TM_ETIMEOUT";
+    case TM_ESTATE: return "TM_ESTATE";
+  }
+  return "TM_UNKNOWN";
+}
+
+tm_status tm_forward(tm_ctx *c, const tm_image *in, const tm_image *out, void *stream) {
+  if (!c) return fail(nullptr, TM_EINVAL, "tm_forward: ctx is NULL");
+  tm_status s;
+  if ((s = validate_image(c, in, "in", true))) return s;
+  if ((s = validate_image(c, out, "out", false))) return s;
+  if (in->width != out->width || in->height != out->height)
+    return fail(c, TM_EINVAL, "in is %dx%d but out is %dx%d", in->width, in->height, out->width,
+                out->height);
+  if (overlap(in, out)) return fail(c, TM_EINVAL, "in and out overlap");
+  return forward_device(c, in, out, static_cast<cudaStream_t>(stream));
+}
+
+tm_status tm_forward_host(tm_ctx *c, const tm_image *in, const tm_image *out, void *stream) {
+  if (!c) return fail(nullptr, TM_EINVAL, "tm_forward_host: ctx is NULL");
+  tm_status s;
+  if ((s = validate_image(c, in, "in", true))) return s;
+  if ((s = validate_image(c, out, "out", false))) return s;
+  if (in->width != out->width || in->height != out->height)
+    return fail(c, TM_EINVAL, "in and out sizes differ");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int W = in->width, H = in->height;
+  const size_t in_row = 3 * (size_t)W * elem_size(in->dtype);
+  const size_t out_row = 3 * (size_t)W * elem_size(out->dtype);
+  const size_t in_bytes = align256(in_row * H), out_bytes = align256(out_row * H);
+  if (c->stage_bytes < in_bytes + out_bytes) {
+    if (c->stage) {
+      TM_CUDA(c, cudaDeviceSynchronize());
+      cudaFree(c->stage);
+      c->stage = nullptr;
+      c->stage_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&c->stage, in_bytes + out_bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, TM_ENOMEM, "staging buffer: %s", cudaGetErrorString(e));
+    }
+    c->stage_bytes = in_bytes + out_bytes;
+  }
+  tm_image din = *in, dout = *out;
+  din.data = c->stage;
+  din.pitch = 3LL * W;
+  dout.data = static_cast<char *>(c->stage) + in_bytes;
+  dout.pitch = 3LL * W;
+  TM_CUDA(c, cudaMemcpy2DAsync(din.data, in_row, in->data, in->pitch * elem_size(in->dtype), in_row,
+                               H, cudaMemcpyHostToDevice, st));
+  if ((s = forward_device(c, &din, &dout, st))) return s;
+  TM_CUDA(c, cudaMemcpy2DAsync(out->data, out->pitch * elem_size(out->dtype), dout.data, out_row,
+                               out_row, H, cudaMemcpyDeviceToHost, st));
+  TM_CUDA(c, cudaStreamSynchronize(st));
+  return TM_OK;
+}
+
+tm_status tm_forward_batch(tm_ctx *c, int32_t n, const tm_image *in, const tm_image *out,
+                           void *stream) {
+  if (!c) return fail(nullptr, TM_EINVAL, "tm_forward_batch: ctx is NULL");
+  if (n < 0) return fail(c, TM_EINVAL, "n = %d < 0", n);
+  if (n == 0) { c->launches = 0; return TM_OK; }
+  if (!in || !out) return fail(c, TM_EINVAL, "descriptor arrays are NULL");
+  int64_t total = 0;
+  for (int i = 0; i < n; ++i) {
+    tm_status s = tm_forward(c, &in[i], &out[i], stream);
+    if (s) return s;
+    total += c->launches;
+  }
+  c->launches = total;
+  return TM_OK;
+}
+
+tm_status tm_backward(tm_ctx *c, const tm_image *in, const tm_image *grad_out,
+                      const tm_image *grad_in, float *grad_params, void *stream) {
+  (void)in; (void)grad_out; (void)grad_in; (void)grad_params; (void)stream;
+  if (!c) return fail(nullptr, TM_EINVAL, "tm_backward: ctx is NULL");
+  return fail(c, TM_EUNSUPPORTED, "tm_backward is not available in this build");
+}
+
+tm_status tm_integral_image(const int32_t *q, int32_t width, int32_t height, int64_t *s1,
+                            int64_t *s2, void *stream) {
+  if (!q || !s1 || !s2) return fail(nullptr, TM_EINVAL, "tm_integral_image: NULL pointer");
+  if (width < 1 || height < 1) return fail(nullptr, TM_EINVAL, "tm_integral_image: bad size");
+  if (s1 == s2) return fail(nullptr, TM_EINVAL, "tm_integral_image: s1 == s2");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void *scr = nullptr;
+  size_t bytes = 8 * integral_scratch_elems(width, height);
+  cudaError_t e = cudaMallocAsync(&scr, bytes, st);
+  if (e != cudaSuccess) { cudaGetLastError(); return fail(nullptr, TM_ENOMEM, "tm_integral_image: scratch"); }
+  launch_integral_image(q, width, height, s1, s2, static_cast<int64_t *>(scr), st);
+  e = cudaGetLastError();
+  cudaFreeAsync(scr, st);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "tm_integral_image");
+  return TM_OK;
+}
+
+tm_status tm_integral_histogram(const uint8_t *bins, int32_t width, int32_t height,
+                                int32_t n_bins, uint32_t *hk, void *stream) {
+  if (!bins || !hk) return fail(nullptr, TM_EINVAL, "tm_integral_histogram: NULL pointer");
+  if (width < 1 || height < 1) return fail(nullptr, TM_EINVAL, "tm_integral_histogram: bad size");
+  if (n_bins < 1 || n_bins > TM_MAX_BINS)
+    return fail(nullptr, TM_EINVAL, "tm_integral_histogram: n_bins outside 1..256");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void *scr = nullptr;
+  size_t bytes = 4 * hist_scratch_elems(width, height, n_bins);
+  cudaError_t e = cudaMallocAsync(&scr, bytes, st);
+  if (e != cudaSuccess) { cudaGetLastError(); return fail(nullptr, TM_ENOMEM, "tm_integral_histogram: scratch"); }
+  launch_integral_histogram(bins, width, height, n_bins, false, hk, static_cast<uint32_t *>(scr), st);
+  e = cudaGetLastError();
+  cudaFreeAsync(scr, st);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "tm_integral_histogram");
+  return TM_OK;
+}
+
+tm_status tm_set_debug(tm_ctx *c, int32_t enable) {
+  if (!c) return fail(nullptr, TM_EINVAL, "tm_set_debug: ctx is NULL");
+  c->debug = enable ? 1 : 0;
+  return TM_OK;
+}
+
+tm_status tm_debug_size(tm_ctx *c, int32_t what, size_t *bytes) {
+  if (!c || !bytes) return fail(c, TM_EINVAL, "tm_debug_size: NULL argument");
+  if (c->last_W == 0) return fail(c, TM_ESTATE, "no forward has run on this context");
+  const size_t N = (size_t)c->last_W * c->last_H, s = c->p.n_fields;
+  switch (what) {
+    case TM_DBG_RANGE: *bytes = 8; break;
+    case TM_DBG_THRESHOLDS: *bytes = 4 * (size_t)(c->p.n_bins - 1); break;
+    case TM_DBG_BINS: *bytes = N; break;
+    case TM_DBG_Q: *bytes = 4 * N; break;
+    case TM_DBG_COUNTS: case TM_DBG_SIGMA2: case TM_DBG_WEIGHT: case TM_DBG_LF: *bytes = 4 * N * s; break;
+    case TM_DBG_L: *bytes = 4 * N; break;
+    case TM_DBG_QSHIFT: *bytes = 4; break;
+    default: return fail(c, TM_EINVAL, "unknown debug export %d", what);
+  }
+  return TM_OK;
+}
+
+tm_status tm_debug_export(tm_ctx *c, int32_t what, void *dst, size_t bytes, void *stream) {
+  size_t need = 0;
+  tm_status s = tm_debug_size(c, what, &need);
+  if (s) return s;
+  if (!dst) return fail(c, TM_EINVAL, "dst is NULL");
+  if (bytes < need) return fail(c, TM_EINVAL, "dst holds %zu bytes, %zu needed", bytes, need);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const void *src = nullptr;
+  const size_t N = (size_t)c->last_W * c->last_H;
+  switch (what) {
+    case TM_DBG_RANGE: src = &c->stats->imin; break;
+    case TM_DBG_THRESHOLDS: src = c->stats->thr; break;
+    case TM_DBG_BINS: src = c->bins; break;
+    case TM_DBG_Q: src = c->q; break;
+    case TM_DBG_QSHIFT: {
+      int32_t v = c->last_q;
+      TM_CUDA(c, cudaMemcpyAsync(dst, &v, 4, cudaMemcpyHostToDevice, st));
+      TM_CUDA(c, cudaStreamSynchronize(st));
+      return TM_OK;
+    }
+    default:
+      if (!c->dbg.l) return fail(c, TM_ESTATE, "debug planes were not kept (tm_set_debug before forward)");
+      src = what == TM_DBG_COUNTS ? (const void *)c->dbg.cnt
+            : what == TM_DBG_SIGMA2 ? (const void *)c->dbg.sigma2
+            : what == TM_DBG_WEIGHT ? (const void *)c->dbg.weight
+            : what == TM_DBG_LF ? (const void *)c->dbg.lf
+                                : (const void *)c->dbg.l;
+  }
+  (void)N;
+  if (need) TM_CUDA(c, cudaMemcpyAsync(dst, src, need, cudaMemcpyDeviceToDevice, st));
+  return TM_OK;
+}
+
+tm_status tm_set_option(tm_ctx *c, int32_t key, int64_t value) {
+  if (!c) return fail(nullptr, TM_EINVAL, "tm_set_option: ctx is NULL");
+  if (key == TM_OPT_STAGE_TIMING) {
+    c->stage_timing = value ? 1 : 0;
+    return TM_OK;
+  }
+  if (key == TM_OPT_HIST_PATH) {
+    if (value < 0 || value > 2) return fail(c, TM_EINVAL, "TM_OPT_HIST_PATH value %lld", (long long)value);
+    c->hist_path = (int)value;
+    return TM_OK;
+  }
+  return fail(c, TM_EINVAL, "unknown option %d", key);
+}
+
+int64_t tm_last_launch_count(const tm_ctx *c) { return c ? c->launches : 0; }
+
+int32_t tm_stage_times(tm_ctx *c, float *ms, const char **names, int32_t cap) {
+  if (!c || !ms || !names || cap < 0) {
+    fail(c, TM_EINVAL, "tm_stage_times: bad argument");
+    return -1;
+  }
+  for (auto &call : c->marks) {
+    if (call.empty()) continue;
+    if (cudaEventSynchronize(call.back().first) != cudaSuccess) {
+      cudaGetLastError();
+      fail(c, TM_ECUDA, "tm_stage_times: event synchronisation failed");
+      return -1;
+    }
+    for (size_t i = 1; i < call.size(); ++i) {
+      float t = 0.f;
+      if (call[i].second >= 0 && cudaEventElapsedTime(&t, call[i - 1].first, call[i].first) == cudaSuccess)
+        c->stage_ms[call[i].second] += t;
+    }
+    for (auto &m : call) c->event_pool.push_back(m.first);
+  }
+  c->marks.clear();
+  int32_t n = 0;
+  for (int st = 0; st < ST_COUNT && n < cap; ++st)
+    if (c->stage_ms[st] > 0.0) {
+      ms[n] = (float)c->stage_ms[st];
+      names[n] = kStageNames[st];
+      ++n;
+    }
+  for (double &v : c->stage_ms) v = 0.0;
+  return n;
+}
+
+}  // extern "C"

@@ -1,0 +1,194 @@
+// tm_common.cuh -- device-side definitions shared by the tone-mapping kernels.
+//
+// Pixel layout: interleaved RGB (HWC) with a row pitch in elements.
+// Workspace planes: (H+1) x (W+1) row-major with a zero first row and column,
+// so that the window [x0, x1] x [y0, y1] sums to
+//   I(y1+1, x1+1) - I(y1+1, x0) - I(y0, x1+1) + I(y0, x0)      (Eq. 6, Eq. 9)
+// i.e. Algorithm 1's corners x - (r + 1) and x + r shifted by one.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tmk {
+
+constexpr int kMaxFields = 8;
+constexpr int kMaxBins = 256;
+constexpr float kLumFloor = 1e-30f;
+
+enum Dtype { kF32 = 0, kF16 = 1, kU8 = 2 };
+
+// Kernel-argument copy of the operator parameters (paper notation).
+struct DevParams {
+  int n_bins;               // n (Eq. 7)
+  int n_fields;             // s (Eq. 3)
+  int rx[kMaxFields];       // half-widths (Algorithm 1 s_j.x)
+  int ry[kMaxFields];       // half-heights (Algorithm 1 s_j.y)
+  float eps[kMaxFields];    // epsilon of Eq. 4
+  float alpha[kMaxFields];  // field weight multiplying Eq. 4
+  float ld_min, ld_max;     // display range of Eq. 2
+  float sat;                // Eq. 12
+  int qbits;                // Q: q = round(2^Q lhat) - 2^(Q-1)
+};
+
+// Per-image range state, resident in device memory. The range kernel reduces
+// into min_bits/max_bits (luminance is positive, so float bits order like the
+// values), and its last block finalises imin/imax, the bin edges and the
+// constants of the quantised log, then re-arms the accumulators.
+struct Stats {
+  unsigned int min_bits;
+  unsigned int max_bits;
+  unsigned int blocks_done;
+  int degenerate;           // imax == imin
+  float imin, imax;
+  float log2_scale;         // 2^Q / (log2 imax - log2 imin), 0 if degenerate
+  float c0;                 // log2 of imin's significand (in [1, 2))
+  int e0;                   // unbiased exponent of imin
+  int pad[3];
+  float thr[kMaxBins];      // thr[k-1]: lower edge of bin k, k = 1..n-1
+};
+
+struct Image {
+  void *p;
+  int W, H;
+  long long pitch;          // elements
+  int dtype;
+};
+
+// Eq. 11 in float: fixed order, every product and sum rounded, no contraction.
+__device__ __forceinline__ float luminance(float r, float g, float b) {
+  float i = __fadd_rn(__fadd_rn(__fmul_rn(0.2126f, r), __fmul_rn(0.7152f, g)),
+                      __fmul_rn(0.0722f, b));
+  return fmaxf(i, kLumFloor);
+}
+
+__device__ __forceinline__ void load_rgb(const Image &im, int x, int y, float &r,
+                                         float &g, float &b) {
+  long long o = (long long)y * im.pitch + 3LL * x;
+  if (im.dtype == kF16) {
+    const __half *p = static_cast<const __half *>(im.p) + o;
+    r = __half2float(p[0]);
+    g = __half2float(p[1]);
+    b = __half2float(p[2]);
+  } else {
+    const float *p = static_cast<const float *>(im.p) + o;
+    r = p[0];
+    g = p[1];
+    b = p[2];
+  }
+}
+
+__device__ __forceinline__ void store_rgb(const Image &im, int x, int y, float r,
+                                          float g, float b) {
+  long long o = (long long)y * im.pitch + 3LL * x;
+  if (im.dtype == kF32) {
+    float *p = static_cast<float *>(im.p) + o;
+    p[0] = r;
+    p[1] = g;
+    p[2] = b;
+  } else if (im.dtype == kF16) {
+    __half *p = static_cast<__half *>(im.p) + o;
+    p[0] = __float2half_rn(r);
+    p[1] = __float2half_rn(g);
+    p[2] = __float2half_rn(b);
+  } else {
+    uint8_t *p = static_cast<uint8_t *>(im.p) + o;
+    p[0] = (uint8_t)__float2int_rd(fminf(fmaxf(r, 0.f), 1.f) * 255.f + 0.5f);
+    p[1] = (uint8_t)__float2int_rd(fminf(fmaxf(g, 0.f), 1.f) * 255.f + 0.5f);
+    p[2] = (uint8_t)__float2int_rd(fminf(fmaxf(b, 0.f), 1.f) * 255.f + 0.5f);
+  }
+}
+
+// Bin of a luminance (Section II-A): number of edges at or below it.
+__device__ __forceinline__ int bin_of(float i, const float *thr, int n) {
+  int lo = 0, hi = n - 1;  // search thr[0 .. n-2]
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (i >= thr[mid]) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// Quantised normalised log luminance: q = round(2^Q lhat) - 2^(Q-1), with
+// lhat = (log2 i - log2 imin) / (log2 imax - log2 imin). The difference of
+// logs is formed as exponent difference + significand-log difference and the
+// product with the scale is kept as a float pair, so q is accurate to about
+// one unit of 2^-Q.
+__device__ __forceinline__ int quantise_log(float lum, const Stats &st, int qbits) {
+  unsigned bits = __float_as_uint(lum);
+  int e = (int)(bits >> 23) - 127;
+  float m = __uint_as_float((bits & 0x7fffffu) | 0x3f800000u);
+  float f = log2f(m) - st.c0;
+  float de = (float)(e - st.e0);
+  float d_hi = de + f;                       // TwoSum(de, f)
+  float bv = d_hi - de;
+  float d_lo = (de - (d_hi - bv)) + (f - bv);
+  float S = st.log2_scale;
+  float p = S * d_hi;                        // TwoProduct(S, d_hi)
+  float perr = fmaf(S, d_hi, -p);
+  float tail = fmaf(S, d_lo, perr);
+  float pi = rintf(p);
+  float rem = (p - pi) + tail;
+  int half = 1 << (qbits - 1);
+  int q = (int)pi + __float2int_rn(rem) - half;
+  return min(max(q, -half), half);
+}
+
+// Window of field f around (x, y), clipped to the image.
+struct Win {
+  int x0, x1, y0, y1;
+};
+__device__ __forceinline__ Win window_of(const DevParams &P, int f, int x, int y,
+                                         int W, int H) {
+  Win w;
+  w.x0 = max(x - P.rx[f], 0);
+  w.x1 = min(x + P.rx[f], W - 1);
+  w.y0 = max(y - P.ry[f], 0);
+  w.y1 = min(y + P.ry[f], H - 1);
+  return w;
+}
+
+// Exact window variance of q from its window sums (s1 = sum q, s2 = sum q^2):
+// (N s2 - s1^2) / N^2 evaluated in 128-bit integers, then scaled to lhat units.
+__device__ __forceinline__ float window_variance(long long s1, long long s2,
+                                                 float area, unsigned long long N,
+                                                 float inv_scale2) {
+  unsigned long long a1 = (unsigned long long)(s1 < 0 ? -s1 : s1);
+  unsigned __int128 num = (unsigned __int128)N * (unsigned long long)s2 -
+                          (unsigned __int128)a1 * a1;
+  unsigned long long hi = (unsigned long long)(num >> 64);
+  unsigned long long lo = (unsigned long long)num;
+  float numf = __ull2float_rn(hi) * 18446744073709551616.0f + __ull2float_rn(lo);
+  return numf / (area * area) * inv_scale2;
+}
+
+// Eq. 2, Eq. 4, Eq. 3 from per-field counts / areas / variances.
+__device__ __forceinline__ float fuse_fields(const DevParams &P, const unsigned *cnt,
+                                             const float *area, const float *var,
+                                             float *wout, float *lfout) {
+  float wsum = 0.f, acc = 0.f, mean = 0.f;
+  float span = P.ld_max - P.ld_min;
+#pragma unroll
+  for (int f = 0; f < kMaxFields; ++f) {
+    if (f >= P.n_fields) break;
+    float Pf = (float)cnt[f] / area[f];                    // Eq. 1
+    float Lf = fmaf(span, Pf, P.ld_min);                   // Eq. 2
+    float Wf = P.alpha[f] * var[f] / (var[f] + P.eps[f]);  // Eq. 4
+    if (wout) wout[f] = Wf;
+    if (lfout) lfout[f] = Lf;
+    wsum += Wf;
+    acc = fmaf(Wf, Lf, acc);
+    mean += Lf;
+  }
+  return wsum > 0.f ? acc / wsum : mean / (float)P.n_fields;  // Eq. 3
+}
+
+// Eq. 12 with the ratio clamped at zero.
+__device__ __forceinline__ float restore_channel(float C, float i, float sat, float L) {
+  float rho = C / i;
+  rho = rho > 0.f ? rho : 0.f;
+  return powf(rho, sat) * L;
+}
+
+}  // namespace tmk

@@ -1,0 +1,229 @@
+"""GPU parity of the forward path against the FP64 oracle, through the C ABI.
+
+Bit-exact: bin edges, bin map, window counts (Eq. 1 numerator), integral
+images and integral histograms. Floating point: the tone-mapped output within
+|gpu - ref| <= 1e-4 * max(|ref|, 1e-3); the window variance within the bound
+set by the 2^-Q quantisation of the normalised log (see _sigma2_tol).
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2102_01289_gb300 as tm  # noqa: E402
+
+REL = 1e-4
+FLOOR = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    tm.build()
+
+
+def f32(v):
+    return float(np.float32(v))
+
+
+def params_pair(orc, n, radii, eps=0.1, alpha=1.0, ld_min=0.0, ld_max=1.0, sat=0.6):
+    """The same parameters for the library (float) and the oracle (the float
+    values widened to double)."""
+    gp = tm.make_params(n, radii, eps, alpha, ld_min, ld_max, sat)
+    s = len(radii)
+    op = orc.make_params(n, radii, eps=[float(gp.eps[f]) for f in range(s)],
+                         alpha=[float(gp.alpha[f]) for f in range(s)], ld_min=float(gp.ld_min),
+                         ld_max=float(gp.ld_max), sat=float(gp.sat))
+    return gp, op
+
+
+def run_gpu(img, gp, out_dtype=None, debug=True):
+    x = torch.from_numpy(np.ascontiguousarray(img)).cuda()
+    ctx = tm.tm_create(gp)
+    try:
+        tm.tm_set_debug(ctx, debug)
+        out = torch.empty(x.shape, dtype=out_dtype or torch.float32, device="cuda")
+        tm.tm_forward(ctx, x, out)
+        d = {}
+        if debug:
+            H, W = img.shape[:2]
+            s = gp.n_fields
+            d["range"] = tm.tm_debug_export(ctx, tm.TM_DBG_RANGE).cpu().numpy()
+            d["thr"] = tm.tm_debug_export(ctx, tm.TM_DBG_THRESHOLDS).cpu().numpy() if gp.n_bins > 1 else np.zeros(0, np.float32)
+            d["bins"] = tm.tm_debug_export(ctx, tm.TM_DBG_BINS).cpu().numpy().reshape(H, W)
+            d["cnt"] = tm.tm_debug_export(ctx, tm.TM_DBG_COUNTS).cpu().numpy().view(np.uint32).reshape(s, H, W)
+            d["sigma2"] = tm.tm_debug_export(ctx, tm.TM_DBG_SIGMA2).cpu().numpy().reshape(s, H, W)
+            d["weight"] = tm.tm_debug_export(ctx, tm.TM_DBG_WEIGHT).cpu().numpy().reshape(s, H, W)
+            d["lf"] = tm.tm_debug_export(ctx, tm.TM_DBG_LF).cpu().numpy().reshape(s, H, W)
+            d["l"] = tm.tm_debug_export(ctx, tm.TM_DBG_L).cpu().numpy().reshape(H, W)
+            d["qbits"] = int(tm.tm_debug_export(ctx, tm.TM_DBG_QSHIFT).cpu().numpy()[0])
+        torch.cuda.synchronize()
+        return out.cpu().numpy(), d
+    finally:
+        tm.tm_destroy(ctx)
+
+
+def _sigma2_tol(ref, qbits):
+    # q carries at most ~1 unit of 2^-Q error per pixel (rounding + log2f);
+    # var(l + e) - var(l) <= 2 sigma |e| + |e|^2
+    d = 2.0 ** -qbits
+    return 2.5 * np.sqrt(np.maximum(ref, 0)) * d + 3 * d * d + 2e-6 * ref
+
+
+def assert_out_close(got, ref, rel=REL, floor=FLOOR):
+    err = np.abs(got.astype(np.float64) - ref)
+    tol = rel * np.maximum(np.abs(ref), floor)
+    bad = err > tol
+    assert not bad.any(), (f"{bad.sum()} of {bad.size} outside tolerance; worst err {err.max():.3e} "
+                           f"at ref {ref.ravel()[np.argmax(err)]:.4e}")
+
+
+CASES = [
+    # (H, W, n, radii, seed)
+    (384, 512, 32, [4, 16, 64], 0),      # 512x384, 32 bins, radii 4/16/64
+    (61, 97, 16, [1, 5, 40], 1),         # ragged, last window larger than the image
+    (45, 70, 64, [(3, 1), (0, 7), 12], 2),  # rectangular fields, r = 0 width
+    (33, 40, 256, [2, 9], 3),            # maximum bin count
+    (20, 30, 1, [3], 4),                 # one bin: every count is zero
+]
+
+
+@pytest.mark.parametrize("H,W,n,radii,seed", CASES)
+def test_forward_matches_oracle(orc, H, W, n, radii, seed):
+    img = synth.wdr_image(H, W, seed=seed)
+    gp, op = params_pair(orc, n, radii, eps=[0.1, 0.05, 0.2][: len(radii)],
+                         alpha=[1.0, 0.7, 1.3][: len(radii)], ld_min=0.02, ld_max=0.98)
+    out, d = run_gpu(img, gp)
+    ref, fl = orc.forward(img, op)
+    pre = orc.prepare(img, n)
+    assert d["range"][0] == pre["imin"] and d["range"][1] == pre["imax"]
+    assert np.array_equal(d["thr"], pre["thr"])                 # bin edges, bitwise
+    assert np.array_equal(d["bins"], pre["bins"])               # bin map (Section II-A)
+    assert np.array_equal(d["cnt"], fl.cnt)                     # Eq. 1 numerators
+    tol = _sigma2_tol(fl.sigma2, d["qbits"])
+    assert np.all(np.abs(d["sigma2"] - fl.sigma2) <= tol)        # Eq. 10
+    assert np.allclose(d["lf"], fl.lf, rtol=1e-6, atol=1e-7)     # Eq. 2
+    assert_out_close(d["l"], fl.l)                               # Eq. 3
+    assert_out_close(out, ref)                                   # Eq. 12
+
+
+def test_degenerate_images(orc):
+    gp, op = params_pair(orc, 8, [1, 3], ld_min=0.3)
+    for shape in [(1, 1), (1, 17), (23, 1)]:
+        img = synth.wdr_image(*shape, seed=7)
+        out, d = run_gpu(img, gp)
+        ref, fl = orc.forward(img, op)
+        assert np.array_equal(d["cnt"], fl.cnt)
+        assert_out_close(out, ref)
+    const = np.full((9, 13, 3), 2.5, np.float32)
+    out, d = run_gpu(const, gp)
+    ref, _ = orc.forward(const, op)
+    assert np.all(d["bins"] == 0) and np.all(d["sigma2"] == 0)
+    assert_out_close(out, ref)
+
+
+def test_half_input_and_outputs(orc):
+    img16 = synth.wdr_image(70, 90, seed=5, dtype=np.float16)
+    gp, op = params_pair(orc, 32, [2, 8, 30])
+    ref, _ = orc.forward(img16.astype(np.float32), op)
+    out, _ = run_gpu(img16, gp, out_dtype=torch.float32, debug=False)
+    assert_out_close(out, ref)
+    out16, _ = run_gpu(img16, gp, out_dtype=torch.float16, debug=False)
+    # half output: the rounding to half adds up to half a half-ulp
+    err = np.abs(out16.astype(np.float64) - ref)
+    ulp = np.spacing(np.abs(ref).astype(np.float16)).astype(np.float64)
+    assert np.all(err <= REL * np.maximum(np.abs(ref), FLOOR) + 0.5 * ulp)
+    out8, _ = run_gpu(img16, gp, out_dtype=torch.uint8, debug=False)
+    ref8 = np.floor(255.0 * np.clip(ref, 0, 1) + 0.5)
+    diff = np.abs(out8.astype(np.int64) - ref8)
+    assert diff.max() <= 1 and (diff > 0).mean() <= 1e-4
+
+
+def test_pitched_input_and_repeat_calls(orc):
+    img = synth.wdr_image(40, 50, seed=6)
+    gp, op = params_pair(orc, 16, [2, 6])
+    big = torch.zeros((40, 64, 3), dtype=torch.float32, device="cuda")
+    big[:, :50] = torch.from_numpy(img).cuda()
+    view = big[:, :50]
+    ctx = tm.tm_create(gp)
+    try:
+        outs = []
+        for _ in range(3):  # the range accumulators re-arm between calls
+            o = torch.empty((40, 50, 3), device="cuda")
+            tm.tm_forward(ctx, view, o)
+            outs.append(o.cpu().numpy())
+        img2 = synth.wdr_image(40, 50, seed=60)
+        o2 = torch.empty((40, 50, 3), device="cuda")
+        tm.tm_forward(ctx, torch.from_numpy(img2).cuda(), o2)
+        torch.cuda.synchronize()
+    finally:
+        tm.tm_destroy(ctx)
+    ref, _ = orc.forward(img, op)
+    for o in outs:
+        assert np.array_equal(o, outs[0])
+        assert_out_close(o, ref)
+    ref2, _ = orc.forward(img2, op)
+    assert_out_close(o2.cpu().numpy(), ref2)
+
+
+def test_host_buffers_match_device(orc):
+    img = synth.wdr_image(64, 80, seed=8)
+    gp, op = params_pair(orc, 32, [3, 10])
+    out_dev, _ = run_gpu(img, gp, debug=False)
+    ctx = tm.tm_create(gp)
+    try:
+        out_host = np.empty_like(img)
+        tm.tm_forward_host(ctx, img, out_host)
+    finally:
+        tm.tm_destroy(ctx)
+    assert np.array_equal(out_host, out_dev)
+
+
+def test_integral_image_entry_point_exact(orc):
+    rng = np.random.default_rng(0)
+    for H, W in [(1, 1), (7, 3000), (300, 257), (2500, 5)]:
+        q = rng.integers(-(2 ** 23), 2 ** 23 + 1, size=(H, W)).astype(np.int32)
+        qt = torch.from_numpy(q).cuda()
+        s1 = torch.empty((H + 1, W + 1), dtype=torch.int64, device="cuda")
+        s2 = torch.empty_like(s1)
+        tm.tm_integral_image(qt, s1, s2)
+        torch.cuda.synchronize()
+        r1 = orc.integral_i64(q)
+        r2 = orc.integral_i64(q.astype(np.int64) ** 2)
+        assert np.array_equal(s1.cpu().numpy().view(np.uint64), r1)
+        assert np.array_equal(s2.cpu().numpy().view(np.uint64), r2)
+
+
+def test_integral_histogram_entry_point_exact(orc):
+    rng = np.random.default_rng(1)
+    for H, W, n in [(1, 1, 1), (37, 2100, 5), (129, 64, 64), (9, 11, 256)]:
+        b = rng.integers(0, n, size=(H, W)).astype(np.uint8)
+        bt = torch.from_numpy(b).cuda()
+        hk = torch.empty((n, H + 1, W + 1), dtype=torch.int32, device="cuda")
+        tm.tm_integral_histogram(bt, n, hk)
+        torch.cuda.synchronize()
+        assert np.array_equal(hk.cpu().numpy().view(np.uint32), orc.integral_histogram(b, n))
+
+
+def test_full_size_12mp_sampled(orc):
+    """4000 x 3000, 64 bins, radii 8/32/128: edges and the whole bin map
+    bit-exact; outputs at sampled pixels (corners, borders, interior) against
+    the oracle's direct per-pixel evaluation."""
+    H, W = 3000, 4000
+    img = synth.wdr_image(H, W, seed=1, decades=(-3.0, 5.0))
+    gp, op = params_pair(orc, 64, [8, 32, 128])
+    out, d = run_gpu(img, gp)
+    pre = orc.prepare(img, 64)
+    assert np.array_equal(d["thr"], pre["thr"])
+    assert np.array_equal(d["bins"], pre["bins"])
+    rng = np.random.default_rng(2)
+    ys = np.concatenate([[0, 0, H - 1, H - 1, 127, 128, 129, H - 129], rng.integers(0, H, 120)])
+    xs = np.concatenate([[0, W - 1, 0, W - 1, 4000 - 129, 128, 3, 2000], rng.integers(0, W, 120)])
+    ref, dd = orc.forward_pixels(img, op, xs, ys)
+    assert np.array_equal(d["cnt"][:, ys, xs].T, dd["cnt"])
+    assert_out_close(out[ys, xs], ref)
