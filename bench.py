@@ -267,7 +267,7 @@ def run_ours(args):
         "config": {"workload": wl["name"], "height": H, "width": W, "channels": 3, "input": "float32",
                    "n_bins": wl["n_bins"], "radii": wl["radii"], "parallelism": "replicas",
                    "l2": "inputs larger than L2 (two 144 MB images alternated)",
-                   "hist_path": "materialised"},
+                   "hist_path": "fused" if "fused_sweep" in stages else "materialised"},
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
                      "traffic": traffic, "peak_kind": peak_kind,

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "tm.h"
+#include "tm_fused.cuh"
 #include "tm_kernels.cuh"
 
 using namespace tmk;
@@ -35,6 +36,9 @@ struct tm_ctx {
   DebugPlanes dbg{};
   // stage timing: events recorded on the call's stream after each stage
   int stage_timing = 0;
+  int num_sms = 0;
+  size_t smem_optin = 0;
+  int last_path = 0;  // 1 fused, 2 materialised
   std::vector<std::vector<std::pair<cudaEvent_t, int>>> marks;
   std::vector<cudaEvent_t> event_pool;
   double stage_ms[16] = {};
@@ -185,10 +189,11 @@ DevParams dev_params(const tm_params &p, int qbits) {
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t bins, q, s1, s2, iscr, cpl, hscr, dcnt, dvar, dw, dlf, dl, total;
+  size_t bins, q, s1, s2, iscr, cpl, hscr, cring, dcnt, dvar, dw, dlf, dl, total;
 };
 
-Layout plan(const tm_params &p, int W, int H, bool debug, bool materialised) {
+Layout plan(const tm_params &p, int W, int H, bool debug, bool materialised,
+            size_t cring_elems) {
   Layout L{};
   const size_t N = (size_t)W * H;
   const size_t plane = (size_t)(W + 1) * (H + 1);
@@ -204,6 +209,7 @@ Layout plan(const tm_params &p, int W, int H, bool debug, bool materialised) {
     L.cpl = take(4 * plane * (size_t)(p.n_bins - 1));
     L.hscr = take(4 * hist_scratch_elems(W, H, p.n_bins - 1));
   }
+  if (!materialised) L.cring = take(2 * cring_elems);
   if (debug) {
     L.dcnt = take(4 * N * s);
     L.dvar = take(4 * N * s);
@@ -213,6 +219,17 @@ Layout plan(const tm_params &p, int W, int H, bool debug, bool materialised) {
   }
   L.total = off;
   return L;
+}
+
+tm_status ensure_device_info(tm_ctx *c) {
+  if (c->num_sms) return TM_OK;
+  int dev = 0, v = 0;
+  TM_CUDA(c, cudaGetDevice(&dev));
+  TM_CUDA(c, cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+  c->num_sms = v;
+  TM_CUDA(c, cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  c->smem_optin = (size_t)v;
+  return TM_OK;
 }
 
 tm_status ensure_stats(tm_ctx *c) {
@@ -262,14 +279,19 @@ tm_status check_launch(tm_ctx *c, const char *what) {
 // The forward launch sequence on one image (device buffers already checked).
 tm_status forward_device(tm_ctx *c, const tm_image *in, const tm_image *out, cudaStream_t s) {
   const int W = in->width, H = in->height;
-  const bool materialised = true;
   tm_status st = ensure_stats(c);
   if (st) return st;
-  Layout L = plan(c->p, W, H, c->debug != 0, materialised);
-  if ((st = ensure_ws(c, L.total))) return st;
-  char *ws = static_cast<char *>(c->ws);
+  if ((st = ensure_device_info(c))) return st;
   const int qbits = choose_qbits(c->p, W, H);
   const DevParams P = dev_params(c->p, qbits);
+  SweepPlan SP{};
+  bool fused = c->hist_path != 2 && c->p.n_bins > 1 &&
+               plan_sweep(P, W, H, c->num_sms, c->smem_optin - 1024, SP);
+  if (c->hist_path == 1 && !fused && c->p.n_bins > 1)
+    return fail(c, TM_EUNSUPPORTED, "fused sweep does not fit these fields (use the materialised path)");
+  Layout L = plan(c->p, W, H, c->debug != 0, !fused, fused ? sweep_count_elems(SP) : 0);
+  if ((st = ensure_ws(c, L.total))) return st;
+  char *ws = static_cast<char *>(c->ws);
   const Image iin = to_image(in), iout = to_image(out);
   uint8_t *bins = reinterpret_cast<uint8_t *>(ws + L.bins);
   int32_t *q = reinterpret_cast<int32_t *>(ws + L.q);
@@ -293,16 +315,27 @@ tm_status forward_device(tm_ctx *c, const tm_image *in, const tm_image *out, cud
   mark(c, s, ST_PREP);
   n += launch_integral_image(q, W, H, s1, s2, reinterpret_cast<int64_t *>(ws + L.iscr), s);
   mark(c, s, ST_INTEGRAL);
-  uint32_t *cpl = nullptr;
-  if (c->p.n_bins > 1) {
-    cpl = reinterpret_cast<uint32_t *>(ws + L.cpl);
-    n += launch_integral_histogram(bins, W, H, c->p.n_bins, true, cpl,
-                                   reinterpret_cast<uint32_t *>(ws + L.hscr), s);
+  if (fused) {
+    uint16_t *counts = reinterpret_cast<uint16_t *>(ws + L.cring);
+    const int ls = launch_sweep(P, SP, bins, counts, s);
+    if (ls < 0) return check_launch(c, "sweep shared-memory attribute");
+    n += ls;
+    mark(c, s, ST_SWEEP);
+    n += launch_lookup_counts(iin, iout, P, SP, counts, s1, s2, dbg, s);
+    mark(c, s, ST_LOOKUP);
+  } else {
+    uint32_t *cpl = nullptr;
+    if (c->p.n_bins > 1) {
+      cpl = reinterpret_cast<uint32_t *>(ws + L.cpl);
+      n += launch_integral_histogram(bins, W, H, c->p.n_bins, true, cpl,
+                                     reinterpret_cast<uint32_t *>(ws + L.hscr), s);
+    }
+    mark(c, s, ST_HIST);
+    n += launch_lookup_materialised(iin, iout, P, bins, cpl, s1, s2, dbg, s);
+    mark(c, s, ST_LOOKUP);
   }
-  mark(c, s, ST_HIST);
-  n += launch_lookup_materialised(iin, iout, P, bins, cpl, s1, s2, dbg, s);
-  mark(c, s, ST_LOOKUP);
   if ((st = check_launch(c, "forward launch"))) return st;
+  c->last_path = fused ? 1 : 2;
   c->launches = n;
   c->last_W = W;
   c->last_H = H;

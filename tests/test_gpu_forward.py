@@ -42,11 +42,12 @@ def params_pair(orc, n, radii, eps=0.1, alpha=1.0, ld_min=0.0, ld_max=1.0, sat=0
     return gp, op
 
 
-def run_gpu(img, gp, out_dtype=None, debug=True):
+def run_gpu(img, gp, out_dtype=None, debug=True, path=0):
     x = torch.from_numpy(np.ascontiguousarray(img)).cuda()
     ctx = tm.tm_create(gp)
     try:
         tm.tm_set_debug(ctx, debug)
+        tm.tm_set_option(ctx, tm.TM_OPT_HIST_PATH, path)
         out = torch.empty(x.shape, dtype=out_dtype or torch.float32, device="cuda")
         tm.tm_forward(ctx, x, out)
         d = {}
@@ -93,12 +94,16 @@ CASES = [
 ]
 
 
+PATHS = [1, 2]  # fused sweep, materialised integral histogram
+
+
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("H,W,n,radii,seed", CASES)
-def test_forward_matches_oracle(orc, H, W, n, radii, seed):
+def test_forward_matches_oracle(orc, H, W, n, radii, seed, path):
     img = synth.wdr_image(H, W, seed=seed)
     gp, op = params_pair(orc, n, radii, eps=[0.1, 0.05, 0.2][: len(radii)],
                          alpha=[1.0, 0.7, 1.3][: len(radii)], ld_min=0.02, ld_max=0.98)
-    out, d = run_gpu(img, gp)
+    out, d = run_gpu(img, gp, path=path)
     ref, fl = orc.forward(img, op)
     pre = orc.prepare(img, n)
     assert d["range"][0] == pre["imin"] and d["range"][1] == pre["imax"]
@@ -112,16 +117,17 @@ def test_forward_matches_oracle(orc, H, W, n, radii, seed):
     assert_out_close(out, ref)                                   # Eq. 12
 
 
-def test_degenerate_images(orc):
+@pytest.mark.parametrize("path", PATHS)
+def test_degenerate_images(orc, path):
     gp, op = params_pair(orc, 8, [1, 3], ld_min=0.3)
-    for shape in [(1, 1), (1, 17), (23, 1)]:
+    for shape in [(1, 1), (1, 17), (23, 1), (2, 2)]:
         img = synth.wdr_image(*shape, seed=7)
-        out, d = run_gpu(img, gp)
+        out, d = run_gpu(img, gp, path=path)
         ref, fl = orc.forward(img, op)
         assert np.array_equal(d["cnt"], fl.cnt)
         assert_out_close(out, ref)
     const = np.full((9, 13, 3), 2.5, np.float32)
-    out, d = run_gpu(const, gp)
+    out, d = run_gpu(const, gp, path=path)
     ref, _ = orc.forward(const, op)
     assert np.all(d["bins"] == 0) and np.all(d["sigma2"] == 0)
     assert_out_close(out, ref)
@@ -208,6 +214,17 @@ def test_integral_histogram_entry_point_exact(orc):
         tm.tm_integral_histogram(bt, n, hk)
         torch.cuda.synchronize()
         assert np.array_equal(hk.cpu().numpy().view(np.uint32), orc.integral_histogram(b, n))
+
+
+def test_big_window_slabs_and_tile_edges(orc):
+    """Windows over 2^16 pixels are split into row slabs; tiles leave ragged
+    edges. 600 x 700, radii 5/40/150 (301 x 301 > 2^16), 24 bins."""
+    img = synth.wdr_image(600, 700, seed=13)
+    gp, op = params_pair(orc, 24, [5, 40, (150, 150)])
+    out, d = run_gpu(img, gp, path=1)
+    ref, fl = orc.forward(img, op)
+    assert np.array_equal(d["cnt"], fl.cnt)
+    assert_out_close(out, ref)
 
 
 def test_full_size_12mp_sampled(orc):
