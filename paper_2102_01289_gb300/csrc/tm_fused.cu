@@ -92,7 +92,8 @@ __global__ void __launch_bounds__(kNT, 1)
     k_sweep(DevParams P, SweepPlan S, const uint8_t *__restrict__ bins, uint16_t *__restrict__ counts) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Smem sm = carve(S, smem_raw);
-  __shared__ int evt[2 * kMaxSlabs][4];  // per event of the row: valid, acc, bring, rx
+  // per event of the row (double-buffered by row parity): row, acc offset, bring offset, rx
+  __shared__ int evt_buf[2][2 * kMaxSlabs][4];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int W = S.W, H = S.H;
   const long long N = (long long)W * H;
@@ -147,6 +148,22 @@ __global__ void __launch_bounds__(kNT, 1)
   for (int t = tid; t < nw; t += kNT) sm.m[t] = 0u;
   for (int y = Y0; y < min(Y1, rL + S.Ry + 2); ++y)
     for (int x = tid; x < TXc; x += kNT) sm.bring[(y % S.BR) * S.TX + x] = bins[(long long)y * W + X0 + x];
+  // per-event constants and ring positions, one thread per event: event e is
+  // slab e/2, top corner (e even) or bottom corner (e odd); its pixel row
+  // advances by one per swept row, so its ring slots advance by one too
+  int ev_a = 0, ev_b = 0, ev_roff = 0, ev_rlen = 1, ev_rx = 0, ev_y = 0, ev_slot = 0, ev_bslot = 0;
+  if (tid < ne) {
+    const int s = tid >> 1;
+    ev_a = S.slab_a[s];
+    ev_b = S.slab_b[s];
+    ev_roff = S.ring_off[s];
+    ev_rlen = S.ring_len[s];
+    ev_rx = P.rx[S.slab_field[s]];
+    ev_y = (tid & 1) ? rL - ev_b : rL - ev_a + 1;  // pixel row of the event at v = rL
+    ev_slot = ((ev_y % ev_rlen) + ev_rlen) % ev_rlen;
+    ev_bslot = ((ev_y % S.BR) + S.BR) % S.BR;
+  }
+  int yn_slot = ((rL + S.Ry + 2) % S.BR + S.BR) % S.BR;  // bring slot of the row entering at rL+1
   // bins of the first swept row and of the pixel row entering with it
   int pb = 255, pn = 0;
   if (rL + 1 <= rR) {
@@ -163,7 +180,8 @@ __global__ void __launch_bounds__(kNT, 1)
       uint8_t *bw = reinterpret_cast<uint8_t *>(sm.brow);
       if (tid < nseg * kSeg) bw[tid + 4 * (tid >> 4)] = tid < ncol ? (uint8_t)pb : (uint8_t)255;
       const int yn = v + S.Ry + 1;
-      if (yn >= Y0 && yn < Y1 && tid < TXc) sm.bring[(yn % S.BR) * S.TX + tid] = (uint8_t)pn;
+      if (yn >= Y0 && yn < Y1 && tid < TXc) sm.bring[yn_slot * S.TX + tid] = (uint8_t)pn;
+      yn_slot = yn_slot + 1 == S.BR ? 0 : yn_slot + 1;
       if (v + 1 <= rR) {
         if (tid < ncol) pb = __ldg(bins + (long long)(v + 1) * W + cL + 1 + tid);
         if (yn + 1 >= Y0 && yn + 1 < Y1 && tid < TXc) pn = __ldg(bins + (long long)(yn + 1) * W + X0 + tid);
@@ -171,19 +189,23 @@ __global__ void __launch_bounds__(kNT, 1)
       const int lo = sm.rowlo[v - rL - 1], hi = sm.rowhi[v - rL - 1];
       const int j0 = min(nw, max(0, (lo - kmin) >> 1));
       const int j1 = min(nw, max(j0, (hi - kmin + 1) >> 1));
-      for (int j = j1 + tid; j < nw; j += kNT) sm.m[j] += 0x10001u;
-      if (!burst && tid < ne) {
-        const int s = tid >> 1, bottom = tid & 1;
-        const int a = S.slab_a[s], bb = S.slab_b[s];
-        const int y = bottom ? v - bb : v - a + 1;
-        const int T = max(y + a - 1, -1), B = min(y + bb, H - 1);
-        const bool valid = y >= Y0 && y < Y1 && B > T;
-        evt[tid][0] = valid ? y : -1;
-        evt[tid][1] = valid ? (S.ring_off[s] + y % S.ring_len[s]) * S.TX : 0;
-        evt[tid][2] = valid ? (y % S.BR) * S.TX : 0;
-        evt[tid][3] = P.rx[S.slab_field[s]];
+      int (*evt)[4] = evt_buf[v & 1];
+      if (tid < ne) {
+        ++ev_y;
+        ev_slot = ev_slot + 1 == ev_rlen ? 0 : ev_slot + 1;
+        ev_bslot = ev_bslot + 1 == S.BR ? 0 : ev_bslot + 1;
+        if (!burst) {
+          const int T = max(ev_y + ev_a - 1, -1), B = min(ev_y + ev_b, H - 1);
+          const bool valid = ev_y >= Y0 && ev_y < Y1 && B > T;
+          evt[tid][0] = valid ? ev_y : -1;
+          evt[tid][1] = (ev_roff + ev_slot) * S.TX;
+          evt[tid][2] = ev_bslot * S.TX;
+          evt[tid][3] = ev_rx;
+        }
       }
       __syncthreads();
+      // rows entirely below a threshold pair only bump its row count
+      for (int j = j1 + tid; j < nw; j += kNT) sm.m[j] += 0x10001u;
       // ---- dense words: one warp per word, one lane per segment ----
       for (int j = j0 + wid; j < j1; j += kWarps) {
         const int klo = kmin + 1 + 2 * j;
@@ -219,23 +241,23 @@ __global__ void __launch_bounds__(kNT, 1)
       }
       __syncthreads();
     } else if (!burst) {
+      int (*evt)[4] = evt_buf[v & 1];
       if (tid < ne) {
-        const int s = tid >> 1, bottom = tid & 1;
-        const int a = S.slab_a[s], bb = S.slab_b[s];
-        const int y = bottom ? v - bb : v - a + 1;
-        const int T = max(y + a - 1, -1), B = min(y + bb, H - 1);
-        const bool valid = y >= Y0 && y < Y1 && B > T;
-        evt[tid][0] = valid ? y : -1;
-        evt[tid][1] = valid ? (S.ring_off[s] + y % S.ring_len[s]) * S.TX : 0;
-        evt[tid][2] = valid ? (y % S.BR) * S.TX : 0;
-        evt[tid][3] = P.rx[S.slab_field[s]];
+        const int T = max(ev_y + ev_a - 1, -1), B = min(ev_y + ev_b, H - 1);
+        const bool valid = ev_y >= Y0 && ev_y < Y1 && B > T;
+        evt[tid][0] = valid ? ev_y : -1;
+        evt[tid][1] = (ev_roff + ev_slot) * S.TX;
+        evt[tid][2] = ev_bslot * S.TX;
+        evt[tid][3] = ev_rx;
       }
       __syncthreads();
     }
 
     // ---- corner events of row v: top corners park, bottom corners complete ----
     if (!burst) {
+      int (*evt)[4] = evt_buf[v & 1];
       const int ntask = ne * TXc;
+#pragma unroll 2
       for (int t = tid; t < ntask; t += kNT) {
         const int e = min(__float2int_rz(((float)t + 0.5f) * invTX), ne - 1);
         const int y = evt[e][0];
@@ -298,7 +320,9 @@ __global__ void __launch_bounds__(kNT, 1)
         __syncthreads();  // a burst may park and complete the same slot
       }
     }
-    __syncthreads();
+    // no barrier here: the next row only writes its own bin slots and event
+    // descriptors before its first barrier, which every warp reaches after
+    // finishing this row's events
   }
 }
 

@@ -44,45 +44,55 @@ constexpr int kItems = 8;
 constexpr int kTile = kNT * kItems;
 
 // Row prefixes of q and q^2 into rows 1..H of s1 / s2 (Eq. 5, first pass).
+// Loads and stores go through shared memory so that global accesses are
+// coalesced while each thread scans eight consecutive elements; the shared
+// layouts are padded (9 slots per 8 elements) against bank conflicts.
+__device__ __forceinline__ int pad9(int i) { return (i >> 3) * 9 + (i & 7); }
+
 __global__ void __launch_bounds__(kNT) k_rows_q(const int32_t *__restrict__ q, int W, int H,
                                                 long long *s1, long long *s2) {
-  __shared__ int32_t tile[kTile];
+  __shared__ int32_t tile[kTile / 8 * 9];
+  __shared__ long long out1[kTile / 8 * 9], out2[kTile / 8 * 9];
   __shared__ long long wt1[kNT / 32], wt2[kNT / 32];
   const long long W1 = (long long)W + 1;
-  const int y = blockIdx.x;
-  if (y == 0)
-    for (long long x = threadIdx.x; x < W1; x += kNT) s1[x] = 0, s2[x] = 0;
-  const int32_t *row = q + (long long)y * W;
-  long long *o1 = s1 + (long long)(y + 1) * W1;
-  long long *o2 = s2 + (long long)(y + 1) * W1;
-  if (threadIdx.x == 0) o1[0] = 0, o2[0] = 0;
-  long long carry1 = 0, carry2 = 0;
-  for (int base = 0; base < W; base += kTile) {
-    for (int i = threadIdx.x; i < kTile; i += kNT) tile[i] = base + i < W ? row[base + i] : 0;
-    __syncthreads();
-    long long a1 = 0, a2 = 0, l1[kItems], l2[kItems];
+  for (int y = blockIdx.x; y < H; y += gridDim.x) {
+    if (y == 0)
+      for (long long x = threadIdx.x; x < W1; x += kNT) s1[x] = 0, s2[x] = 0;
+    const int32_t *row = q + (long long)y * W;
+    long long *o1 = s1 + (long long)(y + 1) * W1;
+    long long *o2 = s2 + (long long)(y + 1) * W1;
+    if (threadIdx.x == 0) o1[0] = 0, o2[0] = 0;
+    long long carry1 = 0, carry2 = 0;
+    for (int base = 0; base < W; base += kTile) {
+      for (int i = threadIdx.x; i < kTile; i += kNT) tile[pad9(i)] = base + i < W ? __ldg(row + base + i) : 0;
+      __syncthreads();
+      long long a1 = 0, a2 = 0, l1[kItems], l2[kItems];
 #pragma unroll
-    for (int j = 0; j < kItems; ++j) {
-      long long v = tile[threadIdx.x * kItems + j];
-      a1 += v;
-      a2 += v * v;
-      l1[j] = a1;
-      l2[j] = a2;
-    }
-    long long t1, t2;
-    long long e1 = block_exclusive_scan<long long, kNT>(a1, wt1, t1);
-    long long e2 = block_exclusive_scan<long long, kNT>(a2, wt2, t2);
-#pragma unroll
-    for (int j = 0; j < kItems; ++j) {
-      int x = base + threadIdx.x * kItems + j;
-      if (x < W) {
-        o1[x + 1] = carry1 + e1 + l1[j];
-        o2[x + 1] = carry2 + e2 + l2[j];
+      for (int j = 0; j < kItems; ++j) {
+        const long long v = tile[threadIdx.x * 9 + j];
+        a1 += v;
+        a2 += v * v;
+        l1[j] = a1;
+        l2[j] = a2;
       }
+      long long t1, t2;
+      const long long e1 = block_exclusive_scan<long long, kNT>(a1, wt1, t1) + carry1;
+      const long long e2 = block_exclusive_scan<long long, kNT>(a2, wt2, t2) + carry2;
+#pragma unroll
+      for (int j = 0; j < kItems; ++j) {
+        out1[threadIdx.x * 9 + j] = e1 + l1[j];
+        out2[threadIdx.x * 9 + j] = e2 + l2[j];
+      }
+      __syncthreads();
+      const int n = min(kTile, W - base);
+      for (int i = threadIdx.x; i < n; i += kNT) {
+        o1[base + i + 1] = out1[pad9(i)];
+        o2[base + i + 1] = out2[pad9(i)];
+      }
+      carry1 += t1;
+      carry2 += t2;
+      __syncthreads();
     }
-    carry1 += t1;
-    carry2 += t2;
-    __syncthreads();
   }
 }
 
@@ -94,7 +104,7 @@ __global__ void __launch_bounds__(kNT) k_rows_hist(const uint8_t *__restrict__ b
   __shared__ uint8_t tile[kTile];
   __shared__ unsigned wt[kNT / 32];
   const long long W1 = (long long)W + 1;
-  const int y = blockIdx.x;
+  for (int y = blockIdx.x; y < H; y += gridDim.x) {
   const uint8_t *row = bins + (long long)y * W;
   const int p0 = blockIdx.y * per_block, p1 = min(p0 + per_block, n_planes);
   for (int pl = p0; pl < p1; ++pl) {
@@ -126,6 +136,7 @@ __global__ void __launch_bounds__(kNT) k_rows_hist(const uint8_t *__restrict__ b
       carry += t;
       __syncthreads();
     }
+  }
   }
 }
 
@@ -200,8 +211,8 @@ size_t hist_scratch_elems(int W, int H, int planes) {
 
 int launch_integral_image(const int32_t *q, int W, int H, int64_t *s1, int64_t *s2,
                           int64_t *scratch, cudaStream_t s) {
-  k_rows_q<<<H, kNT, 0, s>>>(q, W, H, reinterpret_cast<long long *>(s1),
-                             reinterpret_cast<long long *>(s2));
+  k_rows_q<<<H < 65535 ? H : 65535, kNT, 0, s>>>(q, W, H, reinterpret_cast<long long *>(s1),
+                                                 reinterpret_cast<long long *>(s2));
   // s1 and s2 are laid out back to back so one column pass covers both
   // one column pass covers both planes: the second is addressed through the
   // element distance between the two (both are 8-byte aligned)
@@ -220,7 +231,7 @@ int launch_integral_histogram(const uint8_t *bins, int W, int H, int n_bins, boo
   if (n_planes <= 0) return 0;
   const long long stride = ((long long)W + 1) * ((long long)H + 1);
   const int per_block = 8;
-  dim3 grid(H, (n_planes + per_block - 1) / per_block);
+  dim3 grid(H < 65535 ? H : 65535, (n_planes + per_block - 1) / per_block);
   k_rows_hist<<<grid, kNT, 0, s>>>(bins, W, H, k_begin, n_planes, per_block, cumulative ? 1 : 0,
                                    planes, stride);
   int nseg, seg_rows;

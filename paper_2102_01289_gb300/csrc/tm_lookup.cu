@@ -52,9 +52,9 @@ __device__ __forceinline__ void finish_pixel(const Image &in, const Image &out, 
   const float L = fuse_fields(P, cnt, area, var, wv, lf);
   float r, g, b;
   load_rgb(in, x, y, r, g, b);
-  const float i = luminance(r, g, b);
-  store_rgb(out, x, y, restore_channel(r, i, P.sat, L), restore_channel(g, i, P.sat, L),
-            restore_channel(b, i, P.sat, L));
+  const float inv_i = __frcp_rn(luminance(r, g, b));
+  store_rgb(out, x, y, restore_channel(r, inv_i, P.sat, L), restore_channel(g, inv_i, P.sat, L),
+            restore_channel(b, inv_i, P.sat, L));
   if (dbg.l) {
     const long long N = (long long)W * H, pix = (long long)y * W + x;
     dbg.l[pix] = L;

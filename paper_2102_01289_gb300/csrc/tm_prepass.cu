@@ -4,27 +4,105 @@
 // compression, Section II-A the n equal-width bins of the log over the
 // image's value range. The range is a global reduction, so the input is read
 // once here to find it and once more by every later stage.
+//
+// Pixels are read four at a time: twelve float samples as three 16-byte loads
+// (or twelve halves as three 8-byte loads) when rows are aligned for it, with
+// a scalar path for ragged row ends and unaligned images.
 #include "tm_kernels.cuh"
 
 namespace tmk {
+namespace {
+
+// Four consecutive pixels of row y starting at x (x + 3 < W), vector loads.
+__device__ __forceinline__ void load4_vec(const Image &im, int x, int y, float r[4], float g[4],
+                                          float b[4]) {
+  const long long o = (long long)y * im.pitch + 3LL * x;
+  float v[12];
+  if (im.dtype == kF16) {
+    const uint2 *p = reinterpret_cast<const uint2 *>(static_cast<const __half *>(im.p) + o);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const uint2 u = __ldg(p + k);
+      const __half2 h0 = *reinterpret_cast<const __half2 *>(&u.x);
+      const __half2 h1 = *reinterpret_cast<const __half2 *>(&u.y);
+      v[4 * k + 0] = __low2float(h0);
+      v[4 * k + 1] = __high2float(h0);
+      v[4 * k + 2] = __low2float(h1);
+      v[4 * k + 3] = __high2float(h1);
+    }
+  } else {
+    const float4 *p = reinterpret_cast<const float4 *>(static_cast<const float *>(im.p) + o);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float4 f = __ldg(p + k);
+      v[4 * k + 0] = f.x;
+      v[4 * k + 1] = f.y;
+      v[4 * k + 2] = f.z;
+      v[4 * k + 3] = f.w;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    r[i] = v[3 * i];
+    g[i] = v[3 * i + 1];
+    b[i] = v[3 * i + 2];
+  }
+}
+
+// Up to four pixels of row y from x (n of them), scalar loads.
+__device__ __forceinline__ void load4_scalar(const Image &im, int x, int y, int n, float r[4],
+                                             float g[4], float b[4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (i < n) load_rgb(im, x + i, y, r[i], g[i], b[i]);
+    else r[i] = g[i] = b[i] = 1.f;
+  }
+}
+
+__device__ __forceinline__ void load4(const Image &im, bool vec, int x, int y, int n, float r[4],
+                                      float g[4], float b[4]) {
+  if (vec && n == 4) load4_vec(im, x, y, r, g, b);
+  else load4_scalar(im, x, y, n, r, g, b);
+}
+
+}  // namespace
 
 // Range of Eq. 11 luminance. Block min/max are folded with unsigned atomics;
 // the last block to finish computes the bin edges and the quantisation
 // constants in double precision, then re-arms the accumulators for the next
 // image, so no host round trip is needed between the stages.
-__global__ void __launch_bounds__(256) k_range(Image in, Stats *st, int n_bins, int qbits) {
+__global__ void __launch_bounds__(256) k_range(Image in, bool vec, Stats *st, int n_bins, int qbits) {
   __shared__ unsigned smin[8], smax[8];
   __shared__ int last;
   unsigned bmin = 0x7f800000u, bmax = 0u;
   const int W = in.W, H = in.H;
-  for (int y = blockIdx.y; y < H; y += gridDim.y)
-    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < W; x += gridDim.x * blockDim.x) {
-      float r, g, b;
-      load_rgb(in, x, y, r, g, b);
-      unsigned v = __float_as_uint(luminance(r, g, b));
-      bmin = min(bmin, v);
-      bmax = max(bmax, v);
+  const int gpr = (W + 3) >> 2;  // groups of four pixels per row
+  const long long ng = (long long)gpr * H;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long g0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; g0 < ng; g0 += 2 * stride) {
+    float r[2][4], gg[2][4], b[2][4];
+    int n[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {  // two groups in flight per thread
+      const long long g = g0 + u * stride;
+      n[u] = 0;
+      if (g < ng) {
+        const int gi = (int)g;  // fewer than 2^31 pixels
+        const int y = gi / gpr, x = (gi - y * gpr) * 4;
+        n[u] = min(4, W - x);
+        load4(in, vec, x, y, n[u], r[u], gg[u], b[u]);
+      }
     }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (i < n[u]) {
+          const unsigned v = __float_as_uint(luminance(r[u][i], gg[u][i], b[u][i]));
+          bmin = min(bmin, v);
+          bmax = max(bmax, v);
+        }
+  }
   bmin = __reduce_min_sync(0xffffffffu, bmin);
   bmax = __reduce_max_sync(0xffffffffu, bmax);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -38,8 +116,8 @@ __global__ void __launch_bounds__(256) k_range(Image in, Stats *st, int n_bins, 
     atomicMin(&st->min_bits, bmin);
     atomicMax(&st->max_bits, bmax);
     __threadfence();
-    unsigned ticket = atomicAdd(&st->blocks_done, 1u);
-    last = (ticket == gridDim.x * gridDim.y - 1);
+    const unsigned ticket = atomicAdd(&st->blocks_done, 1u);
+    last = (ticket == gridDim.x - 1);
   }
   __syncthreads();
   if (!last) return;
@@ -52,15 +130,15 @@ __global__ void __launch_bounds__(256) k_range(Image in, Stats *st, int n_bins, 
   for (int k = 1 + threadIdx.x; k < n_bins; k += blockDim.x) {
     float edge = __int_as_float(0x7f800000);
     if (!degenerate) {
-      double t = exp(lmin + (lmax - lmin) * ((double)k / (double)n_bins));
+      const double t = exp(lmin + (lmax - lmin) * ((double)k / (double)n_bins));
       edge = __double2float_ru(t);  // smallest float >= t
     }
     st->thr[k - 1] = edge;
   }
   if (threadIdx.x == 0) {
-    unsigned bits = __float_as_uint(imin);
+    const unsigned bits = __float_as_uint(imin);
     st->e0 = (int)(bits >> 23) - 127;
-    double m0 = (double)__uint_as_float((bits & 0x7fffffu) | 0x3f800000u);
+    const double m0 = (double)__uint_as_float((bits & 0x7fffffu) | 0x3f800000u);
     st->c0 = (float)log2(m0);
     st->log2_scale =
         degenerate ? 0.f : (float)(ldexp(1.0, qbits) / (log2((double)imax) - log2((double)imin)));
@@ -74,39 +152,72 @@ __global__ void __launch_bounds__(256) k_range(Image in, Stats *st, int n_bins, 
 }
 
 // Bin map (Section II-A, edges from k_range) and quantised normalised log.
-__global__ void __launch_bounds__(256) k_prep(Image in, const Stats *st, int n_bins, int qbits,
-                                               uint8_t *bins, int32_t *q) {
+// One thread per group of four pixels.
+__global__ void __launch_bounds__(256) k_prep(Image in, bool vec, const Stats *st, int n_bins,
+                                               int qbits, uint8_t *bins, int32_t *q) {
   __shared__ float thr[kMaxBins];
-  __shared__ Stats sst;
   for (int k = threadIdx.x; k < n_bins - 1; k += blockDim.x) thr[k] = st->thr[k];
-  if (threadIdx.x == 0) sst = *st;
+  Stats sst;  // only the three constants quantise_log reads
+  sst.c0 = __ldg(&st->c0);
+  sst.e0 = __ldg(&st->e0);
+  sst.log2_scale = __ldg(&st->log2_scale);
   __syncthreads();
   const int W = in.W, H = in.H;
-  for (int y = blockIdx.y; y < H; y += gridDim.y)
-    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < W; x += gridDim.x * blockDim.x) {
-      float r, g, b;
-      load_rgb(in, x, y, r, g, b);
-      float i = luminance(r, g, b);
-      long long o = (long long)y * W + x;
-      bins[o] = (uint8_t)bin_of(i, thr, n_bins);
-      q[o] = quantise_log(i, sst, qbits);
+  const int gpr = (W + 3) >> 2;
+  const int ng = gpr * H;  // fewer than 2^31 pixels
+  for (int gi = blockIdx.x * blockDim.x + threadIdx.x; gi < ng; gi += gridDim.x * blockDim.x) {
+    const int y = gi / gpr, x = (gi - y * gpr) * 4;
+    const int n = min(4, W - x);
+    float r[4], g[4], b[4];
+    load4(in, vec, x, y, n, r, g, b);
+    unsigned bq = 0;
+    int qq[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float l = luminance(r[i], g[i], b[i]);
+      bq |= (unsigned)bin_of(l, thr, n_bins) << (8 * i);
+      qq[i] = quantise_log(l, sst, qbits);
     }
+    const long long o = (long long)y * W + x;
+    if (n == 4 && (o & 3) == 0) {
+      *reinterpret_cast<unsigned *>(bins + o) = bq;
+      *reinterpret_cast<int4 *>(q + o) = make_int4(qq[0], qq[1], qq[2], qq[3]);
+    } else {
+      for (int i = 0; i < n; ++i) {
+        bins[o + i] = (uint8_t)(bq >> (8 * i));
+        q[o + i] = qq[i];
+      }
+    }
+  }
+}
+
+// Rows of `im` can be read with the vector loads above.
+bool vec_ok(const Image &im) {
+  const size_t es = im.dtype == kF16 ? 2 : 4;
+  const size_t align = im.dtype == kF16 ? 8 : 16;
+  return ((uintptr_t)im.p % align) == 0 && ((size_t)im.pitch * es) % align == 0;
 }
 
 void launch_range(const Image &in, Stats *st, int n_bins, int qbits, cudaStream_t s) {
-  dim3 block(256);
-  int gx = (in.W + 255) / 256;
-  int gy = in.H < 1024 ? in.H : 1024;
-  while ((long long)gx * gy > 4096 && gy > 1) gy = (gy + 1) / 2;
-  k_range<<<dim3(gx, gy), block, 0, s>>>(in, st, n_bins, qbits);
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long groups = (long long)((in.W + 3) / 4) * in.H;
+  long long blocks = (groups + 511) / 512;
+  blocks = blocks < 1 ? 1 : blocks;
+  if (blocks > 4LL * sms) blocks = 4LL * sms;
+  k_range<<<(int)blocks, 256, 0, s>>>(in, vec_ok(in), st, n_bins, qbits);
 }
 
-void launch_prep(const Image &in, const Stats *st, int n_bins, int qbits, uint8_t *bins,
-                 int32_t *q, cudaStream_t s) {
-  dim3 block(256);
-  int gx = (in.W + 255) / 256;
-  int gy = in.H < 2048 ? in.H : 2048;
-  k_prep<<<dim3(gx, gy), block, 0, s>>>(in, st, n_bins, qbits, bins, q);
+void launch_prep(const Image &in, const Stats *st, int n_bins, int qbits, uint8_t *bins, int32_t *q,
+                 cudaStream_t s) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long groups = (long long)((in.W + 3) / 4) * in.H;
+  long long blocks = (groups + 255) / 256;
+  if (blocks > 16LL * sms) blocks = 16LL * sms;
+  k_prep<<<(int)(blocks < 1 ? 1 : blocks), 256, 0, s>>>(in, vec_ok(in), st, n_bins, qbits, bins, q);
 }
 
 }  // namespace tmk
