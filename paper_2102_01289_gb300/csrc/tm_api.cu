@@ -1,6 +1,7 @@
 // tm_api.cu -- the C ABI declared in include/tm.h: parameter validation,
 // context and workspace management, and the launch sequences of the forward
 // path. Every entry point validates on the host before issuing GPU work.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -11,7 +12,6 @@
 #include <vector>
 
 #include "tm.h"
-#include "tm_fused.cuh"
 #include "tm_kernels.cuh"
 
 using namespace tmk;
@@ -22,23 +22,34 @@ struct tm_ctx {
   int debug = 0;
   int hist_path = 0;
   int64_t launches = 0;
-  // device workspace (grown on demand)
+  int num_sms = 0;
+  size_t smem_optin = 0;
+  // device workspace (grown on demand; growing drops the cached graph)
   void *ws = nullptr;
   size_t ws_bytes = 0;
-  Stats *stats = nullptr;
+  Stats *stats = nullptr;  // one per image of the largest batch so far
+  int stats_n = 0;
+  Job *djobs = nullptr;    // device copy of the job array
+  int2 *ditems = nullptr;  // device copy of the sweep queue
+  size_t djobs_bytes = 0, ditems_bytes = 0;
+  Job *hjobs = nullptr;    // pinned host staging of the job array
+  int2 *hitems = nullptr;  // pinned host staging of the sweep queue
+  size_t hjobs_bytes = 0, hitems_bytes = 0;
   // staging for tm_forward_host
   void *stage = nullptr;
   size_t stage_bytes = 0;
-  // layout of the last forward (for debug exports)
-  int last_W = 0, last_H = 0, last_q = 0;
+  // layout of the last single-image forward (for debug exports)
+  int last_W = 0, last_H = 0, last_q = 0, last_path = 0;
   uint8_t *bins = nullptr;
   int32_t *q = nullptr;
   DebugPlanes dbg{};
+  // CUDA graph of the last batch, replayed while the batch is unchanged
+  cudaGraphExec_t graph = nullptr;
+  std::vector<tm_image> graph_in, graph_out;
+  cudaStream_t graph_stream = nullptr;
+  int64_t graph_launches = 0;
   // stage timing: events recorded on the call's stream after each stage
   int stage_timing = 0;
-  int num_sms = 0;
-  size_t smem_optin = 0;
-  int last_path = 0;  // 1 fused, 2 materialised
   std::vector<std::vector<std::pair<cudaEvent_t, int>>> marks;
   std::vector<cudaEvent_t> event_pool;
   double stage_ms[16] = {};
@@ -188,39 +199,6 @@ DevParams dev_params(const tm_params &p, int qbits) {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-struct Layout {
-  size_t bins, q, s1, s2, iscr, cpl, hscr, cring, dcnt, dvar, dw, dlf, dl, total;
-};
-
-Layout plan(const tm_params &p, int W, int H, bool debug, bool materialised,
-            size_t cring_elems) {
-  Layout L{};
-  const size_t N = (size_t)W * H;
-  const size_t plane = (size_t)(W + 1) * (H + 1);
-  const int s = p.n_fields;
-  size_t off = 0;
-  auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
-  L.bins = take(N);
-  L.q = take(4 * N);
-  L.s1 = take(8 * plane);
-  L.s2 = take(8 * plane);
-  L.iscr = take(8 * integral_scratch_elems(W, H));
-  if (materialised && p.n_bins > 1) {
-    L.cpl = take(4 * plane * (size_t)(p.n_bins - 1));
-    L.hscr = take(4 * hist_scratch_elems(W, H, p.n_bins - 1));
-  }
-  if (!materialised) L.cring = take(2 * cring_elems);
-  if (debug) {
-    L.dcnt = take(4 * N * s);
-    L.dvar = take(4 * N * s);
-    L.dw = take(4 * N * s);
-    L.dlf = take(4 * N * s);
-    L.dl = take(4 * N);
-  }
-  L.total = off;
-  return L;
-}
-
 tm_status ensure_device_info(tm_ctx *c) {
   if (c->num_sms) return TM_OK;
   int dev = 0, v = 0;
@@ -232,31 +210,66 @@ tm_status ensure_device_info(tm_ctx *c) {
   return TM_OK;
 }
 
-tm_status ensure_stats(tm_ctx *c) {
-  if (c->stats) return TM_OK;
-  Stats h{};
-  h.min_bits = 0x7f800000u;
-  h.max_bits = 0u;
-  h.blocks_done = 0u;
-  TM_CUDA(c, cudaMalloc(&c->stats, sizeof(Stats)));
-  TM_CUDA(c, cudaMemcpy(c->stats, &h, sizeof(Stats), cudaMemcpyHostToDevice));
+void drop_graph(tm_ctx *c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+  c->graph_in.clear();
+  c->graph_out.clear();
+}
+
+tm_status ensure_stats(tm_ctx *c, int n) {
+  if (c->stats_n >= n) return TM_OK;
+  drop_graph(c);
+  if (c->stats) {
+    TM_CUDA(c, cudaDeviceSynchronize());
+    cudaFree(c->stats);
+    c->stats = nullptr;
+    c->stats_n = 0;
+  }
+  std::vector<Stats> h((size_t)n);
+  for (auto &st : h) {
+    memset(&st, 0, sizeof st);
+    st.min_bits = 0x7f800000u;
+  }
+  TM_CUDA(c, cudaMalloc(&c->stats, sizeof(Stats) * (size_t)n));
+  TM_CUDA(c, cudaMemcpy(c->stats, h.data(), sizeof(Stats) * (size_t)n, cudaMemcpyHostToDevice));
+  c->stats_n = n;
   return TM_OK;
 }
 
-tm_status ensure_ws(tm_ctx *c, size_t bytes) {
-  if (c->ws_bytes >= bytes) return TM_OK;
-  if (c->ws) {
+tm_status grow_device(tm_ctx *c, void **p, size_t *have, size_t bytes) {
+  if (*have >= bytes) return TM_OK;
+  drop_graph(c);
+  if (*p) {
     TM_CUDA(c, cudaDeviceSynchronize());
-    cudaFree(c->ws);
-    c->ws = nullptr;
-    c->ws_bytes = 0;
+    cudaFree(*p);
+    *p = nullptr;
+    *have = 0;
   }
-  cudaError_t e = cudaMalloc(&c->ws, bytes);
+  cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    return fail(c, TM_ENOMEM, "workspace of %zu bytes: %s", bytes, cudaGetErrorString(e));
+    return fail(c, TM_ENOMEM, "device allocation of %zu bytes: %s", bytes, cudaGetErrorString(e));
   }
-  c->ws_bytes = bytes;
+  *have = bytes;
+  return TM_OK;
+}
+
+tm_status grow_pinned(tm_ctx *c, void **p, size_t *have, size_t bytes) {
+  if (*have >= bytes) return TM_OK;
+  drop_graph(c);
+  if (*p) {
+    TM_CUDA(c, cudaDeviceSynchronize());
+    cudaFreeHost(*p);
+    *p = nullptr;
+    *have = 0;
+  }
+  cudaError_t e = cudaMallocHost(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, TM_ENOMEM, "pinned allocation of %zu bytes: %s", bytes, cudaGetErrorString(e));
+  }
+  *have = bytes;
   return TM_OK;
 }
 
@@ -276,74 +289,282 @@ tm_status check_launch(tm_ctx *c, const char *what) {
   return TM_OK;
 }
 
-// The forward launch sequence on one image (device buffers already checked).
-tm_status forward_device(tm_ctx *c, const tm_image *in, const tm_image *out, cudaStream_t s) {
-  const int W = in->width, H = in->height;
-  tm_status st = ensure_stats(c);
-  if (st) return st;
-  if ((st = ensure_device_info(c))) return st;
-  const int qbits = choose_qbits(c->p, W, H);
-  const DevParams P = dev_params(c->p, qbits);
-  SweepPlan SP{};
-  bool fused = c->hist_path != 2 && c->p.n_bins > 1 &&
-               plan_sweep(P, W, H, c->num_sms, c->smem_optin - 1024, SP);
-  if (c->hist_path == 1 && !fused && c->p.n_bins > 1)
-    return fail(c, TM_EUNSUPPORTED, "fused sweep does not fit these fields (use the materialised path)");
-  Layout L = plan(c->p, W, H, c->debug != 0, !fused, fused ? sweep_count_elems(SP) : 0);
-  if ((st = ensure_ws(c, L.total))) return st;
-  char *ws = static_cast<char *>(c->ws);
-  const Image iin = to_image(in), iout = to_image(out);
-  uint8_t *bins = reinterpret_cast<uint8_t *>(ws + L.bins);
-  int32_t *q = reinterpret_cast<int32_t *>(ws + L.q);
-  int64_t *s1 = reinterpret_cast<int64_t *>(ws + L.s1);
-  int64_t *s2 = reinterpret_cast<int64_t *>(ws + L.s2);
-  DebugPlanes dbg{};
-  if (c->debug) {
-    dbg.cnt = reinterpret_cast<unsigned *>(ws + L.dcnt);
-    dbg.sigma2 = reinterpret_cast<float *>(ws + L.dvar);
-    dbg.weight = reinterpret_cast<float *>(ws + L.dw);
-    dbg.lf = reinterpret_cast<float *>(ws + L.dlf);
-    dbg.l = reinterpret_cast<float *>(ws + L.dl);
+bool same_images(const std::vector<tm_image> &a, const tm_image *b, int n) {
+  if ((int)a.size() != n) return false;
+  for (int i = 0; i < n; ++i)
+    if (a[i].data != b[i].data || a[i].width != b[i].width || a[i].height != b[i].height ||
+        a[i].pitch != b[i].pitch || a[i].dtype != b[i].dtype)
+      return false;
+  return true;
+}
+
+// Per-image sizes of the forward workspace.
+struct JobLayout {
+  size_t bins, q, s1, s2, segtot, counts, dcnt, dvar, dw, dlf, dl, total;
+};
+
+JobLayout job_layout(const tm_params &p, int W, int H, int nseg, size_t count_elems, bool debug) {
+  JobLayout L{};
+  const size_t N = (size_t)W * H;
+  const size_t plane = (size_t)(W + 1) * (H + 1);
+  const int s = p.n_fields;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
+  L.bins = take(N);
+  L.q = take(4 * N);
+  L.s1 = take(8 * plane);
+  L.s2 = take(8 * plane);
+  L.segtot = take(8 * 2 * (size_t)nseg * (W + 1));
+  L.counts = take(2 * count_elems);
+  if (debug) {
+    L.dcnt = take(4 * N * s);
+    L.dvar = take(4 * N * s);
+    L.dw = take(4 * N * s);
+    L.dlf = take(4 * N * s);
+    L.dl = take(4 * N);
   }
+  L.total = off;
+  return L;
+}
+
+// The materialised path for one image: range, bins, integral images,
+// bin-major cumulative integral histogram, lookup. Used when the fused sweep
+// does not fit the fields, or on request (TM_OPT_HIST_PATH = 2).
+tm_status forward_materialised(tm_ctx *c, const tm_image *in, const tm_image *out, cudaStream_t s) {
+  const int W = in->width, H = in->height;
+  const int qbits = choose_qbits(c->p, W, H);
+  DevParams P = dev_params(c->p, qbits);
+  int nseg, seg_rows;
+  column_segments(W, H, 2, nseg, seg_rows);
+  JobLayout L = job_layout(c->p, W, H, nseg, 0, c->debug != 0);
+  const size_t plane = (size_t)(W + 1) * (H + 1);
+  size_t off_cpl = align256(L.total), off_hscr = 0, total = off_cpl;
+  if (c->p.n_bins > 1) {
+    total = off_cpl + align256(4 * plane * (size_t)(c->p.n_bins - 1));
+    off_hscr = total;
+    total += align256(4 * hist_scratch_elems(W, H, c->p.n_bins - 1));
+  }
+  tm_status st;
+  if ((st = ensure_stats(c, 1))) return st;
+  if ((st = grow_device(c, &c->ws, &c->ws_bytes, total))) return st;
+  if ((st = grow_device(c, (void **)&c->djobs, &c->djobs_bytes, sizeof(Job)))) return st;
+  if ((st = grow_pinned(c, (void **)&c->hjobs, &c->hjobs_bytes, sizeof(Job)))) return st;
+  char *ws = static_cast<char *>(c->ws);
+  Job J{};
+  J.in = to_image(in);
+  J.out = to_image(out);
+  J.st = c->stats;
+  J.bins = reinterpret_cast<uint8_t *>(ws + L.bins);
+  J.q = reinterpret_cast<int32_t *>(ws + L.q);
+  J.s1 = reinterpret_cast<long long *>(ws + L.s1);
+  J.s2 = reinterpret_cast<long long *>(ws + L.s2);
+  J.segtot = reinterpret_cast<long long *>(ws + L.segtot);
+  J.qbits = qbits;
+  J.nseg = nseg;
+  J.seg_rows = seg_rows;
+  if (c->debug) {
+    J.dbg.cnt = reinterpret_cast<unsigned *>(ws + L.dcnt);
+    J.dbg.sigma2 = reinterpret_cast<float *>(ws + L.dvar);
+    J.dbg.weight = reinterpret_cast<float *>(ws + L.dw);
+    J.dbg.lf = reinterpret_cast<float *>(ws + L.dlf);
+    J.dbg.l = reinterpret_cast<float *>(ws + L.dl);
+  }
+  const int rb = range_blocks(W, H, c->num_sms, 1.0), pb = prep_blocks(W, H, c->num_sms, 1.0);
+  const int cb = col_blocks(W, nseg);
+  J.b0[kStRange] = J.b0[kStPrep] = J.b0[kStRows] = J.b0[kStCols] = J.b0[kStLook] = 0;
+  drop_graph(c);  // the staging below is what a cached graph copies
+  *c->hjobs = J;
+  TM_CUDA(c, cudaMemcpyAsync(c->djobs, c->hjobs, sizeof(Job), cudaMemcpyHostToDevice, s));
   int64_t n = 0;
   mark(c, s, -1);
-  launch_range(iin, c->stats, c->p.n_bins, qbits, s);
-  n += 1;
+  launch_range(c->djobs, 1, rb, c->p.n_bins, s);
   mark(c, s, ST_RANGE);
-  launch_prep(iin, c->stats, c->p.n_bins, qbits, bins, q, s);
-  n += 1;
+  launch_prep(c->djobs, 1, pb, c->p.n_bins, s);
   mark(c, s, ST_PREP);
-  n += launch_integral_image(q, W, H, s1, s2, reinterpret_cast<int64_t *>(ws + L.iscr), s);
+  n += 2 + launch_integral_jobs(c->djobs, 1, H, cb, nseg > 1, s);
   mark(c, s, ST_INTEGRAL);
-  if (fused) {
-    uint16_t *counts = reinterpret_cast<uint16_t *>(ws + L.cring);
-    const int ls = launch_sweep(P, SP, bins, counts, s);
-    if (ls < 0) return check_launch(c, "sweep shared-memory attribute");
-    n += ls;
-    mark(c, s, ST_SWEEP);
-    n += launch_lookup_counts(iin, iout, P, SP, counts, s1, s2, dbg, s);
-    mark(c, s, ST_LOOKUP);
-  } else {
-    uint32_t *cpl = nullptr;
-    if (c->p.n_bins > 1) {
-      cpl = reinterpret_cast<uint32_t *>(ws + L.cpl);
-      n += launch_integral_histogram(bins, W, H, c->p.n_bins, true, cpl,
-                                     reinterpret_cast<uint32_t *>(ws + L.hscr), s);
-    }
-    mark(c, s, ST_HIST);
-    n += launch_lookup_materialised(iin, iout, P, bins, cpl, s1, s2, dbg, s);
-    mark(c, s, ST_LOOKUP);
+  uint32_t *cpl = nullptr;
+  if (c->p.n_bins > 1) {
+    cpl = reinterpret_cast<uint32_t *>(ws + off_cpl);
+    n += launch_integral_histogram(J.bins, W, H, c->p.n_bins, true, cpl,
+                                   reinterpret_cast<uint32_t *>(ws + off_hscr), s);
   }
+  mark(c, s, ST_HIST);
+  n += launch_lookup_materialised(J.in, J.out, P, J.bins, cpl, reinterpret_cast<int64_t *>(J.s1),
+                                  reinterpret_cast<int64_t *>(J.s2), J.dbg, s);
+  mark(c, s, ST_LOOKUP);
   if ((st = check_launch(c, "forward launch"))) return st;
-  c->last_path = fused ? 1 : 2;
   c->launches = n;
   c->last_W = W;
   c->last_H = H;
   c->last_q = qbits;
-  c->bins = bins;
-  c->q = q;
-  c->dbg = dbg;
+  c->last_path = 2;
+  c->bins = J.bins;
+  c->q = J.q;
+  c->dbg = J.dbg;
   return TM_OK;
+}
+
+// The fused path over a batch of images: one launch per stage for the whole
+// batch, the sweep as a persistent kernel over a queue of (image, tile)
+// items. `graph`: capture the batch into a CUDA graph and replay it while the
+// batch is unchanged. Returns TM_EUNSUPPORTED if some image cannot be swept.
+tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image *out, cudaStream_t s,
+                        bool graph) {
+  tm_status st;
+  if (graph && c->graph && same_images(c->graph_in, in, nimg) && same_images(c->graph_out, out, nimg)) {
+    TM_CUDA(c, cudaGraphLaunch(c->graph, s));
+    c->launches = c->graph_launches;
+    return TM_OK;
+  }
+  const bool debug = c->debug != 0 && nimg == 1 && !graph;
+  double total_px = 0;
+  for (int i = 0; i < nimg; ++i) total_px += (double)in[i].width * in[i].height;
+  std::vector<Job> jobs((size_t)nimg);
+  std::vector<JobLayout> lays((size_t)nimg);
+  std::vector<size_t> offs((size_t)nimg);
+  size_t ws_total = 0, smem = 0;
+  const size_t smem_limit = c->smem_optin - 2048;
+  int b_range = 0, b_prep = 0, b_rows = 0, b_cols = 0, b_look = 0;
+  bool multi_seg = false;
+  std::vector<std::pair<double, int2>> items;
+  for (int i = 0; i < nimg; ++i) {
+    const int W = in[i].width, H = in[i].height;
+    const double share = nimg == 1 ? 1.0 : std::max(1.0 / c->num_sms, W * (double)H / total_px);
+    Job &J = jobs[(size_t)i];
+    memset(&J, 0, sizeof J);
+    J.qbits = choose_qbits(c->p, W, H);
+    const DevParams P = dev_params(c->p, J.qbits);
+    const int sms_share = std::max(1, (int)std::lround(c->num_sms * share));
+    if (!plan_sweep(P, W, H, sms_share, smem_limit, J.plan)) return TM_EUNSUPPORTED;
+    smem = std::max(smem, J.plan.smem);
+    column_segments(W, H, 2, J.nseg, J.seg_rows);
+    multi_seg = multi_seg || J.nseg > 1;
+    lays[(size_t)i] = job_layout(c->p, W, H, J.nseg, sweep_count_elems(J.plan), debug);
+    offs[(size_t)i] = ws_total;
+    ws_total += lays[(size_t)i].total;
+    J.b0[kStRange] = b_range;
+    b_range += range_blocks(W, H, c->num_sms, share);
+    J.b0[kStPrep] = b_prep;
+    b_prep += prep_blocks(W, H, c->num_sms, share);
+    J.b0[kStRows] = b_rows;
+    b_rows += H;
+    J.b0[kStCols] = b_cols;
+    b_cols += col_blocks(W, J.nseg);
+    J.b0[kStLook] = b_look;
+    b_look += lookup_blocks(W, H);
+    const int ntiles = J.plan.tiles_x * J.plan.tiles_y;
+    const double rows = std::min(J.plan.TY + 2.0 * J.plan.Ry + 1, H + 1.0);
+    const double cols = std::min(J.plan.TX + 2.0 * J.plan.Rx + 2, W + 1.0);
+    for (int t = 0; t < ntiles; ++t) items.push_back({rows * (cols * 0.25 + 300.0), make_int2(i, t)});
+  }
+  // longest items first
+  std::stable_sort(items.begin(), items.end(),
+                   [](const std::pair<double, int2> &a, const std::pair<double, int2> &b) { return a.first > b.first; });
+  const int nitems = (int)items.size();
+  if ((st = ensure_stats(c, nimg))) return st;
+  if ((st = grow_device(c, &c->ws, &c->ws_bytes, ws_total))) return st;
+  if ((st = grow_device(c, (void **)&c->djobs, &c->djobs_bytes, sizeof(Job) * nimg))) return st;
+  if ((st = grow_device(c, (void **)&c->ditems, &c->ditems_bytes, sizeof(int2) * nitems + sizeof(int)))) return st;
+  if ((st = grow_pinned(c, (void **)&c->hjobs, &c->hjobs_bytes, sizeof(Job) * nimg))) return st;
+  if ((st = grow_pinned(c, (void **)&c->hitems, &c->hitems_bytes, sizeof(int2) * nitems))) return st;
+  char *ws = static_cast<char *>(c->ws);
+  for (int i = 0; i < nimg; ++i) {
+    Job &J = jobs[(size_t)i];
+    const JobLayout &L = lays[(size_t)i];
+    char *b = ws + offs[(size_t)i];
+    J.in = to_image(&in[i]);
+    J.out = to_image(&out[i]);
+    J.st = c->stats + i;
+    J.bins = reinterpret_cast<uint8_t *>(b + L.bins);
+    J.q = reinterpret_cast<int32_t *>(b + L.q);
+    J.s1 = reinterpret_cast<long long *>(b + L.s1);
+    J.s2 = reinterpret_cast<long long *>(b + L.s2);
+    J.segtot = reinterpret_cast<long long *>(b + L.segtot);
+    J.counts = reinterpret_cast<uint16_t *>(b + L.counts);
+    if (debug) {
+      J.dbg.cnt = reinterpret_cast<unsigned *>(b + L.dcnt);
+      J.dbg.sigma2 = reinterpret_cast<float *>(b + L.dvar);
+      J.dbg.weight = reinterpret_cast<float *>(b + L.dw);
+      J.dbg.lf = reinterpret_cast<float *>(b + L.dlf);
+      J.dbg.l = reinterpret_cast<float *>(b + L.dl);
+    }
+  }
+  if (!graph) drop_graph(c);  // the staging below is what a cached graph copies
+  memcpy(c->hjobs, jobs.data(), sizeof(Job) * nimg);
+  for (int k = 0; k < nitems; ++k) c->hitems[k] = items[(size_t)k].second;
+  const DevParams P = dev_params(c->p, jobs[0].qbits);  // qbits is per job
+  int *queue = reinterpret_cast<int *>(c->ditems + nitems);
+  const int ctas = std::min(nitems, c->num_sms);
+  // a batch is captured on the context's own stream (capture is not allowed on
+  // the legacy default stream) and the graph is then launched on the caller's
+  const cudaStream_t caller = s;
+  if (graph) {
+    drop_graph(c);
+    if (!c->graph_stream) TM_CUDA(c, cudaStreamCreateWithFlags(&c->graph_stream, cudaStreamNonBlocking));
+    s = c->graph_stream;
+    TM_CUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  }
+  cudaMemcpyAsync(c->djobs, c->hjobs, sizeof(Job) * nimg, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(c->ditems, c->hitems, sizeof(int2) * nitems, cudaMemcpyHostToDevice, s);
+  int64_t n = 0;
+  if (!graph) mark(c, s, -1);
+  launch_range(c->djobs, nimg, b_range, c->p.n_bins, s);
+  if (!graph) mark(c, s, ST_RANGE);
+  launch_prep(c->djobs, nimg, b_prep, c->p.n_bins, s);
+  if (!graph) mark(c, s, ST_PREP);
+  n += 2 + launch_integral_jobs(c->djobs, nimg, b_rows, b_cols, multi_seg, s);
+  if (!graph) mark(c, s, ST_INTEGRAL);
+  const int ls = launch_sweep(P, c->djobs, c->ditems, nitems, queue, smem, ctas, s);
+  if (!graph) mark(c, s, ST_SWEEP);
+  n += launch_lookup_counts(P, c->djobs, nimg, b_look, s) + 1;
+  if (!graph) mark(c, s, ST_LOOKUP);
+  if (graph) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (e != cudaSuccess || ls < 0) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return fail(c, TM_ECUDA, "batch capture failed: %s", cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      c->graph = nullptr;
+      return cuda_fail(c, e, "cudaGraphInstantiate");
+    }
+    c->graph_in.assign(in, in + nimg);
+    c->graph_out.assign(out, out + nimg);
+    c->graph_launches = n;
+    TM_CUDA(c, cudaGraphLaunch(c->graph, caller));
+  } else if (ls < 0) {
+    return check_launch(c, "sweep shared-memory attribute");
+  }
+  if ((st = check_launch(c, "forward launch"))) return st;
+  c->launches = n;
+  if (nimg == 1) {
+    c->last_W = in[0].width;
+    c->last_H = in[0].height;
+    c->last_q = jobs[0].qbits;
+    c->last_path = 1;
+    c->bins = jobs[0].bins;
+    c->q = jobs[0].q;
+    c->dbg = jobs[0].dbg;
+  }
+  return TM_OK;
+}
+
+// The forward launch sequence on one image (device buffers already checked).
+tm_status forward_device(tm_ctx *c, const tm_image *in, const tm_image *out, cudaStream_t s) {
+  tm_status st = ensure_device_info(c);
+  if (st) return st;
+  if (c->p.n_bins > 1 && c->hist_path != 2) {
+    st = forward_fused(c, 1, in, out, s, false);
+    if (st != TM_EUNSUPPORTED) return st;
+    if (c->hist_path == 1)
+      return fail(c, TM_EUNSUPPORTED, "fused sweep does not fit these fields (use the materialised path)");
+  }
+  return forward_materialised(c, in, out, s);
 }
 
 }  // namespace
@@ -397,13 +618,19 @@ tm_status tm_create(const tm_params *params, tm_ctx **out) {
 
 void tm_destroy(tm_ctx *c) {
   if (!c) return;
-  if (c->ws || c->stats || c->stage) cudaDeviceSynchronize();
+  if (c->ws || c->stats || c->stage || c->djobs || c->graph) cudaDeviceSynchronize();
+  drop_graph(c);
   for (auto &call : c->marks)
     for (auto &m : call) cudaEventDestroy(m.first);
   for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
   if (c->ws) cudaFree(c->ws);
   if (c->stats) cudaFree(c->stats);
   if (c->stage) cudaFree(c->stage);
+  if (c->djobs) cudaFree(c->djobs);
+  if (c->ditems) cudaFree(c->ditems);
+  if (c->graph_stream) cudaStreamDestroy(c->graph_stream);
+  if (c->hjobs) cudaFreeHost(c->hjobs);
+  if (c->hitems) cudaFreeHost(c->hitems);
   delete c;
 }
 
@@ -484,10 +711,31 @@ tm_status tm_forward_batch(tm_ctx *c, int32_t n, const tm_image *in, const tm_im
   if (n < 0) return fail(c, TM_EINVAL, "n = %d < 0", n);
   if (n == 0) { c->launches = 0; return TM_OK; }
   if (!in || !out) return fail(c, TM_EINVAL, "descriptor arrays are NULL");
+  for (int i = 0; i < n; ++i) {
+    tm_status s;
+    char nm[32];
+    snprintf(nm, sizeof nm, "in[%d]", i);
+    if ((s = validate_image(c, &in[i], nm, true))) return s;
+    snprintf(nm, sizeof nm, "out[%d]", i);
+    if ((s = validate_image(c, &out[i], nm, false))) return s;
+    if (in[i].width != out[i].width || in[i].height != out[i].height)
+      return fail(c, TM_EINVAL, "image %d: in and out sizes differ", i);
+    if (overlap(&in[i], &out[i])) return fail(c, TM_EINVAL, "image %d: in and out overlap", i);
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  tm_status s = ensure_device_info(c);
+  if (s) return s;
+  if (c->p.n_bins > 1 && c->hist_path != 2) {
+    mark(c, st, -1);
+    s = forward_fused(c, n, in, out, st, true);
+    mark(c, st, ST_BATCH);
+    if (s != TM_EUNSUPPORTED) return s;
+    if (c->hist_path == 1)
+      return fail(c, TM_EUNSUPPORTED, "fused sweep does not fit these fields (use the materialised path)");
+  }
   int64_t total = 0;
   for (int i = 0; i < n; ++i) {
-    tm_status s = tm_forward(c, &in[i], &out[i], stream);
-    if (s) return s;
+    if ((s = forward_device(c, &in[i], &out[i], st))) return s;
     total += c->launches;
   }
   c->launches = total;
@@ -505,14 +753,28 @@ tm_status tm_integral_image(const int32_t *q, int32_t width, int32_t height, int
                             int64_t *s2, void *stream) {
   if (!q || !s1 || !s2) return fail(nullptr, TM_EINVAL, "tm_integral_image: NULL pointer");
   if (width < 1 || height < 1) return fail(nullptr, TM_EINVAL, "tm_integral_image: bad size");
+  if ((long long)width * height > (1LL << 31) - 1)
+    return fail(nullptr, TM_EINVAL, "tm_integral_image: more than 2^31-1 elements");
   if (s1 == s2) return fail(nullptr, TM_EINVAL, "tm_integral_image: s1 == s2");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Job J{};
+  J.in.W = width;
+  J.in.H = height;
+  J.q = const_cast<int32_t *>(q);
+  J.s1 = reinterpret_cast<long long *>(s1);
+  J.s2 = reinterpret_cast<long long *>(s2);
+  column_segments(width, height, 2, J.nseg, J.seg_rows);
+  const size_t seg_bytes = 8 * 2 * (size_t)J.nseg * (width + 1);
   void *scr = nullptr;
-  size_t bytes = 8 * integral_scratch_elems(width, height);
-  cudaError_t e = cudaMallocAsync(&scr, bytes, st);
+  cudaError_t e = cudaMallocAsync(&scr, align256(sizeof(Job)) + seg_bytes, st);
   if (e != cudaSuccess) { cudaGetLastError(); return fail(nullptr, TM_ENOMEM, "tm_integral_image: scratch"); }
-  launch_integral_image(q, width, height, s1, s2, static_cast<int64_t *>(scr), st);
-  e = cudaGetLastError();
+  J.segtot = reinterpret_cast<long long *>(static_cast<char *>(scr) + align256(sizeof(Job)));
+  e = cudaMemcpyAsync(scr, &J, sizeof(Job), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    launch_integral_jobs(static_cast<Job *>(scr), 1, height, col_blocks(width, J.nseg), J.nseg > 1, st);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // J lives on this stack frame
+  }
   cudaFreeAsync(scr, st);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "tm_integral_image");
   return TM_OK;

@@ -56,6 +56,69 @@ struct Image {
   int dtype;
 };
 
+// Debug planes written by the lookup kernels (each may be null).
+struct DebugPlanes {
+  unsigned *cnt;   // s * H * W
+  float *sigma2;   // s * H * W
+  float *weight;   // s * H * W
+  float *lf;       // s * H * W
+  float *l;        // H * W
+};
+
+constexpr int kMaxSlabs = 16;
+
+// Tiling and ring layout of the fused sweep over one image (host-computed).
+struct SweepPlan {
+  int W, H;
+  int TX, TY, tiles_x, tiles_y;   // output tile and tile grid
+  int Rx, Ry;                     // largest half-width / half-height
+  int nslabs;                     // row slabs over all fields (each < 2^16 pixels)
+  int slab_field[kMaxSlabs];      // field of each slab
+  int slab_a[kMaxSlabs];          // first row offset of the slab (relative to y)
+  int slab_b[kMaxSlabs];          // last row offset of the slab
+  int ring_len[kMaxSlabs];        // rows of the parked-corner ring of each slab
+  int ring_off[kMaxSlabs];        // first row of that ring in the shared ring array
+  int ring_total;
+  int bmax;                       // largest slab_b
+  int BR;                         // rows of the tile's own bin ring
+  int nseg_max;                   // 16-column segments of the widest swept row (<= 32)
+  int rows_max;                   // rows of the widest swept band
+  int nw_max;                     // threshold words (two thresholds each) allocated
+  int text_max;                   // widest tile row including both side bands
+  int cstride;                    // words per threshold row in shared memory (odd)
+  size_t smem;                    // dynamic shared memory bytes
+};
+
+// Batched stages; every stage kernel of a batch maps its blocks to images
+// through the per-image first-block offsets b0[stage].
+enum StageId { kStRange = 0, kStPrep, kStRows, kStCols, kStLook, kNumStages };
+
+// One image of a batch: its buffers and its share of every batched launch.
+struct Job {
+  Image in, out;
+  Stats *st;                // range state
+  uint8_t *bins;            // H*W bin map
+  int32_t *q;               // H*W quantised log
+  long long *s1, *s2;       // (H+1)*(W+1) integral images of q and q^2
+  long long *segtot;        // 2*nseg*(W+1) column-pass segment sums
+  uint16_t *counts;         // nslabs*H*W slab counts from the sweep
+  DebugPlanes dbg;
+  int qbits;
+  int nseg, seg_rows;       // column-pass segmentation
+  int b0[kNumStages];       // first block of this job in each batched stage
+  SweepPlan plan;           // sweep tiling of this image
+};
+
+// Index of the job owning block `blk` of stage `st` (jobs sorted by b0).
+__device__ __forceinline__ int find_job(const Job *jobs, int njobs, int st, int blk) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].b0[st] <= blk) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 // Eq. 11 in float: fixed order, every product and sum rounded, no contraction.
 __device__ __forceinline__ float luminance(float r, float g, float b) {
   float i = __fadd_rn(__fadd_rn(__fmul_rn(0.2126f, r), __fmul_rn(0.7152f, g)),

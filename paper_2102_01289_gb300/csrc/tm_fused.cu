@@ -30,7 +30,7 @@
 // into row slabs each holding fewer, so every slab count is exact. Each
 // completed slab count is written once (uint16 per pixel and slab); the
 // per-pixel lookup kernel then evaluates Eq. 2-4, 10, 3 and 12.
-#include "tm_fused.cuh"
+#include "tm_kernels.cuh"
 
 namespace tmk {
 namespace {
@@ -88,16 +88,16 @@ __device__ __forceinline__ Smem carve(const SweepPlan &S, unsigned char *base) {
   return mm;
 }
 
-__global__ void __launch_bounds__(kNT, 1)
-    k_sweep(DevParams P, SweepPlan S, const uint8_t *__restrict__ bins, uint16_t *__restrict__ counts) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+// One output tile of one image. evt_buf: per event of the row (double
+// buffered by row parity): pixel row, ring offset, bin-ring offset, rx.
+__device__ __forceinline__ void sweep_tile(const DevParams &P, const SweepPlan &S,
+                                           const uint8_t *__restrict__ bins,
+                                           uint16_t *__restrict__ counts, int tile,
+                                           unsigned char *smem_raw, int (*evt_buf)[2 * kMaxSlabs][4]) {
   const Smem sm = carve(S, smem_raw);
-  // per event of the row (double-buffered by row parity): row, acc offset, bring offset, rx
-  __shared__ int evt_buf[2][2 * kMaxSlabs][4];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int W = S.W, H = S.H;
   const long long N = (long long)W * H;
-  const int tile = blockIdx.x;
   const int tx = tile % S.tiles_x, ty = tile / S.tiles_x;
   const int X0 = tx * S.TX, X1 = min(X0 + S.TX, W);
   const int Y0 = ty * S.TY, Y1 = min(Y0 + S.TY, H);
@@ -326,6 +326,27 @@ __global__ void __launch_bounds__(kNT, 1)
   }
 }
 
+// Persistent sweep over a queue of (image, tile) items, longest first: each
+// CTA pops the next item until the queue is drained.
+__global__ void __launch_bounds__(kNT, 1)
+    k_sweep(DevParams P, const Job *__restrict__ jobs, const int2 *__restrict__ items, int nitems,
+            int *queue) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int evt_buf[2][2 * kMaxSlabs][4];
+  __shared__ int item_sh;
+  for (;;) {
+    if (threadIdx.x == 0) item_sh = atomicAdd(queue, 1);
+    __syncthreads();
+    const int it = item_sh;
+    __syncthreads();
+    if (it >= nitems) break;
+    const int2 jt = items[it];
+    const Job &J = jobs[jt.x];
+    sweep_tile(P, J.plan, J.bins, J.counts, jt.y, smem_raw, evt_buf);
+    __syncthreads();  // the next item reuses shared memory
+  }
+}
+
 size_t smem_bytes(const SweepPlan &S) {
   return (size_t)S.nw_max * S.cstride * 4 + (size_t)S.nw_max * 4 + (size_t)S.nseg_max * 20 + 64 * 4 +
          (size_t)S.ring_total * S.TX * 2 + (size_t)S.BR * S.TX + 2 * (size_t)S.rows_max + 16;
@@ -364,18 +385,15 @@ bool plan_sweep(const DevParams &P, int W, int H, int num_sms, size_t smem_limit
     }
   }
   base.nslabs = ns;
-  int bmin = 1 << 30, bmax = -(1 << 30), ring_total = 0;
+  int bmax = -(1 << 30), ring_total = 0;
   for (int s = 0; s < ns; ++s) {
     base.ring_len[s] = base.slab_b[s] - base.slab_a[s] + 2;
     base.ring_off[s] = ring_total;
     ring_total += base.ring_len[s];
-    bmin = min(bmin, base.slab_b[s]);
     bmax = max(bmax, base.slab_b[s]);
   }
   base.ring_total = ring_total;
   base.bmax = bmax;
-  base.LB = 4;
-  base.CR = bmax - min(bmin, 0) + 2 + base.LB;
   base.BR = base.Ry + max(bmax, 0) + 3;
   base.nw_max = P.n_bins / 2 + 1;
   const int cand_tx[] = {32, 48, 64, 80, 96, 112, 128, 160, 192, 224, 256, 320, 384, 448, 512};
@@ -417,14 +435,14 @@ bool plan_sweep(const DevParams &P, int W, int H, int num_sms, size_t smem_limit
 
 size_t sweep_count_elems(const SweepPlan &S) { return (size_t)S.nslabs * S.W * S.H; }
 
-int launch_sweep(const DevParams &P, const SweepPlan &S, const uint8_t *bins, uint16_t *counts,
-                 cudaStream_t s) {
-  // dynamic shared memory beyond 48 KB needs the opt-in attribute (static
-  // shared memory of the kernel is counted separately by the planner's margin)
-  cudaError_t e = cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem);
+int launch_sweep(const DevParams &P, const Job *jobs, const int2 *items, int nitems, int *queue,
+                 size_t smem, int ctas, cudaStream_t s) {
+  // dynamic shared memory beyond 48 KB needs the opt-in attribute (the static
+  // shared memory of the kernel is covered by the planner's margin)
+  cudaError_t e = cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return -1;
-  const int ctas = S.tiles_x * S.tiles_y;
-  k_sweep<<<ctas, kNT, S.smem, s>>>(P, S, bins, counts);
+  cudaMemsetAsync(queue, 0, sizeof(int), s);
+  k_sweep<<<ctas, kNT, smem, s>>>(P, jobs, items, nitems, queue);
   return 1;
 }
 

@@ -49,50 +49,94 @@ constexpr int kTile = kNT * kItems;
 // layouts are padded (9 slots per 8 elements) against bank conflicts.
 __device__ __forceinline__ int pad9(int i) { return (i >> 3) * 9 + (i & 7); }
 
-__global__ void __launch_bounds__(kNT) k_rows_q(const int32_t *__restrict__ q, int W, int H,
-                                                long long *s1, long long *s2) {
+__global__ void __launch_bounds__(kNT) k_rows_q(const Job *__restrict__ jobs, int njobs) {
   __shared__ int32_t tile[kTile / 8 * 9];
   __shared__ long long out1[kTile / 8 * 9], out2[kTile / 8 * 9];
   __shared__ long long wt1[kNT / 32], wt2[kNT / 32];
+  const int j = find_job(jobs, njobs, kStRows, blockIdx.x);
+  const Job &J = jobs[j];
+  const int y = blockIdx.x - J.b0[kStRows];
+  const int W = J.in.W;
   const long long W1 = (long long)W + 1;
-  for (int y = blockIdx.x; y < H; y += gridDim.x) {
-    if (y == 0)
-      for (long long x = threadIdx.x; x < W1; x += kNT) s1[x] = 0, s2[x] = 0;
-    const int32_t *row = q + (long long)y * W;
-    long long *o1 = s1 + (long long)(y + 1) * W1;
-    long long *o2 = s2 + (long long)(y + 1) * W1;
-    if (threadIdx.x == 0) o1[0] = 0, o2[0] = 0;
-    long long carry1 = 0, carry2 = 0;
-    for (int base = 0; base < W; base += kTile) {
-      for (int i = threadIdx.x; i < kTile; i += kNT) tile[pad9(i)] = base + i < W ? __ldg(row + base + i) : 0;
-      __syncthreads();
-      long long a1 = 0, a2 = 0, l1[kItems], l2[kItems];
+  long long *s1 = J.s1, *s2 = J.s2;
+  if (y == 0)
+    for (long long x = threadIdx.x; x < W1; x += kNT) s1[x] = 0, s2[x] = 0;
+  const int32_t *row = J.q + (long long)y * W;
+  long long *o1 = s1 + (long long)(y + 1) * W1;
+  long long *o2 = s2 + (long long)(y + 1) * W1;
+  if (threadIdx.x == 0) o1[0] = 0, o2[0] = 0;
+  long long carry1 = 0, carry2 = 0;
+  for (int base = 0; base < W; base += kTile) {
+    for (int i = threadIdx.x; i < kTile; i += kNT) tile[pad9(i)] = base + i < W ? __ldg(row + base + i) : 0;
+    __syncthreads();
+    long long a1 = 0, a2 = 0, l1[kItems], l2[kItems];
 #pragma unroll
-      for (int j = 0; j < kItems; ++j) {
-        const long long v = tile[threadIdx.x * 9 + j];
-        a1 += v;
-        a2 += v * v;
-        l1[j] = a1;
-        l2[j] = a2;
-      }
-      long long t1, t2;
-      const long long e1 = block_exclusive_scan<long long, kNT>(a1, wt1, t1) + carry1;
-      const long long e2 = block_exclusive_scan<long long, kNT>(a2, wt2, t2) + carry2;
-#pragma unroll
-      for (int j = 0; j < kItems; ++j) {
-        out1[threadIdx.x * 9 + j] = e1 + l1[j];
-        out2[threadIdx.x * 9 + j] = e2 + l2[j];
-      }
-      __syncthreads();
-      const int n = min(kTile, W - base);
-      for (int i = threadIdx.x; i < n; i += kNT) {
-        o1[base + i + 1] = out1[pad9(i)];
-        o2[base + i + 1] = out2[pad9(i)];
-      }
-      carry1 += t1;
-      carry2 += t2;
-      __syncthreads();
+    for (int k = 0; k < kItems; ++k) {
+      const long long v = tile[threadIdx.x * 9 + k];
+      a1 += v;
+      a2 += v * v;
+      l1[k] = a1;
+      l2[k] = a2;
     }
+    long long t1, t2;
+    const long long e1 = block_exclusive_scan<long long, kNT>(a1, wt1, t1) + carry1;
+    const long long e2 = block_exclusive_scan<long long, kNT>(a2, wt2, t2) + carry2;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+      out1[threadIdx.x * 9 + k] = e1 + l1[k];
+      out2[threadIdx.x * 9 + k] = e2 + l2[k];
+    }
+    __syncthreads();
+    const int n = min(kTile, W - base);
+    for (int i = threadIdx.x; i < n; i += kNT) {
+      o1[base + i + 1] = out1[pad9(i)];
+      o2[base + i + 1] = out2[pad9(i)];
+    }
+    carry1 += t1;
+    carry2 += t2;
+    __syncthreads();
+  }
+}
+
+// Column pass over the integral images of the jobs: block -> (plane, segment,
+// 128-column chunk) of its job. First kernel: segment sums.
+__global__ void __launch_bounds__(128) k_colsum_jobs(const Job *__restrict__ jobs, int njobs) {
+  const int j = find_job(jobs, njobs, kStCols, blockIdx.x);
+  const Job &J = jobs[j];
+  const int lb = blockIdx.x - J.b0[kStCols];
+  const int cols = J.in.W + 1, rows = J.in.H + 1;
+  const int chunks = (cols + 127) / 128;
+  const int pl = lb / (chunks * J.nseg), rem = lb - pl * chunks * J.nseg;
+  const int seg = rem / chunks, ch = rem - seg * chunks;
+  const int c = ch * 128 + threadIdx.x;
+  if (c >= cols) return;
+  const long long *P = pl ? J.s2 : J.s1;
+  const int r0 = 1 + seg * J.seg_rows, r1 = min(rows, r0 + J.seg_rows);
+  long long acc = 0;
+#pragma unroll 4
+  for (int r = r0; r < r1; ++r) acc += P[(long long)r * cols + c];
+  J.segtot[((long long)pl * J.nseg + seg) * cols + c] = acc;
+}
+
+// Second kernel: offset by the segments above, scan in place.
+__global__ void __launch_bounds__(128) k_colscan_jobs(const Job *__restrict__ jobs, int njobs) {
+  const int j = find_job(jobs, njobs, kStCols, blockIdx.x);
+  const Job &J = jobs[j];
+  const int lb = blockIdx.x - J.b0[kStCols];
+  const int cols = J.in.W + 1, rows = J.in.H + 1;
+  const int chunks = (cols + 127) / 128;
+  const int pl = lb / (chunks * J.nseg), rem = lb - pl * chunks * J.nseg;
+  const int seg = rem / chunks, ch = rem - seg * chunks;
+  const int c = ch * 128 + threadIdx.x;
+  if (c >= cols) return;
+  long long *P = pl ? J.s2 : J.s1;
+  long long acc = 0;
+  for (int s = 0; s < seg; ++s) acc += J.segtot[((long long)pl * J.nseg + s) * cols + c];
+  const int r0 = 1 + seg * J.seg_rows, r1 = min(rows, r0 + J.seg_rows);
+#pragma unroll 4
+  for (int r = r0; r < r1; ++r) {
+    acc += P[(long long)r * cols + c];
+    P[(long long)r * cols + c] = acc;
   }
 }
 
@@ -197,31 +241,24 @@ void column_pass(T *base, long long plane_stride, int planes, int W, int H, T *s
 
 }  // namespace
 
-size_t integral_scratch_elems(int W, int H) {
-  int nseg, seg_rows;
-  segments(W + 1, H, 2, nseg, seg_rows);
-  return (size_t)2 * nseg * (W + 1);
+void column_segments(int W, int H, int planes, int &nseg, int &seg_rows) {
+  segments(W + 1, H, planes, nseg, seg_rows);
+}
+
+int col_blocks(int W, int nseg) { return ((W + 1 + 127) / 128) * nseg * 2; }
+
+int launch_integral_jobs(const Job *jobs, int njobs, int row_blocks, int colb, bool multi_seg,
+                         cudaStream_t s) {
+  k_rows_q<<<row_blocks, kNT, 0, s>>>(jobs, njobs);
+  if (multi_seg) k_colsum_jobs<<<colb, 128, 0, s>>>(jobs, njobs);
+  k_colscan_jobs<<<colb, 128, 0, s>>>(jobs, njobs);
+  return multi_seg ? 3 : 2;
 }
 
 size_t hist_scratch_elems(int W, int H, int planes) {
   int nseg, seg_rows;
   segments(W + 1, H, planes, nseg, seg_rows);
   return (size_t)planes * nseg * (W + 1);
-}
-
-int launch_integral_image(const int32_t *q, int W, int H, int64_t *s1, int64_t *s2,
-                          int64_t *scratch, cudaStream_t s) {
-  k_rows_q<<<H < 65535 ? H : 65535, kNT, 0, s>>>(q, W, H, reinterpret_cast<long long *>(s1),
-                                                 reinterpret_cast<long long *>(s2));
-  // s1 and s2 are laid out back to back so one column pass covers both
-  // one column pass covers both planes: the second is addressed through the
-  // element distance between the two (both are 8-byte aligned)
-  long long stride = (long long)(((intptr_t)s2 - (intptr_t)s1) / (intptr_t)sizeof(long long));
-  int nseg, seg_rows;
-  segments(W + 1, H, 2, nseg, seg_rows);
-  column_pass<long long>(reinterpret_cast<long long *>(s1), stride, 2, W, H,
-                         reinterpret_cast<long long *>(scratch), s);
-  return 1 + (nseg > 1 ? 2 : 1);
 }
 
 int launch_integral_histogram(const uint8_t *bins, int W, int H, int n_bins, bool cumulative,

@@ -1,4 +1,8 @@
 // tm_kernels.cuh -- host-side launchers of the tone-mapping kernels.
+//
+// The forward stages run over a batch of jobs (one per image; a single image
+// is a batch of one). Every launcher takes the device copy of the job array,
+// the job count and the total number of blocks of its stage.
 #pragma once
 
 #include "tm_common.cuh"
@@ -6,39 +10,42 @@
 namespace tmk {
 
 // Stage a0: range of Eq. 11 luminance, bin edges, quantisation constants.
-void launch_range(const Image &in, Stats *st, int n_bins, int qbits, cudaStream_t s);
+void launch_range(const Job *jobs, int njobs, int blocks, int n_bins, cudaStream_t s);
 // Stage a1: bin map (uint8) and quantised normalised log (int32).
-void launch_prep(const Image &in, const Stats *st, int n_bins, int qbits, uint8_t *bins,
-                 int32_t *q, cudaStream_t s);
+void launch_prep(const Job *jobs, int njobs, int blocks, int n_bins, cudaStream_t s);
+// Blocks of the range / prep stages for one image.
+int range_blocks(int W, int H, int num_sms, double share);
+int prep_blocks(int W, int H, int num_sms, double share);
 
 // Stage a2 (Eq. 5): integral images of q and q^2, (H+1) x (W+1) int64.
-// `scratch` holds at least integral_scratch_elems(W, H) int64 elements.
-size_t integral_scratch_elems(int W, int H);
-int launch_integral_image(const int32_t *q, int W, int H, int64_t *s1, int64_t *s2,
-                          int64_t *scratch, cudaStream_t s);
+// Row pass: one block per image row. Column pass: blocks per image =
+// col_blocks(W, nseg); nseg/seg_rows from column_segments().
+void column_segments(int W, int H, int planes, int &nseg, int &seg_rows);
+int col_blocks(int W, int nseg);
+int launch_integral_jobs(const Job *jobs, int njobs, int row_blocks, int colb, bool multi_seg,
+                         cudaStream_t s);
 
-// Stage a3 (Eq. 7-8): integral histogram planes, (H+1) x (W+1) uint32 each.
-// cumulative = true: planes k = 1..n-1 hold the integral of [b < k];
-// cumulative = false: planes k = 0..n-1 hold the integral of [b == k].
-// `scratch` holds at least hist_scratch_elems(W, H, planes) uint32 elements.
+// Stage a3 (Eq. 7-8), materialised: integral histogram planes,
+// (H+1) x (W+1) uint32 each. cumulative = true: planes k = 1..n-1 hold the
+// integral of [b < k]; cumulative = false: planes k = 0..n-1 the integral of
+// [b == k]. `scratch` holds at least hist_scratch_elems(W, H, planes).
 size_t hist_scratch_elems(int W, int H, int planes);
 int launch_integral_histogram(const uint8_t *bins, int W, int H, int n_bins, bool cumulative,
                               uint32_t *planes, uint32_t *scratch, cudaStream_t s);
 
-// Debug planes written by the lookup kernels (each may be null).
-struct DebugPlanes {
-  unsigned *cnt;   // s * H * W
-  float *sigma2;   // s * H * W
-  float *weight;   // s * H * W
-  float *lf;       // s * H * W
-  float *l;        // H * W
-};
+// Stage a3', fused: plan of one image's sweep (false if the fields do not
+// fit), slab-count elements, and the persistent launch over a queue of
+// (job, tile) items sorted longest first.
+bool plan_sweep(const DevParams &P, int W, int H, int num_sms, size_t smem_limit, SweepPlan &S);
+size_t sweep_count_elems(const SweepPlan &S);
+int launch_sweep(const DevParams &P, const Job *jobs, const int2 *items, int nitems, int *queue,
+                 size_t smem, int ctas, cudaStream_t s);
 
-// Stage a4 over materialised structures: per-pixel multi-field lookup, tone
-// curve, fusion and colour restoration.
+// Stage a4: per-pixel lookup, tone curve, fusion and colour restoration.
+int lookup_blocks(int W, int H);
+int launch_lookup_counts(const DevParams &P, const Job *jobs, int njobs, int blocks, cudaStream_t s);
 int launch_lookup_materialised(const Image &in, const Image &out, const DevParams &P,
-                               const uint8_t *bins, const uint32_t *cplanes,
-                               const int64_t *s1, const int64_t *s2, const DebugPlanes &dbg,
-                               cudaStream_t s);
+                               const uint8_t *bins, const uint32_t *cplanes, const int64_t *s1,
+                               const int64_t *s2, const DebugPlanes &dbg, cudaStream_t s);
 
 }  // namespace tmk

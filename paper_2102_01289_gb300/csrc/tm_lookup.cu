@@ -8,7 +8,6 @@
 // then Eq. 2, Eq. 4, the fusion of Eq. 3 and the colour restoration of Eq. 12.
 // The fields are evaluated in one pass instead of the paper's per-scale loop
 // (Section III-A).
-#include "tm_fused.cuh"
 #include "tm_kernels.cuh"
 
 namespace tmk {
@@ -91,23 +90,28 @@ __global__ void __launch_bounds__(256)
   finish_pixel(in, out, P, x, y, cnt, s1, s2, dbg);
 }
 
-__global__ void __launch_bounds__(256)
-    k_lookup_counts(Image in, Image out, DevParams P, SweepPlan S, const uint16_t *__restrict__ counts,
-                    const long long *__restrict__ s1, const long long *__restrict__ s2,
-                    DebugPlanes dbg) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int W = in.W, H = in.H;
+// Lookup from the sweep's per-slab counts, over a batch of jobs: block ->
+// (image, 32 x 8 pixel tile).
+__global__ void __launch_bounds__(256) k_lookup_counts(DevParams P, const Job *__restrict__ jobs, int njobs) {
+  const int j = find_job(jobs, njobs, kStLook, blockIdx.x);
+  const Job &J = jobs[j];
+  const int lb = blockIdx.x - J.b0[kStLook];
+  const int W = J.in.W, H = J.in.H;
+  const int bx = (W + 31) / 32;
+  const int x = (lb % bx) * 32 + (threadIdx.x & 31);
+  const int y = (lb / bx) * 8 + (threadIdx.x >> 5);
   if (x >= W || y >= H) return;
+  P.qbits = J.qbits;
+  const SweepPlan &S = J.plan;
   const long long N = (long long)W * H, pix = (long long)y * W + x;
   unsigned cnt[kMaxFields];
 #pragma unroll
   for (int f = 0; f < kMaxFields; ++f) cnt[f] = 0u;
   for (int s = 0; s < S.nslabs; ++s) {
     const int T = max(y + S.slab_a[s] - 1, -1), B = min(y + S.slab_b[s], H - 1);
-    if (B > T) cnt[S.slab_field[s]] += __ldg(counts + s * N + pix);
+    if (B > T) cnt[S.slab_field[s]] += __ldg(J.counts + s * N + pix);
   }
-  finish_pixel(in, out, P, x, y, cnt, s1, s2, dbg);
+  finish_pixel(J.in, J.out, P, x, y, cnt, J.s1, J.s2, J.dbg);
 }
 
 }  // namespace
@@ -122,12 +126,10 @@ int launch_lookup_materialised(const Image &in, const Image &out, const DevParam
   return 1;
 }
 
-int launch_lookup_counts(const Image &in, const Image &out, const DevParams &P, const SweepPlan &S,
-                         const uint16_t *counts, const int64_t *s1, const int64_t *s2,
-                         const DebugPlanes &dbg, cudaStream_t s) {
-  dim3 block(32, 8), grid((in.W + 31) / 32, (in.H + 7) / 8);
-  k_lookup_counts<<<grid, block, 0, s>>>(in, out, P, S, counts, reinterpret_cast<const long long *>(s1),
-                                         reinterpret_cast<const long long *>(s2), dbg);
+int lookup_blocks(int W, int H) { return ((W + 31) / 32) * ((H + 7) / 8); }
+
+int launch_lookup_counts(const DevParams &P, const Job *jobs, int njobs, int blocks, cudaStream_t s) {
+  k_lookup_counts<<<blocks, 256, 0, s>>>(P, jobs, njobs);
   return 1;
 }
 

@@ -67,28 +67,41 @@ __device__ __forceinline__ void load4(const Image &im, bool vec, int x, int y, i
 
 }  // namespace
 
-// Range of Eq. 11 luminance. Block min/max are folded with unsigned atomics;
-// the last block to finish computes the bin edges and the quantisation
-// constants in double precision, then re-arms the accumulators for the next
-// image, so no host round trip is needed between the stages.
-__global__ void __launch_bounds__(256) k_range(Image in, bool vec, Stats *st, int n_bins, int qbits) {
+// Rows of `im` can be read with the vector loads above.
+__device__ __forceinline__ bool vec_ok(const Image &im) {
+  const size_t es = im.dtype == kF16 ? 2 : 4;
+  const size_t align = im.dtype == kF16 ? 8 : 16;
+  return ((uintptr_t)im.p % align) == 0 && ((size_t)im.pitch * es) % align == 0;
+}
+
+// Range of Eq. 11 luminance, per image of the batch. Block min/max are folded
+// with unsigned atomics; the last block of an image computes its bin edges
+// and quantisation constants in double precision, then re-arms the
+// accumulators for the next call, so no host round trip is needed.
+__global__ void __launch_bounds__(256) k_range(const Job *__restrict__ jobs, int njobs, int n_bins) {
   __shared__ unsigned smin[8], smax[8];
   __shared__ int last;
+  const int j = find_job(jobs, njobs, kStRange, blockIdx.x);
+  const Job &J = jobs[j];
+  const int lb = blockIdx.x - J.b0[kStRange];
+  const int nb = (j + 1 < njobs ? jobs[j + 1].b0[kStRange] : (int)gridDim.x) - J.b0[kStRange];
+  const Image in = J.in;
+  const bool vec = vec_ok(in);
+  Stats *st = J.st;
   unsigned bmin = 0x7f800000u, bmax = 0u;
   const int W = in.W, H = in.H;
   const int gpr = (W + 3) >> 2;  // groups of four pixels per row
-  const long long ng = (long long)gpr * H;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long g0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; g0 < ng; g0 += 2 * stride) {
+  const int ng = gpr * H;        // fewer than 2^31 pixels
+  const int stride = nb * blockDim.x;
+  for (int g0 = lb * blockDim.x + threadIdx.x; g0 < ng; g0 += 2 * stride) {
     float r[2][4], gg[2][4], b[2][4];
     int n[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {  // two groups in flight per thread
-      const long long g = g0 + u * stride;
+      const int g = g0 + u * stride;
       n[u] = 0;
       if (g < ng) {
-        const int gi = (int)g;  // fewer than 2^31 pixels
-        const int y = gi / gpr, x = (gi - y * gpr) * 4;
+        const int y = g / gpr, x = (g - y * gpr) * 4;
         n[u] = min(4, W - x);
         load4(in, vec, x, y, n[u], r[u], gg[u], b[u]);
       }
@@ -117,7 +130,7 @@ __global__ void __launch_bounds__(256) k_range(Image in, bool vec, Stats *st, in
     atomicMax(&st->max_bits, bmax);
     __threadfence();
     const unsigned ticket = atomicAdd(&st->blocks_done, 1u);
-    last = (ticket == gridDim.x - 1);
+    last = (ticket == (unsigned)nb - 1);
   }
   __syncthreads();
   if (!last) return;
@@ -141,7 +154,7 @@ __global__ void __launch_bounds__(256) k_range(Image in, bool vec, Stats *st, in
     const double m0 = (double)__uint_as_float((bits & 0x7fffffu) | 0x3f800000u);
     st->c0 = (float)log2(m0);
     st->log2_scale =
-        degenerate ? 0.f : (float)(ldexp(1.0, qbits) / (log2((double)imax) - log2((double)imin)));
+        degenerate ? 0.f : (float)(ldexp(1.0, J.qbits) / (log2((double)imax) - log2((double)imin)));
     st->imin = imin;
     st->imax = imax;
     st->degenerate = degenerate ? 1 : 0;
@@ -153,19 +166,27 @@ __global__ void __launch_bounds__(256) k_range(Image in, bool vec, Stats *st, in
 
 // Bin map (Section II-A, edges from k_range) and quantised normalised log.
 // One thread per group of four pixels.
-__global__ void __launch_bounds__(256) k_prep(Image in, bool vec, const Stats *st, int n_bins,
-                                               int qbits, uint8_t *bins, int32_t *q) {
+__global__ void __launch_bounds__(256) k_prep(const Job *__restrict__ jobs, int njobs, int n_bins) {
   __shared__ float thr[kMaxBins];
+  const int j = find_job(jobs, njobs, kStPrep, blockIdx.x);
+  const Job &J = jobs[j];
+  const int lb = blockIdx.x - J.b0[kStPrep];
+  const int nb = (j + 1 < njobs ? jobs[j + 1].b0[kStPrep] : (int)gridDim.x) - J.b0[kStPrep];
+  const Image in = J.in;
+  const bool vec = vec_ok(in);
+  const Stats *st = J.st;
   for (int k = threadIdx.x; k < n_bins - 1; k += blockDim.x) thr[k] = st->thr[k];
   Stats sst;  // only the three constants quantise_log reads
   sst.c0 = __ldg(&st->c0);
   sst.e0 = __ldg(&st->e0);
   sst.log2_scale = __ldg(&st->log2_scale);
   __syncthreads();
-  const int W = in.W, H = in.H;
+  const int W = in.W, H = in.H, qbits = J.qbits;
+  uint8_t *bins = J.bins;
+  int32_t *q = J.q;
   const int gpr = (W + 3) >> 2;
-  const int ng = gpr * H;  // fewer than 2^31 pixels
-  for (int gi = blockIdx.x * blockDim.x + threadIdx.x; gi < ng; gi += gridDim.x * blockDim.x) {
+  const int ng = gpr * H;
+  for (int gi = lb * blockDim.x + threadIdx.x; gi < ng; gi += nb * blockDim.x) {
     const int y = gi / gpr, x = (gi - y * gpr) * 4;
     const int n = min(4, W - x);
     float r[4], g[4], b[4];
@@ -191,33 +212,28 @@ __global__ void __launch_bounds__(256) k_prep(Image in, bool vec, const Stats *s
   }
 }
 
-// Rows of `im` can be read with the vector loads above.
-bool vec_ok(const Image &im) {
-  const size_t es = im.dtype == kF16 ? 2 : 4;
-  const size_t align = im.dtype == kF16 ? 8 : 16;
-  return ((uintptr_t)im.p % align) == 0 && ((size_t)im.pitch * es) % align == 0;
+int range_blocks(int W, int H, int num_sms, double share) {
+  const long long groups = (long long)((W + 3) / 4) * H;
+  long long b = (groups + 511) / 512;
+  const long long cap = (long long)(4.0 * num_sms * share) + 1;
+  if (b > cap) b = cap;
+  return (int)(b < 1 ? 1 : b);
 }
 
-void launch_range(const Image &in, Stats *st, int n_bins, int qbits, cudaStream_t s) {
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const long long groups = (long long)((in.W + 3) / 4) * in.H;
-  long long blocks = (groups + 511) / 512;
-  blocks = blocks < 1 ? 1 : blocks;
-  if (blocks > 4LL * sms) blocks = 4LL * sms;
-  k_range<<<(int)blocks, 256, 0, s>>>(in, vec_ok(in), st, n_bins, qbits);
+int prep_blocks(int W, int H, int num_sms, double share) {
+  const long long groups = (long long)((W + 3) / 4) * H;
+  long long b = (groups + 255) / 256;
+  const long long cap = (long long)(16.0 * num_sms * share) + 1;
+  if (b > cap) b = cap;
+  return (int)(b < 1 ? 1 : b);
 }
 
-void launch_prep(const Image &in, const Stats *st, int n_bins, int qbits, uint8_t *bins, int32_t *q,
-                 cudaStream_t s) {
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const long long groups = (long long)((in.W + 3) / 4) * in.H;
-  long long blocks = (groups + 255) / 256;
-  if (blocks > 16LL * sms) blocks = 16LL * sms;
-  k_prep<<<(int)(blocks < 1 ? 1 : blocks), 256, 0, s>>>(in, vec_ok(in), st, n_bins, qbits, bins, q);
+void launch_range(const Job *jobs, int njobs, int blocks, int n_bins, cudaStream_t s) {
+  k_range<<<blocks, 256, 0, s>>>(jobs, njobs, n_bins);
+}
+
+void launch_prep(const Job *jobs, int njobs, int blocks, int n_bins, cudaStream_t s) {
+  k_prep<<<blocks, 256, 0, s>>>(jobs, njobs, n_bins);
 }
 
 }  // namespace tmk

@@ -1,0 +1,106 @@
+"""Batched forward (one launch per stage for the whole batch, the sweep as a
+persistent kernel over an (image, tile) queue, captured in a CUDA graph):
+every image must equal its own single-image forward bit for bit, graph
+replays must track the current input contents, and one image of the batch is
+checked against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2102_01289_gb300 as tm  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    tm.build()
+
+
+SIZES = [(97, 61), (640, 480), (333, 257), (1, 1), (1280, 720), (45, 900), (200, 3)]
+
+
+def _single(ctx, x):
+    y = torch.empty_like(x) if x.dtype != torch.float16 else torch.empty_like(x)
+    tm.tm_forward(ctx, x, y)
+    return y
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float16])
+def test_batch_equals_per_image(dtype):
+    p = tm.make_params(32, [4, 16, 64])
+    imgs = [synth.wdr_image(h, w, seed=i, dtype=dtype) for i, (w, h) in enumerate(SIZES)]
+    xs = [torch.from_numpy(a).cuda() for a in imgs]
+    ys = [torch.empty_like(x) for x in xs]
+    ctx = tm.tm_create(p)
+    try:
+        tm.tm_forward_batch(ctx, xs, ys)
+        torch.cuda.synchronize()
+        for x, y in zip(xs, ys):
+            ref = _single(ctx, x)
+            torch.cuda.synchronize()
+            assert torch.equal(y, ref)
+    finally:
+        tm.tm_destroy(ctx)
+
+
+def test_graph_replay_tracks_inputs():
+    p = tm.make_params(16, [2, 9, 40])
+    sizes = [(300, 200), (128, 96), (257, 255)]
+    xs = [torch.from_numpy(synth.wdr_image(h, w, seed=10 + i)).cuda() for i, (w, h) in enumerate(sizes)]
+    ys = [torch.empty_like(x) for x in xs]
+    ctx = tm.tm_create(p)
+    try:
+        tm.tm_forward_batch(ctx, xs, ys)  # captures
+        first = [y.clone() for y in ys]
+        tm.tm_forward_batch(ctx, xs, ys)  # replays
+        torch.cuda.synchronize()
+        for a, b in zip(first, ys):
+            assert torch.equal(a, b)
+        # new contents in the same buffers: the replay must see them
+        for i, (w, h) in enumerate(sizes):
+            xs[i].copy_(torch.from_numpy(synth.wdr_image(h, w, seed=50 + i)).cuda())
+        tm.tm_forward_batch(ctx, xs, ys)
+        torch.cuda.synchronize()
+        for x, y in zip(xs, ys):
+            assert torch.equal(y, _single(ctx, x))
+        # a single forward in between invalidates nothing visible to the caller
+        _single(ctx, xs[0])
+        tm.tm_forward_batch(ctx, xs, ys)
+        torch.cuda.synchronize()
+        for x, y in zip(xs, ys):
+            assert torch.equal(y, _single(ctx, x))
+    finally:
+        tm.tm_destroy(ctx)
+
+
+def test_batch_image_matches_oracle(orc):
+    p = tm.make_params(32, [4, 16, 64])
+    op = orc.make_params(32, [4, 16, 64], eps=float(np.float32(0.1)), sat=float(np.float32(0.6)))
+    imgs = [synth.wdr_image(h, w, seed=i) for i, (w, h) in enumerate([(90, 70), (160, 120), (50, 40)])]
+    xs = [torch.from_numpy(a).cuda() for a in imgs]
+    ys = [torch.empty_like(x) for x in xs]
+    ctx = tm.tm_create(p)
+    try:
+        tm.tm_forward_batch(ctx, xs, ys)
+        torch.cuda.synchronize()
+    finally:
+        tm.tm_destroy(ctx)
+    for a, y in zip(imgs, ys):
+        ref, _ = orc.forward(a, op)
+        got = y.cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(got - ref) <= 1e-4 * np.maximum(np.abs(ref), 1e-3))
+
+
+def test_empty_batch_is_noop():
+    ctx = tm.tm_create(tm.make_params(8, [1]))
+    try:
+        tm.tm_forward_batch(ctx, [], [])
+        assert tm.tm_last_launch_count(ctx) == 0
+    finally:
+        tm.tm_destroy(ctx)
