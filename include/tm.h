@@ -161,6 +161,27 @@ tm_status tm_backward(tm_ctx *ctx, const tm_image *in, const tm_image *grad_out,
 tm_status tm_integral_image(const int32_t *q, int32_t width, int32_t height,
                             int64_t *s1, int64_t *s2, void *stream);
 
+/* tm_integral_image without any allocation (the paper has no counterpart).
+ * For callers that must not allocate device memory once running: code under
+ * a real-time or per-frame deadline that forbids allocator calls after
+ * start-up, code running inside another framework's memory-pool or allocation
+ * callbacks where re-entering the CUDA allocator is not allowed, and
+ * processes that reserved all device memory up front. Same arguments, layout
+ * and results as tm_integral_image; the scratch it needs (a 256-byte-aligned
+ * job descriptor plus 16 * nseg * (width + 1) bytes of column-pass sums, nseg
+ * <= 64 segments of rows) lives in a static device array of 8 MiB that every
+ * GPU loading this library keeps until the process exits.
+ *   - The first call on a device looks the array's address up for that
+ *     device (with it current); make that first call before any stream
+ *     capture.
+ *   - Calls share the array: calls that overlap on the GPU (on different
+ *     streams, or from several host threads without ordering) race.
+ *   - Returns TM_EINVAL for bad arguments or a size whose scratch exceeds
+ *     8 MiB (use tm_integral_image then), TM_ECUDA if a CUDA call fails.
+ *     It never calls cudaMalloc, cudaFree or any allocating routine. */
+tm_status tm_integral_image_noalloc(const int32_t *q, int32_t width, int32_t height,
+                                    int64_t *s1, int64_t *s2, void *stream);
+
 /* Eq. 7-8 on a caller-supplied bin map: hk = n_bins planes, each the
  * (height+1) x (width+1) uint32 integral image of [bins == k] (zero first row
  * and column), plane-major. bins: device uint8[height*width], values < n_bins.

@@ -31,6 +31,7 @@ EXPORTS = (
     "tm_status_string", "tm_forward", "tm_forward_host", "tm_forward_batch", "tm_backward",
     "tm_integral_image", "tm_integral_histogram", "tm_set_debug", "tm_debug_size",
     "tm_debug_export", "tm_set_option", "tm_last_launch_count", "tm_stage_times",
+    "tm_integral_image_noalloc",
 )
 
 
@@ -104,6 +105,7 @@ def lib():
             "tm_set_option": (st, [P, i32, i64]),
             "tm_last_launch_count": (i64, [P]),
             "tm_stage_times": (i32, [P, P, P, i32]),
+            "tm_integral_image_noalloc": (st, [P, i32, i32, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -240,6 +242,14 @@ def tm_backward(ctx, inp, grad_out, grad_in=None, grad_params=None, stream=None)
 def tm_integral_image(q, s1, s2, stream=None) -> None:
     H, W = q.shape
     _check(lib().tm_integral_image(q.data_ptr(), W, H, s1.data_ptr(), s2.data_ptr(), _stream_ptr(stream)))
+
+
+def tm_integral_image_noalloc(q, s1, s2, stream=None) -> None:
+    """tm_integral_image for callers that must not allocate: its scratch is a
+    static 8 MiB device array of the library (see include/tm.h)."""
+    H, W = q.shape
+    _check(lib().tm_integral_image_noalloc(q.data_ptr(), W, H, s1.data_ptr(), s2.data_ptr(),
+                                           _stream_ptr(stream)))
 
 
 def tm_integral_histogram(bins, n_bins: int, hk, stream=None) -> None:
