@@ -294,6 +294,98 @@ def tm_debug_export(ctx, what: int, stream=None):
     return dst[: n.value // elem]
 
 
+def params_tensor(p: TmParams):
+    """[ld_min, ld_max, sat, eps[0..s-1], alpha[0..s-1]] as a float32 CPU tensor
+    (the layout tm_backward's grad_params uses)."""
+    import torch
+
+    s = p.n_fields
+    vals = [p.ld_min, p.ld_max, p.sat] + [p.eps[f] for f in range(s)] + [p.alpha[f] for f in range(s)]
+    return torch.tensor(vals, dtype=torch.float32)
+
+
+def params_from_tensor(template: TmParams, t) -> TmParams:
+    """Parameters of `template` with the differentiable values taken from t."""
+    p = TmParams.from_buffer_copy(template)
+    v = [float(x) for x in t.detach().cpu().reshape(-1)]
+    s = p.n_fields
+    p.ld_min, p.ld_max, p.sat = v[0], v[1], v[2]
+    for f in range(s):
+        p.eps[f] = v[3 + f]
+        p.alpha[f] = v[3 + s + f]
+    return p
+
+
+class _CtxCache:
+    """tm_ctx per distinct parameter values (the C context copies them)."""
+
+    def __init__(self, template: TmParams):
+        self.template = template
+        self.ctxs = {}
+
+    def get(self, t):
+        key = tuple(round(float(x), 9) for x in t.detach().cpu().reshape(-1))
+        if key not in self.ctxs:
+            self.ctxs[key] = tm_create(params_from_tensor(self.template, t))
+        return self.ctxs[key]
+
+    def close(self):
+        for c in self.ctxs.values():
+            tm_destroy(c)
+        self.ctxs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+try:
+    import torch as _torch
+
+    class TMFunction(_torch.autograd.Function):
+        """Differentiable tone mapping: forward through tm_forward, backward
+        through the hand-written adjoint tm_backward (bins held fixed).
+
+        Inputs: img (H, W, 3) or (B, H, W, 3) float32 CUDA tensor; theta, the
+        float32 parameter vector of params_tensor(); cache, a _CtxCache.
+        Returns the tone-mapped image (float32)."""
+
+        @staticmethod
+        def forward(ctx, img, theta, cache):
+            c = cache.get(theta)
+            x = img.contiguous()
+            out = _torch.empty_like(x)
+            if x.dim() == 3:
+                tm_forward(c, x, out)
+            else:
+                for b in range(x.shape[0]):
+                    tm_forward(c, x[b], out[b])
+            ctx.save_for_backward(x, theta)
+            ctx.cache = cache
+            return out
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            x, theta = ctx.saved_tensors
+            c = ctx.cache.get(theta)
+            g = grad_out.contiguous().float()
+            gin = _torch.empty_like(x) if ctx.needs_input_grad[0] else None
+            gp_total = _torch.zeros(theta.numel(), dtype=_torch.float32, device=x.device)
+            gp = _torch.empty_like(gp_total)
+            items = [(x, g, gin)] if x.dim() == 3 else [
+                (x[b], g[b], gin[b] if gin is not None else None) for b in range(x.shape[0])]
+            for xi, gi, gii in items:
+                tm_backward(c, xi, gi, gii, gp)
+                gp_total += gp
+            gtheta = gp_total.to(theta.device) if ctx.needs_input_grad[1] else None
+            return gin, gtheta, None
+
+except ImportError:  # pragma: no cover
+    TMFunction = None
+
+
 class ToneMapper:
     """Owns a ``tm_ctx``; ``forward`` runs the whole operator on a device image."""
 

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "tm.h"
+#include "tm_backward.cuh"
 #include "tm_kernels.cuh"
 
 using namespace tmk;
@@ -35,6 +36,9 @@ struct tm_ctx {
   Job *hjobs = nullptr;    // pinned host staging of the job array
   int2 *hitems = nullptr;  // pinned host staging of the sweep queue
   size_t hjobs_bytes = 0, hitems_bytes = 0;
+  // backward workspace
+  void *bws = nullptr;
+  size_t bws_bytes = 0;
   // staging for tm_forward_host
   void *stage = nullptr;
   size_t stage_bytes = 0;
@@ -410,7 +414,7 @@ tm_status forward_materialised(tm_ctx *c, const tm_image *in, const tm_image *ou
 // items. `graph`: capture the batch into a CUDA graph and replay it while the
 // batch is unchanged. Returns TM_EUNSUPPORTED if some image cannot be swept.
 tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image *out, cudaStream_t s,
-                        bool graph) {
+                        bool graph, bool do_lookup = true, Job *job0 = nullptr) {
   tm_status st;
   if (graph && c->graph && same_images(c->graph_in, in, nimg) && same_images(c->graph_out, out, nimg)) {
     TM_CUDA(c, cudaGraphLaunch(c->graph, s));
@@ -517,8 +521,10 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   if (!graph) mark(c, s, ST_INTEGRAL);
   const int ls = launch_sweep(P, c->djobs, c->ditems, nitems, queue, smem, ctas, s);
   if (!graph) mark(c, s, ST_SWEEP);
-  n += launch_lookup_counts(P, c->djobs, nimg, b_look, s) + 1;
-  if (!graph) mark(c, s, ST_LOOKUP);
+  if (do_lookup) {
+    n += launch_lookup_counts(P, c->djobs, nimg, b_look, s) + 1;
+    if (!graph) mark(c, s, ST_LOOKUP);
+  }
   if (graph) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(s, &g);
@@ -542,6 +548,7 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   }
   if ((st = check_launch(c, "forward launch"))) return st;
   c->launches = n;
+  if (job0) *job0 = jobs[0];
   if (nimg == 1) {
     c->last_W = in[0].width;
     c->last_H = in[0].height;
@@ -624,6 +631,7 @@ void tm_destroy(tm_ctx *c) {
     for (auto &m : call) cudaEventDestroy(m.first);
   for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
   if (c->ws) cudaFree(c->ws);
+  if (c->bws) cudaFree(c->bws);
   if (c->stats) cudaFree(c->stats);
   if (c->stage) cudaFree(c->stage);
   if (c->djobs) cudaFree(c->djobs);
@@ -744,9 +752,55 @@ tm_status tm_forward_batch(tm_ctx *c, int32_t n, const tm_image *in, const tm_im
 
 tm_status tm_backward(tm_ctx *c, const tm_image *in, const tm_image *grad_out,
                       const tm_image *grad_in, float *grad_params, void *stream) {
-  (void)in; (void)grad_out; (void)grad_in; (void)grad_params; (void)stream;
   if (!c) return fail(nullptr, TM_EINVAL, "tm_backward: ctx is NULL");
-  return fail(c, TM_EUNSUPPORTED, "tm_backward is not available in this build");
+  tm_status st;
+  if ((st = validate_image(c, in, "in", true))) return st;
+  if ((st = validate_image(c, grad_out, "grad_out", false))) return st;
+  if (grad_out->dtype != TM_F32) return fail(c, TM_EUNSUPPORTED, "grad_out must be float32");
+  if (grad_out->width != in->width || grad_out->height != in->height)
+    return fail(c, TM_EINVAL, "grad_out size differs from in");
+  if (grad_in) {
+    if ((st = validate_image(c, grad_in, "grad_in", false))) return st;
+    if (grad_in->dtype != TM_F32) return fail(c, TM_EUNSUPPORTED, "grad_in must be float32");
+    if (grad_in->width != in->width || grad_in->height != in->height)
+      return fail(c, TM_EINVAL, "grad_in size differs from in");
+    if (overlap(grad_in, in) || overlap(grad_in, grad_out))
+      return fail(c, TM_EINVAL, "grad_in overlaps in or grad_out");
+  }
+  if (c->p.n_bins < 2 || c->hist_path == 2)
+    return fail(c, TM_EUNSUPPORTED, "the backward runs on the fused path (n_bins >= 2)");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = ensure_device_info(c))) return st;
+  Job J;
+  st = forward_fused(c, 1, in, in, s, false, false, &J);
+  if (st == TM_EUNSUPPORTED) return fail(c, st, "fused sweep does not fit these fields");
+  if (st) return st;
+  const int W = in->width, H = in->height, nf = c->p.n_fields;
+  const size_t N = (size_t)W * H, plane = (size_t)(W + 1) * (H + 1);
+  const size_t o_acc = 0, o_u = align256(sizeof(BwdAcc)), o_v = o_u + align256(4 * N * nf),
+               o_gi = o_v + align256(4 * N * nf), o_iu = o_gi + align256(4 * N),
+               total = o_iu + 8 * plane * 2 * nf;
+  if ((st = grow_device(c, &c->bws, &c->bws_bytes, total))) return st;
+  char *b = static_cast<char *>(c->bws);
+  BwdJob B{};
+  B.grad_out = to_image(grad_out);
+  if (grad_in) B.grad_in = to_image(grad_in);
+  B.grad_params = grad_params;
+  B.acc = reinterpret_cast<BwdAcc *>(b + o_acc);
+  B.U = reinterpret_cast<float *>(b + o_u);
+  B.V = reinterpret_cast<float *>(b + o_v);
+  B.gi_direct = reinterpret_cast<float *>(b + o_gi);
+  B.IU = reinterpret_cast<double *>(b + o_iu);
+  B.IV = B.IU + plane * nf;
+  TM_CUDA(c, cudaMemsetAsync(B.acc, 0, sizeof(BwdAcc), s));
+  TM_CUDA(c, cudaMemsetAsync(&B.acc->argmin, 0xff, 2 * sizeof(unsigned long long), s));
+  const DevParams P = dev_params(c->p, J.qbits);
+  const int64_t nfwd = c->launches;
+  const int nb = launch_backward(P, J, B, s);
+  mark(c, s, ST_BWD_ADJOINT);
+  if ((st = check_launch(c, "backward launch"))) return st;
+  c->launches = nfwd + nb;
+  return TM_OK;
 }
 
 tm_status tm_integral_image(const int32_t *q, int32_t width, int32_t height, int64_t *s1,
