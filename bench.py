@@ -128,7 +128,7 @@ def oracle_rate(img, wl, budget_s: float, seed: int = 0):
     H, W = img.shape[:2]
     rng = np.random.default_rng(seed)
     done, t0 = 0, time.perf_counter()
-    chunk = 64
+    chunk = 2048
     # each call re-runs the O(N) pre-pass; its cost is part of the oracle
     while time.perf_counter() - t0 < budget_s:
         ys = rng.integers(0, H, chunk)
@@ -295,6 +295,149 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------- other workloads --
+def _timed(fn, steps, stream):
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(steps):
+        fn(i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_batch_workload(args, kind):
+    """Batched graph path vs per-image forward on the same images.
+    batch-video: 120 1920x1080 FP16 frames (moving rectangles over a drifting
+    ramp, per-frame noise), 32 bins, half-sizes 8/32/128, FP16 output.
+    batch-uneven: 64 float32 images, W ~ U{640..4096}, 4:3 or 16:9, 64 bins."""
+    import torch
+
+    import paper_2102_01289_gb300 as tm
+    import synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    tm.build()
+    if kind == "batch-video":
+        n, dt = 120, np.float16
+        frames = [synth.wdr_video_frame(1080, 1920, seed=7 + rank, frame=f) for f in range(n)]
+        params = tm.make_params(32, [8, 32, 128])
+        name = "wdr-video-1080p-fp16-x120"
+    else:
+        dt = np.float32
+        sizes = synth.uneven_sizes(64, seed=rank)
+        frames = [synth.wdr_image(h, w, seed=k + 100 * rank) for k, (w, h) in enumerate(sizes)]
+        params = tm.make_params(64, [8, 32, 128])
+        name = "wdr-uneven-x64"
+    npx = sum(f.shape[0] * f.shape[1] for f in frames)
+    xs = [torch.from_numpy(f).to(dev) for f in frames]
+    ys = [torch.empty_like(x) for x in xs]
+    ctx = tm.tm_create(params)
+    stream = torch.cuda.current_stream(dev)
+    clocks = ClockSampler(local)
+    for _ in range(args.warmup):
+        tm.tm_forward_batch(ctx, xs, ys, stream)
+    launches = tm.tm_last_launch_count(ctx)
+    clocks.start()
+    time.sleep(0.3)
+    ms_batch = _timed(lambda i: tm.tm_forward_batch(ctx, xs, ys, stream), args.steps, stream)
+    clk = clocks.stop()
+    # per-image forward on the same images
+    for x, y in zip(xs[:4], ys[:4]):
+        tm.tm_forward(ctx, x, y, stream)
+
+    def per_image(i):
+        for x, y in zip(xs, ys):
+            tm.tm_forward(ctx, x, y, stream)
+
+    ms_single = _timed(per_image, max(1, args.steps // 2), stream)
+    tm.tm_destroy(ctx)
+    bpp = 18 if kind == "batch-video" else 36
+    peak, peak_kind = load_peaks()
+    value = npx / (ms_batch / 1e3) / 1e6
+    line = {
+        "metric": METRIC, "value": value, "unit": "MP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_batch, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f16" if dt == np.float16 else "f32", "data": "synthetic",
+        "config": {"workload": name, "images": len(frames), "megapixels": npx / 1e6,
+                   "n_bins": params.n_bins, "radii": [8, 32, 128], "path": "batched graph",
+                   "l2": "inputs larger than L2"},
+        "per_image_forward": {"value": npx / (ms_single / 1e3) / 1e6, "unit": "MP/s", "ms": ms_single},
+        "path_roofline": {"bytes_per_px": bpp, "achieved": bpp * npx / (ms_batch / 1e3) / 1e9,
+                          "peak": peak, "unit": "GB/s",
+                          "frac": bpp * npx / (ms_batch / 1e3) / 1e9 / peak, "peak_kind": peak_kind},
+        "clocks": clk, "gpu_launches": int(launches * args.steps),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_fwd_bwd(args):
+    """16 float32 1024x1024 images, 32 bins, half-sizes 8/32/128: forward
+    plus hand-written backward (input and parameter gradients), against the
+    plain forward of the same images."""
+    import torch
+
+    import paper_2102_01289_gb300 as tm
+    import synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    tm.build()
+    n, H, W = 16, 1024, 1024
+    xs = [torch.from_numpy(synth.wdr_image(H, W, seed=s + 16 * rank)).to(dev) for s in range(n)]
+    ys = [torch.empty_like(x) for x in xs]
+    gs = [torch.randn_like(x) for x in xs]
+    gins = [torch.empty_like(x) for x in xs]
+    params = tm.make_params(32, [8, 32, 128])
+    gp = torch.empty(3 + 2 * 3, device=dev)
+    ctx = tm.tm_create(params)
+    stream = torch.cuda.current_stream(dev)
+
+    def fwd(i):
+        for x, y in zip(xs, ys):
+            tm.tm_forward(ctx, x, y, stream)
+
+    def fwd_bwd(i):
+        for x, y, g, gi in zip(xs, ys, gs, gins):
+            tm.tm_forward(ctx, x, y, stream)
+            tm.tm_backward(ctx, x, g, gi, gp, stream)
+
+    for _ in range(args.warmup):
+        fwd_bwd(0)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ms_fb = _timed(fwd_bwd, args.steps, stream)
+    clk = clocks.stop()
+    ms_f = _timed(fwd, args.steps, stream)
+    tm.tm_destroy(ctx)
+    npx = n * H * W
+    peak, peak_kind = load_peaks()
+    line = {
+        "metric": METRIC, "value": npx / (ms_fb / 1e3) / 1e6, "unit": "MP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_fb, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "wdr-1mp-x16-fwd-bwd", "images": n, "height": H, "width": W,
+                   "n_bins": 32, "radii": [8, 32, 128], "l2": "inputs larger than L2"},
+        "forward_only": {"value": npx / (ms_f / 1e3) / 1e6, "unit": "MP/s", "ms": ms_f},
+        "path_roofline": {"bytes_per_px": 36 + 48, "achieved": 84 * npx / (ms_fb / 1e3) / 1e9,
+                          "peak": peak, "unit": "GB/s", "frac": 84 * npx / (ms_fb / 1e3) / 1e9 / peak,
+                          "peak_kind": peak_kind},
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def load_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary."""
     if not kernel:
@@ -331,11 +474,17 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="fwd-12mp",
+                    choices=["fwd-12mp", "batch-video", "batch-uneven", "fwd-bwd"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload in ("batch-video", "batch-uneven"):
+        return run_batch_workload(args, args.workload)
+    if args.workload == "fwd-bwd":
+        return run_fwd_bwd(args)
     return run_ours(args)
 
 

@@ -17,6 +17,18 @@
 
 using namespace tmk;
 
+namespace {
+// Pinned host staging of one call's job array and sweep queue.
+struct Staging {
+  Job *jobs = nullptr;
+  int2 *items = nullptr;
+  size_t jobs_bytes = 0, items_bytes = 0;
+  cudaEvent_t done = nullptr;  // recorded after the last copy out of this slot
+  bool pending = false;
+};
+constexpr int kStagingSlots = 4;
+}  // namespace
+
 struct tm_ctx {
   tm_params p;
   std::string err;
@@ -30,12 +42,22 @@ struct tm_ctx {
   size_t ws_bytes = 0;
   Stats *stats = nullptr;  // one per image of the largest batch so far
   int stats_n = 0;
-  Job *djobs = nullptr;    // device copy of the job array
+  // job descriptors and sweep queue: pinned host staging copied to device
+  // buffers at the start of each call. The device buffers are stream-ordered
+  // like the workspace; the host staging is not (the copy runs when the
+  // stream reaches it), so calls rotate over several staging slots and wait,
+  // before rewriting a slot, for the event recorded after its last copy.
+  // The cached batch graph has its own staging and device buffers: its copy
+  // nodes read them at every replay.
+  Staging slots[kStagingSlots];
+  int slot_next = 0;
+  Job *djobs = nullptr;    // device copy of the job array (calls outside the graph)
   int2 *ditems = nullptr;  // device copy of the sweep queue
   size_t djobs_bytes = 0, ditems_bytes = 0;
-  Job *hjobs = nullptr;    // pinned host staging of the job array
-  int2 *hitems = nullptr;  // pinned host staging of the sweep queue
-  size_t hjobs_bytes = 0, hitems_bytes = 0;
+  Staging gstage;          // staging read by the cached graph
+  Job *gdjobs = nullptr;   // device buffers written by the cached graph
+  int2 *gditems = nullptr;
+  size_t gdjobs_bytes = 0, gditems_bytes = 0;
   // backward workspace
   void *bws = nullptr;
   size_t bws_bytes = 0;
@@ -259,21 +281,43 @@ tm_status grow_device(tm_ctx *c, void **p, size_t *have, size_t bytes) {
   return TM_OK;
 }
 
-tm_status grow_pinned(tm_ctx *c, void **p, size_t *have, size_t bytes) {
+// Pinned host buffer of at least `bytes`; the caller has made sure no copy
+// still reads the old one.
+tm_status grow_host(tm_ctx *c, void **p, size_t *have, size_t bytes) {
   if (*have >= bytes) return TM_OK;
-  drop_graph(c);
-  if (*p) {
-    TM_CUDA(c, cudaDeviceSynchronize());
-    cudaFreeHost(*p);
-    *p = nullptr;
-    *have = 0;
-  }
+  if (*p) cudaFreeHost(*p);
+  *p = nullptr;
+  *have = 0;
   cudaError_t e = cudaMallocHost(p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(c, TM_ENOMEM, "pinned allocation of %zu bytes: %s", bytes, cudaGetErrorString(e));
   }
   *have = bytes;
+  return TM_OK;
+}
+
+// A staging slot able to hold `njobs` jobs and `nitems` queue items, free to
+// be rewritten: waits for the copies that last read it.
+tm_status acquire_staging(tm_ctx *c, Staging *S, int njobs, int nitems) {
+  if (!S->done) TM_CUDA(c, cudaEventCreateWithFlags(&S->done, cudaEventDisableTiming));
+  if (S->pending) TM_CUDA(c, cudaEventSynchronize(S->done));
+  S->pending = false;
+  tm_status st;
+  if ((st = grow_host(c, (void **)&S->jobs, &S->jobs_bytes, sizeof(Job) * std::max(njobs, 1)))) return st;
+  return grow_host(c, (void **)&S->items, &S->items_bytes, sizeof(int2) * std::max(nitems, 1));
+}
+
+Staging *next_slot(tm_ctx *c) {
+  Staging *S = &c->slots[c->slot_next];
+  c->slot_next = (c->slot_next + 1) % kStagingSlots;
+  return S;
+}
+
+// Event after the copies out of S on stream s.
+tm_status release_staging(tm_ctx *c, Staging *S, cudaStream_t s) {
+  TM_CUDA(c, cudaEventRecord(S->done, s));
+  S->pending = true;
   return TM_OK;
 }
 
@@ -352,7 +396,8 @@ tm_status forward_materialised(tm_ctx *c, const tm_image *in, const tm_image *ou
   if ((st = ensure_stats(c, 1))) return st;
   if ((st = grow_device(c, &c->ws, &c->ws_bytes, total))) return st;
   if ((st = grow_device(c, (void **)&c->djobs, &c->djobs_bytes, sizeof(Job)))) return st;
-  if ((st = grow_pinned(c, (void **)&c->hjobs, &c->hjobs_bytes, sizeof(Job)))) return st;
+  Staging *S = next_slot(c);
+  if ((st = acquire_staging(c, S, 1, 0))) return st;
   char *ws = static_cast<char *>(c->ws);
   Job J{};
   J.in = to_image(in);
@@ -376,9 +421,9 @@ tm_status forward_materialised(tm_ctx *c, const tm_image *in, const tm_image *ou
   const int rb = range_blocks(W, H, c->num_sms, 1.0), pb = prep_blocks(W, H, c->num_sms, 1.0);
   const int cb = col_blocks(W, nseg);
   J.b0[kStRange] = J.b0[kStPrep] = J.b0[kStRows] = J.b0[kStCols] = J.b0[kStLook] = 0;
-  drop_graph(c);  // the staging below is what a cached graph copies
-  *c->hjobs = J;
-  TM_CUDA(c, cudaMemcpyAsync(c->djobs, c->hjobs, sizeof(Job), cudaMemcpyHostToDevice, s));
+  *S->jobs = J;
+  TM_CUDA(c, cudaMemcpyAsync(c->djobs, S->jobs, sizeof(Job), cudaMemcpyHostToDevice, s));
+  if ((st = release_staging(c, S, s))) return st;
   int64_t n = 0;
   mark(c, s, -1);
   launch_range(c->djobs, 1, rb, c->p.n_bins, s);
@@ -418,6 +463,7 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   tm_status st;
   if (graph && c->graph && same_images(c->graph_in, in, nimg) && same_images(c->graph_out, out, nimg)) {
     TM_CUDA(c, cudaGraphLaunch(c->graph, s));
+    if ((st = release_staging(c, &c->gstage, s))) return st;
     c->launches = c->graph_launches;
     return TM_OK;
   }
@@ -468,10 +514,16 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   const int nitems = (int)items.size();
   if ((st = ensure_stats(c, nimg))) return st;
   if ((st = grow_device(c, &c->ws, &c->ws_bytes, ws_total))) return st;
-  if ((st = grow_device(c, (void **)&c->djobs, &c->djobs_bytes, sizeof(Job) * nimg))) return st;
-  if ((st = grow_device(c, (void **)&c->ditems, &c->ditems_bytes, sizeof(int2) * nitems + sizeof(int)))) return st;
-  if ((st = grow_pinned(c, (void **)&c->hjobs, &c->hjobs_bytes, sizeof(Job) * nimg))) return st;
-  if ((st = grow_pinned(c, (void **)&c->hitems, &c->hitems_bytes, sizeof(int2) * nitems))) return st;
+  if (graph) drop_graph(c);  // re-captured below
+  Job **djobs = graph ? &c->gdjobs : &c->djobs;
+  int2 **ditems = graph ? &c->gditems : &c->ditems;
+  if ((st = grow_device(c, (void **)djobs, graph ? &c->gdjobs_bytes : &c->djobs_bytes, sizeof(Job) * nimg)))
+    return st;
+  if ((st = grow_device(c, (void **)ditems, graph ? &c->gditems_bytes : &c->ditems_bytes,
+                        sizeof(int2) * nitems + sizeof(int))))
+    return st;
+  Staging *S = graph ? &c->gstage : next_slot(c);
+  if ((st = acquire_staging(c, S, nimg, nitems))) return st;
   char *ws = static_cast<char *>(c->ws);
   for (int i = 0; i < nimg; ++i) {
     Job &J = jobs[(size_t)i];
@@ -494,35 +546,36 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
       J.dbg.l = reinterpret_cast<float *>(b + L.dl);
     }
   }
-  if (!graph) drop_graph(c);  // the staging below is what a cached graph copies
-  memcpy(c->hjobs, jobs.data(), sizeof(Job) * nimg);
-  for (int k = 0; k < nitems; ++k) c->hitems[k] = items[(size_t)k].second;
+  memcpy(S->jobs, jobs.data(), sizeof(Job) * nimg);
+  for (int k = 0; k < nitems; ++k) S->items[k] = items[(size_t)k].second;
   const DevParams P = dev_params(c->p, jobs[0].qbits);  // qbits is per job
-  int *queue = reinterpret_cast<int *>(c->ditems + nitems);
+  Job *dj = *djobs;
+  int2 *di = *ditems;
+  int *queue = reinterpret_cast<int *>(di + nitems);
   const int ctas = std::min(nitems, c->num_sms);
   // a batch is captured on the context's own stream (capture is not allowed on
   // the legacy default stream) and the graph is then launched on the caller's
   const cudaStream_t caller = s;
   if (graph) {
-    drop_graph(c);
     if (!c->graph_stream) TM_CUDA(c, cudaStreamCreateWithFlags(&c->graph_stream, cudaStreamNonBlocking));
     s = c->graph_stream;
     TM_CUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   }
-  cudaMemcpyAsync(c->djobs, c->hjobs, sizeof(Job) * nimg, cudaMemcpyHostToDevice, s);
-  cudaMemcpyAsync(c->ditems, c->hitems, sizeof(int2) * nitems, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(dj, S->jobs, sizeof(Job) * nimg, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(di, S->items, sizeof(int2) * nitems, cudaMemcpyHostToDevice, s);
+  if (!graph && (st = release_staging(c, S, s))) return st;
   int64_t n = 0;
   if (!graph) mark(c, s, -1);
-  launch_range(c->djobs, nimg, b_range, c->p.n_bins, s);
+  launch_range(dj, nimg, b_range, c->p.n_bins, s);
   if (!graph) mark(c, s, ST_RANGE);
-  launch_prep(c->djobs, nimg, b_prep, c->p.n_bins, s);
+  launch_prep(dj, nimg, b_prep, c->p.n_bins, s);
   if (!graph) mark(c, s, ST_PREP);
-  n += 2 + launch_integral_jobs(c->djobs, nimg, b_rows, b_cols, multi_seg, s);
+  n += 2 + launch_integral_jobs(dj, nimg, b_rows, b_cols, multi_seg, s);
   if (!graph) mark(c, s, ST_INTEGRAL);
-  const int ls = launch_sweep(P, c->djobs, c->ditems, nitems, queue, smem, ctas, s);
+  const int ls = launch_sweep(P, dj, di, nitems, queue, smem, ctas, s);
   if (!graph) mark(c, s, ST_SWEEP);
   if (do_lookup) {
-    n += launch_lookup_counts(P, c->djobs, nimg, b_look, s) + 1;
+    n += launch_lookup_counts(P, dj, nimg, b_look, s) + 1;
     if (!graph) mark(c, s, ST_LOOKUP);
   }
   if (graph) {
@@ -543,6 +596,7 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
     c->graph_out.assign(out, out + nimg);
     c->graph_launches = n;
     TM_CUDA(c, cudaGraphLaunch(c->graph, caller));
+    if ((st = release_staging(c, S, caller))) return st;
   } else if (ls < 0) {
     return check_launch(c, "sweep shared-memory attribute");
   }
@@ -625,7 +679,7 @@ tm_status tm_create(const tm_params *params, tm_ctx **out) {
 
 void tm_destroy(tm_ctx *c) {
   if (!c) return;
-  if (c->ws || c->stats || c->stage || c->djobs || c->graph) cudaDeviceSynchronize();
+  if (c->ws || c->stats || c->stage || c->djobs || c->gdjobs || c->graph) cudaDeviceSynchronize();
   drop_graph(c);
   for (auto &call : c->marks)
     for (auto &m : call) cudaEventDestroy(m.first);
@@ -637,8 +691,15 @@ void tm_destroy(tm_ctx *c) {
   if (c->djobs) cudaFree(c->djobs);
   if (c->ditems) cudaFree(c->ditems);
   if (c->graph_stream) cudaStreamDestroy(c->graph_stream);
-  if (c->hjobs) cudaFreeHost(c->hjobs);
-  if (c->hitems) cudaFreeHost(c->hitems);
+  if (c->gdjobs) cudaFree(c->gdjobs);
+  if (c->gditems) cudaFree(c->gditems);
+  auto free_staging = [](Staging &S) {
+    if (S.jobs) cudaFreeHost(S.jobs);
+    if (S.items) cudaFreeHost(S.items);
+    if (S.done) cudaEventDestroy(S.done);
+  };
+  free_staging(c->gstage);
+  for (Staging &S : c->slots) free_staging(S);
   delete c;
 }
 
@@ -779,7 +840,8 @@ tm_status tm_backward(tm_ctx *c, const tm_image *in, const tm_image *grad_out,
   const size_t N = (size_t)W * H, plane = (size_t)(W + 1) * (H + 1);
   const size_t o_acc = 0, o_u = align256(sizeof(BwdAcc)), o_v = o_u + align256(4 * N * nf),
                o_gi = o_v + align256(4 * N * nf), o_iu = o_gi + align256(4 * N),
-               total = o_iu + 8 * plane * 2 * nf;
+               o_cs = o_iu + align256(8 * plane * 2 * nf),
+               total = o_cs + 8 * hist_scratch_elems(W, H, 2 * nf);
   if ((st = grow_device(c, &c->bws, &c->bws_bytes, total))) return st;
   char *b = static_cast<char *>(c->bws);
   BwdJob B{};
@@ -792,6 +854,7 @@ tm_status tm_backward(tm_ctx *c, const tm_image *in, const tm_image *grad_out,
   B.gi_direct = reinterpret_cast<float *>(b + o_gi);
   B.IU = reinterpret_cast<double *>(b + o_iu);
   B.IV = B.IU + plane * nf;
+  B.colscr = reinterpret_cast<double *>(b + o_cs);
   TM_CUDA(c, cudaMemsetAsync(B.acc, 0, sizeof(BwdAcc), s));
   TM_CUDA(c, cudaMemsetAsync(&B.acc->argmin, 0xff, 2 * sizeof(unsigned long long), s));
   const DevParams P = dev_params(c->p, J.qbits);

@@ -189,17 +189,6 @@ __global__ void __launch_bounds__(kBT) k_rows_f64(const float *__restrict__ src,
   }
 }
 
-__global__ void k_cols_f64(double *base, long long plane, int cols, int rows) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x, pl = blockIdx.y;
-  if (c >= cols) return;
-  double *P = base + pl * plane;
-  double acc = 0.0;
-  for (int r = 1; r < rows; ++r) {
-    acc += P[(long long)r * cols + c];
-    P[(long long)r * cols + c] = acc;
-  }
-}
-
 // Per pixel: the adjoint of the window variances, through the normalised log,
 // into the luminance and Eq. 11; range-term partial sums.
 __global__ void __launch_bounds__(kBT) k_bwd_input(DevParams P, Job J, BwdJob B) {
@@ -293,12 +282,11 @@ int launch_backward(const DevParams &P, const Job &J, const BwdJob &B, cudaStrea
   dim3 rg(H, P.n_fields);
   k_rows_f64<<<rg, kBT, 0, s>>>(B.U, W, H, B.IU);
   k_rows_f64<<<rg, kBT, 0, s>>>(B.V, W, H, B.IV);
-  // U and V integral planes are contiguous: one column pass over 2s planes
-  dim3 cg((W + 1 + 127) / 128, 2 * P.n_fields);
-  k_cols_f64<<<cg, 128, 0, s>>>(B.IU, plane, W + 1, H + 1);
+  // U and V integral planes are contiguous: one segmented column pass over 2s planes
+  const int nc = launch_column_pass_f64(B.IU, plane, 2 * P.n_fields, W, H, B.colscr, s);
   k_bwd_input<<<blocks, kBT, 0, s>>>(P, J, B);
   k_bwd_finish<<<1, 32, 0, s>>>(P, J, B);
-  return 6;
+  return 5 + nc;
 }
 
 }  // namespace tmk

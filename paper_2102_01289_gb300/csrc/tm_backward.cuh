@@ -21,6 +21,7 @@ struct BwdJob {
   float *U, *V;        // s x H x W: u_f = 2 dLoss/ds_f / N_f and u_f * mu_f
   float *gi_direct;    // H x W: dLoss/di through Eq. 12 directly
   double *IU, *IV;     // s planes of (H+1) x (W+1) each, contiguous (IV = IU + s planes)
+  double *colscr;      // column-pass segment totals, hist_scratch_elems(W, H, 2s) doubles
   BwdAcc *acc;
 };
 

@@ -104,3 +104,35 @@ def test_empty_batch_is_noop():
         assert tm.tm_last_launch_count(ctx) == 0
     finally:
         tm.tm_destroy(ctx)
+
+
+def test_unsynchronised_calls_of_different_sizes():
+    """Calls issued back to back without synchronisation, on images whose sizes
+    (and so job layouts, sweep plans and tile queues) all differ, interleaved
+    with batch captures and replays: the per-call descriptor staging must not
+    be rewritten while an earlier call's copy is still pending."""
+    p = tm.make_params(32, [4, 16, 64])
+    sizes = [(1500, 1000), (97, 61), (1200, 900), (333, 257), (1024, 1024), (45, 900), (800, 600)]
+    xs = [torch.from_numpy(synth.wdr_image(h, w, seed=70 + i)).cuda() for i, (w, h) in enumerate(sizes)]
+    ctx = tm.tm_create(p)
+    try:
+        refs = []
+        for x in xs:
+            refs.append(_single(ctx, x))
+            torch.cuda.synchronize()
+        ys = [torch.empty_like(x) for x in xs]
+        for rep in range(3):
+            for x, y in zip(xs, ys):
+                tm.tm_forward(ctx, x, y)
+            yb = [torch.empty_like(x) for x in xs[:3]]
+            tm.tm_forward_batch(ctx, xs[:3], yb)  # capture, then replays
+            for x, y in zip(reversed(xs), reversed(ys)):
+                tm.tm_forward(ctx, x, y)
+            tm.tm_forward_batch(ctx, xs[:3], yb)
+        torch.cuda.synchronize()
+        for y, r in zip(ys, refs):
+            assert torch.equal(y, r)
+        for y, r in zip(yb, refs[:3]):
+            assert torch.equal(y, r)
+    finally:
+        tm.tm_destroy(ctx)
