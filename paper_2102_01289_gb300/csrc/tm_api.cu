@@ -852,9 +852,9 @@ tm_status tm_backward(tm_ctx *c, const tm_image *in, const tm_image *grad_out,
   B.U = reinterpret_cast<float *>(b + o_u);
   B.V = reinterpret_cast<float *>(b + o_v);
   B.gi_direct = reinterpret_cast<float *>(b + o_gi);
-  B.IU = reinterpret_cast<double *>(b + o_iu);
+  B.IU = reinterpret_cast<unsigned long long *>(b + o_iu);
   B.IV = B.IU + plane * nf;
-  B.colscr = reinterpret_cast<double *>(b + o_cs);
+  B.colscr = reinterpret_cast<unsigned long long *>(b + o_cs);
   TM_CUDA(c, cudaMemsetAsync(B.acc, 0, sizeof(BwdAcc), s));
   TM_CUDA(c, cudaMemsetAsync(&B.acc->argmin, 0xff, 2 * sizeof(unsigned long long), s));
   const DevParams P = dev_params(c->p, J.qbits);

@@ -16,58 +16,72 @@
 //           u_f = 2 gs_f / N_f, v_f = u_f mu_f. The windows are symmetric, so
 //           the adjoint of the window sum is the same clipped box sum around
 //           r (the reversed scan of the integral image, Eq. 5-6). The box sums
-//           of u and v come from FP64 integral images.
+//           of u and v come from integral images of u and v in 64-bit fixed
+//           point, one binary scale per plane chosen from its largest |value|
+//           so that every window sum fits in 62 bits; the sums are exact
+//           modulo 2^64, so only the conversion to fixed point rounds.
 //   lhat    = (ln i - ln imin) / D: dlhat/di = 1 / (i D), plus the range terms
 //           through ln imin and ln imax, routed to the first pixel (raster
 //           order) holding imin / imax.
 //   Eq. 11  i = 0.2126 R + 0.7152 G + 0.0722 B (no gradient where floored).
-// Parameter gradients are reduced in FP64 per block and added with atomics.
+// Per-pixel arithmetic is FP32 (FP64 throughput is a small fraction of FP32
+// on this part). Parameter gradients are summed per block in FP32 and the
+// block sums added into FP64 accumulators with one atomic each.
 #include "tm_backward.cuh"
 
 namespace tmk {
 namespace {
 
 constexpr int kBT = 256;
+constexpr int kWarpsB = kBT / 32;
+// per-thread partials: [ld_min, ld_max, sat, eps[kMaxFields], alpha[kMaxFields]]
+constexpr int kNAcc = 3 + 2 * kMaxFields;
 
-__device__ __forceinline__ double block_sum_d(double v, double *sh) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) sh[wid] = v;
-  __syncthreads();
-  double t = 0.0;
-  if (threadIdx.x < 32) {
-    t = threadIdx.x < (int)(blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-  }
-  return t;  // valid in thread 0
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Largest window of field f (pixels), as a float.
+__device__ __forceinline__ float window_max(const DevParams &P, int f, int W, int H) {
+  return (float)min(2 * P.rx[f] + 1, W) * (float)min(2 * P.ry[f] + 1, H);
+}
+
+// Binary scale of a fixed-point plane whose largest |value| has bits `amax`:
+// every window sum of round(value x 2^shift) stays below 2^61 in magnitude.
+__device__ __forceinline__ int fix_shift(unsigned amax, float nmax) {
+  const float m = __uint_as_float(amax) * nmax;
+  if (!(m > 0.f) || !(m < 3.0e38f)) return 0;
+  int e;
+  frexpf(m, &e);  // m < 2^e
+  return 61 - e;
 }
 
 // Per pixel: forward recomputation, Eq. 12/3/2/4 adjoints, u_f and v_f,
-// direct gradients of the colour restoration, parameter partial sums.
+// direct gradients of the colour restoration, parameter partial sums and the
+// largest |u_f|, |v_f| (for the fixed-point scales).
 __global__ void __launch_bounds__(kBT) k_bwd_pixel(DevParams P, Job J, BwdJob B) {
-  __shared__ double sh[32];
+  __shared__ float sh[kNAcc][kWarpsB];
+  __shared__ unsigned shm[2 * kMaxFields][kWarpsB];
   const int W = J.in.W, H = J.in.H;
   const long long N = (long long)W * H;
   const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int s = P.n_fields;
-  double acc_ld0 = 0.0, acc_ld1 = 0.0, acc_sat = 0.0, acc_eps[kMaxFields], acc_alpha[kMaxFields];
+  float acc[kNAcc];
+  unsigned amax[2 * kMaxFields];
 #pragma unroll
-  for (int f = 0; f < kMaxFields; ++f) acc_eps[f] = acc_alpha[f] = 0.0;
+  for (int k = 0; k < kNAcc; ++k) acc[k] = 0.f;
+#pragma unroll
+  for (int k = 0; k < 2 * kMaxFields; ++k) amax[k] = 0u;
   if (pix < N) {
     const int y = (int)(pix / W), x = (int)(pix - (long long)y * W);
     const SweepPlan &S = J.plan;
     const float inv_scale = ldexpf(1.f, -J.qbits);
     const float inv_scale2 = inv_scale * inv_scale;
     unsigned cnt[kMaxFields];
-#pragma unroll
-    for (int f = 0; f < kMaxFields; ++f) cnt[f] = 0u;
-    for (int sl = 0; sl < S.nslabs; ++sl) {
-      const int T = max(y + S.slab_a[sl] - 1, -1), Bb = min(y + S.slab_b[sl], H - 1);
-      if (Bb > T) cnt[S.slab_field[sl]] += J.counts[sl * N + pix];
-    }
+    slab_counts(S, J.counts, N, pix, y, H, cnt);
     const long long W1 = (long long)W + 1;
-    float area[kMaxFields], var[kMaxFields], mu[kMaxFields];
+    float rarea[kMaxFields], var[kMaxFields], mu[kMaxFields];
 #pragma unroll
     for (int f = 0; f < kMaxFields; ++f) {
       if (f >= s) break;
@@ -79,14 +93,16 @@ __global__ void __launch_bounds__(kBT) k_bwd_pixel(DevParams P, Job J, BwdJob B)
                                        (unsigned long long)J.s1[iB] + (unsigned long long)J.s1[iA]);
       const long long q2 = (long long)((unsigned long long)J.s2[iC] - (unsigned long long)J.s2[iD] -
                                        (unsigned long long)J.s2[iB] + (unsigned long long)J.s2[iA]);
-      area[f] = (float)Nw;
-      var[f] = window_variance(q1, q2, area[f], Nw, inv_scale2);
-      mu[f] = (float)((double)q1 / (double)Nw) * inv_scale + 0.5f;  // mean of lhat
+      rarea[f] = __frcp_rn((float)Nw);
+      var[f] = window_variance(q1, q2, Nw, rarea[f], inv_scale2);
+      mu[f] = (float)q1 * rarea[f] * inv_scale + 0.5f;  // mean of lhat
     }
     float wv[kMaxFields], lf[kMaxFields];
-    const float L = fuse_fields(P, cnt, area, var, wv, lf);
+    const float L = fuse_fields(P, cnt, rarea, var, wv, lf);
     float wsum = 0.f;
-    for (int f = 0; f < s; ++f) wsum += wv[f];
+#pragma unroll
+    for (int f = 0; f < kMaxFields; ++f)
+      if (f < s) wsum += wv[f];
     // Eq. 12
     float rgb[3];
     load_rgb(J.in, x, y, rgb[0], rgb[1], rgb[2]);
@@ -96,6 +112,7 @@ __global__ void __launch_bounds__(kBT) k_bwd_pixel(DevParams P, Job J, BwdJob B)
     const float inv_i = __frcp_rn(i);
     const float *go = static_cast<const float *>(B.grad_out.p) + (long long)y * B.grad_out.pitch + 3LL * x;
     float gL = 0.f, gi_direct = 0.f, gC[3];
+#pragma unroll
     for (int c = 0; c < 3; ++c) {
       const float g = go[c];
       const float rho = rgb[c] * inv_i;
@@ -106,27 +123,32 @@ __global__ void __launch_bounds__(kBT) k_bwd_pixel(DevParams P, Job J, BwdJob B)
       }
       const float rs = exp2f(P.sat * __log2f(rho));
       gL += g * rs;
-      acc_sat += (double)g * rs * __logf(rho) * L;
+      acc[2] += g * rs * __logf(rho) * L;
       gC[c] = g * P.sat * rs * L * inv_i / rho;
       gi_direct -= g * P.sat * rs * L * inv_i;
     }
     // Eq. 3, 2, 4
-    const float span = P.ld_max - P.ld_min;
-    for (int f = 0; f < s; ++f) {
-      const float Pf = (float)cnt[f] / area[f];
-      const float dLdLf = wsum > 0.f ? wv[f] / wsum : 1.f / (float)s;
-      const float dLdW = wsum > 0.f ? (lf[f] - L) / wsum : 0.f;
-      acc_ld0 += (double)gL * dLdLf * (1.f - Pf);
-      acc_ld1 += (double)gL * dLdLf * Pf;
+    const float rws = wsum > 0.f ? 1.f / wsum : 0.f;
+#pragma unroll
+    for (int f = 0; f < kMaxFields; ++f) {
+      if (f >= s) break;
+      const float Pf = (float)cnt[f] * rarea[f];
+      const float dLdLf = wsum > 0.f ? wv[f] * rws : 1.f / (float)s;
+      const float dLdW = (lf[f] - L) * rws;
+      acc[0] += gL * dLdLf * (1.f - Pf);
+      acc[1] += gL * dLdLf * Pf;
       const float gW = gL * dLdW;
       const float v = var[f], e = P.eps[f], a = P.alpha[f];
       const float den = (v + e) * (v + e);
-      acc_eps[f] += (double)gW * (-a * v / den);
-      acc_alpha[f] += (double)gW * (v / (v + e));
+      acc[3 + f] += gW * (-a * v / den);
+      acc[3 + kMaxFields + f] += gW * (v / (v + e));
       const float gv = gW * a * e / den;
-      const float u = 2.f * gv / area[f];
+      const float u = 2.f * gv * rarea[f];
+      const float vv = u * mu[f];
       B.U[f * N + pix] = u;
-      B.V[f * N + pix] = u * mu[f];
+      B.V[f * N + pix] = vv;
+      amax[f] = max(amax[f], __float_as_uint(fabsf(u)));
+      amax[kMaxFields + f] = max(amax[kMaxFields + f], __float_as_uint(fabsf(vv)));
     }
     B.gi_direct[pix] = gi_direct;
     float *gin = static_cast<float *>(B.grad_in.p) + (long long)y * B.grad_in.pitch + 3LL * x;
@@ -139,47 +161,74 @@ __global__ void __launch_bounds__(kBT) k_bwd_pixel(DevParams P, Job J, BwdJob B)
     if (i == J.st->imin) atomicMin(&B.acc->argmin, (unsigned long long)pix);
     if (i == J.st->imax) atomicMin(&B.acc->argmax, (unsigned long long)pix);
   }
-  // parameter partial sums
-  double t = block_sum_d(acc_ld0, sh);
-  if (threadIdx.x == 0) atomicAdd(&B.acc->g[0], t);
-  t = block_sum_d(acc_ld1, sh);
-  if (threadIdx.x == 0) atomicAdd(&B.acc->g[1], t);
-  t = block_sum_d(acc_sat, sh);
-  if (threadIdx.x == 0) atomicAdd(&B.acc->g[2], t);
-  for (int f = 0; f < s; ++f) {
-    t = block_sum_d(acc_eps[f], sh);
-    if (threadIdx.x == 0) atomicAdd(&B.acc->g[3 + f], t);
-    t = block_sum_d(acc_alpha[f], sh);
-    if (threadIdx.x == 0) atomicAdd(&B.acc->g[3 + s + f], t);
+  // block sums of the parameter partials and block maxima of |u|, |v|
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kNAcc; ++k) {
+    const int f = k < 3 + kMaxFields ? k - 3 : k - 3 - kMaxFields;
+    if (k >= 3 && f >= s) continue;
+    const float t = warp_sum(acc[k]);
+    if (lane == 0) sh[k][wid] = t;
+  }
+#pragma unroll
+  for (int k = 0; k < 2 * kMaxFields; ++k) {
+    if ((k & (kMaxFields - 1)) >= s) continue;
+    const unsigned t = __reduce_max_sync(0xffffffffu, amax[k]);
+    if (lane == 0) shm[k][wid] = t;
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  if (t < kNAcc) {
+    const int f = t < 3 + kMaxFields ? t - 3 : t - 3 - kMaxFields;
+    if (t < 3 || f < s) {
+      float sum = 0.f;
+      for (int w = 0; w < kWarpsB; ++w) sum += sh[t][w];
+      atomicAdd(&B.acc->g[t < 3 + kMaxFields ? t : 3 + s + f], (double)sum);
+    }
+  } else if (t >= 32 && t < 32 + 2 * kMaxFields) {
+    const int k = t - 32;
+    if ((k & (kMaxFields - 1)) < s) {
+      unsigned m = 0u;
+      for (int w = 0; w < kWarpsB; ++w) m = max(m, shm[k][w]);
+      if (m) atomicMax(&B.acc->amax[k], m);
+    }
   }
 }
 
-// Row prefixes of the float planes u_f, v_f into FP64 integral planes.
-__global__ void __launch_bounds__(kBT) k_rows_f64(const float *__restrict__ src, int W, int H,
-                                                  double *__restrict__ dst) {
-  __shared__ double wt[kBT / 32];
-  const long long W1 = (long long)W + 1, plane = W1 * ((long long)H + 1);
-  const int y = blockIdx.x, pl = blockIdx.y;
-  const float *row = src + (long long)pl * W * H + (long long)y * W;
-  double *P = dst + (long long)pl * plane;
+// Row prefixes of the planes u_f (plane f) and v_f (plane s + f) in fixed
+// point into rows 1..H of 64-bit integral planes (row 0 and column 0 zero),
+// modulo 2^64. Block -> (row, plane).
+__global__ void __launch_bounds__(kBT) k_rows_fix(DevParams P, const float *__restrict__ U,
+                                                  const float *__restrict__ V, int W, int H,
+                                                  const BwdAcc *__restrict__ acc,
+                                                  unsigned long long *__restrict__ dst) {
+  __shared__ unsigned long long wt[kWarpsB];
+  const int s = P.n_fields;
+  const int y = blockIdx.x, pl = blockIdx.y, f = pl < s ? pl : pl - s;
+  const long long W1 = (long long)W + 1, plane = W1 * ((long long)H + 1), N = (long long)W * H;
+  const float *row = (pl < s ? U : V) + (long long)f * N + (long long)y * W;
+  const int sh = fix_shift(acc->amax[pl < s ? f : kMaxFields + f], window_max(P, f, W, H));
+  unsigned long long *Pl = dst + (long long)pl * plane;
   if (y == 0)
-    for (long long x = threadIdx.x; x < W1; x += kBT) P[x] = 0.0;
-  double *o = P + (long long)(y + 1) * W1;
-  if (threadIdx.x == 0) o[0] = 0.0;
-  double carry = 0.0;
+    for (long long x = threadIdx.x; x < W1; x += kBT) Pl[x] = 0ull;
+  unsigned long long *o = Pl + (long long)(y + 1) * W1;
+  if (threadIdx.x == 0) o[0] = 0ull;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned long long carry = 0ull;
   for (int base = 0; base < W; base += kBT) {
     const int x = base + threadIdx.x;
-    const double v = x < W ? (double)row[x] : 0.0;
-    double sc = v;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long sc =
+        x < W ? (unsigned long long)__float2ll_rn(ldexpf(row[x], sh)) : 0ull;
+#pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-      const double nb = __shfl_up_sync(0xffffffffu, sc, off);
+      const unsigned long long nb = __shfl_up_sync(0xffffffffu, sc, off);
       if (lane >= off) sc += nb;
     }
     if (lane == 31) wt[wid] = sc;
     __syncthreads();
-    double before = 0.0, total = 0.0;
-    for (int k = 0; k < kBT / 32; ++k) {
+    unsigned long long before = 0ull, total = 0ull;
+#pragma unroll
+    for (int k = 0; k < kWarpsB; ++k) {
       if (k < wid) before += wt[k];
       total += wt[k];
     }
@@ -192,58 +241,65 @@ __global__ void __launch_bounds__(kBT) k_rows_f64(const float *__restrict__ src,
 // Per pixel: the adjoint of the window variances, through the normalised log,
 // into the luminance and Eq. 11; range-term partial sums.
 __global__ void __launch_bounds__(kBT) k_bwd_input(DevParams P, Job J, BwdJob B) {
-  __shared__ double sh[32];
+  __shared__ float sh[2][kWarpsB];
   const int W = J.in.W, H = J.in.H;
   const long long N = (long long)W * H;
   const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const float imin = J.st->imin, imax = J.st->imax;
-  const double D = imax > imin ? log((double)imax) - log((double)imin) : 0.0;
-  double acc_lmin = 0.0, acc_lmax = 0.0;
-  if (pix < N && D > 0.0) {
+  const int s = P.n_fields;
+  // D = ln imax - ln imin = ln 2 x 2^Q / log2_scale (log2_scale = 2^Q / log2(imax / imin))
+  const float l2s = J.st->log2_scale;
+  const float D = J.st->imax > J.st->imin && l2s > 0.f ? 0.69314718f * ldexpf(1.f, J.qbits) / l2s : 0.f;
+  float acc_lmin = 0.f, acc_lmax = 0.f;
+  if (pix < N) {
     const int y = (int)(pix / W), x = (int)(pix - (long long)y * W);
-    const long long W1 = (long long)W + 1, plane = W1 * ((long long)H + 1);
-    const double lh = (double)J.q[pix] * ldexp(1.0, -J.qbits) + 0.5;
-    double gl = 0.0;
-    for (int f = 0; f < P.n_fields; ++f) {
-      Win w = window_of(P, f, x, y, W, H);
-      const long long iA = (long long)w.y0 * W1 + w.x0, iB = (long long)w.y0 * W1 + w.x1 + 1;
-      const long long iC = (long long)(w.y1 + 1) * W1 + w.x1 + 1, iD = (long long)(w.y1 + 1) * W1 + w.x0;
-      const double *IU = B.IU + (long long)f * plane, *IV = B.IV + (long long)f * plane;
-      const double bu = IU[iC] - IU[iD] - IU[iB] + IU[iA];
-      const double bv = IV[iC] - IV[iD] - IV[iB] + IV[iA];
-      gl += lh * bu - bv;
-    }
     float r, g, b;
     load_rgb(J.in, x, y, r, g, b);
     const float raw = __fadd_rn(__fadd_rn(__fmul_rn(0.2126f, r), __fmul_rn(0.7152f, g)), __fmul_rn(0.0722f, b));
-    const float i = fmaxf(raw, kLumFloor);
-    const double gi = gl / ((double)i * D) + (double)B.gi_direct[pix];
-    acc_lmin = gl * (lh - 1.0) / D;
-    acc_lmax = -gl * lh / D;
+    float gi = B.gi_direct[pix];
+    if (D > 0.f) {
+      const long long W1 = (long long)W + 1, plane = W1 * ((long long)H + 1);
+      const float lh = (float)J.q[pix] * ldexpf(1.f, -J.qbits) + 0.5f;
+      float gl = 0.f;
+#pragma unroll
+      for (int f = 0; f < kMaxFields; ++f) {
+        if (f >= s) break;
+        Win w = window_of(P, f, x, y, W, H);
+        const long long iA = (long long)w.y0 * W1 + w.x0, iB = (long long)w.y0 * W1 + w.x1 + 1;
+        const long long iC = (long long)(w.y1 + 1) * W1 + w.x1 + 1, iD = (long long)(w.y1 + 1) * W1 + w.x0;
+        const unsigned long long *IU = B.IU + (long long)f * plane, *IV = B.IV + (long long)f * plane;
+        const long long bu = (long long)(IU[iC] - IU[iD] - IU[iB] + IU[iA]);
+        const long long bv = (long long)(IV[iC] - IV[iD] - IV[iB] + IV[iA]);
+        const float nmax = window_max(P, f, W, H);
+        const float fu = ldexpf(__ll2float_rn(bu), -fix_shift(B.acc->amax[f], nmax));
+        const float fv = ldexpf(__ll2float_rn(bv), -fix_shift(B.acc->amax[kMaxFields + f], nmax));
+        gl += lh * fu - fv;
+      }
+      const float i = fmaxf(raw, kLumFloor);
+      gi += gl / (i * D);
+      acc_lmin = gl * (lh - 1.f) / D;
+      acc_lmax = -gl * lh / D;
+    }
+    // degenerate range: only the direct colour-restoration term reaches i
     if (B.grad_in.p && raw > kLumFloor) {
       float *gin = static_cast<float *>(B.grad_in.p) + (long long)y * B.grad_in.pitch + 3LL * x;
-      gin[0] += (float)(0.2126 * gi);
-      gin[1] += (float)(0.7152 * gi);
-      gin[2] += (float)(0.0722 * gi);
-    }
-  } else if (pix < N && B.grad_in.p) {
-    // degenerate range: only the direct colour-restoration term reaches i
-    const int y = (int)(pix / W), x = (int)(pix - (long long)y * W);
-    float r, g, b;
-    load_rgb(J.in, x, y, r, g, b);
-    const float raw = __fadd_rn(__fadd_rn(__fmul_rn(0.2126f, r), __fmul_rn(0.7152f, g)), __fmul_rn(0.0722f, b));
-    if (raw > kLumFloor) {
-      const double gi = (double)B.gi_direct[pix];
-      float *gin = static_cast<float *>(B.grad_in.p) + (long long)y * B.grad_in.pitch + 3LL * x;
-      gin[0] += (float)(0.2126 * gi);
-      gin[1] += (float)(0.7152 * gi);
-      gin[2] += (float)(0.0722 * gi);
+      gin[0] += 0.2126f * gi;
+      gin[1] += 0.7152f * gi;
+      gin[2] += 0.0722f * gi;
     }
   }
-  double t = block_sum_d(acc_lmin, sh);
-  if (threadIdx.x == 0) atomicAdd(&B.acc->lmin, t);
-  t = block_sum_d(acc_lmax, sh);
-  if (threadIdx.x == 0) atomicAdd(&B.acc->lmax, t);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  acc_lmin = warp_sum(acc_lmin);
+  acc_lmax = warp_sum(acc_lmax);
+  if (lane == 0) {
+    sh[0][wid] = acc_lmin;
+    sh[1][wid] = acc_lmax;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    float sum = 0.f;
+    for (int w = 0; w < kWarpsB; ++w) sum += sh[threadIdx.x][w];
+    atomicAdd(threadIdx.x == 0 ? &B.acc->lmin : &B.acc->lmax, (double)sum);
+  }
 }
 
 // Range terms at the argmin / argmax pixels, and the parameter gradients.
@@ -279,14 +335,14 @@ int launch_backward(const DevParams &P, const Job &J, const BwdJob &B, cudaStrea
   k_bwd_pixel<<<blocks, kBT, 0, s>>>(P, J, B);
   const int W = J.in.W, H = J.in.H;
   const long long plane = ((long long)W + 1) * ((long long)H + 1);
-  dim3 rg(H, P.n_fields);
-  k_rows_f64<<<rg, kBT, 0, s>>>(B.U, W, H, B.IU);
-  k_rows_f64<<<rg, kBT, 0, s>>>(B.V, W, H, B.IV);
-  // U and V integral planes are contiguous: one segmented column pass over 2s planes
-  const int nc = launch_column_pass_f64(B.IU, plane, 2 * P.n_fields, W, H, B.colscr, s);
+  // U and V integral planes are contiguous: one row pass and one segmented
+  // column pass over 2s planes
+  dim3 rg(H, 2 * P.n_fields);
+  k_rows_fix<<<rg, kBT, 0, s>>>(P, B.U, B.V, W, H, B.acc, B.IU);
+  const int nc = launch_column_pass_u64(B.IU, plane, 2 * P.n_fields, W, H, B.colscr, s);
   k_bwd_input<<<blocks, kBT, 0, s>>>(P, J, B);
   k_bwd_finish<<<1, 32, 0, s>>>(P, J, B);
-  return 5 + nc;
+  return 4 + nc;
 }
 
 }  // namespace tmk

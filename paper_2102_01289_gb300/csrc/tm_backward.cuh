@@ -11,6 +11,7 @@ struct BwdAcc {
   double g[3 + 2 * kMaxFields];  // [d ld_min, d ld_max, d sat, d eps[s], d alpha[s]]
   double lmin, lmax;             // dLoss/d ln imin, dLoss/d ln imax (times D)
   unsigned long long argmin, argmax;
+  unsigned amax[2 * kMaxFields];  // float bits of max |u_f| (f) and max |v_f| (kMaxFields + f)
 };
 
 // Buffers of one backward call.
@@ -20,8 +21,9 @@ struct BwdJob {
   float *grad_params;  // device float[3 + 2s] or nullptr
   float *U, *V;        // s x H x W: u_f = 2 dLoss/ds_f / N_f and u_f * mu_f
   float *gi_direct;    // H x W: dLoss/di through Eq. 12 directly
-  double *IU, *IV;     // s planes of (H+1) x (W+1) each, contiguous (IV = IU + s planes)
-  double *colscr;      // column-pass segment totals, hist_scratch_elems(W, H, 2s) doubles
+  unsigned long long *IU, *IV;  // fixed-point integral planes of u_f and v_f: s planes of
+                                //   (H+1) x (W+1) each, contiguous (IV = IU + s planes)
+  unsigned long long *colscr;   // column-pass segment totals, hist_scratch_elems(W, H, 2s)
   BwdAcc *acc;
 };
 

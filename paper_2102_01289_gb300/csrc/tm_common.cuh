@@ -73,7 +73,8 @@ struct SweepPlan {
   int TX, TY, tiles_x, tiles_y;   // output tile and tile grid
   int Rx, Ry;                     // largest half-width / half-height
   int nslabs;                     // row slabs over all fields (each < 2^16 pixels)
-  int slab_field[kMaxSlabs];      // field of each slab
+  int slab_field[kMaxSlabs];      // field of each slab (slabs are ordered by field)
+  int field_slab0[kMaxFields + 1];  // slabs of field f: field_slab0[f] .. field_slab0[f+1]-1
   int slab_a[kMaxSlabs];          // first row offset of the slab (relative to y)
   int slab_b[kMaxSlabs];          // last row offset of the slab
   int ring_len[kMaxSlabs];        // rows of the parked-corner ring of each slab
@@ -213,38 +214,55 @@ __device__ __forceinline__ Win window_of(const DevParams &P, int f, int x, int y
 }
 
 // Exact window variance of q from its window sums (s1 = sum q, s2 = sum q^2):
-// (N s2 - s1^2) / N^2 evaluated in 128-bit integers, then scaled to lhat units.
-__device__ __forceinline__ float window_variance(long long s1, long long s2,
-                                                 float area, unsigned long long N,
-                                                 float inv_scale2) {
+// N s2 - s1^2 evaluated in 128-bit integers, rounded once to float, then
+// scaled by 1/N^2 (rN = rounded 1/N) and 2^-2Q to lhat units.
+__device__ __forceinline__ float window_variance(long long s1, long long s2, unsigned long long N,
+                                                 float rN, float inv_scale2) {
   unsigned long long a1 = (unsigned long long)(s1 < 0 ? -s1 : s1);
   unsigned __int128 num = (unsigned __int128)N * (unsigned long long)s2 -
                           (unsigned __int128)a1 * a1;
   unsigned long long hi = (unsigned long long)(num >> 64);
   unsigned long long lo = (unsigned long long)num;
   float numf = __ull2float_rn(hi) * 18446744073709551616.0f + __ull2float_rn(lo);
-  return numf / (area * area) * inv_scale2;
+  return numf * (rN * rN * inv_scale2);
 }
 
-// Eq. 2, Eq. 4, Eq. 3 from per-field counts / areas / variances.
+// Eq. 2, Eq. 4, Eq. 3 from per-field counts, reciprocal areas and variances.
+// The Eq. 1 quotient is count x (1/N); the Eq. 4 and Eq. 3 quotients use the
+// fast division (about 2 ulp).
 __device__ __forceinline__ float fuse_fields(const DevParams &P, const unsigned *cnt,
-                                             const float *area, const float *var,
+                                             const float *rarea, const float *var,
                                              float *wout, float *lfout) {
   float wsum = 0.f, acc = 0.f, mean = 0.f;
   float span = P.ld_max - P.ld_min;
 #pragma unroll
   for (int f = 0; f < kMaxFields; ++f) {
     if (f >= P.n_fields) break;
-    float Pf = (float)cnt[f] / area[f];                    // Eq. 1
-    float Lf = fmaf(span, Pf, P.ld_min);                   // Eq. 2
-    float Wf = P.alpha[f] * var[f] / (var[f] + P.eps[f]);  // Eq. 4
+    float Pf = (float)cnt[f] * rarea[f];                                 // Eq. 1
+    float Lf = fmaf(span, Pf, P.ld_min);                                 // Eq. 2
+    float Wf = __fdividef(P.alpha[f] * var[f], var[f] + P.eps[f]);      // Eq. 4
     if (wout) wout[f] = Wf;
     if (lfout) lfout[f] = Lf;
     wsum += Wf;
     acc = fmaf(Wf, Lf, acc);
     mean += Lf;
   }
-  return wsum > 0.f ? acc / wsum : mean / (float)P.n_fields;  // Eq. 3
+  return wsum > 0.f ? __fdividef(acc, wsum) : __fdividef(mean, (float)P.n_fields);  // Eq. 3
+}
+
+// Eq. 1 numerators of every field from the sweep's per-slab counts at pixel
+// (x, y) = pix: a slab whose rows all fall outside the image counts 0.
+__device__ __forceinline__ void slab_counts(const SweepPlan &S, const uint16_t *__restrict__ counts,
+                                            long long N, long long pix, int y, int H,
+                                            unsigned *cnt) {
+#pragma unroll
+  for (int f = 0; f < kMaxFields; ++f) {
+    cnt[f] = 0u;
+    for (int s = S.field_slab0[f]; s < S.field_slab0[f + 1]; ++s) {
+      const int T = max(y + S.slab_a[s] - 1, -1), B = min(y + S.slab_b[s], H - 1);
+      if (B > T) cnt[f] += __ldg(counts + s * N + pix);
+    }
+  }
 }
 
 // Eq. 12 with the ratio clamped at zero; inv_i = 1 / i. The power is taken

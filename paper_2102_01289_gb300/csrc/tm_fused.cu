@@ -38,6 +38,7 @@ namespace {
 constexpr int kNT = 512;
 constexpr int kWarps = kNT / 32;
 constexpr int kSeg = 16;  // columns per segment
+constexpr int kTaskMax = 4;  // corner-event tasks per thread (planner: events x TX <= kTaskMax x kNT)
 
 __device__ __forceinline__ unsigned thr_inc(int b, int klo) {
   // thresholds klo (low half) and klo + 1 (high half): [b < k] each
@@ -163,6 +164,29 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const SweepPlan &
     ev_slot = ((ev_y % ev_rlen) + ev_rlen) % ev_rlen;
     ev_bslot = ((ev_y % S.BR) + S.BR) % S.BR;
   }
+  // corner-event tasks of this thread, fixed for the tile: task t = tid + i kNT
+  // is (event e, column xo), e-major so a warp shares one event; the shared
+  // positions of the two columns it reads and its m multiplier are constant
+  int tk_ex[kTaskMax], tk_pos[kTaskMax], tk_coef[kTaskMax];
+  {
+    const int ntask = ne * TXc;
+#pragma unroll
+    for (int i = 0; i < kTaskMax; ++i) {
+      const int t = tid + i * kNT;
+      tk_ex[i] = -1;
+      tk_pos[i] = 0;
+      tk_coef[i] = 0;
+      if (t < ntask) {
+        const int e = t / TXc, xo = t - e * TXc;
+        const int rx = P.rx[S.slab_field[e >> 1]];
+        const int x = X0 + xo;
+        const int ir = min(x + rx, W - 1) - cL, il = max(x - rx - 1, -1) - cL;
+        tk_ex[i] = xo | (e << 16);
+        tk_pos[i] = (ir > 0 ? dpos(ir) : 0) | ((il > 0 ? dpos(il) : 0) << 16);  // position 0 holds 0
+        tk_coef[i] = ir - il;
+      }
+    }
+  }
   int yn_slot = ((rL + S.Ry + 2) % S.BR + S.BR) % S.BR;  // bring slot of the row entering at rL+1
   // bins of the first swept row and of the pixel row entering with it
   int pb = 255, pn = 0;
@@ -255,29 +279,28 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const SweepPlan &
 
     // ---- corner events of row v: top corners park, bottom corners complete ----
     if (!burst) {
-      int (*evt)[4] = evt_buf[v & 1];
-      const int ntask = ne * TXc;
-#pragma unroll 2
-      for (int t = tid; t < ntask; t += kNT) {
-        const int e = min(__float2int_rz(((float)t + 0.5f) * invTX), ne - 1);
-        const int y = evt[e][0];
-        if (y < 0) continue;
-        const int xo = t - e * TXc, x = X0 + xo;
-        const int b = sm.bring[evt[e][2] + xo];
+      const int4 *evt = reinterpret_cast<const int4 *>(evt_buf[v & 1]);
+#pragma unroll
+      for (int i = 0; i < kTaskMax; ++i) {
+        if (tk_ex[i] < 0) continue;
+        const int e = tk_ex[i] >> 16, xo = tk_ex[i] & 0xffff;
+        const int4 ev = evt[e];  // pixel row, ring offset, bin-ring offset
+        if (ev.x < 0) continue;
+        const int b = sm.bring[ev.z + xo];
         unsigned g = 0;
         if (b > kmin) {
-          const int rx = evt[e][3];
           const int kk = b - kmin - 1;
           const int j = kk >> 1, sh = (kk & 1) << 4;
-          const int ir = min(x + rx, W - 1) - cL, il = max(x - rx - 1, -1) - cL;
           const unsigned *row = sm.D + j * S.cstride;
           const unsigned mk = (sm.m[j] >> sh) & 0xffffu;
-          const unsigned dr = ir > 0 ? row[dpos(ir)] : 0u, dl = il > 0 ? row[dpos(il)] : 0u;
-          g = ((dr >> sh) - (dl >> sh) + (unsigned)(ir - il) * mk) & 0xffffu;
+          const unsigned dr = row[tk_pos[i] & 0xffff], dl = row[tk_pos[i] >> 16];
+          g = ((dr >> sh) - (dl >> sh) + (unsigned)tk_coef[i] * mk) & 0xffffu;
         }
-        uint16_t *ac = sm.acc + evt[e][1] + xo;
+        uint16_t *ac = sm.acc + ev.y + xo;
         if (!(e & 1)) *ac = (uint16_t)g;
-        else counts[(long long)(e >> 1) * N + (long long)y * W + x] = (uint16_t)((g - (unsigned)*ac) & 0xffffu);
+        else
+          counts[(long long)(e >> 1) * N + (long long)ev.x * W + X0 + xo] =
+              (uint16_t)((g - (unsigned)*ac) & 0xffffu);
       }
     } else {
       for (int pass = 0; pass < 2; ++pass) {  // tops, then bottoms
@@ -332,7 +355,7 @@ __global__ void __launch_bounds__(kNT, 1)
     k_sweep(DevParams P, const Job *__restrict__ jobs, const int2 *__restrict__ items, int nitems,
             int *queue) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int evt_buf[2][2 * kMaxSlabs][4];
+  __shared__ __align__(16) int evt_buf[2][2 * kMaxSlabs][4];
   __shared__ int item_sh;
   for (;;) {
     if (threadIdx.x == 0) item_sh = atomicAdd(queue, 1);
@@ -385,6 +408,10 @@ bool plan_sweep(const DevParams &P, int W, int H, int num_sms, size_t smem_limit
     }
   }
   base.nslabs = ns;
+  for (int f = 0, s = 0; f <= kMaxFields; ++f) {
+    while (s < ns && base.slab_field[s] < f) ++s;
+    base.field_slab0[f] = s;
+  }
   int bmax = -(1 << 30), ring_total = 0;
   for (int s = 0; s < ns; ++s) {
     base.ring_len[s] = base.slab_b[s] - base.slab_a[s] + 2;
@@ -405,6 +432,7 @@ bool plan_sweep(const DevParams &P, int W, int H, int num_sms, size_t smem_limit
     const int text_max = min(S2.TX + 2 * S2.Rx + 2, W + 1);
     S2.nseg_max = (text_max - 1 + 15) / 16;
     if (S2.nseg_max > 32) continue;  // one lane per 16-column segment
+    if (2 * ns * S2.TX > kTaskMax * kNT) continue;  // corner-event tasks held in registers
     S2.text_max = text_max;
     S2.cstride = (1 + 17 * S2.nseg_max) | 1;
     for (int tiles_y = 1; tiles_y <= H; tiles_y = tiles_y < 8 ? tiles_y + 1 : tiles_y + tiles_y / 4) {

@@ -255,11 +255,11 @@ int launch_integral_jobs(const Job *jobs, int njobs, int row_blocks, int colb, b
   return multi_seg ? 3 : 2;
 }
 
-int launch_column_pass_f64(double *base, long long plane_stride, int planes, int W, int H,
-                           double *scratch, cudaStream_t s) {
+int launch_column_pass_u64(unsigned long long *base, long long plane_stride, int planes, int W, int H,
+                           unsigned long long *scratch, cudaStream_t s) {
   int nseg, seg_rows;
   segments(W + 1, H, planes, nseg, seg_rows);
-  column_pass<double>(base, plane_stride, planes, W, H, scratch, s);
+  column_pass<unsigned long long>(base, plane_stride, planes, W, H, scratch, s);
   return nseg > 1 ? 2 : 1;
 }
 

@@ -30,11 +30,12 @@ int launch_integral_jobs(const Job *jobs, int njobs, int row_blocks, int colb, b
 // integral of [b < k]; cumulative = false: planes k = 0..n-1 the integral of
 // [b == k]. `scratch` holds at least hist_scratch_elems(W, H, planes).
 size_t hist_scratch_elems(int W, int H, int planes);
-// In-place column prefix sums of `planes` FP64 planes of (H+1) x (W+1) whose
-// row 0 is zero and whose rows hold row prefixes; `scratch` holds at least
-// hist_scratch_elems(W, H, planes) doubles. Returns the number of launches.
-int launch_column_pass_f64(double *base, long long plane_stride, int planes, int W, int H,
-                           double *scratch, cudaStream_t s);
+// In-place column prefix sums (modulo 2^64) of `planes` 64-bit planes of
+// (H+1) x (W+1) whose row 0 is zero and whose rows hold row prefixes;
+// `scratch` holds at least hist_scratch_elems(W, H, planes) elements.
+// Returns the number of launches.
+int launch_column_pass_u64(unsigned long long *base, long long plane_stride, int planes, int W, int H,
+                           unsigned long long *scratch, cudaStream_t s);
 int launch_integral_histogram(const uint8_t *bins, int W, int H, int n_bins, bool cumulative,
                               uint32_t *planes, uint32_t *scratch, cudaStream_t s);
 

@@ -13,11 +13,12 @@
 namespace tmk {
 namespace {
 
-// Window statistics of field f at (x, y): area and variance (Eq. 6, Eq. 10).
+// Window statistics of field f at (x, y): reciprocal area and variance
+// (Eq. 6, Eq. 10).
 __device__ __forceinline__ void window_stats(const DevParams &P, int f, int x, int y, int W, int H,
                                              const long long *__restrict__ s1,
                                              const long long *__restrict__ s2, float inv_scale2,
-                                             float &area, float &var) {
+                                             float &rarea, float &var) {
   const long long W1 = (long long)W + 1;
   Win w = window_of(P, f, x, y, W, H);
   const long long iA = (long long)w.y0 * W1 + w.x0;
@@ -29,41 +30,50 @@ __device__ __forceinline__ void window_stats(const DevParams &P, int f, int x, i
                                    (unsigned long long)__ldg(s1 + iB) + (unsigned long long)__ldg(s1 + iA));
   const long long q2 = (long long)((unsigned long long)__ldg(s2 + iC) - (unsigned long long)__ldg(s2 + iD) -
                                    (unsigned long long)__ldg(s2 + iB) + (unsigned long long)__ldg(s2 + iA));
-  area = (float)N;
-  var = window_variance(q1, q2, area, N, inv_scale2);
+  rarea = __frcp_rn((float)N);
+  var = window_variance(q1, q2, N, rarea, inv_scale2);
 }
 
-// Eq. 2, 4, 3 and 12 for one pixel from its per-field counts.
-__device__ __forceinline__ void finish_pixel(const Image &in, const Image &out, const DevParams &P,
-                                             int x, int y, const unsigned *cnt,
-                                             const long long *__restrict__ s1,
-                                             const long long *__restrict__ s2,
-                                             const DebugPlanes &dbg) {
-  const int W = in.W, H = in.H;
-  const float inv_scale2 = ldexpf(1.f, -2 * P.qbits);
-  float area[kMaxFields], var[kMaxFields];
-#pragma unroll
-  for (int f = 0; f < kMaxFields; ++f) {
-    if (f >= P.n_fields) break;
-    window_stats(P, f, x, y, W, H, s1, s2, inv_scale2, area[f], var[f]);
+// Running sums of the fusion of Eq. 3 over the fields.
+struct Fusion {
+  float wsum = 0.f, acc = 0.f, mean = 0.f;
+};
+
+// Field f of pixel (x, y) with Eq. 1 numerator cnt: Eq. 2 and Eq. 4 folded
+// into the Eq. 3 sums (the same arithmetic as fuse_fields, one field at a
+// time, so no per-field state is kept).
+__device__ __forceinline__ void fold_field(const DevParams &P, int f, int x, int y, int W, int H,
+                                           unsigned cnt, const long long *__restrict__ s1,
+                                           const long long *__restrict__ s2, float inv_scale2,
+                                           Fusion &fu, const DebugPlanes &dbg) {
+  float rarea, var;
+  window_stats(P, f, x, y, W, H, s1, s2, inv_scale2, rarea, var);
+  const float Pf = (float)cnt * rarea;                                  // Eq. 1
+  const float Lf = fmaf(P.ld_max - P.ld_min, Pf, P.ld_min);             // Eq. 2
+  const float Wf = __fdividef(P.alpha[f] * var, var + P.eps[f]);       // Eq. 4
+  fu.wsum += Wf;
+  fu.acc = fmaf(Wf, Lf, fu.acc);
+  fu.mean += Lf;
+  if (dbg.l) {
+    const long long N = (long long)W * H, pix = (long long)y * W + x;
+    dbg.cnt[f * N + pix] = cnt;
+    dbg.sigma2[f * N + pix] = var;
+    dbg.weight[f * N + pix] = Wf;
+    dbg.lf[f * N + pix] = Lf;
   }
-  float wv[kMaxFields], lf[kMaxFields];
-  const float L = fuse_fields(P, cnt, area, var, wv, lf);
+}
+
+// Eq. 3 and Eq. 12 for one pixel from the folded sums.
+__device__ __forceinline__ void finish_pixel(const Image &in, const Image &out, const DevParams &P,
+                                             int x, int y, const Fusion &fu, const DebugPlanes &dbg) {
+  const float L = fu.wsum > 0.f ? __fdividef(fu.acc, fu.wsum)
+                                : __fdividef(fu.mean, (float)P.n_fields);  // Eq. 3
   float r, g, b;
   load_rgb(in, x, y, r, g, b);
   const float inv_i = __frcp_rn(luminance(r, g, b));
   store_rgb(out, x, y, restore_channel(r, inv_i, P.sat, L), restore_channel(g, inv_i, P.sat, L),
             restore_channel(b, inv_i, P.sat, L));
-  if (dbg.l) {
-    const long long N = (long long)W * H, pix = (long long)y * W + x;
-    dbg.l[pix] = L;
-    for (int f = 0; f < P.n_fields; ++f) {
-      dbg.cnt[f * N + pix] = cnt[f];
-      dbg.sigma2[f * N + pix] = var[f];
-      dbg.weight[f * N + pix] = wv[f];
-      dbg.lf[f * N + pix] = lf[f];
-    }
-  }
+  if (dbg.l) dbg.l[(long long)y * in.W + x] = L;
 }
 
 __global__ void __launch_bounds__(256)
@@ -78,20 +88,24 @@ __global__ void __launch_bounds__(256)
   const long long plane = W1 * ((long long)H + 1);
   const int b = bins[(long long)y * W + x];
   const unsigned *C = b > 0 ? cplanes + (long long)(b - 1) * plane : nullptr;
-  unsigned cnt[kMaxFields];
-#pragma unroll
-  for (int f = 0; f < kMaxFields; ++f) {
-    cnt[f] = 0u;
-    if (f >= P.n_fields || !C) continue;
-    Win w = window_of(P, f, x, y, W, H);
-    cnt[f] = __ldg(C + (long long)(w.y1 + 1) * W1 + w.x1 + 1) - __ldg(C + (long long)(w.y1 + 1) * W1 + w.x0) -
-             __ldg(C + (long long)w.y0 * W1 + w.x1 + 1) + __ldg(C + (long long)w.y0 * W1 + w.x0);
+  const float inv_scale2 = ldexpf(1.f, -2 * P.qbits);
+  Fusion fu;
+  for (int f = 0; f < P.n_fields; ++f) {
+    unsigned cnt = 0u;
+    if (C) {
+      Win w = window_of(P, f, x, y, W, H);
+      cnt = __ldg(C + (long long)(w.y1 + 1) * W1 + w.x1 + 1) - __ldg(C + (long long)(w.y1 + 1) * W1 + w.x0) -
+            __ldg(C + (long long)w.y0 * W1 + w.x1 + 1) + __ldg(C + (long long)w.y0 * W1 + w.x0);
+    }
+    fold_field(P, f, x, y, W, H, cnt, s1, s2, inv_scale2, fu, dbg);
   }
-  finish_pixel(in, out, P, x, y, cnt, s1, s2, dbg);
+  finish_pixel(in, out, P, x, y, fu, dbg);
 }
 
 // Lookup from the sweep's per-slab counts, over a batch of jobs: block ->
-// (image, 32 x 8 pixel tile).
+// (image, 32 x 8 pixel tile). NF = number of fields, so the field loop is
+// straight-line code and the loads of all fields can be issued together.
+template <int NF>
 __global__ void __launch_bounds__(256) k_lookup_counts(DevParams P, const Job *__restrict__ jobs, int njobs) {
   const int j = find_job(jobs, njobs, kStLook, blockIdx.x);
   const Job &J = jobs[j];
@@ -101,17 +115,20 @@ __global__ void __launch_bounds__(256) k_lookup_counts(DevParams P, const Job *_
   const int x = (lb % bx) * 32 + (threadIdx.x & 31);
   const int y = (lb / bx) * 8 + (threadIdx.x >> 5);
   if (x >= W || y >= H) return;
-  P.qbits = J.qbits;
   const SweepPlan &S = J.plan;
   const long long N = (long long)W * H, pix = (long long)y * W + x;
-  unsigned cnt[kMaxFields];
+  const float inv_scale2 = ldexpf(1.f, -2 * J.qbits);  // Q is per image
+  Fusion fu;
 #pragma unroll
-  for (int f = 0; f < kMaxFields; ++f) cnt[f] = 0u;
-  for (int s = 0; s < S.nslabs; ++s) {
-    const int T = max(y + S.slab_a[s] - 1, -1), B = min(y + S.slab_b[s], H - 1);
-    if (B > T) cnt[S.slab_field[s]] += __ldg(J.counts + s * N + pix);
+  for (int f = 0; f < NF; ++f) {
+    unsigned cnt = 0u;
+    for (int s = S.field_slab0[f]; s < S.field_slab0[f + 1]; ++s) {
+      const int T = max(y + S.slab_a[s] - 1, -1), B = min(y + S.slab_b[s], H - 1);
+      if (B > T) cnt += __ldg(J.counts + s * N + pix);
+    }
+    fold_field(P, f, x, y, W, H, cnt, J.s1, J.s2, inv_scale2, fu, J.dbg);
   }
-  finish_pixel(J.in, J.out, P, x, y, cnt, J.s1, J.s2, J.dbg);
+  finish_pixel(J.in, J.out, P, x, y, fu, J.dbg);
 }
 
 }  // namespace
@@ -129,7 +146,16 @@ int launch_lookup_materialised(const Image &in, const Image &out, const DevParam
 int lookup_blocks(int W, int H) { return ((W + 31) / 32) * ((H + 7) / 8); }
 
 int launch_lookup_counts(const DevParams &P, const Job *jobs, int njobs, int blocks, cudaStream_t s) {
-  k_lookup_counts<<<blocks, 256, 0, s>>>(P, jobs, njobs);
+  switch (P.n_fields) {
+    case 1: k_lookup_counts<1><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
+    case 2: k_lookup_counts<2><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
+    case 3: k_lookup_counts<3><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
+    case 4: k_lookup_counts<4><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
+    case 5: k_lookup_counts<5><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
+    case 6: k_lookup_counts<6><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
+    case 7: k_lookup_counts<7><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
+    default: k_lookup_counts<8><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
+  }
   return 1;
 }
 
