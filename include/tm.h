@@ -134,7 +134,10 @@ tm_status tm_forward(tm_ctx *ctx, const tm_image *in, const tm_image *out,
 
 /* Same operator on host buffers: copies `in` to the device, runs tm_forward
  * and copies the result back into `out`, then synchronises `stream`. Host
- * buffers may be pageable; pinned buffers make the copies asynchronous. */
+ * buffers may be pageable; pinned buffers make the copies asynchronous. A
+ * page-locked output buffer (cudaHostAlloc / cudaHostRegister) is written
+ * directly by the last kernel over the host link instead of being copied
+ * after it; the result is the same. */
 tm_status tm_forward_host(tm_ctx *ctx, const tm_image *in_host,
                           const tm_image *out_host, void *stream);
 

@@ -182,10 +182,12 @@ def image_of(t) -> TmImage:
 def image_of_numpy(a) -> TmImage:
     import numpy as np
 
-    if a.ndim != 3 or a.shape[2] != 3 or not a.flags["C_CONTIGUOUS"]:
-        raise ValueError("host images are C-contiguous (H, W, 3)")
+    es = a.itemsize
+    if (a.ndim != 3 or a.shape[2] != 3 or a.strides[2] != es or a.strides[1] != 3 * es
+            or a.strides[0] % es or a.strides[0] < 3 * es * a.shape[1]):
+        raise ValueError("host images are (H, W, 3) with contiguous pixels and rows (rows may be padded)")
     code = {np.dtype(np.float32): TM_F32, np.dtype(np.float16): TM_F16, np.dtype(np.uint8): TM_U8}[a.dtype]
-    return TmImage(a.ctypes.data, a.shape[1], a.shape[0], 3 * a.shape[1], code)
+    return TmImage(a.ctypes.data, a.shape[1], a.shape[0], a.strides[0] // es, code)
 
 
 def _stream_ptr(stream) -> Optional[int]:

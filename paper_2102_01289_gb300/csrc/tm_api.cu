@@ -763,13 +763,30 @@ tm_status tm_forward_host(tm_ctx *c, const tm_image *in, const tm_image *out, vo
   tm_image din = *in, dout = *out;
   din.data = c->stage;
   din.pitch = 3LL * W;
-  dout.data = static_cast<char *>(c->stage) + in_bytes;
-  dout.pitch = 3LL * W;
+  // A page-locked (pinned or registered) output buffer is addressable from
+  // the device: the last kernel then stores the result straight into it over
+  // the host link, overlapping the download with its own work instead of
+  // following it with a copy. Pageable output goes through the staging copy.
+  void *out_dev = nullptr;
+  {
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, out->data) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+        pa.devicePointer != nullptr)
+      out_dev = pa.devicePointer;
+    cudaGetLastError();
+  }
+  if (out_dev) {
+    dout.data = out_dev;
+  } else {
+    dout.data = static_cast<char *>(c->stage) + in_bytes;
+    dout.pitch = 3LL * W;
+  }
   TM_CUDA(c, cudaMemcpy2DAsync(din.data, in_row, in->data, in->pitch * elem_size(in->dtype), in_row,
                                H, cudaMemcpyHostToDevice, st));
   if ((s = forward_device(c, &din, &dout, st))) return s;
-  TM_CUDA(c, cudaMemcpy2DAsync(out->data, out->pitch * elem_size(out->dtype), dout.data, out_row,
-                               out_row, H, cudaMemcpyDeviceToHost, st));
+  if (!out_dev)
+    TM_CUDA(c, cudaMemcpy2DAsync(out->data, out->pitch * elem_size(out->dtype), dout.data, out_row,
+                                 out_row, H, cudaMemcpyDeviceToHost, st));
   TM_CUDA(c, cudaStreamSynchronize(st));
   return TM_OK;
 }

@@ -190,6 +190,40 @@ def test_host_buffers_match_device(orc):
     assert np.array_equal(out_host, out_dev)
 
 
+def test_pinned_host_output_written_directly(orc):
+    """A page-locked output buffer is written by the last kernel itself; the
+    result equals the device path, for float32 and float16 outputs, and for a
+    pitched (row-padded) pinned buffer."""
+    img = synth.wdr_image(300, 410, seed=9)
+    gp, op = params_pair(orc, 32, [3, 10, 60])
+    out_dev, _ = run_gpu(img, gp, debug=False)
+    ctx = tm.tm_create(gp)
+    try:
+        hin = torch.from_numpy(img).pin_memory()
+        hout = torch.empty_like(hin).pin_memory()
+        for _ in range(2):  # a second call reuses the context's staging
+            hout.zero_()
+            tm.tm_forward_host(ctx, hin.numpy(), hout.numpy())
+            assert np.array_equal(hout.numpy(), out_dev)
+        # float16 output through a pinned buffer
+        h16 = torch.empty(img.shape, dtype=torch.float16).pin_memory()
+        tm.tm_forward_host(ctx, hin.numpy(), h16.numpy())
+        x = torch.from_numpy(img).cuda()
+        y16 = torch.empty(img.shape, dtype=torch.float16, device="cuda")
+        tm.tm_forward(ctx, x, y16)
+        torch.cuda.synchronize()
+        assert torch.equal(h16, y16.cpu())
+        # pitched pinned output: rows padded by 7 pixels
+        H, W = img.shape[:2]
+        big = torch.zeros((H, W + 7, 3), dtype=torch.float32).pin_memory()
+        view = big.numpy()[:, :W, :]
+        tm.tm_forward_host(ctx, hin.numpy(), view)
+        assert np.array_equal(view, out_dev)
+        assert not big.numpy()[:, W:, :].any()
+    finally:
+        tm.tm_destroy(ctx)
+
+
 def test_integral_image_entry_point_exact(orc):
     rng = np.random.default_rng(0)
     for H, W in [(1, 1), (7, 3000), (300, 257), (2500, 5)]:
