@@ -157,6 +157,20 @@ tm_status tm_forward_batch(tm_ctx *ctx, int32_t n, const tm_image *in,
 tm_status tm_backward(tm_ctx *ctx, const tm_image *in, const tm_image *grad_out,
                       const tm_image *grad_in, float *grad_params, void *stream);
 
+/* tm_backward over n images of possibly different sizes: the forward
+ * intermediates of all images are recomputed in one batched pass (as in
+ * tm_forward_batch), then the adjoint runs image by image.
+ *   in[i], grad_out[i]  host arrays of n device-image descriptors.
+ *   grad_in             host array of n descriptors, or NULL to skip.
+ *   grad_params         device float[3 + 2*s] receiving the SUM over the n
+ *                       images (one shared parameter set); NULL to skip.
+ *                       n == 0 writes zeros.
+ * Per-image results equal tm_backward's, up to the summation order of the
+ * floating-point block sums. Errors as tm_backward, with the image index in
+ * the message. */
+tm_status tm_backward_batch(tm_ctx *ctx, int32_t n, const tm_image *in, const tm_image *grad_out,
+                            const tm_image *grad_in, float *grad_params, void *stream);
+
 /* Eq. 5 on a caller-supplied integer plane: s1 = integral of q, s2 = integral
  * of q*q, both int64 modulo 2^64, (height+1) x (width+1) row-major with a zero
  * first row and column. q: device int32[height*width], |q| <= 2^23.

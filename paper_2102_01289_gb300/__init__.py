@@ -31,7 +31,7 @@ EXPORTS = (
     "tm_status_string", "tm_forward", "tm_forward_host", "tm_forward_batch", "tm_backward",
     "tm_integral_image", "tm_integral_histogram", "tm_set_debug", "tm_debug_size",
     "tm_debug_export", "tm_set_option", "tm_last_launch_count", "tm_stage_times",
-    "tm_integral_image_noalloc",
+    "tm_integral_image_noalloc", "tm_backward_batch",
 )
 
 
@@ -106,6 +106,7 @@ def lib():
             "tm_last_launch_count": (i64, [P]),
             "tm_stage_times": (i32, [P, P, P, i32]),
             "tm_integral_image_noalloc": (st, [P, i32, i32, P, P, P]),
+            "tm_backward_batch": (st, [P, i32, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -241,6 +242,18 @@ def tm_backward(ctx, inp, grad_out, grad_in=None, grad_params=None, stream=None)
     _check(lib().tm_backward(ctx, ctypes.byref(a), ctypes.byref(g), gi, gp, _stream_ptr(stream)), ctx)
 
 
+def tm_backward_batch(ctx, inputs, grad_outs, grad_ins=None, grad_params=None, stream=None) -> None:
+    """tm_backward over a list of images; grad_params receives the sum over them."""
+    n = len(inputs)
+    if n != len(grad_outs) or (grad_ins is not None and n != len(grad_ins)):
+        raise ValueError("inputs, grad_outs and grad_ins differ in length")
+    A = (TmImage * max(n, 1))(*[image_of(t) for t in inputs])
+    G = (TmImage * max(n, 1))(*[image_of(t) for t in grad_outs])
+    GI = (TmImage * max(n, 1))(*[image_of(t) for t in grad_ins]) if grad_ins is not None else None
+    gp = grad_params.data_ptr() if grad_params is not None else None
+    _check(lib().tm_backward_batch(ctx, n, A, G, GI, gp, _stream_ptr(stream)), ctx)
+
+
 def tm_integral_image(q, s1, s2, stream=None) -> None:
     H, W = q.shape
     _check(lib().tm_integral_image(q.data_ptr(), W, H, s1.data_ptr(), s2.data_ptr(), _stream_ptr(stream)))
@@ -347,8 +360,9 @@ try:
     import torch as _torch
 
     class TMFunction(_torch.autograd.Function):
-        """Differentiable tone mapping: forward through tm_forward, backward
-        through the hand-written adjoint tm_backward (bins held fixed).
+        """Differentiable tone mapping: forward through tm_forward (a batch
+        through tm_forward_batch), backward through the hand-written adjoint
+        tm_backward / tm_backward_batch (bins held fixed).
 
         Inputs: img (H, W, 3) or (B, H, W, 3) float32 CUDA tensor; theta, the
         float32 parameter vector of params_tensor(); cache, a _CtxCache.
@@ -362,8 +376,7 @@ try:
             if x.dim() == 3:
                 tm_forward(c, x, out)
             else:
-                for b in range(x.shape[0]):
-                    tm_forward(c, x[b], out[b])
+                tm_forward_batch(c, [x[b] for b in range(x.shape[0])], [out[b] for b in range(x.shape[0])])
             ctx.save_for_backward(x, theta)
             ctx.cache = cache
             return out
@@ -374,14 +387,14 @@ try:
             c = ctx.cache.get(theta)
             g = grad_out.contiguous().float()
             gin = _torch.empty_like(x) if ctx.needs_input_grad[0] else None
-            gp_total = _torch.zeros(theta.numel(), dtype=_torch.float32, device=x.device)
-            gp = _torch.empty_like(gp_total)
-            items = [(x, g, gin)] if x.dim() == 3 else [
-                (x[b], g[b], gin[b] if gin is not None else None) for b in range(x.shape[0])]
-            for xi, gi, gii in items:
-                tm_backward(c, xi, gi, gii, gp)
-                gp_total += gp
-            gtheta = gp_total.to(theta.device) if ctx.needs_input_grad[1] else None
+            gp = _torch.empty(theta.numel(), dtype=_torch.float32, device=x.device)
+            if x.dim() == 3:
+                tm_backward(c, x, g, gin, gp)
+            else:
+                B = x.shape[0]
+                tm_backward_batch(c, [x[b] for b in range(B)], [g[b] for b in range(B)],
+                                  [gin[b] for b in range(B)] if gin is not None else None, gp)
+            gtheta = gp.to(theta.device) if ctx.needs_input_grad[1] else None
             return gin, gtheta, None
 
 except ImportError:  # pragma: no cover

@@ -459,7 +459,7 @@ tm_status forward_materialised(tm_ctx *c, const tm_image *in, const tm_image *ou
 // items. `graph`: capture the batch into a CUDA graph and replay it while the
 // batch is unchanged. Returns TM_EUNSUPPORTED if some image cannot be swept.
 tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image *out, cudaStream_t s,
-                        bool graph, bool do_lookup = true, Job *job0 = nullptr) {
+                        bool graph, bool do_lookup = true, std::vector<Job> *jobs_out = nullptr) {
   tm_status st;
   if (graph && c->graph && same_images(c->graph_in, in, nimg) && same_images(c->graph_out, out, nimg)) {
     TM_CUDA(c, cudaGraphLaunch(c->graph, s));
@@ -602,7 +602,7 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   }
   if ((st = check_launch(c, "forward launch"))) return st;
   c->launches = n;
-  if (job0) *job0 = jobs[0];
+  if (jobs_out) *jobs_out = jobs;
   if (nimg == 1) {
     c->last_W = in[0].width;
     c->last_H = in[0].height;
@@ -626,6 +626,91 @@ tm_status forward_device(tm_ctx *c, const tm_image *in, const tm_image *out, cud
       return fail(c, TM_EUNSUPPORTED, "fused sweep does not fit these fields (use the materialised path)");
   }
   return forward_materialised(c, in, out, s);
+}
+
+// Backward of one image given its forward job: workspace carved for this
+// image out of c->bws (grown by the caller to the largest image), per-image
+// accumulators cleared, the parameter sums cleared only for the first image
+// and written out only when grad_params is given (the last image).
+tm_status backward_image(tm_ctx *c, const Job &J, const tm_image *grad_out, const tm_image *grad_in,
+                         float *grad_params, bool first, cudaStream_t s, int64_t &launches) {
+  const int W = J.in.W, H = J.in.H, nf = c->p.n_fields;
+  const size_t N = (size_t)W * H, plane = (size_t)(W + 1) * (H + 1);
+  const size_t o_acc = 0, o_u = align256(sizeof(BwdAcc)), o_v = o_u + align256(4 * N * nf),
+               o_gi = o_v + align256(4 * N * nf), o_iu = o_gi + align256(4 * N),
+               o_cs = o_iu + align256(8 * plane * 2 * nf);
+  char *b = static_cast<char *>(c->bws);
+  BwdJob B{};
+  B.grad_out = to_image(grad_out);
+  if (grad_in) B.grad_in = to_image(grad_in);
+  B.grad_params = grad_params;
+  B.acc = reinterpret_cast<BwdAcc *>(b + o_acc);
+  B.U = reinterpret_cast<float *>(b + o_u);
+  B.V = reinterpret_cast<float *>(b + o_v);
+  B.gi_direct = reinterpret_cast<float *>(b + o_gi);
+  B.IU = reinterpret_cast<unsigned long long *>(b + o_iu);
+  B.IV = B.IU + plane * nf;
+  B.colscr = reinterpret_cast<unsigned long long *>(b + o_cs);
+  if (first) TM_CUDA(c, cudaMemsetAsync(B.acc->g, 0, sizeof(B.acc->g), s));
+  char *z0 = reinterpret_cast<char *>(&B.acc->lmin), *z1 = reinterpret_cast<char *>(&B.acc->argmin);
+  TM_CUDA(c, cudaMemsetAsync(z0, 0, (size_t)(z1 - z0), s));
+  TM_CUDA(c, cudaMemsetAsync(&B.acc->argmin, 0xff, 2 * sizeof(unsigned long long), s));
+  const DevParams P = dev_params(c->p, J.qbits);
+  launches += launch_backward(P, J, B, s);
+  return TM_OK;
+}
+
+size_t backward_bytes(const tm_params &p, int W, int H) {
+  const size_t N = (size_t)W * H, plane = (size_t)(W + 1) * (H + 1);
+  const int nf = p.n_fields;
+  return align256(sizeof(BwdAcc)) + 2 * align256(4 * N * nf) + align256(4 * N) +
+         align256(8 * plane * 2 * nf) + 8 * hist_scratch_elems(W, H, 2 * nf);
+}
+
+// tm_backward / tm_backward_batch: validate, recompute the forward of every
+// image in one batched pass, then run the adjoint image by image on one
+// shared workspace (the parameter gradients accumulate over the images).
+tm_status backward_images(tm_ctx *c, int n, const tm_image *in, const tm_image *grad_out,
+                          const tm_image *grad_in, float *grad_params, cudaStream_t s) {
+  tm_status st;
+  size_t need = 0;
+  for (int i = 0; i < n; ++i) {
+    char nm[40];
+    snprintf(nm, sizeof nm, "in[%d]", i);
+    if ((st = validate_image(c, &in[i], nm, true))) return st;
+    snprintf(nm, sizeof nm, "grad_out[%d]", i);
+    if ((st = validate_image(c, &grad_out[i], nm, false))) return st;
+    if (grad_out[i].dtype != TM_F32) return fail(c, TM_EUNSUPPORTED, "grad_out[%d] must be float32", i);
+    if (grad_out[i].width != in[i].width || grad_out[i].height != in[i].height)
+      return fail(c, TM_EINVAL, "grad_out[%d] size differs from in[%d]", i, i);
+    if (grad_in) {
+      snprintf(nm, sizeof nm, "grad_in[%d]", i);
+      if ((st = validate_image(c, &grad_in[i], nm, false))) return st;
+      if (grad_in[i].dtype != TM_F32) return fail(c, TM_EUNSUPPORTED, "grad_in[%d] must be float32", i);
+      if (grad_in[i].width != in[i].width || grad_in[i].height != in[i].height)
+        return fail(c, TM_EINVAL, "grad_in[%d] size differs from in[%d]", i, i);
+      if (overlap(&grad_in[i], &in[i]) || overlap(&grad_in[i], &grad_out[i]))
+        return fail(c, TM_EINVAL, "grad_in[%d] overlaps in[%d] or grad_out[%d]", i, i, i);
+    }
+    need = std::max(need, backward_bytes(c->p, in[i].width, in[i].height));
+  }
+  if (c->p.n_bins < 2 || c->hist_path == 2)
+    return fail(c, TM_EUNSUPPORTED, "the backward runs on the fused path (n_bins >= 2)");
+  if ((st = ensure_device_info(c))) return st;
+  std::vector<Job> jobs;
+  st = forward_fused(c, n, in, in, s, false, false, &jobs);
+  if (st == TM_EUNSUPPORTED) return fail(c, st, "fused sweep does not fit these fields");
+  if (st) return st;
+  int64_t launches = c->launches;
+  if ((st = grow_device(c, &c->bws, &c->bws_bytes, need))) return st;
+  for (int i = 0; i < n; ++i)
+    if ((st = backward_image(c, jobs[(size_t)i], &grad_out[i], grad_in ? &grad_in[i] : nullptr,
+                             i == n - 1 ? grad_params : nullptr, i == 0, s, launches)))
+      return st;
+  mark(c, s, ST_BWD_ADJOINT);
+  if ((st = check_launch(c, "backward launch"))) return st;
+  c->launches = launches;
+  return TM_OK;
 }
 
 }  // namespace
@@ -831,56 +916,21 @@ tm_status tm_forward_batch(tm_ctx *c, int32_t n, const tm_image *in, const tm_im
 tm_status tm_backward(tm_ctx *c, const tm_image *in, const tm_image *grad_out,
                       const tm_image *grad_in, float *grad_params, void *stream) {
   if (!c) return fail(nullptr, TM_EINVAL, "tm_backward: ctx is NULL");
-  tm_status st;
-  if ((st = validate_image(c, in, "in", true))) return st;
-  if ((st = validate_image(c, grad_out, "grad_out", false))) return st;
-  if (grad_out->dtype != TM_F32) return fail(c, TM_EUNSUPPORTED, "grad_out must be float32");
-  if (grad_out->width != in->width || grad_out->height != in->height)
-    return fail(c, TM_EINVAL, "grad_out size differs from in");
-  if (grad_in) {
-    if ((st = validate_image(c, grad_in, "grad_in", false))) return st;
-    if (grad_in->dtype != TM_F32) return fail(c, TM_EUNSUPPORTED, "grad_in must be float32");
-    if (grad_in->width != in->width || grad_in->height != in->height)
-      return fail(c, TM_EINVAL, "grad_in size differs from in");
-    if (overlap(grad_in, in) || overlap(grad_in, grad_out))
-      return fail(c, TM_EINVAL, "grad_in overlaps in or grad_out");
-  }
-  if (c->p.n_bins < 2 || c->hist_path == 2)
-    return fail(c, TM_EUNSUPPORTED, "the backward runs on the fused path (n_bins >= 2)");
+  return backward_images(c, 1, in, grad_out, grad_in, grad_params, static_cast<cudaStream_t>(stream));
+}
+
+tm_status tm_backward_batch(tm_ctx *c, int32_t n, const tm_image *in, const tm_image *grad_out,
+                            const tm_image *grad_in, float *grad_params, void *stream) {
+  if (!c) return fail(nullptr, TM_EINVAL, "tm_backward_batch: ctx is NULL");
+  if (n < 0) return fail(c, TM_EINVAL, "n = %d < 0", n);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if ((st = ensure_device_info(c))) return st;
-  Job J;
-  st = forward_fused(c, 1, in, in, s, false, false, &J);
-  if (st == TM_EUNSUPPORTED) return fail(c, st, "fused sweep does not fit these fields");
-  if (st) return st;
-  const int W = in->width, H = in->height, nf = c->p.n_fields;
-  const size_t N = (size_t)W * H, plane = (size_t)(W + 1) * (H + 1);
-  const size_t o_acc = 0, o_u = align256(sizeof(BwdAcc)), o_v = o_u + align256(4 * N * nf),
-               o_gi = o_v + align256(4 * N * nf), o_iu = o_gi + align256(4 * N),
-               o_cs = o_iu + align256(8 * plane * 2 * nf),
-               total = o_cs + 8 * hist_scratch_elems(W, H, 2 * nf);
-  if ((st = grow_device(c, &c->bws, &c->bws_bytes, total))) return st;
-  char *b = static_cast<char *>(c->bws);
-  BwdJob B{};
-  B.grad_out = to_image(grad_out);
-  if (grad_in) B.grad_in = to_image(grad_in);
-  B.grad_params = grad_params;
-  B.acc = reinterpret_cast<BwdAcc *>(b + o_acc);
-  B.U = reinterpret_cast<float *>(b + o_u);
-  B.V = reinterpret_cast<float *>(b + o_v);
-  B.gi_direct = reinterpret_cast<float *>(b + o_gi);
-  B.IU = reinterpret_cast<unsigned long long *>(b + o_iu);
-  B.IV = B.IU + plane * nf;
-  B.colscr = reinterpret_cast<unsigned long long *>(b + o_cs);
-  TM_CUDA(c, cudaMemsetAsync(B.acc, 0, sizeof(BwdAcc), s));
-  TM_CUDA(c, cudaMemsetAsync(&B.acc->argmin, 0xff, 2 * sizeof(unsigned long long), s));
-  const DevParams P = dev_params(c->p, J.qbits);
-  const int64_t nfwd = c->launches;
-  const int nb = launch_backward(P, J, B, s);
-  mark(c, s, ST_BWD_ADJOINT);
-  if ((st = check_launch(c, "backward launch"))) return st;
-  c->launches = nfwd + nb;
-  return TM_OK;
+  if (n == 0) {
+    c->launches = 0;
+    if (grad_params) TM_CUDA(c, cudaMemsetAsync(grad_params, 0, sizeof(float) * (3 + 2 * c->p.n_fields), s));
+    return TM_OK;
+  }
+  if (!in || !grad_out) return fail(c, TM_EINVAL, "descriptor arrays are NULL");
+  return backward_images(c, n, in, grad_out, grad_in, grad_params, s);
 }
 
 tm_status tm_integral_image(const int32_t *q, int32_t width, int32_t height, int64_t *s1,

@@ -7,11 +7,13 @@ namespace tmk {
 
 // FP64 accumulators of one backward call (cleared before it: sums to 0,
 // argmin/argmax to all ones).
+// g accumulates over the images of a batch; the fields from lmin on are per
+// image (lmin .. amax cleared to 0, argmin / argmax to all ones).
 struct BwdAcc {
-  double g[3 + 2 * kMaxFields];  // [d ld_min, d ld_max, d sat, d eps[s], d alpha[s]]
-  double lmin, lmax;             // dLoss/d ln imin, dLoss/d ln imax (times D)
-  unsigned long long argmin, argmax;
+  double g[3 + 2 * kMaxFields];   // [d ld_min, d ld_max, d sat, d eps[s], d alpha[s]]
+  double lmin, lmax;              // dLoss/d ln imin, dLoss/d ln imax (times D)
   unsigned amax[2 * kMaxFields];  // float bits of max |u_f| (f) and max |v_f| (kMaxFields + f)
+  unsigned long long argmin, argmax;
 };
 
 // Buffers of one backward call.
