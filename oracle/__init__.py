@@ -57,11 +57,19 @@ class Params(ctypes.Structure):
         ("ld_min", ctypes.c_double),
         ("ld_max", ctypes.c_double),
         ("sat", ctypes.c_double),
+        ("flags", ctypes.c_int32),
     ]
 
 
+# Reading variants (tm_oracle.h): Eq. 1 with <=, Algorithm 1's unclipped
+# window area (zero padding), Eq. 10 on i / imax.
+CDF_INCLUSIVE = 1
+AREA_LITERAL = 2
+VAR_LINEAR = 4
+
+
 def make_params(n_bins: int, radii: Sequence, eps=0.1, alpha=1.0, ld_min=0.0,
-                ld_max=1.0, sat=0.6) -> Params:
+                ld_max=1.0, sat=0.6, flags=0) -> Params:
     """Build oracle parameters. ``radii`` holds r or (rx, ry) per field.
 
     Defaults follow the paper: eps = 0.1 (Section II-C), sat = 0.6 (Eq. 12),
@@ -76,7 +84,23 @@ def make_params(n_bins: int, radii: Sequence, eps=0.1, alpha=1.0, ld_min=0.0,
         p.eps[f] = float(eps[f] if not np.isscalar(eps) else eps)
         p.alpha[f] = float(alpha[f] if not np.isscalar(alpha) else alpha)
     p.ld_min, p.ld_max, p.sat = float(ld_min), float(ld_max), float(sat)
+    p.flags = int(flags)
     return p
+
+
+def srgb_encode(c):
+    """The sRGB transfer function (IEC 61966-2-1) on linear values in [0, 1]:
+    12.92 c up to 0.0031308, 1.055 c^(1/2.4) - 0.055 above (FP64)."""
+    c = np.clip(np.asarray(c, dtype=np.float64), 0.0, 1.0)
+    return np.where(c <= 0.0031308, 12.92 * c, 1.055 * np.power(c, 1.0 / 2.4) - 0.055)
+
+
+def to_u8(c, srgb=False):
+    """uint8 output: floor(255 clamp(c, 0, 1) + 0.5), optionally sRGB-encoded first."""
+    c = np.clip(np.asarray(c, dtype=np.float64), 0.0, 1.0)
+    if srgb:
+        c = srgb_encode(c)
+    return np.floor(255.0 * c + 0.5).astype(np.uint8)
 
 
 def _load():

@@ -156,23 +156,34 @@ static uint32_t box_u32(const uint32_t *S, int W, win_t w) {
          S[(int64_t)w.y0 * W1 + w.x1 + 1] + S[(int64_t)w.y0 * W1 + w.x0];
 }
 
-/* R5: variance of lhat over the window, as the mean of squared deviations.
- * Summed about the centre value c (the variance does not depend on the
- * shift), which keeps a constant window at exactly zero. */
-static void window_moments(const double *lhat, int W, win_t w, double c,
+/* R5: variance over the window, as the mean of squared deviations. Summed
+ * about the centre value c (the variance does not depend on the shift), which
+ * keeps a constant window at exactly zero. T is the area the moments divide
+ * by; when it exceeds the clipped window (TMO_AREA_LITERAL) the missing
+ * pixels take part with the value `pad`. */
+static void window_moments(const double *v, int W, win_t w, double c, double T, double pad,
                            double *mu, double *var) {
   double s1 = 0.0, s2 = 0.0;
-  double T = (double)(w.x1 - w.x0 + 1) * (double)(w.y1 - w.y0 + 1);
+  double Tc = (double)(w.x1 - w.x0 + 1) * (double)(w.y1 - w.y0 + 1);
   for (int y = w.y0; y <= w.y1; ++y)
     for (int x = w.x0; x <= w.x1; ++x) {
-      double d = lhat[(int64_t)y * W + x] - c;
+      double d = v[(int64_t)y * W + x] - c;
       s1 += d;
       s2 += d * d;
     }
+  s1 += (T - Tc) * (pad - c);
+  s2 += (T - Tc) * (pad - c) * (pad - c);
   double m = s1 / T;
-  double v = s2 / T - m * m;
+  double r = s2 / T - m * m;
   *mu = c + m;
-  *var = v > 0.0 ? v : 0.0;
+  *var = r > 0.0 ? r : 0.0;
+}
+
+/* Area of field f's window at a pixel: clipped (default) or the literal
+ * (2 rx + 1)(2 ry + 1) of Algorithm 1. */
+static uint32_t window_area(const tmo_params *p, int f, win_t w) {
+  if (p->flags & TMO_AREA_LITERAL) return (uint32_t)(2 * p->rx[f] + 1) * (uint32_t)(2 * p->ry[f] + 1);
+  return (uint32_t)((w.x1 - w.x0 + 1) * (w.y1 - w.y0 + 1));
 }
 
 /* Eq. 2, Eq. 4 and Eq. 3 for one pixel, from its per-field counts/moments. */
@@ -202,7 +213,9 @@ static int params_ok(const tmo_params *p) {
   if (p->n_bins < 1 || p->n_bins > TMO_MAX_BINS) return 0;
   if (p->n_fields < 1 || p->n_fields > TMO_MAX_FIELDS) return 0;
   for (int f = 0; f < p->n_fields; ++f)
-    if (p->rx[f] < 0 || p->ry[f] < 0 || !(p->eps[f] > 0.0)) return 0;
+    if (p->rx[f] < 0 || p->ry[f] < 0 || p->rx[f] > 32767 || p->ry[f] > 32767 || !(p->eps[f] > 0.0))
+      return 0;
+  if (p->flags & ~(TMO_CDF_INCLUSIVE | TMO_AREA_LITERAL | TMO_VAR_LINEAR)) return 0;
   return 1;
 }
 
@@ -291,10 +304,20 @@ static int core_run(const double *rgb, int W, int H, const tmo_params *p,
   c->D = (c->imax > c->imin) ? log(c->imax) - c->lmin : 0.0;
   for (int64_t q = 0; q < N; ++q)
     c->lhat[q] = c->D > 0.0 ? (log(c->lum[q]) - c->lmin) / c->D : 0.0;
+  /* the values whose window variance Eq. 10 takes */
+  const double *vdom = c->lhat;
+  double *lin = NULL;
+  if (p->flags & TMO_VAR_LINEAR) {
+    lin = malloc(sizeof(double) * N);
+    if (!lin) { core_free(c); return -2; }
+    for (int64_t q = 0; q < N; ++q) lin[q] = c->lum[q] / c->imax;
+    vdom = lin;
+  }
+  const int incl = (p->flags & TMO_CDF_INCLUSIVE) ? 1 : 0;
   /* Eq. 7-8 integral histogram */
   int64_t P = ((int64_t)W + 1) * ((int64_t)H + 1);
   uint32_t *Hk = malloc(sizeof(uint32_t) * P * n);
-  if (!Hk) { core_free(c); return -2; }
+  if (!Hk) { free(lin); core_free(c); return -2; }
   tmo_integral_histogram(c->bins, W, H, n, Hk);
   for (int y = 0; y < H; ++y)
     for (int x = 0; x < W; ++x) {
@@ -304,12 +327,12 @@ static int core_run(const double *rgb, int W, int H, const tmo_params *p,
       for (int f = 0; f < s; ++f) {
         win_t w = window_of(p, f, x, y, W, H);
         uint32_t k_count = 0;
-        for (int k = 0; k < c->bins[q]; ++k)           /* Eq. 1: b_i < b */
+        for (int k = 0; k < c->bins[q] + incl; ++k)    /* Eq. 1: b_i < b (or <=) */
           k_count += box_u32(Hk + (int64_t)k * P, W, w); /* Eq. 9 */
         cnt[f] = k_count;
-        area[f] = (uint32_t)((w.x1 - w.x0 + 1) * (w.y1 - w.y0 + 1));
+        area[f] = window_area(p, f, w);
         double mu;
-        window_moments(c->lhat, W, w, c->lhat[q], &mu, &var[f]);
+        window_moments(vdom, W, w, vdom[q], (double)area[f], 0.0, &mu, &var[f]);
         c->mu[f * N + q] = mu;
       }
       double L = fuse(p, cnt, area, var, wgt, lf);
@@ -326,6 +349,7 @@ static int core_run(const double *rgb, int W, int H, const tmo_params *p,
       c->wsum[q] = ws;
     }
   free(Hk);
+  free(lin);
   return 0;
 }
 
@@ -384,6 +408,9 @@ int tmo_forward_pixels(const float *rgb, int32_t W, int32_t H,
   if (!lum || !bins || !lhat) { free(lum); free(bins); free(lhat); return -2; }
   float imin, imax, thr[TMO_MAX_BINS];
   tmo_prepare(rgb, W, H, p->n_bins, lum, &imin, &imax, thr, bins, lhat);
+  if (p->flags & TMO_VAR_LINEAR)  /* the window variance of Eq. 10 on i / imax */
+    for (int64_t q = 0; q < N; ++q) lhat[q] = (double)lum[q] / (double)imax;
+  const int incl = (p->flags & TMO_CDF_INCLUSIVE) ? 1 : 0;
   for (int64_t k = 0; k < K; ++k) {
     int x = xs[k], y = ys[k];
     if (x < 0 || x >= W || y < 0 || y >= H) { free(lum); free(bins); free(lhat); return -1; }
@@ -395,11 +422,11 @@ int tmo_forward_pixels(const float *rgb, int32_t W, int32_t H,
       uint32_t below = 0;                                 /* Eq. 1 by counting */
       for (int yy = w.y0; yy <= w.y1; ++yy)
         for (int xx = w.x0; xx <= w.x1; ++xx)
-          if (bins[(int64_t)yy * W + xx] < bins[q]) ++below;
+          if (bins[(int64_t)yy * W + xx] < bins[q] + incl) ++below;
       cnt[f] = below;
-      area[f] = (uint32_t)((w.x1 - w.x0 + 1) * (w.y1 - w.y0 + 1));
+      area[f] = window_area(p, f, w);
       double mu;
-      window_moments(lhat, W, w, lhat[q], &mu, &var[f]);
+      window_moments(lhat, W, w, lhat[q], (double)area[f], 0.0, &mu, &var[f]);
     }
     double L = fuse(p, cnt, area, var, wgt, lf);
     for (int ch = 0; ch < 3; ++ch)
@@ -425,6 +452,7 @@ int tmo_forward_pixels(const float *rgb, int32_t W, int32_t H,
 int tmo_backward(const double *rgb, int32_t W, int32_t H, const tmo_params *p,
                  int32_t lum_f64, const uint8_t *bins, const double *grad_out,
                  double *grad_in, double *grad_params) {
+  if (p->flags & TMO_VAR_LINEAR) return -3;  /* the adjoint covers the log-domain variance */
   core_t c;
   int rc = core_run(rgb, W, H, p, lum_f64, bins, &c);
   if (rc) return rc;

@@ -33,7 +33,20 @@ typedef struct {
   double alpha[TMO_MAX_FIELDS];/* field weight multiplying Eq. 4 (1 = paper) */
   double ld_min, ld_max;       /* min(L_d), max(L_d) of Eq. 2          */
   double sat;                  /* sat of Eq. 12                        */
+  int32_t flags;               /* reading variants, TMO_* below (0 = defaults) */
 } tmo_params;
+
+/* Reading variants (0 selects the default readings):
+ *   TMO_CDF_INCLUSIVE  Eq. 1 counts b(q) <= b(p) instead of b(q) < b(p).
+ *   TMO_AREA_LITERAL   the window area is the unclipped (2 rx + 1)(2 ry + 1)
+ *                      of Algorithm 1; pixels outside the image take part as
+ *                      zeros (they are never counted by Eq. 1 and contribute
+ *                      a normalised log of 0 to the window moments).
+ *   TMO_VAR_LINEAR     Eq. 10 on the linear luminance normalised by the image
+ *                      maximum, i / imax, instead of the normalised log. */
+#define TMO_CDF_INCLUSIVE 1
+#define TMO_AREA_LITERAL 2
+#define TMO_VAR_LINEAR 4
 
 /* Per-pixel, per-field intermediates (optional debug / backward state). */
 typedef struct {

@@ -278,3 +278,45 @@ def test_full_size_12mp_sampled(orc):
     ref, dd = orc.forward_pixels(img, op, xs, ys)
     assert np.array_equal(d["cnt"][:, ys, xs].T, dd["cnt"])
     assert_out_close(out[ys, xs], ref)
+
+
+def _pyramid_pair(orc, W, H, s=5, n=5):
+    """The paper's preset (Section IV): s fields halving from the whole
+    image (rectangular windows), n bins, eps 0.1, sat 0.6."""
+    gp = tm.tm_params_pyramid(W, H, s, n)
+    radii = [(int(gp.rx[f]), int(gp.ry[f])) for f in range(s)]
+    op = orc.make_params(n, radii, eps=[float(gp.eps[f]) for f in range(s)],
+                         alpha=[float(gp.alpha[f]) for f in range(s)], ld_min=float(gp.ld_min),
+                         ld_max=float(gp.ld_max), sat=float(gp.sat))
+    return gp, op
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_paper_preset_matches_oracle(orc, path):
+    """s = 5 fields from the whole image down by halves, n = 5: windows larger
+    than the image (clipped areas), rectangular fields, few bins."""
+    H, W = 150, 220
+    img = synth.wdr_image(H, W, seed=31)
+    gp, op = _pyramid_pair(orc, W, H)
+    out, d = run_gpu(img, gp, path=path)
+    ref, fl = orc.forward(img, op)
+    assert np.array_equal(d["cnt"], fl.cnt)
+    assert_out_close(out, ref)
+
+
+def test_paper_preset_12mp_sampled(orc):
+    """The preset at 4000 x 3000: the largest window is the whole image, more
+    slabs than the sweep holds, so the context takes the materialised
+    integral histogram (4 cumulative planes at n = 5). Bin map bit-exact,
+    outputs at sampled pixels against direct per-pixel evaluation."""
+    H, W = 3000, 4000
+    img = synth.wdr_image(H, W, seed=3, decades=(-3.0, 5.0))
+    gp, op = _pyramid_pair(orc, W, H)
+    out, d = run_gpu(img, gp)
+    pre = orc.prepare(img, 5)
+    assert np.array_equal(d["bins"], pre["bins"])
+    ys = np.array([0, H - 1, 0, H - 1, 1500, 777, 2999, 1])
+    xs = np.array([0, W - 1, W - 1, 0, 2000, 3333, 17, 3998])
+    ref, dd = orc.forward_pixels(img, op, xs, ys)
+    assert np.array_equal(d["cnt"][:, ys, xs].T, dd["cnt"])
+    assert_out_close(out[ys, xs], ref)

@@ -364,3 +364,78 @@ def test_value_on_bin_edge_goes_to_upper_bin(orc):
     d2 = orc.prepare(img, n)
     assert d2["imin"] == d["imin"] and d2["imax"] == d["imax"]
     assert d2["lum"][2, 3] == edge and d2["bins"][2, 3] == k
+
+
+# ------------------------------------------- reading variants (flags) -----
+@pytest.mark.parametrize("radii", [[0], [(2, 1), 3], [1, 40]])
+def test_variant_flags_against_brute_force(orc, radii):
+    """Eq. 1 with <= (inclusive), Algorithm 1's unclipped area with zero
+    padding, and Eq. 10 on i / imax, each against explicit numpy windows."""
+    img = synth.wdr_image(9, 11, seed=21)
+    n = 7
+    d = orc.prepare(img, n)
+    b, lh, lum = d["bins"].astype(np.int64), d["lhat"], d["lum"].astype(np.float64)
+    H, W = b.shape
+    lin = lum / lum.max()
+    for flags in (orc.CDF_INCLUSIVE, orc.AREA_LITERAL, orc.VAR_LINEAR,
+                  orc.CDF_INCLUSIVE | orc.AREA_LITERAL | orc.VAR_LINEAR):
+        p = orc.make_params(n, radii, flags=flags)
+        _, fl = orc.forward(img, p)
+        _, dd = orc.forward_pixels(img, p, np.arange(W).repeat(H), np.tile(np.arange(H), W))
+        vals = lin if flags & orc.VAR_LINEAR else lh
+        for f, r in enumerate(radii):
+            rx, ry = (r, r) if np.isscalar(r) else r
+            padded = np.pad(vals, ((ry, ry), (rx, rx)))  # zeros outside the image
+            for y in range(H):
+                for x in range(W):
+                    ys = slice(max(y - ry, 0), min(y + ry, H - 1) + 1)
+                    xs = slice(max(x - rx, 0), min(x + rx, W - 1) + 1)
+                    wb = b[ys, xs]
+                    cnt = int(np.sum(wb <= b[y, x])) if flags & orc.CDF_INCLUSIVE else int(np.sum(wb < b[y, x]))
+                    if flags & orc.AREA_LITERAL:
+                        area = (2 * rx + 1) * (2 * ry + 1)
+                        v = float(np.var(padded[y:y + 2 * ry + 1, x:x + 2 * rx + 1]))
+                    else:
+                        area = wb.size
+                        v = float(np.var(vals[ys, xs]))
+                    assert fl.cnt[f, y, x] == cnt and fl.area[f, y, x] == area
+                    assert abs(fl.sigma2[f, y, x] - v) <= 1e-12 + 1e-9 * v
+                    k = x * H + y  # the direct per-pixel path agrees
+                    assert dd["cnt"][k, f] == cnt
+                    assert abs(dd["sigma2"][k, f] - v) <= 1e-12 + 1e-9 * v
+
+
+def test_inclusive_single_global_field_is_inclusive_histogram_cdf(orc):
+    """s = 1 covering the image with Eq. 1 read as <=: P is the inclusive
+    histogram CDF, so the brightest bin maps to ld_max."""
+    img = synth.wdr_image(14, 17, seed=4)
+    n = 10
+    p = orc.make_params(n, [100], ld_min=0.0, ld_max=1.0, flags=orc.CDF_INCLUSIVE)
+    _, fl = orc.forward(img, p)
+    b = orc.prepare(img, n)["bins"]
+    cdf = np.cumsum(np.bincount(b.ravel(), minlength=n)) / b.size
+    assert np.allclose(fl.lf[0], cdf[b], atol=1e-15)
+    assert np.isclose(fl.lf[0][b == b.max()].min(), 1.0)
+
+
+def test_literal_area_constant_image(orc):
+    """A constant image under Algorithm 1's area: P = 0 everywhere (nothing is
+    strictly below), and near the border the zero padding gives a positive
+    variance of the normalised log only if the value differs from 0; for the
+    darkest possible constant image (lhat = 0 everywhere) it stays 0."""
+    img = _grey(np.full((6, 8), 3.5))
+    p = orc.make_params(8, [2], flags=orc.AREA_LITERAL)
+    _, fl = orc.forward(img, p)
+    assert np.all(fl.cnt == 0) and np.all(fl.area == 25)
+    assert np.all(fl.sigma2 == 0)
+
+
+def test_srgb_encode_published_values(orc):
+    """IEC 61966-2-1 transfer function at published points: linear 0.5 ->
+    0.7353569830524495 (8-bit 188), 0.18 -> 0.4613561295004773, the knee
+    0.0031308 -> 0.040449936, 0 -> 0, 1 -> 1; 8-bit 128 decodes to linear
+    0.21586050011389926 and encodes back."""
+    enc = orc.srgb_encode([0.5, 0.18, 0.0031308, 0.0, 1.0, 0.21586050011389926])
+    ref = [0.7353569830524495, 0.4613561295004773, 0.040449936, 0.0, 1.0, 128 / 255]
+    assert np.allclose(enc, ref, rtol=0, atol=2e-9)
+    assert orc.to_u8([0.5], srgb=True)[0] == 188 and orc.to_u8([0.5])[0] == 128
