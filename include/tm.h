@@ -65,9 +65,23 @@ typedef enum tm_dtype {
  *   alpha     weight multiplying W of Eq. 4 per field, >= 0 (1 = the paper).
  *   ld_min, ld_max  min(L_d), max(L_d) of Eq. 2, ld_max >= ld_min.
  *   sat       colour saturation of Eq. 12, >= 0. Paper 0.6.
- *   flags     reserved, must be 0.
+ *   flags     reading variants; 0 selects the defaults. A combination of
+ *               TM_FLAG_CDF_INCLUSIVE  Eq. 1 counts b(q) <= b(p) (default <).
+ *               TM_FLAG_AREA_LITERAL   window area (2 rx + 1)(2 ry + 1) of
+ *                                      Algorithm 1, the pixels outside the
+ *                                      image taking part as zeros (default:
+ *                                      the window clipped to the image).
+ *               TM_FLAG_VAR_LINEAR     Eq. 10 on i / imax (default: the
+ *                                      normalised log). tm_backward rejects it.
+ *               TM_FLAG_SRGB_U8        TM_U8 outputs are sRGB-encoded
+ *                                      (IEC 61966-2-1) before quantisation.
+ *             Other bits: TM_EINVAL.
  * Variance of Eq. 10 is taken over the normalised log luminance
  * (ln i - ln imin) / (ln imax - ln imin); it is the window variance. */
+#define TM_FLAG_CDF_INCLUSIVE 1
+#define TM_FLAG_AREA_LITERAL 2
+#define TM_FLAG_VAR_LINEAR 4
+#define TM_FLAG_SRGB_U8 8
 typedef struct tm_params {
   int32_t n_bins;
   int32_t n_fields;

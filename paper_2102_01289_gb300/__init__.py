@@ -24,6 +24,8 @@ TM_F32, TM_F16, TM_U8 = 0, 1, 2
  TM_DBG_WEIGHT, TM_DBG_LF, TM_DBG_L, TM_DBG_QSHIFT) = range(1, 11)
 TM_OPT_HIST_PATH = 1
 TM_OPT_STAGE_TIMING = 2
+# reading variants (tm_params.flags)
+TM_FLAG_CDF_INCLUSIVE, TM_FLAG_AREA_LITERAL, TM_FLAG_VAR_LINEAR, TM_FLAG_SRGB_U8 = 1, 2, 4, 8
 
 # Every symbol include/tm.h declares.
 EXPORTS = (
@@ -143,7 +145,7 @@ def tm_params_pyramid(width: int, height: int, n_fields: int, n_bins: int) -> Tm
 
 
 def make_params(n_bins: int, radii: Sequence, eps=0.1, alpha=1.0, ld_min=0.0, ld_max=1.0,
-                sat=0.6) -> TmParams:
+                sat=0.6, flags=0) -> TmParams:
     """Parameters from plain values; ``radii`` holds r or (rx, ry) per field."""
     p = tm_params_default()
     p.n_bins = int(n_bins)
@@ -158,6 +160,7 @@ def make_params(n_bins: int, radii: Sequence, eps=0.1, alpha=1.0, ld_min=0.0, ld
         else:
             p.rx[f] = p.ry[f] = 0
     p.ld_min, p.ld_max, p.sat = float(ld_min), float(ld_max), float(sat)
+    p.flags = int(flags)
     return p
 
 

@@ -135,7 +135,9 @@ tm_status validate_params(const tm_params *p, std::string &why) {
     why = "need finite ld_min <= ld_max"; return TM_EINVAL;
   }
   if (!std::isfinite(p->sat) || p->sat < 0.f) { why = "sat must be finite and >= 0"; return TM_EINVAL; }
-  if (p->flags != 0) { why = "flags must be 0"; return TM_EINVAL; }
+  if (p->flags & ~(TM_FLAG_CDF_INCLUSIVE | TM_FLAG_AREA_LITERAL | TM_FLAG_VAR_LINEAR | TM_FLAG_SRGB_U8)) {
+    snprintf(b, sizeof b, "flags 0x%x has undefined bits", (unsigned)p->flags); why = b; return TM_EINVAL;
+  }
   return TM_OK;
 }
 
@@ -197,8 +199,10 @@ bool overlap(const tm_image *a, const tm_image *b) {
 int choose_qbits(const tm_params &p, int W, int H) {
   unsigned long long n_max = 1;
   for (int f = 0; f < p.n_fields; ++f) {
-    unsigned long long wx = std::min<long long>(2LL * p.rx[f] + 1, W);
-    unsigned long long wy = std::min<long long>(2LL * p.ry[f] + 1, H);
+    // the unclipped window under TM_FLAG_AREA_LITERAL (zero padding)
+    const bool lit = (p.flags & TM_FLAG_AREA_LITERAL) != 0;
+    unsigned long long wx = lit ? 2ULL * p.rx[f] + 1 : std::min<long long>(2LL * p.rx[f] + 1, W);
+    unsigned long long wy = lit ? 2ULL * p.ry[f] + 1 : std::min<long long>(2LL * p.ry[f] + 1, H);
     n_max = std::max(n_max, wx * wy);
   }
   int Q = 24;
@@ -220,6 +224,7 @@ DevParams dev_params(const tm_params &p, int qbits) {
   d.ld_max = p.ld_max;
   d.sat = p.sat;
   d.qbits = qbits;
+  d.flags = p.flags;
   return d;
 }
 
@@ -428,7 +433,7 @@ tm_status forward_materialised(tm_ctx *c, const tm_image *in, const tm_image *ou
   mark(c, s, -1);
   launch_range(c->djobs, 1, rb, c->p.n_bins, s);
   mark(c, s, ST_RANGE);
-  launch_prep(c->djobs, 1, pb, c->p.n_bins, s);
+  launch_prep(c->djobs, 1, pb, c->p.n_bins, c->p.flags, s);
   mark(c, s, ST_PREP);
   n += 2 + launch_integral_jobs(c->djobs, 1, H, cb, nseg > 1, s);
   mark(c, s, ST_INTEGRAL);
@@ -568,7 +573,7 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   if (!graph) mark(c, s, -1);
   launch_range(dj, nimg, b_range, c->p.n_bins, s);
   if (!graph) mark(c, s, ST_RANGE);
-  launch_prep(dj, nimg, b_prep, c->p.n_bins, s);
+  launch_prep(dj, nimg, b_prep, c->p.n_bins, c->p.flags, s);
   if (!graph) mark(c, s, ST_PREP);
   n += 2 + launch_integral_jobs(dj, nimg, b_rows, b_cols, multi_seg, s);
   if (!graph) mark(c, s, ST_INTEGRAL);
@@ -696,6 +701,8 @@ tm_status backward_images(tm_ctx *c, int n, const tm_image *in, const tm_image *
   }
   if (c->p.n_bins < 2 || c->hist_path == 2)
     return fail(c, TM_EUNSUPPORTED, "the backward runs on the fused path (n_bins >= 2)");
+  if (c->p.flags & TM_FLAG_VAR_LINEAR)
+    return fail(c, TM_EUNSUPPORTED, "the backward covers the log-domain variance (not TM_FLAG_VAR_LINEAR)");
   if ((st = ensure_device_info(c))) return st;
   std::vector<Job> jobs;
   st = forward_fused(c, n, in, in, s, false, false, &jobs);

@@ -88,11 +88,12 @@ __global__ void __launch_bounds__(kBT) k_bwd_pixel(DevParams P, Job J, BwdJob B)
       Win w = window_of(P, f, x, y, W, H);
       const long long iA = (long long)w.y0 * W1 + w.x0, iB = (long long)w.y0 * W1 + w.x1 + 1;
       const long long iC = (long long)(w.y1 + 1) * W1 + w.x1 + 1, iD = (long long)(w.y1 + 1) * W1 + w.x0;
-      const unsigned long long Nw = (unsigned long long)(w.x1 - w.x0 + 1) * (w.y1 - w.y0 + 1);
-      const long long q1 = (long long)((unsigned long long)J.s1[iC] - (unsigned long long)J.s1[iD] -
-                                       (unsigned long long)J.s1[iB] + (unsigned long long)J.s1[iA]);
-      const long long q2 = (long long)((unsigned long long)J.s2[iC] - (unsigned long long)J.s2[iD] -
-                                       (unsigned long long)J.s2[iB] + (unsigned long long)J.s2[iA]);
+      unsigned long long Nw = (unsigned long long)(w.x1 - w.x0 + 1) * (w.y1 - w.y0 + 1);
+      long long q1 = (long long)((unsigned long long)J.s1[iC] - (unsigned long long)J.s1[iD] -
+                                 (unsigned long long)J.s1[iB] + (unsigned long long)J.s1[iA]);
+      long long q2 = (long long)((unsigned long long)J.s2[iC] - (unsigned long long)J.s2[iD] -
+                                 (unsigned long long)J.s2[iB] + (unsigned long long)J.s2[iA]);
+      literal_area(P, f, J.qbits, q1, q2, Nw);  // Algorithm 1's area: zero padding
       rarea[f] = __frcp_rn((float)Nw);
       var[f] = window_variance(q1, q2, Nw, rarea[f], inv_scale2);
       mu[f] = (float)q1 * rarea[f] * inv_scale + 0.5f;  // mean of lhat

@@ -30,7 +30,14 @@ struct DevParams {
   float ld_min, ld_max;     // display range of Eq. 2
   float sat;                // Eq. 12
   int qbits;                // Q: q = round(2^Q lhat) - 2^(Q-1)
+  int flags;                // TM_FLAG_* reading variants
 };
+
+// Reading variants (the TM_FLAG_* bits of tm_params.flags).
+constexpr int kFlagCdfIncl = 1;  // Eq. 1 with <=
+constexpr int kFlagAreaLit = 2;  // unclipped window area, zero padding
+constexpr int kFlagVarLin = 4;   // Eq. 10 on i / imax
+constexpr int kFlagSrgb = 8;     // sRGB-encoded uint8 output
 
 // Per-image range state, resident in device memory. The range kernel reduces
 // into min_bits/max_bits (luminance is positive, so float bits order like the
@@ -45,7 +52,8 @@ struct Stats {
   float log2_scale;         // 2^Q / (log2 imax - log2 imin), 0 if degenerate
   float c0;                 // log2 of imin's significand (in [1, 2))
   int e0;                   // unbiased exponent of imin
-  int pad[3];
+  float lin_scale;          // 2^Q / imax (quantisation of i / imax)
+  int pad[2];
   float thr[kMaxBins];      // thr[k-1]: lower edge of bin k, k = 1..n-1
 };
 
@@ -143,8 +151,14 @@ __device__ __forceinline__ void load_rgb(const Image &im, int x, int y, float &r
   }
 }
 
+// sRGB transfer function (IEC 61966-2-1) on a value clamped to [0, 1].
+__device__ __forceinline__ float srgb_encode(float c) {
+  c = fminf(fmaxf(c, 0.f), 1.f);
+  return c <= 0.0031308f ? 12.92f * c : 1.055f * powf(c, 1.f / 2.4f) - 0.055f;
+}
+
 __device__ __forceinline__ void store_rgb(const Image &im, int x, int y, float r,
-                                          float g, float b) {
+                                          float g, float b, bool srgb = false) {
   long long o = (long long)y * im.pitch + 3LL * x;
   if (im.dtype == kF32) {
     float *p = static_cast<float *>(im.p) + o;
@@ -158,6 +172,11 @@ __device__ __forceinline__ void store_rgb(const Image &im, int x, int y, float r
     p[2] = __float2half_rn(b);
   } else {
     uint8_t *p = static_cast<uint8_t *>(im.p) + o;
+    if (srgb) {
+      r = srgb_encode(r);
+      g = srgb_encode(g);
+      b = srgb_encode(b);
+    }
     p[0] = (uint8_t)__float2int_rd(fminf(fmaxf(r, 0.f), 1.f) * 255.f + 0.5f);
     p[1] = (uint8_t)__float2int_rd(fminf(fmaxf(g, 0.f), 1.f) * 255.f + 0.5f);
     p[2] = (uint8_t)__float2int_rd(fminf(fmaxf(b, 0.f), 1.f) * 255.f + 0.5f);
@@ -197,6 +216,29 @@ __device__ __forceinline__ int quantise_log(float lum, const Stats &st, int qbit
   int half = 1 << (qbits - 1);
   int q = (int)pi + __float2int_rn(rem) - half;
   return min(max(q, -half), half);
+}
+
+// Quantised linear luminance for the variance under TM_FLAG_VAR_LINEAR:
+// q = round(2^Q i / imax) - 2^(Q-1).
+__device__ __forceinline__ int quantise_lin(float lum, const Stats &st, int qbits) {
+  const int half = 1 << (qbits - 1);
+  const int q = __float2int_rn(lum * st.lin_scale) - half;
+  return min(max(q, -half), half);
+}
+
+// Under TM_FLAG_AREA_LITERAL: the window sums of q and q^2 and the area of
+// field f grow from the clipped window (area N) to the unclipped (2 rx + 1)
+// (2 ry + 1), the missing pixels taking the value 0 (q = -2^(Q-1)). Exact in
+// 64-bit arithmetic (Q is chosen for the unclipped area).
+__device__ __forceinline__ void literal_area(const DevParams &P, int f, int qbits, long long &q1,
+                                             long long &q2, unsigned long long &N) {
+  if (!(P.flags & kFlagAreaLit)) return;
+  const unsigned long long Nl = (unsigned long long)(2 * P.rx[f] + 1) * (unsigned long long)(2 * P.ry[f] + 1);
+  const unsigned long long pad = Nl - N;
+  const unsigned long long h = 1ull << (qbits - 1);
+  q1 = (long long)((unsigned long long)q1 - pad * h);
+  q2 = (long long)((unsigned long long)q2 + pad * (h * h));
+  N = Nl;
 }
 
 // Window of field f around (x, y), clipped to the image.

@@ -143,7 +143,10 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const SweepPlan &
     kmax = max(kmax, sm.red[32 + w]);
   }
   if (kmax < kmin) kmax = kmin = 0;
-  const int nw = (kmax - kmin + 1) >> 1;  // thresholds kmin+1 .. kmax, two per word
+  // Eq. 1 reads C_{b} (strict) or C_{b+1} (TM_FLAG_CDF_INCLUSIVE) at the
+  // corners: thresholds kmin+1 .. kmax + incl, two per word
+  const int incl = (P.flags & kFlagCdfIncl) ? 1 : 0;
+  const int nw = (kmax + incl - kmin + 1) >> 1;
 
   for (int t = tid; t < nw * S.cstride; t += kNT) sm.D[t] = 0u;
   for (int t = tid; t < nw; t += kNT) sm.m[t] = 0u;
@@ -286,7 +289,7 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const SweepPlan &
         const int e = tk_ex[i] >> 16, xo = tk_ex[i] & 0xffff;
         const int4 ev = evt[e];  // pixel row, ring offset, bin-ring offset
         if (ev.x < 0) continue;
-        const int b = sm.bring[ev.z + xo];
+        const int b = sm.bring[ev.z + xo] + incl;
         unsigned g = 0;
         if (b > kmin) {
           const int kk = b - kmin - 1;
@@ -324,7 +327,7 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const SweepPlan &
             const int y = ylo + yy, xo = t - yy * TXc, x = X0 + xo;
             const int T = max(y + a - 1, -1), B = min(y + bb, H - 1);
             if (B <= T) continue;  // empty slab: counted as 0 by the lookup
-            const int b = sm.bring[(y % S.BR) * S.TX + xo];
+            const int b = sm.bring[(y % S.BR) * S.TX + xo] + incl;
             unsigned g = 0;
             if (b > kmin) {
               const int kk = b - kmin - 1;

@@ -12,7 +12,7 @@ namespace tmk {
 // Stage a0: range of Eq. 11 luminance, bin edges, quantisation constants.
 void launch_range(const Job *jobs, int njobs, int blocks, int n_bins, cudaStream_t s);
 // Stage a1: bin map (uint8) and quantised normalised log (int32).
-void launch_prep(const Job *jobs, int njobs, int blocks, int n_bins, cudaStream_t s);
+void launch_prep(const Job *jobs, int njobs, int blocks, int n_bins, int flags, cudaStream_t s);
 // Blocks of the range / prep stages for one image.
 int range_blocks(int W, int H, int num_sms, double share);
 int prep_blocks(int W, int H, int num_sms, double share);

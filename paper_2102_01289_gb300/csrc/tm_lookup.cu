@@ -17,19 +17,20 @@ namespace {
 // (Eq. 6, Eq. 10).
 __device__ __forceinline__ void window_stats(const DevParams &P, int f, int x, int y, int W, int H,
                                              const long long *__restrict__ s1,
-                                             const long long *__restrict__ s2, float inv_scale2,
-                                             float &rarea, float &var) {
+                                             const long long *__restrict__ s2, int qbits,
+                                             float inv_scale2, float &rarea, float &var) {
   const long long W1 = (long long)W + 1;
   Win w = window_of(P, f, x, y, W, H);
   const long long iA = (long long)w.y0 * W1 + w.x0;
   const long long iB = (long long)w.y0 * W1 + w.x1 + 1;
   const long long iC = (long long)(w.y1 + 1) * W1 + w.x1 + 1;
   const long long iD = (long long)(w.y1 + 1) * W1 + w.x0;
-  const unsigned long long N = (unsigned long long)(w.x1 - w.x0 + 1) * (w.y1 - w.y0 + 1);
-  const long long q1 = (long long)((unsigned long long)__ldg(s1 + iC) - (unsigned long long)__ldg(s1 + iD) -
-                                   (unsigned long long)__ldg(s1 + iB) + (unsigned long long)__ldg(s1 + iA));
-  const long long q2 = (long long)((unsigned long long)__ldg(s2 + iC) - (unsigned long long)__ldg(s2 + iD) -
-                                   (unsigned long long)__ldg(s2 + iB) + (unsigned long long)__ldg(s2 + iA));
+  unsigned long long N = (unsigned long long)(w.x1 - w.x0 + 1) * (w.y1 - w.y0 + 1);
+  long long q1 = (long long)((unsigned long long)__ldg(s1 + iC) - (unsigned long long)__ldg(s1 + iD) -
+                             (unsigned long long)__ldg(s1 + iB) + (unsigned long long)__ldg(s1 + iA));
+  long long q2 = (long long)((unsigned long long)__ldg(s2 + iC) - (unsigned long long)__ldg(s2 + iD) -
+                             (unsigned long long)__ldg(s2 + iB) + (unsigned long long)__ldg(s2 + iA));
+  literal_area(P, f, qbits, q1, q2, N);
   rarea = __frcp_rn((float)N);
   var = window_variance(q1, q2, N, rarea, inv_scale2);
 }
@@ -44,10 +45,10 @@ struct Fusion {
 // time, so no per-field state is kept).
 __device__ __forceinline__ void fold_field(const DevParams &P, int f, int x, int y, int W, int H,
                                            unsigned cnt, const long long *__restrict__ s1,
-                                           const long long *__restrict__ s2, float inv_scale2,
-                                           Fusion &fu, const DebugPlanes &dbg) {
+                                           const long long *__restrict__ s2, int qbits,
+                                           float inv_scale2, Fusion &fu, const DebugPlanes &dbg) {
   float rarea, var;
-  window_stats(P, f, x, y, W, H, s1, s2, inv_scale2, rarea, var);
+  window_stats(P, f, x, y, W, H, s1, s2, qbits, inv_scale2, rarea, var);
   const float Pf = (float)cnt * rarea;                                  // Eq. 1
   const float Lf = fmaf(P.ld_max - P.ld_min, Pf, P.ld_min);             // Eq. 2
   const float Wf = __fdividef(P.alpha[f] * var, var + P.eps[f]);       // Eq. 4
@@ -72,7 +73,7 @@ __device__ __forceinline__ void finish_pixel(const Image &in, const Image &out, 
   load_rgb(in, x, y, r, g, b);
   const float inv_i = __frcp_rn(luminance(r, g, b));
   store_rgb(out, x, y, restore_channel(r, inv_i, P.sat, L), restore_channel(g, inv_i, P.sat, L),
-            restore_channel(b, inv_i, P.sat, L));
+            restore_channel(b, inv_i, P.sat, L), (P.flags & kFlagSrgb) != 0);
   if (dbg.l) dbg.l[(long long)y * in.W + x] = L;
 }
 
@@ -86,18 +87,21 @@ __global__ void __launch_bounds__(256)
   if (x >= W || y >= H) return;
   const long long W1 = (long long)W + 1;
   const long long plane = W1 * ((long long)H + 1);
-  const int b = bins[(long long)y * W + x];
-  const unsigned *C = b > 0 ? cplanes + (long long)(b - 1) * plane : nullptr;
+  // Eq. 1 numerator: box sum of C_t, t = b (strict) or b + 1 (inclusive);
+  // C_0 = 0 and C_n is the whole (clipped) window
+  const int t = bins[(long long)y * W + x] + ((P.flags & kFlagCdfIncl) ? 1 : 0);
+  const unsigned *C = t > 0 && t < P.n_bins ? cplanes + (long long)(t - 1) * plane : nullptr;
   const float inv_scale2 = ldexpf(1.f, -2 * P.qbits);
   Fusion fu;
   for (int f = 0; f < P.n_fields; ++f) {
     unsigned cnt = 0u;
-    if (C) {
-      Win w = window_of(P, f, x, y, W, H);
+    Win w = window_of(P, f, x, y, W, H);
+    if (C)
       cnt = __ldg(C + (long long)(w.y1 + 1) * W1 + w.x1 + 1) - __ldg(C + (long long)(w.y1 + 1) * W1 + w.x0) -
             __ldg(C + (long long)w.y0 * W1 + w.x1 + 1) + __ldg(C + (long long)w.y0 * W1 + w.x0);
-    }
-    fold_field(P, f, x, y, W, H, cnt, s1, s2, inv_scale2, fu, dbg);
+    else if (t >= P.n_bins)
+      cnt = (unsigned)((w.x1 - w.x0 + 1) * (w.y1 - w.y0 + 1));
+    fold_field(P, f, x, y, W, H, cnt, s1, s2, P.qbits, inv_scale2, fu, dbg);
   }
   finish_pixel(in, out, P, x, y, fu, dbg);
 }
@@ -126,7 +130,7 @@ __global__ void __launch_bounds__(256) k_lookup_counts(DevParams P, const Job *_
       const int T = max(y + S.slab_a[s] - 1, -1), B = min(y + S.slab_b[s], H - 1);
       if (B > T) cnt += __ldg(J.counts + s * N + pix);
     }
-    fold_field(P, f, x, y, W, H, cnt, J.s1, J.s2, inv_scale2, fu, J.dbg);
+    fold_field(P, f, x, y, W, H, cnt, J.s1, J.s2, J.qbits, inv_scale2, fu, J.dbg);
   }
   finish_pixel(J.in, J.out, P, x, y, fu, J.dbg);
 }

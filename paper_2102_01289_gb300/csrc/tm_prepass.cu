@@ -155,6 +155,7 @@ __global__ void __launch_bounds__(256) k_range(const Job *__restrict__ jobs, int
     st->c0 = (float)log2(m0);
     st->log2_scale =
         degenerate ? 0.f : (float)(ldexp(1.0, J.qbits) / (log2((double)imax) - log2((double)imin)));
+    st->lin_scale = (float)(ldexp(1.0, J.qbits) / (double)imax);
     st->imin = imin;
     st->imax = imax;
     st->degenerate = degenerate ? 1 : 0;
@@ -164,9 +165,11 @@ __global__ void __launch_bounds__(256) k_range(const Job *__restrict__ jobs, int
   }
 }
 
-// Bin map (Section II-A, edges from k_range) and quantised normalised log.
-// One thread per group of four pixels.
-__global__ void __launch_bounds__(256) k_prep(const Job *__restrict__ jobs, int njobs, int n_bins) {
+// Bin map (Section II-A, edges from k_range) and the quantised values whose
+// window variance Eq. 10 takes: the normalised log, or i / imax under
+// TM_FLAG_VAR_LINEAR. One thread per group of four pixels.
+__global__ void __launch_bounds__(256) k_prep(const Job *__restrict__ jobs, int njobs, int n_bins,
+                                              int flags) {
   __shared__ float thr[kMaxBins];
   const int j = find_job(jobs, njobs, kStPrep, blockIdx.x);
   const Job &J = jobs[j];
@@ -180,6 +183,8 @@ __global__ void __launch_bounds__(256) k_prep(const Job *__restrict__ jobs, int 
   sst.c0 = __ldg(&st->c0);
   sst.e0 = __ldg(&st->e0);
   sst.log2_scale = __ldg(&st->log2_scale);
+  sst.lin_scale = __ldg(&st->lin_scale);
+  const bool lin = (flags & kFlagVarLin) != 0;
   __syncthreads();
   const int W = in.W, H = in.H, qbits = J.qbits;
   uint8_t *bins = J.bins;
@@ -197,7 +202,7 @@ __global__ void __launch_bounds__(256) k_prep(const Job *__restrict__ jobs, int 
     for (int i = 0; i < 4; ++i) {
       const float l = luminance(r[i], g[i], b[i]);
       bq |= (unsigned)bin_of(l, thr, n_bins) << (8 * i);
-      qq[i] = quantise_log(l, sst, qbits);
+      qq[i] = lin ? quantise_lin(l, sst, qbits) : quantise_log(l, sst, qbits);
     }
     const long long o = (long long)y * W + x;
     if (n == 4 && (o & 3) == 0) {
@@ -232,8 +237,8 @@ void launch_range(const Job *jobs, int njobs, int blocks, int n_bins, cudaStream
   k_range<<<blocks, 256, 0, s>>>(jobs, njobs, n_bins);
 }
 
-void launch_prep(const Job *jobs, int njobs, int blocks, int n_bins, cudaStream_t s) {
-  k_prep<<<blocks, 256, 0, s>>>(jobs, njobs, n_bins);
+void launch_prep(const Job *jobs, int njobs, int blocks, int n_bins, int flags, cudaStream_t s) {
+  k_prep<<<blocks, 256, 0, s>>>(jobs, njobs, n_bins, flags);
 }
 
 }  // namespace tmk

@@ -60,7 +60,7 @@ def test_defaults_are_the_papers(built):
 
 @pytest.mark.parametrize("field,value", [
     ("n_bins", 0), ("n_bins", 257), ("n_fields", 0), ("n_fields", 9), ("sat", -1.0),
-    ("ld_min", 2.0), ("flags", 1),
+    ("ld_min", 2.0), ("flags", 16), ("flags", -1),
 ])
 def test_create_rejects_bad_params(built, field, value):
     p = tm.make_params(8, [1, 2])
@@ -120,3 +120,11 @@ def test_missing_library_fails_loudly(monkeypatch):
     monkeypatch.setattr(tm, "LIB_PATH", "/nonexistent/libtm.so")
     with pytest.raises(RuntimeError, match="missing"):
         tm.tm_create(tm.TmParams())
+
+
+def test_defined_flags_accepted(built):
+    for flags in (tm.TM_FLAG_CDF_INCLUSIVE, tm.TM_FLAG_AREA_LITERAL, tm.TM_FLAG_VAR_LINEAR,
+                  tm.TM_FLAG_SRGB_U8, 15):
+        p = tm.make_params(8, [1, 2])
+        p.flags = flags
+        tm.tm_destroy(tm.tm_create(p))

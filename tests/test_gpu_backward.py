@@ -24,12 +24,12 @@ def _built():
     tm.build()
 
 
-def _pair(orc, n, radii, eps, alpha, ld_min=0.05, ld_max=0.95, sat=0.6):
-    gp = tm.make_params(n, radii, eps, alpha, ld_min, ld_max, sat)
+def _pair(orc, n, radii, eps, alpha, ld_min=0.05, ld_max=0.95, sat=0.6, flags=0):
+    gp = tm.make_params(n, radii, eps, alpha, ld_min, ld_max, sat, flags=flags)
     s = len(radii)
     op = orc.make_params(n, radii, eps=[float(gp.eps[f]) for f in range(s)],
                          alpha=[float(gp.alpha[f]) for f in range(s)], ld_min=float(gp.ld_min),
-                         ld_max=float(gp.ld_max), sat=float(gp.sat))
+                         ld_max=float(gp.ld_max), sat=float(gp.sat), flags=flags)
     return gp, op
 
 
@@ -54,12 +54,13 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("flags", [0, 3])  # defaults; inclusive CDF + Algorithm 1's area
 @pytest.mark.parametrize("H,W,n,radii", CASES)
-def test_backward_matches_oracle_adjoint(orc, H, W, n, radii):
+def test_backward_matches_oracle_adjoint(orc, H, W, n, radii, flags):
     rng = np.random.default_rng(H + W)
     img = synth.wdr_image(H, W, seed=H * 7 + W)
     s = len(radii)
-    gp, op = _pair(orc, n, radii, eps=[0.1, 0.03, 0.2][:s], alpha=[1.0, 0.8, 1.2][:s])
+    gp, op = _pair(orc, n, radii, eps=[0.1, 0.03, 0.2][:s], alpha=[1.0, 0.8, 1.2][:s], flags=flags)
     gout = rng.standard_normal(img.shape)
     gin, gpar = _gpu_backward(img, gp, gout)
     ref_in, ref_p = orc.backward(img.astype(np.float64), op, gout, lum_f64=False)
@@ -172,5 +173,17 @@ def test_backward_batch_matches_per_image():
         tm.tm_backward_batch(ctx, [], [], None, gp_b)
         torch.cuda.synchronize()
         assert float(gp_b.abs().max()) == 0.0
+    finally:
+        tm.tm_destroy(ctx)
+
+
+def test_backward_rejects_linear_variance():
+    p = tm.make_params(8, [1, 3], flags=tm.TM_FLAG_VAR_LINEAR)
+    x = torch.from_numpy(synth.wdr_image(16, 16, seed=1)).cuda()
+    ctx = tm.tm_create(p)
+    try:
+        with pytest.raises(tm.TmError) as e:
+            tm.tm_backward(ctx, x, torch.ones_like(x), torch.empty_like(x))
+        assert e.value.status == tm.TM_EUNSUPPORTED
     finally:
         tm.tm_destroy(ctx)

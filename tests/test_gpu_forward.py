@@ -31,14 +31,15 @@ def f32(v):
     return float(np.float32(v))
 
 
-def params_pair(orc, n, radii, eps=0.1, alpha=1.0, ld_min=0.0, ld_max=1.0, sat=0.6):
+def params_pair(orc, n, radii, eps=0.1, alpha=1.0, ld_min=0.0, ld_max=1.0, sat=0.6, flags=0):
     """The same parameters for the library (float) and the oracle (the float
-    values widened to double)."""
-    gp = tm.make_params(n, radii, eps, alpha, ld_min, ld_max, sat)
+    values widened to double). The sRGB output bit has no oracle counterpart:
+    the oracle's float output is encoded by the test."""
+    gp = tm.make_params(n, radii, eps, alpha, ld_min, ld_max, sat, flags=flags)
     s = len(radii)
     op = orc.make_params(n, radii, eps=[float(gp.eps[f]) for f in range(s)],
                          alpha=[float(gp.alpha[f]) for f in range(s)], ld_min=float(gp.ld_min),
-                         ld_max=float(gp.ld_max), sat=float(gp.sat))
+                         ld_max=float(gp.ld_max), sat=float(gp.sat), flags=flags & ~tm.TM_FLAG_SRGB_U8)
     return gp, op
 
 
@@ -320,3 +321,51 @@ def test_paper_preset_12mp_sampled(orc):
     ref, dd = orc.forward_pixels(img, op, xs, ys)
     assert np.array_equal(d["cnt"][:, ys, xs].T, dd["cnt"])
     assert_out_close(out[ys, xs], ref)
+
+
+FLAG_SETS = [tm.TM_FLAG_CDF_INCLUSIVE, tm.TM_FLAG_AREA_LITERAL, tm.TM_FLAG_VAR_LINEAR,
+             tm.TM_FLAG_CDF_INCLUSIVE | tm.TM_FLAG_AREA_LITERAL | tm.TM_FLAG_VAR_LINEAR]
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("flags", FLAG_SETS)
+def test_reading_variants_match_oracle(orc, flags, path):
+    """Each reading variant (Eq. 1 with <=, Algorithm 1's unclipped area,
+    Eq. 10 on i / imax) against the oracle's: counts bit-exact, variances
+    within the quantisation bound, outputs within the float tolerance. The
+    last field is larger than the image (clipping and padding matter)."""
+    H, W = 61, 97
+    img = synth.wdr_image(H, W, seed=41)
+    gp, op = params_pair(orc, 16, [1, (6, 3), 40], eps=[0.1, 0.05, 0.2], flags=flags)
+    out, d = run_gpu(img, gp, path=path)
+    ref, fl = orc.forward(img, op)
+    assert np.array_equal(d["cnt"], fl.cnt)
+    assert np.all(np.abs(d["sigma2"] - fl.sigma2) <= _sigma2_tol(fl.sigma2, d["qbits"]))
+    assert_out_close(d["l"], fl.l)
+    assert_out_close(out, ref)
+
+
+def test_inclusive_cdf_on_the_sweep_at_full_bin_range(orc):
+    """Eq. 1 with <= reads threshold b + 1, one past the highest bin of a
+    tile; 256 bins and a region spanning all of them."""
+    img = synth.wdr_image(40, 60, seed=42, decades=(-4.0, 6.0))
+    gp, op = params_pair(orc, 256, [2, 9], flags=tm.TM_FLAG_CDF_INCLUSIVE)
+    out, d = run_gpu(img, gp, path=1)
+    ref, fl = orc.forward(img, op)
+    assert np.array_equal(d["cnt"], fl.cnt)
+    assert_out_close(out, ref)
+
+
+def test_srgb_uint8_output(orc):
+    """TM_FLAG_SRGB_U8: uint8 output is floor(255 srgb(clamp(c)) + 0.5) of
+    the oracle's float result, within 1 LSB on at most 0.01% of the values."""
+    img = synth.wdr_image(70, 90, seed=43)
+    gp, op = params_pair(orc, 32, [2, 8, 30], flags=tm.TM_FLAG_SRGB_U8)
+    ref, _ = orc.forward(img, op)
+    out8, _ = run_gpu(img, gp, out_dtype=torch.uint8, debug=False)
+    ref8 = orc.to_u8(ref, srgb=True).astype(np.int64)
+    diff = np.abs(out8.astype(np.int64) - ref8)
+    assert diff.max() <= 1 and (diff > 0).mean() <= 1e-4
+    # float outputs are not encoded
+    outf, _ = run_gpu(img, gp, debug=False)
+    assert_out_close(outf, ref)

@@ -292,18 +292,20 @@ def test_weight_limits(orc):
 
 
 # --------------------------------------------------------------- adjoint --
-def _fd_setup(orc, seed=0, H=6, W=7, radii=(1, 2, 9)):
+def _fd_setup(orc, seed=0, H=6, W=7, radii=(1, 2, 9), flags=0):
     rng = np.random.default_rng(seed)
     img = synth.wdr_image(H, W, seed=seed).astype(np.float64)
     p = orc.make_params(5, list(radii), eps=[0.05, 0.1, 0.2][: len(radii)],
-                        alpha=[1.0, 0.8, 1.2][: len(radii)], ld_min=0.05, ld_max=0.95, sat=0.6)
+                        alpha=[1.0, 0.8, 1.2][: len(radii)], ld_min=0.05, ld_max=0.95, sat=0.6,
+                        flags=flags)
     bins = orc.prepare(img.astype(np.float32), 5)["bins"]
     g = rng.standard_normal(img.shape)
     return img, p, bins, g
 
 
-def test_adjoint_matches_central_differences_input(orc):
-    img, p, bins, g = _fd_setup(orc)
+@pytest.mark.parametrize("flags", [0, 3])  # defaults; inclusive CDF + Algorithm 1's area
+def test_adjoint_matches_central_differences_input(orc, flags):
+    img, p, bins, g = _fd_setup(orc, flags=flags)
     gin, _ = orc.backward(img, p, g, lum_f64=True, bins=bins)
     rng = np.random.default_rng(1)
     idx = [tuple(rng.integers(0, s) for s in img.shape) for _ in range(12)]
@@ -320,8 +322,9 @@ def test_adjoint_matches_central_differences_input(orc):
         assert abs(fd - gin[ix]) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(gin).max()), (ix, fd, gin[ix])
 
 
-def test_adjoint_matches_central_differences_params(orc):
-    img, p, bins, g = _fd_setup(orc, seed=3)
+@pytest.mark.parametrize("flags", [0, 3])
+def test_adjoint_matches_central_differences_params(orc, flags):
+    img, p, bins, g = _fd_setup(orc, seed=3, flags=flags)
     _, gp = orc.backward(img, p, g, lum_f64=True, bins=bins)
 
     def loss(q):
