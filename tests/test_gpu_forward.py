@@ -227,7 +227,8 @@ def test_pinned_host_output_written_directly(orc):
 
 def test_integral_image_entry_point_exact(orc):
     rng = np.random.default_rng(0)
-    for H, W in [(1, 1), (7, 3000), (300, 257), (2500, 5)]:
+    # up to a full-size ragged plane (several row segments of the column pass)
+    for H, W in [(1, 1), (7, 3000), (300, 257), (2500, 5), (33, 129), (3001, 4003)]:
         q = rng.integers(-(2 ** 23), 2 ** 23 + 1, size=(H, W)).astype(np.int32)
         qt = torch.from_numpy(q).cuda()
         s1 = torch.empty((H + 1, W + 1), dtype=torch.int64, device="cuda")
