@@ -118,6 +118,7 @@ def _load():
             lib.tmo_integral_f64.argtypes = [P, i32, i32, P]
             lib.tmo_integral_histogram.argtypes = [P, i32, i32, i32, P]
             lib.tmo_forward.argtypes = [P, i32, i32, P, P, P]
+            lib.tmo_forward_range.argtypes = [P, i32, i32, P, P, P, P]
             lib.tmo_forward_pixels.argtypes = [P, i32, i32, P, P, P, i64, P, P, P, P, P, P]
             lib.tmo_forward_fixed_bins.argtypes = [P, i32, i32, P, P, P]
             lib.tmo_backward.argtypes = [P, i32, i32, P, i32, P, P, P, P]
@@ -208,8 +209,10 @@ class _CFields(ctypes.Structure):
     _fields_ = [(n, ctypes.c_void_p) for n in ("cnt", "area", "mu", "sigma2", "weight", "lf", "l")]
 
 
-def forward(rgb, p: Params):
-    """Full forward (Eq. 11 -> Eq. 12). Returns (out (H,W,3) f64, Fields)."""
+def forward(rgb, p: Params, range_=None):
+    """Full forward (Eq. 11 -> Eq. 12). Returns (out (H,W,3) f64, Fields).
+    range_: None, or (imin, imax) floats of an earlier frame to bin and
+    normalise with (streaming reuse; the normalised log is clamped to [0, 1])."""
     a = _rgb32(rgb)
     H, W, _ = a.shape
     s = p.n_fields
@@ -218,7 +221,11 @@ def forward(rgb, p: Params):
                 mu=np.empty((s, H, W)), sigma2=np.empty((s, H, W)), weight=np.empty((s, H, W)),
                 lf=np.empty((s, H, W)), l=np.empty((H, W)))
     cf = _CFields(*[f.ctypes.data for f in (fl.cnt, fl.area, fl.mu, fl.sigma2, fl.weight, fl.lf, fl.l)])
-    rc = _load().tmo_forward(_ptr(a), W, H, ctypes.byref(p), _ptr(out), ctypes.byref(cf))
+    rng = None
+    if range_ is not None:
+        rng = np.ascontiguousarray(np.asarray(range_, dtype=np.float32))
+    rc = _load().tmo_forward_range(_ptr(a), W, H, ctypes.byref(p), _ptr(rng) if rng is not None else None,
+                                   _ptr(out), ctypes.byref(cf))
     if rc:
         raise ValueError(f"tmo_forward failed ({rc})")
     return out, fl

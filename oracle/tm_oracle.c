@@ -244,8 +244,11 @@ static void core_free(core_t *c) {
   memset(c, 0, sizeof(*c));
 }
 
+/* range: NULL, or {imin, imax} to bin and normalise with instead of the
+ * image's own range (streaming reuse of an earlier frame's range); the
+ * normalised log is then clamped to [0, 1]. */
 static int core_run(const double *rgb, int W, int H, const tmo_params *p,
-                    int lum_f64, const uint8_t *fixed_bins, core_t *c) {
+                    int lum_f64, const uint8_t *fixed_bins, const float *range, core_t *c) {
   memset(c, 0, sizeof(*c));
   if (W <= 0 || H <= 0 || !params_ok(p)) return -1;
   int s = p->n_fields, n = p->n_bins;
@@ -290,6 +293,10 @@ static int core_run(const double *rgb, int W, int H, const tmo_params *p,
   }
   c->imin = c->lum[c->argmin];
   c->imax = c->lum[c->argmax];
+  if (range) {
+    c->imin = (double)range[0];
+    c->imax = (double)range[1];
+  }
   /* Sec. II-A bins (R3) */
   if (fixed_bins) {
     memcpy(c->bins, fixed_bins, N);
@@ -302,8 +309,10 @@ static int core_run(const double *rgb, int W, int H, const tmo_params *p,
   /* Sec. II log compression, normalised (R2) */
   c->lmin = log(c->imin);
   c->D = (c->imax > c->imin) ? log(c->imax) - c->lmin : 0.0;
-  for (int64_t q = 0; q < N; ++q)
-    c->lhat[q] = c->D > 0.0 ? (log(c->lum[q]) - c->lmin) / c->D : 0.0;
+  for (int64_t q = 0; q < N; ++q) {
+    double l = c->D > 0.0 ? (log(c->lum[q]) - c->lmin) / c->D : 0.0;
+    c->lhat[q] = l < 0.0 ? 0.0 : l > 1.0 ? 1.0 : l;  /* a no-op with the image's own range */
+  }
   /* the values whose window variance Eq. 10 takes */
   const double *vdom = c->lhat;
   double *lin = NULL;
@@ -353,15 +362,15 @@ static int core_run(const double *rgb, int W, int H, const tmo_params *p,
   return 0;
 }
 
-int tmo_forward(const float *rgb, int32_t W, int32_t H, const tmo_params *p,
-                double *out, tmo_fields *fields) {
+int tmo_forward_range(const float *rgb, int32_t W, int32_t H, const tmo_params *p,
+                      const float *range, double *out, tmo_fields *fields) {
   if (W <= 0 || H <= 0) return -1;
   int64_t N = (int64_t)W * H;
   double *rgbd = malloc(sizeof(double) * 3 * N);
   if (!rgbd) return -2;
   for (int64_t q = 0; q < 3 * N; ++q) rgbd[q] = (double)rgb[q];
   core_t c;
-  int rc = core_run(rgbd, W, H, p, 0, NULL, &c);
+  int rc = core_run(rgbd, W, H, p, 0, NULL, range, &c);
   free(rgbd);
   if (rc) return rc;
   for (int64_t q = 0; q < N; ++q)
@@ -381,11 +390,16 @@ int tmo_forward(const float *rgb, int32_t W, int32_t H, const tmo_params *p,
   return 0;
 }
 
+int tmo_forward(const float *rgb, int32_t W, int32_t H, const tmo_params *p,
+                double *out, tmo_fields *fields) {
+  return tmo_forward_range(rgb, W, H, p, NULL, out, fields);
+}
+
 int tmo_forward_fixed_bins(const double *rgb, int32_t W, int32_t H,
                            const tmo_params *p, const uint8_t *bins,
                            double *out) {
   core_t c;
-  int rc = core_run(rgb, W, H, p, 1, bins, &c);
+  int rc = core_run(rgb, W, H, p, 1, bins, NULL, &c);
   if (rc) return rc;
   for (int64_t q = 0; q < c.N; ++q)
     for (int ch = 0; ch < 3; ++ch)
@@ -454,7 +468,7 @@ int tmo_backward(const double *rgb, int32_t W, int32_t H, const tmo_params *p,
                  double *grad_in, double *grad_params) {
   if (p->flags & TMO_VAR_LINEAR) return -3;  /* the adjoint covers the log-domain variance */
   core_t c;
-  int rc = core_run(rgb, W, H, p, lum_f64, bins, &c);
+  int rc = core_run(rgb, W, H, p, lum_f64, bins, NULL, &c);
   if (rc) return rc;
   int s = c.s;
   int64_t N = c.N;

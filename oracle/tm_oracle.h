@@ -83,6 +83,12 @@ void tmo_integral_histogram(const uint8_t *bins, int32_t W, int32_t H,
 
 /* Full forward over the image (counts through Eq. 9, variance by direct
  * window sums). out: H*W*3 doubles. fields: optional (NULL fields ignored). */
+/* tmo_forward with bins and the normalised log taken over a given range
+ * {imin, imax} (an earlier frame's) instead of the image's own; the
+ * normalised log is clamped to [0, 1]. range == NULL is tmo_forward. */
+int tmo_forward_range(const float *rgb, int32_t W, int32_t H, const tmo_params *p,
+                      const float *range, double *out, tmo_fields *fields);
+
 int tmo_forward(const float *rgb, int32_t W, int32_t H, const tmo_params *p,
                 double *out, tmo_fields *fields);
 

@@ -442,3 +442,32 @@ def test_srgb_encode_published_values(orc):
     ref = [0.7353569830524495, 0.4613561295004773, 0.040449936, 0.0, 1.0, 128 / 255]
     assert np.allclose(enc, ref, rtol=0, atol=2e-9)
     assert orc.to_u8([0.5], srgb=True)[0] == 188 and orc.to_u8([0.5])[0] == 128
+
+
+def test_forward_with_a_given_range(orc):
+    """Streaming reuse reads an earlier frame's range: with the image's own
+    range it is the plain forward; with a narrower range the bins come from
+    that range's edges (numpy searchsorted on exp-spaced edges) and the
+    normalised log is clamped to [0, 1]."""
+    img = synth.wdr_image(12, 15, seed=6)
+    n = 8
+    p = orc.make_params(n, [1, 4])
+    d = orc.prepare(img, n)
+    own = (float(d["imin"]), float(d["imax"]))
+    o1, f1 = orc.forward(img, p)
+    o2, f2 = orc.forward(img, p, range_=own)
+    assert np.array_equal(o1, o2) and np.array_equal(f1.cnt, f2.cnt)
+    lum = d["lum"].astype(np.float64)
+    lo, hi = np.quantile(lum, [0.2, 0.8]).astype(np.float32)
+    _, f3 = orc.forward(img, p, range_=(lo, hi))
+    k = np.arange(1, n)
+    edges = np.exp(np.log(float(lo)) + (np.log(float(hi)) - np.log(float(lo))) * k / n)
+    b = np.searchsorted(edges, lum, side="right")  # edge value -> upper bin
+    lhat = np.clip((np.log(lum) - np.log(float(lo))) / (np.log(float(hi)) - np.log(float(lo))), 0, 1)
+    H, W = b.shape
+    for y in range(H):
+        for x in range(W):
+            w = (slice(max(y - 1, 0), min(y + 1, H - 1) + 1), slice(max(x - 1, 0), min(x + 1, W - 1) + 1))
+            assert f3.cnt[0, y, x] == int(np.sum(b[w] < b[y, x]))
+            v = float(np.var(lhat[w]))
+            assert abs(f3.sigma2[0, y, x] - v) <= 1e-12 + 1e-9 * v
