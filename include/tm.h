@@ -255,8 +255,20 @@ tm_status tm_debug_export(tm_ctx *ctx, int32_t what, void *dst, size_t bytes,
  *                        2 = materialised bin-major integral histogram.
  *   TM_OPT_STAGE_TIMING  1 = record a CUDA event after every stage of each
  *                        forward/backward call on its stream (see
- *                        tm_stage_times); 0 = off (default). */
-enum { TM_OPT_HIST_PATH = 1, TM_OPT_STAGE_TIMING = 2 };
+ *                        tm_stage_times); 0 = off (default).
+ *   TM_OPT_REUSE_RANGE   1 = streaming video: tm_forward bins and
+ *                        normalises each image with the luminance range of
+ *                        the previous tm_forward on this context (same size),
+ *                        and takes the image's own range for the next one
+ *                        inside the bin pass, so the input is read once less.
+ *                        The normalised log is clamped to [0, 1]. The first
+ *                        image, and one whose size differs from the previous,
+ *                        use their own range. A variant of the paper's method
+ *                        (which takes each image's own range); off by default.
+ *                        Batches and tm_backward always use each image's own
+ *                        range.
+ */
+enum { TM_OPT_HIST_PATH = 1, TM_OPT_STAGE_TIMING = 2, TM_OPT_REUSE_RANGE = 3 };
 tm_status tm_set_option(tm_ctx *ctx, int32_t key, int64_t value);
 
 /* Per-stage device time, summed over every call since the previous read,

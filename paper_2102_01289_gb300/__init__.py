@@ -24,6 +24,7 @@ TM_F32, TM_F16, TM_U8 = 0, 1, 2
  TM_DBG_WEIGHT, TM_DBG_LF, TM_DBG_L, TM_DBG_QSHIFT) = range(1, 11)
 TM_OPT_HIST_PATH = 1
 TM_OPT_STAGE_TIMING = 2
+TM_OPT_REUSE_RANGE = 3
 # reading variants (tm_params.flags)
 TM_FLAG_CDF_INCLUSIVE, TM_FLAG_AREA_LITERAL, TM_FLAG_VAR_LINEAR, TM_FLAG_SRGB_U8 = 1, 2, 4, 8
 

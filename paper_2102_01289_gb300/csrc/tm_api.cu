@@ -74,6 +74,12 @@ struct tm_ctx {
   std::vector<tm_image> graph_in, graph_out;
   cudaStream_t graph_stream = nullptr;
   int64_t graph_launches = 0;
+  // streaming range reuse (TM_OPT_REUSE_RANGE): two range states; a forward
+  // bins with rr_stats[rr_cur] and leaves its own range in the other
+  int reuse_range = 0;
+  Stats *rr_stats = nullptr;
+  int rr_cur = 0, rr_valid = 0, rr_W = 0, rr_H = 0, rr_q = 0;
+  const Stats *last_stats = nullptr;  // range state of the last single-image forward
   // stage timing: events recorded on the call's stream after each stage
   int stage_timing = 0;
   std::vector<std::vector<std::pair<cudaEvent_t, int>>> marks;
@@ -268,6 +274,30 @@ tm_status ensure_stats(tm_ctx *c, int n) {
   return TM_OK;
 }
 
+// Range states of a single-image forward under TM_OPT_REUSE_RANGE: the image
+// is binned over *cur, which holds the previous image's range, unless there
+// is no usable previous image (first call, other size or Q): then *own is set
+// and the range pass fills *cur first. The bin pass leaves the image's own
+// range in *next, the state the following call bins over.
+tm_status reuse_states(tm_ctx *c, int W, int H, int qbits, Stats **cur, Stats **next, bool *own) {
+  if (!c->rr_stats) {
+    Stats h[2];
+    memset(h, 0, sizeof h);
+    h[0].min_bits = h[1].min_bits = 0x7f800000u;
+    TM_CUDA(c, cudaMalloc(&c->rr_stats, sizeof h));
+    TM_CUDA(c, cudaMemcpy(c->rr_stats, h, sizeof h, cudaMemcpyHostToDevice));
+  }
+  *own = !(c->rr_valid && c->rr_W == W && c->rr_H == H && c->rr_q == qbits);
+  *cur = c->rr_stats + c->rr_cur;
+  *next = c->rr_stats + (c->rr_cur ^ 1);
+  c->rr_cur ^= 1;
+  c->rr_valid = 1;
+  c->rr_W = W;
+  c->rr_H = H;
+  c->rr_q = qbits;
+  return TM_OK;
+}
+
 tm_status grow_device(tm_ctx *c, void **p, size_t *have, size_t bytes) {
   if (*have >= bytes) return TM_OK;
   drop_graph(c);
@@ -408,6 +438,12 @@ tm_status forward_materialised(tm_ctx *c, const tm_image *in, const tm_image *ou
   J.in = to_image(in);
   J.out = to_image(out);
   J.st = c->stats;
+  bool run_range = true;
+  if (c->reuse_range) {
+    bool own = true;
+    if ((st = reuse_states(c, W, H, qbits, &J.st, &J.st_next, &own))) return st;
+    run_range = own;
+  }
   J.bins = reinterpret_cast<uint8_t *>(ws + L.bins);
   J.q = reinterpret_cast<int32_t *>(ws + L.q);
   J.s1 = reinterpret_cast<long long *>(ws + L.s1);
@@ -431,11 +467,11 @@ tm_status forward_materialised(tm_ctx *c, const tm_image *in, const tm_image *ou
   if ((st = release_staging(c, S, s))) return st;
   int64_t n = 0;
   mark(c, s, -1);
-  launch_range(c->djobs, 1, rb, c->p.n_bins, s);
+  if (run_range) launch_range(c->djobs, 1, rb, c->p.n_bins, s);
   mark(c, s, ST_RANGE);
   launch_prep(c->djobs, 1, pb, c->p.n_bins, c->p.flags, s);
   mark(c, s, ST_PREP);
-  n += 2 + launch_integral_jobs(c->djobs, 1, H, cb, nseg > 1, s);
+  n += (run_range ? 2 : 1) + launch_integral_jobs(c->djobs, 1, H, cb, nseg > 1, s);
   mark(c, s, ST_INTEGRAL);
   uint32_t *cpl = nullptr;
   if (c->p.n_bins > 1) {
@@ -456,6 +492,7 @@ tm_status forward_materialised(tm_ctx *c, const tm_image *in, const tm_image *ou
   c->bins = J.bins;
   c->q = J.q;
   c->dbg = J.dbg;
+  c->last_stats = J.st;
   return TM_OK;
 }
 
@@ -537,6 +574,7 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
     J.in = to_image(&in[i]);
     J.out = to_image(&out[i]);
     J.st = c->stats + i;
+    J.st_next = nullptr;
     J.bins = reinterpret_cast<uint8_t *>(b + L.bins);
     J.q = reinterpret_cast<int32_t *>(b + L.q);
     J.s1 = reinterpret_cast<long long *>(b + L.s1);
@@ -550,6 +588,13 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
       J.dbg.lf = reinterpret_cast<float *>(b + L.dlf);
       J.dbg.l = reinterpret_cast<float *>(b + L.dl);
     }
+  }
+  bool run_range = true;
+  if (c->reuse_range && nimg == 1 && !graph && do_lookup) {
+    bool own = true;
+    if ((st = reuse_states(c, in[0].width, in[0].height, jobs[0].qbits, &jobs[0].st, &jobs[0].st_next, &own)))
+      return st;
+    run_range = own;
   }
   memcpy(S->jobs, jobs.data(), sizeof(Job) * nimg);
   for (int k = 0; k < nitems; ++k) S->items[k] = items[(size_t)k].second;
@@ -571,11 +616,11 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   if (!graph && (st = release_staging(c, S, s))) return st;
   int64_t n = 0;
   if (!graph) mark(c, s, -1);
-  launch_range(dj, nimg, b_range, c->p.n_bins, s);
+  if (run_range) launch_range(dj, nimg, b_range, c->p.n_bins, s);
   if (!graph) mark(c, s, ST_RANGE);
   launch_prep(dj, nimg, b_prep, c->p.n_bins, c->p.flags, s);
   if (!graph) mark(c, s, ST_PREP);
-  n += 2 + launch_integral_jobs(dj, nimg, b_rows, b_cols, multi_seg, s);
+  n += (run_range ? 2 : 1) + launch_integral_jobs(dj, nimg, b_rows, b_cols, multi_seg, s);
   if (!graph) mark(c, s, ST_INTEGRAL);
   const int ls = launch_sweep(P, dj, di, nitems, queue, smem, ctas, s);
   if (!graph) mark(c, s, ST_SWEEP);
@@ -616,6 +661,7 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
     c->bins = jobs[0].bins;
     c->q = jobs[0].q;
     c->dbg = jobs[0].dbg;
+    c->last_stats = jobs[0].st;
   }
   return TM_OK;
 }
@@ -771,7 +817,7 @@ tm_status tm_create(const tm_params *params, tm_ctx **out) {
 
 void tm_destroy(tm_ctx *c) {
   if (!c) return;
-  if (c->ws || c->stats || c->stage || c->djobs || c->gdjobs || c->graph) cudaDeviceSynchronize();
+  if (c->ws || c->stats || c->rr_stats || c->stage || c->djobs || c->gdjobs || c->graph) cudaDeviceSynchronize();
   drop_graph(c);
   for (auto &call : c->marks)
     for (auto &m : call) cudaEventDestroy(m.first);
@@ -779,6 +825,7 @@ void tm_destroy(tm_ctx *c) {
   if (c->ws) cudaFree(c->ws);
   if (c->bws) cudaFree(c->bws);
   if (c->stats) cudaFree(c->stats);
+  if (c->rr_stats) cudaFree(c->rr_stats);
   if (c->stage) cudaFree(c->stage);
   if (c->djobs) cudaFree(c->djobs);
   if (c->ditems) cudaFree(c->ditems);
@@ -1022,8 +1069,8 @@ tm_status tm_debug_export(tm_ctx *c, int32_t what, void *dst, size_t bytes, void
   const void *src = nullptr;
   const size_t N = (size_t)c->last_W * c->last_H;
   switch (what) {
-    case TM_DBG_RANGE: src = &c->stats->imin; break;
-    case TM_DBG_THRESHOLDS: src = c->stats->thr; break;
+    case TM_DBG_RANGE: src = &(c->last_stats ? c->last_stats : c->stats)->imin; break;
+    case TM_DBG_THRESHOLDS: src = (c->last_stats ? c->last_stats : c->stats)->thr; break;
     case TM_DBG_BINS: src = c->bins; break;
     case TM_DBG_Q: src = c->q; break;
     case TM_DBG_QSHIFT: {
@@ -1049,6 +1096,11 @@ tm_status tm_set_option(tm_ctx *c, int32_t key, int64_t value) {
   if (!c) return fail(nullptr, TM_EINVAL, "tm_set_option: ctx is NULL");
   if (key == TM_OPT_STAGE_TIMING) {
     c->stage_timing = value ? 1 : 0;
+    return TM_OK;
+  }
+  if (key == TM_OPT_REUSE_RANGE) {
+    c->reuse_range = value ? 1 : 0;
+    c->rr_valid = 0;
     return TM_OK;
   }
   if (key == TM_OPT_HIST_PATH) {

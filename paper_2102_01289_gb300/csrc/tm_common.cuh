@@ -105,7 +105,8 @@ enum StageId { kStRange = 0, kStPrep, kStRows, kStCols, kStLook, kNumStages };
 // One image of a batch: its buffers and its share of every batched launch.
 struct Job {
   Image in, out;
-  Stats *st;                // range state
+  Stats *st;                // range state the bins and q are taken over
+  Stats *st_next;           // streaming reuse: receives this image's own range (else null)
   uint8_t *bins;            // H*W bin map
   int32_t *q;               // H*W quantised log
   long long *s1, *s2;       // (H+1)*(W+1) integral images of q and q^2

@@ -74,48 +74,14 @@ __device__ __forceinline__ bool vec_ok(const Image &im) {
   return ((uintptr_t)im.p % align) == 0 && ((size_t)im.pitch * es) % align == 0;
 }
 
-// Range of Eq. 11 luminance, per image of the batch. Block min/max are folded
-// with unsigned atomics; the last block of an image computes its bin edges
-// and quantisation constants in double precision, then re-arms the
-// accumulators for the next call, so no host round trip is needed.
-__global__ void __launch_bounds__(256) k_range(const Job *__restrict__ jobs, int njobs, int n_bins) {
-  __shared__ unsigned smin[8], smax[8];
+// Fold a block's luminance range (float bits of its min and max) into *st;
+// the block that arrives last (of nb) computes the bin edges and the
+// quantisation constants in double precision and re-arms the accumulators for
+// the next call, so no host round trip is needed. All threads of the block
+// call this.
+__device__ void commit_range(Stats *st, unsigned bmin, unsigned bmax, int nb, int n_bins, int qbits) {
+  __shared__ unsigned smin[32], smax[32];
   __shared__ int last;
-  const int j = find_job(jobs, njobs, kStRange, blockIdx.x);
-  const Job &J = jobs[j];
-  const int lb = blockIdx.x - J.b0[kStRange];
-  const int nb = (j + 1 < njobs ? jobs[j + 1].b0[kStRange] : (int)gridDim.x) - J.b0[kStRange];
-  const Image in = J.in;
-  const bool vec = vec_ok(in);
-  Stats *st = J.st;
-  unsigned bmin = 0x7f800000u, bmax = 0u;
-  const int W = in.W, H = in.H;
-  const int gpr = (W + 3) >> 2;  // groups of four pixels per row
-  const int ng = gpr * H;        // fewer than 2^31 pixels
-  const int stride = nb * blockDim.x;
-  for (int g0 = lb * blockDim.x + threadIdx.x; g0 < ng; g0 += 2 * stride) {
-    float r[2][4], gg[2][4], b[2][4];
-    int n[2];
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {  // two groups in flight per thread
-      const int g = g0 + u * stride;
-      n[u] = 0;
-      if (g < ng) {
-        const int y = g / gpr, x = (g - y * gpr) * 4;
-        n[u] = min(4, W - x);
-        load4(in, vec, x, y, n[u], r[u], gg[u], b[u]);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < 2; ++u)
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (i < n[u]) {
-          const unsigned v = __float_as_uint(luminance(r[u][i], gg[u][i], b[u][i]));
-          bmin = min(bmin, v);
-          bmax = max(bmax, v);
-        }
-  }
   bmin = __reduce_min_sync(0xffffffffu, bmin);
   bmax = __reduce_max_sync(0xffffffffu, bmax);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -154,8 +120,8 @@ __global__ void __launch_bounds__(256) k_range(const Job *__restrict__ jobs, int
     const double m0 = (double)__uint_as_float((bits & 0x7fffffu) | 0x3f800000u);
     st->c0 = (float)log2(m0);
     st->log2_scale =
-        degenerate ? 0.f : (float)(ldexp(1.0, J.qbits) / (log2((double)imax) - log2((double)imin)));
-    st->lin_scale = (float)(ldexp(1.0, J.qbits) / (double)imax);
+        degenerate ? 0.f : (float)(ldexp(1.0, qbits) / (log2((double)imax) - log2((double)imin)));
+    st->lin_scale = (float)(ldexp(1.0, qbits) / (double)imax);
     st->imin = imin;
     st->imax = imax;
     st->degenerate = degenerate ? 1 : 0;
@@ -163,6 +129,47 @@ __global__ void __launch_bounds__(256) k_range(const Job *__restrict__ jobs, int
     st->max_bits = 0u;
     st->blocks_done = 0u;
   }
+}
+
+// Range of Eq. 11 luminance, per image of the batch: block min/max folded
+// into the image's Stats by commit_range.
+__global__ void __launch_bounds__(256) k_range(const Job *__restrict__ jobs, int njobs, int n_bins) {
+  const int j = find_job(jobs, njobs, kStRange, blockIdx.x);
+  const Job &J = jobs[j];
+  const int lb = blockIdx.x - J.b0[kStRange];
+  const int nb = (j + 1 < njobs ? jobs[j + 1].b0[kStRange] : (int)gridDim.x) - J.b0[kStRange];
+  const Image in = J.in;
+  const bool vec = vec_ok(in);
+  Stats *st = J.st;
+  unsigned bmin = 0x7f800000u, bmax = 0u;
+  const int W = in.W, H = in.H;
+  const int gpr = (W + 3) >> 2;  // groups of four pixels per row
+  const int ng = gpr * H;        // fewer than 2^31 pixels
+  const int stride = nb * blockDim.x;
+  for (int g0 = lb * blockDim.x + threadIdx.x; g0 < ng; g0 += 2 * stride) {
+    float r[2][4], gg[2][4], b[2][4];
+    int n[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {  // two groups in flight per thread
+      const int g = g0 + u * stride;
+      n[u] = 0;
+      if (g < ng) {
+        const int y = g / gpr, x = (g - y * gpr) * 4;
+        n[u] = min(4, W - x);
+        load4(in, vec, x, y, n[u], r[u], gg[u], b[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (i < n[u]) {
+          const unsigned v = __float_as_uint(luminance(r[u][i], gg[u][i], b[u][i]));
+          bmin = min(bmin, v);
+          bmax = max(bmax, v);
+        }
+  }
+  commit_range(st, bmin, bmax, nb, n_bins, J.qbits);
 }
 
 // Bin map (Section II-A, edges from k_range) and the quantised values whose
@@ -191,6 +198,7 @@ __global__ void __launch_bounds__(256) k_prep(const Job *__restrict__ jobs, int 
   int32_t *q = J.q;
   const int gpr = (W + 3) >> 2;
   const int ng = gpr * H;
+  unsigned bmin = 0x7f800000u, bmax = 0u;  // this image's own range (streaming reuse)
   for (int gi = lb * blockDim.x + threadIdx.x; gi < ng; gi += nb * blockDim.x) {
     const int y = gi / gpr, x = (gi - y * gpr) * 4;
     const int n = min(4, W - x);
@@ -203,6 +211,10 @@ __global__ void __launch_bounds__(256) k_prep(const Job *__restrict__ jobs, int 
       const float l = luminance(r[i], g[i], b[i]);
       bq |= (unsigned)bin_of(l, thr, n_bins) << (8 * i);
       qq[i] = lin ? quantise_lin(l, sst, qbits) : quantise_log(l, sst, qbits);
+      if (i < n) {
+        bmin = min(bmin, __float_as_uint(l));
+        bmax = max(bmax, __float_as_uint(l));
+      }
     }
     const long long o = (long long)y * W + x;
     if (n == 4 && (o & 3) == 0) {
@@ -215,6 +227,9 @@ __global__ void __launch_bounds__(256) k_prep(const Job *__restrict__ jobs, int 
       }
     }
   }
+  // streaming reuse: the bins above used an earlier frame's range; this
+  // frame's own range goes to st_next for the frame after
+  if (J.st_next) commit_range(J.st_next, bmin, bmax, nb, n_bins, qbits);
 }
 
 int range_blocks(int W, int H, int num_sms, double share) {

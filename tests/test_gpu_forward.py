@@ -370,3 +370,54 @@ def test_srgb_uint8_output(orc):
     # float outputs are not encoded
     outf, _ = run_gpu(img, gp, debug=False)
     assert_out_close(outf, ref)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_streaming_range_reuse(orc, path):
+    """TM_OPT_REUSE_RANGE: each frame is binned and normalised over the
+    previous frame's range (pixels outside it clamp to the end bins and to
+    lhat 0 / 1), and the bin pass takes the frame's own range for the next
+    one. The first frame, a frame of another size, and any frame after the
+    option is switched off use their own range."""
+    H, W = 90, 120
+    frames = [synth.wdr_image(H, W, seed=50), 3.0 * synth.wdr_image(H, W, seed=51),
+              0.5 * synth.wdr_image(H, W, seed=52)]
+    frames = [f.astype(np.float32) for f in frames]
+    gp, op = params_pair(orc, 32, [2, 8, 30])
+    ranges = [tuple(float(v) for v in (orc.prepare(f, 32)["imin"], orc.prepare(f, 32)["imax"])) for f in frames]
+    ctx = tm.tm_create(gp)
+    try:
+        tm.tm_set_debug(ctx, True)
+        tm.tm_set_option(ctx, tm.TM_OPT_HIST_PATH, path)
+        tm.tm_set_option(ctx, tm.TM_OPT_REUSE_RANGE, 1)
+
+        def fwd(img):
+            x = torch.from_numpy(np.ascontiguousarray(img)).cuda()
+            y = torch.empty_like(x)
+            tm.tm_forward(ctx, x, y)
+            cnt = tm.tm_debug_export(ctx, tm.TM_DBG_COUNTS).cpu().numpy().view(np.uint32)
+            rng = tm.tm_debug_export(ctx, tm.TM_DBG_RANGE).cpu().numpy()
+            torch.cuda.synchronize()
+            return y.cpu().numpy(), cnt.reshape(3, *img.shape[:2]), (float(rng[0]), float(rng[1]))
+
+        used = [None, ranges[0], ranges[1]]
+        for k, img in enumerate(frames):
+            out, cnt, rng = fwd(img)
+            ref, fl = orc.forward(img, op, range_=used[k])
+            assert rng == (used[k] or ranges[0])
+            assert np.array_equal(cnt, fl.cnt)
+            assert_out_close(out, ref)
+        # another size: its own range
+        small = synth.wdr_image(40, 50, seed=53)
+        out, cnt, rng = fwd(small)
+        ref, fl = orc.forward(small, op)
+        assert np.array_equal(cnt, fl.cnt)
+        assert_out_close(out, ref)
+        # option off: own range again
+        tm.tm_set_option(ctx, tm.TM_OPT_REUSE_RANGE, 0)
+        out, cnt, rng = fwd(frames[1])
+        ref, fl = orc.forward(frames[1], op)
+        assert rng == ranges[1]
+        assert_out_close(out, ref)
+    finally:
+        tm.tm_destroy(ctx)
