@@ -116,6 +116,48 @@ def dist_env():
     return rank, world, local
 
 
+# Replicas: every rank tone-maps its own images (the path has no exchange
+# step); the job's time is the slowest rank's, its throughput all ranks' units
+# over that time. These helpers are the whole multi-rank logic.
+def dist_init(backend: str):
+    """Join the process group when launched with WORLD_SIZE > 1."""
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend)
+    return rank, world, local
+
+
+def dist_barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest x over the ranks (every rank gets it)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seed(base: int, rank: int, j: int) -> int:
+    """Seed of image j of `rank`: distinct images on every rank."""
+    return base + rank * 2 + j
+
+
+def job_rate(units_per_rank: float, world: int, steps: int, ms_max: float) -> float:
+    """Whole-job throughput: all ranks' units over the slowest rank's time (units/s / 1e6)."""
+    return world * units_per_rank * steps / (ms_max / 1e3) / 1e6
+
+
 # ------------------------------------------------------------ reference arm --
 def oracle_rate(img, wl, budget_s: float, seed: int = 0):
     """Oracle MP/s on sampled pixels of the workload: the global pre-pass over
@@ -147,7 +189,7 @@ def run_reference(args):
 
     wl = WORKLOAD
     img = synth.wdr_image(wl["H"], wl["W"], seed=wl["seed"], decades=wl["decades"])
-    budget = max(2.0, min(20.0, 60.0 / max(args.steps + args.warmup, 1)))
+    budget = args.ref_seconds or max(2.0, min(20.0, 60.0 / max(args.steps + args.warmup, 1)))
     for _ in range(args.warmup):
         oracle_rate(img, wl, budget / 4)
     rates, pix, secs = [], 0, 0.0
@@ -180,11 +222,7 @@ def run_ours(args):
     import paper_2102_01289_gb300 as tm
     import synth
 
-    rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl")
+    rank, world, local = dist_init("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     tm.build()
@@ -196,7 +234,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     # two resident inputs > L2 each, alternated so no step reuses cached input
-    imgs = [synth.wdr_image(H, W, seed=wl["seed"] + rank * 2 + j, decades=wl["decades"]) for j in range(2)]
+    imgs = [synth.wdr_image(H, W, seed=replica_seed(wl["seed"], rank, j), decades=wl["decades"]) for j in range(2)]
     xin = [torch.from_numpy(a).to(dev) for a in imgs]
     xout = [torch.empty_like(x) for x in xin]
 
@@ -212,8 +250,7 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    if world > 1:
-        dist.barrier()
+    dist_barrier(world)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -221,18 +258,14 @@ def run_ours(args):
         tm.tm_forward(ctx, xin[i % 2], xout[i % 2], stream)
     e1.record(stream)
     torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    dist_barrier(world)
     ms = e0.elapsed_time(e1)
     stages = tm.tm_stage_times(ctx)
     tm.tm_set_option(ctx, tm.TM_OPT_STAGE_TIMING, 0)
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     ms_step = ms / args.steps
-    value = world * npx * args.steps / (ms / 1e3) / 1e6
+    value = job_rate(npx, world, args.steps, ms)
 
     # end to end through the public API with host buffers: pinned host in/out,
     # H2D copy of the input and D2H of the result inside every step
@@ -242,17 +275,12 @@ def run_ours(args):
     for i in range(2):
         tm.tm_forward_host(ctx, hin[i].numpy(), hout[i].numpy(), stream)
     torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    dist_barrier(world)
     t0 = time.perf_counter()
     for i in range(e2e_steps):
         tm.tm_forward_host(ctx, hin[i % 2].numpy(), hout[i % 2].numpy(), stream)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * npx * e2e_steps / e2e_s / 1e6
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e_value = job_rate(npx, world, e2e_steps, e2e_s * 1e3)
 
     peak, peak_kind = load_peaks()
     dominant = max(stages.items(), key=lambda kv: kv[1])[0] if stages else None
@@ -289,6 +317,8 @@ def run_ours(args):
                                           f"direct window loops, {dt:.1f} s"}
     tm.tm_destroy(ctx)
     if world > 1:
+        import torch.distributed as dist
+
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -544,6 +574,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=0.0,
+                    help="oracle sample per step of the reference arm (default: sized so the run takes ~1 min)")
     ap.add_argument("--workload", default="fwd-12mp",
                     choices=["fwd-12mp", "batch-video", "batch-uneven", "fwd-bwd", "paper-preset"])
     args = ap.parse_args()
