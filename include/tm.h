@@ -253,6 +253,13 @@ tm_status tm_debug_export(tm_ctx *ctx, int32_t what, void *dst, size_t bytes,
 /* Tuning options.
  *   TM_OPT_HIST_PATH     0 = automatic (default), 1 = fused sliding sweep,
  *                        2 = materialised bin-major integral histogram.
+ *                        Automatic: the first single-image forward of each
+ *                        (width, height, input dtype, output dtype) on a
+ *                        context runs both paths twice, timing the second
+ *                        runs (it synchronises its stream once), and keeps
+ *                        the faster; later forwards of that size take it
+ *                        directly. Batches and tm_backward take the fused
+ *                        path where it fits.
  *   TM_OPT_STAGE_TIMING  1 = record a CUDA event after every stage of each
  *                        forward/backward call on its stream (see
  *                        tm_stage_times); 0 = off (default).

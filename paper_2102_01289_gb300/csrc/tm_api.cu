@@ -6,7 +6,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <utility>
 #include <vector>
@@ -80,6 +82,8 @@ struct tm_ctx {
   Stats *rr_stats = nullptr;
   int rr_cur = 0, rr_valid = 0, rr_W = 0, rr_H = 0, rr_q = 0;
   const Stats *last_stats = nullptr;  // range state of the last single-image forward
+  // automatic histogram path: the measured choice per (width, height, in dtype, out dtype)
+  std::map<std::tuple<int, int, int, int>, int> path_choice;
   // stage timing: events recorded on the call's stream after each stage
   int stage_timing = 0;
   std::vector<std::vector<std::pair<cudaEvent_t, int>>> marks;
@@ -666,11 +670,59 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   return TM_OK;
 }
 
+// Automatic histogram path: run each path twice on this image and time the
+// second run with events (synchronising the stream); 1 = fused, 2 = materialised.
+tm_status choose_path(tm_ctx *c, const tm_image *in, const tm_image *out, cudaStream_t s, int *choice) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  TM_CUDA(c, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    cudaGetLastError();
+    return fail(c, TM_ECUDA, "cudaEventCreate");
+  }
+  float ms[3] = {0.f, 0.f, 0.f};
+  tm_status st = TM_OK;
+  bool fused_ok = true;
+  for (int path = 1; path <= 2 && !st; ++path) {
+    for (int rep = 0; rep < 2 && !st; ++rep) {
+      cudaEventRecord(e0, s);
+      st = path == 1 ? forward_fused(c, 1, in, out, s, false) : forward_materialised(c, in, out, s);
+      if (path == 1 && st == TM_EUNSUPPORTED) {
+        fused_ok = false;
+        st = TM_OK;
+        break;
+      }
+      cudaEventRecord(e1, s);
+    }
+    if (!st && (path == 2 || fused_ok)) {
+      cudaError_t e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[path], e0, e1);
+      if (e != cudaSuccess) st = cuda_fail(c, e, "timing the histogram paths");
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st) return st;
+  *choice = fused_ok && ms[1] <= ms[2] ? 1 : 2;
+  return TM_OK;
+}
+
 // The forward launch sequence on one image (device buffers already checked).
 tm_status forward_device(tm_ctx *c, const tm_image *in, const tm_image *out, cudaStream_t s) {
   tm_status st = ensure_device_info(c);
   if (st) return st;
-  if (c->p.n_bins > 1 && c->hist_path != 2) {
+  int path = c->hist_path;
+  if (c->p.n_bins < 2) path = 2;  // no thresholds: nothing to sweep
+  if (path == 0) {
+    const auto key = std::make_tuple((int)in->width, (int)in->height, (int)in->dtype, (int)out->dtype);
+    auto it = c->path_choice.find(key);
+    if (it == c->path_choice.end()) {
+      if ((st = choose_path(c, in, out, s, &path))) return st;
+      it = c->path_choice.emplace(key, path).first;
+    }
+    path = it->second;
+  }
+  if (path == 1) {
     st = forward_fused(c, 1, in, out, s, false);
     if (st != TM_EUNSUPPORTED) return st;
     if (c->hist_path == 1)
@@ -1106,6 +1158,7 @@ tm_status tm_set_option(tm_ctx *c, int32_t key, int64_t value) {
   if (key == TM_OPT_HIST_PATH) {
     if (value < 0 || value > 2) return fail(c, TM_EINVAL, "TM_OPT_HIST_PATH value %lld", (long long)value);
     c->hist_path = (int)value;
+    c->path_choice.clear();
     return TM_OK;
   }
   return fail(c, TM_EINVAL, "unknown option %d", key);

@@ -421,3 +421,28 @@ def test_streaming_range_reuse(orc, path):
         assert_out_close(out, ref)
     finally:
         tm.tm_destroy(ctx)
+
+
+@pytest.mark.parametrize("n", [5, 48])
+def test_automatic_path_matches_forced_paths(orc, n):
+    """TM_OPT_HIST_PATH = 0 times both histogram paths on the first image of a
+    size and keeps the faster; every call, first and later, agrees with both
+    forced paths and with the oracle."""
+    img = synth.wdr_image(200, 300, seed=60)
+    gp, op = params_pair(orc, n, [3, 12, 40])
+    ref, _ = orc.forward(img, op)
+    outs = {}
+    for path in (1, 2):
+        outs[path], _ = run_gpu(img, gp, debug=False, path=path)
+    x = torch.from_numpy(img).cuda()
+    ctx = tm.tm_create(gp)
+    try:
+        for _ in range(3):  # the first call measures, the later ones reuse the choice
+            y = torch.empty_like(x)
+            tm.tm_forward(ctx, x, y)
+            torch.cuda.synchronize()
+            got = y.cpu().numpy()
+            assert_out_close(got, ref)
+            assert np.allclose(got, outs[1], rtol=1e-6, atol=1e-7) and np.allclose(got, outs[2], rtol=1e-6, atol=1e-7)
+    finally:
+        tm.tm_destroy(ctx)
