@@ -34,8 +34,6 @@ namespace {
 
 constexpr int kBT = 256;
 constexpr int kWarpsB = kBT / 32;
-// per-thread partials: [ld_min, ld_max, sat, eps[kMaxFields], alpha[kMaxFields]]
-constexpr int kNAcc = 3 + 2 * kMaxFields;
 
 __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -59,32 +57,37 @@ __device__ __forceinline__ int fix_shift(unsigned amax, float nmax) {
 
 // Per pixel: forward recomputation, Eq. 12/3/2/4 adjoints, u_f and v_f,
 // direct gradients of the colour restoration, parameter partial sums and the
-// largest |u_f|, |v_f| (for the fixed-point scales).
+// largest |u_f|, |v_f| (for the fixed-point scales). NF = number of fields
+// (so every per-field array lives in registers).
+template <int NF>
 __global__ void __launch_bounds__(kBT) k_bwd_pixel(DevParams P, Job J, BwdJob B) {
-  __shared__ float sh[kNAcc][kWarpsB];
-  __shared__ unsigned shm[2 * kMaxFields][kWarpsB];
+  constexpr int kA = 3 + 2 * NF;  // [ld_min, ld_max, sat, eps[NF], alpha[NF]], the layout of BwdAcc::g
+  __shared__ float sh[kA][kWarpsB];
+  __shared__ unsigned shm[2 * NF][kWarpsB];
   const int W = J.in.W, H = J.in.H;
   const long long N = (long long)W * H;
   const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int s = P.n_fields;
-  float acc[kNAcc];
-  unsigned amax[2 * kMaxFields];
+  float acc[kA];
+  unsigned amax[2 * NF];
 #pragma unroll
-  for (int k = 0; k < kNAcc; ++k) acc[k] = 0.f;
+  for (int k = 0; k < kA; ++k) acc[k] = 0.f;
 #pragma unroll
-  for (int k = 0; k < 2 * kMaxFields; ++k) amax[k] = 0u;
+  for (int k = 0; k < 2 * NF; ++k) amax[k] = 0u;
   if (pix < N) {
     const int y = (int)(pix / W), x = (int)(pix - (long long)y * W);
     const SweepPlan &S = J.plan;
     const float inv_scale = ldexpf(1.f, -J.qbits);
     const float inv_scale2 = inv_scale * inv_scale;
-    unsigned cnt[kMaxFields];
-    slab_counts(S, J.counts, N, pix, y, H, cnt);
     const long long W1 = (long long)W + 1;
-    float rarea[kMaxFields], var[kMaxFields], mu[kMaxFields];
+    float Pf[NF], rarea[NF], var[NF], mu[NF], wv[NF], lf[NF];
+    float wsum = 0.f, accL = 0.f, meanL = 0.f;
 #pragma unroll
-    for (int f = 0; f < kMaxFields; ++f) {
-      if (f >= s) break;
+    for (int f = 0; f < NF; ++f) {
+      unsigned cnt = 0u;
+      for (int sl = S.field_slab0[f]; sl < S.field_slab0[f + 1]; ++sl) {
+        const int T = max(y + S.slab_a[sl] - 1, -1), Bb = min(y + S.slab_b[sl], H - 1);
+        if (Bb > T) cnt += J.counts[sl * N + pix];
+      }
       Win w = window_of(P, f, x, y, W, H);
       const long long iA = (long long)w.y0 * W1 + w.x0, iB = (long long)w.y0 * W1 + w.x1 + 1;
       const long long iC = (long long)(w.y1 + 1) * W1 + w.x1 + 1, iD = (long long)(w.y1 + 1) * W1 + w.x0;
@@ -97,13 +100,15 @@ __global__ void __launch_bounds__(kBT) k_bwd_pixel(DevParams P, Job J, BwdJob B)
       rarea[f] = __frcp_rn((float)Nw);
       var[f] = window_variance(q1, q2, Nw, rarea[f], inv_scale2);
       mu[f] = (float)q1 * rarea[f] * inv_scale + 0.5f;  // mean of lhat
+      // Eq. 1, 2, 4 and the sums of Eq. 3, as in the forward
+      Pf[f] = (float)cnt * rarea[f];
+      lf[f] = fmaf(P.ld_max - P.ld_min, Pf[f], P.ld_min);
+      wv[f] = __fdividef(P.alpha[f] * var[f], var[f] + P.eps[f]);
+      wsum += wv[f];
+      accL = fmaf(wv[f], lf[f], accL);
+      meanL += lf[f];
     }
-    float wv[kMaxFields], lf[kMaxFields];
-    const float L = fuse_fields(P, cnt, rarea, var, wv, lf);
-    float wsum = 0.f;
-#pragma unroll
-    for (int f = 0; f < kMaxFields; ++f)
-      if (f < s) wsum += wv[f];
+    const float L = wsum > 0.f ? __fdividef(accL, wsum) : __fdividef(meanL, (float)NF);
     // Eq. 12
     float rgb[3];
     load_rgb(J.in, x, y, rgb[0], rgb[1], rgb[2]);
@@ -131,25 +136,23 @@ __global__ void __launch_bounds__(kBT) k_bwd_pixel(DevParams P, Job J, BwdJob B)
     // Eq. 3, 2, 4
     const float rws = wsum > 0.f ? 1.f / wsum : 0.f;
 #pragma unroll
-    for (int f = 0; f < kMaxFields; ++f) {
-      if (f >= s) break;
-      const float Pf = (float)cnt[f] * rarea[f];
-      const float dLdLf = wsum > 0.f ? wv[f] * rws : 1.f / (float)s;
+    for (int f = 0; f < NF; ++f) {
+      const float dLdLf = wsum > 0.f ? wv[f] * rws : 1.f / (float)NF;
       const float dLdW = (lf[f] - L) * rws;
-      acc[0] += gL * dLdLf * (1.f - Pf);
-      acc[1] += gL * dLdLf * Pf;
+      acc[0] += gL * dLdLf * (1.f - Pf[f]);
+      acc[1] += gL * dLdLf * Pf[f];
       const float gW = gL * dLdW;
       const float v = var[f], e = P.eps[f], a = P.alpha[f];
       const float den = (v + e) * (v + e);
       acc[3 + f] += gW * (-a * v / den);
-      acc[3 + kMaxFields + f] += gW * (v / (v + e));
+      acc[3 + NF + f] += gW * (v / (v + e));
       const float gv = gW * a * e / den;
       const float u = 2.f * gv * rarea[f];
       const float vv = u * mu[f];
       B.U[f * N + pix] = u;
       B.V[f * N + pix] = vv;
       amax[f] = max(amax[f], __float_as_uint(fabsf(u)));
-      amax[kMaxFields + f] = max(amax[kMaxFields + f], __float_as_uint(fabsf(vv)));
+      amax[NF + f] = max(amax[NF + f], __float_as_uint(fabsf(vv)));
     }
     B.gi_direct[pix] = gi_direct;
     float *gin = static_cast<float *>(B.grad_in.p) + (long long)y * B.grad_in.pitch + 3LL * x;
@@ -165,34 +168,26 @@ __global__ void __launch_bounds__(kBT) k_bwd_pixel(DevParams P, Job J, BwdJob B)
   // block sums of the parameter partials and block maxima of |u|, |v|
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-  for (int k = 0; k < kNAcc; ++k) {
-    const int f = k < 3 + kMaxFields ? k - 3 : k - 3 - kMaxFields;
-    if (k >= 3 && f >= s) continue;
+  for (int k = 0; k < kA; ++k) {
     const float t = warp_sum(acc[k]);
     if (lane == 0) sh[k][wid] = t;
   }
 #pragma unroll
-  for (int k = 0; k < 2 * kMaxFields; ++k) {
-    if ((k & (kMaxFields - 1)) >= s) continue;
+  for (int k = 0; k < 2 * NF; ++k) {
     const unsigned t = __reduce_max_sync(0xffffffffu, amax[k]);
     if (lane == 0) shm[k][wid] = t;
   }
   __syncthreads();
   const int t = threadIdx.x;
-  if (t < kNAcc) {
-    const int f = t < 3 + kMaxFields ? t - 3 : t - 3 - kMaxFields;
-    if (t < 3 || f < s) {
-      float sum = 0.f;
-      for (int w = 0; w < kWarpsB; ++w) sum += sh[t][w];
-      atomicAdd(&B.acc->g[t < 3 + kMaxFields ? t : 3 + s + f], (double)sum);
-    }
-  } else if (t >= 32 && t < 32 + 2 * kMaxFields) {
+  if (t < kA) {
+    float sum = 0.f;
+    for (int w = 0; w < kWarpsB; ++w) sum += sh[t][w];
+    atomicAdd(&B.acc->g[t], (double)sum);
+  } else if (t >= 32 && t < 32 + 2 * NF) {
     const int k = t - 32;
-    if ((k & (kMaxFields - 1)) < s) {
-      unsigned m = 0u;
-      for (int w = 0; w < kWarpsB; ++w) m = max(m, shm[k][w]);
-      if (m) atomicMax(&B.acc->amax[k], m);
-    }
+    unsigned m = 0u;
+    for (int w = 0; w < kWarpsB; ++w) m = max(m, shm[k][w]);
+    if (m) atomicMax(&B.acc->amax[k < NF ? k : kMaxFields + (k - NF)], m);
   }
 }
 
@@ -241,12 +236,12 @@ __global__ void __launch_bounds__(kBT) k_rows_fix(DevParams P, const float *__re
 
 // Per pixel: the adjoint of the window variances, through the normalised log,
 // into the luminance and Eq. 11; range-term partial sums.
+template <int NF>
 __global__ void __launch_bounds__(kBT) k_bwd_input(DevParams P, Job J, BwdJob B) {
   __shared__ float sh[2][kWarpsB];
   const int W = J.in.W, H = J.in.H;
   const long long N = (long long)W * H;
   const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int s = P.n_fields;
   // D = ln imax - ln imin = ln 2 x 2^Q / log2_scale (log2_scale = 2^Q / log2(imax / imin))
   const float l2s = J.st->log2_scale;
   const float D = J.st->imax > J.st->imin && l2s > 0.f ? 0.69314718f * ldexpf(1.f, J.qbits) / l2s : 0.f;
@@ -262,8 +257,7 @@ __global__ void __launch_bounds__(kBT) k_bwd_input(DevParams P, Job J, BwdJob B)
       const float lh = (float)J.q[pix] * ldexpf(1.f, -J.qbits) + 0.5f;
       float gl = 0.f;
 #pragma unroll
-      for (int f = 0; f < kMaxFields; ++f) {
-        if (f >= s) break;
+      for (int f = 0; f < NF; ++f) {
         Win w = window_of(P, f, x, y, W, H);
         const long long iA = (long long)w.y0 * W1 + w.x0, iB = (long long)w.y0 * W1 + w.x1 + 1;
         const long long iC = (long long)(w.y1 + 1) * W1 + w.x1 + 1, iD = (long long)(w.y1 + 1) * W1 + w.x0;
@@ -333,7 +327,12 @@ __global__ void k_bwd_finish(DevParams P, Job J, BwdJob B) {
 int launch_backward(const DevParams &P, const Job &J, const BwdJob &B, cudaStream_t s) {
   const long long N = (long long)J.in.W * J.in.H;
   const int blocks = (int)((N + kBT - 1) / kBT);
-  k_bwd_pixel<<<blocks, kBT, 0, s>>>(P, J, B);
+  switch (P.n_fields) {
+#define TM_BWD_PIXEL(nf) case nf: k_bwd_pixel<nf><<<blocks, kBT, 0, s>>>(P, J, B); break;
+    TM_BWD_PIXEL(1) TM_BWD_PIXEL(2) TM_BWD_PIXEL(3) TM_BWD_PIXEL(4) TM_BWD_PIXEL(5) TM_BWD_PIXEL(6)
+    TM_BWD_PIXEL(7) default: k_bwd_pixel<8><<<blocks, kBT, 0, s>>>(P, J, B); break;
+#undef TM_BWD_PIXEL
+  }
   const int W = J.in.W, H = J.in.H;
   const long long plane = ((long long)W + 1) * ((long long)H + 1);
   // U and V integral planes are contiguous: one row pass and one segmented
@@ -341,7 +340,12 @@ int launch_backward(const DevParams &P, const Job &J, const BwdJob &B, cudaStrea
   dim3 rg(H, 2 * P.n_fields);
   k_rows_fix<<<rg, kBT, 0, s>>>(P, B.U, B.V, W, H, B.acc, B.IU);
   const int nc = launch_column_pass_u64(B.IU, plane, 2 * P.n_fields, W, H, B.colscr, s);
-  k_bwd_input<<<blocks, kBT, 0, s>>>(P, J, B);
+  switch (P.n_fields) {
+#define TM_BWD_INPUT(nf) case nf: k_bwd_input<nf><<<blocks, kBT, 0, s>>>(P, J, B); break;
+    TM_BWD_INPUT(1) TM_BWD_INPUT(2) TM_BWD_INPUT(3) TM_BWD_INPUT(4) TM_BWD_INPUT(5) TM_BWD_INPUT(6)
+    TM_BWD_INPUT(7) default: k_bwd_input<8><<<blocks, kBT, 0, s>>>(P, J, B); break;
+#undef TM_BWD_INPUT
+  }
   k_bwd_finish<<<1, 32, 0, s>>>(P, J, B);
   return 4 + nc;
 }

@@ -77,6 +77,7 @@ __device__ __forceinline__ void finish_pixel(const Image &in, const Image &out, 
   if (dbg.l) dbg.l[(long long)y * in.W + x] = L;
 }
 
+template <int NF>
 __global__ void __launch_bounds__(256)
     k_lookup_materialised(Image in, Image out, DevParams P, const uint8_t *__restrict__ bins,
                           const unsigned *__restrict__ cplanes, const long long *__restrict__ s1,
@@ -93,7 +94,8 @@ __global__ void __launch_bounds__(256)
   const unsigned *C = t > 0 && t < P.n_bins ? cplanes + (long long)(t - 1) * plane : nullptr;
   const float inv_scale2 = ldexpf(1.f, -2 * P.qbits);
   Fusion fu;
-  for (int f = 0; f < P.n_fields; ++f) {
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
     unsigned cnt = 0u;
     Win w = window_of(P, f, x, y, W, H);
     if (C)
@@ -141,9 +143,15 @@ int launch_lookup_materialised(const Image &in, const Image &out, const DevParam
                                const uint8_t *bins, const uint32_t *cplanes, const int64_t *s1,
                                const int64_t *s2, const DebugPlanes &dbg, cudaStream_t s) {
   dim3 block(32, 8), grid((in.W + 31) / 32, (in.H + 7) / 8);
-  k_lookup_materialised<<<grid, block, 0, s>>>(in, out, P, bins, cplanes,
-                                               reinterpret_cast<const long long *>(s1),
-                                               reinterpret_cast<const long long *>(s2), dbg);
+  const long long *S1 = reinterpret_cast<const long long *>(s1), *S2 = reinterpret_cast<const long long *>(s2);
+  switch (P.n_fields) {
+#define TM_LOOKUP_MAT(nf) \
+  case nf: k_lookup_materialised<nf><<<grid, block, 0, s>>>(in, out, P, bins, cplanes, S1, S2, dbg); break;
+    TM_LOOKUP_MAT(1) TM_LOOKUP_MAT(2) TM_LOOKUP_MAT(3) TM_LOOKUP_MAT(4) TM_LOOKUP_MAT(5) TM_LOOKUP_MAT(6)
+    TM_LOOKUP_MAT(7)
+    default: k_lookup_materialised<8><<<grid, block, 0, s>>>(in, out, P, bins, cplanes, S1, S2, dbg); break;
+#undef TM_LOOKUP_MAT
+  }
   return 1;
 }
 
