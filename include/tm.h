@@ -141,8 +141,11 @@ const char *tm_status_string(tm_status s);
  *   in   device image, dtype TM_F32 or TM_F16.
  *   out  device image of the same width/height, dtype TM_F32, TM_F16 or TM_U8;
  *        must not overlap in.
- * Asynchronous on `stream`. The context's workspace is reused, so calls on one
- * context must be ordered (same stream, or synchronised). */
+ * Asynchronous on `stream`, except that with the automatic histogram path
+ * (TM_OPT_HIST_PATH = 0, the default) the first call for an image size and
+ * dtype pair times both paths and synchronises `stream` once. The context's
+ * workspace is reused, so calls on one context must be ordered (same stream,
+ * or synchronised). */
 tm_status tm_forward(tm_ctx *ctx, const tm_image *in, const tm_image *out,
                      void *stream);
 
@@ -155,9 +158,15 @@ tm_status tm_forward(tm_ctx *ctx, const tm_image *in, const tm_image *out,
 tm_status tm_forward_host(tm_ctx *ctx, const tm_image *in_host,
                           const tm_image *out_host, void *stream);
 
-/* Forward over n images of possibly different sizes in one persistent launch
- * over a shared tile queue. in[i], out[i] as for tm_forward (host arrays of
- * descriptors; the pixel data is on the device). n == 0 is a no-op. */
+/* Forward over n images of possibly different sizes: one launch per stage for
+ * the whole batch, the fused sweep as one persistent launch over a shared
+ * queue of (image, tile) items. in[i], out[i] as for tm_forward (host arrays
+ * of descriptors; the pixel data is on the device). n == 0 is a no-op. The
+ * launch sequence is captured in a CUDA graph and replayed while the same
+ * descriptors (pointers, sizes, pitches, dtypes) are passed; a replay reads
+ * the current pixel contents. If the fused sweep does not fit the fields, the
+ * images are processed one by one as by tm_forward. Results are bit-identical
+ * to per-image tm_forward calls on the fused path. */
 tm_status tm_forward_batch(tm_ctx *ctx, int32_t n, const tm_image *in,
                            const tm_image *out, void *stream);
 
