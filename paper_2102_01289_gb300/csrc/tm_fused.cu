@@ -104,7 +104,6 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const SweepPlan &
   const int Y0 = ty * S.TY, Y1 = min(Y0 + S.TY, H);
   if (X0 >= W || Y0 >= H) return;
   const int TXc = X1 - X0;
-  const float invTX = 1.f / (float)TXc;
   const int cL = max(X0 - S.Rx - 1, -1), cR = min(X1 - 1 + S.Rx, W - 1);
   const int text = cR - cL + 1;  // columns cL..cR; index 0 is the origin
   const int ncol = text - 1;     // swept columns 1..text-1
@@ -393,20 +392,23 @@ bool plan_sweep(const DevParams &P, int W, int H, int num_sms, size_t smem_limit
   base.H = H;
   base.Rx = min(Rx, W);
   base.Ry = min(Ry, H);
-  // slabs: split a field's rows evenly so that every slab holds < 2^16 pixels
+  // slabs: split a field's rows evenly so that every slab holds < 2^16 pixels.
+  // Row offsets beyond +-(H-1) never reach a row of the image, so a half-height
+  // is clipped to H-1 first: the clipped window of every pixel is unchanged.
   int ns = 0;
   for (int f = 0; f < P.n_fields; ++f) {
     const long long wx = min(2LL * P.rx[f] + 1, (long long)W);
-    const long long rows = 2LL * P.ry[f] + 1;
+    const long long ry = min((long long)P.ry[f], (long long)H - 1);
+    const long long rows = 2 * ry + 1;
     const long long cap = 65535LL / wx;
     if (cap < 1) return false;
     const long long pieces = (rows + cap - 1) / cap;
     const long long hs = (rows + pieces - 1) / pieces;
-    for (long long a = -P.ry[f]; a <= P.ry[f]; a += hs) {
+    for (long long a = -ry; a <= ry; a += hs) {
       if (ns >= kMaxSlabs) return false;
       base.slab_field[ns] = f;
       base.slab_a[ns] = (int)a;
-      base.slab_b[ns] = (int)min(a + hs - 1, (long long)P.ry[f]);
+      base.slab_b[ns] = (int)min(a + hs - 1, ry);
       ++ns;
     }
   }

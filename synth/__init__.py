@@ -21,7 +21,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["wdr_image", "wdr_video_frame", "uneven_sizes", "box_image"]
+__all__ = ["wdr_image", "wdr_mosaic", "wdr_video_frame", "uneven_sizes", "box_image"]
 
 
 def _draw_scene(rng: np.random.Generator, H: int, W: int, n_rects: int):
@@ -69,6 +69,23 @@ def wdr_image(H: int, W: int, seed: int, decades=(-2.0, 4.0), n_rects: int = 20,
     rng = np.random.default_rng(seed)
     theta, rects, bg = _draw_scene(rng, H, W, n_rects)
     return _render(H, W, decades[0], decades[1], theta, rects, bg, rng, noise, dtype=dtype)
+
+
+def wdr_mosaic(H: int, W: int, seed: int, tile=(3072, 4096), dtype=np.float32) -> np.ndarray:
+    """A large (H, W, 3) image without a full-size float64 render: one
+    ``tile``-sized scene (``wdr_image``) repeated over the frame, each copy
+    flipped by its grid position and scaled by 10^U(-1, 1) of its own, so the
+    copies differ in range and orientation. Memory stays near 2x the output."""
+    th, tw = min(tile[0], H), min(tile[1], W)
+    base = wdr_image(th, tw, seed=seed, dtype=dtype)
+    rng = np.random.default_rng(seed + 1)
+    out = np.empty((H, W, 3), dtype)
+    for i, y0 in enumerate(range(0, H, th)):
+        for j, x0 in enumerate(range(0, W, tw)):
+            t = base[:: (-1 if i % 2 else 1), :: (-1 if j % 2 else 1)]
+            h, w = min(th, H - y0), min(tw, W - x0)
+            np.multiply(t[:h, :w], dtype(10.0 ** rng.uniform(-1.0, 1.0)), out=out[y0:y0 + h, x0:x0 + w])
+    return out
 
 
 def wdr_video_frame(H: int, W: int, seed: int, frame: int, decades=(-2.0, 4.0),

@@ -51,6 +51,7 @@ CASES = [
     (40, 56, 16, [2, 7, 30]),
     (33, 47, 32, [(3, 1), 9]),
     (64, 64, 8, [4, 16, 64]),  # last window larger than the image
+    (37, 53, 16, [0, 1, 3, (7, 2), 12, 25, (32767, 4), 32767]),  # 8 fields up to the largest radius
 ]
 
 
@@ -60,7 +61,8 @@ def test_backward_matches_oracle_adjoint(orc, H, W, n, radii, flags):
     rng = np.random.default_rng(H + W)
     img = synth.wdr_image(H, W, seed=H * 7 + W)
     s = len(radii)
-    gp, op = _pair(orc, n, radii, eps=[0.1, 0.03, 0.2][:s], alpha=[1.0, 0.8, 1.2][:s], flags=flags)
+    gp, op = _pair(orc, n, radii, eps=[(0.1, 0.03, 0.2)[f % 3] for f in range(s)],
+                   alpha=[(1.0, 0.8, 1.2)[f % 3] for f in range(s)], flags=flags)
     gout = rng.standard_normal(img.shape)
     gin, gpar = _gpu_backward(img, gp, gout)
     ref_in, ref_p = orc.backward(img.astype(np.float64), op, gout, lum_f64=False)

@@ -446,3 +446,95 @@ def test_automatic_path_matches_forced_paths(orc, n):
             assert np.allclose(got, outs[1], rtol=1e-6, atol=1e-7) and np.allclose(got, outs[2], rtol=1e-6, atol=1e-7)
     finally:
         tm.tm_destroy(ctx)
+
+
+MAX_FIELDS_RADII = [0, 1, 3, (7, 2), 15, (40, 0), (32767, 5), 32767]
+MAX_FIELDS_EPS = [0.1, 0.05, 0.2, 0.08, 0.3, 0.1, 0.02, 0.15]
+MAX_FIELDS_ALPHA = [1.0, 0.7, 1.3, 0.9, 1.1, 0.5, 1.0, 0.8]
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("flags", [0, tm.TM_FLAG_CDF_INCLUSIVE | tm.TM_FLAG_AREA_LITERAL])
+def test_eight_fields_and_maximum_radius(orc, flags, path):
+    """TM_MAX_FIELDS fields with half-sizes from 0 to TM_MAX_RADIUS: the last
+    two windows span the image in one or both directions (the sweep clips
+    their row slabs to the image); under Algorithm 1's area the largest window
+    is 65535 x 65535 pixels, an Eq. 1 denominator just under 2^32. Counts
+    bit-exact, variances within the quantisation bound, outputs within the
+    float tolerance, on a 70 x 90 and a 37 x 300 image."""
+    for H, W, seed in [(70, 90, 70), (37, 300, 71)]:
+        img = synth.wdr_image(H, W, seed=seed)
+        gp, op = params_pair(orc, 16, MAX_FIELDS_RADII, eps=MAX_FIELDS_EPS, alpha=MAX_FIELDS_ALPHA,
+                             ld_min=0.02, ld_max=0.98, flags=flags)
+        out, d = run_gpu(img, gp, path=path)
+        ref, fl = orc.forward(img, op)
+        assert np.array_equal(d["cnt"], fl.cnt)
+        assert np.all(np.abs(d["sigma2"] - fl.sigma2) <= _sigma2_tol(fl.sigma2, d["qbits"]))
+        assert np.allclose(d["lf"], fl.lf, rtol=1e-6, atol=1e-7)
+        assert_out_close(d["l"], fl.l)
+        assert_out_close(out, ref)
+
+
+def _mem_available_gb():
+    try:
+        with open("/proc/meminfo") as fh:
+            for line in fh:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) / 2 ** 20
+    except OSError:
+        pass
+    return 0.0
+
+
+LARGE_RADII = [(150, 150), (140, 150), (150, 120), 130, (110, 150), (150, 110), 145, (120, 140)]
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_large_image_64bit_offsets_sampled(orc, path):
+    """16384 x 12288 (201 MP) with 8 fields whose windows each hold more than
+    2^16 pixels: two row slabs per field, 16 slab count planes, element
+    offsets past 2^31 on the fused path; 16 bins, 15 cumulative planes of
+    805 MB on the materialised one. Range, bin edges and bin map exact;
+    counts, variances and outputs at sampled pixels (corners, edges, tile
+    seams, random) against the oracle's direct per-pixel evaluation."""
+    H, W = 12288, 16384
+    if _mem_available_gb() < 24 or torch.cuda.mem_get_info()[0] < 80 * 2 ** 30:
+        pytest.skip("needs 24 GB of host and 80 GB of device memory")
+    img = synth.wdr_mosaic(H, W, seed=80)
+    gp, op = params_pair(orc, 16, LARGE_RADII, eps=MAX_FIELDS_EPS, alpha=MAX_FIELDS_ALPHA)
+    rng = np.random.default_rng(81)
+    ys = np.concatenate([[0, 0, H - 1, H - 1, 3071, 3072, 6143, 6144, 150, H - 151],
+                         rng.integers(0, H, 110)])
+    xs = np.concatenate([[0, W - 1, 0, W - 1, 4095, 4096, 8191, 8192, W - 151, 150],
+                         rng.integers(0, W, 110)])
+    x = torch.from_numpy(img).cuda()
+    y = torch.empty_like(x)
+    yi, xi = torch.from_numpy(ys).cuda(), torch.from_numpy(xs).cuda()
+    ctx = tm.tm_create(gp)
+    try:
+        tm.tm_set_debug(ctx, True)
+        tm.tm_set_option(ctx, tm.TM_OPT_HIST_PATH, path)
+        tm.tm_forward(ctx, x, y)
+        rng_dev = tm.tm_debug_export(ctx, tm.TM_DBG_RANGE).cpu().numpy()
+        thr = tm.tm_debug_export(ctx, tm.TM_DBG_THRESHOLDS).cpu().numpy()
+        bins = tm.tm_debug_export(ctx, tm.TM_DBG_BINS).view(H, W).cpu().numpy()
+        qbits = int(tm.tm_debug_export(ctx, tm.TM_DBG_QSHIFT).cpu().numpy()[0])
+        sampled = {}
+        for key, what in (("cnt", tm.TM_DBG_COUNTS), ("sigma2", tm.TM_DBG_SIGMA2)):
+            plane = tm.tm_debug_export(ctx, what).view(gp.n_fields, H, W)
+            sampled[key] = plane[:, yi, xi].T.cpu().numpy()
+            del plane
+        out = y[yi, xi].cpu().numpy()
+        torch.cuda.synchronize()
+    finally:
+        tm.tm_destroy(ctx)
+    del x, y
+    pre = orc.prepare(img, 16)
+    assert rng_dev[0] == pre["imin"] and rng_dev[1] == pre["imax"]
+    assert np.array_equal(thr, pre["thr"])
+    assert np.array_equal(bins, pre["bins"])
+    del pre, bins
+    ref, dd = orc.forward_pixels(img, op, xs, ys)
+    assert np.array_equal(sampled["cnt"].view(np.uint32), dd["cnt"])
+    assert np.all(np.abs(sampled["sigma2"] - dd["sigma2"]) <= _sigma2_tol(dd["sigma2"], qbits))
+    assert_out_close(out, ref)
