@@ -42,13 +42,14 @@ constexpr int kTaskMax = 4;  // corner-event tasks per thread (planner: events x
 
 __device__ __forceinline__ unsigned thr_inc(int b, int klo) {
   // thresholds klo (low half) and klo + 1 (high half): [b < k] each
-  return (b < klo ? 1u : 0u) + (b <= klo ? 0x10000u : 0u);
+  return b < klo ? 0x10001u : (b == klo ? 0x10000u : 0u);
 }
 
-// Two independent 16-bit lanes added modulo 2^16 each (no carry between them).
-__device__ __forceinline__ unsigned add16x2(unsigned a, unsigned b) {
-  const unsigned m = 0x7fff7fffu;
-  return ((a & m) + (b & m)) ^ ((a ^ b) & 0x80008000u);
+// a + b + c in two independent 16-bit lanes, each modulo 2^16, when both
+// halves of b + c are below 2^15: with a's top bits set aside no carry leaves
+// a lane, and xor puts the top bits back.
+__device__ __forceinline__ unsigned add16x2_small(unsigned a, unsigned b, unsigned c) {
+  return ((a & 0x7fff7fffu) + b + c) ^ (a & 0x80008000u);
 }
 
 // Position of swept column i (i >= 1) in a 17-word-per-segment row.
@@ -146,6 +147,7 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const SweepPlan &
   // corners: thresholds kmin+1 .. kmax + incl, two per word
   const int incl = (P.flags & kFlagCdfIncl) ? 1 : 0;
   const int nw = (kmax + incl - kmin + 1) >> 1;
+  const int koff = kmin + 1 - incl;  // corner events read threshold b(p) + incl, stored at index k - kmin - 1
 
   for (int t = tid; t < nw * S.cstride; t += kNT) sm.D[t] = 0u;
   for (int t = tid; t < nw; t += kNT) sm.m[t] = 0u;
@@ -199,15 +201,16 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const SweepPlan &
   }
   __syncthreads();
 
+  const int pRy = S.Ry, pBR = S.BR, pTX = S.TX, pCs = S.cstride;
   for (int v = rL; v <= rR; ++v) {
     const bool burst = (v < 0) || (v == H - 1);
     if (v > rL) {
       // ---- row v into shared memory; fetch row v+1 for the next step ----
       uint8_t *bw = reinterpret_cast<uint8_t *>(sm.brow);
       if (tid < nseg * kSeg) bw[tid + 4 * (tid >> 4)] = tid < ncol ? (uint8_t)pb : (uint8_t)255;
-      const int yn = v + S.Ry + 1;
-      if (yn >= Y0 && yn < Y1 && tid < TXc) sm.bring[yn_slot * S.TX + tid] = (uint8_t)pn;
-      yn_slot = yn_slot + 1 == S.BR ? 0 : yn_slot + 1;
+      const int yn = v + pRy + 1;
+      if (yn >= Y0 && yn < Y1 && tid < TXc) sm.bring[yn_slot * pTX + tid] = (uint8_t)pn;
+      yn_slot = yn_slot + 1 == pBR ? 0 : yn_slot + 1;
       if (v + 1 <= rR) {
         if (tid < ncol) pb = __ldg(bins + (long long)(v + 1) * W + cL + 1 + tid);
         if (yn + 1 >= Y0 && yn + 1 < Y1 && tid < TXc) pn = __ldg(bins + (long long)(yn + 1) * W + X0 + tid);
@@ -219,13 +222,13 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const SweepPlan &
       if (tid < ne) {
         ++ev_y;
         ev_slot = ev_slot + 1 == ev_rlen ? 0 : ev_slot + 1;
-        ev_bslot = ev_bslot + 1 == S.BR ? 0 : ev_bslot + 1;
+        ev_bslot = ev_bslot + 1 == pBR ? 0 : ev_bslot + 1;
         if (!burst) {
           const int T = max(ev_y + ev_a - 1, -1), B = min(ev_y + ev_b, H - 1);
           const bool valid = ev_y >= Y0 && ev_y < Y1 && B > T;
-          evt[tid][0] = valid ? ev_y : -1;
-          evt[tid][1] = (ev_roff + ev_slot) * S.TX;
-          evt[tid][2] = ev_bslot * S.TX;
+          evt[tid][0] = valid ? ev_y * W : -1;  // row offset of the pixel
+          evt[tid][1] = (ev_roff + ev_slot) * pTX;
+          evt[tid][2] = ev_bslot * pTX;
           evt[tid][3] = ev_rx;
         }
       }
@@ -235,7 +238,7 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const SweepPlan &
       // ---- dense words: one warp per word, one lane per segment ----
       for (int j = j0 + wid; j < j1; j += kWarps) {
         const int klo = kmin + 1 + 2 * j;
-        unsigned inc[kSeg];
+        unsigned loc[kSeg];  // running increments within the lane's segment
         unsigned tot = 0;
         if (lane < nseg) {
           const unsigned *bp = sm.brow + lane * 5;
@@ -244,8 +247,8 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const SweepPlan &
             const unsigned w4 = bp[q];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-              inc[q * 4 + e] = thr_inc((int)((w4 >> (8 * e)) & 0xffu), klo);
-              tot += inc[q * 4 + e];
+              tot += thr_inc((int)__byte_perm(w4, 0u, 0x4440u + e), klo);
+              loc[q * 4 + e] = tot;
             }
           }
         }
@@ -256,13 +259,11 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const SweepPlan &
           if (lane >= o) pre += yv;
         }
         if (lane < nseg) {
-          unsigned run = pre - tot;  // lanes stay below 2^15: one row of columns
-          unsigned *row = sm.D + j * S.cstride + 1 + lane * 17;
+          const unsigned base = pre - tot;  // lanes stay below 2^15: one row of columns
+          unsigned *row = sm.D + j * pCs + 1 + lane * 17;
 #pragma unroll
-          for (int c = 0; c < kSeg; ++c) {
-            run += inc[c];
-            row[c] = add16x2(row[c], run);  // columns past the edge are never read
-          }
+          for (int c = 0; c < kSeg; ++c)
+            row[c] = add16x2_small(row[c], loc[c], base);  // columns past the edge are never read
         }
       }
       __syncthreads();
@@ -271,9 +272,9 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const SweepPlan &
       if (tid < ne) {
         const int T = max(ev_y + ev_a - 1, -1), B = min(ev_y + ev_b, H - 1);
         const bool valid = ev_y >= Y0 && ev_y < Y1 && B > T;
-        evt[tid][0] = valid ? ev_y : -1;
-        evt[tid][1] = (ev_roff + ev_slot) * S.TX;
-        evt[tid][2] = ev_bslot * S.TX;
+        evt[tid][0] = valid ? ev_y * W : -1;  // row offset of the pixel
+        evt[tid][1] = (ev_roff + ev_slot) * pTX;
+        evt[tid][2] = ev_bslot * pTX;
         evt[tid][3] = ev_rx;
       }
       __syncthreads();
@@ -286,23 +287,21 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const SweepPlan &
       for (int i = 0; i < kTaskMax; ++i) {
         if (tk_ex[i] < 0) continue;
         const int e = tk_ex[i] >> 16, xo = tk_ex[i] & 0xffff;
-        const int4 ev = evt[e];  // pixel row, ring offset, bin-ring offset
+        const int4 ev = evt[e];  // pixel row offset, ring offset, bin-ring offset
         if (ev.x < 0) continue;
-        const int b = sm.bring[ev.z + xo] + incl;
+        const int kk = (int)sm.bring[ev.z + xo] - koff;  // threshold index of b(p) (+1 if inclusive)
         unsigned g = 0;
-        if (b > kmin) {
-          const int kk = b - kmin - 1;
+        if (kk >= 0) {
           const int j = kk >> 1, sh = (kk & 1) << 4;
-          const unsigned *row = sm.D + j * S.cstride;
-          const unsigned mk = (sm.m[j] >> sh) & 0xffffu;
+          const unsigned *row = sm.D + j * pCs;
+          const unsigned mk = sm.m[j] >> sh;  // bits above the lane drop out in the final mask
           const unsigned dr = row[tk_pos[i] & 0xffff], dl = row[tk_pos[i] >> 16];
-          g = ((dr >> sh) - (dl >> sh) + (unsigned)tk_coef[i] * mk) & 0xffffu;
+          g = (dr >> sh) - (dl >> sh) + (unsigned)tk_coef[i] * mk;
         }
         uint16_t *ac = sm.acc + ev.y + xo;
         if (!(e & 1)) *ac = (uint16_t)g;
         else
-          counts[(long long)(e >> 1) * N + (long long)ev.x * W + X0 + xo] =
-              (uint16_t)((g - (unsigned)*ac) & 0xffffu);
+          counts[(long long)(e >> 1) * N + (unsigned)(ev.x + X0 + xo)] = (uint16_t)(g - (unsigned)*ac);
       }
     } else {
       for (int pass = 0; pass < 2; ++pass) {  // tops, then bottoms
@@ -326,18 +325,18 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const SweepPlan &
             const int y = ylo + yy, xo = t - yy * TXc, x = X0 + xo;
             const int T = max(y + a - 1, -1), B = min(y + bb, H - 1);
             if (B <= T) continue;  // empty slab: counted as 0 by the lookup
-            const int b = sm.bring[(y % S.BR) * S.TX + xo] + incl;
+            const int b = sm.bring[(y % pBR) * pTX + xo] + incl;
             unsigned g = 0;
             if (b > kmin) {
               const int kk = b - kmin - 1;
               const int j = kk >> 1, sh = (kk & 1) << 4;
               const int ir = min(x + rx, W - 1) - cL, il = max(x - rx - 1, -1) - cL;
-              const unsigned *row = sm.D + j * S.cstride;
+              const unsigned *row = sm.D + j * pCs;
               const unsigned mk = (sm.m[j] >> sh) & 0xffffu;
               const unsigned dr = ir > 0 ? row[dpos(ir)] : 0u, dl = il > 0 ? row[dpos(il)] : 0u;
               g = ((dr >> sh) - (dl >> sh) + (unsigned)(ir - il) * mk) & 0xffffu;
             }
-            uint16_t *ac = sm.acc + (size_t)(S.ring_off[s] + y % S.ring_len[s]) * S.TX + xo;
+            uint16_t *ac = sm.acc + (size_t)(S.ring_off[s] + y % S.ring_len[s]) * pTX + xo;
             if (pass == 0) *ac = (uint16_t)g;
             else counts[(long long)s * N + (long long)y * W + x] = (uint16_t)((g - (unsigned)*ac) & 0xffffu);
           }
