@@ -20,11 +20,10 @@
 using namespace tmk;
 
 namespace {
-// Pinned host staging of one call's job array and sweep queue.
+// Pinned host staging of one call's job array.
 struct Staging {
   Job *jobs = nullptr;
-  int2 *items = nullptr;
-  size_t jobs_bytes = 0, items_bytes = 0;
+  size_t jobs_bytes = 0;
   cudaEvent_t done = nullptr;  // recorded after the last copy out of this slot
   bool pending = false;
 };
@@ -44,8 +43,8 @@ struct tm_ctx {
   size_t ws_bytes = 0;
   Stats *stats = nullptr;  // one per image of the largest batch so far
   int stats_n = 0;
-  // job descriptors and sweep queue: pinned host staging copied to device
-  // buffers at the start of each call. The device buffers are stream-ordered
+  // job descriptors: pinned host staging copied to a device buffer at the
+  // start of each call (the sweep queue is written on the device). The device buffers are stream-ordered
   // like the workspace; the host staging is not (the copy runs when the
   // stream reaches it), so calls rotate over several staging slots and wait,
   // before rewriting a slot, for the event recorded after its last copy.
@@ -54,11 +53,11 @@ struct tm_ctx {
   Staging slots[kStagingSlots];
   int slot_next = 0;
   Job *djobs = nullptr;    // device copy of the job array (calls outside the graph)
-  int2 *ditems = nullptr;  // device copy of the sweep queue
+  int4 *ditems = nullptr;  // sweep queue: items and the pop counter
   size_t djobs_bytes = 0, ditems_bytes = 0;
   Staging gstage;          // staging read by the cached graph
   Job *gdjobs = nullptr;   // device buffers written by the cached graph
-  int2 *gditems = nullptr;
+  int4 *gditems = nullptr;
   size_t gdjobs_bytes = 0, gditems_bytes = 0;
   // backward workspace
   void *bws = nullptr;
@@ -152,10 +151,10 @@ tm_status validate_params(const tm_params *p, std::string &why) {
 }
 
 enum Stage { ST_RANGE, ST_PREP, ST_INTEGRAL, ST_HIST, ST_LOOKUP, ST_SWEEP, ST_BATCH,
-             ST_BWD_PIXEL, ST_BWD_ADJOINT, ST_BWD_INPUT, ST_COUNT };
+             ST_BWD_PIXEL, ST_BWD_ADJOINT, ST_BWD_INPUT, ST_PLAN, ST_COUNT };
 const char *const kStageNames[ST_COUNT] = {"range", "prep", "integral_image", "integral_histogram",
                                           "lookup", "fused_sweep", "batch", "bwd_pixel",
-                                          "bwd_adjoint", "bwd_input"};
+                                          "bwd_adjoint", "bwd_input", "sweep_plan"};
 
 // Record a stage boundary on stream s (stage < 0 opens a new call).
 void mark(tm_ctx *c, cudaStream_t s, int stage) {
@@ -336,15 +335,13 @@ tm_status grow_host(tm_ctx *c, void **p, size_t *have, size_t bytes) {
   return TM_OK;
 }
 
-// A staging slot able to hold `njobs` jobs and `nitems` queue items, free to
-// be rewritten: waits for the copies that last read it.
-tm_status acquire_staging(tm_ctx *c, Staging *S, int njobs, int nitems) {
+// A staging slot able to hold `njobs` jobs, free to be rewritten: waits for
+// the copy that last read it.
+tm_status acquire_staging(tm_ctx *c, Staging *S, int njobs) {
   if (!S->done) TM_CUDA(c, cudaEventCreateWithFlags(&S->done, cudaEventDisableTiming));
   if (S->pending) TM_CUDA(c, cudaEventSynchronize(S->done));
   S->pending = false;
-  tm_status st;
-  if ((st = grow_host(c, (void **)&S->jobs, &S->jobs_bytes, sizeof(Job) * std::max(njobs, 1)))) return st;
-  return grow_host(c, (void **)&S->items, &S->items_bytes, sizeof(int2) * std::max(nitems, 1));
+  return grow_host(c, (void **)&S->jobs, &S->jobs_bytes, sizeof(Job) * std::max(njobs, 1));
 }
 
 Staging *next_slot(tm_ctx *c) {
@@ -387,10 +384,14 @@ bool same_images(const std::vector<tm_image> &a, const tm_image *b, int n) {
 
 // Per-image sizes of the forward workspace.
 struct JobLayout {
-  size_t bins, q, s1, s2, segtot, counts, dcnt, dvar, dw, dlf, dl, total;
+  size_t bins, q, s1, s2, segtot, counts, lohi, bcost, dcnt, dvar, dw, dlf, dl, total;
 };
 
-JobLayout job_layout(const tm_params &p, int W, int H, int nseg, size_t count_elems, bool debug) {
+// Workspace of one image. count_elems, lohi_elems, bcost_elems: the sweep's
+// slab counts, per strip and row bin ranges and per strip block costs (0 on
+// the materialised path).
+JobLayout job_layout(const tm_params &p, int W, int H, int nseg, size_t count_elems, bool debug,
+                     size_t lohi_elems = 0, size_t bcost_elems = 0) {
   JobLayout L{};
   const size_t N = (size_t)W * H;
   const size_t plane = (size_t)(W + 1) * (H + 1);
@@ -403,6 +404,8 @@ JobLayout job_layout(const tm_params &p, int W, int H, int nseg, size_t count_el
   L.s2 = take(8 * plane);
   L.segtot = take(8 * 2 * (size_t)nseg * (W + 1));
   L.counts = take(2 * count_elems);
+  L.lohi = take(2 * lohi_elems);
+  L.bcost = take(4 * bcost_elems);
   if (debug) {
     L.dcnt = take(4 * N * s);
     L.dvar = take(4 * N * s);
@@ -436,7 +439,7 @@ tm_status forward_materialised(tm_ctx *c, const tm_image *in, const tm_image *ou
   if ((st = grow_device(c, &c->ws, &c->ws_bytes, total))) return st;
   if ((st = grow_device(c, (void **)&c->djobs, &c->djobs_bytes, sizeof(Job)))) return st;
   Staging *S = next_slot(c);
-  if ((st = acquire_staging(c, S, 1, 0))) return st;
+  if ((st = acquire_staging(c, S, 1))) return st;
   char *ws = static_cast<char *>(c->ws);
   Job J{};
   J.in = to_image(in);
@@ -501,8 +504,8 @@ tm_status forward_materialised(tm_ctx *c, const tm_image *in, const tm_image *ou
 }
 
 // The fused path over a batch of images: one launch per stage for the whole
-// batch, the sweep as a persistent kernel over a queue of (image, tile)
-// items. `graph`: capture the batch into a CUDA graph and replay it while the
+// batch, the sweep as a persistent kernel over a queue of (image, strip, rows)
+// items that the device plans from the bin map. `graph`: capture the batch into a CUDA graph and replay it while the
 // batch is unchanged. Returns TM_EUNSUPPORTED if some image cannot be swept.
 tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image *out, cudaStream_t s,
                         bool graph, bool do_lookup = true, std::vector<Job> *jobs_out = nullptr) {
@@ -521,9 +524,9 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   std::vector<size_t> offs((size_t)nimg);
   size_t ws_total = 0, smem = 0;
   const size_t smem_limit = c->smem_optin - 2048;
-  int b_range = 0, b_prep = 0, b_rows = 0, b_cols = 0, b_look = 0;
+  int b_range = 0, b_prep = 0, b_rows = 0, b_cols = 0, b_look = 0, b_scan = 0;
   bool multi_seg = false;
-  std::vector<std::pair<double, int2>> items;
+  std::vector<std::pair<double, int>> order;  // (cost of a uniform tile, image)
   for (int i = 0; i < nimg; ++i) {
     const int W = in[i].width, H = in[i].height;
     const double share = nimg == 1 ? 1.0 : std::max(1.0 / c->num_sms, W * (double)H / total_px);
@@ -536,7 +539,9 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
     smem = std::max(smem, J.plan.smem);
     column_segments(W, H, 2, J.nseg, J.seg_rows);
     multi_seg = multi_seg || J.nseg > 1;
-    lays[(size_t)i] = job_layout(c->p, W, H, J.nseg, sweep_count_elems(J.plan), debug);
+    sweep_cost_blocks(J.plan, J.rb, J.nb, J.adaptive);
+    lays[(size_t)i] = job_layout(c->p, W, H, J.nseg, sweep_count_elems(J.plan), debug,
+                                 (size_t)J.plan.tiles_x * H, (size_t)J.plan.tiles_x * J.nb);
     offs[(size_t)i] = ws_total;
     ws_total += lays[(size_t)i].total;
     J.b0[kStRange] = b_range;
@@ -549,27 +554,34 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
     b_cols += col_blocks(W, J.nseg);
     J.b0[kStLook] = b_look;
     b_look += lookup_blocks(W, H);
-    const int ntiles = J.plan.tiles_x * J.plan.tiles_y;
+    J.b0[kStScan] = b_scan;
+    b_scan += strip_scan_blocks(J.plan, J.nb);
+    J.nitem = J.plan.tiles_x * J.plan.tiles_y;
     const double rows = std::min(J.plan.TY + 2.0 * J.plan.Ry + 1, H + 1.0);
     const double cols = std::min(J.plan.TX + 2.0 * J.plan.Rx + 2, W + 1.0);
-    for (int t = 0; t < ntiles; ++t) items.push_back({rows * (cols * 0.25 + 300.0), make_int2(i, t)});
+    order.push_back({rows * (cols * 0.25 + 300.0), i});
   }
-  // longest items first
-  std::stable_sort(items.begin(), items.end(),
-                   [](const std::pair<double, int2> &a, const std::pair<double, int2> &b) { return a.first > b.first; });
-  const int nitems = (int)items.size();
+  // the queue holds each image's tiles together, images with the longest
+  // uniform tiles first (the device balances the tiles within an image)
+  std::stable_sort(order.begin(), order.end(),
+                   [](const std::pair<double, int> &a, const std::pair<double, int> &b) { return a.first > b.first; });
+  int nitems = 0;
+  for (const auto &o : order) {
+    jobs[(size_t)o.second].item0 = nitems;
+    nitems += jobs[(size_t)o.second].nitem;
+  }
   if ((st = ensure_stats(c, nimg))) return st;
   if ((st = grow_device(c, &c->ws, &c->ws_bytes, ws_total))) return st;
   if (graph) drop_graph(c);  // re-captured below
   Job **djobs = graph ? &c->gdjobs : &c->djobs;
-  int2 **ditems = graph ? &c->gditems : &c->ditems;
+  int4 **ditems = graph ? &c->gditems : &c->ditems;
   if ((st = grow_device(c, (void **)djobs, graph ? &c->gdjobs_bytes : &c->djobs_bytes, sizeof(Job) * nimg)))
     return st;
   if ((st = grow_device(c, (void **)ditems, graph ? &c->gditems_bytes : &c->ditems_bytes,
-                        sizeof(int2) * nitems + sizeof(int))))
+                        sizeof(int4) * nitems + sizeof(int))))
     return st;
   Staging *S = graph ? &c->gstage : next_slot(c);
-  if ((st = acquire_staging(c, S, nimg, nitems))) return st;
+  if ((st = acquire_staging(c, S, nimg))) return st;
   char *ws = static_cast<char *>(c->ws);
   for (int i = 0; i < nimg; ++i) {
     Job &J = jobs[(size_t)i];
@@ -585,6 +597,8 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
     J.s2 = reinterpret_cast<long long *>(b + L.s2);
     J.segtot = reinterpret_cast<long long *>(b + L.segtot);
     J.counts = reinterpret_cast<uint16_t *>(b + L.counts);
+    J.lohi = reinterpret_cast<uint16_t *>(b + L.lohi);
+    J.bcost = reinterpret_cast<int *>(b + L.bcost);
     if (debug) {
       J.dbg.cnt = reinterpret_cast<unsigned *>(b + L.dcnt);
       J.dbg.sigma2 = reinterpret_cast<float *>(b + L.dvar);
@@ -601,10 +615,9 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
     run_range = own;
   }
   memcpy(S->jobs, jobs.data(), sizeof(Job) * nimg);
-  for (int k = 0; k < nitems; ++k) S->items[k] = items[(size_t)k].second;
   const DevParams P = dev_params(c->p, jobs[0].qbits);  // qbits is per job
   Job *dj = *djobs;
-  int2 *di = *ditems;
+  int4 *di = *ditems;
   int *queue = reinterpret_cast<int *>(di + nitems);
   const int ctas = std::min(nitems, c->num_sms);
   // a batch is captured on the context's own stream (capture is not allowed on
@@ -616,7 +629,6 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
     TM_CUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   }
   cudaMemcpyAsync(dj, S->jobs, sizeof(Job) * nimg, cudaMemcpyHostToDevice, s);
-  cudaMemcpyAsync(di, S->items, sizeof(int2) * nitems, cudaMemcpyHostToDevice, s);
   if (!graph && (st = release_staging(c, S, s))) return st;
   int64_t n = 0;
   if (!graph) mark(c, s, -1);
@@ -626,6 +638,8 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   if (!graph) mark(c, s, ST_PREP);
   n += (run_range ? 2 : 1) + launch_integral_jobs(dj, nimg, b_rows, b_cols, multi_seg, s);
   if (!graph) mark(c, s, ST_INTEGRAL);
+  n += launch_sweep_plan(dj, nimg, b_scan, di, s);  // brings the bin map into L2 for the sweep
+  if (!graph) mark(c, s, ST_PLAN);
   const int ls = launch_sweep(P, dj, di, nitems, queue, smem, ctas, s);
   if (!graph) mark(c, s, ST_SWEEP);
   if (do_lookup) {
@@ -886,7 +900,6 @@ void tm_destroy(tm_ctx *c) {
   if (c->gditems) cudaFree(c->gditems);
   auto free_staging = [](Staging &S) {
     if (S.jobs) cudaFreeHost(S.jobs);
-    if (S.items) cudaFreeHost(S.items);
     if (S.done) cudaEventDestroy(S.done);
   };
   free_staging(c->gstage);

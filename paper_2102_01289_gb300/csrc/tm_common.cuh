@@ -91,7 +91,7 @@ struct SweepPlan {
   int bmax;                       // largest slab_b
   int BR;                         // rows of the tile's own bin ring
   int nseg_max;                   // 16-column segments of the widest swept row (<= 32)
-  int rows_max;                   // rows of the widest swept band
+  int rows_max;                   // rows of the tallest swept band of a uniform tile
   int nw_max;                     // threshold words (two thresholds each) allocated
   int text_max;                   // widest tile row including both side bands
   int cstride;                    // words per threshold row in shared memory (odd)
@@ -100,7 +100,7 @@ struct SweepPlan {
 
 // Batched stages; every stage kernel of a batch maps its blocks to images
 // through the per-image first-block offsets b0[stage].
-enum StageId { kStRange = 0, kStPrep, kStRows, kStCols, kStLook, kNumStages };
+enum StageId { kStRange = 0, kStPrep, kStRows, kStCols, kStLook, kStScan, kNumStages };
 
 // One image of a batch: its buffers and its share of every batched launch.
 struct Job {
@@ -112,10 +112,16 @@ struct Job {
   long long *s1, *s2;       // (H+1)*(W+1) integral images of q and q^2
   long long *segtot;        // 2*nseg*(W+1) column-pass segment sums
   uint16_t *counts;         // nslabs*H*W slab counts from the sweep
+  uint16_t *lohi;           // tiles_x*H: per strip and row, smallest | largest << 8 bin
+                            //   over the strip's swept columns
+  int *bcost;               // tiles_x*nb: per strip, summed row costs of each block of rb rows
   DebugPlanes dbg;
   int qbits;
   int nseg, seg_rows;       // column-pass segmentation
   int b0[kNumStages];       // first block of this job in each batched stage
+  int rb, nb;               // rows per cost block, blocks per strip
+  int adaptive;             // 1: tile heights from the row costs; 0: the plan's uniform TY
+  int item0, nitem;         // this job's slots in the sweep queue
   SweepPlan plan;           // sweep tiling of this image
 };
 

@@ -44,7 +44,15 @@ int launch_integral_histogram(const uint8_t *bins, int W, int H, int n_bins, boo
 // (job, tile) items sorted longest first.
 bool plan_sweep(const DevParams &P, int W, int H, int num_sms, size_t smem_limit, SweepPlan &S);
 size_t sweep_count_elems(const SweepPlan &S);
-int launch_sweep(const DevParams &P, const Job *jobs, const int2 *items, int nitems, int *queue,
+// Row blocking of the per-strip cost scan and whether the adaptive tiling
+// applies to this plan (its prefix sums fit the planner's shared memory).
+void sweep_cost_blocks(const SweepPlan &S, int &rb, int &nb, int &adaptive);
+int strip_scan_blocks(const SweepPlan &S, int nb);
+// Per strip and row bin ranges and per block row costs of every job, then one
+// CTA per job writing its sweep items (job, strip, Y0, Y1) into
+// items[J.item0 .. J.item0 + J.nitem) (job = -1 for unused slots).
+int launch_sweep_plan(const Job *jobs, int njobs, int scan_blocks, int4 *items, cudaStream_t s);
+int launch_sweep(const DevParams &P, const Job *jobs, const int4 *items, int nitems, int *queue,
                  size_t smem, int ctas, cudaStream_t s);
 
 // Stage a4: per-pixel lookup, tone curve, fusion and colour restoration.
