@@ -35,15 +35,6 @@ WORKLOAD = dict(name="wdr-12mp-fwd", H=3000, W=4000, n_bins=64, radii=[8, 32, 12
 # Algorithmic HBM bytes per pixel (float32 RGB): the path must read the input
 # twice (the global range precedes binning) and write the output once.
 PATH_BYTES_PER_PX = 36
-# Compulsory bytes per pixel of the kernels that can dominate a step.
-KERNEL_BYTES_PER_PX = {
-    "fused_sweep": 12 + 12 + 1 + 4,      # RGB in, RGB out, bin map, q
-    "lookup": 12 + 12 + 1,               # RGB in, RGB out, bin map
-    "integral_histogram": 1,             # bin map in (planes are not algorithmic)
-    "integral_image": 4,                 # q in
-    "prep": 12 + 1 + 4,                  # RGB in, bin map + q out
-    "range": 12,                         # RGB in
-}
 
 
 def load_peaks():
@@ -231,6 +222,7 @@ def run_ours(args):
     npx = H * W
     params = tm.make_params(wl["n_bins"], wl["radii"], eps=0.1, sat=0.6)
     ctx = tm.tm_create(params)
+    tm.tm_set_option(ctx, tm.TM_OPT_HIST_PATH, HIST_PATHS[args.hist_path])
     stream = torch.cuda.current_stream(dev)
 
     # two resident inputs > L2 each, alternated so no step reuses cached input
@@ -285,7 +277,9 @@ def run_ours(args):
     peak, peak_kind = load_peaks()
     dominant = max(stages.items(), key=lambda kv: kv[1])[0] if stages else None
     dom_ms = stages.get(dominant, 0.0) / args.steps if dominant else 0.0
-    bpp = KERNEL_BYTES_PER_PX.get(dominant, PATH_BYTES_PER_PX)
+    # the roofline of the dominant kernel takes the path's algorithmic bytes per
+    # pixel times the pixels one launch processes, over that kernel's mean time
+    bpp = PATH_BYTES_PER_PX
     achieved = bpp * npx / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else None
     traffic = load_traffic(dominant)
     line = {
@@ -368,6 +362,7 @@ def run_batch_workload(args, kind):
     xs = [torch.from_numpy(f).to(dev) for f in frames]
     ys = [torch.empty_like(x) for x in xs]
     ctx = tm.tm_create(params)
+    tm.tm_set_option(ctx, tm.TM_OPT_HIST_PATH, HIST_PATHS[args.hist_path])
     stream = torch.cuda.current_stream(dev)
     clocks = ClockSampler(local)
     for _ in range(args.warmup):
@@ -377,14 +372,13 @@ def run_batch_workload(args, kind):
     time.sleep(0.3)
     ms_batch = _timed(lambda i: tm.tm_forward_batch(ctx, xs, ys, stream), args.steps, stream)
     clk = clocks.stop()
-    # per-image forward on the same images
-    for x, y in zip(xs[:4], ys[:4]):
-        tm.tm_forward(ctx, x, y, stream)
-
+    # per-image forward on the same images, after one untimed pass over all of
+    # them (the first forward of each image size measures both histogram paths)
     def per_image(i):
         for x, y in zip(xs, ys):
             tm.tm_forward(ctx, x, y, stream)
 
+    per_image(0)
     ms_single = _timed(per_image, max(1, args.steps // 2), stream)
     ms_reuse = None
     if kind == "batch-video":  # streaming variant: each frame binned over the previous frame's range
@@ -438,6 +432,7 @@ def run_fwd_bwd(args):
     params = tm.make_params(32, [8, 32, 128])
     gp = torch.empty(3 + 2 * 3, device=dev)
     ctx = tm.tm_create(params)
+    tm.tm_set_option(ctx, tm.TM_OPT_HIST_PATH, HIST_PATHS[args.hist_path])
     stream = torch.cuda.current_stream(dev)
 
     def batched(i):
@@ -503,6 +498,7 @@ def run_paper_preset(args):
     ys = [torch.empty_like(x) for x in xs]
     params = tm.tm_params_pyramid(W, H, 5, 5)
     ctx = tm.tm_create(params)
+    tm.tm_set_option(ctx, tm.TM_OPT_HIST_PATH, HIST_PATHS[args.hist_path])
     stream = torch.cuda.current_stream(dev)
     for i in range(args.warmup):
         tm.tm_forward(ctx, xs[i % 2], ys[i % 2], stream)
@@ -552,6 +548,9 @@ def load_traffic(kernel):
     return e.get("bytes_per_launch")
 
 
+HIST_PATHS = {"auto": 0, "fused": 1, "materialised": 2}
+
+
 def kernel_source_hash(kernel):
     import hashlib
 
@@ -574,6 +573,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--hist-path", choices=sorted(HIST_PATHS), default="auto",
+                    help="histogram path: auto (the library measures both once), fused or materialised")
     ap.add_argument("--ref-seconds", type=float, default=0.0,
                     help="oracle sample per step of the reference arm (default: sized so the run takes ~1 min)")
     ap.add_argument("--workload", default="fwd-12mp",
