@@ -208,9 +208,10 @@ tm_status tm_integral_image(const int32_t *q, int32_t width, int32_t height,
  * callbacks where re-entering the CUDA allocator is not allowed, and
  * processes that reserved all device memory up front. Same arguments, layout
  * and results as tm_integral_image; the scratch it needs (a 256-byte-aligned
- * job descriptor plus 16 * nseg * (width + 1) bytes of column-pass sums, nseg
- * <= 64 segments of rows) lives in a static device array of 8 MiB that every
- * GPU loading this library keeps until the process exits.
+ * job descriptor plus the tile sums: 16 bytes per column and row segment,
+ * with row segments of 16 rows, doubled while the scratch would not fit, and
+ * 16 bytes per row and 1024-column chunk) lives in a static device array of
+ * 8 MiB that every GPU loading this library keeps until the process exits.
  *   - The first call on a device looks the array's address up for that
  *     device (with it current); make that first call before any stream
  *     capture.

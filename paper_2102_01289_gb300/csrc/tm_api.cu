@@ -13,6 +13,8 @@
 #include <utility>
 #include <vector>
 
+#include <cstdint>
+
 #include "tm.h"
 #include "tm_backward.cuh"
 #include "tm_kernels.cuh"
@@ -392,6 +394,7 @@ struct JobLayout {
 // the materialised path).
 JobLayout job_layout(const tm_params &p, int W, int H, int nseg, size_t count_elems, bool debug,
                      size_t lohi_elems = 0, size_t bcost_elems = 0) {
+  // nseg: row segments of the integral images (integral_layout)
   JobLayout L{};
   const size_t N = (size_t)W * H;
   const size_t plane = (size_t)(W + 1) * (H + 1);
@@ -402,7 +405,7 @@ JobLayout job_layout(const tm_params &p, int W, int H, int nseg, size_t count_el
   L.q = take(4 * N);
   L.s1 = take(8 * plane);
   L.s2 = take(8 * plane);
-  L.segtot = take(8 * 2 * (size_t)nseg * (W + 1));
+  L.segtot = take(8 * integral_scratch_elems(W, H, nseg));
   L.counts = take(2 * count_elems);
   L.lohi = take(2 * lohi_elems);
   L.bcost = take(4 * bcost_elems);
@@ -425,7 +428,7 @@ tm_status forward_materialised(tm_ctx *c, const tm_image *in, const tm_image *ou
   const int qbits = choose_qbits(c->p, W, H);
   DevParams P = dev_params(c->p, qbits);
   int nseg, seg_rows;
-  column_segments(W, H, 2, nseg, seg_rows);
+  integral_layout(W, H, SIZE_MAX, nseg, seg_rows);
   JobLayout L = job_layout(c->p, W, H, nseg, 0, c->debug != 0);
   const size_t plane = (size_t)(W + 1) * (H + 1);
   size_t off_cpl = align256(L.total), off_hscr = 0, total = off_cpl;
@@ -467,7 +470,6 @@ tm_status forward_materialised(tm_ctx *c, const tm_image *in, const tm_image *ou
     J.dbg.l = reinterpret_cast<float *>(ws + L.dl);
   }
   const int rb = range_blocks(W, H, c->num_sms, 1.0), pb = prep_blocks(W, H, c->num_sms, 1.0);
-  const int cb = col_blocks(W, nseg);
   J.b0[kStRange] = J.b0[kStPrep] = J.b0[kStRows] = J.b0[kStCols] = J.b0[kStLook] = 0;
   *S->jobs = J;
   TM_CUDA(c, cudaMemcpyAsync(c->djobs, S->jobs, sizeof(Job), cudaMemcpyHostToDevice, s));
@@ -478,7 +480,8 @@ tm_status forward_materialised(tm_ctx *c, const tm_image *in, const tm_image *ou
   mark(c, s, ST_RANGE);
   launch_prep(c->djobs, 1, pb, c->p.n_bins, c->p.flags, s);
   mark(c, s, ST_PREP);
-  n += (run_range ? 2 : 1) + launch_integral_jobs(c->djobs, 1, H, cb, nseg > 1, s);
+  n += (run_range ? 2 : 1) +
+       launch_integral_jobs(c->djobs, 1, integral_tile_blocks(W, nseg), integral_col_blocks(W), s);
   mark(c, s, ST_INTEGRAL);
   uint32_t *cpl = nullptr;
   if (c->p.n_bins > 1) {
@@ -525,7 +528,6 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   size_t ws_total = 0, smem = 0;
   const size_t smem_limit = c->smem_optin - 2048;
   int b_range = 0, b_prep = 0, b_rows = 0, b_cols = 0, b_look = 0, b_scan = 0;
-  bool multi_seg = false;
   std::vector<std::pair<double, int>> order;  // (cost of a uniform tile, image)
   for (int i = 0; i < nimg; ++i) {
     const int W = in[i].width, H = in[i].height;
@@ -537,8 +539,7 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
     const int sms_share = std::max(1, (int)std::lround(c->num_sms * share));
     if (!plan_sweep(P, W, H, sms_share, smem_limit, J.plan)) return TM_EUNSUPPORTED;
     smem = std::max(smem, J.plan.smem);
-    column_segments(W, H, 2, J.nseg, J.seg_rows);
-    multi_seg = multi_seg || J.nseg > 1;
+    integral_layout(W, H, SIZE_MAX, J.nseg, J.seg_rows);
     sweep_cost_blocks(J.plan, J.rb, J.nb, J.adaptive);
     lays[(size_t)i] = job_layout(c->p, W, H, J.nseg, sweep_count_elems(J.plan), debug,
                                  (size_t)J.plan.tiles_x * H, (size_t)J.plan.tiles_x * J.nb);
@@ -549,9 +550,9 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
     J.b0[kStPrep] = b_prep;
     b_prep += prep_blocks(W, H, c->num_sms, share);
     J.b0[kStRows] = b_rows;
-    b_rows += H;
+    b_rows += integral_tile_blocks(W, J.nseg);
     J.b0[kStCols] = b_cols;
-    b_cols += col_blocks(W, J.nseg);
+    b_cols += integral_col_blocks(W);
     J.b0[kStLook] = b_look;
     b_look += lookup_blocks(W, H);
     J.b0[kStScan] = b_scan;
@@ -636,7 +637,7 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   if (!graph) mark(c, s, ST_RANGE);
   launch_prep(dj, nimg, b_prep, c->p.n_bins, c->p.flags, s);
   if (!graph) mark(c, s, ST_PREP);
-  n += (run_range ? 2 : 1) + launch_integral_jobs(dj, nimg, b_rows, b_cols, multi_seg, s);
+  n += (run_range ? 2 : 1) + launch_integral_jobs(dj, nimg, b_rows, b_cols, s);
   if (!graph) mark(c, s, ST_INTEGRAL);
   n += launch_sweep_plan(dj, nimg, b_scan, di, s);  // brings the bin map into L2 for the sweep
   if (!graph) mark(c, s, ST_PLAN);
@@ -1066,15 +1067,16 @@ tm_status tm_integral_image(const int32_t *q, int32_t width, int32_t height, int
   J.q = const_cast<int32_t *>(q);
   J.s1 = reinterpret_cast<long long *>(s1);
   J.s2 = reinterpret_cast<long long *>(s2);
-  column_segments(width, height, 2, J.nseg, J.seg_rows);
-  const size_t seg_bytes = 8 * 2 * (size_t)J.nseg * (width + 1);
+  integral_layout(width, height, SIZE_MAX, J.nseg, J.seg_rows);
+  const size_t seg_bytes = 8 * integral_scratch_elems(width, height, J.nseg);
   void *scr = nullptr;
   cudaError_t e = cudaMallocAsync(&scr, align256(sizeof(Job)) + seg_bytes, st);
   if (e != cudaSuccess) { cudaGetLastError(); return fail(nullptr, TM_ENOMEM, "tm_integral_image: scratch"); }
   J.segtot = reinterpret_cast<long long *>(static_cast<char *>(scr) + align256(sizeof(Job)));
   e = cudaMemcpyAsync(scr, &J, sizeof(Job), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) {
-    launch_integral_jobs(static_cast<Job *>(scr), 1, height, col_blocks(width, J.nseg), J.nseg > 1, st);
+    launch_integral_jobs(static_cast<Job *>(scr), 1, integral_tile_blocks(width, J.nseg),
+                         integral_col_blocks(width), st);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // J lives on this stack frame
   }

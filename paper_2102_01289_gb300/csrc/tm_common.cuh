@@ -110,14 +110,14 @@ struct Job {
   uint8_t *bins;            // H*W bin map
   int32_t *q;               // H*W quantised log
   long long *s1, *s2;       // (H+1)*(W+1) integral images of q and q^2
-  long long *segtot;        // 2*nseg*(W+1) column-pass segment sums
+  long long *segtot;        // integral-image scratch, integral_scratch_elems(W, H, nseg)
   uint16_t *counts;         // nslabs*H*W slab counts from the sweep
   uint16_t *lohi;           // tiles_x*H: per strip and row, smallest | largest << 8 bin
                             //   over the strip's swept columns
   int *bcost;               // tiles_x*nb: per strip, summed row costs of each block of rb rows
   DebugPlanes dbg;
   int qbits;
-  int nseg, seg_rows;       // column-pass segmentation
+  int nseg, seg_rows;       // integral images: row segments of the tiles
   int b0[kNumStages];       // first block of this job in each batched stage
   int rb, nb;               // rows per cost block, blocks per strip
   int adaptive;             // 1: tile heights from the row costs; 0: the plan's uniform TY

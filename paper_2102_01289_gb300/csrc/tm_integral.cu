@@ -1,12 +1,23 @@
 // tm_integral.cu -- integral images (Eq. 5) and integral histograms (Eq. 7-8).
 //
-// Both are two-pass: a row pass (block-wide scans, warp shuffles inside each
-// warp) writes row prefixes into an (H+1) x (W+1) plane with a zero first row
-// and column; a column pass then accumulates down the rows. The column pass is
-// split into row segments: a first kernel sums each segment, a second one adds
-// the sums of the segments above and scans its own segment. Integer
-// arithmetic is modular (2^64 for q sums, 2^32 for counts), so box sums
-// (Eq. 6, Eq. 9) are exact whatever the image size.
+// The integral images of q and q^2 are built over tiles of kIR rows x kIC
+// columns in three launches that read q twice and write each plane once:
+//   1. per tile: the column sums of the tile's chunk-local row prefixes, each
+//      row's chunk total, and the tile total;
+//   2. per column: the exclusive prefix over the row segments of those column
+//      sums plus the row totals of the chunks to the left (the value of the
+//      plane just above each segment);
+//   3. per tile: the row prefixes again, offset by the chunks to the left, and
+//      accumulated down the tile from the column's offset, written once.
+// The integral histograms (and the backward's fixed-point planes) use a row
+// pass (block-wide scans, warp shuffles inside each warp) into an (H+1) x
+// (W+1) plane with a zero first row and column, then a column pass split into
+// row segments: a first kernel sums each segment, a second one adds the sums
+// of the segments above and scans its own segment. Integer arithmetic is
+// modular (2^64 for q sums, 2^32 for counts), so box sums (Eq. 6, Eq. 9) are
+// exact whatever the image size or summation order.
+#include <algorithm>
+
 #include "tm_kernels.cuh"
 
 namespace tmk {
@@ -43,100 +54,271 @@ constexpr int kNT = 256;
 constexpr int kItems = 8;
 constexpr int kTile = kNT * kItems;
 
-// Row prefixes of q and q^2 into rows 1..H of s1 / s2 (Eq. 5, first pass).
-// Loads and stores go through shared memory so that global accesses are
-// coalesced while each thread scans eight consecutive elements; the shared
-// layouts are padded (9 slots per 8 elements) against bank conflicts.
+// Rows go through shared memory so that global accesses are coalesced while
+// each thread scans eight consecutive elements; the shared layouts are padded
+// (9 slots per 8 elements) against bank conflicts.
 __device__ __forceinline__ int pad9(int i) { return (i >> 3) * 9 + (i & 7); }
 
-__global__ void __launch_bounds__(kNT) k_rows_q(const Job *__restrict__ jobs, int njobs) {
-  __shared__ int32_t tile[kTile / 8 * 9];
-  __shared__ long long out1[kTile / 8 * 9], out2[kTile / 8 * 9];
-  __shared__ long long wt1[kNT / 32], wt2[kNT / 32];
-  const int j = find_job(jobs, njobs, kStRows, blockIdx.x);
-  const Job &J = jobs[j];
-  const int y = blockIdx.x - J.b0[kStRows];
-  const int W = J.in.W;
-  const long long W1 = (long long)W + 1;
-  long long *s1 = J.s1, *s2 = J.s2;
-  if (y == 0)
-    for (long long x = threadIdx.x; x < W1; x += kNT) s1[x] = 0, s2[x] = 0;
-  const int32_t *row = J.q + (long long)y * W;
-  long long *o1 = s1 + (long long)(y + 1) * W1;
-  long long *o2 = s2 + (long long)(y + 1) * W1;
-  if (threadIdx.x == 0) o1[0] = 0, o2[0] = 0;
-  long long carry1 = 0, carry2 = 0;
-  for (int base = 0; base < W; base += kTile) {
-    for (int i = threadIdx.x; i < kTile; i += kNT) tile[pad9(i)] = base + i < W ? __ldg(row + base + i) : 0;
-    __syncthreads();
-    long long a1 = 0, a2 = 0, l1[kItems], l2[kItems];
+// ---- integral images of q and q^2 over tiles ----
+constexpr int kINT = 128;               // threads of a tile kernel
+constexpr int kIC = kINT * kItems;      // columns of a tile (1024)
+constexpr int kIR = 16;                 // rows of a tile (one row segment) unless scratch is tight
+constexpr int kMidCols = 32;            // columns of a column-prefix block
+constexpr int kMidGroups = 16;          // segment groups of a column-prefix block
+constexpr int kMidPer = 8;              // segments of a group per batch
+
+// Scratch of one job (int64): the tiles' column sums, rewritten in place by
+// the column prefix (2 planes x nseg x W), the rows' chunk totals
+// (2 x H x nchunk) and the tile totals (2 x nseg x nchunk). Row segments of
+// J.seg_rows rows, J.nseg of them.
+struct IntScratch {
+  long long *colsum, *rowsum, *tiletot;
+  int nseg, nchunk;
+};
+__device__ __forceinline__ IntScratch int_scratch(const Job &J) {
+  IntScratch r;
+  const int W = J.in.W, H = J.in.H;
+  r.nseg = J.nseg;
+  r.nchunk = (W + kIC - 1) / kIC;
+  r.colsum = J.segtot;
+  r.rowsum = r.colsum + 2LL * r.nseg * W;
+  r.tiletot = r.rowsum + 2LL * H * r.nchunk;
+  return r;
+}
+
+// Exclusive block scan of a pair of values with one set of barriers.
+__device__ __forceinline__ void block_scan_pair(long long v1, long long v2, long long (*wt)[kINT / 32],
+                                                long long &e1, long long &e2, long long &t1, long long &t2) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  long long x1 = v1, x2 = v2;
 #pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-      const long long v = tile[threadIdx.x * 9 + k];
-      a1 += v;
-      a2 += v * v;
-      l1[k] = a1;
-      l2[k] = a2;
-    }
-    long long t1, t2;
-    const long long e1 = block_exclusive_scan<long long, kNT>(a1, wt1, t1) + carry1;
-    const long long e2 = block_exclusive_scan<long long, kNT>(a2, wt2, t2) + carry2;
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y1 = __shfl_up_sync(0xffffffffu, x1, o), y2 = __shfl_up_sync(0xffffffffu, x2, o);
+    if (lane >= o) x1 += y1, x2 += y2;
+  }
+  if (lane == 31) wt[0][wid] = x1, wt[1][wid] = x2;
+  __syncthreads();
+  long long b1 = 0, b2 = 0;
 #pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-      out1[threadIdx.x * 9 + k] = e1 + l1[k];
-      out2[threadIdx.x * 9 + k] = e2 + l2[k];
-    }
-    __syncthreads();
-    const int n = min(kTile, W - base);
-    for (int i = threadIdx.x; i < n; i += kNT) {
-      o1[base + i + 1] = out1[pad9(i)];
-      o2[base + i + 1] = out2[pad9(i)];
-    }
-    carry1 += t1;
-    carry2 += t2;
-    __syncthreads();
+  for (int w = 0; w < kINT / 32; ++w) {
+    if (w < wid) b1 += wt[0][w], b2 += wt[1][w];
+  }
+  t1 = 0;
+  t2 = 0;
+#pragma unroll
+  for (int w = 0; w < kINT / 32; ++w) t1 += wt[0][w], t2 += wt[1][w];
+  e1 = b1 + x1 - v1;
+  e2 = b2 + x2 - v2;
+  __syncthreads();  // wt is rewritten by the next scan
+}
+
+// The thread's kItems strided elements (i = threadIdx.x + m kINT) of a row's
+// chunk; 0 past the chunk's nc columns.
+__device__ __forceinline__ void load_chunk_row(const int32_t *__restrict__ row, int nc, int32_t *v) {
+#pragma unroll
+  for (int m = 0; m < kItems; ++m) {
+    const int i = threadIdx.x + m * kINT;
+    v[m] = i < nc ? __ldg(row + i) : 0;
   }
 }
 
-// Column pass over the integral images of the jobs: block -> (plane, segment,
-// 128-column chunk) of its job. First kernel: segment sums.
-__global__ void __launch_bounds__(128) k_colsum_jobs(const Job *__restrict__ jobs, int njobs) {
-  const int j = find_job(jobs, njobs, kStCols, blockIdx.x);
-  const Job &J = jobs[j];
-  const int lb = blockIdx.x - J.b0[kStCols];
-  const int cols = J.in.W + 1, rows = J.in.H + 1;
-  const int chunks = (cols + 127) / 128;
-  const int pl = lb / (chunks * J.nseg), rem = lb - pl * chunks * J.nseg;
-  const int seg = rem / chunks, ch = rem - seg * chunks;
-  const int c = ch * 128 + threadIdx.x;
-  if (c >= cols) return;
-  const long long *P = pl ? J.s2 : J.s1;
-  const int r0 = 1 + seg * J.seg_rows, r1 = min(rows, r0 + J.seg_rows);
-  long long acc = 0;
-#pragma unroll 4
-  for (int r = r0; r < r1; ++r) acc += P[(long long)r * cols + c];
-  J.segtot[((long long)pl * J.nseg + seg) * cols + c] = acc;
+// Chunk-local row prefixes of q and q^2 of one row, given the thread's
+// strided elements of it (load_chunk_row): thread-local running sums of its
+// kItems consecutive columns (l1, l2) and the exclusive offsets of the thread
+// (e1, e2); t1, t2 are the row's chunk totals. The row goes through shared
+// memory so that the loads were coalesced and each thread scans consecutive
+// columns.
+__device__ __forceinline__ void chunk_row_prefix(const int32_t *v, int32_t *tile, long long (*wt)[kINT / 32],
+                                                 long long *l1, long long *l2, long long &e1, long long &e2,
+                                                 long long &t1, long long &t2) {
+#pragma unroll
+  for (int m = 0; m < kItems; ++m) tile[pad9(threadIdx.x + m * kINT)] = v[m];
+  __syncthreads();
+  long long a1 = 0, a2 = 0;
+#pragma unroll
+  for (int k = 0; k < kItems; ++k) {
+    const long long x = tile[threadIdx.x * 9 + k];
+    a1 += x;
+    a2 += x * x;
+    l1[k] = a1;
+    l2[k] = a2;
+  }
+  block_scan_pair(a1, a2, wt, e1, e2, t1, t2);  // its barriers also order the tile's reuse
 }
 
-// Second kernel: offset by the segments above, scan in place.
-__global__ void __launch_bounds__(128) k_colscan_jobs(const Job *__restrict__ jobs, int njobs) {
+// Launch 1: per tile, the column sums of the chunk-local row prefixes, the
+// rows' chunk totals and the tile totals.
+__global__ void __launch_bounds__(kINT, 4) k_int_stats(const Job *__restrict__ jobs, int njobs) {
+  __shared__ int32_t tile[kIC / 8 * 9];
+  __shared__ long long wt[2][kINT / 32];
+  const int j = find_job(jobs, njobs, kStRows, blockIdx.x);
+  const Job &J = jobs[j];
+  const int W = J.in.W, H = J.in.H;
+  const IntScratch X = int_scratch(J);
+  const int lb = blockIdx.x - J.b0[kStRows];
+  const int seg = lb / X.nchunk, k = lb - seg * X.nchunk;
+  const int R0 = seg * J.seg_rows, R1 = min(R0 + J.seg_rows, H), C0 = k * kIC, nc = min(kIC, W - C0);
+  long long acc1[kItems], acc2[kItems];
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) acc1[i] = acc2[i] = 0;
+  long long T1 = 0, T2 = 0;
+  int32_t cur[kItems], nxt[kItems];
+  load_chunk_row(J.q + (long long)R0 * W + C0, nc, cur);
+  for (int r = R0; r < R1; ++r) {
+    if (r + 1 < R1) load_chunk_row(J.q + (long long)(r + 1) * W + C0, nc, nxt);  // in flight meanwhile
+    long long l1[kItems], l2[kItems], e1, e2, t1, t2;
+    chunk_row_prefix(cur, tile, wt, l1, l2, e1, e2, t1, t2);
+#pragma unroll
+    for (int m = 0; m < kItems; ++m) cur[m] = nxt[m];
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+      acc1[i] += e1 + l1[i];
+      acc2[i] += e2 + l2[i];
+    }
+    if (threadIdx.x == 0) {
+      X.rowsum[(long long)r * X.nchunk + k] = t1;
+      X.rowsum[((long long)H + r) * X.nchunk + k] = t2;
+    }
+    T1 += t1;
+    T2 += t2;
+  }
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    const int c = C0 + threadIdx.x * kItems + i;
+    if (c < W) {
+      X.colsum[(long long)seg * W + c] = acc1[i];
+      X.colsum[((long long)X.nseg + seg) * W + c] = acc2[i];
+    }
+  }
+  if (threadIdx.x == 0) {
+    X.tiletot[(long long)seg * X.nchunk + k] = T1;
+    X.tiletot[((long long)X.nseg + seg) * X.nchunk + k] = T2;
+  }
+}
+
+// Launch 2: per column c (of q), replace each segment's column sum by the
+// plane value just above the segment: the sum, over the segments above, of
+// their column sums plus the totals of their chunks left of c's chunk. A
+// block covers kMidCols columns of one chunk; its kMidGroups groups take
+// kMidPer consecutive segments each per batch, with all loads of a batch in
+// flight together.
+__global__ void __launch_bounds__(kMidCols * kMidGroups) k_int_mid(const Job *__restrict__ jobs, int njobs) {
+  constexpr int kBatch = kMidGroups * kMidPer;
+  __shared__ long long part[2][kMidGroups][kMidCols];
+  __shared__ long long leftT[2][kBatch];
   const int j = find_job(jobs, njobs, kStCols, blockIdx.x);
   const Job &J = jobs[j];
-  const int lb = blockIdx.x - J.b0[kStCols];
-  const int cols = J.in.W + 1, rows = J.in.H + 1;
-  const int chunks = (cols + 127) / 128;
-  const int pl = lb / (chunks * J.nseg), rem = lb - pl * chunks * J.nseg;
-  const int seg = rem / chunks, ch = rem - seg * chunks;
-  const int c = ch * 128 + threadIdx.x;
-  if (c >= cols) return;
-  long long *P = pl ? J.s2 : J.s1;
-  long long acc = 0;
-  for (int s = 0; s < seg; ++s) acc += J.segtot[((long long)pl * J.nseg + s) * cols + c];
-  const int r0 = 1 + seg * J.seg_rows, r1 = min(rows, r0 + J.seg_rows);
-#pragma unroll 4
-  for (int r = r0; r < r1; ++r) {
-    acc += P[(long long)r * cols + c];
-    P[(long long)r * cols + c] = acc;
+  const int W = J.in.W;
+  const IntScratch X = int_scratch(J);
+  const int lane = threadIdx.x % kMidCols, g = threadIdx.x / kMidCols;
+  const int c0 = (blockIdx.x - J.b0[kStCols]) * kMidCols, c = c0 + lane;
+  const int k = c0 / kIC;  // the block's chunk (kMidCols divides kIC)
+  long long carry1 = 0, carry2 = 0;
+  for (int sb = 0; sb < X.nseg; sb += kBatch) {
+    // totals of the batch's segments over the chunks left of k
+    for (int t = threadIdx.x; t < 2 * kBatch; t += kMidCols * kMidGroups) {
+      const int pl = t / kBatch, s = sb + t % kBatch;
+      long long v = 0;
+      if (s < X.nseg)
+        for (int kk = 0; kk < k; ++kk) v += X.tiletot[((long long)pl * X.nseg + s) * X.nchunk + kk];
+      leftT[pl][t % kBatch] = v;
+    }
+    __syncthreads();
+    const int s0 = sb + g * kMidPer;
+    long long v1[kMidPer], v2[kMidPer], sum1 = 0, sum2 = 0;
+#pragma unroll
+    for (int i = 0; i < kMidPer; ++i) {
+      const int s = s0 + i;
+      const bool ok = s < X.nseg && c < W;
+      v1[i] = ok ? X.colsum[(long long)s * W + c] : 0;
+      v2[i] = ok ? X.colsum[((long long)X.nseg + s) * W + c] : 0;
+    }
+#pragma unroll
+    for (int i = 0; i < kMidPer; ++i) {
+      if (s0 + i < X.nseg) {
+        v1[i] += leftT[0][g * kMidPer + i];
+        v2[i] += leftT[1][g * kMidPer + i];
+      }
+      sum1 += v1[i];
+      sum2 += v2[i];
+    }
+    part[0][g][lane] = sum1;
+    part[1][g][lane] = sum2;
+    __syncthreads();
+    long long run1 = carry1, run2 = carry2;
+    for (int h = 0; h < g; ++h) run1 += part[0][h][lane], run2 += part[1][h][lane];
+#pragma unroll
+    for (int i = 0; i < kMidPer; ++i) {
+      const int s = s0 + i;
+      if (s < X.nseg && c < W) {
+        X.colsum[(long long)s * W + c] = run1;
+        X.colsum[((long long)X.nseg + s) * W + c] = run2;
+      }
+      run1 += v1[i];
+      run2 += v2[i];
+    }
+    for (int h = 0; h < kMidGroups; ++h) carry1 += part[0][h][lane], carry2 += part[1][h][lane];
+    __syncthreads();  // part and leftT are rewritten by the next batch
+  }
+}
+
+// Launch 3: per tile, the full row prefixes (chunk-local prefix plus the
+// row's totals of the chunks to the left) accumulated down the tile from the
+// value above it, written to rows 1..H, columns 1..W of s1 / s2; tiles of the
+// first segment also write row 0, tiles of the first chunk column 0.
+__global__ void __launch_bounds__(kINT, 4) k_int_write(const Job *__restrict__ jobs, int njobs) {
+  __shared__ int32_t tile[kIC / 8 * 9];
+  __shared__ long long out1[kIC / 8 * 9], out2[kIC / 8 * 9];
+  __shared__ long long wt[2][kINT / 32];
+  const int j = find_job(jobs, njobs, kStRows, blockIdx.x);
+  const Job &J = jobs[j];
+  const int W = J.in.W, H = J.in.H;
+  const long long W1 = (long long)W + 1;
+  const IntScratch X = int_scratch(J);
+  const int lb = blockIdx.x - J.b0[kStRows];
+  const int seg = lb / X.nchunk, k = lb - seg * X.nchunk;
+  const int R0 = seg * J.seg_rows, R1 = min(R0 + J.seg_rows, H), C0 = k * kIC, nc = min(kIC, W - C0);
+  long long *s1 = J.s1, *s2 = J.s2;
+  if (seg == 0) {
+    for (int i = threadIdx.x; i < nc; i += kINT) s1[C0 + 1 + i] = 0, s2[C0 + 1 + i] = 0;
+    if (k == 0 && threadIdx.x == 0) s1[0] = 0, s2[0] = 0;
+  }
+  if (k == 0)
+    for (int r = R0 + (int)threadIdx.x; r < R1; r += kINT) s1[(r + 1) * W1] = 0, s2[(r + 1) * W1] = 0;
+  long long acc1[kItems], acc2[kItems];
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    const int c = C0 + threadIdx.x * kItems + i;
+    acc1[i] = c < W ? X.colsum[(long long)seg * W + c] : 0;
+    acc2[i] = c < W ? X.colsum[((long long)X.nseg + seg) * W + c] : 0;
+  }
+  int32_t cur[kItems], nxt[kItems];
+  load_chunk_row(J.q + (long long)R0 * W + C0, nc, cur);
+  for (int r = R0; r < R1; ++r) {
+    if (r + 1 < R1) load_chunk_row(J.q + (long long)(r + 1) * W + C0, nc, nxt);  // in flight meanwhile
+    long long L1 = 0, L2 = 0;  // the row's totals of the chunks to the left
+    for (int kk = 0; kk < k; ++kk) {
+      L1 += X.rowsum[(long long)r * X.nchunk + kk];
+      L2 += X.rowsum[((long long)H + r) * X.nchunk + kk];
+    }
+    long long l1[kItems], l2[kItems], e1, e2, t1, t2;
+    chunk_row_prefix(cur, tile, wt, l1, l2, e1, e2, t1, t2);
+#pragma unroll
+    for (int m = 0; m < kItems; ++m) cur[m] = nxt[m];
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+      acc1[i] += L1 + e1 + l1[i];
+      acc2[i] += L2 + e2 + l2[i];
+      out1[threadIdx.x * 9 + i] = acc1[i];
+      out2[threadIdx.x * 9 + i] = acc2[i];
+    }
+    __syncthreads();
+    long long *o1 = s1 + (long long)(r + 1) * W1 + C0 + 1, *o2 = s2 + (long long)(r + 1) * W1 + C0 + 1;
+    for (int i = threadIdx.x; i < nc; i += kINT) {
+      o1[i] = out1[pad9(i)];
+      o2[i] = out2[pad9(i)];
+    }
+    __syncthreads();  // out1 / out2 are rewritten by the next row
   }
 }
 
@@ -241,18 +423,30 @@ void column_pass(T *base, long long plane_stride, int planes, int W, int H, T *s
 
 }  // namespace
 
-void column_segments(int W, int H, int planes, int &nseg, int &seg_rows) {
-  segments(W + 1, H, planes, nseg, seg_rows);
+void integral_layout(int W, int H, size_t max_scratch_elems, int &nseg, int &seg_rows) {
+  // the shortest segments (most tiles) whose scratch fits, at least kIR rows
+  seg_rows = kIR;
+  for (;;) {
+    nseg = (H + seg_rows - 1) / seg_rows;
+    if (integral_scratch_elems(W, H, nseg) <= max_scratch_elems || seg_rows >= H) return;
+    seg_rows = std::min(H, seg_rows * 2);
+  }
 }
 
-int col_blocks(int W, int nseg) { return ((W + 1 + 127) / 128) * nseg * 2; }
+size_t integral_scratch_elems(int W, int H, int nseg) {
+  const long long nchunk = (W + kIC - 1) / kIC;
+  return (size_t)(2LL * nseg * W + 2LL * H * nchunk + 2LL * nseg * nchunk);
+}
 
-int launch_integral_jobs(const Job *jobs, int njobs, int row_blocks, int colb, bool multi_seg,
-                         cudaStream_t s) {
-  k_rows_q<<<row_blocks, kNT, 0, s>>>(jobs, njobs);
-  if (multi_seg) k_colsum_jobs<<<colb, 128, 0, s>>>(jobs, njobs);
-  k_colscan_jobs<<<colb, 128, 0, s>>>(jobs, njobs);
-  return multi_seg ? 3 : 2;
+int integral_tile_blocks(int W, int nseg) { return nseg * ((W + kIC - 1) / kIC); }
+
+int integral_col_blocks(int W) { return (W + kMidCols - 1) / kMidCols; }
+
+int launch_integral_jobs(const Job *jobs, int njobs, int tile_blocks, int col_blocks, cudaStream_t s) {
+  k_int_stats<<<tile_blocks, kINT, 0, s>>>(jobs, njobs);
+  k_int_mid<<<col_blocks, kMidCols * kMidGroups, 0, s>>>(jobs, njobs);
+  k_int_write<<<tile_blocks, kINT, 0, s>>>(jobs, njobs);
+  return 3;
 }
 
 int launch_column_pass_u64(unsigned long long *base, long long plane_stride, int planes, int W, int H,

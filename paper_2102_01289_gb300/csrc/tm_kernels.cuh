@@ -17,13 +17,19 @@ void launch_prep(const Job *jobs, int njobs, int blocks, int n_bins, int flags, 
 int range_blocks(int W, int H, int num_sms, double share);
 int prep_blocks(int W, int H, int num_sms, double share);
 
-// Stage a2 (Eq. 5): integral images of q and q^2, (H+1) x (W+1) int64.
-// Row pass: one block per image row. Column pass: blocks per image =
-// col_blocks(W, nseg); nseg/seg_rows from column_segments().
-void column_segments(int W, int H, int planes, int &nseg, int &seg_rows);
-int col_blocks(int W, int nseg);
-int launch_integral_jobs(const Job *jobs, int njobs, int row_blocks, int colb, bool multi_seg,
-                         cudaStream_t s);
+// Stage a2 (Eq. 5): integral images of q and q^2, (H+1) x (W+1) int64, over
+// tiles of row segments x column chunks. integral_layout picks the segments
+// (J.nseg of J.seg_rows rows) whose scratch fits max_scratch_elems (the
+// shortest such, at least 16 rows; at worst one segment). Per image:
+// integral_tile_blocks(W, nseg) blocks of the tile launches (first block
+// J.b0[kStRows]), integral_col_blocks(W) of the column-prefix launch
+// (J.b0[kStCols]), and integral_scratch_elems(W, H, nseg) int64 elements of
+// scratch at J.segtot. Returns the number of launches.
+void integral_layout(int W, int H, size_t max_scratch_elems, int &nseg, int &seg_rows);
+size_t integral_scratch_elems(int W, int H, int nseg);
+int integral_tile_blocks(int W, int nseg);
+int integral_col_blocks(int W);
+int launch_integral_jobs(const Job *jobs, int njobs, int tile_blocks, int col_blocks, cudaStream_t s);
 
 // Stage a3 (Eq. 7-8), materialised: integral histogram planes,
 // (H+1) x (W+1) uint32 each. cumulative = true: planes k = 1..n-1 hold the

@@ -1,7 +1,7 @@
 // tm_noalloc.cu -- integral images without any allocation.
 //
 // tm_integral_image needs scratch device memory (one job descriptor and the
-// column pass's per-segment sums) and obtains it with cudaMallocAsync. Some
+// tile sums of the integral images) and obtains it with cudaMallocAsync. Some
 // callers cannot allocate at all: code running under a real-time or frame-
 // deadline contract that forbids allocator calls after start-up, code that
 // runs inside another framework's memory-pool or allocation callbacks (where
@@ -21,7 +21,7 @@ namespace {
 
 constexpr size_t kScratchBytes = (size_t)8 << 20;  // 8 MiB
 
-// Shared by every call on a device: [job descriptor | column-pass segment sums].
+// Shared by every call on a device: [job descriptor | integral-image scratch].
 static __device__ __align__(256) unsigned char g_integral_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -36,10 +36,10 @@ extern "C" tm_status tm_integral_image_noalloc(const int32_t *q, int32_t width, 
                                                int64_t *s1, int64_t *s2, void *stream) {
   if (!q || !s1 || !s2 || s1 == s2) return TM_EINVAL;
   if (width < 1 || height < 1 || (long long)width * height > (1LL << 31) - 1) return TM_EINVAL;
-  int nseg = 1, seg_rows = 1;
-  column_segments(width, height, 2, nseg, seg_rows);
   const size_t job_bytes = round256(sizeof(Job));
-  const size_t need = job_bytes + 8 * 2 * (size_t)nseg * ((size_t)width + 1);
+  int nseg = 1, seg_rows = 1;
+  integral_layout(width, height, (kScratchBytes - job_bytes) / 8, nseg, seg_rows);
+  const size_t need = job_bytes + 8 * integral_scratch_elems(width, height, nseg);
   if (need > kScratchBytes) return TM_EINVAL;  // larger than the static scratch
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -72,14 +72,15 @@ extern "C" tm_status tm_integral_image_noalloc(const int32_t *q, int32_t width, 
   J.nseg = nseg;
   J.seg_rows = seg_rows;
   J.segtot = reinterpret_cast<long long *>(static_cast<char *>(base) + job_bytes);
-  // The segment sums are fully rewritten before they are read, so nothing
+  // The scratch is fully rewritten before it is read, so nothing
   // left in the array by an earlier call needs clearing. The descriptor comes
   // from pageable memory: the copy has consumed it when this call returns.
   if (cudaMemcpyAsync(base, &J, sizeof(Job), cudaMemcpyHostToDevice, st) != cudaSuccess) {
     cudaGetLastError();
     return TM_ECUDA;
   }
-  launch_integral_jobs(static_cast<const Job *>(base), 1, height, col_blocks(width, nseg), nseg > 1, st);
+  launch_integral_jobs(static_cast<const Job *>(base), 1, integral_tile_blocks(width, nseg), integral_col_blocks(width),
+                       st);
   if (cudaGetLastError() != cudaSuccess) return TM_ECUDA;
   return TM_OK;
 }

@@ -21,7 +21,7 @@ def _built():
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
-    # 600000 x 1 needs 16 * 600001 bytes of column sums: more than 8 MiB
+    # 600000 x 1 needs 16 * 600000 bytes of column sums: more than 8 MiB
     L = tm.lib()
     fake = ctypes.c_void_p(0x1000)
     assert L.tm_integral_image_noalloc(fake, 600000, 1, ctypes.c_void_p(0x2000),
