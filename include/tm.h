@@ -158,6 +158,19 @@ tm_status tm_forward(tm_ctx *ctx, const tm_image *in, const tm_image *out,
 tm_status tm_forward_host(tm_ctx *ctx, const tm_image *in_host,
                           const tm_image *out_host, void *stream);
 
+/* tm_forward_host without the synchronisation, for streams of host images:
+ * in_host and out_host must be page-locked (cudaHostAlloc / cudaHostRegister;
+ * TM_EINVAL otherwise). The upload runs on an internal copy stream into one
+ * of two device slots used in turn, the forward on `stream` after it, and the
+ * last kernel stores the result into out_host over the host link; so one
+ * call's upload overlaps the previous call's forward. Returns once the work
+ * is enqueued: in_host must stay unchanged and out_host unread until `stream`
+ * has been synchronised. Results are identical to tm_forward_host. (Writing
+ * the result to a device slot and downloading it on a third stream was
+ * measured slower: concurrent uploads and downloads share the host link.) */
+tm_status tm_forward_host_async(tm_ctx *ctx, const tm_image *in_host,
+                                const tm_image *out_host, void *stream);
+
 /* Forward over n images of possibly different sizes: one launch per stage for
  * the whole batch, the fused sweep as one persistent launch over a shared
  * queue of (image, tile) items. in[i], out[i] as for tm_forward (host arrays

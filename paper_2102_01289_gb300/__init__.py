@@ -34,7 +34,7 @@ EXPORTS = (
     "tm_status_string", "tm_forward", "tm_forward_host", "tm_forward_batch", "tm_backward",
     "tm_integral_image", "tm_integral_histogram", "tm_set_debug", "tm_debug_size",
     "tm_debug_export", "tm_set_option", "tm_last_launch_count", "tm_stage_times",
-    "tm_integral_image_noalloc", "tm_backward_batch",
+    "tm_integral_image_noalloc", "tm_backward_batch", "tm_forward_host_async",
 )
 
 
@@ -110,6 +110,7 @@ def lib():
             "tm_stage_times": (i32, [P, P, P, i32]),
             "tm_integral_image_noalloc": (st, [P, i32, i32, P, P, P]),
             "tm_backward_batch": (st, [P, i32, P, P, P, P, P]),
+            "tm_forward_host_async": (st, [P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -228,6 +229,14 @@ def tm_forward_host(ctx, inp, out, stream=None) -> None:
     """Host (numpy) buffers in and out; copies and synchronisation inside."""
     a, b = image_of_numpy(inp), image_of_numpy(out)
     _check(lib().tm_forward_host(ctx, ctypes.byref(a), ctypes.byref(b), _stream_ptr(stream)), ctx)
+
+
+def tm_forward_host_async(ctx, inp, out, stream=None) -> None:
+    """Page-locked host (numpy) buffers in and out; enqueued on `stream`
+    without synchronising (the upload overlaps the previous call's forward).
+    Synchronise the stream before reading `out` or changing `inp`."""
+    a, b = image_of_numpy(inp), image_of_numpy(out)
+    _check(lib().tm_forward_host_async(ctx, ctypes.byref(a), ctypes.byref(b), _stream_ptr(stream)), ctx)
 
 
 def tm_forward_batch(ctx, inputs, outputs, stream=None) -> None:

@@ -67,6 +67,13 @@ struct tm_ctx {
   // staging for tm_forward_host
   void *stage = nullptr;
   size_t stage_bytes = 0;
+  // tm_forward_host_async: two device input slots filled on a copy stream,
+  // each guarded by the event after the forward that last read it
+  void *hslot[2] = {nullptr, nullptr};
+  size_t hslot_bytes = 0;
+  cudaEvent_t hslot_free[2] = {nullptr, nullptr}, hslot_full[2] = {nullptr, nullptr};
+  cudaStream_t copy_stream = nullptr;
+  int hslot_next = 0;
   // layout of the last single-image forward (for debug exports)
   int last_W = 0, last_H = 0, last_q = 0, last_path = 0;
   uint8_t *bins = nullptr;
@@ -884,7 +891,8 @@ tm_status tm_create(const tm_params *params, tm_ctx **out) {
 
 void tm_destroy(tm_ctx *c) {
   if (!c) return;
-  if (c->ws || c->stats || c->rr_stats || c->stage || c->djobs || c->gdjobs || c->graph) cudaDeviceSynchronize();
+  if (c->ws || c->stats || c->rr_stats || c->stage || c->djobs || c->gdjobs || c->graph || c->hslot[0])
+    cudaDeviceSynchronize();
   drop_graph(c);
   for (auto &call : c->marks)
     for (auto &m : call) cudaEventDestroy(m.first);
@@ -894,6 +902,12 @@ void tm_destroy(tm_ctx *c) {
   if (c->stats) cudaFree(c->stats);
   if (c->rr_stats) cudaFree(c->rr_stats);
   if (c->stage) cudaFree(c->stage);
+  for (int k = 0; k < 2; ++k) {
+    if (c->hslot[k]) cudaFree(c->hslot[k]);
+    for (cudaEvent_t e : {c->hslot_free[k], c->hslot_full[k]})
+      if (e) cudaEventDestroy(e);
+  }
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   if (c->djobs) cudaFree(c->djobs);
   if (c->ditems) cudaFree(c->ditems);
   if (c->graph_stream) cudaStreamDestroy(c->graph_stream);
@@ -993,6 +1007,67 @@ tm_status tm_forward_host(tm_ctx *c, const tm_image *in, const tm_image *out, vo
     TM_CUDA(c, cudaMemcpy2DAsync(out->data, out->pitch * elem_size(out->dtype), dout.data, out_row,
                                  out_row, H, cudaMemcpyDeviceToHost, st));
   TM_CUDA(c, cudaStreamSynchronize(st));
+  return TM_OK;
+}
+
+// Device address of a page-locked host buffer, or null.
+static void *locked_device_pointer(const void *p) {
+  cudaPointerAttributes pa{};
+  void *d = nullptr;
+  if (cudaPointerGetAttributes(&pa, p) == cudaSuccess && pa.type == cudaMemoryTypeHost) d = pa.devicePointer;
+  cudaGetLastError();
+  return d;
+}
+
+tm_status tm_forward_host_async(tm_ctx *c, const tm_image *in, const tm_image *out, void *stream) {
+  if (!c) return fail(nullptr, TM_EINVAL, "tm_forward_host_async: ctx is NULL");
+  tm_status s;
+  if ((s = validate_image(c, in, "in", true))) return s;
+  if ((s = validate_image(c, out, "out", false))) return s;
+  if (in->width != out->width || in->height != out->height)
+    return fail(c, TM_EINVAL, "in and out sizes differ");
+  void *out_dev = locked_device_pointer(out->data);
+  if (!locked_device_pointer(in->data) || !out_dev)
+    return fail(c, TM_EINVAL, "tm_forward_host_async needs page-locked in and out (use tm_forward_host)");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int W = in->width, H = in->height;
+  const size_t in_row = 3 * (size_t)W * elem_size(in->dtype);
+  const size_t in_bytes = align256(in_row * H);
+  if (c->hslot_bytes < in_bytes) {
+    if (c->hslot[0]) TM_CUDA(c, cudaDeviceSynchronize());  // both slots may still be in use
+    for (int k = 0; k < 2; ++k) {
+      if (c->hslot[k]) cudaFree(c->hslot[k]);
+      c->hslot[k] = nullptr;
+    }
+    c->hslot_bytes = 0;
+    for (int k = 0; k < 2; ++k) {
+      cudaError_t e = cudaMalloc(&c->hslot[k], in_bytes);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, TM_ENOMEM, "input slots: %s", cudaGetErrorString(e));
+      }
+    }
+    c->hslot_bytes = in_bytes;
+  }
+  if (!c->copy_stream) TM_CUDA(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+  for (int k = 0; k < 2; ++k)
+    for (cudaEvent_t *e : {&c->hslot_free[k], &c->hslot_full[k]})
+      if (!*e) TM_CUDA(c, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  const int k = c->hslot_next;
+  c->hslot_next ^= 1;
+  // the upload waits for the forward that last read this slot (a wait on an
+  // event never recorded returns at once); the forward waits for the upload
+  TM_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->hslot_free[k], 0));
+  TM_CUDA(c, cudaMemcpy2DAsync(c->hslot[k], in_row, in->data, in->pitch * elem_size(in->dtype), in_row, H,
+                               cudaMemcpyHostToDevice, c->copy_stream));
+  TM_CUDA(c, cudaEventRecord(c->hslot_full[k], c->copy_stream));
+  TM_CUDA(c, cudaStreamWaitEvent(st, c->hslot_full[k], 0));
+  tm_image din = *in, dout = *out;
+  din.data = c->hslot[k];
+  din.pitch = 3LL * W;
+  dout.data = out_dev;  // the last kernel stores the result over the host link
+  if ((s = forward_device(c, &din, &dout, st))) return s;
+  TM_CUDA(c, cudaEventRecord(c->hslot_free[k], st));
   return TM_OK;
 }
 

@@ -225,6 +225,31 @@ def test_pinned_host_output_written_directly(orc):
         tm.tm_destroy(ctx)
 
 
+def test_async_host_stream_matches_device(orc):
+    """tm_forward_host_async over a stream of page-locked frames, with two
+    sizes interleaved (slot reuse and a slot regrow) and no synchronisation
+    between calls: every output equals the device path's. Pageable buffers
+    are rejected with TM_EINVAL."""
+    gp, op = params_pair(orc, 32, [3, 10, 60])
+    frames = [synth.wdr_image(*hw, seed=20 + k) for k, hw in enumerate([(120, 160)] * 3 + [(200, 150)] * 2 + [(120, 160)])]
+    refs = [run_gpu(f, gp, debug=False)[0] for f in frames]
+    ctx = tm.tm_create(gp)
+    try:
+        hins = [torch.from_numpy(f).pin_memory() for f in frames]
+        houts = [torch.zeros_like(h).pin_memory() for h in hins]
+        stream = torch.cuda.current_stream()
+        for hi, ho in zip(hins, houts):
+            tm.tm_forward_host_async(ctx, hi.numpy(), ho.numpy(), stream)
+        stream.synchronize()
+        for ho, ref in zip(houts, refs):
+            assert np.array_equal(ho.numpy(), ref)
+        with pytest.raises(tm.TmError) as ei:
+            tm.tm_forward_host_async(ctx, frames[0], np.empty_like(frames[0]), stream)
+        assert ei.value.status == tm.TM_EINVAL
+    finally:
+        tm.tm_destroy(ctx)
+
+
 def test_integral_image_entry_point_exact(orc):
     rng = np.random.default_rng(0)
     # up to a full-size ragged plane (several row segments of the column pass)
