@@ -297,8 +297,19 @@ tm_status tm_debug_export(tm_ctx *ctx, int32_t what, void *dst, size_t bytes,
  *                        (which takes each image's own range); off by default.
  *                        Batches and tm_backward always use each image's own
  *                        range.
+ *   TM_OPT_BACKWARD_REUSE 1 = tm_backward / tm_backward_batch take the forward
+ *                        intermediates (bin map, quantised log, integral
+ *                        images, slab counts) from the context's workspace
+ *                        instead of recomputing them, when the last forward
+ *                        call on the context ran the fused path, each image
+ *                        over its own range, on the same image descriptors
+ *                        (pointers, sizes, pitches, dtypes) in the same order.
+ *                        The caller guarantees that the pixels of `in` have
+ *                        not changed since that forward (an autograd function
+ *                        holding its saved input does). Results are those of
+ *                        the recomputation. 0 = always recompute (default).
  */
-enum { TM_OPT_HIST_PATH = 1, TM_OPT_STAGE_TIMING = 2, TM_OPT_REUSE_RANGE = 3 };
+enum { TM_OPT_HIST_PATH = 1, TM_OPT_STAGE_TIMING = 2, TM_OPT_REUSE_RANGE = 3, TM_OPT_BACKWARD_REUSE = 4 };
 tm_status tm_set_option(tm_ctx *ctx, int32_t key, int64_t value);
 
 /* Per-stage device time, summed over every call since the previous read,

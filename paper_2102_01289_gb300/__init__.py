@@ -25,6 +25,7 @@ TM_F32, TM_F16, TM_U8 = 0, 1, 2
 TM_OPT_HIST_PATH = 1
 TM_OPT_STAGE_TIMING = 2
 TM_OPT_REUSE_RANGE = 3
+TM_OPT_BACKWARD_REUSE = 4
 # reading variants (tm_params.flags)
 TM_FLAG_CDF_INCLUSIVE, TM_FLAG_AREA_LITERAL, TM_FLAG_VAR_LINEAR, TM_FLAG_SRGB_U8 = 1, 2, 4, 8
 
@@ -354,7 +355,12 @@ class _CtxCache:
     def get(self, t):
         key = tuple(round(float(x), 9) for x in t.detach().cpu().reshape(-1))
         if key not in self.ctxs:
-            self.ctxs[key] = tm_create(params_from_tensor(self.template, t))
+            c = tm_create(params_from_tensor(self.template, t))
+            # the autograd function keeps its input saved and unchanged between
+            # forward and backward, so the backward may take the forward's
+            # intermediates from the context (it checks they are that input's)
+            tm_set_option(c, TM_OPT_BACKWARD_REUSE, 1)
+            self.ctxs[key] = c
         return self.ctxs[key]
 
     def close(self):

@@ -90,6 +90,13 @@ struct tm_ctx {
   Stats *rr_stats = nullptr;
   int rr_cur = 0, rr_valid = 0, rr_W = 0, rr_H = 0, rr_q = 0;
   const Stats *last_stats = nullptr;  // range state of the last single-image forward
+  // TM_OPT_BACKWARD_REUSE: the job descriptors of the last fused forward that
+  // left its intermediates (bins, q, integral images, slab counts) in the
+  // workspace, the images it ran on, and those of the cached batch graph
+  int bwd_reuse = 0;
+  bool fwd_valid = false;
+  std::vector<Job> fwd_jobs, graph_jobs;
+  std::vector<tm_image> fwd_in;
   // automatic histogram path: the measured choice per (width, height, in dtype, out dtype)
   std::map<std::tuple<int, int, int, int>, int> path_choice;
   // stage timing: events recorded on the call's stream after each stage
@@ -431,6 +438,7 @@ JobLayout job_layout(const tm_params &p, int W, int H, int nseg, size_t count_el
 // bin-major cumulative integral histogram, lookup. Used when the fused sweep
 // does not fit the fields, or on request (TM_OPT_HIST_PATH = 2).
 tm_status forward_materialised(tm_ctx *c, const tm_image *in, const tm_image *out, cudaStream_t s) {
+  c->fwd_valid = false;  // its workspace layout holds no slab counts
   const int W = in->width, H = in->height;
   const int qbits = choose_qbits(c->p, W, H);
   DevParams P = dev_params(c->p, qbits);
@@ -521,11 +529,16 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
                         bool graph, bool do_lookup = true, std::vector<Job> *jobs_out = nullptr) {
   tm_status st;
   if (graph && c->graph && same_images(c->graph_in, in, nimg) && same_images(c->graph_out, out, nimg)) {
+    c->fwd_valid = false;
     TM_CUDA(c, cudaGraphLaunch(c->graph, s));
     if ((st = release_staging(c, &c->gstage, s))) return st;
     c->launches = c->graph_launches;
+    c->fwd_jobs = c->graph_jobs;
+    c->fwd_in.assign(in, in + nimg);
+    c->fwd_valid = true;
     return TM_OK;
   }
+  c->fwd_valid = false;  // the workspace is rewritten below
   const bool debug = c->debug != 0 && nimg == 1 && !graph;
   double total_px = 0;
   for (int i = 0; i < nimg; ++i) total_px += (double)in[i].width * in[i].height;
@@ -671,6 +684,7 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
     c->graph_in.assign(in, in + nimg);
     c->graph_out.assign(out, out + nimg);
     c->graph_launches = n;
+    c->graph_jobs = jobs;
     TM_CUDA(c, cudaGraphLaunch(c->graph, caller));
     if ((st = release_staging(c, S, caller))) return st;
   } else if (ls < 0) {
@@ -679,6 +693,11 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   if ((st = check_launch(c, "forward launch"))) return st;
   c->launches = n;
   if (jobs_out) *jobs_out = jobs;
+  if (run_range) {  // each image binned over its own range, as a recomputation would
+    c->fwd_jobs = jobs;
+    c->fwd_in.assign(in, in + nimg);
+    c->fwd_valid = true;
+  }
   if (nimg == 1) {
     c->last_W = in[0].width;
     c->last_H = in[0].height;
@@ -825,10 +844,15 @@ tm_status backward_images(tm_ctx *c, int n, const tm_image *in, const tm_image *
     return fail(c, TM_EUNSUPPORTED, "the backward covers the log-domain variance (not TM_FLAG_VAR_LINEAR)");
   if ((st = ensure_device_info(c))) return st;
   std::vector<Job> jobs;
-  st = forward_fused(c, n, in, in, s, false, false, &jobs);
-  if (st == TM_EUNSUPPORTED) return fail(c, st, "fused sweep does not fit these fields");
-  if (st) return st;
-  int64_t launches = c->launches;
+  int64_t launches = 0;
+  if (c->bwd_reuse && c->fwd_valid && (int)c->fwd_in.size() == n && same_images(c->fwd_in, in, n)) {
+    jobs = c->fwd_jobs;  // the last forward's intermediates of these images are in the workspace
+  } else {
+    st = forward_fused(c, n, in, in, s, false, false, &jobs);
+    if (st == TM_EUNSUPPORTED) return fail(c, st, "fused sweep does not fit these fields");
+    if (st) return st;
+    launches = c->launches;
+  }
   if ((st = grow_device(c, &c->bws, &c->bws_bytes, need))) return st;
   for (int i = 0; i < n; ++i)
     if ((st = backward_image(c, jobs[(size_t)i], &grad_out[i], grad_in ? &grad_in[i] : nullptr,
@@ -1243,6 +1267,10 @@ tm_status tm_set_option(tm_ctx *c, int32_t key, int64_t value) {
   if (key == TM_OPT_REUSE_RANGE) {
     c->reuse_range = value ? 1 : 0;
     c->rr_valid = 0;
+    return TM_OK;
+  }
+  if (key == TM_OPT_BACKWARD_REUSE) {
+    c->bwd_reuse = value ? 1 : 0;
     return TM_OK;
   }
   if (key == TM_OPT_HIST_PATH) {

@@ -73,6 +73,50 @@ def test_backward_matches_oracle_adjoint(orc, H, W, n, radii, flags):
     assert np.allclose(gpar, ref_vec, rtol=1e-3, atol=1e-3 * np.abs(ref_vec).max())
 
 
+def test_backward_reuses_forward_intermediates():
+    """TM_OPT_BACKWARD_REUSE: right after a forward of the same images the
+    backward takes the forward's intermediates (fewer launches) with results
+    identical to the recomputation; other images, or a forward of other
+    images in between, are recomputed."""
+    n, H, W = 3, 60, 80
+    xs = [torch.from_numpy(synth.wdr_image(H, W, seed=70 + k)).cuda() for k in range(n)]
+    ys = [torch.empty_like(x) for x in xs]
+    gs = [torch.randn_like(x) for x in xs]
+    p = tm.make_params(16, [2, 8, 30])
+
+    def run(reuse, between=None):
+        ctx = tm.tm_create(p)
+        try:
+            tm.tm_set_option(ctx, tm.TM_OPT_BACKWARD_REUSE, reuse)
+            gins = [torch.empty_like(x) for x in xs]
+            gp = torch.empty(9, device="cuda")
+            tm.tm_forward_batch(ctx, xs, ys)
+            if between is not None:
+                tm.tm_forward(ctx, between, torch.empty_like(between))
+            tm.tm_backward_batch(ctx, xs, gs, gins, gp)
+            launches = tm.tm_last_launch_count(ctx)
+            gin1 = torch.empty_like(xs[0])
+            gp1 = torch.empty(9, device="cuda")
+            tm.tm_forward(ctx, xs[0], ys[0])
+            tm.tm_backward(ctx, xs[0], gs[0], gin1, gp1)
+            torch.cuda.synchronize()
+            return [g.cpu() for g in gins], gp.cpu(), gin1.cpu(), gp1.cpu(), launches
+        finally:
+            tm.tm_destroy(ctx)
+
+    ref = run(0)
+    got = run(1)
+    for a, b in zip(ref[0], got[0]):
+        assert torch.equal(a, b)
+    assert torch.equal(ref[1], got[1]) and torch.equal(ref[2], got[2]) and torch.equal(ref[3], got[3])
+    assert got[4] < ref[4]  # the recomputation's launches were skipped
+    other = torch.from_numpy(synth.wdr_image(50, 50, seed=99)).cuda()
+    mixed = run(1, between=other)
+    for a, b in zip(ref[0], mixed[0]):
+        assert torch.equal(a, b)
+    assert mixed[4] == ref[4]
+
+
 def test_backward_matches_gpu_finite_differences(orc):
     """Central differences of the GPU forward (h = 1e-3 relative) at pixels
     whose normalised log sits at least a quarter bin from any edge."""
