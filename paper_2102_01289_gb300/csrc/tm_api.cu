@@ -580,10 +580,38 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
     J.nitem = J.plan.tiles_x * J.plan.tiles_y;
     const double rows = std::min(J.plan.TY + 2.0 * J.plan.Ry + 1, H + 1.0);
     const double cols = std::min(J.plan.TX + 2.0 * J.plan.Rx + 2, W + 1.0);
-    order.push_back({rows * (cols * 0.25 + 300.0), i});
+    order.push_back({rows * (cols * 0.25 + 300.0) * J.nitem, i});  // the image's work estimate
   }
-  // the queue holds each image's tiles together, images with the longest
-  // uniform tiles first (the device balances the tiles within an image)
+  // A batch's queue is made a whole number of waves of the persistent sweep
+  // (one CTA per SM): a last partial wave would leave most SMs idle while it
+  // runs. The budgets of the images planned on the device are scaled up to
+  // the next multiple of the SM count (at least one tile per strip).
+  if (nimg > 1) {
+    long long total = 0, fixed = 0, minimum = 0;
+    for (const Job &J : jobs) {
+      total += J.nitem;
+      if (!J.adaptive) fixed += J.nitem;
+      else minimum += J.plan.tiles_x;
+    }
+    const long long waves = (total + c->num_sms - 1) / c->num_sms;
+    const long long want = std::max(minimum, waves * c->num_sms - fixed), scalable = total - fixed;
+    if (total > c->num_sms && scalable > 0 && want != scalable) {
+      long long got = 0;
+      for (Job &J : jobs)
+        if (J.adaptive) {
+          J.nitem = (int)std::max<long long>(J.plan.tiles_x, (long long)J.nitem * want / scalable);
+          got += J.nitem;
+        }
+      for (size_t i = 0; got < want; i = (i + 1) % jobs.size())  // the remainder, one tile each
+        if (jobs[i].adaptive) {
+          ++jobs[i].nitem;
+          ++got;
+        }
+    }
+  }
+  // the queue holds each image's tiles together, images with the costliest
+  // tiles first (the device balances the tiles within an image)
+  for (auto &o : order) o.first /= jobs[(size_t)o.second].nitem;
   std::stable_sort(order.begin(), order.end(),
                    [](const std::pair<double, int> &a, const std::pair<double, int> &b) { return a.first > b.first; });
   int nitems = 0;
