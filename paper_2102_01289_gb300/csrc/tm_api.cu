@@ -836,7 +836,7 @@ size_t backward_bytes(const tm_params &p, int W, int H) {
   const size_t N = (size_t)W * H, plane = (size_t)(W + 1) * (H + 1);
   const int nf = p.n_fields;
   return align256(sizeof(BwdAcc)) + 2 * align256(4 * N * nf) + align256(4 * N) +
-         align256(8 * plane * 2 * nf) + 8 * hist_scratch_elems(W, H, 2 * nf);
+         align256(8 * plane * 2 * nf) + 8 * fix_integral_scratch_elems(W, H, nf);
 }
 
 // tm_backward / tm_backward_batch: validate, recompute the forward of every

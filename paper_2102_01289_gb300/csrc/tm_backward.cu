@@ -40,21 +40,6 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-// Largest window of field f (pixels), as a float.
-__device__ __forceinline__ float window_max(const DevParams &P, int f, int W, int H) {
-  return (float)min(2 * P.rx[f] + 1, W) * (float)min(2 * P.ry[f] + 1, H);
-}
-
-// Binary scale of a fixed-point plane whose largest |value| has bits `amax`:
-// every window sum of round(value x 2^shift) stays below 2^61 in magnitude.
-__device__ __forceinline__ int fix_shift(unsigned amax, float nmax) {
-  const float m = __uint_as_float(amax) * nmax;
-  if (!(m > 0.f) || !(m < 3.0e38f)) return 0;
-  int e;
-  frexpf(m, &e);  // m < 2^e
-  return 61 - e;
-}
-
 // Per pixel: forward recomputation, Eq. 12/3/2/4 adjoints, u_f and v_f,
 // direct gradients of the colour restoration, parameter partial sums and the
 // largest |u_f|, |v_f| (for the fixed-point scales). NF = number of fields
@@ -191,49 +176,6 @@ __global__ void __launch_bounds__(kBT) k_bwd_pixel(DevParams P, Job J, BwdJob B)
   }
 }
 
-// Row prefixes of the planes u_f (plane f) and v_f (plane s + f) in fixed
-// point into rows 1..H of 64-bit integral planes (row 0 and column 0 zero),
-// modulo 2^64. Block -> (row, plane).
-__global__ void __launch_bounds__(kBT) k_rows_fix(DevParams P, const float *__restrict__ U,
-                                                  const float *__restrict__ V, int W, int H,
-                                                  const BwdAcc *__restrict__ acc,
-                                                  unsigned long long *__restrict__ dst) {
-  __shared__ unsigned long long wt[kWarpsB];
-  const int s = P.n_fields;
-  const int y = blockIdx.x, pl = blockIdx.y, f = pl < s ? pl : pl - s;
-  const long long W1 = (long long)W + 1, plane = W1 * ((long long)H + 1), N = (long long)W * H;
-  const float *row = (pl < s ? U : V) + (long long)f * N + (long long)y * W;
-  const int sh = fix_shift(acc->amax[pl < s ? f : kMaxFields + f], window_max(P, f, W, H));
-  unsigned long long *Pl = dst + (long long)pl * plane;
-  if (y == 0)
-    for (long long x = threadIdx.x; x < W1; x += kBT) Pl[x] = 0ull;
-  unsigned long long *o = Pl + (long long)(y + 1) * W1;
-  if (threadIdx.x == 0) o[0] = 0ull;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  unsigned long long carry = 0ull;
-  for (int base = 0; base < W; base += kBT) {
-    const int x = base + threadIdx.x;
-    unsigned long long sc =
-        x < W ? (unsigned long long)__float2ll_rn(ldexpf(row[x], sh)) : 0ull;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const unsigned long long nb = __shfl_up_sync(0xffffffffu, sc, off);
-      if (lane >= off) sc += nb;
-    }
-    if (lane == 31) wt[wid] = sc;
-    __syncthreads();
-    unsigned long long before = 0ull, total = 0ull;
-#pragma unroll
-    for (int k = 0; k < kWarpsB; ++k) {
-      if (k < wid) before += wt[k];
-      total += wt[k];
-    }
-    if (x < W) o[x + 1] = carry + before + sc;
-    carry += total;
-    __syncthreads();
-  }
-}
-
 // Per pixel: the adjoint of the window variances, through the normalised log,
 // into the luminance and Eq. 11; range-term partial sums.
 template <int NF>
@@ -334,12 +276,12 @@ int launch_backward(const DevParams &P, const Job &J, const BwdJob &B, cudaStrea
 #undef TM_BWD_PIXEL
   }
   const int W = J.in.W, H = J.in.H;
-  const long long plane = ((long long)W + 1) * ((long long)H + 1);
-  // U and V integral planes are contiguous: one row pass and one segmented
-  // column pass over 2s planes
-  dim3 rg(H, 2 * P.n_fields);
-  k_rows_fix<<<rg, kBT, 0, s>>>(P, B.U, B.V, W, H, B.acc, B.IU);
-  const int nc = launch_column_pass_u64(B.IU, plane, 2 * P.n_fields, W, H, B.colscr, s);
+  // the integral planes of u_f and v_f in fixed point (IV = IU + s planes),
+  // over tiles, one (u_f, v_f) pair per grid row
+  float nmax[kMaxFields];
+  for (int f = 0; f < P.n_fields; ++f) nmax[f] = window_max(P, f, W, H);
+  const int nc = launch_fix_integrals(B.U, B.V, W, H, P.n_fields, B.acc->amax, nmax, B.IU,
+                                      reinterpret_cast<long long *>(B.colscr), s);
   switch (P.n_fields) {
 #define TM_BWD_INPUT(nf) case nf: k_bwd_input<nf><<<blocks, kBT, 0, s>>>(P, J, B); break;
     TM_BWD_INPUT(1) TM_BWD_INPUT(2) TM_BWD_INPUT(3) TM_BWD_INPUT(4) TM_BWD_INPUT(5) TM_BWD_INPUT(6)
@@ -347,7 +289,7 @@ int launch_backward(const DevParams &P, const Job &J, const BwdJob &B, cudaStrea
 #undef TM_BWD_INPUT
   }
   k_bwd_finish<<<1, 32, 0, s>>>(P, J, B);
-  return 4 + nc;
+  return 3 + nc;
 }
 
 }  // namespace tmk

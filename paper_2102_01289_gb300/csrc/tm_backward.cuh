@@ -25,7 +25,7 @@ struct BwdJob {
   float *gi_direct;    // H x W: dLoss/di through Eq. 12 directly
   unsigned long long *IU, *IV;  // fixed-point integral planes of u_f and v_f: s planes of
                                 //   (H+1) x (W+1) each, contiguous (IV = IU + s planes)
-  unsigned long long *colscr;   // column-pass segment totals, hist_scratch_elems(W, H, 2s)
+  unsigned long long *colscr;   // tile sums of the integral planes, fix_integral_scratch_elems(W, H, s)
   BwdAcc *acc;
 };
 

@@ -135,6 +135,22 @@ __device__ __forceinline__ int find_job(const Job *jobs, int njobs, int st, int 
   return lo;
 }
 
+// Largest window of field f (pixels), as a float (host and device).
+__host__ __device__ __forceinline__ float window_max(const DevParams &P, int f, int W, int H) {
+  return (float)min(2 * P.rx[f] + 1, W) * (float)min(2 * P.ry[f] + 1, H);
+}
+
+// Binary scale of a backward fixed-point plane whose largest |value| has bits
+// `amax` and whose windows hold at most nmax pixels: every window sum of
+// round(value x 2^shift) stays below 2^61 in magnitude.
+__device__ __forceinline__ int fix_shift(unsigned amax, float nmax) {
+  const float m = __uint_as_float(amax) * nmax;
+  if (!(m > 0.f) || !(m < 3.0e38f)) return 0;
+  int e;
+  frexpf(m, &e);  // m < 2^e
+  return 61 - e;
+}
+
 // Eq. 11 in float: fixed order, every product and sum rounded, no contraction.
 __device__ __forceinline__ float luminance(float r, float g, float b) {
   float i = __fadd_rn(__fadd_rn(__fmul_rn(0.2126f, r), __fmul_rn(0.7152f, g)),

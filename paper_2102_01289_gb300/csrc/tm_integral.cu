@@ -17,6 +17,7 @@
 // modular (2^64 for q sums, 2^32 for counts), so box sums (Eq. 6, Eq. 9) are
 // exact whatever the image size or summation order.
 #include <algorithm>
+#include <cstdint>
 
 #include "tm_kernels.cuh"
 
@@ -67,24 +68,62 @@ constexpr int kMidCols = 32;            // columns of a column-prefix block
 constexpr int kMidGroups = 16;          // segment groups of a column-prefix block
 constexpr int kMidPer = 8;              // segments of a group per batch
 
-// Scratch of one job (int64): the tiles' column sums, rewritten in place by
-// the column prefix (2 planes x nseg x W), the rows' chunk totals
-// (2 x H x nchunk) and the tile totals (2 x nseg x nchunk). Row segments of
-// J.seg_rows rows, J.nseg of them.
-struct IntScratch {
+// One tiled integral task: two (H+1) x (W+1) int64 planes A and B of an
+// image (row 0 and column 0 zero), with their scratch (int64): the tiles'
+// column sums, rewritten in place by the column prefix (2 planes x nseg x W),
+// the rows' chunk totals (2 x H x nchunk) and the tile totals
+// (2 x nseg x nchunk). Row segments of seg_rows rows, nseg of them.
+struct IntTask {
+  int W, H, nseg, seg_rows, nchunk;
   long long *colsum, *rowsum, *tiletot;
-  int nseg, nchunk;
+  long long *outA, *outB;
 };
-__device__ __forceinline__ IntScratch int_scratch(const Job &J) {
-  IntScratch r;
-  const int W = J.in.W, H = J.in.H;
-  r.nseg = J.nseg;
-  r.nchunk = (W + kIC - 1) / kIC;
-  r.colsum = J.segtot;
-  r.rowsum = r.colsum + 2LL * r.nseg * W;
-  r.tiletot = r.rowsum + 2LL * H * r.nchunk;
-  return r;
+
+__device__ __forceinline__ IntTask int_task(int W, int H, int nseg, int seg_rows, long long *scratch,
+                                            long long *outA, long long *outB) {
+  IntTask t;
+  t.W = W;
+  t.H = H;
+  t.nseg = nseg;
+  t.seg_rows = seg_rows;
+  t.nchunk = (W + kIC - 1) / kIC;
+  t.colsum = scratch;
+  t.rowsum = t.colsum + 2LL * nseg * W;
+  t.tiletot = t.rowsum + 2LL * H * t.nchunk;
+  t.outA = outA;
+  t.outB = outB;
+  return t;
 }
+
+// Values of the planes: q and q^2 of the quantised log (Eq. 5 of q).
+struct QSource {
+  using Raw = int32_t;
+  const int32_t *q;
+  int W;
+  __device__ __forceinline__ Raw load(int r, int c) const { return __ldg(q + (long long)r * W + c); }
+  __device__ __forceinline__ Raw zero() const { return 0; }
+  __device__ __forceinline__ void values(Raw x, long long &a, long long &b) const {
+    a = x;
+    b = (long long)x * x;
+  }
+};
+
+// Values of the planes: two float planes in 64-bit fixed point, u x 2^sa and
+// v x 2^sb rounded to nearest.
+struct FixSource {
+  using Raw = float2;
+  const float *u, *v;
+  int W, sa, sb;
+  __device__ __forceinline__ Raw load(int r, int c) const {
+    const long long o = (long long)r * W + c;
+    return make_float2(__ldg(u + o), __ldg(v + o));
+  }
+  __device__ __forceinline__ Raw zero() const { return make_float2(0.f, 0.f); }
+  __device__ __forceinline__ void values(Raw x, long long &a, long long &b) const {
+    a = __float2ll_rn(ldexpf(x.x, sa));
+    b = __float2ll_rn(ldexpf(x.y, sb));
+  }
+};
 
 // Exclusive block scan of a pair of values with one set of barriers.
 __device__ __forceinline__ void block_scan_pair(long long v1, long long v2, long long (*wt)[kINT / 32],
@@ -112,23 +151,26 @@ __device__ __forceinline__ void block_scan_pair(long long v1, long long v2, long
   __syncthreads();  // wt is rewritten by the next scan
 }
 
-// The thread's kItems strided elements (i = threadIdx.x + m kINT) of a row's
-// chunk; 0 past the chunk's nc columns.
-__device__ __forceinline__ void load_chunk_row(const int32_t *__restrict__ row, int nc, int32_t *v) {
+// The thread's kItems strided raw elements (i = threadIdx.x + m kINT) of
+// chunk [C0, C0 + nc) of row r; zero past the chunk.
+template <class Src>
+__device__ __forceinline__ void load_chunk_row(const Src &src, int r, int C0, int nc, typename Src::Raw *v) {
 #pragma unroll
   for (int m = 0; m < kItems; ++m) {
     const int i = threadIdx.x + m * kINT;
-    v[m] = i < nc ? __ldg(row + i) : 0;
+    v[m] = i < nc ? src.load(r, C0 + i) : src.zero();
   }
 }
 
-// Chunk-local row prefixes of q and q^2 of one row, given the thread's
-// strided elements of it (load_chunk_row): thread-local running sums of its
-// kItems consecutive columns (l1, l2) and the exclusive offsets of the thread
-// (e1, e2); t1, t2 are the row's chunk totals. The row goes through shared
-// memory so that the loads were coalesced and each thread scans consecutive
-// columns.
-__device__ __forceinline__ void chunk_row_prefix(const int32_t *v, int32_t *tile, long long (*wt)[kINT / 32],
+// Chunk-local row prefixes of planes A and B of one row, given the thread's
+// strided raw elements of it (load_chunk_row): thread-local running sums of
+// its kItems consecutive columns (l1, l2) and the exclusive offsets of the
+// thread (e1, e2); t1, t2 are the row's chunk totals. The row goes through
+// shared memory so that the loads were coalesced and each thread scans
+// consecutive columns.
+template <class Src>
+__device__ __forceinline__ void chunk_row_prefix(const Src &src, const typename Src::Raw *v,
+                                                 typename Src::Raw *tile, long long (*wt)[kINT / 32],
                                                  long long *l1, long long *l2, long long &e1, long long &e2,
                                                  long long &t1, long long &t2) {
 #pragma unroll
@@ -137,37 +179,33 @@ __device__ __forceinline__ void chunk_row_prefix(const int32_t *v, int32_t *tile
   long long a1 = 0, a2 = 0;
 #pragma unroll
   for (int k = 0; k < kItems; ++k) {
-    const long long x = tile[threadIdx.x * 9 + k];
-    a1 += x;
-    a2 += x * x;
+    long long x1, x2;
+    src.values(tile[threadIdx.x * 9 + k], x1, x2);
+    a1 += x1;
+    a2 += x2;
     l1[k] = a1;
     l2[k] = a2;
   }
   block_scan_pair(a1, a2, wt, e1, e2, t1, t2);  // its barriers also order the tile's reuse
 }
 
-// Launch 1: per tile, the column sums of the chunk-local row prefixes, the
-// rows' chunk totals and the tile totals.
-__global__ void __launch_bounds__(kINT, 4) k_int_stats(const Job *__restrict__ jobs, int njobs) {
-  __shared__ int32_t tile[kIC / 8 * 9];
-  __shared__ long long wt[2][kINT / 32];
-  const int j = find_job(jobs, njobs, kStRows, blockIdx.x);
-  const Job &J = jobs[j];
-  const int W = J.in.W, H = J.in.H;
-  const IntScratch X = int_scratch(J);
-  const int lb = blockIdx.x - J.b0[kStRows];
-  const int seg = lb / X.nchunk, k = lb - seg * X.nchunk;
-  const int R0 = seg * J.seg_rows, R1 = min(R0 + J.seg_rows, H), C0 = k * kIC, nc = min(kIC, W - C0);
+// Launch 1: per tile (seg, k), the column sums of the chunk-local row
+// prefixes, the rows' chunk totals and the tile totals.
+template <class Src>
+__device__ __forceinline__ void int_stats_tile(const IntTask &X, const Src &src, int seg, int k,
+                                               typename Src::Raw *tile, long long (*wt)[kINT / 32]) {
+  const int W = X.W, H = X.H;
+  const int R0 = seg * X.seg_rows, R1 = min(R0 + X.seg_rows, H), C0 = k * kIC, nc = min(kIC, W - C0);
   long long acc1[kItems], acc2[kItems];
 #pragma unroll
   for (int i = 0; i < kItems; ++i) acc1[i] = acc2[i] = 0;
   long long T1 = 0, T2 = 0;
-  int32_t cur[kItems], nxt[kItems];
-  load_chunk_row(J.q + (long long)R0 * W + C0, nc, cur);
+  typename Src::Raw cur[kItems], nxt[kItems];
+  load_chunk_row(src, R0, C0, nc, cur);
   for (int r = R0; r < R1; ++r) {
-    if (r + 1 < R1) load_chunk_row(J.q + (long long)(r + 1) * W + C0, nc, nxt);  // in flight meanwhile
+    if (r + 1 < R1) load_chunk_row(src, r + 1, C0, nc, nxt);  // in flight meanwhile
     long long l1[kItems], l2[kItems], e1, e2, t1, t2;
-    chunk_row_prefix(cur, tile, wt, l1, l2, e1, e2, t1, t2);
+    chunk_row_prefix(src, cur, tile, wt, l1, l2, e1, e2, t1, t2);
 #pragma unroll
     for (int m = 0; m < kItems; ++m) cur[m] = nxt[m];
 #pragma unroll
@@ -196,32 +234,28 @@ __global__ void __launch_bounds__(kINT, 4) k_int_stats(const Job *__restrict__ j
   }
 }
 
-// Launch 2: per column c (of q), replace each segment's column sum by the
-// plane value just above the segment: the sum, over the segments above, of
-// their column sums plus the totals of their chunks left of c's chunk. A
-// block covers kMidCols columns of one chunk; its kMidGroups groups take
-// kMidPer consecutive segments each per batch, with all loads of a batch in
-// flight together.
-__global__ void __launch_bounds__(kMidCols * kMidGroups) k_int_mid(const Job *__restrict__ jobs, int njobs) {
-  constexpr int kBatch = kMidGroups * kMidPer;
-  __shared__ long long part[2][kMidGroups][kMidCols];
-  __shared__ long long leftT[2][kBatch];
-  const int j = find_job(jobs, njobs, kStCols, blockIdx.x);
-  const Job &J = jobs[j];
-  const int W = J.in.W;
-  const IntScratch X = int_scratch(J);
+// Launch 2: for columns c0 .. c0 + kMidCols - 1 (of the image, one chunk),
+// replace each segment's column sum by the plane value just above the
+// segment: the sum, over the segments above, of their column sums plus the
+// totals of their chunks left of c's chunk. The block's kMidGroups groups
+// take kMidPer consecutive segments each per batch, with all loads of a batch
+// in flight together.
+constexpr int kMidBatch = kMidGroups * kMidPer;
+__device__ __forceinline__ void int_mid_cols(const IntTask &X, int c0, long long (*part)[kMidGroups][kMidCols],
+                                             long long (*leftT)[kMidBatch]) {
+  const int W = X.W;
   const int lane = threadIdx.x % kMidCols, g = threadIdx.x / kMidCols;
-  const int c0 = (blockIdx.x - J.b0[kStCols]) * kMidCols, c = c0 + lane;
+  const int c = c0 + lane;
   const int k = c0 / kIC;  // the block's chunk (kMidCols divides kIC)
   long long carry1 = 0, carry2 = 0;
-  for (int sb = 0; sb < X.nseg; sb += kBatch) {
+  for (int sb = 0; sb < X.nseg; sb += kMidBatch) {
     // totals of the batch's segments over the chunks left of k
-    for (int t = threadIdx.x; t < 2 * kBatch; t += kMidCols * kMidGroups) {
-      const int pl = t / kBatch, s = sb + t % kBatch;
+    for (int t = threadIdx.x; t < 2 * kMidBatch; t += kMidCols * kMidGroups) {
+      const int pl = t / kMidBatch, s = sb + t % kMidBatch;
       long long v = 0;
       if (s < X.nseg)
         for (int kk = 0; kk < k; ++kk) v += X.tiletot[((long long)pl * X.nseg + s) * X.nchunk + kk];
-      leftT[pl][t % kBatch] = v;
+      leftT[pl][t % kMidBatch] = v;
     }
     __syncthreads();
     const int s0 = sb + g * kMidPer;
@@ -264,21 +298,16 @@ __global__ void __launch_bounds__(kMidCols * kMidGroups) k_int_mid(const Job *__
 
 // Launch 3: per tile, the full row prefixes (chunk-local prefix plus the
 // row's totals of the chunks to the left) accumulated down the tile from the
-// value above it, written to rows 1..H, columns 1..W of s1 / s2; tiles of the
-// first segment also write row 0, tiles of the first chunk column 0.
-__global__ void __launch_bounds__(kINT, 4) k_int_write(const Job *__restrict__ jobs, int njobs) {
-  __shared__ int32_t tile[kIC / 8 * 9];
-  __shared__ long long out1[kIC / 8 * 9], out2[kIC / 8 * 9];
-  __shared__ long long wt[2][kINT / 32];
-  const int j = find_job(jobs, njobs, kStRows, blockIdx.x);
-  const Job &J = jobs[j];
-  const int W = J.in.W, H = J.in.H;
+// value above it, written to rows 1..H, columns 1..W of planes A and B; tiles
+// of the first segment also write row 0, tiles of the first chunk column 0.
+template <class Src>
+__device__ __forceinline__ void int_write_tile(const IntTask &X, const Src &src, int seg, int k,
+                                               typename Src::Raw *tile, long long *out1, long long *out2,
+                                               long long (*wt)[kINT / 32]) {
+  const int W = X.W, H = X.H;
   const long long W1 = (long long)W + 1;
-  const IntScratch X = int_scratch(J);
-  const int lb = blockIdx.x - J.b0[kStRows];
-  const int seg = lb / X.nchunk, k = lb - seg * X.nchunk;
-  const int R0 = seg * J.seg_rows, R1 = min(R0 + J.seg_rows, H), C0 = k * kIC, nc = min(kIC, W - C0);
-  long long *s1 = J.s1, *s2 = J.s2;
+  const int R0 = seg * X.seg_rows, R1 = min(R0 + X.seg_rows, H), C0 = k * kIC, nc = min(kIC, W - C0);
+  long long *s1 = X.outA, *s2 = X.outB;
   if (seg == 0) {
     for (int i = threadIdx.x; i < nc; i += kINT) s1[C0 + 1 + i] = 0, s2[C0 + 1 + i] = 0;
     if (k == 0 && threadIdx.x == 0) s1[0] = 0, s2[0] = 0;
@@ -292,17 +321,17 @@ __global__ void __launch_bounds__(kINT, 4) k_int_write(const Job *__restrict__ j
     acc1[i] = c < W ? X.colsum[(long long)seg * W + c] : 0;
     acc2[i] = c < W ? X.colsum[((long long)X.nseg + seg) * W + c] : 0;
   }
-  int32_t cur[kItems], nxt[kItems];
-  load_chunk_row(J.q + (long long)R0 * W + C0, nc, cur);
+  typename Src::Raw cur[kItems], nxt[kItems];
+  load_chunk_row(src, R0, C0, nc, cur);
   for (int r = R0; r < R1; ++r) {
-    if (r + 1 < R1) load_chunk_row(J.q + (long long)(r + 1) * W + C0, nc, nxt);  // in flight meanwhile
+    if (r + 1 < R1) load_chunk_row(src, r + 1, C0, nc, nxt);  // in flight meanwhile
     long long L1 = 0, L2 = 0;  // the row's totals of the chunks to the left
     for (int kk = 0; kk < k; ++kk) {
       L1 += X.rowsum[(long long)r * X.nchunk + kk];
       L2 += X.rowsum[((long long)H + r) * X.nchunk + kk];
     }
     long long l1[kItems], l2[kItems], e1, e2, t1, t2;
-    chunk_row_prefix(cur, tile, wt, l1, l2, e1, e2, t1, t2);
+    chunk_row_prefix(src, cur, tile, wt, l1, l2, e1, e2, t1, t2);
 #pragma unroll
     for (int m = 0; m < kItems; ++m) cur[m] = nxt[m];
 #pragma unroll
@@ -320,6 +349,91 @@ __global__ void __launch_bounds__(kINT, 4) k_int_write(const Job *__restrict__ j
     }
     __syncthreads();  // out1 / out2 are rewritten by the next row
   }
+}
+
+// The q integrals of a batch of jobs: block -> job through the batched stage
+// offsets, then the job's tile or column block.
+__device__ __forceinline__ IntTask job_task(const Job &J) {
+  return int_task(J.in.W, J.in.H, J.nseg, J.seg_rows, J.segtot, J.s1, J.s2);
+}
+
+__global__ void __launch_bounds__(kINT, 4) k_int_stats(const Job *__restrict__ jobs, int njobs) {
+  __shared__ int32_t tile[kIC / 8 * 9];
+  __shared__ long long wt[2][kINT / 32];
+  const Job &J = jobs[find_job(jobs, njobs, kStRows, blockIdx.x)];
+  const IntTask X = job_task(J);
+  const int lb = blockIdx.x - J.b0[kStRows];
+  const QSource src{J.q, J.in.W};
+  int_stats_tile(X, src, lb / X.nchunk, lb % X.nchunk, tile, wt);
+}
+
+__global__ void __launch_bounds__(kMidCols * kMidGroups) k_int_mid(const Job *__restrict__ jobs, int njobs) {
+  __shared__ long long part[2][kMidGroups][kMidCols];
+  __shared__ long long leftT[2][kMidBatch];
+  const Job &J = jobs[find_job(jobs, njobs, kStCols, blockIdx.x)];
+  int_mid_cols(job_task(J), (blockIdx.x - J.b0[kStCols]) * kMidCols, part, leftT);
+}
+
+__global__ void __launch_bounds__(kINT, 4) k_int_write(const Job *__restrict__ jobs, int njobs) {
+  __shared__ int32_t tile[kIC / 8 * 9];
+  __shared__ long long out1[kIC / 8 * 9], out2[kIC / 8 * 9];
+  __shared__ long long wt[2][kINT / 32];
+  const Job &J = jobs[find_job(jobs, njobs, kStRows, blockIdx.x)];
+  const IntTask X = job_task(J);
+  const int lb = blockIdx.x - J.b0[kStRows];
+  const QSource src{J.q, J.in.W};
+  int_write_tile(X, src, lb / X.nchunk, lb % X.nchunk, tile, out1, out2, wt);
+}
+
+// The fixed-point integral planes of float plane pairs (u_p, v_p), p =
+// blockIdx.y: plane p of `u` and of `v` (each W x H), scaled by
+// 2^fix_shift(amax[p], nmax[p]) and 2^fix_shift(amax[kMaxFields + p], nmax[p])
+// (the scales the backward converts back with), into planes p and np + p of
+// `dst`; scratch per pair.
+struct FixPairs {
+  const float *u, *v;
+  const unsigned *amax;  // device: float bits of the largest |u_p| (p) and |v_p| (kMaxFields + p)
+  unsigned long long *dst;
+  long long *scratch;
+  size_t scratch_stride;
+  int W, H, nseg, seg_rows, np;
+  float nmax[kMaxFields];
+};
+
+__device__ __forceinline__ IntTask fix_task(const FixPairs &F, int p) {
+  const long long plane = ((long long)F.W + 1) * ((long long)F.H + 1);
+  long long *d = reinterpret_cast<long long *>(F.dst);
+  return int_task(F.W, F.H, F.nseg, F.seg_rows, F.scratch + (long long)p * F.scratch_stride, d + p * plane,
+                  d + (F.np + p) * plane);
+}
+
+__device__ __forceinline__ FixSource fix_source(const FixPairs &F, int p) {
+  const long long N = (long long)F.W * F.H;
+  return FixSource{F.u + p * N, F.v + p * N, F.W, fix_shift(__ldg(F.amax + p), F.nmax[p]),
+                   fix_shift(__ldg(F.amax + kMaxFields + p), F.nmax[p])};
+}
+
+__global__ void __launch_bounds__(kINT, 4) k_fix_stats(FixPairs F) {
+  __shared__ float2 tile[kIC / 8 * 9];
+  __shared__ long long wt[2][kINT / 32];
+  const int p = blockIdx.y;
+  const IntTask X = fix_task(F, p);
+  int_stats_tile(X, fix_source(F, p), blockIdx.x / X.nchunk, blockIdx.x % X.nchunk, tile, wt);
+}
+
+__global__ void __launch_bounds__(kMidCols * kMidGroups) k_fix_mid(FixPairs F) {
+  __shared__ long long part[2][kMidGroups][kMidCols];
+  __shared__ long long leftT[2][kMidBatch];
+  int_mid_cols(fix_task(F, blockIdx.y), blockIdx.x * kMidCols, part, leftT);
+}
+
+__global__ void __launch_bounds__(kINT, 4) k_fix_write(FixPairs F) {
+  __shared__ float2 tile[kIC / 8 * 9];
+  __shared__ long long out1[kIC / 8 * 9], out2[kIC / 8 * 9];
+  __shared__ long long wt[2][kINT / 32];
+  const int p = blockIdx.y;
+  const IntTask X = fix_task(F, p);
+  int_write_tile(X, fix_source(F, p), blockIdx.x / X.nchunk, blockIdx.x % X.nchunk, tile, out1, out2, wt);
 }
 
 // Row prefixes of bin indicators (Eq. 7) into rows 1..H of each plane.
@@ -442,19 +556,46 @@ int integral_tile_blocks(int W, int nseg) { return nseg * ((W + kIC - 1) / kIC);
 
 int integral_col_blocks(int W) { return (W + kMidCols - 1) / kMidCols; }
 
+// Row segments of the fixed-point pairs: short enough for about 2048 tiles
+// over all pairs (the planes of a backward image are small), 4 to kIR rows.
+static void fix_layout(int W, int H, int pairs, int &nseg, int &seg_rows) {
+  const long long tiles_per_row = (long long)pairs * ((W + kIC - 1) / kIC);
+  seg_rows = (int)std::min<long long>(kIR, std::max<long long>(4, H * tiles_per_row / 2048));
+  nseg = (H + seg_rows - 1) / seg_rows;
+}
+
+size_t fix_integral_scratch_elems(int W, int H, int pairs) {
+  int nseg, seg_rows;
+  fix_layout(W, H, pairs, nseg, seg_rows);
+  return (size_t)pairs * integral_scratch_elems(W, H, nseg);
+}
+
+int launch_fix_integrals(const float *u, const float *v, int W, int H, int pairs, const unsigned *amax,
+                         const float *nmax, unsigned long long *dst, long long *scratch, cudaStream_t s) {
+  FixPairs F{};
+  F.u = u;
+  F.v = v;
+  F.amax = amax;
+  F.dst = dst;
+  F.W = W;
+  F.H = H;
+  F.np = pairs;
+  fix_layout(W, H, pairs, F.nseg, F.seg_rows);
+  F.scratch = scratch;
+  F.scratch_stride = integral_scratch_elems(W, H, F.nseg);
+  for (int i = 0; i < pairs; ++i) F.nmax[i] = nmax[i];
+  const dim3 tiles(integral_tile_blocks(W, F.nseg), pairs), cols(integral_col_blocks(W), pairs);
+  k_fix_stats<<<tiles, kINT, 0, s>>>(F);
+  k_fix_mid<<<cols, kMidCols * kMidGroups, 0, s>>>(F);
+  k_fix_write<<<tiles, kINT, 0, s>>>(F);
+  return 3;
+}
+
 int launch_integral_jobs(const Job *jobs, int njobs, int tile_blocks, int col_blocks, cudaStream_t s) {
   k_int_stats<<<tile_blocks, kINT, 0, s>>>(jobs, njobs);
   k_int_mid<<<col_blocks, kMidCols * kMidGroups, 0, s>>>(jobs, njobs);
   k_int_write<<<tile_blocks, kINT, 0, s>>>(jobs, njobs);
   return 3;
-}
-
-int launch_column_pass_u64(unsigned long long *base, long long plane_stride, int planes, int W, int H,
-                           unsigned long long *scratch, cudaStream_t s) {
-  int nseg, seg_rows;
-  segments(W + 1, H, planes, nseg, seg_rows);
-  column_pass<unsigned long long>(base, plane_stride, planes, W, H, scratch, s);
-  return nseg > 1 ? 2 : 1;
 }
 
 size_t hist_scratch_elems(int W, int H, int planes) {

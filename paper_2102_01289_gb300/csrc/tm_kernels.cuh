@@ -31,17 +31,20 @@ int integral_tile_blocks(int W, int nseg);
 int integral_col_blocks(int W);
 int launch_integral_jobs(const Job *jobs, int njobs, int tile_blocks, int col_blocks, cudaStream_t s);
 
+// Integral planes (64-bit fixed point) of `pairs` float plane pairs (u_p,
+// v_p), each W x H, over the same tiles: u_p scaled by 2^fix_shift(amax[p],
+// nmax[p]) into plane p of dst, v_p by 2^fix_shift(amax[kMaxFields + p],
+// nmax[p]) into plane pairs + p; amax on the device, nmax on the host.
+// scratch: fix_integral_scratch_elems(W, H, pairs) int64. Returns launches.
+size_t fix_integral_scratch_elems(int W, int H, int pairs);
+int launch_fix_integrals(const float *u, const float *v, int W, int H, int pairs, const unsigned *amax,
+                         const float *nmax, unsigned long long *dst, long long *scratch, cudaStream_t s);
+
 // Stage a3 (Eq. 7-8), materialised: integral histogram planes,
 // (H+1) x (W+1) uint32 each. cumulative = true: planes k = 1..n-1 hold the
 // integral of [b < k]; cumulative = false: planes k = 0..n-1 the integral of
 // [b == k]. `scratch` holds at least hist_scratch_elems(W, H, planes).
 size_t hist_scratch_elems(int W, int H, int planes);
-// In-place column prefix sums (modulo 2^64) of `planes` 64-bit planes of
-// (H+1) x (W+1) whose row 0 is zero and whose rows hold row prefixes;
-// `scratch` holds at least hist_scratch_elems(W, H, planes) elements.
-// Returns the number of launches.
-int launch_column_pass_u64(unsigned long long *base, long long plane_stride, int planes, int W, int H,
-                           unsigned long long *scratch, cudaStream_t s);
 int launch_integral_histogram(const uint8_t *bins, int W, int H, int n_bins, bool cumulative,
                               uint32_t *planes, uint32_t *scratch, cudaStream_t s);
 
