@@ -173,13 +173,14 @@ tm_status tm_forward_host_async(tm_ctx *ctx, const tm_image *in_host,
 
 /* Forward over n images of possibly different sizes: one launch per stage for
  * the whole batch, the fused sweep as one persistent launch over a shared
- * queue of (image, tile) items. in[i], out[i] as for tm_forward (host arrays
- * of descriptors; the pixel data is on the device). n == 0 is a no-op. The
- * launch sequence is captured in a CUDA graph and replayed while the same
- * descriptors (pointers, sizes, pitches, dtypes) are passed; a replay reads
- * the current pixel contents. If the fused sweep does not fit the fields, the
- * images are processed one by one as by tm_forward. Results are bit-identical
- * to per-image tm_forward calls on the fused path. */
+ * queue of (image, strip, rows) tiles planned on the device. in[i], out[i]
+ * as for tm_forward (host arrays of descriptors; the pixel data is on the
+ * device). n == 0 is a no-op. The launch sequence is captured in a CUDA
+ * graph and replayed while the same descriptors (pointers, sizes, pitches,
+ * dtypes) are passed; a replay reads the current pixel contents. If the
+ * fused sweep does not fit the fields, the images are processed one by one
+ * as by tm_forward. Results are bit-identical to per-image tm_forward calls
+ * on the fused path. */
 tm_status tm_forward_batch(tm_ctx *ctx, int32_t n, const tm_image *in,
                            const tm_image *out, void *stream);
 
