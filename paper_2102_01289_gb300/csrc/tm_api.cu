@@ -450,7 +450,7 @@ tm_status forward_materialised(tm_ctx *c, const tm_image *in, const tm_image *ou
   if (c->p.n_bins > 1) {
     total = off_cpl + align256(4 * plane * (size_t)(c->p.n_bins - 1));
     off_hscr = total;
-    total += align256(4 * hist_scratch_elems(W, H, c->p.n_bins - 1));
+    total += align256(hist_scratch_bytes(W, H, c->p.n_bins - 1));
   }
   tm_status st;
   if ((st = ensure_stats(c, 1))) return st;
@@ -501,8 +501,7 @@ tm_status forward_materialised(tm_ctx *c, const tm_image *in, const tm_image *ou
   uint32_t *cpl = nullptr;
   if (c->p.n_bins > 1) {
     cpl = reinterpret_cast<uint32_t *>(ws + off_cpl);
-    n += launch_integral_histogram(J.bins, W, H, c->p.n_bins, true, cpl,
-                                   reinterpret_cast<uint32_t *>(ws + off_hscr), s);
+    n += launch_integral_histogram(J.bins, W, H, c->p.n_bins, true, cpl, ws + off_hscr, s);
   }
   mark(c, s, ST_HIST);
   n += launch_lookup_materialised(J.in, J.out, P, J.bins, cpl, reinterpret_cast<int64_t *>(J.s1),
@@ -1220,10 +1219,10 @@ tm_status tm_integral_histogram(const uint8_t *bins, int32_t width, int32_t heig
     return fail(nullptr, TM_EINVAL, "tm_integral_histogram: n_bins outside 1..256");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   void *scr = nullptr;
-  size_t bytes = 4 * hist_scratch_elems(width, height, n_bins);
+  size_t bytes = hist_scratch_bytes(width, height, n_bins);
   cudaError_t e = cudaMallocAsync(&scr, bytes, st);
   if (e != cudaSuccess) { cudaGetLastError(); return fail(nullptr, TM_ENOMEM, "tm_integral_histogram: scratch"); }
-  launch_integral_histogram(bins, width, height, n_bins, false, hk, static_cast<uint32_t *>(scr), st);
+  launch_integral_histogram(bins, width, height, n_bins, false, hk, scr, st);
   e = cudaGetLastError();
   cudaFreeAsync(scr, st);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "tm_integral_histogram");

@@ -9,13 +9,12 @@
 //      plane just above each segment);
 //   3. per tile: the row prefixes again, offset by the chunks to the left, and
 //      accumulated down the tile from the column's offset, written once.
-// The integral histograms (and the backward's fixed-point planes) use a row
-// pass (block-wide scans, warp shuffles inside each warp) into an (H+1) x
-// (W+1) plane with a zero first row and column, then a column pass split into
-// row segments: a first kernel sums each segment, a second one adds the sums
-// of the segments above and scans its own segment. Integer arithmetic is
-// modular (2^64 for q sums, 2^32 for counts), so box sums (Eq. 6, Eq. 9) are
-// exact whatever the image size or summation order.
+// The same tile kernels, templated on the source of their two planes, build
+// the backward's fixed-point integral planes of (u_f, v_f) and the integral
+// histograms (indicator planes of the bin map, two thresholds per tile
+// task). Integer arithmetic is modular (2^64 in the sums, 2^32 in the
+// histogram planes), so box sums (Eq. 6, Eq. 9) are exact whatever the image
+// size or summation order.
 #include <algorithm>
 #include <cstdint>
 
@@ -24,36 +23,7 @@
 namespace tmk {
 namespace {
 
-template <typename T, int NT>
-__device__ __forceinline__ T block_exclusive_scan(T v, T *warp_tot, T &total) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  T x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    T y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) warp_tot[wid] = x;
-  __syncthreads();
-  if (wid == 0) {
-    T w = lane < NT / 32 ? warp_tot[lane] : T(0);
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      T y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += y;
-    }
-    if (lane < NT / 32) warp_tot[lane] = w;
-  }
-  __syncthreads();
-  T before = wid > 0 ? warp_tot[wid - 1] : T(0);
-  total = warp_tot[NT / 32 - 1];
-  __syncthreads();
-  return before + x - v;
-}
-
-constexpr int kNT = 256;
-constexpr int kItems = 8;
-constexpr int kTile = kNT * kItems;
+constexpr int kItems = 8;  // consecutive columns per thread in a tile row
 
 // Rows go through shared memory so that global accesses are coalesced while
 // each thread scans eight consecutive elements; the shared layouts are padded
@@ -76,11 +46,9 @@ constexpr int kMidPer = 8;              // segments of a group per batch
 struct IntTask {
   int W, H, nseg, seg_rows, nchunk;
   long long *colsum, *rowsum, *tiletot;
-  long long *outA, *outB;
 };
 
-__device__ __forceinline__ IntTask int_task(int W, int H, int nseg, int seg_rows, long long *scratch,
-                                            long long *outA, long long *outB) {
+__device__ __forceinline__ IntTask int_task(int W, int H, int nseg, int seg_rows, long long *scratch) {
   IntTask t;
   t.W = W;
   t.H = H;
@@ -90,8 +58,6 @@ __device__ __forceinline__ IntTask int_task(int W, int H, int nseg, int seg_rows
   t.colsum = scratch;
   t.rowsum = t.colsum + 2LL * nseg * W;
   t.tiletot = t.rowsum + 2LL * H * t.nchunk;
-  t.outA = outA;
-  t.outB = outB;
   return t;
 }
 
@@ -122,6 +88,20 @@ struct FixSource {
   __device__ __forceinline__ void values(Raw x, long long &a, long long &b) const {
     a = __float2ll_rn(ldexpf(x.x, sa));
     b = __float2ll_rn(ldexpf(x.y, sb));
+  }
+};
+
+// Values of the planes: indicators of a bin map for thresholds k0 and k0 + 1,
+// [b < k] (cumulative) or [b == k]; raw -1 stands for no pixel.
+struct BinSource {
+  using Raw = int;
+  const uint8_t *bins;
+  int W, k0, eq;
+  __device__ __forceinline__ Raw load(int r, int c) const { return __ldg(bins + (long long)r * W + c); }
+  __device__ __forceinline__ Raw zero() const { return -1; }
+  __device__ __forceinline__ void values(Raw x, long long &a, long long &b) const {
+    a = x >= 0 && (eq ? x == k0 : x < k0);
+    b = x >= 0 && (eq ? x == k0 + 1 : x < k0 + 1);
   }
 };
 
@@ -298,22 +278,32 @@ __device__ __forceinline__ void int_mid_cols(const IntTask &X, int c0, long long
 
 // Launch 3: per tile, the full row prefixes (chunk-local prefix plus the
 // row's totals of the chunks to the left) accumulated down the tile from the
-// value above it, written to rows 1..H, columns 1..W of planes A and B; tiles
-// of the first segment also write row 0, tiles of the first chunk column 0.
-template <class Src>
-__device__ __forceinline__ void int_write_tile(const IntTask &X, const Src &src, int seg, int k,
-                                               typename Src::Raw *tile, long long *out1, long long *out2,
+// value above it, written to rows 1..H, columns 1..W of planes s1 and s2 (as
+// OutT, modulo its range; s2 may be null); tiles of the first segment also
+// write row 0, tiles of the first chunk column 0.
+template <class Src, class OutT>
+__device__ __forceinline__ void int_write_tile(const IntTask &X, const Src &src, OutT *s1, OutT *s2, int seg,
+                                               int k, typename Src::Raw *tile, long long *out1, long long *out2,
                                                long long (*wt)[kINT / 32]) {
   const int W = X.W, H = X.H;
   const long long W1 = (long long)W + 1;
   const int R0 = seg * X.seg_rows, R1 = min(R0 + X.seg_rows, H), C0 = k * kIC, nc = min(kIC, W - C0);
-  long long *s1 = X.outA, *s2 = X.outB;
+  const bool two = s2 != nullptr;
   if (seg == 0) {
-    for (int i = threadIdx.x; i < nc; i += kINT) s1[C0 + 1 + i] = 0, s2[C0 + 1 + i] = 0;
-    if (k == 0 && threadIdx.x == 0) s1[0] = 0, s2[0] = 0;
+    for (int i = threadIdx.x; i < nc; i += kINT) {
+      s1[C0 + 1 + i] = 0;
+      if (two) s2[C0 + 1 + i] = 0;
+    }
+    if (k == 0 && threadIdx.x == 0) {
+      s1[0] = 0;
+      if (two) s2[0] = 0;
+    }
   }
   if (k == 0)
-    for (int r = R0 + (int)threadIdx.x; r < R1; r += kINT) s1[(r + 1) * W1] = 0, s2[(r + 1) * W1] = 0;
+    for (int r = R0 + (int)threadIdx.x; r < R1; r += kINT) {
+      s1[(r + 1) * W1] = 0;
+      if (two) s2[(r + 1) * W1] = 0;
+    }
   long long acc1[kItems], acc2[kItems];
 #pragma unroll
   for (int i = 0; i < kItems; ++i) {
@@ -342,10 +332,11 @@ __device__ __forceinline__ void int_write_tile(const IntTask &X, const Src &src,
       out2[threadIdx.x * 9 + i] = acc2[i];
     }
     __syncthreads();
-    long long *o1 = s1 + (long long)(r + 1) * W1 + C0 + 1, *o2 = s2 + (long long)(r + 1) * W1 + C0 + 1;
-    for (int i = threadIdx.x; i < nc; i += kINT) {
-      o1[i] = out1[pad9(i)];
-      o2[i] = out2[pad9(i)];
+    OutT *o1 = s1 + (long long)(r + 1) * W1 + C0 + 1;
+    for (int i = threadIdx.x; i < nc; i += kINT) o1[i] = (OutT)out1[pad9(i)];
+    if (two) {
+      OutT *o2 = s2 + (long long)(r + 1) * W1 + C0 + 1;
+      for (int i = threadIdx.x; i < nc; i += kINT) o2[i] = (OutT)out2[pad9(i)];
     }
     __syncthreads();  // out1 / out2 are rewritten by the next row
   }
@@ -354,7 +345,7 @@ __device__ __forceinline__ void int_write_tile(const IntTask &X, const Src &src,
 // The q integrals of a batch of jobs: block -> job through the batched stage
 // offsets, then the job's tile or column block.
 __device__ __forceinline__ IntTask job_task(const Job &J) {
-  return int_task(J.in.W, J.in.H, J.nseg, J.seg_rows, J.segtot, J.s1, J.s2);
+  return int_task(J.in.W, J.in.H, J.nseg, J.seg_rows, J.segtot);
 }
 
 __global__ void __launch_bounds__(kINT, 4) k_int_stats(const Job *__restrict__ jobs, int njobs) {
@@ -382,7 +373,7 @@ __global__ void __launch_bounds__(kINT, 4) k_int_write(const Job *__restrict__ j
   const IntTask X = job_task(J);
   const int lb = blockIdx.x - J.b0[kStRows];
   const QSource src{J.q, J.in.W};
-  int_write_tile(X, src, lb / X.nchunk, lb % X.nchunk, tile, out1, out2, wt);
+  int_write_tile(X, src, J.s1, J.s2, lb / X.nchunk, lb % X.nchunk, tile, out1, out2, wt);
 }
 
 // The fixed-point integral planes of float plane pairs (u_p, v_p), p =
@@ -401,10 +392,7 @@ struct FixPairs {
 };
 
 __device__ __forceinline__ IntTask fix_task(const FixPairs &F, int p) {
-  const long long plane = ((long long)F.W + 1) * ((long long)F.H + 1);
-  long long *d = reinterpret_cast<long long *>(F.dst);
-  return int_task(F.W, F.H, F.nseg, F.seg_rows, F.scratch + (long long)p * F.scratch_stride, d + p * plane,
-                  d + (F.np + p) * plane);
+  return int_task(F.W, F.H, F.nseg, F.seg_rows, F.scratch + (long long)p * F.scratch_stride);
 }
 
 __device__ __forceinline__ FixSource fix_source(const FixPairs &F, int p) {
@@ -433,106 +421,55 @@ __global__ void __launch_bounds__(kINT, 4) k_fix_write(FixPairs F) {
   __shared__ long long wt[2][kINT / 32];
   const int p = blockIdx.y;
   const IntTask X = fix_task(F, p);
-  int_write_tile(X, fix_source(F, p), blockIdx.x / X.nchunk, blockIdx.x % X.nchunk, tile, out1, out2, wt);
+  const long long plane = ((long long)F.W + 1) * ((long long)F.H + 1);
+  long long *d = reinterpret_cast<long long *>(F.dst);
+  int_write_tile(X, fix_source(F, p), d + p * plane, d + (F.np + p) * plane, blockIdx.x / X.nchunk,
+                 blockIdx.x % X.nchunk, tile, out1, out2, wt);
 }
 
-// Row prefixes of bin indicators (Eq. 7) into rows 1..H of each plane.
-__global__ void __launch_bounds__(kNT) k_rows_hist(const uint8_t *__restrict__ bins, int W, int H,
-                                                   int k_begin, int n_planes, int per_block,
-                                                   int cumulative, unsigned *planes,
-                                                   long long plane_stride) {
-  __shared__ uint8_t tile[kTile];
-  __shared__ unsigned wt[kNT / 32];
-  const long long W1 = (long long)W + 1;
-  for (int y = blockIdx.x; y < H; y += gridDim.x) {
-  const uint8_t *row = bins + (long long)y * W;
-  const int p0 = blockIdx.y * per_block, p1 = min(p0 + per_block, n_planes);
-  for (int pl = p0; pl < p1; ++pl) {
-    const int k = k_begin + pl;
-    unsigned *P = planes + pl * plane_stride;
-    if (y == 0)
-      for (long long x = threadIdx.x; x < W1; x += kNT) P[x] = 0;
-    unsigned *o = P + (long long)(y + 1) * W1;
-    if (threadIdx.x == 0) o[0] = 0;
-    unsigned carry = 0;
-    for (int base = 0; base < W; base += kTile) {
-      for (int i = threadIdx.x; i < kTile; i += kNT) tile[i] = base + i < W ? row[base + i] : 0xff;
-      __syncthreads();
-      unsigned a = 0, l[kItems];
-#pragma unroll
-      for (int j = 0; j < kItems; ++j) {
-        int b = tile[threadIdx.x * kItems + j];
-        bool in_img = base + threadIdx.x * kItems + j < W;
-        a += (in_img && (cumulative ? (b < k) : (b == k))) ? 1u : 0u;
-        l[j] = a;
-      }
-      unsigned t;
-      unsigned e = block_exclusive_scan<unsigned, kNT>(a, wt, t);
-#pragma unroll
-      for (int j = 0; j < kItems; ++j) {
-        int x = base + threadIdx.x * kItems + j;
-        if (x < W) o[x + 1] = carry + e + l[j];
-      }
-      carry += t;
-      __syncthreads();
-    }
-  }
-  }
+// Integral histogram planes (uint32, modulo 2^32) of a bin map over the same
+// tiles: pair p = pair0 + blockIdx.y holds planes 2p and 2p + 1 of `planes`
+// (thresholds k_begin + 2p and + 1; the second is skipped past n_planes),
+// scratch per grid row.
+struct HistPairs {
+  const uint8_t *bins;
+  uint32_t *planes;
+  long long *scratch;
+  size_t scratch_stride;
+  int W, H, nseg, seg_rows, k_begin, n_planes, eq, pair0;
+};
+
+__device__ __forceinline__ IntTask hist_task(const HistPairs &Q) {
+  return int_task(Q.W, Q.H, Q.nseg, Q.seg_rows, Q.scratch + (long long)blockIdx.y * Q.scratch_stride);
 }
 
-// Column pass, first kernel: sum of each row segment of each column.
-template <typename T>
-__global__ void k_colsum(const T *__restrict__ base, long long plane_stride, int cols, int rows,
-                         int seg_rows, int nseg, T *segtot) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  const int seg = blockIdx.y, pl = blockIdx.z;
-  if (c >= cols) return;
-  const T *P = base + pl * plane_stride;
-  const int r0 = 1 + seg * seg_rows, r1 = min(rows, r0 + seg_rows);
-  T acc = 0;
-#pragma unroll 4
-  for (int r = r0; r < r1; ++r) acc += P[(long long)r * cols + c];
-  segtot[((long long)pl * nseg + seg) * cols + c] = acc;
+__device__ __forceinline__ BinSource hist_source(const HistPairs &Q) {
+  return BinSource{Q.bins, Q.W, Q.k_begin + 2 * (Q.pair0 + (int)blockIdx.y), Q.eq};
 }
 
-// Column pass, second kernel: offset by the segments above, scan in place.
-template <typename T>
-__global__ void k_colscan(T *base, long long plane_stride, int cols, int rows, int seg_rows,
-                          int nseg, const T *__restrict__ segtot) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  const int seg = blockIdx.y, pl = blockIdx.z;
-  if (c >= cols) return;
-  T *P = base + pl * plane_stride;
-  T acc = 0;
-  for (int s = 0; s < seg; ++s) acc += segtot[((long long)pl * nseg + s) * cols + c];
-  const int r0 = 1 + seg * seg_rows, r1 = min(rows, r0 + seg_rows);
-#pragma unroll 4
-  for (int r = r0; r < r1; ++r) {
-    acc += P[(long long)r * cols + c];
-    P[(long long)r * cols + c] = acc;
-  }
+__global__ void __launch_bounds__(kINT, 4) k_hist_stats(HistPairs Q) {
+  __shared__ int tile[kIC / 8 * 9];
+  __shared__ long long wt[2][kINT / 32];
+  const IntTask X = hist_task(Q);
+  int_stats_tile(X, hist_source(Q), blockIdx.x / X.nchunk, blockIdx.x % X.nchunk, tile, wt);
 }
 
-void segments(int cols, int H, int planes, int &nseg, int &seg_rows) {
-  long long target = 160000;
-  long long per = (long long)cols * planes;
-  nseg = (int)((target + per - 1) / per);
-  if (nseg < 1) nseg = 1;
-  if (nseg > 64) nseg = 64;
-  if (nseg > H) nseg = H;
-  seg_rows = (H + nseg - 1) / nseg;
-  nseg = (H + seg_rows - 1) / seg_rows;
+__global__ void __launch_bounds__(kMidCols * kMidGroups) k_hist_mid(HistPairs Q) {
+  __shared__ long long part[2][kMidGroups][kMidCols];
+  __shared__ long long leftT[2][kMidBatch];
+  int_mid_cols(hist_task(Q), blockIdx.x * kMidCols, part, leftT);
 }
 
-template <typename T>
-void column_pass(T *base, long long plane_stride, int planes, int W, int H, T *scratch,
-                 cudaStream_t s) {
-  const int cols = W + 1, rows = H + 1;
-  int nseg, seg_rows;
-  segments(cols, H, planes, nseg, seg_rows);
-  dim3 block(128), grid((cols + 127) / 128, nseg, planes);
-  if (nseg > 1) k_colsum<T><<<grid, block, 0, s>>>(base, plane_stride, cols, rows, seg_rows, nseg, scratch);
-  k_colscan<T><<<grid, block, 0, s>>>(base, plane_stride, cols, rows, seg_rows, nseg, scratch);
+__global__ void __launch_bounds__(kINT, 4) k_hist_write(HistPairs Q) {
+  __shared__ int tile[kIC / 8 * 9];
+  __shared__ long long out1[kIC / 8 * 9], out2[kIC / 8 * 9];
+  __shared__ long long wt[2][kINT / 32];
+  const IntTask X = hist_task(Q);
+  const long long plane = ((long long)Q.W + 1) * ((long long)Q.H + 1);
+  const int p = Q.pair0 + (int)blockIdx.y;
+  uint32_t *a = Q.planes + 2LL * p * plane;
+  uint32_t *b = 2 * p + 1 < Q.n_planes ? a + plane : nullptr;
+  int_write_tile(X, hist_source(Q), a, b, blockIdx.x / X.nchunk, blockIdx.x % X.nchunk, tile, out1, out2, wt);
 }
 
 }  // namespace
@@ -598,26 +535,42 @@ int launch_integral_jobs(const Job *jobs, int njobs, int tile_blocks, int col_bl
   return 3;
 }
 
-size_t hist_scratch_elems(int W, int H, int planes) {
+constexpr int kHistPairs = 8;  // plane pairs per launch of the histogram tiles
+
+size_t hist_scratch_bytes(int W, int H, int planes) {
   int nseg, seg_rows;
-  segments(W + 1, H, planes, nseg, seg_rows);
-  return (size_t)planes * nseg * (W + 1);
+  integral_layout(W, H, SIZE_MAX, nseg, seg_rows);
+  const int pairs = std::min((planes + 1) / 2, kHistPairs);
+  return 8 * (size_t)std::max(pairs, 1) * integral_scratch_elems(W, H, nseg);
 }
 
 int launch_integral_histogram(const uint8_t *bins, int W, int H, int n_bins, bool cumulative,
-                              uint32_t *planes, uint32_t *scratch, cudaStream_t s) {
+                              uint32_t *planes, void *scratch, cudaStream_t s) {
   const int k_begin = cumulative ? 1 : 0;
   const int n_planes = cumulative ? n_bins - 1 : n_bins;
   if (n_planes <= 0) return 0;
-  const long long stride = ((long long)W + 1) * ((long long)H + 1);
-  const int per_block = 8;
-  dim3 grid(H < 65535 ? H : 65535, (n_planes + per_block - 1) / per_block);
-  k_rows_hist<<<grid, kNT, 0, s>>>(bins, W, H, k_begin, n_planes, per_block, cumulative ? 1 : 0,
-                                   planes, stride);
-  int nseg, seg_rows;
-  segments(W + 1, H, n_planes, nseg, seg_rows);
-  column_pass<unsigned>(planes, stride, n_planes, W, H, scratch, s);
-  return 1 + (nseg > 1 ? 2 : 1);
+  HistPairs Q{};
+  Q.bins = bins;
+  Q.planes = planes;
+  Q.scratch = static_cast<long long *>(scratch);
+  Q.W = W;
+  Q.H = H;
+  integral_layout(W, H, SIZE_MAX, Q.nseg, Q.seg_rows);
+  Q.scratch_stride = integral_scratch_elems(W, H, Q.nseg);
+  Q.k_begin = k_begin;
+  Q.n_planes = n_planes;
+  Q.eq = cumulative ? 0 : 1;
+  const int pairs = (n_planes + 1) / 2;
+  int n = 0;
+  for (Q.pair0 = 0; Q.pair0 < pairs; Q.pair0 += kHistPairs) {  // groups share the scratch in turn
+    const int g = std::min(kHistPairs, pairs - Q.pair0);
+    const dim3 tiles(integral_tile_blocks(W, Q.nseg), g), cols(integral_col_blocks(W), g);
+    k_hist_stats<<<tiles, kINT, 0, s>>>(Q);
+    k_hist_mid<<<cols, kMidCols * kMidGroups, 0, s>>>(Q);
+    k_hist_write<<<tiles, kINT, 0, s>>>(Q);
+    n += 3;
+  }
+  return n;
 }
 
 }  // namespace tmk

@@ -41,12 +41,14 @@ int launch_fix_integrals(const float *u, const float *v, int W, int H, int pairs
                          const float *nmax, unsigned long long *dst, long long *scratch, cudaStream_t s);
 
 // Stage a3 (Eq. 7-8), materialised: integral histogram planes,
-// (H+1) x (W+1) uint32 each. cumulative = true: planes k = 1..n-1 hold the
-// integral of [b < k]; cumulative = false: planes k = 0..n-1 the integral of
-// [b == k]. `scratch` holds at least hist_scratch_elems(W, H, planes).
-size_t hist_scratch_elems(int W, int H, int planes);
+// (H+1) x (W+1) uint32 each (modulo 2^32, zero first row and column), over
+// the integral images' tiles, two planes per tile task. cumulative = true:
+// planes k = 1..n-1 hold the integral of [b < k]; cumulative = false: planes
+// k = 0..n-1 the integral of [b == k]. `scratch` holds at least
+// hist_scratch_bytes(W, H, planes) bytes. Returns the number of launches.
+size_t hist_scratch_bytes(int W, int H, int planes);
 int launch_integral_histogram(const uint8_t *bins, int W, int H, int n_bins, bool cumulative,
-                              uint32_t *planes, uint32_t *scratch, cudaStream_t s);
+                              uint32_t *planes, void *scratch, cudaStream_t s);
 
 // Stage a3', fused: plan of one image's sweep (false if the fields do not
 // fit), slab-count elements, and the persistent launch over a queue of
