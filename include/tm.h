@@ -160,14 +160,18 @@ tm_status tm_forward_host(tm_ctx *ctx, const tm_image *in_host,
 
 /* tm_forward_host without the synchronisation, for streams of host images:
  * in_host and out_host must be page-locked (cudaHostAlloc / cudaHostRegister;
- * TM_EINVAL otherwise). The upload runs on an internal copy stream into one
- * of two device slots used in turn, the forward on `stream` after it, and the
- * last kernel stores the result into out_host over the host link; so one
- * call's upload overlaps the previous call's forward. Returns once the work
- * is enqueued: in_host must stay unchanged and out_host unread until `stream`
- * has been synchronised. Results are identical to tm_forward_host. (Writing
- * the result to a device slot and downloading it on a third stream was
- * measured slower: concurrent uploads and downloads share the host link.) */
+ * TM_EINVAL otherwise). Call k uploads in_host into device input slot k%2 on
+ * an internal copy stream, runs the forward into device output slot k%2 on an
+ * internal forward stream, and downloads that slot into out_host on `stream`.
+ * So the upload of the next image, the forward of this one and the download
+ * of the previous one run at the same time (the host link carries uploads
+ * and downloads concurrently). Returns once the work is enqueued: in_host
+ * must stay unchanged and out_host unread until `stream` has been
+ * synchronised, which covers the upload, forward and download of every call
+ * made on it. The upload is not ordered after earlier work on `stream` (write
+ * in_host on the host). Other calls on the context wait for the pending
+ * forwards before using the workspace, and the next forward waits for them.
+ * Results are identical to tm_forward_host. */
 tm_status tm_forward_host_async(tm_ctx *ctx, const tm_image *in_host,
                                 const tm_image *out_host, void *stream);
 

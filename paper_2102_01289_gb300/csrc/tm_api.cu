@@ -22,14 +22,43 @@
 using namespace tmk;
 
 namespace {
-// Pinned host staging of one call's job array.
-struct Staging {
-  Job *jobs = nullptr;
-  size_t jobs_bytes = 0;
-  cudaEvent_t done = nullptr;  // recorded after the last copy out of this slot
-  bool pending = false;
+// Job descriptors reach the device as kernel parameters of a one-block copy
+// kernel, not through a host-to-device copy: such a copy waits on the copy
+// engine behind any large upload in flight on another stream (the next image
+// of tm_forward_host_async), which would stall the forward it starts.
+constexpr int kPutJobs = 32;  // 32 x 672-byte jobs fit the 32 KB parameter space
+template <int N>
+struct JobPack {
+  Job j[N];
 };
-constexpr int kStagingSlots = 4;
+
+template <int N>
+__global__ void k_put_jobs(const __grid_constant__ JobPack<N> p, Job *dst, int n) {
+  const unsigned *src = reinterpret_cast<const unsigned *>(p.j);
+  unsigned *d = reinterpret_cast<unsigned *>(dst);
+  const int words = n * (int)(sizeof(Job) / 4);
+  for (int i = threadIdx.x; i < words; i += blockDim.x) d[i] = src[i];
+}
+static_assert(sizeof(Job) % 4 == 0, "jobs are copied as words");
+
+// Writes jobs h[0..n) to d on stream s; returns the launches made.
+int put_jobs(const Job *h, int n, Job *d, cudaStream_t s) {
+  if (n == 1) {
+    JobPack<1> p;
+    p.j[0] = h[0];
+    k_put_jobs<1><<<1, 128, 0, s>>>(p, d, 1);
+    return 1;
+  }
+  int launches = 0;
+  for (int i = 0; i < n; i += kPutJobs) {
+    JobPack<kPutJobs> p;
+    const int m = std::min(kPutJobs, n - i);
+    std::memcpy(p.j, h + i, sizeof(Job) * (size_t)m);
+    k_put_jobs<kPutJobs><<<1, 256, 0, s>>>(p, d + i, m);
+    ++launches;
+  }
+  return launches;
+}
 }  // namespace
 
 struct tm_ctx {
@@ -45,19 +74,13 @@ struct tm_ctx {
   size_t ws_bytes = 0;
   Stats *stats = nullptr;  // one per image of the largest batch so far
   int stats_n = 0;
-  // job descriptors: pinned host staging copied to a device buffer at the
-  // start of each call (the sweep queue is written on the device). The device buffers are stream-ordered
-  // like the workspace; the host staging is not (the copy runs when the
-  // stream reaches it), so calls rotate over several staging slots and wait,
-  // before rewriting a slot, for the event recorded after its last copy.
-  // The cached batch graph has its own staging and device buffers: its copy
-  // nodes read them at every replay.
-  Staging slots[kStagingSlots];
-  int slot_next = 0;
+  // job descriptors: written to a device buffer at the start of each call by
+  // put_jobs (the sweep queue is written on the device); stream-ordered like
+  // the workspace. The cached batch graph has its own device buffers, written
+  // by its own nodes at every replay.
   Job *djobs = nullptr;    // device copy of the job array (calls outside the graph)
   int4 *ditems = nullptr;  // sweep queue: items and the pop counter
   size_t djobs_bytes = 0, ditems_bytes = 0;
-  Staging gstage;          // staging read by the cached graph
   Job *gdjobs = nullptr;   // device buffers written by the cached graph
   int4 *gditems = nullptr;
   size_t gdjobs_bytes = 0, gditems_bytes = 0;
@@ -67,13 +90,22 @@ struct tm_ctx {
   // staging for tm_forward_host
   void *stage = nullptr;
   size_t stage_bytes = 0;
-  // tm_forward_host_async: two device input slots filled on a copy stream,
-  // each guarded by the event after the forward that last read it
-  void *hslot[2] = {nullptr, nullptr};
-  size_t hslot_bytes = 0;
+  // tm_forward_host_async: call k uploads into input slot k%2 on copy_stream,
+  // runs the forward into output slot k%2 on fwd_stream and downloads that
+  // slot on the caller's stream. hslot_free/oslot_free are recorded after the
+  // last read of a slot (the forward, the download), *_full after its write.
+  void *hslot[2] = {nullptr, nullptr}, *oslot[2] = {nullptr, nullptr};
+  size_t hslot_bytes = 0, oslot_bytes = 0;
   cudaEvent_t hslot_free[2] = {nullptr, nullptr}, hslot_full[2] = {nullptr, nullptr};
-  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t oslot_free[2] = {nullptr, nullptr}, oslot_full[2] = {nullptr, nullptr};
+  cudaStream_t copy_stream = nullptr, fwd_stream = nullptr;
   int hslot_next = 0;
+  // The forwards on fwd_stream share the workspace with the calls made on the
+  // caller's streams: a call waits for fwd_done (the last forward on
+  // fwd_stream) if one is pending, and the next forward on fwd_stream waits
+  // for ext_done (recorded after the last such call).
+  cudaEvent_t fwd_done = nullptr, ext_done = nullptr;
+  bool fwd_pending = false, ext_pending = false;
   // layout of the last single-image forward (for debug exports)
   int last_W = 0, last_H = 0, last_q = 0, last_path = 0;
   uint8_t *bins = nullptr;
@@ -335,44 +367,6 @@ tm_status grow_device(tm_ctx *c, void **p, size_t *have, size_t bytes) {
   return TM_OK;
 }
 
-// Pinned host buffer of at least `bytes`; the caller has made sure no copy
-// still reads the old one.
-tm_status grow_host(tm_ctx *c, void **p, size_t *have, size_t bytes) {
-  if (*have >= bytes) return TM_OK;
-  if (*p) cudaFreeHost(*p);
-  *p = nullptr;
-  *have = 0;
-  cudaError_t e = cudaMallocHost(p, bytes);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return fail(c, TM_ENOMEM, "pinned allocation of %zu bytes: %s", bytes, cudaGetErrorString(e));
-  }
-  *have = bytes;
-  return TM_OK;
-}
-
-// A staging slot able to hold `njobs` jobs, free to be rewritten: waits for
-// the copy that last read it.
-tm_status acquire_staging(tm_ctx *c, Staging *S, int njobs) {
-  if (!S->done) TM_CUDA(c, cudaEventCreateWithFlags(&S->done, cudaEventDisableTiming));
-  if (S->pending) TM_CUDA(c, cudaEventSynchronize(S->done));
-  S->pending = false;
-  return grow_host(c, (void **)&S->jobs, &S->jobs_bytes, sizeof(Job) * std::max(njobs, 1));
-}
-
-Staging *next_slot(tm_ctx *c) {
-  Staging *S = &c->slots[c->slot_next];
-  c->slot_next = (c->slot_next + 1) % kStagingSlots;
-  return S;
-}
-
-// Event after the copies out of S on stream s.
-tm_status release_staging(tm_ctx *c, Staging *S, cudaStream_t s) {
-  TM_CUDA(c, cudaEventRecord(S->done, s));
-  S->pending = true;
-  return TM_OK;
-}
-
 Image to_image(const tm_image *im) {
   Image r;
   r.p = im->data;
@@ -456,8 +450,6 @@ tm_status forward_materialised(tm_ctx *c, const tm_image *in, const tm_image *ou
   if ((st = ensure_stats(c, 1))) return st;
   if ((st = grow_device(c, &c->ws, &c->ws_bytes, total))) return st;
   if ((st = grow_device(c, (void **)&c->djobs, &c->djobs_bytes, sizeof(Job)))) return st;
-  Staging *S = next_slot(c);
-  if ((st = acquire_staging(c, S, 1))) return st;
   char *ws = static_cast<char *>(c->ws);
   Job J{};
   J.in = to_image(in);
@@ -486,10 +478,7 @@ tm_status forward_materialised(tm_ctx *c, const tm_image *in, const tm_image *ou
   }
   const int rb = range_blocks(W, H, c->num_sms, 1.0), pb = prep_blocks(W, H, c->num_sms, 1.0);
   J.b0[kStRange] = J.b0[kStPrep] = J.b0[kStRows] = J.b0[kStCols] = J.b0[kStLook] = 0;
-  *S->jobs = J;
-  TM_CUDA(c, cudaMemcpyAsync(c->djobs, S->jobs, sizeof(Job), cudaMemcpyHostToDevice, s));
-  if ((st = release_staging(c, S, s))) return st;
-  int64_t n = 0;
+  int64_t n = put_jobs(&J, 1, c->djobs, s);
   mark(c, s, -1);
   if (run_range) launch_range(c->djobs, 1, rb, c->p.n_bins, s);
   mark(c, s, ST_RANGE);
@@ -530,7 +519,6 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   if (graph && c->graph && same_images(c->graph_in, in, nimg) && same_images(c->graph_out, out, nimg)) {
     c->fwd_valid = false;
     TM_CUDA(c, cudaGraphLaunch(c->graph, s));
-    if ((st = release_staging(c, &c->gstage, s))) return st;
     c->launches = c->graph_launches;
     c->fwd_jobs = c->graph_jobs;
     c->fwd_in.assign(in, in + nimg);
@@ -628,8 +616,6 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   if ((st = grow_device(c, (void **)ditems, graph ? &c->gditems_bytes : &c->ditems_bytes,
                         sizeof(int4) * nitems + sizeof(int))))
     return st;
-  Staging *S = graph ? &c->gstage : next_slot(c);
-  if ((st = acquire_staging(c, S, nimg))) return st;
   char *ws = static_cast<char *>(c->ws);
   for (int i = 0; i < nimg; ++i) {
     Job &J = jobs[(size_t)i];
@@ -662,7 +648,6 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
       return st;
     run_range = own;
   }
-  memcpy(S->jobs, jobs.data(), sizeof(Job) * nimg);
   const DevParams P = dev_params(c->p, jobs[0].qbits);  // qbits is per job
   Job *dj = *djobs;
   int4 *di = *ditems;
@@ -676,9 +661,7 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
     s = c->graph_stream;
     TM_CUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   }
-  cudaMemcpyAsync(dj, S->jobs, sizeof(Job) * nimg, cudaMemcpyHostToDevice, s);
-  if (!graph && (st = release_staging(c, S, s))) return st;
-  int64_t n = 0;
+  int64_t n = put_jobs(jobs.data(), nimg, dj, s);
   if (!graph) mark(c, s, -1);
   if (run_range) launch_range(dj, nimg, b_range, c->p.n_bins, s);
   if (!graph) mark(c, s, ST_RANGE);
@@ -713,7 +696,6 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
     c->graph_launches = n;
     c->graph_jobs = jobs;
     TM_CUDA(c, cudaGraphLaunch(c->graph, caller));
-    if ((st = release_staging(c, S, caller))) return st;
   } else if (ls < 0) {
     return check_launch(c, "sweep shared-memory attribute");
   }
@@ -893,6 +875,46 @@ tm_status backward_images(tm_ctx *c, int n, const tm_image *in, const tm_image *
 
 }  // namespace
 
+// Calls on a caller's stream share the workspace with the forwards that
+// tm_forward_host_async runs on the context's forward stream: enter_caller
+// orders stream s after the last of those forwards, leave_caller (given the
+// call's status) marks the end of a successful call for the next one.
+tm_status enter_caller(tm_ctx *c, cudaStream_t s) {
+  if (c->fwd_pending) {
+    TM_CUDA(c, cudaStreamWaitEvent(s, c->fwd_done, 0));
+    c->fwd_pending = false;
+  }
+  return TM_OK;
+}
+
+tm_status leave_caller(tm_ctx *c, cudaStream_t s, tm_status st) {
+  if (st || !c->fwd_stream) return st;
+  TM_CUDA(c, cudaEventRecord(c->ext_done, s));
+  c->ext_pending = true;
+  return TM_OK;
+}
+
+// tm_forward_batch on validated arguments, n >= 1.
+tm_status forward_batch(tm_ctx *c, int n, const tm_image *in, const tm_image *out, cudaStream_t st) {
+  tm_status s = ensure_device_info(c);
+  if (s) return s;
+  if (c->p.n_bins > 1 && c->hist_path != 2) {
+    mark(c, st, -1);
+    s = forward_fused(c, n, in, out, st, true);
+    mark(c, st, ST_BATCH);
+    if (s != TM_EUNSUPPORTED) return s;
+    if (c->hist_path == 1)
+      return fail(c, TM_EUNSUPPORTED, "fused sweep does not fit these fields (use the materialised path)");
+  }
+  int64_t total = 0;
+  for (int i = 0; i < n; ++i) {
+    if ((s = forward_device(c, &in[i], &out[i], st))) return s;
+    total += c->launches;
+  }
+  c->launches = total;
+  return TM_OK;
+}
+
 extern "C" {
 
 void tm_params_default(tm_params *p) {
@@ -954,22 +976,20 @@ void tm_destroy(tm_ctx *c) {
   if (c->rr_stats) cudaFree(c->rr_stats);
   if (c->stage) cudaFree(c->stage);
   for (int k = 0; k < 2; ++k) {
-    if (c->hslot[k]) cudaFree(c->hslot[k]);
-    for (cudaEvent_t e : {c->hslot_free[k], c->hslot_full[k]})
+    for (void *b : {c->hslot[k], c->oslot[k]})
+      if (b) cudaFree(b);
+    for (cudaEvent_t e : {c->hslot_free[k], c->hslot_full[k], c->oslot_free[k], c->oslot_full[k]})
       if (e) cudaEventDestroy(e);
   }
-  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  for (cudaEvent_t e : {c->fwd_done, c->ext_done})
+    if (e) cudaEventDestroy(e);
+  for (cudaStream_t q : {c->copy_stream, c->fwd_stream})
+    if (q) cudaStreamDestroy(q);
   if (c->djobs) cudaFree(c->djobs);
   if (c->ditems) cudaFree(c->ditems);
   if (c->graph_stream) cudaStreamDestroy(c->graph_stream);
   if (c->gdjobs) cudaFree(c->gdjobs);
   if (c->gditems) cudaFree(c->gditems);
-  auto free_staging = [](Staging &S) {
-    if (S.jobs) cudaFreeHost(S.jobs);
-    if (S.done) cudaEventDestroy(S.done);
-  };
-  free_staging(c->gstage);
-  for (Staging &S : c->slots) free_staging(S);
   delete c;
 }
 
@@ -1001,7 +1021,9 @@ tm_status tm_forward(tm_ctx *c, const tm_image *in, const tm_image *out, void *s
     return fail(c, TM_EINVAL, "in is %dx%d but out is %dx%d", in->width, in->height, out->width,
                 out->height);
   if (overlap(in, out)) return fail(c, TM_EINVAL, "in and out overlap");
-  return forward_device(c, in, out, static_cast<cudaStream_t>(stream));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((s = enter_caller(c, st))) return s;
+  return leave_caller(c, st, forward_device(c, in, out, st));
 }
 
 tm_status tm_forward_host(tm_ctx *c, const tm_image *in, const tm_image *out, void *stream) {
@@ -1051,9 +1073,10 @@ tm_status tm_forward_host(tm_ctx *c, const tm_image *in, const tm_image *out, vo
     dout.data = static_cast<char *>(c->stage) + in_bytes;
     dout.pitch = 3LL * W;
   }
+  if ((s = enter_caller(c, st))) return s;
   TM_CUDA(c, cudaMemcpy2DAsync(din.data, in_row, in->data, in->pitch * elem_size(in->dtype), in_row,
                                H, cudaMemcpyHostToDevice, st));
-  if ((s = forward_device(c, &din, &dout, st))) return s;
+  if ((s = leave_caller(c, st, forward_device(c, &din, &dout, st)))) return s;
   if (!out_dev)
     TM_CUDA(c, cudaMemcpy2DAsync(out->data, out->pitch * elem_size(out->dtype), dout.data, out_row,
                                  out_row, H, cudaMemcpyDeviceToHost, st));
@@ -1061,13 +1084,31 @@ tm_status tm_forward_host(tm_ctx *c, const tm_image *in, const tm_image *out, vo
   return TM_OK;
 }
 
-// Device address of a page-locked host buffer, or null.
-static void *locked_device_pointer(const void *p) {
+static bool page_locked(const void *p) {
   cudaPointerAttributes pa{};
-  void *d = nullptr;
-  if (cudaPointerGetAttributes(&pa, p) == cudaSuccess && pa.type == cudaMemoryTypeHost) d = pa.devicePointer;
+  const bool r = cudaPointerGetAttributes(&pa, p) == cudaSuccess && pa.type == cudaMemoryTypeHost;
   cudaGetLastError();
-  return d;
+  return r;
+}
+
+// Two device buffers of at least `bytes` each (grown after the device is idle).
+static tm_status grow_slots(tm_ctx *c, void **slot, size_t *have, size_t bytes, const char *what) {
+  if (*have >= bytes) return TM_OK;
+  if (slot[0]) TM_CUDA(c, cudaDeviceSynchronize());  // both slots may still be in use
+  *have = 0;
+  for (int k = 0; k < 2; ++k) {
+    if (slot[k]) cudaFree(slot[k]);
+    slot[k] = nullptr;
+  }
+  for (int k = 0; k < 2; ++k) {
+    cudaError_t e = cudaMalloc(&slot[k], bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, TM_ENOMEM, "%s slots: %s", what, cudaGetErrorString(e));
+    }
+  }
+  *have = bytes;
+  return TM_OK;
 }
 
 tm_status tm_forward_host_async(tm_ctx *c, const tm_image *in, const tm_image *out, void *stream) {
@@ -1077,48 +1118,54 @@ tm_status tm_forward_host_async(tm_ctx *c, const tm_image *in, const tm_image *o
   if ((s = validate_image(c, out, "out", false))) return s;
   if (in->width != out->width || in->height != out->height)
     return fail(c, TM_EINVAL, "in and out sizes differ");
-  void *out_dev = locked_device_pointer(out->data);
-  if (!locked_device_pointer(in->data) || !out_dev)
+  if (!page_locked(in->data) || !page_locked(out->data))
     return fail(c, TM_EINVAL, "tm_forward_host_async needs page-locked in and out (use tm_forward_host)");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int W = in->width, H = in->height;
   const size_t in_row = 3 * (size_t)W * elem_size(in->dtype);
-  const size_t in_bytes = align256(in_row * H);
-  if (c->hslot_bytes < in_bytes) {
-    if (c->hslot[0]) TM_CUDA(c, cudaDeviceSynchronize());  // both slots may still be in use
-    for (int k = 0; k < 2; ++k) {
-      if (c->hslot[k]) cudaFree(c->hslot[k]);
-      c->hslot[k] = nullptr;
-    }
-    c->hslot_bytes = 0;
-    for (int k = 0; k < 2; ++k) {
-      cudaError_t e = cudaMalloc(&c->hslot[k], in_bytes);
-      if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(c, TM_ENOMEM, "input slots: %s", cudaGetErrorString(e));
-      }
-    }
-    c->hslot_bytes = in_bytes;
-  }
-  if (!c->copy_stream) TM_CUDA(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+  const size_t out_row = 3 * (size_t)W * elem_size(out->dtype);
+  if ((s = grow_slots(c, c->hslot, &c->hslot_bytes, align256(in_row * H), "input"))) return s;
+  if ((s = grow_slots(c, c->oslot, &c->oslot_bytes, align256(out_row * H), "output"))) return s;
+  for (cudaStream_t *q : {&c->copy_stream, &c->fwd_stream})
+    if (!*q) TM_CUDA(c, cudaStreamCreateWithFlags(q, cudaStreamNonBlocking));
   for (int k = 0; k < 2; ++k)
-    for (cudaEvent_t *e : {&c->hslot_free[k], &c->hslot_full[k]})
+    for (cudaEvent_t *e : {&c->hslot_free[k], &c->hslot_full[k], &c->oslot_free[k], &c->oslot_full[k]})
       if (!*e) TM_CUDA(c, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  for (cudaEvent_t *e : {&c->fwd_done, &c->ext_done})
+    if (!*e) TM_CUDA(c, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   const int k = c->hslot_next;
   c->hslot_next ^= 1;
-  // the upload waits for the forward that last read this slot (a wait on an
-  // event never recorded returns at once); the forward waits for the upload
+  // upload k: after the forward that last read input slot k (a wait on an
+  // event never recorded returns at once)
   TM_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->hslot_free[k], 0));
   TM_CUDA(c, cudaMemcpy2DAsync(c->hslot[k], in_row, in->data, in->pitch * elem_size(in->dtype), in_row, H,
                                cudaMemcpyHostToDevice, c->copy_stream));
   TM_CUDA(c, cudaEventRecord(c->hslot_full[k], c->copy_stream));
-  TM_CUDA(c, cudaStreamWaitEvent(st, c->hslot_full[k], 0));
+  // forward k: after upload k, the download that last read output slot k and
+  // the last call on a caller's stream; it does not wait for download k-1
+  const cudaStream_t fs = c->fwd_stream;
+  TM_CUDA(c, cudaStreamWaitEvent(fs, c->hslot_full[k], 0));
+  TM_CUDA(c, cudaStreamWaitEvent(fs, c->oslot_free[k], 0));
+  if (c->ext_pending) {
+    TM_CUDA(c, cudaStreamWaitEvent(fs, c->ext_done, 0));
+    c->ext_pending = false;
+  }
   tm_image din = *in, dout = *out;
   din.data = c->hslot[k];
   din.pitch = 3LL * W;
-  dout.data = out_dev;  // the last kernel stores the result over the host link
-  if ((s = forward_device(c, &din, &dout, st))) return s;
-  TM_CUDA(c, cudaEventRecord(c->hslot_free[k], st));
+  dout.data = c->oslot[k];
+  dout.pitch = 3LL * W;
+  if ((s = forward_device(c, &din, &dout, fs))) return s;
+  TM_CUDA(c, cudaEventRecord(c->hslot_free[k], fs));
+  TM_CUDA(c, cudaEventRecord(c->oslot_full[k], fs));
+  TM_CUDA(c, cudaEventRecord(c->fwd_done, fs));
+  c->fwd_pending = true;
+  // download k on the caller's stream, so that synchronising it covers the
+  // upload, the forward and the download of every call made on it
+  TM_CUDA(c, cudaStreamWaitEvent(st, c->oslot_full[k], 0));
+  TM_CUDA(c, cudaMemcpy2DAsync(out->data, out->pitch * elem_size(out->dtype), c->oslot[k], out_row, out_row, H,
+                               cudaMemcpyDeviceToHost, st));
+  TM_CUDA(c, cudaEventRecord(c->oslot_free[k], st));
   return TM_OK;
 }
 
@@ -1140,29 +1187,18 @@ tm_status tm_forward_batch(tm_ctx *c, int32_t n, const tm_image *in, const tm_im
     if (overlap(&in[i], &out[i])) return fail(c, TM_EINVAL, "image %d: in and out overlap", i);
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  tm_status s = ensure_device_info(c);
-  if (s) return s;
-  if (c->p.n_bins > 1 && c->hist_path != 2) {
-    mark(c, st, -1);
-    s = forward_fused(c, n, in, out, st, true);
-    mark(c, st, ST_BATCH);
-    if (s != TM_EUNSUPPORTED) return s;
-    if (c->hist_path == 1)
-      return fail(c, TM_EUNSUPPORTED, "fused sweep does not fit these fields (use the materialised path)");
-  }
-  int64_t total = 0;
-  for (int i = 0; i < n; ++i) {
-    if ((s = forward_device(c, &in[i], &out[i], st))) return s;
-    total += c->launches;
-  }
-  c->launches = total;
-  return TM_OK;
+  tm_status s;
+  if ((s = enter_caller(c, st))) return s;
+  return leave_caller(c, st, forward_batch(c, n, in, out, st));
 }
 
 tm_status tm_backward(tm_ctx *c, const tm_image *in, const tm_image *grad_out,
                       const tm_image *grad_in, float *grad_params, void *stream) {
   if (!c) return fail(nullptr, TM_EINVAL, "tm_backward: ctx is NULL");
-  return backward_images(c, 1, in, grad_out, grad_in, grad_params, static_cast<cudaStream_t>(stream));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  tm_status st;
+  if ((st = enter_caller(c, s))) return st;
+  return leave_caller(c, s, backward_images(c, 1, in, grad_out, grad_in, grad_params, s));
 }
 
 tm_status tm_backward_batch(tm_ctx *c, int32_t n, const tm_image *in, const tm_image *grad_out,
@@ -1176,7 +1212,9 @@ tm_status tm_backward_batch(tm_ctx *c, int32_t n, const tm_image *in, const tm_i
     return TM_OK;
   }
   if (!in || !grad_out) return fail(c, TM_EINVAL, "descriptor arrays are NULL");
-  return backward_images(c, n, in, grad_out, grad_in, grad_params, s);
+  tm_status st;
+  if ((st = enter_caller(c, s))) return st;
+  return leave_caller(c, s, backward_images(c, n, in, grad_out, grad_in, grad_params, s));
 }
 
 tm_status tm_integral_image(const int32_t *q, int32_t width, int32_t height, int64_t *s1,
@@ -1199,13 +1237,10 @@ tm_status tm_integral_image(const int32_t *q, int32_t width, int32_t height, int
   cudaError_t e = cudaMallocAsync(&scr, align256(sizeof(Job)) + seg_bytes, st);
   if (e != cudaSuccess) { cudaGetLastError(); return fail(nullptr, TM_ENOMEM, "tm_integral_image: scratch"); }
   J.segtot = reinterpret_cast<long long *>(static_cast<char *>(scr) + align256(sizeof(Job)));
-  e = cudaMemcpyAsync(scr, &J, sizeof(Job), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) {
-    launch_integral_jobs(static_cast<Job *>(scr), 1, integral_tile_blocks(width, J.nseg),
-                         integral_col_blocks(width), st);
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // J lives on this stack frame
-  }
+  put_jobs(&J, 1, static_cast<Job *>(scr), st);
+  launch_integral_jobs(static_cast<Job *>(scr), 1, integral_tile_blocks(width, J.nseg),
+                       integral_col_blocks(width), st);
+  e = cudaGetLastError();
   cudaFreeAsync(scr, st);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "tm_integral_image");
   return TM_OK;
@@ -1259,8 +1294,8 @@ tm_status tm_debug_export(tm_ctx *c, int32_t what, void *dst, size_t bytes, void
   if (!dst) return fail(c, TM_EINVAL, "dst is NULL");
   if (bytes < need) return fail(c, TM_EINVAL, "dst holds %zu bytes, %zu needed", bytes, need);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((s = enter_caller(c, st))) return s;
   const void *src = nullptr;
-  const size_t N = (size_t)c->last_W * c->last_H;
   switch (what) {
     case TM_DBG_RANGE: src = &(c->last_stats ? c->last_stats : c->stats)->imin; break;
     case TM_DBG_THRESHOLDS: src = (c->last_stats ? c->last_stats : c->stats)->thr; break;
@@ -1280,9 +1315,8 @@ tm_status tm_debug_export(tm_ctx *c, int32_t what, void *dst, size_t bytes, void
             : what == TM_DBG_LF ? (const void *)c->dbg.lf
                                 : (const void *)c->dbg.l;
   }
-  (void)N;
   if (need) TM_CUDA(c, cudaMemcpyAsync(dst, src, need, cudaMemcpyDeviceToDevice, st));
-  return TM_OK;
+  return leave_caller(c, st, TM_OK);
 }
 
 tm_status tm_set_option(tm_ctx *c, int32_t key, int64_t value) {

@@ -250,6 +250,56 @@ def test_async_host_stream_matches_device(orc):
         tm.tm_destroy(ctx)
 
 
+def test_async_host_interleaved_with_caller_stream_calls(orc):
+    """Device-path calls on the same context between asynchronous host calls
+    (a forward of another size, a backward, a debug export) share its
+    workspace with the forwards in flight on the internal forward stream; a
+    second caller stream and a uint8 output slot are mixed in. Every result
+    equals the one from a fresh context."""
+    gp, op = params_pair(orc, 32, [3, 10, 60])
+    frames = [synth.wdr_image(120, 160, seed=40 + k) for k in range(4)]
+    other = synth.wdr_image(90, 210, seed=50)
+    refs = [run_gpu(f, gp, debug=False)[0] for f in frames]
+    ref_u8 = run_gpu(frames[3], gp, out_dtype=torch.uint8, debug=False)[0]
+    ref_other, d_other = run_gpu(other, gp, debug=True)
+    xo = torch.from_numpy(other).cuda()
+    g = torch.from_numpy(synth.wdr_image(90, 210, seed=51)).cuda()
+    fresh = tm.tm_create(gp)
+    try:
+        gin_ref = torch.empty_like(xo)
+        tm.tm_forward(fresh, xo, torch.empty_like(xo))
+        tm.tm_backward(fresh, xo, g, gin_ref)
+        torch.cuda.synchronize()
+    finally:
+        tm.tm_destroy(fresh)
+    ctx = tm.tm_create(gp)
+    try:
+        hins = [torch.from_numpy(f).pin_memory() for f in frames]
+        houts = [torch.zeros_like(h).pin_memory() for h in hins]
+        hu8 = torch.zeros(hins[3].shape, dtype=torch.uint8).pin_memory()
+        s1, s2 = torch.cuda.current_stream(), torch.cuda.Stream()
+        yo = torch.empty_like(xo)
+        gin = torch.empty_like(xo)
+        tm.tm_forward_host_async(ctx, hins[0].numpy(), houts[0].numpy(), s1)
+        tm.tm_forward_host_async(ctx, hins[1].numpy(), houts[1].numpy(), s1)
+        tm.tm_forward(ctx, xo, yo, s1)
+        bins = tm.tm_debug_export(ctx, tm.TM_DBG_BINS, s1)
+        tm.tm_forward_host_async(ctx, hins[2].numpy(), houts[2].numpy(), s2)
+        tm.tm_backward(ctx, xo, g, gin, stream=s2)
+        tm.tm_forward_host_async(ctx, hins[3].numpy(), houts[3].numpy(), s2)
+        tm.tm_forward_host_async(ctx, hins[3].numpy(), hu8.numpy(), s2)
+        s1.synchronize()
+        s2.synchronize()
+        for ho, ref in zip(houts, refs):
+            assert np.array_equal(ho.numpy(), ref)
+        assert np.array_equal(hu8.numpy(), ref_u8)
+        assert np.array_equal(yo.cpu().numpy(), ref_other)
+        assert np.array_equal(bins.cpu().numpy().reshape(90, 210), d_other["bins"])
+        assert torch.equal(gin.cpu(), gin_ref.cpu())
+    finally:
+        tm.tm_destroy(ctx)
+
+
 def test_integral_image_entry_point_exact(orc):
     rng = np.random.default_rng(0)
     # up to a full-size ragged plane (several row segments of the column pass)
