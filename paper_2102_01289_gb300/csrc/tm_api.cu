@@ -394,7 +394,7 @@ bool same_images(const std::vector<tm_image> &a, const tm_image *b, int n) {
 
 // Per-image sizes of the forward workspace.
 struct JobLayout {
-  size_t bins, q, s1, s2, segtot, counts, lohi, bcost, dcnt, dvar, dw, dlf, dl, total;
+  size_t bins, q, s12, segtot, counts, lohi, bcost, dcnt, dvar, dw, dlf, dl, total;
 };
 
 // Workspace of one image. count_elems, lohi_elems, bcost_elems: the sweep's
@@ -411,8 +411,7 @@ JobLayout job_layout(const tm_params &p, int W, int H, int nseg, size_t count_el
   auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
   L.bins = take(N);
   L.q = take(4 * N);
-  L.s1 = take(8 * plane);
-  L.s2 = take(8 * plane);
+  L.s12 = take(16 * plane);  // the integral images of q and q^2, interleaved
   L.segtot = take(8 * integral_scratch_elems(W, H, nseg));
   L.counts = take(2 * count_elems);
   L.lohi = take(2 * lohi_elems);
@@ -463,8 +462,9 @@ tm_status forward_materialised(tm_ctx *c, const tm_image *in, const tm_image *ou
   }
   J.bins = reinterpret_cast<uint8_t *>(ws + L.bins);
   J.q = reinterpret_cast<int32_t *>(ws + L.q);
-  J.s1 = reinterpret_cast<long long *>(ws + L.s1);
-  J.s2 = reinterpret_cast<long long *>(ws + L.s2);
+  J.s1 = reinterpret_cast<long long *>(ws + L.s12);
+  J.s2 = J.s1 + 1;
+  J.s_pair = 1;
   J.segtot = reinterpret_cast<long long *>(ws + L.segtot);
   J.qbits = qbits;
   J.nseg = nseg;
@@ -493,8 +493,7 @@ tm_status forward_materialised(tm_ctx *c, const tm_image *in, const tm_image *ou
     n += launch_integral_histogram(J.bins, W, H, c->p.n_bins, true, cpl, ws + off_hscr, s);
   }
   mark(c, s, ST_HIST);
-  n += launch_lookup_materialised(J.in, J.out, P, J.bins, cpl, reinterpret_cast<int64_t *>(J.s1),
-                                  reinterpret_cast<int64_t *>(J.s2), J.dbg, s);
+  n += launch_lookup_materialised(J.in, J.out, P, J.bins, cpl, reinterpret_cast<int64_t *>(J.s1), J.dbg, s);
   mark(c, s, ST_LOOKUP);
   if ((st = check_launch(c, "forward launch"))) return st;
   c->launches = n;
@@ -627,8 +626,9 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
     J.st_next = nullptr;
     J.bins = reinterpret_cast<uint8_t *>(b + L.bins);
     J.q = reinterpret_cast<int32_t *>(b + L.q);
-    J.s1 = reinterpret_cast<long long *>(b + L.s1);
-    J.s2 = reinterpret_cast<long long *>(b + L.s2);
+    J.s1 = reinterpret_cast<long long *>(b + L.s12);
+    J.s2 = J.s1 + 1;
+    J.s_pair = 1;
     J.segtot = reinterpret_cast<long long *>(b + L.segtot);
     J.counts = reinterpret_cast<uint16_t *>(b + L.counts);
     J.lohi = reinterpret_cast<uint16_t *>(b + L.lohi);

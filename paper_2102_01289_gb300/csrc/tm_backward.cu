@@ -77,10 +77,12 @@ __global__ void __launch_bounds__(kBT) k_bwd_pixel(DevParams P, Job J, BwdJob B)
       const long long iA = (long long)w.y0 * W1 + w.x0, iB = (long long)w.y0 * W1 + w.x1 + 1;
       const long long iC = (long long)(w.y1 + 1) * W1 + w.x1 + 1, iD = (long long)(w.y1 + 1) * W1 + w.x0;
       unsigned long long Nw = (unsigned long long)(w.x1 - w.x0 + 1) * (w.y1 - w.y0 + 1);
-      long long q1 = (long long)((unsigned long long)J.s1[iC] - (unsigned long long)J.s1[iD] -
-                                 (unsigned long long)J.s1[iB] + (unsigned long long)J.s1[iA]);
-      long long q2 = (long long)((unsigned long long)J.s2[iC] - (unsigned long long)J.s2[iD] -
-                                 (unsigned long long)J.s2[iB] + (unsigned long long)J.s2[iA]);
+      const longlong2 *s12 = reinterpret_cast<const longlong2 *>(J.s1);  // interleaved (q, q^2) sums
+      const longlong2 a = s12[iA], b = s12[iB], c = s12[iC], d = s12[iD];
+      long long q1 = (long long)((unsigned long long)c.x - (unsigned long long)d.x - (unsigned long long)b.x +
+                                 (unsigned long long)a.x);
+      long long q2 = (long long)((unsigned long long)c.y - (unsigned long long)d.y - (unsigned long long)b.y +
+                                 (unsigned long long)a.y);
       literal_area(P, f, J.qbits, q1, q2, Nw);  // Algorithm 1's area: zero padding
       rarea[f] = __frcp_rn((float)Nw);
       var[f] = window_variance(q1, q2, Nw, rarea[f], inv_scale2);

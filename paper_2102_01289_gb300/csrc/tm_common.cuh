@@ -109,7 +109,8 @@ struct Job {
   Stats *st_next;           // streaming reuse: receives this image's own range (else null)
   uint8_t *bins;            // H*W bin map
   int32_t *q;               // H*W quantised log
-  long long *s1, *s2;       // (H+1)*(W+1) integral images of q and q^2
+  long long *s1, *s2;       // (H+1)*(W+1) integral images of q and q^2; with s_pair
+                            //   interleaved: position i of both at s1[2i], s1[2i+1], s2 = s1 + 1
   long long *segtot;        // integral-image scratch, integral_scratch_elems(W, H, nseg)
   uint16_t *counts;         // nslabs*H*W slab counts from the sweep
   uint16_t *lohi;           // tiles_x*H: per strip and row, smallest | largest << 8 bin
@@ -117,6 +118,7 @@ struct Job {
   int *bcost;               // tiles_x*nb: per strip, summed row costs of each block of rb rows
   DebugPlanes dbg;
   int qbits;
+  int s_pair;               // 1: s1 and s2 interleaved (the forward's workspace)
   int nseg, seg_rows;       // integral images: row segments of the tiles
   int b0[kNumStages];       // first block of this job in each batched stage
   int rb, nb;               // rows per cost block, blocks per strip

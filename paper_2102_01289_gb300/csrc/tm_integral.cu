@@ -280,8 +280,10 @@ __device__ __forceinline__ void int_mid_cols(const IntTask &X, int c0, long long
 // row's totals of the chunks to the left) accumulated down the tile from the
 // value above it, written to rows 1..H, columns 1..W of planes s1 and s2 (as
 // OutT, modulo its range; s2 may be null); tiles of the first segment also
-// write row 0, tiles of the first chunk column 0.
-template <class Src, class OutT>
+// write row 0, tiles of the first chunk column 0. Pair: the planes are
+// interleaved (s2 = s1 + 1, two elements per position), and each position is
+// written with one 16-byte store.
+template <class Src, class OutT, bool Pair = false>
 __device__ __forceinline__ void int_write_tile(const IntTask &X, const Src &src, OutT *s1, OutT *s2, int seg,
                                                int k, typename Src::Raw *tile, long long *out1, long long *out2,
                                                long long (*wt)[kINT / 32]) {
@@ -289,10 +291,11 @@ __device__ __forceinline__ void int_write_tile(const IntTask &X, const Src &src,
   const long long W1 = (long long)W + 1;
   const int R0 = seg * X.seg_rows, R1 = min(R0 + X.seg_rows, H), C0 = k * kIC, nc = min(kIC, W - C0);
   const bool two = s2 != nullptr;
+  const long long os = Pair ? 2 : 1;  // elements per position (Pair: s2 = s1 + 1)
   if (seg == 0) {
     for (int i = threadIdx.x; i < nc; i += kINT) {
-      s1[C0 + 1 + i] = 0;
-      if (two) s2[C0 + 1 + i] = 0;
+      s1[(C0 + 1 + i) * os] = 0;
+      if (two) s2[(C0 + 1 + i) * os] = 0;
     }
     if (k == 0 && threadIdx.x == 0) {
       s1[0] = 0;
@@ -301,8 +304,8 @@ __device__ __forceinline__ void int_write_tile(const IntTask &X, const Src &src,
   }
   if (k == 0)
     for (int r = R0 + (int)threadIdx.x; r < R1; r += kINT) {
-      s1[(r + 1) * W1] = 0;
-      if (two) s2[(r + 1) * W1] = 0;
+      s1[(r + 1) * W1 * os] = 0;
+      if (two) s2[(r + 1) * W1 * os] = 0;
     }
   long long acc1[kItems], acc2[kItems];
 #pragma unroll
@@ -332,6 +335,12 @@ __device__ __forceinline__ void int_write_tile(const IntTask &X, const Src &src,
       out2[threadIdx.x * 9 + i] = acc2[i];
     }
     __syncthreads();
+    if (Pair) {  // one 16-byte store per position
+      longlong2 *o = reinterpret_cast<longlong2 *>(s1) + (long long)(r + 1) * W1 + C0 + 1;
+      for (int i = threadIdx.x; i < nc; i += kINT) o[i] = make_longlong2(out1[pad9(i)], out2[pad9(i)]);
+      __syncthreads();
+      continue;
+    }
     OutT *o1 = s1 + (long long)(r + 1) * W1 + C0 + 1;
     for (int i = threadIdx.x; i < nc; i += kINT) o1[i] = (OutT)out1[pad9(i)];
     if (two) {
@@ -373,7 +382,10 @@ __global__ void __launch_bounds__(kINT, 4) k_int_write(const Job *__restrict__ j
   const IntTask X = job_task(J);
   const int lb = blockIdx.x - J.b0[kStRows];
   const QSource src{J.q, J.in.W};
-  int_write_tile(X, src, J.s1, J.s2, lb / X.nchunk, lb % X.nchunk, tile, out1, out2, wt);
+  if (J.s_pair)
+    int_write_tile<QSource, long long, true>(X, src, J.s1, J.s2, lb / X.nchunk, lb % X.nchunk, tile, out1, out2, wt);
+  else
+    int_write_tile(X, src, J.s1, J.s2, lb / X.nchunk, lb % X.nchunk, tile, out1, out2, wt);
 }
 
 // The fixed-point integral planes of float plane pairs (u_p, v_p), p =

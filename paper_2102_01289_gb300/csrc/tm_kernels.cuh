@@ -70,7 +70,7 @@ int launch_sweep(const DevParams &P, const Job *jobs, const int4 *items, int nit
 int lookup_blocks(int W, int H);
 int launch_lookup_counts(const DevParams &P, const Job *jobs, int njobs, int blocks, cudaStream_t s);
 int launch_lookup_materialised(const Image &in, const Image &out, const DevParams &P,
-                               const uint8_t *bins, const uint32_t *cplanes, const int64_t *s1,
-                               const int64_t *s2, const DebugPlanes &dbg, cudaStream_t s);
+                               const uint8_t *bins, const uint32_t *cplanes, const int64_t *s12,
+                               const DebugPlanes &dbg, cudaStream_t s);
 
 }  // namespace tmk

@@ -14,10 +14,10 @@ namespace tmk {
 namespace {
 
 // Window statistics of field f at (x, y): reciprocal area and variance
-// (Eq. 6, Eq. 10).
+// (Eq. 6, Eq. 10). s12: the integral images of q and q^2 interleaved, one
+// 16-byte load per corner.
 __device__ __forceinline__ void window_stats(const DevParams &P, int f, int x, int y, int W, int H,
-                                             const long long *__restrict__ s1,
-                                             const long long *__restrict__ s2, int qbits,
+                                             const longlong2 *__restrict__ s12, int qbits,
                                              float inv_scale2, float &rarea, float &var) {
   const long long W1 = (long long)W + 1;
   Win w = window_of(P, f, x, y, W, H);
@@ -26,10 +26,11 @@ __device__ __forceinline__ void window_stats(const DevParams &P, int f, int x, i
   const long long iC = (long long)(w.y1 + 1) * W1 + w.x1 + 1;
   const long long iD = (long long)(w.y1 + 1) * W1 + w.x0;
   unsigned long long N = (unsigned long long)(w.x1 - w.x0 + 1) * (w.y1 - w.y0 + 1);
-  long long q1 = (long long)((unsigned long long)__ldg(s1 + iC) - (unsigned long long)__ldg(s1 + iD) -
-                             (unsigned long long)__ldg(s1 + iB) + (unsigned long long)__ldg(s1 + iA));
-  long long q2 = (long long)((unsigned long long)__ldg(s2 + iC) - (unsigned long long)__ldg(s2 + iD) -
-                             (unsigned long long)__ldg(s2 + iB) + (unsigned long long)__ldg(s2 + iA));
+  const longlong2 a = __ldg(s12 + iA), b = __ldg(s12 + iB), c = __ldg(s12 + iC), d = __ldg(s12 + iD);
+  long long q1 = (long long)((unsigned long long)c.x - (unsigned long long)d.x - (unsigned long long)b.x +
+                             (unsigned long long)a.x);
+  long long q2 = (long long)((unsigned long long)c.y - (unsigned long long)d.y - (unsigned long long)b.y +
+                             (unsigned long long)a.y);
   literal_area(P, f, qbits, q1, q2, N);
   rarea = __frcp_rn((float)N);
   var = window_variance(q1, q2, N, rarea, inv_scale2);
@@ -44,11 +45,10 @@ struct Fusion {
 // into the Eq. 3 sums (the same arithmetic as fuse_fields, one field at a
 // time, so no per-field state is kept).
 __device__ __forceinline__ void fold_field(const DevParams &P, int f, int x, int y, int W, int H,
-                                           unsigned cnt, const long long *__restrict__ s1,
-                                           const long long *__restrict__ s2, int qbits,
+                                           unsigned cnt, const longlong2 *__restrict__ s12, int qbits,
                                            float inv_scale2, Fusion &fu, const DebugPlanes &dbg) {
   float rarea, var;
-  window_stats(P, f, x, y, W, H, s1, s2, qbits, inv_scale2, rarea, var);
+  window_stats(P, f, x, y, W, H, s12, qbits, inv_scale2, rarea, var);
   const float Pf = (float)cnt * rarea;                                  // Eq. 1
   const float Lf = fmaf(P.ld_max - P.ld_min, Pf, P.ld_min);             // Eq. 2
   const float Wf = __fdividef(P.alpha[f] * var, var + P.eps[f]);       // Eq. 4
@@ -80,8 +80,8 @@ __device__ __forceinline__ void finish_pixel(const Image &in, const Image &out, 
 template <int NF>
 __global__ void __launch_bounds__(256)
     k_lookup_materialised(Image in, Image out, DevParams P, const uint8_t *__restrict__ bins,
-                          const unsigned *__restrict__ cplanes, const long long *__restrict__ s1,
-                          const long long *__restrict__ s2, DebugPlanes dbg) {
+                          const unsigned *__restrict__ cplanes, const longlong2 *__restrict__ s12,
+                          DebugPlanes dbg) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int W = in.W, H = in.H;
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(256)
             __ldg(C + (long long)w.y0 * W1 + w.x1 + 1) + __ldg(C + (long long)w.y0 * W1 + w.x0);
     else if (t >= P.n_bins)
       cnt = (unsigned)((w.x1 - w.x0 + 1) * (w.y1 - w.y0 + 1));
-    fold_field(P, f, x, y, W, H, cnt, s1, s2, P.qbits, inv_scale2, fu, dbg);
+    fold_field(P, f, x, y, W, H, cnt, s12, P.qbits, inv_scale2, fu, dbg);
   }
   finish_pixel(in, out, P, x, y, fu, dbg);
 }
@@ -111,8 +111,9 @@ __global__ void __launch_bounds__(256)
 // Lookup from the sweep's per-slab counts, over a batch of jobs: block ->
 // (image, 32 x 8 pixel tile). NF = number of fields, so the field loop is
 // straight-line code and the loads of all fields can be issued together.
+// Eight blocks per SM (32 registers) keep more of those loads in flight.
 template <int NF>
-__global__ void __launch_bounds__(256) k_lookup_counts(DevParams P, const Job *__restrict__ jobs, int njobs) {
+__global__ void __launch_bounds__(256, 8) k_lookup_counts(DevParams P, const Job *__restrict__ jobs, int njobs) {
   const int j = find_job(jobs, njobs, kStLook, blockIdx.x);
   const Job &J = jobs[j];
   const int lb = blockIdx.x - J.b0[kStLook];
@@ -132,7 +133,8 @@ __global__ void __launch_bounds__(256) k_lookup_counts(DevParams P, const Job *_
       const int T = max(y + S.slab_a[s] - 1, -1), B = min(y + S.slab_b[s], H - 1);
       if (B > T) cnt += __ldg(J.counts + s * N + pix);
     }
-    fold_field(P, f, x, y, W, H, cnt, J.s1, J.s2, J.qbits, inv_scale2, fu, J.dbg);
+    fold_field(P, f, x, y, W, H, cnt, reinterpret_cast<const longlong2 *>(J.s1), J.qbits, inv_scale2, fu,
+               J.dbg);
   }
   finish_pixel(J.in, J.out, P, x, y, fu, J.dbg);
 }
@@ -140,16 +142,16 @@ __global__ void __launch_bounds__(256) k_lookup_counts(DevParams P, const Job *_
 }  // namespace
 
 int launch_lookup_materialised(const Image &in, const Image &out, const DevParams &P,
-                               const uint8_t *bins, const uint32_t *cplanes, const int64_t *s1,
-                               const int64_t *s2, const DebugPlanes &dbg, cudaStream_t s) {
+                               const uint8_t *bins, const uint32_t *cplanes, const int64_t *s12,
+                               const DebugPlanes &dbg, cudaStream_t s) {
   dim3 block(32, 8), grid((in.W + 31) / 32, (in.H + 7) / 8);
-  const long long *S1 = reinterpret_cast<const long long *>(s1), *S2 = reinterpret_cast<const long long *>(s2);
+  const longlong2 *S12 = reinterpret_cast<const longlong2 *>(s12);
   switch (P.n_fields) {
 #define TM_LOOKUP_MAT(nf) \
-  case nf: k_lookup_materialised<nf><<<grid, block, 0, s>>>(in, out, P, bins, cplanes, S1, S2, dbg); break;
+  case nf: k_lookup_materialised<nf><<<grid, block, 0, s>>>(in, out, P, bins, cplanes, S12, dbg); break;
     TM_LOOKUP_MAT(1) TM_LOOKUP_MAT(2) TM_LOOKUP_MAT(3) TM_LOOKUP_MAT(4) TM_LOOKUP_MAT(5) TM_LOOKUP_MAT(6)
     TM_LOOKUP_MAT(7)
-    default: k_lookup_materialised<8><<<grid, block, 0, s>>>(in, out, P, bins, cplanes, S1, S2, dbg); break;
+    default: k_lookup_materialised<8><<<grid, block, 0, s>>>(in, out, P, bins, cplanes, S12, dbg); break;
 #undef TM_LOOKUP_MAT
   }
   return 1;
