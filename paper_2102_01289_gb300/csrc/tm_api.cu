@@ -115,9 +115,6 @@ struct tm_ctx {
   cudaGraphExec_t graph = nullptr;
   std::vector<tm_image> graph_in, graph_out;
   cudaStream_t graph_stream = nullptr;
-  // the fused forward's side stream: the sweep plan beside the integral images
-  cudaStream_t side_stream = nullptr;
-  cudaEvent_t side_fork = nullptr, side_join = nullptr;
   int64_t graph_launches = 0;
   // streaming range reuse (TM_OPT_REUSE_RANGE): two range states; a forward
   // bins with rr_stats[rr_cur] and leaves its own range in the other
@@ -659,9 +656,6 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   // a batch is captured on the context's own stream (capture is not allowed on
   // the legacy default stream) and the graph is then launched on the caller's
   const cudaStream_t caller = s;
-  if (!c->side_stream) TM_CUDA(c, cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking));
-  for (cudaEvent_t *e : {&c->side_fork, &c->side_join})
-    if (!*e) TM_CUDA(c, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   if (graph) {
     if (!c->graph_stream) TM_CUDA(c, cudaStreamCreateWithFlags(&c->graph_stream, cudaStreamNonBlocking));
     s = c->graph_stream;
@@ -673,16 +667,9 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   if (!graph) mark(c, s, ST_RANGE);
   launch_prep(dj, nimg, b_prep, c->p.n_bins, c->p.flags, s);
   if (!graph) mark(c, s, ST_PREP);
-  // the sweep plan reads the bin map only and the integral images q only, so
-  // the plan (a scan and one CTA per image) runs on the side stream beside
-  // the integral images instead of after them; the sweep waits for both
-  cudaEventRecord(c->side_fork, s);
-  cudaStreamWaitEvent(c->side_stream, c->side_fork, 0);
-  n += launch_sweep_plan(dj, nimg, b_scan, di, c->side_stream);
-  cudaEventRecord(c->side_join, c->side_stream);
   n += (run_range ? 2 : 1) + launch_integral_jobs(dj, nimg, b_rows, b_cols, s);
   if (!graph) mark(c, s, ST_INTEGRAL);
-  cudaStreamWaitEvent(s, c->side_join, 0);
+  n += launch_sweep_plan(dj, nimg, b_scan, di, s);  // brings the bin map into L2 for the sweep
   if (!graph) mark(c, s, ST_PLAN);
   const int ls = launch_sweep(P, dj, di, nitems, queue, smem, ctas, s);
   if (!graph) mark(c, s, ST_SWEEP);
@@ -1001,9 +988,6 @@ void tm_destroy(tm_ctx *c) {
   if (c->djobs) cudaFree(c->djobs);
   if (c->ditems) cudaFree(c->ditems);
   if (c->graph_stream) cudaStreamDestroy(c->graph_stream);
-  if (c->side_stream) cudaStreamDestroy(c->side_stream);
-  for (cudaEvent_t e : {c->side_fork, c->side_join})
-    if (e) cudaEventDestroy(e);
   if (c->gdjobs) cudaFree(c->gdjobs);
   if (c->gditems) cudaFree(c->gditems);
   delete c;
