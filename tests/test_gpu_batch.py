@@ -49,6 +49,31 @@ def test_batch_equals_per_image(dtype):
         tm.tm_destroy(ctx)
 
 
+def test_batch_of_more_images_than_one_descriptor_launch():
+    """The job descriptors reach the device as kernel parameters, 32 per
+    launch: batches of 33 and 70 images take two and three such launches,
+    first as a captured graph and then as its replay; every image equals its
+    own call."""
+    p = tm.make_params(16, [2, 9])
+    rng = np.random.default_rng(5)
+    ctx = tm.tm_create(p)
+    try:
+        for n in (33, 70):
+            sizes = [(int(rng.integers(8, 90)), int(rng.integers(8, 90))) for _ in range(n)]
+            xs = [torch.from_numpy(synth.wdr_image(h, w, seed=100 + i)).cuda() for i, (w, h) in enumerate(sizes)]
+            ys = [torch.empty_like(x) for x in xs]
+            refs = [_single(ctx, x) for x in xs]
+            for _ in range(2):  # capture, then replay
+                for y in ys:
+                    y.zero_()
+                tm.tm_forward_batch(ctx, xs, ys)
+                torch.cuda.synchronize()
+                for y, ref in zip(ys, refs):
+                    assert torch.equal(y, ref)
+    finally:
+        tm.tm_destroy(ctx)
+
+
 def test_graph_replay_tracks_inputs():
     p = tm.make_params(16, [2, 9, 40])
     sizes = [(300, 200), (128, 96), (257, 255)]
