@@ -170,47 +170,92 @@ __device__ __forceinline__ void chunk_row_prefix(const Src &src, const typename 
 }
 
 // Launch 1: per tile (seg, k), the column sums of the chunk-local row
-// prefixes, the rows' chunk totals and the tile totals.
+// prefixes, the rows' chunk totals and the tile totals. The column sum of the
+// row prefixes at column c is the prefix, up to c, of the plain column sums
+// (both are the sum of the values above and left of c in the tile), so the
+// rows are only summed down each column and across each row (warp sums, no
+// barrier per row); one block scan over the columns ends the tile.
+constexpr int kRowGroup = 16;  // rows whose warp partial sums are combined together
+struct StatsSmem {
+  long long col[2][kIC / 8 * 9];            // the tile's column sums, padded for the scan
+  long long row[kRowGroup][2][kINT / 32];   // warp partial sums of a group of rows
+  long long wt[2][kINT / 32];               // block scan
+};
+
 template <class Src>
-__device__ __forceinline__ void int_stats_tile(const IntTask &X, const Src &src, int seg, int k,
-                                               typename Src::Raw *tile, long long (*wt)[kINT / 32]) {
+__device__ __forceinline__ void int_stats_tile(const IntTask &X, const Src &src, int seg, int k, StatsSmem &sm) {
   const int W = X.W, H = X.H;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int R0 = seg * X.seg_rows, R1 = min(R0 + X.seg_rows, H), C0 = k * kIC, nc = min(kIC, W - C0);
-  long long acc1[kItems], acc2[kItems];
+  long long c1[kItems], c2[kItems];  // sums down the thread's strided columns threadIdx.x + m kINT
 #pragma unroll
-  for (int i = 0; i < kItems; ++i) acc1[i] = acc2[i] = 0;
-  long long T1 = 0, T2 = 0;
+  for (int m = 0; m < kItems; ++m) c1[m] = c2[m] = 0;
   typename Src::Raw cur[kItems], nxt[kItems];
   load_chunk_row(src, R0, C0, nc, cur);
   for (int r = R0; r < R1; ++r) {
     if (r + 1 < R1) load_chunk_row(src, r + 1, C0, nc, nxt);  // in flight meanwhile
-    long long l1[kItems], l2[kItems], e1, e2, t1, t2;
-    chunk_row_prefix(src, cur, tile, wt, l1, l2, e1, e2, t1, t2);
+    long long s1 = 0, s2 = 0;
 #pragma unroll
-    for (int m = 0; m < kItems; ++m) cur[m] = nxt[m];
+    for (int m = 0; m < kItems; ++m) {
+      long long x1, x2;
+      src.values(cur[m], x1, x2);
+      c1[m] += x1;
+      c2[m] += x2;
+      s1 += x1;
+      s2 += x2;
+      cur[m] = nxt[m];
+    }
 #pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-      acc1[i] += e1 + l1[i];
-      acc2[i] += e2 + l2[i];
+    for (int o = 16; o > 0; o >>= 1) {
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
     }
-    if (threadIdx.x == 0) {
-      X.rowsum[(long long)r * X.nchunk + k] = t1;
-      X.rowsum[((long long)H + r) * X.nchunk + k] = t2;
+    const int g = (r - R0) % kRowGroup;
+    if (lane == 0) {
+      sm.row[g][0][wid] = s1;
+      sm.row[g][1][wid] = s2;
     }
-    T1 += t1;
-    T2 += t2;
+    if (g == kRowGroup - 1 || r == R1 - 1) {  // the group's row totals
+      __syncthreads();
+      if ((int)threadIdx.x <= g) {
+        const int rr = r - g + (int)threadIdx.x;
+        long long t1 = 0, t2 = 0;
+#pragma unroll
+        for (int w = 0; w < kINT / 32; ++w) t1 += sm.row[threadIdx.x][0][w], t2 += sm.row[threadIdx.x][1][w];
+        X.rowsum[(long long)rr * X.nchunk + k] = t1;
+        X.rowsum[((long long)H + rr) * X.nchunk + k] = t2;
+      }
+      __syncthreads();  // sm.row is rewritten by the next group
+    }
   }
+  // chunk-local column prefixes of the column sums: consecutive columns per thread
+#pragma unroll
+  for (int m = 0; m < kItems; ++m) {
+    sm.col[0][pad9(threadIdx.x + m * kINT)] = c1[m];
+    sm.col[1][pad9(threadIdx.x + m * kINT)] = c2[m];
+  }
+  __syncthreads();
+  long long l1[kItems], l2[kItems], a1 = 0, a2 = 0;
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    a1 += sm.col[0][threadIdx.x * 9 + i];
+    a2 += sm.col[1][threadIdx.x * 9 + i];
+    l1[i] = a1;
+    l2[i] = a2;
+  }
+  long long e1, e2, t1, t2;
+  block_scan_pair(a1, a2, sm.wt, e1, e2, t1, t2);
 #pragma unroll
   for (int i = 0; i < kItems; ++i) {
     const int c = C0 + threadIdx.x * kItems + i;
     if (c < W) {
-      X.colsum[(long long)seg * W + c] = acc1[i];
-      X.colsum[((long long)X.nseg + seg) * W + c] = acc2[i];
+      X.colsum[(long long)seg * W + c] = e1 + l1[i];
+      X.colsum[((long long)X.nseg + seg) * W + c] = e2 + l2[i];
     }
   }
   if (threadIdx.x == 0) {
-    X.tiletot[(long long)seg * X.nchunk + k] = T1;
-    X.tiletot[((long long)X.nseg + seg) * X.nchunk + k] = T2;
+    X.tiletot[(long long)seg * X.nchunk + k] = t1;
+    X.tiletot[((long long)X.nseg + seg) * X.nchunk + k] = t2;
   }
 }
 
@@ -358,13 +403,12 @@ __device__ __forceinline__ IntTask job_task(const Job &J) {
 }
 
 __global__ void __launch_bounds__(kINT, 4) k_int_stats(const Job *__restrict__ jobs, int njobs) {
-  __shared__ int32_t tile[kIC / 8 * 9];
-  __shared__ long long wt[2][kINT / 32];
+  __shared__ StatsSmem sm;
   const Job &J = jobs[find_job(jobs, njobs, kStRows, blockIdx.x)];
   const IntTask X = job_task(J);
   const int lb = blockIdx.x - J.b0[kStRows];
   const QSource src{J.q, J.in.W};
-  int_stats_tile(X, src, lb / X.nchunk, lb % X.nchunk, tile, wt);
+  int_stats_tile(X, src, lb / X.nchunk, lb % X.nchunk, sm);
 }
 
 __global__ void __launch_bounds__(kMidCols * kMidGroups) k_int_mid(const Job *__restrict__ jobs, int njobs) {
@@ -414,11 +458,10 @@ __device__ __forceinline__ FixSource fix_source(const FixPairs &F, int p) {
 }
 
 __global__ void __launch_bounds__(kINT, 4) k_fix_stats(FixPairs F) {
-  __shared__ float2 tile[kIC / 8 * 9];
-  __shared__ long long wt[2][kINT / 32];
+  __shared__ StatsSmem sm;
   const int p = blockIdx.y;
   const IntTask X = fix_task(F, p);
-  int_stats_tile(X, fix_source(F, p), blockIdx.x / X.nchunk, blockIdx.x % X.nchunk, tile, wt);
+  int_stats_tile(X, fix_source(F, p), blockIdx.x / X.nchunk, blockIdx.x % X.nchunk, sm);
 }
 
 __global__ void __launch_bounds__(kMidCols * kMidGroups) k_fix_mid(FixPairs F) {
@@ -460,10 +503,9 @@ __device__ __forceinline__ BinSource hist_source(const HistPairs &Q) {
 }
 
 __global__ void __launch_bounds__(kINT, 4) k_hist_stats(HistPairs Q) {
-  __shared__ int tile[kIC / 8 * 9];
-  __shared__ long long wt[2][kINT / 32];
+  __shared__ StatsSmem sm;
   const IntTask X = hist_task(Q);
-  int_stats_tile(X, hist_source(Q), blockIdx.x / X.nchunk, blockIdx.x % X.nchunk, tile, wt);
+  int_stats_tile(X, hist_source(Q), blockIdx.x / X.nchunk, blockIdx.x % X.nchunk, sm);
 }
 
 __global__ void __launch_bounds__(kMidCols * kMidGroups) k_hist_mid(HistPairs Q) {
