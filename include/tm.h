@@ -313,8 +313,19 @@ tm_status tm_debug_export(tm_ctx *ctx, int32_t what, void *dst, size_t bytes,
  *                        not changed since that forward (an autograd function
  *                        holding its saved input does). Results are those of
  *                        the recomputation. 0 = always recompute (default).
+ *   TM_OPT_SWEEP_TILES   tuning: tiles of 256 columns x TY rows that the fused
+ *                        sweep cuts each image into (the rows rounded to whole
+ *                        strips); 0 = automatic (default: one wave of the
+ *                        sweep's resident CTAs, shared among a batch's images
+ *                        by pixel count). Results do not depend on it.
  */
-enum { TM_OPT_HIST_PATH = 1, TM_OPT_STAGE_TIMING = 2, TM_OPT_REUSE_RANGE = 3, TM_OPT_BACKWARD_REUSE = 4 };
+enum {
+  TM_OPT_HIST_PATH = 1,
+  TM_OPT_STAGE_TIMING = 2,
+  TM_OPT_REUSE_RANGE = 3,
+  TM_OPT_BACKWARD_REUSE = 4,
+  TM_OPT_SWEEP_TILES = 5
+};
 tm_status tm_set_option(tm_ctx *ctx, int32_t key, int64_t value);
 
 /* Per-stage device time, summed over every call since the previous read,

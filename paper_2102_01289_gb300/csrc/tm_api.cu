@@ -66,6 +66,7 @@ struct tm_ctx {
   std::string err;
   int debug = 0;
   int hist_path = 0;
+  int sweep_tiles = 0;  // TM_OPT_SWEEP_TILES (0: one wave of the sweep's CTAs per image share)
   int64_t launches = 0;
   int num_sms = 0;
   size_t smem_optin = 0;
@@ -79,7 +80,7 @@ struct tm_ctx {
   // the workspace. The cached batch graph has its own device buffers, written
   // by its own nodes at every replay.
   Job *djobs = nullptr;    // device copy of the job array (calls outside the graph)
-  int4 *ditems = nullptr;  // sweep queue: items and the pop counter
+  int4 *ditems = nullptr;  // sweep queue: the pop counter
   size_t djobs_bytes = 0, ditems_bytes = 0;
   Job *gdjobs = nullptr;   // device buffers written by the cached graph
   int4 *gditems = nullptr;
@@ -199,10 +200,10 @@ tm_status validate_params(const tm_params *p, std::string &why) {
 }
 
 enum Stage { ST_RANGE, ST_PREP, ST_INTEGRAL, ST_HIST, ST_LOOKUP, ST_SWEEP, ST_BATCH,
-             ST_BWD_PIXEL, ST_BWD_ADJOINT, ST_BWD_INPUT, ST_PLAN, ST_COUNT };
+             ST_BWD_PIXEL, ST_BWD_ADJOINT, ST_BWD_INPUT, ST_COUNT };
 const char *const kStageNames[ST_COUNT] = {"range", "prep", "integral_image", "integral_histogram",
                                           "lookup", "fused_sweep", "batch", "bwd_pixel",
-                                          "bwd_adjoint", "bwd_input", "sweep_plan"};
+                                          "bwd_adjoint", "bwd_input"};
 
 // Record a stage boundary on stream s (stage < 0 opens a new call).
 void mark(tm_ctx *c, cudaStream_t s, int stage) {
@@ -394,14 +395,12 @@ bool same_images(const std::vector<tm_image> &a, const tm_image *b, int n) {
 
 // Per-image sizes of the forward workspace.
 struct JobLayout {
-  size_t bins, q, s12, segtot, counts, lohi, bcost, dcnt, dvar, dw, dlf, dl, total;
+  size_t bins, q, s12, segtot, cnt, grp, dcnt, dvar, dw, dlf, dl, total;
 };
 
-// Workspace of one image. count_elems, lohi_elems, bcost_elems: the sweep's
-// slab counts, per strip and row bin ranges and per strip block costs (0 on
-// the materialised path).
-JobLayout job_layout(const tm_params &p, int W, int H, int nseg, size_t count_elems, bool debug,
-                     size_t lohi_elems = 0, size_t bcost_elems = 0) {
+// Workspace of one image. cnt_bytes: the sweep's count planes (0 on the
+// materialised path); grp: per row and 32-column group, the bin range.
+JobLayout job_layout(const tm_params &p, int W, int H, int nseg, size_t cnt_bytes, bool debug) {
   // nseg: row segments of the integral images (integral_layout)
   JobLayout L{};
   const size_t N = (size_t)W * H;
@@ -413,9 +412,8 @@ JobLayout job_layout(const tm_params &p, int W, int H, int nseg, size_t count_el
   L.q = take(4 * N);
   L.s12 = take(16 * plane);  // the integral images of q and q^2, interleaved
   L.segtot = take(8 * integral_scratch_elems(W, H, nseg));
-  L.counts = take(2 * count_elems);
-  L.lohi = take(2 * lohi_elems);
-  L.bcost = take(4 * bcost_elems);
+  L.cnt = take(cnt_bytes);
+  L.grp = take(2 * (size_t)((W + 31) / 32) * H);
   if (debug) {
     L.dcnt = take(4 * N * s);
     L.dvar = take(4 * N * s);
@@ -509,9 +507,10 @@ tm_status forward_materialised(tm_ctx *c, const tm_image *in, const tm_image *ou
 }
 
 // The fused path over a batch of images: one launch per stage for the whole
-// batch, the sweep as a persistent kernel over a queue of (image, strip, rows)
-// items that the device plans from the bin map. `graph`: capture the batch into a CUDA graph and replay it while the
-// batch is unchanged. Returns TM_EUNSUPPORTED if some image cannot be swept.
+// batch, the sweep as a persistent kernel over a queue of (image, strip, row
+// band) tiles. `graph`: capture the batch into a CUDA graph and replay it
+// while the batch is unchanged. Returns TM_EUNSUPPORTED if some image cannot
+// be swept.
 tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image *out, cudaStream_t s,
                         bool graph, bool do_lookup = true, std::vector<Job> *jobs_out = nullptr) {
   tm_status st;
@@ -531,24 +530,32 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   std::vector<Job> jobs((size_t)nimg);
   std::vector<JobLayout> lays((size_t)nimg);
   std::vector<size_t> offs((size_t)nimg);
-  size_t ws_total = 0, smem = 0;
-  const size_t smem_limit = c->smem_optin - 2048;
-  int b_range = 0, b_prep = 0, b_rows = 0, b_cols = 0, b_look = 0, b_scan = 0;
-  std::vector<std::pair<double, int>> order;  // (cost of a uniform tile, image)
+  // two sweep CTAs per SM when the shared memory allows it
+  const size_t smem_limit = std::min(c->smem_optin - 2048, (size_t)110 * 1024);
+  const DevParams P0 = dev_params(c->p, 0);
+  size_t smem = 0;
+  for (int i = 0; i < nimg; ++i) {
+    Job &J = jobs[(size_t)i];
+    memset(&J, 0, sizeof J);
+    if (!plan_sweep(P0, in[i].width, in[i].height, 1, smem_limit, J.plan)) return TM_EUNSUPPORTED;
+    smem = std::max(smem, J.plan.smem);
+  }
+  const int cps = std::max(1, sweep_ctas_per_sm(c->p.n_fields, smem));
+  const int wave = c->num_sms * cps;
+  size_t ws_total = 0;
+  int b_range = 0, b_prep = 0, b_rows = 0, b_cols = 0, b_look = 0;
+  std::vector<std::pair<double, int>> order;  // (work of one tile, image)
   for (int i = 0; i < nimg; ++i) {
     const int W = in[i].width, H = in[i].height;
     const double share = nimg == 1 ? 1.0 : std::max(1.0 / c->num_sms, W * (double)H / total_px);
     Job &J = jobs[(size_t)i];
-    memset(&J, 0, sizeof J);
     J.qbits = choose_qbits(c->p, W, H);
-    const DevParams P = dev_params(c->p, J.qbits);
-    const int sms_share = std::max(1, (int)std::lround(c->num_sms * share));
-    if (!plan_sweep(P, W, H, sms_share, smem_limit, J.plan)) return TM_EUNSUPPORTED;
-    smem = std::max(smem, J.plan.smem);
+    const int target = c->sweep_tiles > 0 ? c->sweep_tiles : std::max(1, (int)std::lround(wave * share));
+    plan_sweep(P0, W, H, target, smem_limit, J.plan);
     integral_layout(W, H, SIZE_MAX, J.nseg, J.seg_rows);
-    sweep_cost_blocks(J.plan, J.rb, J.nb, J.adaptive);
-    lays[(size_t)i] = job_layout(c->p, W, H, J.nseg, sweep_count_elems(J.plan), debug,
-                                 (size_t)J.plan.tiles_x * H, (size_t)J.plan.tiles_x * J.nb);
+    const size_t cnt_bytes = sweep_count_bytes(P0, J.plan, J.cnt_off);
+    J.cnt_wide = J.plan.cnt_wide;
+    lays[(size_t)i] = job_layout(c->p, W, H, J.nseg, cnt_bytes, debug);
     offs[(size_t)i] = ws_total;
     ws_total += lays[(size_t)i].total;
     J.b0[kStRange] = b_range;
@@ -561,43 +568,13 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
     b_cols += integral_col_blocks(W);
     J.b0[kStLook] = b_look;
     b_look += lookup_blocks(W, H);
-    J.b0[kStScan] = b_scan;
-    b_scan += strip_scan_blocks(J.plan, J.nb);
     J.nitem = J.plan.tiles_x * J.plan.tiles_y;
     const double rows = std::min(J.plan.TY + 2.0 * J.plan.Ry + 1, H + 1.0);
     const double cols = std::min(J.plan.TX + 2.0 * J.plan.Rx + 2, W + 1.0);
-    order.push_back({rows * (cols * 0.25 + 300.0) * J.nitem, i});  // the image's work estimate
+    order.push_back({rows * (cols * 0.05 + 100.0) + 6.0 * J.plan.TX * J.plan.TY, i});
   }
-  // A batch's queue is made a whole number of waves of the persistent sweep
-  // (one CTA per SM): a last partial wave would leave most SMs idle while it
-  // runs. The budgets of the images planned on the device are scaled up to
-  // the next multiple of the SM count (at least one tile per strip).
-  if (nimg > 1) {
-    long long total = 0, fixed = 0, minimum = 0;
-    for (const Job &J : jobs) {
-      total += J.nitem;
-      if (!J.adaptive) fixed += J.nitem;
-      else minimum += J.plan.tiles_x;
-    }
-    const long long waves = (total + c->num_sms - 1) / c->num_sms;
-    const long long want = std::max(minimum, waves * c->num_sms - fixed), scalable = total - fixed;
-    if (total > c->num_sms && scalable > 0 && want != scalable) {
-      long long got = 0;
-      for (Job &J : jobs)
-        if (J.adaptive) {
-          J.nitem = (int)std::max<long long>(J.plan.tiles_x, (long long)J.nitem * want / scalable);
-          got += J.nitem;
-        }
-      for (size_t i = 0; got < want; i = (i + 1) % jobs.size())  // the remainder, one tile each
-        if (jobs[i].adaptive) {
-          ++jobs[i].nitem;
-          ++got;
-        }
-    }
-  }
-  // the queue holds each image's tiles together, images with the costliest
-  // tiles first (the device balances the tiles within an image)
-  for (auto &o : order) o.first /= jobs[(size_t)o.second].nitem;
+  // the queue holds each image's tiles together, the images with the
+  // costliest tiles first
   std::stable_sort(order.begin(), order.end(),
                    [](const std::pair<double, int> &a, const std::pair<double, int> &b) { return a.first > b.first; });
   int nitems = 0;
@@ -612,8 +589,7 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   int4 **ditems = graph ? &c->gditems : &c->ditems;
   if ((st = grow_device(c, (void **)djobs, graph ? &c->gdjobs_bytes : &c->djobs_bytes, sizeof(Job) * nimg)))
     return st;
-  if ((st = grow_device(c, (void **)ditems, graph ? &c->gditems_bytes : &c->ditems_bytes,
-                        sizeof(int4) * nitems + sizeof(int))))
+  if ((st = grow_device(c, (void **)ditems, graph ? &c->gditems_bytes : &c->ditems_bytes, sizeof(int4))))
     return st;
   char *ws = static_cast<char *>(c->ws);
   for (int i = 0; i < nimg; ++i) {
@@ -630,9 +606,8 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
     J.s2 = J.s1 + 1;
     J.s_pair = 1;
     J.segtot = reinterpret_cast<long long *>(b + L.segtot);
-    J.counts = reinterpret_cast<uint16_t *>(b + L.counts);
-    J.lohi = reinterpret_cast<uint16_t *>(b + L.lohi);
-    J.bcost = reinterpret_cast<int *>(b + L.bcost);
+    J.cnt = reinterpret_cast<unsigned char *>(b + L.cnt);
+    J.grp = reinterpret_cast<uint16_t *>(b + L.grp);
     if (debug) {
       J.dbg.cnt = reinterpret_cast<unsigned *>(b + L.dcnt);
       J.dbg.sigma2 = reinterpret_cast<float *>(b + L.dvar);
@@ -650,9 +625,8 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   }
   const DevParams P = dev_params(c->p, jobs[0].qbits);  // qbits is per job
   Job *dj = *djobs;
-  int4 *di = *ditems;
-  int *queue = reinterpret_cast<int *>(di + nitems);
-  const int ctas = std::min(nitems, c->num_sms);
+  int *queue = reinterpret_cast<int *>(*ditems);
+  const int ctas = std::min(nitems, wave);
   // a batch is captured on the context's own stream (capture is not allowed on
   // the legacy default stream) and the graph is then launched on the caller's
   const cudaStream_t caller = s;
@@ -669,12 +643,11 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   if (!graph) mark(c, s, ST_PREP);
   n += (run_range ? 2 : 1) + launch_integral_jobs(dj, nimg, b_rows, b_cols, s);
   if (!graph) mark(c, s, ST_INTEGRAL);
-  n += launch_sweep_plan(dj, nimg, b_scan, di, s);  // brings the bin map into L2 for the sweep
-  if (!graph) mark(c, s, ST_PLAN);
-  const int ls = launch_sweep(P, dj, di, nitems, queue, smem, ctas, s);
+  const int ls = launch_sweep(P, dj, nimg, nitems, queue, smem, ctas, s);
+  n += 1;
   if (!graph) mark(c, s, ST_SWEEP);
   if (do_lookup) {
-    n += launch_lookup_counts(P, dj, nimg, b_look, s) + 1;
+    n += launch_lookup_counts(P, dj, nimg, b_look, s);
     if (!graph) mark(c, s, ST_LOOKUP);
   }
   if (graph) {
@@ -1332,6 +1305,12 @@ tm_status tm_set_option(tm_ctx *c, int32_t key, int64_t value) {
   }
   if (key == TM_OPT_BACKWARD_REUSE) {
     c->bwd_reuse = value ? 1 : 0;
+    return TM_OK;
+  }
+  if (key == TM_OPT_SWEEP_TILES) {
+    if (value < 0 || value > (1 << 20)) return fail(c, TM_EINVAL, "TM_OPT_SWEEP_TILES value %lld", (long long)value);
+    c->sweep_tiles = (int)value;
+    drop_graph(c);
     return TM_OK;
   }
   if (key == TM_OPT_HIST_PATH) {

@@ -62,7 +62,6 @@ __global__ void __launch_bounds__(kBT, 6) k_bwd_pixel(DevParams P, Job J, BwdJob
   for (int k = 0; k < 2 * NF; ++k) amax[k] = 0u;
   if (pix < N) {
     const int y = (int)(pix / W), x = (int)(pix - (long long)y * W);
-    const SweepPlan &S = J.plan;
     const float inv_scale = ldexpf(1.f, -J.qbits);
     const float inv_scale2 = inv_scale * inv_scale;
     const long long W1 = (long long)W + 1;
@@ -70,11 +69,7 @@ __global__ void __launch_bounds__(kBT, 6) k_bwd_pixel(DevParams P, Job J, BwdJob
     float wsum = 0.f, accL = 0.f, meanL = 0.f;
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-      unsigned cnt = 0u;
-      for (int sl = S.field_slab0[f]; sl < S.field_slab0[f + 1]; ++sl) {
-        const int T = max(y + S.slab_a[sl] - 1, -1), Bb = min(y + S.slab_b[sl], H - 1);
-        if (Bb > T) cnt += J.counts[sl * N + pix];
-      }
+      const unsigned cnt = load_count(J, f, pix);
       Win w = window_of(P, f, x, y, W, H);
       const long long iA = (long long)w.y0 * W1 + w.x0, iB = (long long)w.y0 * W1 + w.x1 + 1;
       const long long iC = (long long)(w.y1 + 1) * W1 + w.x1 + 1, iD = (long long)(w.y1 + 1) * W1 + w.x0;

@@ -73,34 +73,22 @@ struct DebugPlanes {
   float *l;        // H * W
 };
 
-constexpr int kMaxSlabs = 16;
-
-// Tiling and ring layout of the fused sweep over one image (host-computed).
+// Tiling and shared-memory layout of the fused sweep over one image
+// (host-computed). Tiles are 256-column strips cut into bands of TY rows.
 struct SweepPlan {
   int W, H;
-  int TX, TY, tiles_x, tiles_y;   // output tile and tile grid
-  int Rx, Ry;                     // largest half-width / half-height
-  int nslabs;                     // row slabs over all fields (each < 2^16 pixels)
-  int slab_field[kMaxSlabs];      // field of each slab (slabs are ordered by field)
-  int field_slab0[kMaxFields + 1];  // slabs of field f: field_slab0[f] .. field_slab0[f+1]-1
-  int slab_a[kMaxSlabs];          // first row offset of the slab (relative to y)
-  int slab_b[kMaxSlabs];          // last row offset of the slab
-  int ring_len[kMaxSlabs];        // rows of the parked-corner ring of each slab
-  int ring_off[kMaxSlabs];        // first row of that ring in the shared ring array
-  int ring_total;
-  int bmax;                       // largest slab_b
-  int BR;                         // rows of the tile's own bin ring
-  int nseg_max;                   // 16-column segments of the widest swept row (<= 32)
-  int rows_max;                   // rows of the tallest swept band of a uniform tile
-  int nw_max;                     // threshold words (two thresholds each) allocated
-  int text_max;                   // widest tile row including both side bands
-  int cstride;                    // words per threshold row in shared memory (odd)
+  int TX, TY, tiles_x, tiles_y;   // own tile size and grid
+  int Rx, Ry;                     // largest half-width / half-height (clipped to W-1 / H-1)
+  int nch_max;                    // 32-column chunks of the widest swept row
+  int bstride;                    // uint16 entries per threshold row of the in-chunk counts
+  int kcap;                       // thresholds held in shared memory at once
+  int cnt_wide;                   // bit f: field f's counts are uint32 (else uint16)
   size_t smem;                    // dynamic shared memory bytes
 };
 
 // Batched stages; every stage kernel of a batch maps its blocks to images
 // through the per-image first-block offsets b0[stage].
-enum StageId { kStRange = 0, kStPrep, kStRows, kStCols, kStLook, kStScan, kNumStages };
+enum StageId { kStRange = 0, kStPrep, kStRows, kStCols, kStLook, kNumStages };
 
 // One image of a batch: its buffers and its share of every batched launch.
 struct Job {
@@ -112,18 +100,17 @@ struct Job {
   long long *s1, *s2;       // (H+1)*(W+1) integral images of q and q^2; with s_pair
                             //   interleaved: position i of both at s1[2i], s1[2i+1], s2 = s1 + 1
   long long *segtot;        // integral-image scratch, integral_scratch_elems(W, H, nseg)
-  uint16_t *counts;         // nslabs*H*W slab counts from the sweep
-  uint16_t *lohi;           // tiles_x*H: per strip and row, smallest | largest << 8 bin
-                            //   over the strip's swept columns
-  int *bcost;               // tiles_x*nb: per strip, summed row costs of each block of rb rows
+  unsigned char *cnt;       // Eq. 1 numerators from the sweep: field f's H*W plane at
+                            //   cnt + cnt_off[f], uint32 if bit f of cnt_wide, else uint16
+  long long cnt_off[kMaxFields];
+  int cnt_wide;
+  uint16_t *grp;            // per row and 32-column group: smallest | largest << 8 bin
   DebugPlanes dbg;
   int qbits;
   int s_pair;               // 1: s1 and s2 interleaved (the forward's workspace)
   int nseg, seg_rows;       // integral images: row segments of the tiles
   int b0[kNumStages];       // first block of this job in each batched stage
-  int rb, nb;               // rows per cost block, blocks per strip
-  int adaptive;             // 1: tile heights from the row costs; 0: the plan's uniform TY
-  int item0, nitem;         // this job's slots in the sweep queue
+  int item0, nitem;         // this job's slots in the sweep queue (uniform tiles, row-major)
   SweepPlan plan;           // sweep tiling of this image
 };
 
@@ -280,18 +267,24 @@ __device__ __forceinline__ Win window_of(const DevParams &P, int f, int x, int y
   return w;
 }
 
-// Exact window variance of q from its window sums (s1 = sum q, s2 = sum q^2):
-// N s2 - s1^2 evaluated in 128-bit integers, rounded once to float, then
-// scaled by 1/N^2 (rN = rounded 1/N) and 2^-2Q to lhat units.
+// Window variance of q from its exact window sums s1 = sum q and s2 = sum q^2
+// (modulo 2^64) over N pixels. With m the integer nearest a float estimate of
+// the mean (within a few units of it) and d = s1 - m N,
+//     T = sum (q - m)^2 = s2 - m (s1 + d)     exact in wrapping 64-bit arithmetic,
+//     N^2 var = N T - d^2,
+// so var = (T - d^2 / N) / N. T and d are exact; d^2 / N stays below a few N,
+// so the one float subtraction loses at most a few bits whenever var >= 1
+// unit^2, and far less than the quantisation step below that. rN = rounded
+// 1/N; inv_scale2 = 2^-2Q converts to lhat units.
 __device__ __forceinline__ float window_variance(long long s1, long long s2, unsigned long long N,
                                                  float rN, float inv_scale2) {
-  unsigned long long a1 = (unsigned long long)(s1 < 0 ? -s1 : s1);
-  unsigned __int128 num = (unsigned __int128)N * (unsigned long long)s2 -
-                          (unsigned __int128)a1 * a1;
-  unsigned long long hi = (unsigned long long)(num >> 64);
-  unsigned long long lo = (unsigned long long)num;
-  float numf = __ull2float_rn(hi) * 18446744073709551616.0f + __ull2float_rn(lo);
-  return numf * (rN * rN * inv_scale2);
+  const long long m = (long long)rintf((float)s1 * rN);
+  const long long d = s1 - m * (long long)N;
+  const unsigned long long T =
+      (unsigned long long)s2 - (unsigned long long)m * (unsigned long long)(s1 + d);
+  const float df = (float)d;
+  const float v = fmaf(-df * rN, df, __ull2float_rn(T)) * rN;
+  return fmaxf(v, 0.f) * inv_scale2;
 }
 
 // Eq. 2, Eq. 4, Eq. 3 from per-field counts, reciprocal areas and variances.
@@ -317,19 +310,11 @@ __device__ __forceinline__ float fuse_fields(const DevParams &P, const unsigned 
   return wsum > 0.f ? __fdividef(acc, wsum) : __fdividef(mean, (float)P.n_fields);  // Eq. 3
 }
 
-// Eq. 1 numerators of every field from the sweep's per-slab counts at pixel
-// (x, y) = pix: a slab whose rows all fall outside the image counts 0.
-__device__ __forceinline__ void slab_counts(const SweepPlan &S, const uint16_t *__restrict__ counts,
-                                            long long N, long long pix, int y, int H,
-                                            unsigned *cnt) {
-#pragma unroll
-  for (int f = 0; f < kMaxFields; ++f) {
-    cnt[f] = 0u;
-    for (int s = S.field_slab0[f]; s < S.field_slab0[f + 1]; ++s) {
-      const int T = max(y + S.slab_a[s] - 1, -1), B = min(y + S.slab_b[s], H - 1);
-      if (B > T) cnt[f] += __ldg(counts + s * N + pix);
-    }
-  }
+// Eq. 1 numerator of field f at pixel index pix from the sweep's count planes.
+__device__ __forceinline__ unsigned load_count(const Job &J, int f, long long pix) {
+  const unsigned char *pl = J.cnt + J.cnt_off[f];
+  return ((J.cnt_wide >> f) & 1) ? __ldg(reinterpret_cast<const unsigned *>(pl) + pix)
+                                 : (unsigned)__ldg(reinterpret_cast<const uint16_t *>(pl) + pix);
 }
 
 // Eq. 12 with the ratio clamped at zero; inv_i = 1 / i. The power is taken

@@ -51,20 +51,16 @@ int launch_integral_histogram(const uint8_t *bins, int W, int H, int n_bins, boo
                               uint32_t *planes, void *scratch, cudaStream_t s);
 
 // Stage a3', fused: plan of one image's sweep (false if the fields do not
-// fit), slab-count elements, and the persistent launch over a queue of
-// (job, tile) items sorted longest first.
-bool plan_sweep(const DevParams &P, int W, int H, int num_sms, size_t smem_limit, SweepPlan &S);
-size_t sweep_count_elems(const SweepPlan &S);
-// Row blocking of the per-strip cost scan and whether the adaptive tiling
-// applies to this plan (its prefix sums fit the planner's shared memory).
-void sweep_cost_blocks(const SweepPlan &S, int &rb, int &nb, int &adaptive);
-int strip_scan_blocks(const SweepPlan &S, int nb);
-// Per strip and row bin ranges and per block row costs of every job, then one
-// CTA per job writing its sweep items (job, strip, Y0, Y1) into
-// items[J.item0 .. J.item0 + J.nitem) (job = -1 for unused slots).
-int launch_sweep_plan(const Job *jobs, int njobs, int scan_blocks, int4 *items, cudaStream_t s);
-int launch_sweep(const DevParams &P, const Job *jobs, const int4 *items, int nitems, int *queue,
-                 size_t smem, int ctas, cudaStream_t s);
+// fit: a swept row over 32 chunks of 32 columns, or windows over 2047 rows);
+// tiles_target: tiles wanted for the image (a whole number of waves). Count
+// plane bytes of the plan (off[f]: byte offset of field f's plane). CTAs of
+// the sweep that fit one SM at `smem` bytes of dynamic shared memory. The
+// persistent launch over items [0, nitems) of the jobs' uniform tilings.
+bool plan_sweep(const DevParams &P, int W, int H, int tiles_target, size_t smem_limit, SweepPlan &S);
+size_t sweep_count_bytes(const DevParams &P, const SweepPlan &S, long long *off);
+int sweep_ctas_per_sm(int n_fields, size_t smem);
+int launch_sweep(const DevParams &P, const Job *jobs, int njobs, int nitems, int *queue, size_t smem, int ctas,
+                 cudaStream_t s);
 
 // Stage a4: per-pixel lookup, tone curve, fusion and colour restoration.
 int lookup_blocks(int W, int H);

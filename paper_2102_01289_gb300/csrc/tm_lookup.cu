@@ -2,8 +2,8 @@
 //
 // One thread per pixel. The Eq. 1 numerator of every field comes either from
 // the materialised cumulative integral histogram (C_b = sum_{k < b} H_k, one
-// box sum of the plane of the pixel's own bin, Eq. 9) or from the per-slab
-// counts written by the fused sweep. The window sums of q and q^2 are box sums
+// box sum of the plane of the pixel's own bin, Eq. 9) or from the count
+// planes written by the fused sweep. The window sums of q and q^2 are box sums
 // of their integral images (Eq. 6), giving the exact window variance (Eq. 10);
 // then Eq. 2, Eq. 4, the fusion of Eq. 3 and the colour restoration of Eq. 12.
 // The fields are evaluated in one pass instead of the paper's per-scale loop
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(256, 8)
   finish_pixel(in, out, P, x, y, fu, dbg);
 }
 
-// Lookup from the sweep's per-slab counts, over a batch of jobs: block ->
+// Lookup from the sweep's count planes, over a batch of jobs: block ->
 // (image, 32 x 8 pixel tile). NF = number of fields, so the field loop is
 // straight-line code and the loads of all fields can be issued together.
 // Eight blocks per SM (32 registers) keep more of those loads in flight.
@@ -125,17 +125,12 @@ __global__ void __launch_bounds__(256, 8) k_lookup_counts(DevParams P, const Job
   const int x = (lb % bx) * 32 + (threadIdx.x & 31);
   const int y = (lb / bx) * 8 + (threadIdx.x >> 5);
   if (x >= W || y >= H) return;
-  const SweepPlan &S = J.plan;
-  const long long N = (long long)W * H, pix = (long long)y * W + x;
+  const long long pix = (long long)y * W + x;
   const float inv_scale2 = ldexpf(1.f, -2 * J.qbits);  // Q is per image
   Fusion fu;
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
-    unsigned cnt = 0u;
-    for (int s = S.field_slab0[f]; s < S.field_slab0[f + 1]; ++s) {
-      const int T = max(y + S.slab_a[s] - 1, -1), B = min(y + S.slab_b[s], H - 1);
-      if (B > T) cnt += __ldg(J.counts + s * N + pix);
-    }
+    const unsigned cnt = load_count(J, f, pix);
     fold_field(P, f, x, y, W, H, cnt, reinterpret_cast<const longlong2 *>(J.s1), J.qbits, inv_scale2, fu,
                J.dbg);
   }

@@ -174,7 +174,9 @@ __global__ void __launch_bounds__(256) k_range(const Job *__restrict__ jobs, int
 
 // Bin map (Section II-A, edges from k_range) and the quantised values whose
 // window variance Eq. 10 takes: the normalised log, or i / imax under
-// TM_FLAG_VAR_LINEAR. One thread per group of four pixels.
+// TM_FLAG_VAR_LINEAR. One thread per group of four pixels; rows are padded to
+// whole 32-pixel groups so that eight consecutive lanes share one group,
+// whose bin range (smallest | largest << 8) goes to J.grp for the sweep.
 __global__ void __launch_bounds__(256) k_prep(const Job *__restrict__ jobs, int njobs, int n_bins,
                                               int flags) {
   __shared__ float thr[kMaxBins];
@@ -196,36 +198,52 @@ __global__ void __launch_bounds__(256) k_prep(const Job *__restrict__ jobs, int 
   const int W = in.W, H = in.H, qbits = J.qbits;
   uint8_t *bins = J.bins;
   int32_t *q = J.q;
-  const int gpr = (W + 3) >> 2;
+  const int G = (W + 31) >> 5;  // 32-pixel groups per row
+  const int gpr = 8 * G;        // groups of four pixels per padded row
   const int ng = gpr * H;
+  const int lane = threadIdx.x & 31;
   unsigned bmin = 0x7f800000u, bmax = 0u;  // this image's own range (streaming reuse)
-  for (int gi = lb * blockDim.x + threadIdx.x; gi < ng; gi += nb * blockDim.x) {
+  // whole warps iterate together (the group shuffles need all lanes)
+  for (int g0 = lb * blockDim.x + (threadIdx.x & ~31); g0 < ng; g0 += nb * blockDim.x) {
+    const int gi = g0 + lane;
     const int y = gi / gpr, x = (gi - y * gpr) * 4;
-    const int n = min(4, W - x);
-    float r[4], g[4], b[4];
-    load4(in, vec, x, y, n, r, g, b);
-    unsigned bq = 0;
-    int qq[4];
+    const int n = gi < ng ? max(0, min(4, W - x)) : 0;
+    int kmin = 256, kmax = -1;
+    if (n > 0) {
+      float r[4], g[4], b[4];
+      load4(in, vec, x, y, n, r, g, b);
+      unsigned bq = 0;
+      int qq[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const float l = luminance(r[i], g[i], b[i]);
-      bq |= (unsigned)bin_of(l, thr, n_bins) << (8 * i);
-      qq[i] = lin ? quantise_lin(l, sst, qbits) : quantise_log(l, sst, qbits);
-      if (i < n) {
-        bmin = min(bmin, __float_as_uint(l));
-        bmax = max(bmax, __float_as_uint(l));
+      for (int i = 0; i < 4; ++i) {
+        const float l = luminance(r[i], g[i], b[i]);
+        const int bi = bin_of(l, thr, n_bins);
+        bq |= (unsigned)bi << (8 * i);
+        qq[i] = lin ? quantise_lin(l, sst, qbits) : quantise_log(l, sst, qbits);
+        if (i < n) {
+          bmin = min(bmin, __float_as_uint(l));
+          bmax = max(bmax, __float_as_uint(l));
+          kmin = min(kmin, bi);
+          kmax = max(kmax, bi);
+        }
+      }
+      const long long o = (long long)y * W + x;
+      if (n == 4 && (o & 3) == 0) {
+        *reinterpret_cast<unsigned *>(bins + o) = bq;
+        *reinterpret_cast<int4 *>(q + o) = make_int4(qq[0], qq[1], qq[2], qq[3]);
+      } else {
+        for (int i = 0; i < n; ++i) {
+          bins[o + i] = (uint8_t)(bq >> (8 * i));
+          q[o + i] = qq[i];
+        }
       }
     }
-    const long long o = (long long)y * W + x;
-    if (n == 4 && (o & 3) == 0) {
-      *reinterpret_cast<unsigned *>(bins + o) = bq;
-      *reinterpret_cast<int4 *>(q + o) = make_int4(qq[0], qq[1], qq[2], qq[3]);
-    } else {
-      for (int i = 0; i < n; ++i) {
-        bins[o + i] = (uint8_t)(bq >> (8 * i));
-        q[o + i] = qq[i];
-      }
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+      kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
     }
+    if (J.grp && (lane & 7) == 0 && kmax >= 0) J.grp[(long long)y * G + (x >> 5)] = (uint16_t)(kmin | (kmax << 8));
   }
   // streaming reuse: the bins above used an earlier frame's range; this
   // frame's own range goes to st_next for the frame after
@@ -241,7 +259,7 @@ int range_blocks(int W, int H, int num_sms, double share) {
 }
 
 int prep_blocks(int W, int H, int num_sms, double share) {
-  const long long groups = (long long)((W + 3) / 4) * H;
+  const long long groups = (long long)8 * ((W + 31) / 32) * H;
   long long b = (groups + 255) / 256;
   const long long cap = (long long)(16.0 * num_sms * share) + 1;
   if (b > cap) b = cap;

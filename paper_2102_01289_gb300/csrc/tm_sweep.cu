@@ -1,0 +1,498 @@
+// tm_sweep.cu -- fused integral-histogram sweep: the Eq. 1 numerator of every
+// field at every pixel, without materialising the integral histogram.
+//
+// For a threshold k, let C_k(u, v) be the integral histogram in cumulative
+// form (Eq. 7-8 summed over the bins below k): the number of pixels (u', v')
+// with u0 <= u' <= u, v0 < v' <= v and b(u', v') < k, over a tile-local
+// origin (u0 - 1, v0). A pixel p = (x, y) with threshold k = b(p) (b(p) + 1
+// under TM_FLAG_CDF_INCLUSIVE) needs, per field with half-sizes (rx, ry),
+// the box sum of Eq. 9 over its clipped window [xl, xr] x [yt, yb]:
+//     cnt = E(yb) - E(yt - 1),   E(v) = C_k(xr, v) - C_k(xl - 1, v).
+// Each CTA owns a tile of 256 columns x TY rows and sweeps the rows of the
+// tile widened by the largest half-height above and below it, over its
+// columns widened by the largest half-width on both sides. When the sweep
+// has taken row v in, every pixel whose window starts at row v + 1 takes
+// E(v) (a "top" event, parked in the pixel's count slot) and every pixel
+// whose window ends at row v takes E(v) and subtracts the parked value (a
+// "bottom" event, which leaves the count in the slot).
+//
+// The swept columns are cut into 32-column chunks aligned to the image, one
+// warp lane per column. For every threshold k of the tile the shared-memory
+// state is
+//     C_k(u) = PT_k(c) + B_k(u) + (o + 1) m_k(c)        (c = chunk of u, o = u - 32 c)
+// where, over the rows swept so far,
+//     m_k(c)  counts the rows in which all of chunk c lies below k,
+//     B_k(u)  sums the in-chunk prefix counts #{u' in c, u' <= u : b < k} of
+//             the rows in which chunk c holds bins on both sides of k, and
+//     PT_k(c) sums the counts below k of all chunks left of c.
+// So a row costs per-column work only where a bin edge crosses a chunk (one
+// ballot and popcount per such threshold), plus one prefix over the chunks
+// per threshold inside the row's bin range and one add per chunk for the
+// thresholds above it. PT and m share one word (21 + 11 bits: at most 2047
+// swept rows and 32 chunks, so neither field overflows), B fits 16 bits (32
+// columns x 2047 rows), and every E is exact below 2^21.
+//
+// Per row the CTA runs two phases separated by barriers:
+//   1. the corner events of the previous row (reading the state) and the
+//      chunk summaries of this row (bin range per chunk, mixed counts);
+//   2. the state update of this row (B of the mixed chunks, PT and m).
+// The count slots are the count planes handed to the lookup: a field whose
+// window can hold 2^16 pixels or more gets uint32 slots, the others uint16
+// (whose counts are exact modulo 2^16). A tile whose own pixels use more
+// thresholds than the shared memory holds is swept once per group of them.
+#include <algorithm>
+
+#include "tm_kernels.cuh"
+
+namespace tmk {
+namespace {
+
+constexpr int kNT = 512;
+constexpr int kWarps = kNT / 32;
+constexpr int kTX = 256;            // own columns of a tile; threads t and t + 256 share column t
+constexpr int kMaxChunks = 32;      // 32-column chunks of a swept row
+constexpr int kChunksPerWarp = kMaxChunks / kWarps;
+constexpr int kMaxRows = 2047;      // swept rows of a tile
+constexpr unsigned kPTMask = (1u << 21) - 1;
+constexpr int kPStride = 33;        // words per threshold row of PT | m << 21
+
+static_assert(2 * kTX == kNT, "one top and one bottom event thread per own column");
+
+// The sweep's dynamic shared memory (named at file scope so that every access
+// compiles to a shared-memory load or store).
+extern __shared__ __align__(16) unsigned char g_smem[];
+
+// Shared-memory layout of a CTA (byte offsets from the dynamic array):
+//   PT     kcap x kPStride words   PT_k(c) | m_k(c) << 21
+//   M      kcap words              rows whose bins all lie below k (lazy: such
+//                                  a row adds u - u0 + 1 at every column u)
+//   red    64 words                reductions
+//   rowb   32 x 32 bytes           bins of the current swept row, by chunk
+//   B      kcap x bstride uint16   in-chunk prefix counts of mixed rows
+struct Lay {
+  unsigned PT, M, red, rowb, B;
+};
+
+__host__ __device__ __forceinline__ Lay layout(int kcap) {
+  Lay l;
+  l.PT = 0;
+  l.M = l.PT + (unsigned)kcap * kPStride * 4;
+  l.red = l.M + (unsigned)kcap * 4;
+  l.rowb = l.red + 64 * 4;
+  l.B = l.rowb + kMaxChunks * 32;
+  return l;
+}
+
+__device__ __forceinline__ void put_slot(unsigned char *pl, bool wide, long long pix, unsigned val) {
+  if (wide) reinterpret_cast<unsigned *>(pl)[pix] = val;
+  else reinterpret_cast<uint16_t *>(pl)[pix] = (uint16_t)val;
+}
+
+__device__ __forceinline__ unsigned get_slot(const unsigned char *pl, bool wide, long long pix) {
+  return wide ? reinterpret_cast<const unsigned *>(pl)[pix] : (unsigned)reinterpret_cast<const uint16_t *>(pl)[pix];
+}
+
+// E = C_k(jr) - C_k(jl) from the state of threshold row kk (jl = -1: the
+// origin column, where C = 0). With M_k rows lying wholly below k, C_k(j)
+// gains M_k (j + 1), so the pair gains M_k (jr - jl).
+__device__ __forceinline__ unsigned pair_value(const unsigned *PT, const unsigned *M, const uint16_t *B, int bstride,
+                                               int kk, int jr, int jl) {
+  const unsigned *pr = PT + kk * kPStride;
+  const uint16_t *br = B + kk * bstride;
+  const unsigned wr = pr[jr >> 5];
+  unsigned e = (wr & kPTMask) + (unsigned)br[jr] + (unsigned)((jr & 31) + 1) * (wr >> 21) +
+               M[kk] * (unsigned)(jr - jl);
+  if (jl >= 0) {
+    const unsigned wl = pr[jl >> 5];
+    e -= (wl & kPTMask) + (unsigned)br[jl] + (unsigned)((jl & 31) + 1) * (wl >> 21);
+  }
+  return e;
+}
+
+// One tile: rows [Y0, Y1) of strip `strip` of job J.
+template <int NF>
+__device__ __forceinline__ void sweep_tile(const DevParams &P, const Job &J, int strip, int Y0, int Y1) {
+  unsigned char *const smem = g_smem;
+  const SweepPlan &S = J.plan;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int W = S.W, H = S.H;
+  const int X0 = strip * kTX, X1 = min(X0 + kTX, W);
+  Y1 = min(Y1, H);
+  const int cL = max(X0 - S.Rx - 1, -1);
+  const int cR = min(X1 - 1 + S.Rx, W - 1);
+  const int g0 = (cL + 1) >> 5;
+  const int nch = (cR >> 5) - g0 + 1;
+  const int rL = max(Y0 - S.Ry - 1, -1);
+  const int rR = min(Y1 - 1 + S.Ry, H - 1);
+  const int n = P.n_bins, incl = (P.flags & kFlagCdfIncl) ? 1 : 0;
+  const int kcap = S.kcap, bstride = S.bstride;
+  const Lay L = layout(kcap);
+  unsigned *const sPT = reinterpret_cast<unsigned *>(smem + L.PT);
+  unsigned *const sM = reinterpret_cast<unsigned *>(smem + L.M);
+  int *const sred = reinterpret_cast<int *>(smem + L.red);
+  uint8_t *const srow = smem + L.rowb;
+  uint16_t *const sB = reinterpret_cast<uint16_t *>(smem + L.B);
+  const uint8_t *__restrict__ bins = J.bins;
+  const uint16_t *__restrict__ grp = J.grp;
+  const unsigned wide = (unsigned)J.cnt_wide;
+  const int G = (W + 31) >> 5;
+  unsigned char *pl[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) pl[f] = J.cnt + J.cnt_off[f];
+
+  // ---- bin range of the tile's own pixels, from the per-row group summary ----
+  {
+    const int gx0 = X0 >> 5, ngx = ((X1 - 1) >> 5) - gx0 + 1;
+    int bmin = 255, bmax = 0;
+    for (int i = tid; i < (Y1 - Y0) * ngx; i += kNT) {
+      const int yy = i / ngx;
+      const unsigned v = grp[(long long)(Y0 + yy) * G + gx0 + (i - yy * ngx)];
+      bmin = min(bmin, (int)(v & 0xffu));
+      bmax = max(bmax, (int)(v >> 8));
+    }
+    bmin = __reduce_min_sync(0xffffffffu, bmin);
+    bmax = __reduce_max_sync(0xffffffffu, bmax);
+    if (lane == 0) {
+      sred[wid] = bmin;
+      sred[32 + wid] = bmax;
+    }
+  }
+  __syncthreads();
+  int bmin = 255, bmax = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    bmin = min(bmin, sred[w]);
+    bmax = max(bmax, sred[32 + w]);
+  }
+  const int klo = max(1, bmin + incl), khi = min(n - 1, bmax + incl);
+  const int nK = max(0, khi - klo + 1);
+  const int npass = max(1, (nK + kcap - 1) / kcap);
+
+  // ---- the thread's event column: top events (tid < 256) or bottom events ----
+  const int xo = tid & (kTX - 1);
+  const bool is_bottom = tid >= kTX;
+  const int x = X0 + xo;
+  const bool col_ok = x < X1;
+  // per field: half-height, corner columns (relative to 32 g0; jl = -1 is the
+  // origin), and the offset of the event pixel's row from the swept row
+  int ry[NF], jr[NF], jl[NF], eoff[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    ry[f] = min(P.ry[f], H - 1);
+    const int rx = min(P.rx[f], W - 1);
+    jr[f] = min(x + rx, W - 1) - 32 * g0;
+    jl[f] = max(x - rx, 0) - 1 - 32 * g0;
+    eoff[f] = is_bottom ? -ry[f] : ry[f] + 1;
+  }
+  const unsigned lt = (1u << lane) - 1u, le = lt | (1u << lane);
+
+  for (int pass = 0; pass < npass; ++pass) {
+    const int kp0 = klo + pass * kcap;
+    const int nKp = max(0, min(kcap, khi - kp0 + 1));
+    const bool specials = pass == 0;  // thresholds 0 and n need no state: taken in the first pass
+    __syncthreads();  // the previous pass (or tile) has finished reading the state
+    for (int i = tid; i < nKp * kPStride; i += kNT) sPT[i] = 0u;
+    for (int i = tid; i < nKp; i += kNT) sM[i] = 0u;
+    {
+      unsigned *b32 = reinterpret_cast<unsigned *>(sB);
+      const int words = (nKp * bstride) >> 1;
+      for (int i = tid; i < words; i += kNT) b32[i] = 0u;
+    }
+    // bins of a swept row, a warp per chunk (wid, wid + 16; 256 marks columns
+    // past the image), and the chunks' bin ranges (lanes = chunks) from the
+    // group summary of the bin pass; both loaded one row ahead
+    int bcur[kChunksPerWarp], bnxt[kChunksPerWarp];
+    unsigned gcur, gnxt = 0xffu;
+    {
+      const int v = rL + 1;
+#pragma unroll
+      for (int q = 0; q < kChunksPerWarp; ++q) {
+        const int c = wid + q * kWarps, col = 32 * (g0 + c) + lane;
+        bcur[q] = (c < nch && col < W && v <= rR) ? (int)__ldg(bins + (long long)v * W + col) : 256;
+        bnxt[q] = 256;
+      }
+      gcur = (lane < nch && v <= rR) ? (unsigned)__ldg(grp + (long long)v * G + g0 + lane) : 0xffu;
+    }
+    // events of the pending row: act bit f = the thread's event of field f is
+    // live; ebin = the bin of its pixel; epark = the parked top value (bottom
+    // events; loaded after the barrier that orders it behind the top events
+    // of the same phase)
+    unsigned act = 0u;
+    int ebin[NF];
+    unsigned epark[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      ebin[f] = 0;
+      epark[f] = 0u;
+    }
+    for (int v = rL + 1; v <= rR + 1; ++v) {
+      // ---- phase 1: events of row v - 1; bins of row v into shared memory ----
+      const bool last = v > rR;
+      unsigned nact = 0u;
+      int nbin[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const int y = v + eoff[f];
+        const bool ok = !last && col_ok && (unsigned)(y - Y0) < (unsigned)(Y1 - Y0) && !(is_bottom && v == H - 1);
+        nbin[f] = ok ? (int)__ldg(bins + (long long)y * W + x) : 0;
+        nact |= (ok ? 1u : 0u) << f;
+      }
+      if (!last) {
+#pragma unroll
+        for (int q = 0; q < kChunksPerWarp; ++q) {
+          const int c = wid + q * kWarps, col = 32 * (g0 + c) + lane;
+          bnxt[q] = (c < nch && col < W && v + 1 <= rR) ? (int)__ldg(bins + (long long)(v + 1) * W + col) : 256;
+        }
+        gnxt = (lane < nch && v + 1 <= rR) ? (unsigned)__ldg(grp + (long long)(v + 1) * G + g0 + lane) : 0xffu;
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {  // events of row v - 1
+        if (!((act >> f) & 1u)) continue;
+        const int k = ebin[f] + incl, kk = k - kp0;
+        unsigned E;
+        if ((unsigned)kk < (unsigned)nKp) {
+          E = pair_value(sPT, sM, sB, bstride, kk, jr[f], jl[f]);
+        } else {  // thresholds outside this pass: 0 and n in the first pass, the others later
+          if (!(specials && (k <= 0 || k >= n))) continue;
+          E = k <= 0 ? 0u : (unsigned)(jr[f] - jl[f]) * (unsigned)(v - 1 - rL);
+        }
+        put_slot(pl[f], (wide >> f) & 1u, (long long)(v - 1 + eoff[f]) * W + x, is_bottom ? E - epark[f] : E);
+      }
+      if (last) break;
+#pragma unroll
+      for (int q = 0; q < kChunksPerWarp; ++q) {
+        const int c = wid + q * kWarps;
+        if (c < nch) srow[32 * c + lane] = (uint8_t)min(bcur[q], 255);
+      }
+      __syncthreads();
+      // ---- phase 2: state update of row v, a warp per threshold (lanes =
+      // chunks); parked values for row v's events ----
+      act = nact;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        ebin[f] = nbin[f];
+        epark[f] = 0u;
+        if (is_bottom && ((act >> f) & 1u)) {
+          const int y = v + eoff[f];
+          if (max(y - ry[f], 0) - 1 > rL) epark[f] = get_slot(pl[f], (wide >> f) & 1u, (long long)y * W + x);
+        }
+      }
+      {
+        const bool lc = lane < nch;
+        const int cmin = lc ? (int)(gcur & 0xffu) : 256, cmax = lc ? (int)(gcur >> 8) : -1;
+        const int rmin = __reduce_min_sync(0xffffffffu, cmin);
+        const int rmax = __reduce_max_sync(0xffffffffu, cmax);
+        // thresholds above every bin of the row: the lazy whole-row count
+        if (wid == kWarps - 1)
+          for (int kk = max(0, rmax + 1 - kp0) + lane; kk < nKp; kk += 32) sM[kk] += 1u;
+        // thresholds inside the row's range: prefix over the chunks
+        const int kk_hi = min(nKp - 1, rmax - kp0);
+        for (int kk = max(0, rmin + 1 - kp0) + wid; kk <= kk_hi; kk += kWarps) {
+          const int k = kp0 + kk;
+          const bool below = lc && cmax < k;  // the chunk lies wholly below k
+          const unsigned bm = __ballot_sync(0xffffffffu, below);
+          unsigned mm = __ballot_sync(0xffffffffu, lc && cmin < k && k <= cmax);  // bins on both sides
+          unsigned carry = 32u * (unsigned)__popc(bm & lt);
+          while (mm) {
+            const int c = __ffs(mm) - 1;
+            mm &= mm - 1;
+            // lanes = the columns of mixed chunk c: in-chunk prefix counts
+            const int b = (32 * (g0 + c) + lane < W) ? (int)srow[32 * c + lane] : 256;
+            const unsigned mask = __ballot_sync(0xffffffffu, b < k);
+            uint16_t *bp = sB + kk * bstride + 32 * c + lane;
+            *bp = (uint16_t)(*bp + __popc(mask & le));
+            if (lane > c) carry += (unsigned)__popc(mask);
+          }
+          if (lc) sPT[kk * kPStride + lane] += carry + (below ? (1u << 21) : 0u);
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < kChunksPerWarp; ++q) bcur[q] = bnxt[q];
+      gcur = gnxt;
+    }
+    // windows clipped at the image's last row all end there: every thread
+    // takes (row, column) pairs of them, four at a time
+    if (rR == H - 1) {
+      const int TXc = X1 - X0;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const int ybeg = max(H - 1 - ry[f], Y0), nyb = Y1 - ybeg;
+        if (nyb <= 0) continue;
+        const int rx = min(P.rx[f], W - 1);
+        const int total = nyb * TXc;
+        for (int i0 = tid; i0 < total; i0 += 4 * kNT) {
+          int bb[4], xx[4];
+          unsigned pk[4];
+          long long px[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * kNT;
+            bb[u] = -1;
+            if (i < total) {
+              const int yy = i / TXc, y = ybeg + yy;
+              xx[u] = X0 + (i - yy * TXc);
+              px[u] = (long long)y * W + xx[u];
+              bb[u] = (int)__ldg(bins + px[u]);
+              pk[u] = max(y - ry[f], 0) - 1 > rL ? get_slot(pl[f], (wide >> f) & 1u, px[u]) : 0u;
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (bb[u] < 0) continue;
+            const int k = bb[u] + incl, kk = k - kp0;
+            const int cjr = min(xx[u] + rx, W - 1) - 32 * g0, cjl = max(xx[u] - rx, 0) - 1 - 32 * g0;
+            unsigned E;
+            if ((unsigned)kk < (unsigned)nKp) {
+              E = pair_value(sPT, sM, sB, bstride, kk, cjr, cjl);
+            } else {
+              if (!(specials && (k <= 0 || k >= n))) continue;
+              E = k <= 0 ? 0u : (unsigned)(cjr - cjl) * (unsigned)(H - 1 - rL);
+            }
+            put_slot(pl[f], (wide >> f) & 1u, px[u], E - pk[u]);
+          }
+        }
+      }
+    }
+  }
+}
+
+// Persistent sweep over the tiles of a batch. Item i belongs to the job whose
+// slots [item0, item0 + nitem) hold it (any order of the jobs); its tile is
+// (strip, row band) in row-major order of the job's uniform tiling.
+template <int NF>
+__global__ void __launch_bounds__(kNT, 2) k_sweep(DevParams P, const Job *__restrict__ jobs, int njobs,
+                                                  int nitems, int *queue) {
+  __shared__ int item_sh, job_sh;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      item_sh = atomicAdd(queue, 1);
+      job_sh = -1;
+    }
+    __syncthreads();
+    const int it = item_sh;
+    if (it >= nitems) break;
+    for (int j = threadIdx.x; j < njobs; j += kNT)
+      if (jobs[j].item0 <= it && it < jobs[j].item0 + jobs[j].nitem) job_sh = j;
+    __syncthreads();
+    const int jb = job_sh;
+    if (jb >= 0) {
+      const Job &J = jobs[jb];
+      const int local = it - J.item0;
+      const int strip = local % J.plan.tiles_x, band = local / J.plan.tiles_x;
+      sweep_tile<NF>(P, J, strip, band * J.plan.TY, (band + 1) * J.plan.TY);
+    }
+    __syncthreads();  // item_sh and job_sh are rewritten for the next item
+  }
+}
+
+size_t smem_for(int kcap, int bstride) { return layout(kcap).B + (size_t)kcap * bstride * 2; }
+
+}  // namespace
+
+bool plan_sweep(const DevParams &P, int W, int H, int tiles_target, size_t smem_limit, SweepPlan &S) {
+  SweepPlan s{};
+  s.W = W;
+  s.H = H;
+  int Rx = 0, Ry = 0;
+  for (int f = 0; f < P.n_fields; ++f) {
+    Rx = max(Rx, min(P.rx[f], W - 1));
+    Ry = max(Ry, min(P.ry[f], H - 1));
+  }
+  s.Rx = Rx;
+  s.Ry = Ry;
+  s.TX = kTX;
+  s.tiles_x = (W + kTX - 1) / kTX;
+  // widest swept row: a strip of 256 columns widened by Rx + 1 on the left and
+  // Rx on the right, rounded out to 32-column chunks
+  int nch_max = 0;
+  for (int strip = 0; strip < s.tiles_x; ++strip) {
+    const int X0 = strip * kTX, X1 = min(X0 + kTX, W);
+    const int cL = max(X0 - Rx - 1, -1), cR = min(X1 - 1 + Rx, W - 1);
+    nch_max = max(nch_max, (cR >> 5) - ((cL + 1) >> 5) + 1);
+  }
+  if (nch_max > kMaxChunks) return false;
+  if (2 * Ry + 1 > kMaxRows) return false;
+  s.nch_max = nch_max;
+  s.bstride = 32 * nch_max + 2;  // an odd number of words per threshold row
+  const int nthr = max(1, P.n_bins - 1);
+  int kcap = nthr;
+  while (kcap > 1 && smem_for(kcap, s.bstride) > smem_limit) --kcap;
+  if (smem_for(kcap, s.bstride) > smem_limit) return false;
+  s.kcap = kcap;
+  s.smem = smem_for(kcap, s.bstride);
+  // bands: enough tiles for the target (a whole number of waves), each at most
+  // 2047 swept rows
+  const int max_ty = kMaxRows - 2 * Ry;
+  int bands = max(1, (tiles_target + s.tiles_x - 1) / s.tiles_x);
+  bands = min(bands, H);
+  int TY = (H + bands - 1) / bands;
+  if (TY > max_ty) TY = max_ty;
+  s.TY = TY;
+  s.tiles_y = (H + TY - 1) / TY;
+  // count planes: uint32 slots for windows that can hold 2^16 pixels or more
+  s.cnt_wide = 0;
+  for (int f = 0; f < P.n_fields; ++f) {
+    const long long wx = min(2LL * P.rx[f] + 1, (long long)W), wy = min(2LL * P.ry[f] + 1, (long long)H);
+    if (wx * wy >= 65536) s.cnt_wide |= 1 << f;
+  }
+  S = s;
+  return true;
+}
+
+size_t sweep_count_bytes(const DevParams &P, const SweepPlan &S, long long *off) {
+  const size_t N = (size_t)S.W * S.H;
+  size_t o = 0;
+  for (int f = 0; f < kMaxFields; ++f) {
+    if (off) off[f] = (long long)o;
+    if (f < P.n_fields) o += N * (((S.cnt_wide >> f) & 1) ? 4 : 2);
+    o = (o + 255) & ~(size_t)255;
+  }
+  return o;
+}
+
+template <int NF>
+static int launch_nf(const DevParams &P, const Job *jobs, int njobs, int nitems, int *queue, size_t smem,
+                     int ctas, cudaStream_t s) {
+  if (cudaFuncSetAttribute(k_sweep<NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return -1;
+  k_sweep<NF><<<ctas, kNT, smem, s>>>(P, jobs, njobs, nitems, queue);
+  return 1;
+}
+
+int sweep_ctas_per_sm(int n_fields, size_t smem) {
+  int per = 0;
+  cudaError_t e;
+  switch (n_fields) {
+#define TM_OCC(nf)                                                                                    \
+  case nf:                                                                                            \
+    e = cudaFuncSetAttribute(k_sweep<nf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep<nf>, kNT, smem); \
+    break;
+    TM_OCC(1) TM_OCC(2) TM_OCC(3) TM_OCC(4) TM_OCC(5) TM_OCC(6) TM_OCC(7) TM_OCC(8)
+#undef TM_OCC
+    default: return 0;
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per;
+}
+
+int launch_sweep(const DevParams &P, const Job *jobs, int njobs, int nitems, int *queue, size_t smem, int ctas,
+                 cudaStream_t s) {
+  cudaMemsetAsync(queue, 0, sizeof(int), s);
+  switch (P.n_fields) {
+    case 1: return launch_nf<1>(P, jobs, njobs, nitems, queue, smem, ctas, s);
+    case 2: return launch_nf<2>(P, jobs, njobs, nitems, queue, smem, ctas, s);
+    case 3: return launch_nf<3>(P, jobs, njobs, nitems, queue, smem, ctas, s);
+    case 4: return launch_nf<4>(P, jobs, njobs, nitems, queue, smem, ctas, s);
+    case 5: return launch_nf<5>(P, jobs, njobs, nitems, queue, smem, ctas, s);
+    case 6: return launch_nf<6>(P, jobs, njobs, nitems, queue, smem, ctas, s);
+    case 7: return launch_nf<7>(P, jobs, njobs, nitems, queue, smem, ctas, s);
+    default: return launch_nf<8>(P, jobs, njobs, nitems, queue, smem, ctas, s);
+  }
+}
+
+}  // namespace tmk
