@@ -230,14 +230,16 @@ tm_status tm_integral_image(const int32_t *q, int32_t width, int32_t height,
  * with row segments of 16 rows, doubled while the scratch would not fit, and
  * 16 bytes per row and 1024-column chunk) lives in a static device array of
  * 8 MiB that every GPU loading this library keeps until the process exits.
- *   - The first call on a device looks the array's address up for that
- *     device (with it current); make that first call before any stream
+ *   - Every call looks the array's address up for the current device (a
+ *     host-side lookup that allocates nothing); the first call on a device
+ *     may load the library's device code, so make it before any stream
  *     capture.
  *   - Calls share the array: calls that overlap on the GPU (on different
  *     streams, or from several host threads without ordering) race.
  *   - Returns TM_EINVAL for bad arguments or a size whose scratch exceeds
- *     8 MiB (use tm_integral_image then), TM_ECUDA if a CUDA call fails.
- *     It never calls cudaMalloc, cudaFree or any allocating routine. */
+ *     8 MiB (use tm_integral_image then), TM_ECUDA if a CUDA call fails;
+ *     tm_last_error(NULL) then gives the reason. It never calls cudaMalloc,
+ *     cudaFree or any allocating routine. */
 tm_status tm_integral_image_noalloc(const int32_t *q, int32_t width, int32_t height,
                                     int64_t *s1, int64_t *s2, void *stream);
 

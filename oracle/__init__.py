@@ -37,7 +37,7 @@ def build(force: bool = False) -> str:
     ):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
            "-shared", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
@@ -122,6 +122,9 @@ def _load():
             lib.tmo_forward_pixels.argtypes = [P, i32, i32, P, P, P, i64, P, P, P, P, P, P]
             lib.tmo_forward_fixed_bins.argtypes = [P, i32, i32, P, P, P]
             lib.tmo_backward.argtypes = [P, i32, i32, P, i32, P, P, P, P]
+            lib.tmo_window_counts.argtypes = [P, i32, i32, P, P]
+            lib.tmo_set_threads.argtypes = [i32]
+            lib.tmo_num_procs.restype = i32
             _lib = lib
     return _lib
 
@@ -192,6 +195,28 @@ def integral_histogram(bins, n_bins: int) -> np.ndarray:
     Hk = np.empty((n_bins, H + 1, W + 1), np.uint32)
     _load().tmo_integral_histogram(_ptr(a), W, H, n_bins, _ptr(Hk))
     return Hk
+
+
+def window_counts(bins, p: Params) -> np.ndarray:
+    """Eq. 1 numerators alone, (s, H, W) uint32: the box sums (Eq. 9) of the
+    integral image of [b(q) < b(p)] (Eq. 7-8 summed over the bins below)."""
+    a = np.ascontiguousarray(np.asarray(bins, dtype=np.uint8))
+    H, W = a.shape
+    cnt = np.empty((p.n_fields, H, W), np.uint32)
+    rc = _load().tmo_window_counts(_ptr(a), W, H, ctypes.byref(p), _ptr(cnt))
+    if rc:
+        raise ValueError(f"tmo_window_counts failed ({rc})")
+    return cnt
+
+
+def set_threads(n: int) -> None:
+    """Host threads of the oracle's per-pixel loops (1 by default)."""
+    _load().tmo_set_threads(int(n))
+
+
+def num_procs() -> int:
+    """Host cores the oracle's OpenMP runtime sees."""
+    return int(_load().tmo_num_procs())
 
 
 @dataclass

@@ -21,7 +21,7 @@
  *   Eq. 3   fusion               L = sum W L_w / sum W
  *   Eq. 12  colour restoration   c_out = (C_in / L_in)^sat L_out
  *
- * Readings where the paper is silent or garbled (each listed in the design doc):
+ * Readings where the paper is silent or garbled:
  *   R1 luminance is evaluated in float, left to right, every product and sum
  *      rounded, then floored at 1e-30f.
  *   R2 l is normalised: lhat = (ln i - ln imin) / (ln imax - ln imin); lhat = 0
@@ -42,6 +42,31 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Host threads for the per-pixel loops (pixels are independent: each is
+ * computed exactly as in a single-threaded run). */
+static int g_threads = 1;
+
+void tmo_set_threads(int32_t n) { g_threads = n < 1 ? 1 : n; }
+
+int32_t tmo_num_procs(void) {
+#ifdef _OPENMP
+  return omp_get_num_procs();
+#else
+  return 1;
+#endif
+}
+
+static int thread_id(void) {
+#ifdef _OPENMP
+  return omp_get_thread_num();
+#else
+  return 0;
+#endif
+}
 
 #define TMO_LUM_FLOOR 1e-30f
 
@@ -154,6 +179,48 @@ static uint32_t box_u32(const uint32_t *S, int W, win_t w) {
   int64_t W1 = (int64_t)W + 1;
   return S[((int64_t)w.y1 + 1) * W1 + w.x1 + 1] - S[((int64_t)w.y1 + 1) * W1 + w.x0] -
          S[(int64_t)w.y0 * W1 + w.x1 + 1] + S[(int64_t)w.y0 * W1 + w.x0];
+}
+
+/* Eq. 1 numerators alone, at every pixel and field: #{q in w_i(p) : b(q) < b(p)}
+ * (b(q) <= b(p) under TMO_CDF_INCLUSIVE). Summing the window histogram of
+ * Eq. 9 over the bins below b(p) is, by the linearity of the four-corner sum,
+ * the box sum of the integral image of the indicator [b(q) < k], k = b(p)
+ * (Eq. 7 summed over those bins, then Eq. 8). So one such integral image is
+ * built per threshold k that some pixel needs, and read at those pixels.
+ * cnt: s*H*W (field-major). Returns 0, -1 for bad parameters, -2 when out of
+ * memory. */
+int tmo_window_counts(const uint8_t *bins, int32_t W, int32_t H, const tmo_params *p,
+                      uint32_t *cnt) {
+  if (W < 1 || H < 1 || p->n_fields < 1 || p->n_fields > TMO_MAX_FIELDS || p->n_bins < 1 ||
+      p->n_bins > TMO_MAX_BINS)
+    return -1;
+  const int s = p->n_fields, n = p->n_bins;
+  const int incl = (p->flags & TMO_CDF_INCLUSIVE) ? 1 : 0;
+  const int64_t W1 = (int64_t)W + 1, P = W1 * ((int64_t)H + 1), N = (int64_t)W * H;
+  uint32_t *S = malloc(sizeof(uint32_t) * (size_t)P);
+  if (!S) return -2;
+  unsigned char used[TMO_MAX_BINS + 1];
+  memset(used, 0, sizeof used);
+  for (int64_t q = 0; q < N; ++q) used[bins[q] + incl] = 1;
+  for (int k = 0; k <= n; ++k) {
+    if (!used[k]) continue;
+    memset(S, 0, sizeof(uint32_t) * (size_t)W1);
+    for (int64_t y = 0; y < H; ++y) {
+      S[(y + 1) * W1] = 0;
+      for (int64_t x = 0; x < W; ++x) {
+        uint32_t h = bins[y * W + x] < k ? 1u : 0u;
+        S[(y + 1) * W1 + x + 1] = h + S[(y + 1) * W1 + x] + S[y * W1 + x + 1] - S[y * W1 + x];
+      }
+    }
+    for (int y = 0; y < H; ++y)
+      for (int x = 0; x < W; ++x) {
+        int64_t q = (int64_t)y * W + x;
+        if (bins[q] + incl != k) continue;
+        for (int f = 0; f < s; ++f) cnt[f * N + q] = box_u32(S, W, window_of(p, f, x, y, W, H));
+      }
+  }
+  free(S);
+  return 0;
 }
 
 /* R5: variance over the window, as the mean of squared deviations. Summed
@@ -328,6 +395,7 @@ static int core_run(const double *rgb, int W, int H, const tmo_params *p,
   uint32_t *Hk = malloc(sizeof(uint32_t) * P * n);
   if (!Hk) { free(lin); core_free(c); return -2; }
   tmo_integral_histogram(c->bins, W, H, n, Hk);
+#pragma omp parallel for schedule(dynamic, 1) num_threads(g_threads)
   for (int y = 0; y < H; ++y)
     for (int x = 0; x < W; ++x) {
       int64_t q = (int64_t)y * W + x;
@@ -425,9 +493,11 @@ int tmo_forward_pixels(const float *rgb, int32_t W, int32_t H,
   if (p->flags & TMO_VAR_LINEAR)  /* the window variance of Eq. 10 on i / imax */
     for (int64_t q = 0; q < N; ++q) lhat[q] = (double)lum[q] / (double)imax;
   const int incl = (p->flags & TMO_CDF_INCLUSIVE) ? 1 : 0;
+  for (int64_t k = 0; k < K; ++k)
+    if (xs[k] < 0 || xs[k] >= W || ys[k] < 0 || ys[k] >= H) { free(lum); free(bins); free(lhat); return -1; }
+#pragma omp parallel for schedule(dynamic, 64) num_threads(g_threads)
   for (int64_t k = 0; k < K; ++k) {
     int x = xs[k], y = ys[k];
-    if (x < 0 || x >= W || y < 0 || y >= H) { free(lum); free(bins); free(lhat); return -1; }
     int64_t q = (int64_t)y * W + x;
     uint32_t cnt[TMO_MAX_FIELDS], area[TMO_MAX_FIELDS];
     double var[TMO_MAX_FIELDS], wgt[TMO_MAX_FIELDS], lf[TMO_MAX_FIELDS];
@@ -477,7 +547,18 @@ int tmo_backward(const double *rgb, int32_t W, int32_t H, const tmo_params *p,
   if (!glhat || !gi) { free(glhat); free(gi); core_free(&c); return -2; }
   memset(grad_in, 0, sizeof(double) * 3 * N);
   memset(grad_params, 0, sizeof(double) * (3 + 2 * s));
-  double *g_eps = grad_params + 3, *g_alpha = grad_params + 3 + s;
+  /* each host thread sums the window-variance adjoint and the parameter
+   * gradients into its own copies, added up after the loop */
+  const int nt = g_threads, npar = 3 + 2 * s;
+  double *gl_all = calloc((size_t)N * nt, sizeof(double));
+  double *gp_all = calloc((size_t)npar * nt, sizeof(double));
+  if (!gl_all || !gp_all) { free(gl_all); free(gp_all); free(glhat); free(gi); core_free(&c); return -2; }
+#pragma omp parallel num_threads(nt)
+  {
+  double *glt = gl_all + (int64_t)thread_id() * N;
+  double *gpar = gp_all + (int64_t)thread_id() * npar;
+  double *g_eps = gpar + 3, *g_alpha = gpar + 3 + s;
+#pragma omp for schedule(dynamic, 1)
   for (int y = 0; y < H; ++y)
     for (int x = 0; x < W; ++x) {
       int64_t q = (int64_t)y * W + x;
@@ -493,7 +574,7 @@ int tmo_backward(const double *rgb, int32_t W, int32_t H, const tmo_params *p,
         }
         double rs = pow(rho, p->sat);
         gL += g * rs;
-        grad_params[2] += g * rs * log(rho) * L;
+        gpar[2] += g * rs * log(rho) * L;
         grad_in[3 * q + ch] += g * p->sat * pow(rho, p->sat - 1.0) * L / i;
         gi[q] += -g * p->sat * rs * L / i;
       }
@@ -504,8 +585,8 @@ int tmo_backward(const double *rgb, int32_t W, int32_t H, const tmo_params *p,
         double dLdLf = ws > 0.0 ? c.weight[fq] / ws : 1.0 / (double)s;
         double dLdW = ws > 0.0 ? (c.lf[fq] - L) / ws : 0.0;
         double P = (double)c.cnt[fq] / (double)c.area[fq];
-        grad_params[0] += gL * dLdLf * (1.0 - P);               /* Eq. 2 */
-        grad_params[1] += gL * dLdLf * P;
+        gpar[0] += gL * dLdLf * (1.0 - P);               /* Eq. 2 */
+        gpar[1] += gL * dLdLf * P;
         double gW = gL * dLdW;
         double v = c.var[fq], e = p->eps[f], a = p->alpha[f];
         double den = (v + e) * (v + e);
@@ -519,10 +600,17 @@ int tmo_backward(const double *rgb, int32_t W, int32_t H, const tmo_params *p,
         for (int yy = w.y0; yy <= w.y1; ++yy)
           for (int xx = w.x0; xx <= w.x1; ++xx) {
             int64_t r = (int64_t)yy * W + xx;
-            glhat[r] += gv * (2.0 / T) * (c.lhat[r] - mu);
+            glt[r] += gv * (2.0 / T) * (c.lhat[r] - mu);
           }
       }
     }
+  }
+  for (int t = 0; t < nt; ++t) {
+    for (int64_t q = 0; q < N; ++q) glhat[q] += gl_all[(int64_t)t * N + q];
+    for (int k = 0; k < npar; ++k) grad_params[k] += gp_all[(int64_t)t * npar + k];
+  }
+  free(gl_all);
+  free(gp_all);
   /* normalised log, including the range terms through ln imin and ln imax */
   if (c.D > 0.0) {
     double glmin = 0.0, glmax = 0.0;

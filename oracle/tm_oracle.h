@@ -59,6 +59,12 @@ typedef struct {
   double *l;        /* H*W  : fused L of Eq. 3                               */
 } tmo_fields;
 
+/* Host threads of the per-pixel loops (default 1; the results do not depend
+ * on it, up to the summation order of the adjoint's FP64 sums), and the number
+ * of host cores. */
+void tmo_set_threads(int32_t n);
+int32_t tmo_num_procs(void);
+
 /* Eq. 11 luminance in float, fixed order, each step rounded; floored. */
 float tmo_luminance(float r, float g, float b);
 
@@ -80,6 +86,12 @@ void tmo_integral_f64(const double *v, int32_t W, int32_t H, double *S);
 /* Eq. 7-8 integral histogram: n planes of (H+1)*(W+1) uint32 counts. */
 void tmo_integral_histogram(const uint8_t *bins, int32_t W, int32_t H,
                             int32_t n_bins, uint32_t *Hk);
+
+/* Eq. 1 numerators only, every pixel and field (s*H*W, field-major), from
+ * the integral image of [b(q) < k] per needed threshold k and Eq. 9 box sums;
+ * no variance. Returns 0 on success. */
+int tmo_window_counts(const uint8_t *bins, int32_t W, int32_t H, const tmo_params *p,
+                      uint32_t *cnt);
 
 /* Full forward over the image (counts through Eq. 9, variance by direct
  * window sums). out: H*W*3 doubles. fields: optional (NULL fields ignored). */

@@ -17,6 +17,7 @@
 
 #include "tm.h"
 #include "tm_backward.cuh"
+#include "tm_host.h"
 #include "tm_kernels.cuh"
 
 using namespace tmk;
@@ -40,7 +41,9 @@ __global__ void k_put_jobs(const __grid_constant__ JobPack<N> p, Job *dst, int n
   for (int i = threadIdx.x; i < words; i += blockDim.x) d[i] = src[i];
 }
 static_assert(sizeof(Job) % 4 == 0, "jobs are copied as words");
+}  // namespace
 
+namespace tmk {
 // Writes jobs h[0..n) to d on stream s; returns the launches made.
 int put_jobs(const Job *h, int n, Job *d, cudaStream_t s) {
   if (n == 1) {
@@ -59,7 +62,7 @@ int put_jobs(const Job *h, int n, Job *d, cudaStream_t s) {
   }
   return launches;
 }
-}  // namespace
+}  // namespace tmk
 
 struct tm_ctx {
   tm_params p;
@@ -161,6 +164,13 @@ tm_status fail(tm_ctx *c, tm_status s, const char *fmt, ...) {
 tm_status cuda_fail(tm_ctx *c, cudaError_t e, const char *what) {
   return fail(c, TM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
+}  // namespace
+
+namespace tmk {
+tm_status fail_noctx(tm_status s, const char *msg) { return fail(nullptr, s, "%s", msg); }
+}  // namespace tmk
+
+namespace {
 
 #define TM_CUDA(c, call)                                   \
   do {                                                     \

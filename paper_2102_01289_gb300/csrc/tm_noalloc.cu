@@ -9,10 +9,8 @@
 // reserved all device memory up front. tm_integral_image_noalloc serves them
 // with a file-scope static device array instead; every GPU that loads this
 // library holds the array until the process exits.
-#include <cstring>
-#include <mutex>
-
 #include "tm.h"
+#include "tm_host.h"
 #include "tm_kernels.cuh"
 
 using namespace tmk;
@@ -24,46 +22,35 @@ constexpr size_t kScratchBytes = (size_t)8 << 20;  // 8 MiB
 // Shared by every call on a device: [job descriptor | integral-image scratch].
 static __device__ __align__(256) unsigned char g_integral_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mu;
-void *g_scratch_addr[kMaxDevices];  // device address of the array, per device
-
 size_t round256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 }  // namespace
 
 extern "C" tm_status tm_integral_image_noalloc(const int32_t *q, int32_t width, int32_t height,
                                                int64_t *s1, int64_t *s2, void *stream) {
-  if (!q || !s1 || !s2 || s1 == s2) return TM_EINVAL;
-  if (width < 1 || height < 1 || (long long)width * height > (1LL << 31) - 1) return TM_EINVAL;
+  if (!q || !s1 || !s2 || s1 == s2)
+    return fail_noctx(TM_EINVAL, "tm_integral_image_noalloc: null or aliased plane pointer");
+  if (width < 1 || height < 1 || (long long)width * height > (1LL << 31) - 1)
+    return fail_noctx(TM_EINVAL, "tm_integral_image_noalloc: width and height must be >= 1, below 2^31 pixels");
   const size_t job_bytes = round256(sizeof(Job));
   int nseg = 1, seg_rows = 1;
   integral_layout(width, height, (kScratchBytes - job_bytes) / 8, nseg, seg_rows);
   const size_t need = job_bytes + 8 * integral_scratch_elems(width, height, nseg);
-  if (need > kScratchBytes) return TM_EINVAL;  // larger than the static scratch
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    cudaGetLastError();
-    return TM_ECUDA;
-  }
+  if (need > kScratchBytes)
+    return fail_noctx(TM_EINVAL, "tm_integral_image_noalloc: the image needs more than the 8 MiB static scratch "
+                                 "(use tm_integral_image)");
+  // In host code the array's name is not a device address: look the address
+  // up with the caller's device current. The lookup allocates nothing; doing
+  // it on every call keeps it right for whichever device (or context after a
+  // device reset) is current.
   void *base = nullptr;
-  {
-    // First call on this device (with it current): the host cannot use the
-    // array's name as a device address, so look the address up once.
-    std::lock_guard<std::mutex> g(g_setup_mu);
-    if (!g_scratch_addr[dev]) {
-      void *p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_integral_scratch) != cudaSuccess || !p) {
-        cudaGetLastError();
-        return TM_ECUDA;
-      }
-      g_scratch_addr[dev] = p;
-    }
-    base = g_scratch_addr[dev];
+  cudaError_t e = cudaGetSymbolAddress(&base, g_integral_scratch);
+  if (e != cudaSuccess || !base) {
+    cudaGetLastError();
+    return fail_noctx(TM_ECUDA, "tm_integral_image_noalloc: cudaGetSymbolAddress of the static scratch failed");
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  Job J;
-  memset(&J, 0, sizeof J);
+  Job J{};
   J.in.W = width;
   J.in.H = height;
   J.q = const_cast<int32_t *>(q);
@@ -72,15 +59,14 @@ extern "C" tm_status tm_integral_image_noalloc(const int32_t *q, int32_t width, 
   J.nseg = nseg;
   J.seg_rows = seg_rows;
   J.segtot = reinterpret_cast<long long *>(static_cast<char *>(base) + job_bytes);
-  // The scratch is fully rewritten before it is read, so nothing
-  // left in the array by an earlier call needs clearing. The descriptor comes
-  // from pageable memory: the copy has consumed it when this call returns.
-  if (cudaMemcpyAsync(base, &J, sizeof(Job), cudaMemcpyHostToDevice, st) != cudaSuccess) {
-    cudaGetLastError();
-    return TM_ECUDA;
-  }
+  // The descriptor travels as a kernel parameter of the copy kernel (nothing
+  // is read from host memory after this call returns); the scratch after it is
+  // fully rewritten before it is read, so nothing an earlier call left there
+  // needs clearing.
+  put_jobs(&J, 1, static_cast<Job *>(base), st);
   launch_integral_jobs(static_cast<const Job *>(base), 1, integral_tile_blocks(width, nseg), integral_col_blocks(width),
                        st);
-  if (cudaGetLastError() != cudaSuccess) return TM_ECUDA;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail_noctx(TM_ECUDA, "tm_integral_image_noalloc: kernel launch failed");
   return TM_OK;
 }

@@ -47,6 +47,9 @@ def _gpu_backward(img, gp, gout):
     return gin.cpu().numpy().astype(np.float64), gpar.cpu().numpy().astype(np.float64)
 
 
+# The last case (added below) is 300 x 320 with the C5 radii 8/32/128: r = 128
+# windows lie wholly inside the image and the adjoint's fixed-point integral
+# pass spans several tiles.
 CASES = [
     (40, 56, 16, [2, 7, 30]),
     (33, 47, 32, [(3, 1), 9]),
@@ -56,7 +59,7 @@ CASES = [
 
 
 @pytest.mark.parametrize("flags", [0, 3])  # defaults; inclusive CDF + Algorithm 1's area
-@pytest.mark.parametrize("H,W,n,radii", CASES)
+@pytest.mark.parametrize("H,W,n,radii", CASES + [(300, 320, 32, [8, 32, 128])])
 def test_backward_matches_oracle_adjoint(orc, H, W, n, radii, flags):
     rng = np.random.default_rng(H + W)
     img = synth.wdr_image(H, W, seed=H * 7 + W)
@@ -65,7 +68,11 @@ def test_backward_matches_oracle_adjoint(orc, H, W, n, radii, flags):
                    alpha=[(1.0, 0.8, 1.2)[f % 3] for f in range(s)], flags=flags)
     gout = rng.standard_normal(img.shape)
     gin, gpar = _gpu_backward(img, gp, gout)
-    ref_in, ref_p = orc.backward(img.astype(np.float64), op, gout, lum_f64=False)
+    orc.set_threads(orc.num_procs())  # windows of up to 257 x 257 pixels: the oracle loops are long
+    try:
+        ref_in, ref_p = orc.backward(img.astype(np.float64), op, gout, lum_f64=False)
+    finally:
+        orc.set_threads(1)
     floor = 1e-3 * np.abs(ref_in).max()
     err = np.abs(gin - ref_in)
     assert np.all(err <= 1e-3 * np.abs(ref_in) + floor), (err.max(), np.abs(ref_in).max())

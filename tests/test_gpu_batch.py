@@ -161,3 +161,41 @@ def test_unsynchronised_calls_of_different_sizes():
             assert torch.equal(y, r)
     finally:
         tm.tm_destroy(ctx)
+
+
+def test_uneven_batch_c4_shapes(orc):
+    """An uneven batch shaped like the 64-image workload (64 bins, radii
+    8/32/128): 4096 x 3072, 640 x 480, 1920 x 1080, a 16:9 and a 4:3 image.
+    Every image equals its own single-image forward bit for bit (the largest
+    holds whole-wave tiles over 16 strips), and the largest matches the
+    oracle's direct per-pixel evaluation at sampled pixels (corners, borders,
+    strip seams, random)."""
+    sizes = [(4096, 3072), (640, 480), (1920, 1080), (1280, 720), (2048, 1536)]
+    p = tm.make_params(64, [8, 32, 128])
+    op = orc.make_params(64, [8, 32, 128], eps=float(np.float32(0.1)), sat=float(np.float32(0.6)))
+    imgs = [synth.wdr_image(h, w, seed=200 + i) for i, (w, h) in enumerate(sizes)]
+    xs = [torch.from_numpy(a).cuda() for a in imgs]
+    ys = [torch.empty_like(x) for x in xs]
+    ctx = tm.tm_create(p)
+    try:
+        tm.tm_set_option(ctx, tm.TM_OPT_HIST_PATH, 1)
+        tm.tm_forward_batch(ctx, xs, ys)
+        torch.cuda.synchronize()
+        for x, y in zip(xs, ys):
+            ref = _single(ctx, x)
+            torch.cuda.synchronize()
+            assert torch.equal(y, ref)
+        big = ys[0].cpu().numpy()
+    finally:
+        tm.tm_destroy(ctx)
+    W, H = sizes[0]
+    rng = np.random.default_rng(9)
+    yy = np.concatenate([[0, 0, H - 1, H - 1, 128, H - 129, 1500, 7], rng.integers(0, H, 80)])
+    xx = np.concatenate([[0, W - 1, 0, W - 1, 255, 256, 3839, 3840], rng.integers(0, W, 80)])
+    orc.set_threads(orc.num_procs())
+    try:
+        ref, _ = orc.forward_pixels(imgs[0], op, xx, yy)
+    finally:
+        orc.set_threads(1)
+    got = big[yy, xx].astype(np.float64)
+    assert np.all(np.abs(got - ref) <= 1e-4 * np.maximum(np.abs(ref), 1e-3))

@@ -327,8 +327,8 @@ def test_integral_histogram_entry_point_exact(orc):
         assert np.array_equal(hk.cpu().numpy().view(np.uint32), orc.integral_histogram(b, n))
 
 
-def test_big_window_slabs_and_tile_edges(orc):
-    """Windows over 2^16 pixels are split into row slabs; tiles leave ragged
+def test_big_window_wide_counts_and_tile_edges(orc):
+    """Windows over 2^16 pixels take uint32 count planes; tiles leave ragged
     edges. 600 x 700, radii 5/40/150 (301 x 301 > 2^16), 24 bins."""
     img = synth.wdr_image(600, 700, seed=13)
     gp, op = params_pair(orc, 24, [5, 40, (150, 150)])
@@ -357,6 +357,34 @@ def test_full_size_12mp_sampled(orc):
     assert_out_close(out[ys, xs], ref)
 
 
+@pytest.mark.parametrize("path", PATHS)
+def test_full_size_12mp_every_count(orc, path):
+    """4000 x 3000, 64 bins, radii 8/32/128 on both histogram paths: the Eq. 1
+    numerator of every pixel and every field equals the oracle's (bin map,
+    then the box sums of the integral image of [b < b(p)], Eq. 7-9), bit for
+    bit; the bin map itself too."""
+    H, W = 3000, 4000
+    img = synth.wdr_image(H, W, seed=7, decades=(-3.0, 5.0))
+    gp, op = params_pair(orc, 64, [8, 32, 128])
+    x = torch.from_numpy(img).cuda()
+    y = torch.empty_like(x)
+    ctx = tm.tm_create(gp)
+    try:
+        tm.tm_set_debug(ctx, True)
+        tm.tm_set_option(ctx, tm.TM_OPT_HIST_PATH, path)
+        tm.tm_forward(ctx, x, y)
+        bins = tm.tm_debug_export(ctx, tm.TM_DBG_BINS).cpu().numpy().reshape(H, W)
+        cnt = tm.tm_debug_export(ctx, tm.TM_DBG_COUNTS).cpu().numpy().view(np.uint32).reshape(3, H, W)
+        torch.cuda.synchronize()
+    finally:
+        tm.tm_destroy(ctx)
+    pre = orc.prepare(img, 64)
+    assert np.array_equal(bins, pre["bins"])
+    ref = orc.window_counts(pre["bins"], op)
+    bad = cnt != ref
+    assert not bad.any(), f"{int(bad.sum())} counts differ, first at {np.argwhere(bad)[0]}"
+
+
 def _pyramid_pair(orc, W, H, s=5, n=5):
     """The paper's preset (Section IV): s fields halving from the whole
     image (rectangular windows), n bins, eps 0.1, sat 0.6."""
@@ -382,8 +410,8 @@ def test_paper_preset_matches_oracle(orc, path):
 
 
 def test_paper_preset_12mp_sampled(orc):
-    """The preset at 4000 x 3000: the largest window is the whole image, more
-    slabs than the sweep holds, so the context takes the materialised
+    """The preset at 4000 x 3000: the largest window is the whole image, wider
+    than the 32 chunks of a swept row, so the context takes the materialised
     integral histogram (4 cumulative planes at n = 5). Bin map bit-exact,
     outputs at sampled pixels against direct per-pixel evaluation."""
     H, W = 3000, 4000
@@ -533,7 +561,7 @@ MAX_FIELDS_ALPHA = [1.0, 0.7, 1.3, 0.9, 1.1, 0.5, 1.0, 0.8]
 def test_eight_fields_and_maximum_radius(orc, flags, path):
     """TM_MAX_FIELDS fields with half-sizes from 0 to TM_MAX_RADIUS: the last
     two windows span the image in one or both directions (the sweep clips
-    their row slabs to the image); under Algorithm 1's area the largest window
+    their half-sizes to the image); under Algorithm 1's area the largest window
     is 65535 x 65535 pixels, an Eq. 1 denominator just under 2^32. Counts
     bit-exact, variances within the quantisation bound, outputs within the
     float tolerance, on a 70 x 90 and a 37 x 300 image."""
@@ -567,8 +595,8 @@ LARGE_RADII = [(150, 150), (140, 150), (150, 120), 130, (110, 150), (150, 110), 
 @pytest.mark.parametrize("path", PATHS)
 def test_large_image_64bit_offsets_sampled(orc, path):
     """16384 x 12288 (201 MP) with 8 fields whose windows each hold more than
-    2^16 pixels: two row slabs per field, 16 slab count planes, element
-    offsets past 2^31 on the fused path; 16 bins, 15 cumulative planes of
+    2^16 pixels: 8 uint32 count planes, byte offsets past 2^31 on the fused
+    path; 16 bins, 15 cumulative planes of
     805 MB on the materialised one. Range, bin edges and bin map exact;
     counts, variances and outputs at sampled pixels (corners, edges, tile
     seams, random) against the oracle's direct per-pixel evaluation."""

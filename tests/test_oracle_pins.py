@@ -471,3 +471,57 @@ def test_forward_with_a_given_range(orc):
             assert f3.cnt[0, y, x] == int(np.sum(b[w] < b[y, x]))
             v = float(np.var(lhat[w]))
             assert abs(f3.sigma2[0, y, x] - v) <= 1e-12 + 1e-9 * v
+
+
+# ------------------------------------------ Eq. 1 numerators, counts only --
+@pytest.mark.parametrize("flags", [0, 1])
+@pytest.mark.parametrize("radii", [[0, 1, (3, 2)], [(7, 0), 40]])
+def test_window_counts_against_brute_force(orc, flags, radii):
+    """Counts alone (integral image of [b < k] per threshold) equal a direct
+    count over every clipped window of a tiny image, for < and <=."""
+    img = synth.wdr_image(13, 17, seed=len(radii) + flags)
+    n = 6
+    bins = orc.prepare(img, n)["bins"].astype(np.int64)
+    p = orc.make_params(n, radii, flags=flags)
+    got = orc.window_counts(bins, p)
+    H, W = bins.shape
+    for f, r in enumerate(radii):
+        rx, ry = (r, r) if np.isscalar(r) else r
+        for y in range(H):
+            for x in range(W):
+                win = bins[max(0, y - ry): y + ry + 1, max(0, x - rx): x + rx + 1]
+                k = bins[y, x] + (1 if flags & 1 else 0)
+                assert got[f, y, x] == np.count_nonzero(win < k)
+
+
+def test_window_counts_equal_forward_counts(orc):
+    """The counts-only path and the forward's per-bin box sums (Eq. 9 summed
+    over the bins below) agree everywhere, on every reading variant."""
+    img = synth.wdr_image(40, 57, seed=11)
+    for flags in (0, 1, 2, 3):
+        p = orc.make_params(32, [2, (9, 4), 30], flags=flags)
+        _, fl = orc.forward(img, p)
+        bins = orc.prepare(img, 32)["bins"]
+        assert np.array_equal(orc.window_counts(bins, p), fl.cnt)
+
+
+def test_threads_do_not_change_results(orc):
+    """The per-pixel loops over host threads give the single-thread forward
+    bit for bit, and the adjoint up to FP64 summation order."""
+    img = synth.wdr_image(31, 45, seed=4)
+    p = orc.make_params(16, [3, 11])
+    rng = np.random.default_rng(0)
+    gout = rng.standard_normal(img.shape)
+    try:
+        orc.set_threads(1)
+        ref, fl = orc.forward(img, p)
+        gi1, gp1 = orc.backward(img.astype(np.float64), p, gout)
+        orc.set_threads(4)
+        out, fl4 = orc.forward(img, p)
+        gi4, gp4 = orc.backward(img.astype(np.float64), p, gout)
+    finally:
+        orc.set_threads(1)
+    assert np.array_equal(out, ref) and np.array_equal(fl4.sigma2, fl.sigma2)
+    assert np.allclose(gi4, gi1, rtol=1e-12, atol=1e-15 * np.abs(gi1).max())
+    for k in gp1:
+        assert np.allclose(gp4[k], gp1[k], rtol=1e-12, atol=1e-12)
