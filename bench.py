@@ -150,18 +150,20 @@ def job_rate(units_per_rank: float, world: int, steps: int, ms_max: float) -> fl
 
 
 # ------------------------------------------------------------ reference arm --
-def oracle_rate(img, wl, budget_s: float, seed: int = 0):
+def oracle_rate(img, wl, budget_s: float, seed: int = 0, threads: int = 1):
     """Oracle MP/s on sampled pixels of the workload: the global pre-pass over
-    the whole image plus direct per-pixel evaluation until `budget_s`."""
+    the whole image plus direct per-pixel evaluation until `budget_s`, on
+    `threads` host threads (the per-pixel loop; the pre-pass is serial)."""
     import oracle
 
     oracle.build()
+    oracle.set_threads(threads)
     op = oracle.make_params(wl["n_bins"], wl["radii"], eps=float(np.float32(0.1)),
                             sat=float(np.float32(0.6)))
     H, W = img.shape[:2]
     rng = np.random.default_rng(seed)
     done, t0 = 0, time.perf_counter()
-    chunk = 2048
+    chunk = 2048 * threads  # enough pixels per call that the serial pre-pass does not dominate
     # each call re-runs the O(N) pre-pass; its cost is part of the oracle
     while time.perf_counter() - t0 < budget_s:
         ys = rng.integers(0, H, chunk)
@@ -169,7 +171,45 @@ def oracle_rate(img, wl, budget_s: float, seed: int = 0):
         oracle.forward_pixels(img, op, xs, ys)
         done += chunk
     dt = time.perf_counter() - t0
+    oracle.set_threads(1)
     return done / dt / 1e6, done, dt
+
+
+def oracle_c1_full(threads: int):
+    """The oracle's whole forward over the 512 x 384 workload (32 bins, radii
+    4/16/64) on `threads` host threads: (MP/s, seconds)."""
+    import oracle
+    import synth
+
+    oracle.build()
+    img = synth.wdr_image(384, 512, seed=0)
+    op = oracle.make_params(32, [4, 16, 64], eps=float(np.float32(0.1)), sat=float(np.float32(0.6)))
+    oracle.set_threads(threads)
+    t0 = time.perf_counter()
+    oracle.forward(img, op)
+    dt = time.perf_counter() - t0
+    oracle.set_threads(1)
+    return 384 * 512 / dt / 1e6, dt
+
+
+def host_cores() -> int:
+    return os.cpu_count() or 1
+
+
+def cpu_baseline(img, wl, seconds: float) -> dict:
+    """The oracle as it stands on this host: the 12 MP workload sampled on all
+    cores and on one, and the 512 x 384 workload in full on all cores."""
+    nproc = host_cores()
+    r_all, n_all, dt_all = oracle_rate(img, wl, seconds * 0.45, threads=nproc)
+    r_one, n_one, dt_one = oracle_rate(img, wl, seconds * 0.35, seed=1, threads=1)
+    c1_rate, c1_s = oracle_c1_full(nproc)
+    return {"value": r_all, "unit": "MP/s", "cores": nproc, "kind": "oracle",
+            "sample": f"{n_all} pixels sampled uniformly from the 12 MP image, direct window loops "
+                      f"over {nproc} threads, {dt_all:.1f} s (pre-pass serial)",
+            "one_thread": {"value": r_one, "unit": "MP/s", "cores": 1,
+                           "sample": f"{n_one} sampled pixels, {dt_one:.1f} s"},
+            "c1_full": {"value": c1_rate, "unit": "MP/s", "cores": nproc, "seconds": c1_s,
+                        "sample": "512 x 384, 32 bins, radii 4/16/64, whole forward"}}
 
 
 def run_reference(args):
@@ -181,11 +221,12 @@ def run_reference(args):
     wl = WORKLOAD
     img = synth.wdr_image(wl["H"], wl["W"], seed=wl["seed"], decades=wl["decades"])
     budget = args.ref_seconds or max(2.0, min(20.0, 60.0 / max(args.steps + args.warmup, 1)))
+    nproc = host_cores()
     for _ in range(args.warmup):
-        oracle_rate(img, wl, budget / 4)
+        oracle_rate(img, wl, budget / 4, threads=nproc)
     rates, pix, secs = [], 0, 0.0
     for k in range(args.steps):
-        r, n, dt = oracle_rate(img, wl, budget, seed=k)
+        r, n, dt = oracle_rate(img, wl, budget, seed=k, threads=nproc)
         rates.append(r)
         pix += n
         secs += dt
@@ -197,9 +238,10 @@ def run_reference(args):
         "data": "synthetic",
         "config": {"workload": wl["name"], "height": wl["H"], "width": wl["W"], "n_bins": wl["n_bins"],
                    "radii": wl["radii"], "l2": "n/a (CPU)"},
-        "cpu_baseline": {"value": value, "unit": "MP/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "MP/s", "cores": nproc, "kind": "oracle",
                          "sample": f"{pix} pixels sampled uniformly from the 12 MP image, each "
-                                   "evaluated by direct window loops after the O(N) pre-pass"},
+                                   f"evaluated by direct window loops over {nproc} threads after the "
+                                   "O(N) pre-pass"},
         "e2e": {"value": value, "unit": "MP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -292,6 +334,16 @@ def run_ours(args):
     bpp = PATH_BYTES_PER_PX
     achieved = bpp * npx / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else None
     traffic = load_traffic(dominant)
+    # the dominant kernel is limited by instruction issue, not HBM: its warp
+    # instructions per launch (ncu) over the SMs' issue slots in its time
+    inst = load_profile(dominant, "warp_inst_per_launch")
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clk.get("sm_mhz") or None
+    issue = None
+    if inst and mhz and dom_ms > 0:
+        slots = nsm * 4 * mhz * 1e6 * dom_ms / 1e3
+        issue = {"warp_inst_per_launch": inst, "sms": nsm, "sm_mhz": mhz, "issue_slots": slots,
+                 "frac": inst / slots, "warp_inst_per_px": inst / npx}
     line = {
         "metric": METRIC, "value": value, "unit": "MP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -303,7 +355,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
                      "traffic": traffic, "peak_kind": peak_kind,
-                     "bytes_per_px": bpp, "kernel_ms": dom_ms},
+                     "bytes_per_px": bpp, "kernel_ms": dom_ms, "issue": issue},
         "path_roofline": {"bytes_per_px": PATH_BYTES_PER_PX,
                           "achieved": PATH_BYTES_PER_PX * npx / (ms_step / 1e3) / 1e9,
                           "peak": peak, "unit": "GB/s",
@@ -316,12 +368,17 @@ def run_ours(args):
                 "synchronous_per_call": job_rate(npx, world, e2e_steps, e2e_sync_s * 1e3)},
         "gpu_launches": int(launches_per_step * args.steps),
     }
-    if rank == 0 and not args.no_cpu_baseline:
-        r, n, dt = oracle_rate(imgs[0], wl, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": r, "unit": "MP/s", "cores": 1, "kind": "oracle",
-                                "sample": f"{n} pixels sampled uniformly from the 12 MP image, "
-                                          f"direct window loops, {dt:.1f} s"}
     tm.tm_destroy(ctx)
+    if world == 1 and not args.no_legs:
+        # the other legs of the metric, each against its per-image forward
+        line["legs"] = {
+            "fwd_bwd": leg_fwd_bwd(args, dev),
+            "batch_video": leg_batch(args, dev, "batch-video"),
+            "batch_uneven": leg_batch(args, dev, "batch-uneven"),
+            "paper_preset": leg_paper_preset(args, dev),
+        }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(imgs[0], wl, args.cpu_seconds)
     if world > 1:
         import torch.distributed as dist
 
@@ -345,45 +402,53 @@ def _timed(fn, steps, stream):
     return e0.elapsed_time(e1) / steps
 
 
-def run_batch_workload(args, kind):
+def _roof(bpp, npx, ms):
+    peak, peak_kind = load_peaks()
+    ach = bpp * npx / (ms / 1e3) / 1e9
+    return {"bytes_per_px": bpp, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "peak_kind": peak_kind}
+
+
+def leg_batch(args, dev, kind, steps=None, warmup=None):
     """Batched graph path vs per-image forward on the same images.
     batch-video: 120 1920x1080 FP16 frames (moving rectangles over a drifting
     ramp, per-frame noise), 32 bins, half-sizes 8/32/128, FP16 output.
-    batch-uneven: 64 float32 images, W ~ U{640..4096}, 4:3 or 16:9, 64 bins."""
+    batch-uneven: 64 float32 images, W ~ U{640..4096}, 4:3 or 16:9, 64 bins.
+    Inputs are rendered on the device (synth.wdr_device, the same recipe)."""
     import torch
 
     import paper_2102_01289_gb300 as tm
     import synth
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
+    rank = dist_env()[0]
+    steps = steps or max(3, min(args.steps, 5))
+    warmup = warmup or 3
     tm.build()
     if kind == "batch-video":
-        n, dt = 120, np.float16
-        frames = [synth.wdr_video_frame(1080, 1920, seed=7 + rank, frame=f) for f in range(n)]
+        n = 120
+        xs = [synth.wdr_device(1080, 1920, seed=7 + rank, device=dev, frame=f, dtype=torch.float16)
+              for f in range(n)]
         params = tm.make_params(32, [8, 32, 128])
-        name = "wdr-video-1080p-fp16-x120"
+        name, bpp = "wdr-video-1080p-fp16-x120", 18
     else:
-        dt = np.float32
         sizes = synth.uneven_sizes(64, seed=rank)
-        frames = [synth.wdr_image(h, w, seed=k + 100 * rank) for k, (w, h) in enumerate(sizes)]
+        xs = [synth.wdr_device(h, w, seed=k + 100 * rank, device=dev) for k, (w, h) in enumerate(sizes)]
         params = tm.make_params(64, [8, 32, 128])
-        name = "wdr-uneven-x64"
-    npx = sum(f.shape[0] * f.shape[1] for f in frames)
-    xs = [torch.from_numpy(f).to(dev) for f in frames]
+        name, bpp = "wdr-uneven-x64", 36
+    npx = sum(x.shape[0] * x.shape[1] for x in xs)
     ys = [torch.empty_like(x) for x in xs]
     ctx = tm.tm_create(params)
     tm.tm_set_option(ctx, tm.TM_OPT_HIST_PATH, HIST_PATHS[args.hist_path])
     stream = torch.cuda.current_stream(dev)
-    clocks = ClockSampler(local)
-    for _ in range(args.warmup):
+    clocks = ClockSampler(dev.index or 0)
+    for _ in range(warmup):
         tm.tm_forward_batch(ctx, xs, ys, stream)
     launches = tm.tm_last_launch_count(ctx)
     clocks.start()
     time.sleep(0.3)
-    ms_batch = _timed(lambda i: tm.tm_forward_batch(ctx, xs, ys, stream), args.steps, stream)
+    ms_batch = _timed(lambda i: tm.tm_forward_batch(ctx, xs, ys, stream), steps, stream)
     clk = clocks.stop()
+
     # per-image forward on the same images, after one untimed pass over all of
     # them (the first forward of each image size measures both histogram paths)
     def per_image(i):
@@ -391,38 +456,32 @@ def run_batch_workload(args, kind):
             tm.tm_forward(ctx, x, y, stream)
 
     per_image(0)
-    ms_single = _timed(per_image, max(1, args.steps // 2), stream)
+    ms_single = _timed(per_image, max(1, steps // 2), stream)
     ms_reuse = None
     if kind == "batch-video":  # streaming variant: each frame binned over the previous frame's range
         tm.tm_set_option(ctx, tm.TM_OPT_REUSE_RANGE, 1)
         per_image(0)
-        ms_reuse = _timed(per_image, max(1, args.steps // 2), stream)
+        ms_reuse = _timed(per_image, max(1, steps // 2), stream)
         tm.tm_set_option(ctx, tm.TM_OPT_REUSE_RANGE, 0)
     tm.tm_destroy(ctx)
-    bpp = 18 if kind == "batch-video" else 36
-    peak, peak_kind = load_peaks()
-    value = npx / (ms_batch / 1e3) / 1e6
-    line = {
-        "metric": METRIC, "value": value, "unit": "MP/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_batch, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f16" if dt == np.float16 else "f32", "data": "synthetic",
-        "config": {"workload": name, "images": len(frames), "megapixels": npx / 1e6,
+    del xs, ys
+    rate = lambda ms: npx / (ms / 1e3) / 1e6  # noqa: E731
+    return {
+        "value": rate(ms_batch), "unit": "MP/s", "ms_per_step": ms_batch, "steps": steps, "warmup": warmup,
+        "dtype": "f16" if kind == "batch-video" else "f32",
+        "config": {"workload": name, "images": n if kind == "batch-video" else 64, "megapixels": npx / 1e6,
                    "n_bins": params.n_bins, "radii": [8, 32, 128], "path": "batched graph",
-                   "l2": "inputs larger than L2"},
-        "per_image_forward": {"value": npx / (ms_single / 1e3) / 1e6, "unit": "MP/s", "ms": ms_single},
+                   "l2": "inputs larger than L2", "inputs": "rendered on the device (synth.wdr_device)"},
+        "per_image_forward": {"value": rate(ms_single), "unit": "MP/s", "ms": ms_single},
         "per_image_forward_reused_range": (
-            {"value": npx / (ms_reuse / 1e3) / 1e6, "unit": "MP/s", "ms": ms_reuse} if ms_reuse else None),
-        "path_roofline": {"bytes_per_px": bpp, "achieved": bpp * npx / (ms_batch / 1e3) / 1e9,
-                          "peak": peak, "unit": "GB/s",
-                          "frac": bpp * npx / (ms_batch / 1e3) / 1e9 / peak, "peak_kind": peak_kind},
-        "clocks": clk, "gpu_launches": int(launches * args.steps),
+            {"value": rate(ms_reuse), "unit": "MP/s", "ms": ms_reuse} if ms_reuse else None),
+        "batched_over_per_image": ms_single / ms_batch,
+        "path_roofline": _roof(bpp, npx, ms_batch),
+        "clocks": clk, "gpu_launches": int(launches * steps),
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    return 0
 
 
-def run_fwd_bwd(args):
+def leg_fwd_bwd(args, dev, steps=None, warmup=None):
     """16 float32 1024x1024 images, 32 bins, half-sizes 8/32/128: one step is
     the batched forward (tm_forward_batch) plus the batched backward
     (tm_backward_batch: input and parameter gradients). Also timed: the same
@@ -432,14 +491,16 @@ def run_fwd_bwd(args):
     import paper_2102_01289_gb300 as tm
     import synth
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
+    rank = dist_env()[0]
+    steps = steps or max(3, min(args.steps, 10))
+    warmup = warmup or 3
     tm.build()
     n, H, W = 16, 1024, 1024
-    xs = [torch.from_numpy(synth.wdr_image(H, W, seed=s + 16 * rank)).to(dev) for s in range(n)]
+    xs = [synth.wdr_device(H, W, seed=s + 16 * rank, device=dev) for s in range(n)]
     ys = [torch.empty_like(x) for x in xs]
-    gs = [torch.randn_like(x) for x in xs]
+    g = torch.Generator(device=dev)
+    g.manual_seed(1234 + rank)
+    gs = [torch.randn(x.shape, generator=g, device=dev) for x in xs]
     gins = [torch.empty_like(x) for x in xs]
     params = tm.make_params(32, [8, 32, 128])
     gp = torch.empty(3 + 2 * 3, device=dev)
@@ -455,48 +516,41 @@ def run_fwd_bwd(args):
         tm.tm_backward_batch(ctx, xs, gs, gins, gp, stream)
 
     def per_image(i):
-        for x, y, g, gi in zip(xs, ys, gs, gins):
+        for x, y, gg, gi in zip(xs, ys, gs, gins):
             tm.tm_forward(ctx, x, y, stream)
-            tm.tm_backward(ctx, x, g, gi, gp, stream)
+            tm.tm_backward(ctx, x, gg, gi, gp, stream)
 
     def fwd(i):
         for x, y in zip(xs, ys):
             tm.tm_forward(ctx, x, y, stream)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batched(0)
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(dev.index or 0)
     clocks.start()
     time.sleep(0.3)
-    ms_b = _timed(batched, args.steps, stream)
+    ms_b = _timed(batched, steps, stream)
     clk = clocks.stop()
-    ms_p = _timed(per_image, max(1, args.steps // 2), stream)
-    ms_f = _timed(fwd, args.steps, stream)
+    ms_p = _timed(per_image, max(1, steps // 2), stream)
+    ms_f = _timed(fwd, steps, stream)
     tm.tm_destroy(ctx)
     npx = n * H * W
-    peak, peak_kind = load_peaks()
     rate = lambda ms: npx / (ms / 1e3) / 1e6  # noqa: E731
-    line = {
-        "metric": METRIC, "value": rate(ms_b), "unit": "MP/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+    return {
+        "value": rate(ms_b), "unit": "MP/s", "ms_per_step": ms_b, "steps": steps, "warmup": warmup,
+        "dtype": "f32",
         "config": {"workload": "wdr-1mp-x16-fwd-bwd", "images": n, "height": H, "width": W,
                    "n_bins": 32, "radii": [8, 32, 128],
                    "path": "batched forward + batched backward (forward intermediates reused)",
-                   "l2": "inputs larger than L2"},
+                   "l2": "inputs larger than L2", "inputs": "rendered on the device (synth.wdr_device)"},
         "per_image_fwd_bwd": {"value": rate(ms_p), "unit": "MP/s", "ms": ms_p},
         "per_image_forward": {"value": rate(ms_f), "unit": "MP/s", "ms": ms_f},
-        "path_roofline": {"bytes_per_px": 36 + 48, "achieved": 84 * npx / (ms_b / 1e3) / 1e9,
-                          "peak": peak, "unit": "GB/s", "frac": 84 * npx / (ms_b / 1e3) / 1e9 / peak,
-                          "peak_kind": peak_kind},
+        "path_roofline": _roof(36 + 48, npx, ms_b),
         "clocks": clk,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    return 0
 
 
-def run_paper_preset(args):
+def leg_paper_preset(args, dev, steps=None, warmup=None):
     """The paper's own setting at 12 MP: s = 5 fields halving from the whole
     image (rectangular), n = 5 bins, eps 0.1, sat 0.6 (tm_params_pyramid)."""
     import torch
@@ -504,54 +558,71 @@ def run_paper_preset(args):
     import paper_2102_01289_gb300 as tm
     import synth
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
+    rank = dist_env()[0]
+    steps = steps or max(3, min(args.steps, 10))
+    warmup = warmup or 3
     tm.build()
     H, W = 3000, 4000
-    imgs = [synth.wdr_image(H, W, seed=3 + j + 2 * rank, decades=(-3.0, 5.0)) for j in range(2)]
-    xs = [torch.from_numpy(a).to(dev) for a in imgs]
+    xs = [synth.wdr_device(H, W, seed=3 + j + 2 * rank, device=dev, decades=(-3.0, 5.0)) for j in range(2)]
     ys = [torch.empty_like(x) for x in xs]
     params = tm.tm_params_pyramid(W, H, 5, 5)
     ctx = tm.tm_create(params)
     tm.tm_set_option(ctx, tm.TM_OPT_HIST_PATH, HIST_PATHS[args.hist_path])
     stream = torch.cuda.current_stream(dev)
-    for i in range(args.warmup):
+    for i in range(warmup):
         tm.tm_forward(ctx, xs[i % 2], ys[i % 2], stream)
     launches = tm.tm_last_launch_count(ctx)
     tm.tm_set_option(ctx, tm.TM_OPT_STAGE_TIMING, 1)
     tm.tm_stage_times(ctx)
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(dev.index or 0)
     clocks.start()
     time.sleep(0.3)
-    ms = _timed(lambda i: tm.tm_forward(ctx, xs[i % 2], ys[i % 2], stream), args.steps, stream)
+    ms = _timed(lambda i: tm.tm_forward(ctx, xs[i % 2], ys[i % 2], stream), steps, stream)
     clk = clocks.stop()
     stages = tm.tm_stage_times(ctx)
     tm.tm_destroy(ctx)
-    peak, peak_kind = load_peaks()
     npx = H * W
-    line = {
-        "metric": METRIC, "value": npx / (ms / 1e3) / 1e6, "unit": "MP/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+    return {
+        "value": npx / (ms / 1e3) / 1e6, "unit": "MP/s", "ms_per_step": ms, "steps": steps, "warmup": warmup,
+        "dtype": "f32",
         "config": {"workload": "wdr-12mp-paper-preset", "height": H, "width": W, "n_bins": 5,
                    "fields": [[int(params.rx[f]), int(params.ry[f])] for f in range(5)],
                    "hist_path": "materialised" if "integral_histogram" in stages else "fused",
-                   "l2": "inputs larger than L2 (two 144 MB images alternated)"},
-        "stages_ms_per_step": {k: v / args.steps for k, v in stages.items()},
-        "path_roofline": {"bytes_per_px": PATH_BYTES_PER_PX,
-                          "achieved": PATH_BYTES_PER_PX * npx / (ms / 1e3) / 1e9, "peak": peak,
-                          "unit": "GB/s", "frac": PATH_BYTES_PER_PX * npx / (ms / 1e3) / 1e9 / peak,
-                          "peak_kind": peak_kind},
-        "clocks": clk, "gpu_launches": int(launches * args.steps),
+                   "l2": "inputs larger than L2 (two 144 MB images alternated)",
+                   "inputs": "rendered on the device (synth.wdr_device)"},
+        "stages_ms_per_step": {k: v / steps for k, v in stages.items()},
+        "path_roofline": _roof(PATH_BYTES_PER_PX, npx, ms),
+        "clocks": clk, "gpu_launches": int(launches * steps),
     }
+
+
+def run_leg(args, which):
+    """One leg as its own JSON line (--workload)."""
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if which in ("batch-video", "batch-uneven"):
+        d = leg_batch(args, dev, which, steps=args.steps, warmup=args.warmup)
+    elif which == "fwd-bwd":
+        d = leg_fwd_bwd(args, dev, steps=args.steps, warmup=args.warmup)
+    else:
+        d = leg_paper_preset(args, dev, steps=args.steps, warmup=args.warmup)
+    line = {"metric": METRIC, "value": d.pop("value"), "unit": d.pop("unit"), "n_gpus": world,
+            "steps": d.pop("steps"), "warmup": d.pop("warmup"), "ms_per_step": d.pop("ms_per_step"),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": d.pop("dtype"),
+            "data": "synthetic", "config": d.pop("config")}
+    line.update(d)
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
 
 
-def load_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary."""
+def load_profile(kernel, key="bytes_per_launch"):
+    """A per-launch figure of `kernel` from the committed ncu summary
+    (profiles/traffic.json: DRAM bytes, warp instructions), or None once the
+    kernel's source has changed since it was taken."""
     if not kernel:
         return None
     p = os.path.join(ROOT, "profiles", "traffic.json")
@@ -561,7 +632,11 @@ def load_traffic(kernel):
     e = d.get(kernel)
     if not e or e.get("source_hash") != kernel_source_hash(kernel):
         return None
-    return e.get("bytes_per_launch")
+    return e.get(key)
+
+
+def load_traffic(kernel):
+    return load_profile(kernel, "bytes_per_launch")
 
 
 HIST_PATHS = {"auto": 0, "fused": 1, "materialised": 2}
@@ -572,7 +647,7 @@ def kernel_source_hash(kernel):
 
     import paper_2102_01289_gb300 as tm
 
-    srcs = {"fused_sweep": "tm_fused.cu", "lookup": "tm_lookup.cu",
+    srcs = {"fused_sweep": "tm_sweep.cu", "lookup": "tm_lookup.cu",
             "integral_histogram": "tm_integral.cu", "integral_image": "tm_integral.cu",
             "prep": "tm_prepass.cu", "range": "tm_prepass.cu"}
     f = os.path.join(tm.PKG, "csrc", srcs.get(kernel, ""))
@@ -587,8 +662,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the other legs of the metric (fwd+bwd, batches, paper preset)")
     ap.add_argument("--hist-path", choices=sorted(HIST_PATHS), default="auto",
                     help="histogram path: auto (the library measures both once), fused or materialised")
     ap.add_argument("--ref-seconds", type=float, default=0.0,
@@ -600,12 +677,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload in ("batch-video", "batch-uneven"):
-        return run_batch_workload(args, args.workload)
-    if args.workload == "fwd-bwd":
-        return run_fwd_bwd(args)
-    if args.workload == "paper-preset":
-        return run_paper_preset(args)
+    if args.workload != "fwd-12mp":
+        return run_leg(args, args.workload)
     return run_ours(args)
 
 

@@ -21,7 +21,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["wdr_image", "wdr_mosaic", "wdr_video_frame", "uneven_sizes", "box_image"]
+__all__ = ["wdr_image", "wdr_mosaic", "wdr_video_frame", "uneven_sizes", "box_image", "wdr_device"]
 
 
 def _draw_scene(rng: np.random.Generator, H: int, W: int, n_rects: int):
@@ -124,3 +124,43 @@ def box_image(H: int, W: int, seed: int, levels=(0.01, 100.0), dtype=np.float32)
     y1, x1 = int(rng.integers(y0 + 1, H + 1)), int(rng.integers(x0 + 1, W + 1))
     img[y0:y1, x0:x1] = levels[1]
     return img.astype(dtype), (y0, y1, x0, x1)
+
+
+def wdr_device(H: int, W: int, seed: int, device, decades=(-2.0, 4.0), n_rects: int = 20,
+               noise: float = 0.02, frame=None, drift: float = 0.01, dtype=None):
+    """The same recipe rendered with torch on ``device`` (for benchmarks that
+    need hundreds of megapixels of input quickly). The scene (ramp direction,
+    rectangles, chroma) is drawn from ``seed`` exactly as by ``wdr_image``;
+    ``frame`` (optional) moves the rectangles and drifts the ramp as
+    ``wdr_video_frame`` does. The per-pixel noise comes from a torch generator
+    seeded with ``seed + 1 + frame``, so pixel values differ from the numpy
+    renderers'. Returns an (H, W, 3) tensor (float32 unless ``dtype``)."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    theta, rects, bg = _draw_scene(rng, H, W, n_rects)
+    t = 0.0 if frame is None else float(frame)
+    shift = 0.0 if frame is None else drift * frame
+    lo, hi = decades
+    f64 = torch.float64
+    yy = torch.linspace(-0.5, 0.5, H, dtype=f64, device=device)[:, None]
+    xx = torch.linspace(-0.5, 0.5, W, dtype=f64, device=device)[None, :]
+    ramp = float(np.cos(theta)) * xx + float(np.sin(theta)) * yy
+    ramp = (ramp - ramp.min()) / torch.clamp(ramp.max() - ramp.min(), min=1e-12)
+    dec = lo + (hi - lo) * ramp + shift
+    chroma = torch.empty((H, W, 3), dtype=f64, device=device)
+    chroma[...] = torch.as_tensor(bg, dtype=f64, device=device)
+    for (y0, x0, rh, rw, amp, c, vy, vx) in rects:
+        ys = int(round(y0 + vy * t)) % max(H, 1)
+        xs = int(round(x0 + vx * t)) % max(W, 1)
+        ye, xe = min(ys + rh, H), min(xs + rw, W)
+        dec[ys:ye, xs:xe] += amp
+        chroma[ys:ye, xs:xe] = torch.as_tensor(c, dtype=f64, device=device)
+    dec.clamp_(lo, hi)
+    Y = torch.pow(10.0, dec)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) + 1 + (0 if frame is None else int(frame)))
+    Y *= 1.0 + noise * torch.randn((H, W), generator=g, dtype=f64, device=device)
+    Y.clamp_(min=10.0 ** lo * 1e-3)
+    rgb = chroma * (Y / chroma.mean(dim=2))[..., None]
+    return rgb.to(dtype or torch.float32).contiguous()
