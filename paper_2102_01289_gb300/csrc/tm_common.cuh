@@ -91,7 +91,8 @@ struct SweepPlan {
 enum StageId { kStRange = 0, kStPrep, kStRows, kStCols, kStLook, kNumStages };
 
 // One image of a batch: its buffers and its share of every batched launch.
-struct Job {
+// 16-byte aligned, so that kernels can copy it with 16-byte loads.
+struct alignas(16) Job {
   Image in, out;
   Stats *st;                // range state the bins and q are taken over
   Stats *st_next;           // streaming reuse: receives this image's own range (else null)
@@ -113,6 +114,8 @@ struct Job {
   int item0, nitem;         // this job's slots in the sweep queue (uniform tiles, row-major)
   SweepPlan plan;           // sweep tiling of this image
 };
+
+static_assert(sizeof(Job) % 16 == 0, "jobs are copied in 16-byte words");
 
 // Index of the job owning block `blk` of stage `st` (jobs sorted by b0).
 __device__ __forceinline__ int find_job(const Job *jobs, int njobs, int st, int blk) {
@@ -278,11 +281,11 @@ __device__ __forceinline__ Win window_of(const DevParams &P, int f, int x, int y
 // 1/N; inv_scale2 = 2^-2Q converts to lhat units.
 __device__ __forceinline__ float window_variance(long long s1, long long s2, unsigned long long N,
                                                  float rN, float inv_scale2) {
-  const long long m = (long long)rintf((float)s1 * rN);
-  const long long d = s1 - m * (long long)N;
-  const unsigned long long T =
-      (unsigned long long)s2 - (unsigned long long)m * (unsigned long long)(s1 + d);
-  const float df = (float)d;
+  // |mean| <= 2^(Q-1) <= 2^23: the nearest integer fits 32 bits
+  const int m = __float2int_rn(__ll2float_rn(s1) * rN);
+  const long long d = s1 - (long long)m * (long long)N;
+  const unsigned long long T = (unsigned long long)s2 - (unsigned long long)((long long)m * (s1 + d));
+  const float df = __ll2float_rn(d);
   const float v = fmaf(-df * rN, df, __ull2float_rn(T)) * rN;
   return fmaxf(v, 0.f) * inv_scale2;
 }

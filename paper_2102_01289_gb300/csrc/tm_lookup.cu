@@ -15,24 +15,24 @@ namespace {
 
 // Window statistics of field f at (x, y): reciprocal area and variance
 // (Eq. 6, Eq. 10). s12: the integral images of q and q^2 interleaved, one
-// 16-byte load per corner.
+// 16-byte load per corner; positions fit 32 bits (the image holds fewer than
+// 2^31 pixels). The reciprocal is the fast one (within 1 ulp).
 __device__ __forceinline__ void window_stats(const DevParams &P, int f, int x, int y, int W, int H,
                                              const longlong2 *__restrict__ s12, int qbits,
                                              float inv_scale2, float &rarea, float &var) {
-  const long long W1 = (long long)W + 1;
-  Win w = window_of(P, f, x, y, W, H);
-  const long long iA = (long long)w.y0 * W1 + w.x0;
-  const long long iB = (long long)w.y0 * W1 + w.x1 + 1;
-  const long long iC = (long long)(w.y1 + 1) * W1 + w.x1 + 1;
-  const long long iD = (long long)(w.y1 + 1) * W1 + w.x0;
-  unsigned long long N = (unsigned long long)(w.x1 - w.x0 + 1) * (w.y1 - w.y0 + 1);
-  const longlong2 a = __ldg(s12 + iA), b = __ldg(s12 + iB), c = __ldg(s12 + iC), d = __ldg(s12 + iD);
+  const unsigned W1 = (unsigned)W + 1u;
+  const int x0 = max(x - P.rx[f], 0), x1 = min(x + P.rx[f], W - 1);
+  const int y0 = max(y - P.ry[f], 0), y1 = min(y + P.ry[f], H - 1);
+  const unsigned rt = (unsigned)y0 * W1, rb = (unsigned)(y1 + 1) * W1;
+  const longlong2 a = __ldg(s12 + (rt + (unsigned)x0)), b = __ldg(s12 + (rt + (unsigned)x1 + 1u));
+  const longlong2 c = __ldg(s12 + (rb + (unsigned)x1 + 1u)), d = __ldg(s12 + (rb + (unsigned)x0));
+  unsigned long long N = (unsigned long long)((unsigned)(x1 - x0 + 1) * (unsigned)(y1 - y0 + 1));
   long long q1 = (long long)((unsigned long long)c.x - (unsigned long long)d.x - (unsigned long long)b.x +
                              (unsigned long long)a.x);
   long long q2 = (long long)((unsigned long long)c.y - (unsigned long long)d.y - (unsigned long long)b.y +
                              (unsigned long long)a.y);
   literal_area(P, f, qbits, q1, q2, N);
-  rarea = __frcp_rn((float)N);
+  rarea = __fdividef(1.f, (float)N);
   var = window_variance(q1, q2, N, rarea, inv_scale2);
 }
 
@@ -71,7 +71,7 @@ __device__ __forceinline__ void finish_pixel(const Image &in, const Image &out, 
                                 : __fdividef(fu.mean, (float)P.n_fields);  // Eq. 3
   float r, g, b;
   load_rgb(in, x, y, r, g, b);
-  const float inv_i = __frcp_rn(luminance(r, g, b));
+  const float inv_i = __fdividef(1.f, luminance(r, g, b));
   store_rgb(out, x, y, restore_channel(r, inv_i, P.sat, L), restore_channel(g, inv_i, P.sat, L),
             restore_channel(b, inv_i, P.sat, L), (P.flags & kFlagSrgb) != 0);
   if (dbg.l) dbg.l[(long long)y * in.W + x] = L;
