@@ -490,7 +490,7 @@ tm_status forward_materialised(tm_ctx *c, const tm_image *in, const tm_image *ou
   mark(c, s, -1);
   if (run_range) launch_range(c->djobs, 1, rb, c->p.n_bins, s);
   mark(c, s, ST_RANGE);
-  launch_prep(c->djobs, 1, pb, c->p.n_bins, c->p.flags, s);
+  launch_prep(c->djobs, 1, pb, c->p.n_bins, c->p.flags, c->p.n_fields, s);
   mark(c, s, ST_PREP);
   n += (run_range ? 2 : 1) +
        launch_integral_jobs(c->djobs, 1, integral_tile_blocks(W, nseg), integral_col_blocks(W), s);
@@ -649,7 +649,7 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   if (!graph) mark(c, s, -1);
   if (run_range) launch_range(dj, nimg, b_range, c->p.n_bins, s);
   if (!graph) mark(c, s, ST_RANGE);
-  launch_prep(dj, nimg, b_prep, c->p.n_bins, c->p.flags, s);
+  launch_prep(dj, nimg, b_prep, c->p.n_bins, c->p.flags, c->p.n_fields, s);
   if (!graph) mark(c, s, ST_PREP);
   n += (run_range ? 2 : 1) + launch_integral_jobs(dj, nimg, b_rows, b_cols, s);
   if (!graph) mark(c, s, ST_INTEGRAL);

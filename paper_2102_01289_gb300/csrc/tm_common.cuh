@@ -53,7 +53,8 @@ struct Stats {
   float c0;                 // log2 of imin's significand (in [1, 2))
   int e0;                   // unbiased exponent of imin
   float lin_scale;          // 2^Q / imax (quantisation of i / imax)
-  int pad[2];
+  float lg_min;             // log2 imin (first guess of a bin)
+  float bin_scale;          // n / (log2 imax - log2 imin), 0 if degenerate
   float thr[kMaxBins];      // thr[k-1]: lower edge of bin k, k = 1..n-1
 };
 
@@ -198,14 +199,16 @@ __device__ __forceinline__ void store_rgb(const Image &im, int x, int y, float r
   }
 }
 
-// Bin of a luminance (Section II-A): number of edges at or below it.
-__device__ __forceinline__ int bin_of(float i, const float *thr, int n) {
-  int lo = 0, hi = n - 1;  // search thr[0 .. n-2]
-  while (lo < hi) {
-    int mid = (lo + hi) >> 1;
-    if (i >= thr[mid]) lo = mid + 1; else hi = mid;
-  }
-  return lo;
+// Bin of a luminance (Section II-A): the number of edges at or below it. The
+// first guess comes from the fast base-2 log, scaled to bins; the compares
+// against the exact edges then settle it, so the result does not depend on
+// the guess.
+__device__ __forceinline__ int bin_of(float i, const float *thr, int n, float lg_min, float bin_scale) {
+  int k = (int)((__log2f(i) - lg_min) * bin_scale);
+  k = min(max(k, 0), n - 1);
+  while (k > 0 && i < thr[k - 1]) --k;
+  while (k < n - 1 && i >= thr[k]) ++k;
+  return k;
 }
 
 // Quantised normalised log luminance: q = round(2^Q lhat) - 2^(Q-1), with
@@ -217,7 +220,7 @@ __device__ __forceinline__ int quantise_log(float lum, const Stats &st, int qbit
   unsigned bits = __float_as_uint(lum);
   int e = (int)(bits >> 23) - 127;
   float m = __uint_as_float((bits & 0x7fffffu) | 0x3f800000u);
-  float f = log2f(m) - st.c0;
+  float f = __log2f(m) - st.c0;  // m in [1, 2): absolute error near 2^-22
   float de = (float)(e - st.e0);
   float d_hi = de + f;                       // TwoSum(de, f)
   float bv = d_hi - de;

@@ -11,8 +11,10 @@ namespace tmk {
 
 // Stage a0: range of Eq. 11 luminance, bin edges, quantisation constants.
 void launch_range(const Job *jobs, int njobs, int blocks, int n_bins, cudaStream_t s);
-// Stage a1: bin map (uint8) and quantised normalised log (int32).
-void launch_prep(const Job *jobs, int njobs, int blocks, int n_bins, int flags, cudaStream_t s);
+// Stage a1: bin map (uint8), quantised normalised log (int32), the per-row
+// 32-column bin ranges (J.grp, when set) and zeroed count planes (J.cnt,
+// when set: n_fields uint32 planes).
+void launch_prep(const Job *jobs, int njobs, int blocks, int n_bins, int flags, int n_fields, cudaStream_t s);
 // Blocks of the range / prep stages for one image.
 int range_blocks(int W, int H, int num_sms, double share);
 int prep_blocks(int W, int H, int num_sms, double share);
@@ -51,7 +53,7 @@ int launch_integral_histogram(const uint8_t *bins, int W, int H, int n_bins, boo
                               uint32_t *planes, void *scratch, cudaStream_t s);
 
 // Stage a3', fused: plan of one image's sweep (false if the fields do not
-// fit: a swept row over 32 chunks of 32 columns, or windows over 2047 rows);
+// fit: a swept row over 32 chunks of 32 columns);
 // tiles_target: tiles wanted for the image (a whole number of waves). Count
 // plane bytes of the plan (off[f]: byte offset of field f's plane). CTAs of
 // the sweep that fit one SM at `smem` bytes of dynamic shared memory. The

@@ -122,6 +122,8 @@ __device__ void commit_range(Stats *st, unsigned bmin, unsigned bmax, int nb, in
     st->log2_scale =
         degenerate ? 0.f : (float)(ldexp(1.0, qbits) / (log2((double)imax) - log2((double)imin)));
     st->lin_scale = (float)(ldexp(1.0, qbits) / (double)imax);
+    st->lg_min = (float)log2((double)imin);
+    st->bin_scale = degenerate ? 0.f : (float)((double)n_bins / (log2((double)imax) - log2((double)imin)));
     st->imin = imin;
     st->imax = imax;
     st->degenerate = degenerate ? 1 : 0;
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(256) k_range(const Job *__restrict__ jobs, int
 // whole 32-pixel groups so that eight consecutive lanes share one group,
 // whose bin range (smallest | largest << 8) goes to J.grp for the sweep.
 __global__ void __launch_bounds__(256) k_prep(const Job *__restrict__ jobs, int njobs, int n_bins,
-                                              int flags) {
+                                              int flags, int n_fields) {
   __shared__ float thr[kMaxBins];
   const int j = find_job(jobs, njobs, kStPrep, blockIdx.x);
   const Job &J = jobs[j];
@@ -193,6 +195,7 @@ __global__ void __launch_bounds__(256) k_prep(const Job *__restrict__ jobs, int 
   sst.e0 = __ldg(&st->e0);
   sst.log2_scale = __ldg(&st->log2_scale);
   sst.lin_scale = __ldg(&st->lin_scale);
+  const float lg_min = __ldg(&st->lg_min), bin_scale = __ldg(&st->bin_scale);
   const bool lin = (flags & kFlagVarLin) != 0;
   __syncthreads();
   const int W = in.W, H = in.H, qbits = J.qbits;
@@ -217,7 +220,7 @@ __global__ void __launch_bounds__(256) k_prep(const Job *__restrict__ jobs, int 
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const float l = luminance(r[i], g[i], b[i]);
-        const int bi = bin_of(l, thr, n_bins);
+        const int bi = bin_of(l, thr, n_bins, lg_min, bin_scale);
         bq |= (unsigned)bi << (8 * i);
         qq[i] = lin ? quantise_lin(l, sst, qbits) : quantise_log(l, sst, qbits);
         if (i < n) {
@@ -231,10 +234,16 @@ __global__ void __launch_bounds__(256) k_prep(const Job *__restrict__ jobs, int 
       if (n == 4 && (o & 3) == 0) {
         *reinterpret_cast<unsigned *>(bins + o) = bq;
         *reinterpret_cast<int4 *>(q + o) = make_int4(qq[0], qq[1], qq[2], qq[3]);
+        // the sweep adds its bands' contributions into zeroed count planes
+        if (J.cnt)
+          for (int f = 0; f < n_fields; ++f)
+            *reinterpret_cast<int4 *>(J.cnt + J.cnt_off[f] + 4 * o) = make_int4(0, 0, 0, 0);
       } else {
         for (int i = 0; i < n; ++i) {
           bins[o + i] = (uint8_t)(bq >> (8 * i));
           q[o + i] = qq[i];
+          if (J.cnt)
+            for (int f = 0; f < n_fields; ++f) reinterpret_cast<unsigned *>(J.cnt + J.cnt_off[f])[o + i] = 0u;
         }
       }
     }
@@ -270,8 +279,8 @@ void launch_range(const Job *jobs, int njobs, int blocks, int n_bins, cudaStream
   k_range<<<blocks, 256, 0, s>>>(jobs, njobs, n_bins);
 }
 
-void launch_prep(const Job *jobs, int njobs, int blocks, int n_bins, int flags, cudaStream_t s) {
-  k_prep<<<blocks, 256, 0, s>>>(jobs, njobs, n_bins, flags);
+void launch_prep(const Job *jobs, int njobs, int blocks, int n_bins, int flags, int n_fields, cudaStream_t s) {
+  k_prep<<<blocks, 256, 0, s>>>(jobs, njobs, n_bins, flags, n_fields);
 }
 
 }  // namespace tmk

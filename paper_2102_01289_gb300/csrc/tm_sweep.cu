@@ -83,15 +83,6 @@ __host__ __device__ __forceinline__ Lay layout(int kcap) {
   return l;
 }
 
-__device__ __forceinline__ void put_slot(unsigned char *pl, bool wide, long long pix, unsigned val) {
-  if (wide) reinterpret_cast<unsigned *>(pl)[pix] = val;
-  else reinterpret_cast<uint16_t *>(pl)[pix] = (uint16_t)val;
-}
-
-__device__ __forceinline__ unsigned get_slot(const unsigned char *pl, bool wide, long long pix) {
-  return wide ? reinterpret_cast<const unsigned *>(pl)[pix] : (unsigned)reinterpret_cast<const uint16_t *>(pl)[pix];
-}
-
 // E = C_k(jr) - C_k(jl) from the state of threshold row kk (jl = -1: the
 // origin column, where C = 0). With M_k rows lying wholly below k, C_k(j)
 // gains M_k (j + 1), so the pair gains M_k (jr - jl).
@@ -109,7 +100,17 @@ __device__ __forceinline__ unsigned pair_value(const unsigned *PT, const unsigne
   return e;
 }
 
-// One tile: rows [Y0, Y1) of strip `strip` of job J.
+// Adds v to a count slot (a reduction: the value left there is the sum of
+// every band's contributions, modulo 2^32).
+__device__ __forceinline__ void slot_add(unsigned char *pl, long long pix, unsigned v) {
+  atomicAdd(reinterpret_cast<unsigned *>(pl) + pix, v);
+}
+
+// One tile: rows [Y0, Y1) of strip `strip` of job J. The band's sweep starts
+// at its own first row (origin row Y0 - 1, where C = 0): a window reaching
+// above or below the band takes its rows there from the other bands, each
+// band adding E(last row of the window in the band) - E(row above the first)
+// to the pixel's count.
 template <int NF>
 __device__ __forceinline__ void sweep_tile(const DevParams &P, const Job &J, int strip, int Y0, int Y1) {
   unsigned char *const smem = g_smem;
@@ -122,8 +123,7 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const Job &J, int
   const int cR = min(X1 - 1 + S.Rx, W - 1);
   const int g0 = (cL + 1) >> 5;
   const int nch = (cR >> 5) - g0 + 1;
-  const int rL = max(Y0 - S.Ry - 1, -1);
-  const int rR = min(Y1 - 1 + S.Ry, H - 1);
+  const int rL = Y0 - 1;  // origin row
   const int n = P.n_bins, incl = (P.flags & kFlagCdfIncl) ? 1 : 0;
   const int kcap = S.kcap, bstride = S.bstride;
   const Lay L = layout(kcap);
@@ -134,19 +134,21 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const Job &J, int
   uint16_t *const sB = reinterpret_cast<uint16_t *>(smem + L.B);
   const uint8_t *__restrict__ bins = J.bins;
   const uint16_t *__restrict__ grp = J.grp;
-  const unsigned wide = (unsigned)J.cnt_wide;
   const int G = (W + 31) >> 5;
   unsigned char *pl[NF];
 #pragma unroll
   for (int f = 0; f < NF; ++f) pl[f] = J.cnt + J.cnt_off[f];
 
-  // ---- bin range of the tile's own pixels, from the per-row group summary ----
+  // ---- bin range of the pixels whose windows meet the band (its own
+  // columns, the rows the largest half-height reaches), from the per-row
+  // group summary of the bin pass ----
   {
+    const int ya = max(Y0 - S.Ry, 0), yb = min(Y1 + S.Ry, H);
     const int gx0 = X0 >> 5, ngx = ((X1 - 1) >> 5) - gx0 + 1;
     int bmin = 255, bmax = 0;
-    for (int i = tid; i < (Y1 - Y0) * ngx; i += kNT) {
+    for (int i = tid; i < (yb - ya) * ngx; i += kNT) {
       const int yy = i / ngx;
-      const unsigned v = grp[(long long)(Y0 + yy) * G + gx0 + (i - yy * ngx)];
+      const unsigned v = grp[(long long)(ya + yy) * G + gx0 + (i - yy * ngx)];
       bmin = min(bmin, (int)(v & 0xffu));
       bmax = max(bmax, (int)(v >> 8));
     }
@@ -168,9 +170,10 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const Job &J, int
   const int nK = max(0, khi - klo + 1);
   const int npass = max(1, (nK + kcap - 1) / kcap);
 
-  // ---- the thread's event column: top events (tid < 256) or bottom events ----
+  // ---- the thread's event column: windows opening below a swept row
+  // (tid < 256: subtract E) or closing on it (add E) ----
   const int xo = tid & (kTX - 1);
-  const bool is_bottom = tid >= kTX;
+  const bool is_close = tid >= kTX;
   const int x = X0 + xo;
   const bool col_ok = x < X1;
   // per field: half-height, corner columns (relative to 32 g0; jl = -1 is the
@@ -182,7 +185,7 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const Job &J, int
     const int rx = min(P.rx[f], W - 1);
     jr[f] = min(x + rx, W - 1) - 32 * g0;
     jl[f] = max(x - rx, 0) - 1 - 32 * g0;
-    eoff[f] = is_bottom ? -ry[f] : ry[f] + 1;
+    eoff[f] = is_close ? -ry[f] : ry[f] + 1;
   }
   const unsigned lt = (1u << lane) - 1u, le = lt | (1u << lane);
 
@@ -198,42 +201,47 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const Job &J, int
       const int words = (nKp * bstride) >> 1;
       for (int i = tid; i < words; i += kNT) b32[i] = 0u;
     }
+    // E at swept row v for threshold k = b + incl (corner columns cjr, cjl);
+    // false when the threshold belongs to another pass
+    auto event_value = [&](int b, int cjr, int cjl, int v, unsigned &E) -> bool {
+      const int k = b + incl, kk = k - kp0;
+      if ((unsigned)kk < (unsigned)nKp) {
+        E = pair_value(sPT, sM, sB, bstride, kk, cjr, cjl);
+        return true;
+      }
+      // thresholds 0 (nothing below) and n (the whole window) in the first pass
+      E = k <= 0 ? 0u : (unsigned)(cjr - cjl) * (unsigned)(v - rL);
+      return specials && (k <= 0 || k >= n);
+    };
     // bins of a swept row, a warp per chunk (wid, wid + 16; 256 marks columns
     // past the image), and the chunks' bin ranges (lanes = chunks) from the
     // group summary of the bin pass; both loaded one row ahead
     int bcur[kChunksPerWarp], bnxt[kChunksPerWarp];
     unsigned gcur, gnxt = 0xffu;
-    {
-      const int v = rL + 1;
 #pragma unroll
-      for (int q = 0; q < kChunksPerWarp; ++q) {
-        const int c = wid + q * kWarps, col = 32 * (g0 + c) + lane;
-        bcur[q] = (c < nch && col < W && v <= rR) ? (int)__ldg(bins + (long long)v * W + col) : 256;
-        bnxt[q] = 256;
-      }
-      gcur = (lane < nch && v <= rR) ? (unsigned)__ldg(grp + (long long)v * G + g0 + lane) : 0xffu;
+    for (int q = 0; q < kChunksPerWarp; ++q) {
+      const int c = wid + q * kWarps, col = 32 * (g0 + c) + lane;
+      bcur[q] = (c < nch && col < W) ? (int)__ldg(bins + (long long)Y0 * W + col) : 256;
+      bnxt[q] = 256;
     }
+    gcur = lane < nch ? (unsigned)__ldg(grp + (long long)Y0 * G + g0 + lane) : 0xffu;
     // events of the pending row: act bit f = the thread's event of field f is
-    // live; ebin = the bin of its pixel; epark = the parked top value (bottom
-    // events; loaded after the barrier that orders it behind the top events
-    // of the same phase)
+    // live; ebin = the bin of its pixel
     unsigned act = 0u;
     int ebin[NF];
-    unsigned epark[NF];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      ebin[f] = 0;
-      epark[f] = 0u;
-    }
-    for (int v = rL + 1; v <= rR + 1; ++v) {
+    for (int f = 0; f < NF; ++f) ebin[f] = 0;
+    for (int v = Y0; v <= Y1; ++v) {
       // ---- phase 1: events of row v - 1; bins of row v into shared memory ----
-      const bool last = v > rR;
+      const bool last = v >= Y1;
+      // rows Y0 .. Y1 - 2 take the windows opening below them and those
+      // closing on them; the band's last row is taken after the loop
       unsigned nact = 0u;
       int nbin[NF];
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         const int y = v + eoff[f];
-        const bool ok = !last && col_ok && (unsigned)(y - Y0) < (unsigned)(Y1 - Y0) && !(is_bottom && v == H - 1);
+        const bool ok = v < Y1 - 1 && col_ok && (unsigned)y < (unsigned)H;
         nbin[f] = ok ? (int)__ldg(bins + (long long)y * W + x) : 0;
         nact |= (ok ? 1u : 0u) << f;
       }
@@ -241,22 +249,16 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const Job &J, int
 #pragma unroll
         for (int q = 0; q < kChunksPerWarp; ++q) {
           const int c = wid + q * kWarps, col = 32 * (g0 + c) + lane;
-          bnxt[q] = (c < nch && col < W && v + 1 <= rR) ? (int)__ldg(bins + (long long)(v + 1) * W + col) : 256;
+          bnxt[q] = (c < nch && col < W && v + 1 < Y1) ? (int)__ldg(bins + (long long)(v + 1) * W + col) : 256;
         }
-        gnxt = (lane < nch && v + 1 <= rR) ? (unsigned)__ldg(grp + (long long)(v + 1) * G + g0 + lane) : 0xffu;
+        gnxt = (lane < nch && v + 1 < Y1) ? (unsigned)__ldg(grp + (long long)(v + 1) * G + g0 + lane) : 0xffu;
       }
 #pragma unroll
       for (int f = 0; f < NF; ++f) {  // events of row v - 1
         if (!((act >> f) & 1u)) continue;
-        const int k = ebin[f] + incl, kk = k - kp0;
         unsigned E;
-        if ((unsigned)kk < (unsigned)nKp) {
-          E = pair_value(sPT, sM, sB, bstride, kk, jr[f], jl[f]);
-        } else {  // thresholds outside this pass: 0 and n in the first pass, the others later
-          if (!(specials && (k <= 0 || k >= n))) continue;
-          E = k <= 0 ? 0u : (unsigned)(jr[f] - jl[f]) * (unsigned)(v - 1 - rL);
-        }
-        put_slot(pl[f], (wide >> f) & 1u, (long long)(v - 1 + eoff[f]) * W + x, is_bottom ? E - epark[f] : E);
+        if (event_value(ebin[f], jr[f], jl[f], v - 1, E))
+          slot_add(pl[f], (long long)(v - 1 + eoff[f]) * W + x, is_close ? E : 0u - E);
       }
       if (last) break;
 #pragma unroll
@@ -266,17 +268,10 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const Job &J, int
       }
       __syncthreads();
       // ---- phase 2: state update of row v, a warp per threshold (lanes =
-      // chunks); parked values for row v's events ----
+      // chunks) ----
       act = nact;
 #pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        ebin[f] = nbin[f];
-        epark[f] = 0u;
-        if (is_bottom && ((act >> f) & 1u)) {
-          const int y = v + eoff[f];
-          if (max(y - ry[f], 0) - 1 > rL) epark[f] = get_slot(pl[f], (wide >> f) & 1u, (long long)y * W + x);
-        }
-      }
+      for (int f = 0; f < NF; ++f) ebin[f] = nbin[f];
       {
         const bool lc = lane < nch;
         const int cmin = lc ? (int)(gcur & 0xffu) : 256, cmax = lc ? (int)(gcur >> 8) : -1;
@@ -311,46 +306,35 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const Job &J, int
       for (int q = 0; q < kChunksPerWarp; ++q) bcur[q] = bnxt[q];
       gcur = gnxt;
     }
-    // windows clipped at the image's last row all end there: every thread
-    // takes (row, column) pairs of them, four at a time
-    if (rR == H - 1) {
-      const int TXc = X1 - X0;
+    // the band's last row: every window that reaches it and closes on it or
+    // below it adds E(Y1 - 1); every thread takes (row, column) pairs of them,
+    // four at a time
+    const int TXc = X1 - X0, vlast = Y1 - 1;
 #pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        const int ybeg = max(H - 1 - ry[f], Y0), nyb = Y1 - ybeg;
-        if (nyb <= 0) continue;
-        const int rx = min(P.rx[f], W - 1);
-        const int total = nyb * TXc;
-        for (int i0 = tid; i0 < total; i0 += 4 * kNT) {
-          int bb[4], xx[4];
-          unsigned pk[4];
-          long long px[4];
+    for (int f = 0; f < NF; ++f) {
+      const int ybeg = max(vlast - ry[f], 0), yend = min(vlast + ry[f], H - 1);
+      const int total = (yend - ybeg + 1) * TXc;
+      const int rx = min(P.rx[f], W - 1);
+      for (int i0 = tid; i0 < total; i0 += 4 * kNT) {
+        int bb[4], xx[4];
+        long long px[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int i = i0 + u * kNT;
-            bb[u] = -1;
-            if (i < total) {
-              const int yy = i / TXc, y = ybeg + yy;
-              xx[u] = X0 + (i - yy * TXc);
-              px[u] = (long long)y * W + xx[u];
-              bb[u] = (int)__ldg(bins + px[u]);
-              pk[u] = max(y - ry[f], 0) - 1 > rL ? get_slot(pl[f], (wide >> f) & 1u, px[u]) : 0u;
-            }
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + u * kNT;
+          bb[u] = -1;
+          if (i < total) {
+            const int yy = i / TXc;
+            xx[u] = X0 + (i - yy * TXc);
+            px[u] = (long long)(ybeg + yy) * W + xx[u];
+            bb[u] = (int)__ldg(bins + px[u]);
           }
+        }
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            if (bb[u] < 0) continue;
-            const int k = bb[u] + incl, kk = k - kp0;
-            const int cjr = min(xx[u] + rx, W - 1) - 32 * g0, cjl = max(xx[u] - rx, 0) - 1 - 32 * g0;
-            unsigned E;
-            if ((unsigned)kk < (unsigned)nKp) {
-              E = pair_value(sPT, sM, sB, bstride, kk, cjr, cjl);
-            } else {
-              if (!(specials && (k <= 0 || k >= n))) continue;
-              E = k <= 0 ? 0u : (unsigned)(cjr - cjl) * (unsigned)(H - 1 - rL);
-            }
-            put_slot(pl[f], (wide >> f) & 1u, px[u], E - pk[u]);
-          }
+        for (int u = 0; u < 4; ++u) {
+          if (bb[u] < 0) continue;
+          unsigned E;
+          if (event_value(bb[u], min(xx[u] + rx, W - 1) - 32 * g0, max(xx[u] - rx, 0) - 1 - 32 * g0, vlast, E))
+            slot_add(pl[f], px[u], E);
         }
       }
     }
@@ -412,7 +396,6 @@ bool plan_sweep(const DevParams &P, int W, int H, int tiles_target, size_t smem_
     nch_max = max(nch_max, (cR >> 5) - ((cL + 1) >> 5) + 1);
   }
   if (nch_max > kMaxChunks) return false;
-  if (2 * Ry + 1 > kMaxRows) return false;
   s.nch_max = nch_max;
   s.bstride = 32 * nch_max + 2;  // an odd number of words per threshold row
   const int nthr = max(1, P.n_bins - 1);
@@ -422,20 +405,16 @@ bool plan_sweep(const DevParams &P, int W, int H, int tiles_target, size_t smem_
   s.kcap = kcap;
   s.smem = smem_for(kcap, s.bstride);
   // bands: enough tiles for the target (a whole number of waves), each at most
-  // 2047 swept rows
-  const int max_ty = kMaxRows - 2 * Ry;
+  // 2047 rows (a band sweeps its own rows only)
+  const int max_ty = kMaxRows;
   int bands = max(1, (tiles_target + s.tiles_x - 1) / s.tiles_x);
   bands = min(bands, H);
   int TY = (H + bands - 1) / bands;
   if (TY > max_ty) TY = max_ty;
   s.TY = TY;
   s.tiles_y = (H + TY - 1) / TY;
-  // count planes: uint32 slots for windows that can hold 2^16 pixels or more
-  s.cnt_wide = 0;
-  for (int f = 0; f < P.n_fields; ++f) {
-    const long long wx = min(2LL * P.rx[f] + 1, (long long)W), wy = min(2LL * P.ry[f] + 1, (long long)H);
-    if (wx * wy >= 65536) s.cnt_wide |= 1 << f;
-  }
+  // count planes: uint32, the bands' contributions added into them
+  s.cnt_wide = (1 << P.n_fields) - 1;
   S = s;
   return true;
 }
