@@ -243,6 +243,30 @@ tm_status tm_integral_image(const int32_t *q, int32_t width, int32_t height,
 tm_status tm_integral_image_noalloc(const int32_t *q, int32_t width, int32_t height,
                                     int64_t *s1, int64_t *s2, void *stream);
 
+/* The capture front-end of Section III: the paper's application captures
+ * four exposures and recovers the WDR image from them with Debevec and
+ * Malik's radiance-map method before tone mapping it. For each channel c of
+ * each pixel, with z_j its 8-bit value in exposure j, g_c the channel's log
+ * inverse camera response (g_c(z) = ln of the sensor exposure that maps to
+ * z) and dt_j the exposure times,
+ *     ln E = sum_j w(z_j) (g_c(z_j) - ln dt_j) / sum_j w(z_j),
+ *     w(z) = z for z <= 127, 255 - z above,
+ * and out = E. Where every weight is zero (each exposure at 0 or 255) the
+ * estimate of the shortest exposure is taken if it is saturated, else that
+ * of the longest. The camera response is an input (the paper's capture data
+ * and recovered curve are not available).
+ *   n             exposures, 1..8.
+ *   ldr           host array of n device pointers, each an HWC uint8 image of
+ *                 width x height pixels with `pitch` elements per row.
+ *   times         host array of n exposure times, > 0.
+ *   log_response  host float[3 * 256], channel-major g_c(z); finite.
+ *   out           device image, TM_F32 or TM_F16, width x height.
+ * Standalone (no context), asynchronous on `stream`; allocates nothing.
+ * Errors: TM_EINVAL for bad arguments (message in tm_last_error(NULL)). */
+tm_status tm_merge_exposures(int32_t n, const uint8_t *const *ldr, const float *times, int32_t width,
+                             int32_t height, int64_t pitch, const float *log_response,
+                             const tm_image *out, void *stream);
+
 /* Eq. 7-8 on a caller-supplied bin map: hk = n_bins planes, each the
  * (height+1) x (width+1) uint32 integral image of [bins == k] (zero first row
  * and column), plane-major. bins: device uint8[height*width], values < n_bins.

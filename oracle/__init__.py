@@ -123,6 +123,7 @@ def _load():
             lib.tmo_forward_fixed_bins.argtypes = [P, i32, i32, P, P, P]
             lib.tmo_backward.argtypes = [P, i32, i32, P, i32, P, P, P, P]
             lib.tmo_window_counts.argtypes = [P, i32, i32, P, P]
+            lib.tmo_merge_exposures.argtypes = [i32, P, P, i32, i32, P, P]
             lib.tmo_set_threads.argtypes = [i32]
             lib.tmo_num_procs.restype = i32
             _lib = lib
@@ -207,6 +208,23 @@ def window_counts(bins, p: Params) -> np.ndarray:
     if rc:
         raise ValueError(f"tmo_window_counts failed ({rc})")
     return cnt
+
+
+def merge_exposures(ldr, times, log_response) -> np.ndarray:
+    """Section III front-end (Debevec and Malik): the radiance map of n uint8
+    (H, W, 3) exposures with exposure times ``times`` and the per-channel log
+    inverse response ``log_response`` (3, 256). Returns (H, W, 3) float64."""
+    imgs = [np.ascontiguousarray(np.asarray(a, dtype=np.uint8)) for a in ldr]
+    H, W, _ = imgs[0].shape
+    n = len(imgs)
+    ptrs = (ctypes.c_void_p * n)(*[a.ctypes.data for a in imgs])
+    t = np.ascontiguousarray(np.asarray(times, dtype=np.float64))
+    g = np.ascontiguousarray(np.asarray(log_response, dtype=np.float64).reshape(3, 256))
+    out = np.empty((H, W, 3), np.float64)
+    rc = _load().tmo_merge_exposures(n, ctypes.cast(ptrs, ctypes.c_void_p), _ptr(t), W, H, _ptr(g), _ptr(out))
+    if rc:
+        raise ValueError(f"tmo_merge_exposures failed ({rc})")
+    return out
 
 
 def set_threads(n: int) -> None:

@@ -634,3 +634,48 @@ int tmo_backward(const double *rgb, int32_t W, int32_t H, const tmo_params *p,
   core_free(&c);
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Capture front-end (Section III): the WDR image is recovered from several  */
+/* exposures by Debevec and Malik's radiance-map merge. With g_c the log     */
+/* inverse response of channel c (g_c(z) = ln of the sensor exposure X that  */
+/* maps to pixel value z) and dt_j the exposure times, each channel of each  */
+/* pixel takes the hat-weighted mean of the per-exposure log radiances:      */
+/*   ln E = sum_j w(z_j) (g(z_j) - ln dt_j) / sum_j w(z_j),                  */
+/*   w(z) = z for z <= 127, 255 - z above.                                   */
+/* Reading (the merge is 0/0 when every exposure is at 0 or 255): the        */
+/* shortest exposure's estimate when it is saturated, else the longest's.   */
+
+static double merge_weight(int z) { return z <= 127 ? (double)z : (double)(255 - z); }
+
+int tmo_merge_exposures(int32_t n, const uint8_t *const *ldr, const double *times,
+                        int32_t W, int32_t H, const double *log_response, double *out) {
+  if (n < 1 || W < 1 || H < 1) return -1;
+  int shortest = 0, longest = 0;
+  for (int j = 0; j < n; ++j) {
+    if (!(times[j] > 0.0)) return -1;
+    if (times[j] < times[shortest]) shortest = j;
+    if (times[j] > times[longest]) longest = j;
+  }
+  int64_t N = (int64_t)W * H;
+  for (int64_t p = 0; p < N; ++p)
+    for (int c = 0; c < 3; ++c) {
+      const double *g = log_response + 256 * c;
+      double num = 0.0, den = 0.0;
+      for (int j = 0; j < n; ++j) {
+        int z = ldr[j][3 * p + c];
+        double w = merge_weight(z);
+        num += w * (g[z] - log(times[j]));
+        den += w;
+      }
+      double lnE;
+      if (den > 0.0) {
+        lnE = num / den;
+      } else {
+        int j = ldr[shortest][3 * p + c] == 255 ? shortest : longest;
+        lnE = g[ldr[j][3 * p + c]] - log(times[j]);
+      }
+      out[3 * p + c] = exp(lnE);
+    }
+  return 0;
+}

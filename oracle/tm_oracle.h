@@ -128,4 +128,13 @@ int tmo_backward(const double *rgb, int32_t W, int32_t H, const tmo_params *p,
                  int32_t lum_f64, const uint8_t *bins, const double *grad_out,
                  double *grad_in, double *grad_params);
 
+/* Section III capture front-end: Debevec and Malik's radiance map from n
+ * exposures. ldr: n pointers to H*W*3 uint8 (HWC) images; times: n exposure
+ * times (> 0); log_response: 3 x 256 (channel-major), g_c(z) = ln of the
+ * exposure that maps to value z. out: H*W*3 radiances. Weights: the hat
+ * w(z) = z (z <= 127), 255 - z; where every weight is zero, the shortest
+ * exposure's estimate if it is saturated, else the longest's. */
+int tmo_merge_exposures(int32_t n, const uint8_t *const *ldr, const double *times,
+                        int32_t W, int32_t H, const double *log_response, double *out);
+
 #endif

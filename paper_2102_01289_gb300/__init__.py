@@ -36,7 +36,7 @@ EXPORTS = (
     "tm_status_string", "tm_forward", "tm_forward_host", "tm_forward_batch", "tm_backward",
     "tm_integral_image", "tm_integral_histogram", "tm_set_debug", "tm_debug_size",
     "tm_debug_export", "tm_set_option", "tm_last_launch_count", "tm_stage_times",
-    "tm_integral_image_noalloc", "tm_backward_batch", "tm_forward_host_async",
+    "tm_integral_image_noalloc", "tm_backward_batch", "tm_forward_host_async", "tm_merge_exposures",
 )
 
 
@@ -113,6 +113,7 @@ def lib():
             "tm_integral_image_noalloc": (st, [P, i32, i32, P, P, P]),
             "tm_backward_batch": (st, [P, i32, P, P, P, P, P]),
             "tm_forward_host_async": (st, [P, P, P, P]),
+            "tm_merge_exposures": (st, [i32, P, P, i32, i32, i64, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -280,6 +281,24 @@ def tm_integral_image_noalloc(q, s1, s2, stream=None) -> None:
     H, W = q.shape
     _check(lib().tm_integral_image_noalloc(q.data_ptr(), W, H, s1.data_ptr(), s2.data_ptr(),
                                            _stream_ptr(stream)))
+
+
+def tm_merge_exposures(ldr, times, log_response, out, stream=None) -> None:
+    """Section III capture front-end (Debevec and Malik): the radiance map of
+    n uint8 (H, W, 3) device exposures with exposure times ``times`` (host
+    floats) and the per-channel log inverse response ``log_response`` (3 x 256
+    host floats), into the float32/float16 device image ``out``."""
+    import numpy as np
+
+    n = len(ldr)
+    H, W = ldr[0].shape[:2]
+    ptrs = (ctypes.c_void_p * n)(*[a.data_ptr() for a in ldr])
+    t = (ctypes.c_float * n)(*[float(v) for v in times])
+    g = (ctypes.c_float * 768)(*[float(v) for v in np.asarray(log_response, dtype=np.float64).reshape(-1)])
+    o = image_of(out)
+    _check(lib().tm_merge_exposures(n, ctypes.cast(ptrs, ctypes.c_void_p), ctypes.cast(t, ctypes.c_void_p), W, H,
+                                    int(ldr[0].stride(0)), ctypes.cast(g, ctypes.c_void_p), ctypes.byref(o),
+                                    _stream_ptr(stream)))
 
 
 def tm_integral_histogram(bins, n_bins: int, hk, stream=None) -> None:

@@ -21,7 +21,8 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["wdr_image", "wdr_mosaic", "wdr_video_frame", "uneven_sizes", "box_image", "wdr_device"]
+__all__ = ["wdr_image", "wdr_mosaic", "wdr_video_frame", "uneven_sizes", "box_image", "wdr_device",
+           "camera_exposures", "camera_log_response"]
 
 
 def _draw_scene(rng: np.random.Generator, H: int, W: int, n_rects: int):
@@ -164,3 +165,26 @@ def wdr_device(H: int, W: int, seed: int, device, decades=(-2.0, 4.0), n_rects: 
     Y.clamp_(min=10.0 ** lo * 1e-3)
     rgb = chroma * (Y / chroma.mean(dim=2))[..., None]
     return rgb.to(dtype or torch.float32).contiguous()
+
+
+# An assumed camera for the exposure front-end (the paper's capture data and
+# recovered response are not available): sensor exposure X = radiance x time,
+# pixel value z = round(255 (min(X, xsat) / xsat)^(1/gamma)) per channel.
+def camera_exposures(radiance, times, gamma: float = 2.2, xsat: float = 1.0):
+    """uint8 (H, W, 3) exposures of a linear radiance image, one per time."""
+    E = np.asarray(radiance, dtype=np.float64)
+    out = []
+    for t in times:
+        X = np.clip(E * float(t) / xsat, 0.0, 1.0)
+        out.append(np.rint(255.0 * np.power(X, 1.0 / gamma)).astype(np.uint8))
+    return out
+
+
+def camera_log_response(gamma: float = 2.2, xsat: float = 1.0) -> np.ndarray:
+    """(3, 256) log inverse response of that camera: g(z) = ln(xsat (z/255)^gamma)
+    (the value for z = 0 repeats z = 1's; it only enters through zero weight or
+    the all-dark fallback)."""
+    z = np.arange(256, dtype=np.float64)
+    z[0] = 1.0
+    g = np.log(xsat) + gamma * np.log(z / 255.0)
+    return np.repeat(g[None, :], 3, axis=0)

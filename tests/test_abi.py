@@ -128,3 +128,28 @@ def test_defined_flags_accepted(built):
         p = tm.make_params(8, [1, 2])
         p.flags = flags
         tm.tm_destroy(tm.tm_create(p))
+
+
+def test_merge_exposures_rejects_bad_arguments(built):
+    """Host validation of the capture front-end: no launch for a bad count,
+    time, size or response table (TM_EINVAL with a message)."""
+    import ctypes
+
+    L = built
+    fake = (ctypes.c_void_p * 9)(*([0x1000] * 9))
+    times = (ctypes.c_float * 9)(*([0.01] * 9))
+    g = (ctypes.c_float * 768)(*([0.0] * 768))
+    out = tm.TmImage()
+    out.data, out.width, out.height, out.pitch, out.dtype = 0x2000, 4, 3, 12, tm.TM_F32
+    args = lambda n, t=times, gg=g, w=4: (n, ctypes.cast(fake, ctypes.c_void_p), ctypes.cast(t, ctypes.c_void_p),  # noqa: E731
+                                          w, 3, 12, ctypes.cast(gg, ctypes.c_void_p), ctypes.byref(out), None)
+    assert L.tm_merge_exposures(*args(0)) == tm.TM_EINVAL
+    assert L.tm_merge_exposures(*args(9)) == tm.TM_EINVAL
+    bad_t = (ctypes.c_float * 9)(*([0.01] * 8 + [0.0]))
+    assert L.tm_merge_exposures(*args(9, bad_t)) == tm.TM_EINVAL
+    bad_t4 = (ctypes.c_float * 4)(0.01, -1.0, 0.1, 1.0)
+    assert L.tm_merge_exposures(*args(4, bad_t4)) == tm.TM_EINVAL
+    assert b"times" in L.tm_last_error(None)
+    bad_g = (ctypes.c_float * 768)(*([0.0] * 767 + [float("inf")]))
+    assert L.tm_merge_exposures(*args(4, times, bad_g)) == tm.TM_EINVAL
+    assert L.tm_merge_exposures(*args(4, times, g, 5)) == tm.TM_EINVAL  # out size differs

@@ -525,3 +525,66 @@ def test_threads_do_not_change_results(orc):
     assert np.allclose(gi4, gi1, rtol=1e-12, atol=1e-15 * np.abs(gi1).max())
     for k in gp1:
         assert np.allclose(gp4[k], gp1[k], rtol=1e-12, atol=1e-12)
+
+
+# ------------------------------------- Section III capture front-end --
+def _ln_err_bound(ldr):
+    """|ln E_merged - ln E| for a linear camera: each exposure's estimate is
+    off by at most ln(1 + 0.5/z) <= 0.5/z, and w(z) <= z, so the hat-weighted
+    mean is off by at most 0.5 (contributing exposures) / sum of weights."""
+    z = np.stack([a.astype(np.float64) for a in ldr])
+    w = np.where(z <= 127, z, 255 - z)
+    return 0.5 * (w > 0).sum(axis=0) / np.maximum(w.sum(axis=0), 1e-300), w.sum(axis=0)
+
+
+def test_merge_linear_camera_recovers_radiance(orc):
+    """Under a linear response the merged radiance equals the scene radiance
+    within the quantisation bound wherever some exposure is unclipped."""
+    img = synth.wdr_image(24, 31, seed=5).astype(np.float64)
+    times = [5e-5, 5e-4, 5e-3, 5e-2, 5e-1, 5.0]  # six exposures a decade apart cover the image's range
+    ldr = synth.camera_exposures(img, times, gamma=1.0, xsat=1.0)
+    g = synth.camera_log_response(gamma=1.0, xsat=1.0)
+    E = orc.merge_exposures(ldr, times, g)
+    bound, wsum = _ln_err_bound(ldr)
+    ok = wsum > 0
+    assert ok.mean() > 0.99
+    err = np.abs(np.log(E) - np.log(img))
+    assert np.all(err[ok] <= bound[ok] + 1e-12)
+
+
+def test_merge_single_exposure_inverts_the_response(orc):
+    rng = np.random.default_rng(3)
+    z = rng.integers(1, 255, size=(7, 9, 3)).astype(np.uint8)
+    g = synth.camera_log_response(gamma=2.2, xsat=3.0)
+    E = orc.merge_exposures([z], [0.25], g)
+    expect = np.exp(g[np.arange(3)[None, None, :], z] - np.log(0.25))
+    assert np.allclose(E, expect, rtol=1e-14)
+
+
+def test_merge_time_scaling_and_order(orc):
+    """Scaling every exposure time by c divides the radiance by c; the order
+    of the exposures does not matter."""
+    img = synth.wdr_image(11, 13, seed=6).astype(np.float64)
+    times = np.array([2e-4, 3e-3, 2e-2, 5e-1])
+    ldr = synth.camera_exposures(img, times)
+    g = synth.camera_log_response()
+    E = orc.merge_exposures(ldr, times, g)
+    E2 = orc.merge_exposures(ldr, times * 8.0, g)
+    assert np.allclose(E2 * 8.0, E, rtol=1e-12)
+    perm = [2, 0, 3, 1]
+    E3 = orc.merge_exposures([ldr[i] for i in perm], times[perm], g)
+    assert np.allclose(E3, E, rtol=1e-12)
+
+
+def test_merge_hat_weights_and_clipped_fallback(orc):
+    """Values 0 and 255 carry no weight: a pixel at 200 in one exposure and 255
+    in the other takes the first alone; a pixel clipped everywhere takes the
+    shortest exposure when saturated and the longest when black."""
+    g = synth.camera_log_response(gamma=1.0)
+    a = np.array([[[200, 0, 255]]], np.uint8)
+    b = np.array([[[255, 0, 255]]], np.uint8)
+    times = [0.5, 2.0]
+    E = orc.merge_exposures([a, b], times, g)[0, 0]
+    assert np.isclose(E[0], np.exp(g[0, 200] - np.log(0.5)), rtol=1e-14)
+    assert np.isclose(E[1], np.exp(g[1, 0] - np.log(2.0)), rtol=1e-14)    # black: longest
+    assert np.isclose(E[2], np.exp(g[2, 255] - np.log(0.5)), rtol=1e-14)  # saturated: shortest
