@@ -444,6 +444,14 @@ def leg_batch(args, dev, kind, steps=None, warmup=None):
     for _ in range(warmup):
         tm.tm_forward_batch(ctx, xs, ys, stream)
     launches = tm.tm_last_launch_count(ctx)
+    # which batched pass(es) the images took: the fused sweep and/or the
+    # materialised integral histogram (the per-size choice the library made)
+    tm.tm_set_option(ctx, tm.TM_OPT_STAGE_TIMING, 1)
+    tm.tm_stage_times(ctx)
+    tm.tm_forward_batch(ctx, xs, ys, stream)
+    passes = sorted({"batch": "fused", "batch_materialised": "materialised"}[k]
+                    for k in tm.tm_stage_times(ctx) if k in ("batch", "batch_materialised"))
+    tm.tm_set_option(ctx, tm.TM_OPT_STAGE_TIMING, 0)
     clocks.start()
     time.sleep(0.3)
     ms_batch = _timed(lambda i: tm.tm_forward_batch(ctx, xs, ys, stream), steps, stream)
@@ -471,6 +479,7 @@ def leg_batch(args, dev, kind, steps=None, warmup=None):
         "dtype": "f16" if kind == "batch-video" else "f32",
         "config": {"workload": name, "images": n if kind == "batch-video" else 64, "megapixels": npx / 1e6,
                    "n_bins": params.n_bins, "radii": [8, 32, 128], "path": "batched graph",
+                   "histogram_passes": passes,
                    "l2": "inputs larger than L2", "inputs": "rendered on the device (synth.wdr_device)"},
         "per_image_forward": {"value": rate(ms_single), "unit": "MP/s", "ms": ms_single},
         "per_image_forward_reused_range": (

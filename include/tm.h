@@ -175,16 +175,21 @@ tm_status tm_forward_host(tm_ctx *ctx, const tm_image *in_host,
 tm_status tm_forward_host_async(tm_ctx *ctx, const tm_image *in_host,
                                 const tm_image *out_host, void *stream);
 
-/* Forward over n images of possibly different sizes: one launch per stage for
- * the whole batch, the fused sweep as one persistent launch over a shared
- * queue of (image, strip, rows) tiles planned on the device. in[i], out[i]
- * as for tm_forward (host arrays of descriptors; the pixel data is on the
- * device). n == 0 is a no-op. The launch sequence is captured in a CUDA
- * graph and replayed while the same descriptors (pointers, sizes, pitches,
- * dtypes) are passed; a replay reads the current pixel contents. If the
- * fused sweep does not fit the fields, the images are processed one by one
- * as by tm_forward. Results are bit-identical to per-image tm_forward calls
- * on the fused path. */
+/* Forward over n images of possibly different sizes. Each image takes the
+ * histogram path a single-image tm_forward of its size and dtype pair would
+ * take (TM_OPT_HIST_PATH; automatic: the fused sweep where it fits the
+ * fields and measured faster, else the materialised integral histogram).
+ * The images on the fused path run as one batched pass: one launch per
+ * stage, the sweep as one persistent launch over a shared queue of (image,
+ * strip, row band) tiles. Those on the materialised path run as another:
+ * the range, bin and integral-image stages once for all of them, then each
+ * image's integral histogram and lookup. in[i], out[i] as for tm_forward
+ * (host arrays of descriptors; the pixel data is on the device). n == 0 is a
+ * no-op. Each pass is captured in a CUDA graph and replayed while the same
+ * descriptors (pointers, sizes, pitches, dtypes) are passed; a replay reads
+ * the current pixel contents. The first batch containing a new image size
+ * may time both paths on it (synchronising `stream`, as tm_forward does).
+ * Results are bit-identical to per-image tm_forward calls. */
 tm_status tm_forward_batch(tm_ctx *ctx, int32_t n, const tm_image *in,
                            const tm_image *out, void *stream);
 

@@ -115,9 +115,18 @@ struct tm_ctx {
   uint8_t *bins = nullptr;
   int32_t *q = nullptr;
   DebugPlanes dbg{};
-  // CUDA graph of the last batch, replayed while the batch is unchanged
+  // CUDA graph of the last batch, replayed while the batch is unchanged (the
+  // images taking the fused path), and of the last batch's images taking the
+  // materialised path, with that pass's own workspace and descriptors
   cudaGraphExec_t graph = nullptr;
   std::vector<tm_image> graph_in, graph_out;
+  cudaGraphExec_t mgraph = nullptr;
+  std::vector<tm_image> mgraph_in, mgraph_out;
+  int64_t mgraph_launches = 0;
+  void *mws = nullptr;
+  size_t mws_bytes = 0;
+  Job *mdjobs = nullptr;
+  size_t mdjobs_bytes = 0;
   cudaStream_t graph_stream = nullptr;
   int64_t graph_launches = 0;
   // streaming range reuse (TM_OPT_REUSE_RANGE): two range states; a forward
@@ -210,10 +219,10 @@ tm_status validate_params(const tm_params *p, std::string &why) {
 }
 
 enum Stage { ST_RANGE, ST_PREP, ST_INTEGRAL, ST_HIST, ST_LOOKUP, ST_SWEEP, ST_BATCH,
-             ST_BWD_PIXEL, ST_BWD_ADJOINT, ST_BWD_INPUT, ST_COUNT };
+             ST_BWD_PIXEL, ST_BWD_ADJOINT, ST_BWD_INPUT, ST_BATCH_MAT, ST_COUNT };
 const char *const kStageNames[ST_COUNT] = {"range", "prep", "integral_image", "integral_histogram",
                                           "lookup", "fused_sweep", "batch", "bwd_pixel",
-                                          "bwd_adjoint", "bwd_input"};
+                                          "bwd_adjoint", "bwd_input", "batch_materialised"};
 
 // Record a stage boundary on stream s (stage < 0 opens a new call).
 void mark(tm_ctx *c, cudaStream_t s, int stage) {
@@ -314,6 +323,10 @@ void drop_graph(tm_ctx *c) {
   c->graph = nullptr;
   c->graph_in.clear();
   c->graph_out.clear();
+  if (c->mgraph) cudaGraphExecDestroy(c->mgraph);
+  c->mgraph = nullptr;
+  c->mgraph_in.clear();
+  c->mgraph_out.clear();
 }
 
 tm_status ensure_stats(tm_ctx *c, int n) {
@@ -703,6 +716,116 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   return TM_OK;
 }
 
+// The materialised path over a batch of images (those whose fields do not fit
+// the sweep, or for which it measured faster): the range, bin, quantised-log
+// and integral-image stages run once for the whole batch; then each image's
+// cumulative integral histogram and lookup, on one shared set of planes (the
+// launches are stream-ordered). The stats of image i are c->stats[stats0 + i].
+// `graph`: capture into the context's materialised-batch graph and replay it
+// while the images are unchanged.
+tm_status forward_materialised_batch(tm_ctx *c, int nimg, const tm_image *in, const tm_image *out, cudaStream_t s,
+                                     bool graph, int stats0) {
+  tm_status st;
+  if (graph && c->mgraph && same_images(c->mgraph_in, in, nimg) && same_images(c->mgraph_out, out, nimg)) {
+    TM_CUDA(c, cudaGraphLaunch(c->mgraph, s));
+    c->launches = c->mgraph_launches;
+    return TM_OK;
+  }
+  double total_px = 0;
+  for (int i = 0; i < nimg; ++i) total_px += (double)in[i].width * in[i].height;
+  std::vector<Job> jobs((size_t)nimg);
+  std::vector<size_t> offs((size_t)nimg);
+  std::vector<JobLayout> lays((size_t)nimg);
+  size_t ws_total = 0, planes_bytes = 0, scratch_bytes = 0;
+  int b_range = 0, b_prep = 0, b_rows = 0, b_cols = 0;
+  const int nplanes = c->p.n_bins - 1;
+  for (int i = 0; i < nimg; ++i) {
+    const int W = in[i].width, H = in[i].height;
+    const double share = nimg == 1 ? 1.0 : std::max(1.0 / c->num_sms, W * (double)H / total_px);
+    Job &J = jobs[(size_t)i];
+    memset(&J, 0, sizeof J);
+    J.qbits = choose_qbits(c->p, W, H);
+    integral_layout(W, H, SIZE_MAX, J.nseg, J.seg_rows);
+    lays[(size_t)i] = job_layout(c->p, W, H, J.nseg, 0, false);
+    offs[(size_t)i] = ws_total;
+    ws_total += lays[(size_t)i].total;
+    if (nplanes > 0) {
+      planes_bytes = std::max(planes_bytes, align256(4 * (size_t)(W + 1) * (H + 1) * nplanes));
+      scratch_bytes = std::max(scratch_bytes, align256(hist_scratch_bytes(W, H, nplanes)));
+    }
+    J.b0[kStRange] = b_range;
+    b_range += range_blocks(W, H, c->num_sms, share);
+    J.b0[kStPrep] = b_prep;
+    b_prep += prep_blocks(W, H, c->num_sms, share);
+    J.b0[kStRows] = b_rows;
+    b_rows += integral_tile_blocks(W, J.nseg);
+    J.b0[kStCols] = b_cols;
+    b_cols += integral_col_blocks(W);
+  }
+  if ((st = ensure_stats(c, stats0 + nimg))) return st;
+  if ((st = grow_device(c, &c->mws, &c->mws_bytes, ws_total + planes_bytes + scratch_bytes))) return st;
+  if ((st = grow_device(c, (void **)&c->mdjobs, &c->mdjobs_bytes, sizeof(Job) * nimg))) return st;
+  if (graph && c->mgraph) {
+    cudaGraphExecDestroy(c->mgraph);  // re-captured below
+    c->mgraph = nullptr;
+  }
+  char *ws = static_cast<char *>(c->mws);
+  uint32_t *planes = nplanes > 0 ? reinterpret_cast<uint32_t *>(ws + ws_total) : nullptr;
+  void *scratch = ws + ws_total + planes_bytes;
+  for (int i = 0; i < nimg; ++i) {
+    Job &J = jobs[(size_t)i];
+    const JobLayout &L = lays[(size_t)i];
+    char *b = ws + offs[(size_t)i];
+    J.in = to_image(&in[i]);
+    J.out = to_image(&out[i]);
+    J.st = c->stats + stats0 + i;
+    J.bins = reinterpret_cast<uint8_t *>(b + L.bins);
+    J.q = reinterpret_cast<int32_t *>(b + L.q);
+    J.s1 = reinterpret_cast<long long *>(b + L.s12);
+    J.s2 = J.s1 + 1;
+    J.s_pair = 1;
+    J.segtot = reinterpret_cast<long long *>(b + L.segtot);
+  }
+  const cudaStream_t caller = s;
+  if (graph) {
+    if (!c->graph_stream) TM_CUDA(c, cudaStreamCreateWithFlags(&c->graph_stream, cudaStreamNonBlocking));
+    s = c->graph_stream;
+    TM_CUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  }
+  int64_t n = put_jobs(jobs.data(), nimg, c->mdjobs, s);
+  launch_range(c->mdjobs, nimg, b_range, c->p.n_bins, s);
+  launch_prep(c->mdjobs, nimg, b_prep, c->p.n_bins, c->p.flags, c->p.n_fields, s);
+  n += 2 + launch_integral_jobs(c->mdjobs, nimg, b_rows, b_cols, s);
+  for (int i = 0; i < nimg; ++i) {
+    const Job &J = jobs[(size_t)i];
+    if (planes) n += launch_integral_histogram(J.bins, J.in.W, J.in.H, c->p.n_bins, true, planes, scratch, s);
+    n += launch_lookup_materialised(J.in, J.out, dev_params(c->p, J.qbits), J.bins, planes,
+                                    reinterpret_cast<int64_t *>(J.s1), DebugPlanes{}, s);
+  }
+  if (graph) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return fail(c, TM_ECUDA, "materialised batch capture failed: %s", cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&c->mgraph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      c->mgraph = nullptr;
+      return cuda_fail(c, e, "cudaGraphInstantiate");
+    }
+    c->mgraph_in.assign(in, in + nimg);
+    c->mgraph_out.assign(out, out + nimg);
+    c->mgraph_launches = n;
+    TM_CUDA(c, cudaGraphLaunch(c->mgraph, caller));
+  }
+  if ((st = check_launch(c, "materialised batch launch"))) return st;
+  c->launches = n;
+  return TM_OK;
+}
+
 // Automatic histogram path: run each path twice on this image and time the
 // second run with events (synchronising the stream); 1 = fused, 2 = materialised.
 tm_status choose_path(tm_ctx *c, const tm_image *in, const tm_image *out, cudaStream_t s, int *choice) {
@@ -877,22 +1000,68 @@ tm_status leave_caller(tm_ctx *c, cudaStream_t s, tm_status st) {
   return TM_OK;
 }
 
-// tm_forward_batch on validated arguments, n >= 1.
+// Path of image i of a batch: 1 = fused sweep, 2 = materialised. The fused
+// path needs the sweep to fit the fields; with TM_OPT_HIST_PATH = 0 the
+// choice is the one measured for single images of that size and dtype pair
+// (choose_path, cached per context), so a batch takes the same path as
+// per-image calls would.
+tm_status batch_path(tm_ctx *c, const tm_image *in, const tm_image *out, cudaStream_t s, int *path) {
+  if (c->p.n_bins < 2 || c->hist_path == 2) {
+    *path = 2;
+    return TM_OK;
+  }
+  SweepPlan plan;
+  const bool fits = plan_sweep(dev_params(c->p, 0), in->width, in->height, 1,
+                               std::min(c->smem_optin - 2048, (size_t)110 * 1024), plan);
+  if (c->hist_path == 1) {
+    if (!fits) return fail(c, TM_EUNSUPPORTED, "fused sweep does not fit these fields (use the materialised path)");
+    *path = 1;
+    return TM_OK;
+  }
+  if (!fits) {
+    *path = 2;
+    return TM_OK;
+  }
+  const auto key = std::make_tuple((int)in->width, (int)in->height, (int)in->dtype, (int)out->dtype);
+  auto it = c->path_choice.find(key);
+  if (it == c->path_choice.end()) {
+    int p = 1;
+    tm_status st = choose_path(c, in, out, s, &p);
+    if (st) return st;
+    it = c->path_choice.emplace(key, p).first;
+  }
+  *path = it->second;
+  return TM_OK;
+}
+
+// tm_forward_batch on validated arguments, n >= 1: the images taking the
+// fused path run as one batched pass, those taking the materialised path as
+// another, each captured in its own graph.
 tm_status forward_batch(tm_ctx *c, int n, const tm_image *in, const tm_image *out, cudaStream_t st) {
   tm_status s = ensure_device_info(c);
   if (s) return s;
-  if (c->p.n_bins > 1 && c->hist_path != 2) {
-    mark(c, st, -1);
-    s = forward_fused(c, n, in, out, st, true);
-    mark(c, st, ST_BATCH);
-    if (s != TM_EUNSUPPORTED) return s;
-    if (c->hist_path == 1)
-      return fail(c, TM_EUNSUPPORTED, "fused sweep does not fit these fields (use the materialised path)");
-  }
-  int64_t total = 0;
+  std::vector<tm_image> fin, fout, min_, mout;
   for (int i = 0; i < n; ++i) {
-    if ((s = forward_device(c, &in[i], &out[i], st))) return s;
+    int path = 1;
+    if ((s = batch_path(c, &in[i], &out[i], st, &path))) return s;
+    (path == 1 ? fin : min_).push_back(in[i]);
+    (path == 1 ? fout : mout).push_back(out[i]);
+  }
+  if ((s = ensure_stats(c, n))) return s;
+  int64_t total = 0;
+  if (!fin.empty()) {
+    mark(c, st, -1);
+    s = forward_fused(c, (int)fin.size(), fin.data(), fout.data(), st, true);
+    if (s) return s;
     total += c->launches;
+    mark(c, st, ST_BATCH);
+  }
+  if (!min_.empty()) {
+    mark(c, st, -1);
+    s = forward_materialised_batch(c, (int)min_.size(), min_.data(), mout.data(), st, true, (int)fin.size());
+    if (s) return s;
+    total += c->launches;
+    mark(c, st, ST_BATCH_MAT);
   }
   c->launches = total;
   return TM_OK;
@@ -947,7 +1116,8 @@ tm_status tm_create(const tm_params *params, tm_ctx **out) {
 
 void tm_destroy(tm_ctx *c) {
   if (!c) return;
-  if (c->ws || c->stats || c->rr_stats || c->stage || c->djobs || c->gdjobs || c->graph || c->hslot[0])
+  if (c->ws || c->mws || c->stats || c->rr_stats || c->stage || c->djobs || c->gdjobs || c->graph || c->mgraph ||
+      c->hslot[0])
     cudaDeviceSynchronize();
   drop_graph(c);
   for (auto &call : c->marks)
@@ -973,6 +1143,8 @@ void tm_destroy(tm_ctx *c) {
   if (c->graph_stream) cudaStreamDestroy(c->graph_stream);
   if (c->gdjobs) cudaFree(c->gdjobs);
   if (c->gditems) cudaFree(c->gditems);
+  if (c->mws) cudaFree(c->mws);
+  if (c->mdjobs) cudaFree(c->mdjobs);
   delete c;
 }
 

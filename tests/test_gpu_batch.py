@@ -199,3 +199,58 @@ def test_uneven_batch_c4_shapes(orc):
         orc.set_threads(1)
     got = big[yy, xx].astype(np.float64)
     assert np.all(np.abs(got - ref) <= 1e-4 * np.maximum(np.abs(ref), 1e-3))
+
+
+def _batch_stages(ctx, xs, ys):
+    tm.tm_set_option(ctx, tm.TM_OPT_STAGE_TIMING, 1)
+    tm.tm_stage_times(ctx)
+    tm.tm_forward_batch(ctx, xs, ys)
+    names = set(tm.tm_stage_times(ctx))
+    tm.tm_set_option(ctx, tm.TM_OPT_STAGE_TIMING, 0)
+    return names
+
+
+def test_paper_preset_batch_takes_the_batched_materialised_path():
+    """The paper's preset (s = 5 fields halving from a 2000 x 1500 image, n = 5)
+    is too wide for the sweep at these sizes: the batch runs as one batched
+    materialised pass (no per-image fallback) and equals per-image calls bit
+    for bit, first captured and then replayed."""
+    p = tm.tm_params_pyramid(2000, 1500, 5, 5)
+    sizes = [(2000, 1500), (1024, 768), (640, 480)]
+    xs = [torch.from_numpy(synth.wdr_image(h, w, seed=300 + i)).cuda() for i, (w, h) in enumerate(sizes)]
+    ys = [torch.empty_like(x) for x in xs]
+    ctx = tm.tm_create(p)
+    try:
+        for rep in range(2):
+            for y in ys:
+                y.zero_()
+            names = _batch_stages(ctx, xs, ys)
+            assert "batch_materialised" in names and "batch" not in names, names
+            torch.cuda.synchronize()
+            for x, y in zip(xs, ys):
+                assert torch.equal(y, _single(ctx, x))
+    finally:
+        tm.tm_destroy(ctx)
+
+
+def test_mixed_batch_splits_by_path():
+    """Fields that fit the sweep on a small image but not on a large one: the
+    batch splits into a fused pass and a materialised pass, each image equal
+    to its own call."""
+    p = tm.make_params(16, [4, (700, 600)])
+    sizes = [(2400, 1800), (300, 200), (1600, 1200), (97, 61)]
+    xs = [torch.from_numpy(synth.wdr_image(h, w, seed=400 + i)).cuda() for i, (w, h) in enumerate(sizes)]
+    ys = [torch.empty_like(x) for x in xs]
+    ctx = tm.tm_create(p)
+    try:
+        tm.tm_set_option(ctx, tm.TM_OPT_HIST_PATH, 1)
+        with pytest.raises(tm.TmError):  # forcing the sweep: the large images do not fit
+            tm.tm_forward_batch(ctx, xs, ys)
+        tm.tm_set_option(ctx, tm.TM_OPT_HIST_PATH, 0)
+        names = _batch_stages(ctx, xs, ys)
+        assert "batch_materialised" in names, names
+        torch.cuda.synchronize()
+        for x, y in zip(xs, ys):
+            assert torch.equal(y, _single(ctx, x))
+    finally:
+        tm.tm_destroy(ctx)
