@@ -175,10 +175,11 @@ tm_status tm_forward_host(tm_ctx *ctx, const tm_image *in_host,
 tm_status tm_forward_host_async(tm_ctx *ctx, const tm_image *in_host,
                                 const tm_image *out_host, void *stream);
 
-/* Forward over n images of possibly different sizes. Each image takes the
- * histogram path a single-image tm_forward of its size and dtype pair would
- * take (TM_OPT_HIST_PATH; automatic: the fused sweep where it fits the
- * fields and measured faster, else the materialised integral histogram).
+/* Forward over n images of possibly different sizes. Images whose fields do
+ * not fit the fused sweep take the materialised integral histogram; the
+ * others take TM_OPT_HIST_PATH's path (automatic: the first batch of a given
+ * list of sizes and dtype pairs times both batched passes on those images,
+ * synchronising `stream` once, and keeps the faster for later batches).
  * The images on the fused path run as one batched pass: one launch per
  * stage, the sweep as one persistent launch over a shared queue of (image,
  * strip, row band) tiles. Those on the materialised path run as another:
@@ -187,9 +188,8 @@ tm_status tm_forward_host_async(tm_ctx *ctx, const tm_image *in_host,
  * (host arrays of descriptors; the pixel data is on the device). n == 0 is a
  * no-op. Each pass is captured in a CUDA graph and replayed while the same
  * descriptors (pointers, sizes, pitches, dtypes) are passed; a replay reads
- * the current pixel contents. The first batch containing a new image size
- * may time both paths on it (synchronising `stream`, as tm_forward does).
- * Results are bit-identical to per-image tm_forward calls. */
+ * the current pixel contents. Results are bit-identical to per-image
+ * tm_forward calls (both paths give the same outputs bit for bit). */
 tm_status tm_forward_batch(tm_ctx *ctx, int32_t n, const tm_image *in,
                            const tm_image *out, void *stream);
 

@@ -142,8 +142,10 @@ struct tm_ctx {
   bool fwd_valid = false;
   std::vector<Job> fwd_jobs, graph_jobs;
   std::vector<tm_image> fwd_in;
-  // automatic histogram path: the measured choice per (width, height, in dtype, out dtype)
+  // automatic histogram path: the measured choice per (width, height, in dtype, out dtype),
+  // and per batch of images that fit the sweep (their sizes and dtype pairs)
   std::map<std::tuple<int, int, int, int>, int> path_choice;
+  std::map<std::vector<std::tuple<int, int, int, int>>, int> batch_choice;
   // stage timing: events recorded on the call's stream after each stage
   int stage_timing = 0;
   std::vector<std::vector<std::pair<cudaEvent_t, int>>> marks;
@@ -1000,54 +1002,82 @@ tm_status leave_caller(tm_ctx *c, cudaStream_t s, tm_status st) {
   return TM_OK;
 }
 
-// Path of image i of a batch: 1 = fused sweep, 2 = materialised. The fused
-// path needs the sweep to fit the fields; with TM_OPT_HIST_PATH = 0 the
-// choice is the one measured for single images of that size and dtype pair
-// (choose_path, cached per context), so a batch takes the same path as
-// per-image calls would.
-tm_status batch_path(tm_ctx *c, const tm_image *in, const tm_image *out, cudaStream_t s, int *path) {
-  if (c->p.n_bins < 2 || c->hist_path == 2) {
-    *path = 2;
-    return TM_OK;
-  }
+// Whether the fused sweep fits image `in` under the context's fields.
+bool sweep_fits(tm_ctx *c, const tm_image *in) {
   SweepPlan plan;
-  const bool fits = plan_sweep(dev_params(c->p, 0), in->width, in->height, 1,
-                               std::min(c->smem_optin - 2048, (size_t)110 * 1024), plan);
-  if (c->hist_path == 1) {
-    if (!fits) return fail(c, TM_EUNSUPPORTED, "fused sweep does not fit these fields (use the materialised path)");
-    *path = 1;
-    return TM_OK;
+  return plan_sweep(dev_params(c->p, 0), in->width, in->height, 1,
+                    std::min(c->smem_optin - 2048, (size_t)110 * 1024), plan);
+}
+
+// Automatic path of a batch's images that fit the sweep: run the batched
+// fused pass and the batched materialised pass twice each on them (without
+// graphs) and time the second runs with events (synchronising the stream);
+// 1 = fused, 2 = materialised. Both passes give bit-identical outputs (the
+// counts are exact and the lookups share their arithmetic).
+tm_status choose_batch_path(tm_ctx *c, int n, const tm_image *in, const tm_image *out, cudaStream_t s, int stats0,
+                            int *choice) {
+  cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+  for (auto &ev : e) TM_CUDA(c, cudaEventCreate(&ev));
+  tm_status st = TM_OK;
+  for (int rep = 0; rep < 2 && !st; ++rep) {
+    cudaEventRecord(e[0], s);
+    st = forward_fused(c, n, in, out, s, false);
+    cudaEventRecord(e[1], s);
+    if (!st) st = forward_materialised_batch(c, n, in, out, s, false, stats0);
+    cudaEventRecord(e[2], s);
   }
-  if (!fits) {
-    *path = 2;
-    return TM_OK;
+  float ms_f = 0.f, ms_m = 0.f;
+  if (!st) {
+    cudaError_t r = cudaEventSynchronize(e[2]);
+    if (r == cudaSuccess) r = cudaEventElapsedTime(&ms_f, e[0], e[1]);
+    if (r == cudaSuccess) r = cudaEventElapsedTime(&ms_m, e[1], e[2]);
+    if (r != cudaSuccess) st = cuda_fail(c, r, "timing the batch histogram paths");
   }
-  const auto key = std::make_tuple((int)in->width, (int)in->height, (int)in->dtype, (int)out->dtype);
-  auto it = c->path_choice.find(key);
-  if (it == c->path_choice.end()) {
-    int p = 1;
-    tm_status st = choose_path(c, in, out, s, &p);
-    if (st) return st;
-    it = c->path_choice.emplace(key, p).first;
-  }
-  *path = it->second;
+  for (auto &ev : e)
+    if (ev) cudaEventDestroy(ev);
+  if (st) return st;
+  *choice = ms_f <= ms_m ? 1 : 2;
   return TM_OK;
 }
 
-// tm_forward_batch on validated arguments, n >= 1: the images taking the
-// fused path run as one batched pass, those taking the materialised path as
-// another, each captured in its own graph.
+// tm_forward_batch on validated arguments, n >= 1. Images whose fields do not
+// fit the sweep take the materialised path; with TM_OPT_HIST_PATH = 0 the
+// others take the path measured faster for this batch (cached per context by
+// the images' sizes and dtype pairs). The images of each path run as one
+// batched pass captured in a graph of its own.
 tm_status forward_batch(tm_ctx *c, int n, const tm_image *in, const tm_image *out, cudaStream_t st) {
   tm_status s = ensure_device_info(c);
   if (s) return s;
   std::vector<tm_image> fin, fout, min_, mout;
   for (int i = 0; i < n; ++i) {
-    int path = 1;
-    if ((s = batch_path(c, &in[i], &out[i], st, &path))) return s;
-    (path == 1 ? fin : min_).push_back(in[i]);
-    (path == 1 ? fout : mout).push_back(out[i]);
+    bool fused = c->p.n_bins > 1 && c->hist_path != 2;
+    if (fused && !sweep_fits(c, &in[i])) {
+      if (c->hist_path == 1)
+        return fail(c, TM_EUNSUPPORTED, "fused sweep does not fit image %d's fields (use the materialised path)", i);
+      fused = false;
+    }
+    (fused ? fin : min_).push_back(in[i]);
+    (fused ? fout : mout).push_back(out[i]);
   }
   if ((s = ensure_stats(c, n))) return s;
+  if (!fin.empty() && c->hist_path == 0) {
+    std::vector<std::tuple<int, int, int, int>> key;
+    for (size_t i = 0; i < fin.size(); ++i)
+      key.emplace_back((int)fin[i].width, (int)fin[i].height, (int)fin[i].dtype, (int)fout[i].dtype);
+    auto it = c->batch_choice.find(key);
+    if (it == c->batch_choice.end()) {
+      int choice = 1;
+      if ((s = choose_batch_path(c, (int)fin.size(), fin.data(), fout.data(), st, (int)min_.size(), &choice)))
+        return s;
+      it = c->batch_choice.emplace(key, choice).first;
+    }
+    if (it->second == 2) {
+      min_.insert(min_.end(), fin.begin(), fin.end());
+      mout.insert(mout.end(), fout.begin(), fout.end());
+      fin.clear();
+      fout.clear();
+    }
+  }
   int64_t total = 0;
   if (!fin.empty()) {
     mark(c, st, -1);
@@ -1499,6 +1529,7 @@ tm_status tm_set_option(tm_ctx *c, int32_t key, int64_t value) {
     if (value < 0 || value > 2) return fail(c, TM_EINVAL, "TM_OPT_HIST_PATH value %lld", (long long)value);
     c->hist_path = (int)value;
     c->path_choice.clear();
+    c->batch_choice.clear();
     return TM_OK;
   }
   return fail(c, TM_EINVAL, "unknown option %d", key);
