@@ -41,6 +41,39 @@ __global__ void k_put_jobs(const __grid_constant__ JobPack<N> p, Job *dst, int n
   for (int i = threadIdx.x; i < words; i += blockDim.x) d[i] = src[i];
 }
 static_assert(sizeof(Job) % 4 == 0, "jobs are copied as words");
+
+// Other descriptor arrays, the same way: up to 24 KB of words per launch.
+constexpr int kPutWordsSmall = 256, kPutWordsLarge = 6144;
+template <int N>
+struct WordPack {
+  unsigned w[N];
+};
+template <int N>
+__global__ void k_put_words(const __grid_constant__ WordPack<N> p, unsigned *dst, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = p.w[i];
+}
+
+// Writes `bytes` (a multiple of 4) from h to device memory d on stream s;
+// returns the launches made.
+int put_words(const void *h, size_t bytes, void *d, cudaStream_t s) {
+  const unsigned *src = static_cast<const unsigned *>(h);
+  unsigned *dst = static_cast<unsigned *>(d);
+  const size_t words = bytes / 4;
+  int launches = 0;
+  for (size_t i = 0; i < words; i += kPutWordsLarge, ++launches) {
+    const int m = (int)std::min<size_t>(kPutWordsLarge, words - i);
+    if (m <= kPutWordsSmall) {
+      WordPack<kPutWordsSmall> p;
+      std::memcpy(p.w, src + i, 4 * (size_t)m);
+      k_put_words<kPutWordsSmall><<<1, 256, 0, s>>>(p, dst + i, m);
+    } else {
+      WordPack<kPutWordsLarge> p;
+      std::memcpy(p.w, src + i, 4 * (size_t)m);
+      k_put_words<kPutWordsLarge><<<1, 256, 0, s>>>(p, dst + i, m);
+    }
+  }
+  return launches;
+}
 }  // namespace
 
 namespace tmk {
@@ -889,52 +922,58 @@ tm_status forward_device(tm_ctx *c, const tm_image *in, const tm_image *out, cud
   return forward_materialised(c, in, out, s);
 }
 
-// Backward of one image given its forward job: workspace carved for this
-// image out of c->bws (grown by the caller to the largest image), per-image
-// accumulators cleared, the parameter sums cleared only for the first image
-// and written out only when grad_params is given (the last image).
-tm_status backward_image(tm_ctx *c, const Job &J, const tm_image *grad_out, const tm_image *grad_in,
-                         float *grad_params, bool first, cudaStream_t s, int64_t &launches) {
-  const int W = J.in.W, H = J.in.H, nf = c->p.n_fields;
-  const size_t N = (size_t)W * H, plane = (size_t)(W + 1) * (H + 1);
-  const size_t o_acc = 0, o_u = align256(sizeof(BwdAcc)), o_v = o_u + align256(4 * N * nf),
-               o_gi = o_v + align256(4 * N * nf), o_iu = o_gi + align256(4 * N),
-               o_cs = o_iu + align256(8 * plane * 2 * nf);
-  char *b = static_cast<char *>(c->bws);
-  BwdJob B{};
-  B.grad_out = to_image(grad_out);
-  if (grad_in) B.grad_in = to_image(grad_in);
-  B.grad_params = grad_params;
-  B.acc = reinterpret_cast<BwdAcc *>(b + o_acc);
-  B.U = reinterpret_cast<float *>(b + o_u);
-  B.V = reinterpret_cast<float *>(b + o_v);
-  B.gi_direct = reinterpret_cast<float *>(b + o_gi);
-  B.IU = reinterpret_cast<unsigned long long *>(b + o_iu);
-  B.IV = B.IU + plane * nf;
-  B.colscr = reinterpret_cast<unsigned long long *>(b + o_cs);
-  if (first) TM_CUDA(c, cudaMemsetAsync(B.acc->g, 0, sizeof(B.acc->g), s));
-  char *z0 = reinterpret_cast<char *>(&B.acc->lmin), *z1 = reinterpret_cast<char *>(&B.acc->argmin);
-  TM_CUDA(c, cudaMemsetAsync(z0, 0, (size_t)(z1 - z0), s));
-  TM_CUDA(c, cudaMemsetAsync(&B.acc->argmin, 0xff, 2 * sizeof(unsigned long long), s));
-  const DevParams P = dev_params(c->p, J.qbits);
-  launches += launch_backward(P, J, B, s);
-  return TM_OK;
-}
-
-size_t backward_bytes(const tm_params &p, int W, int H) {
+// The backward's device workspace: a header of the per-image accumulators,
+// the parameter sums and the descriptor arrays of the largest group, then per
+// image of a group its u / v planes, direct luminance gradient, fixed-point
+// pair planes and their scratch.
+size_t backward_image_bytes(const tm_params &p, int W, int H, int nseg) {
   const size_t N = (size_t)W * H, plane = (size_t)(W + 1) * (H + 1);
   const int nf = p.n_fields;
-  return align256(sizeof(BwdAcc)) + 2 * align256(4 * N * nf) + align256(4 * N) +
-         align256(8 * plane * 2 * nf) + 8 * fix_integral_scratch_elems(W, H, nf);
+  return 2 * align256(4 * N * nf) + align256(4 * N) + align256(16 * plane * nf) +
+         align256(8 * fix_integral_scratch_elems(W, H, nf, nseg));
+}
+
+size_t backward_header_bytes(int n) {
+  return align256(sizeof(BwdAcc) * n) + align256(sizeof(double) * kBwdParams) + align256(sizeof(BwdJob) * n) +
+         align256(sizeof(FixJob) * n);
+}
+
+// Images of a backward group: the workspace of one group stays below this
+// (or holds one image); the groups run one after another on the stream.
+constexpr size_t kBwdGroupBytes = size_t(4) << 30;
+
+// Groups [g[k], g[k + 1]) of the images and each image's row segments of the
+// fixed-point integrals.
+void backward_groups(const tm_params &p, int n, const tm_image *in, std::vector<int> &g, std::vector<int> &nseg,
+                     std::vector<int> &seg_rows) {
+  g.assign(1, 0);
+  size_t used = 0;
+  for (int i = 0; i < n; ++i) {
+    int ns, sr;
+    fix_layout(in[i].width, in[i].height, 1, ns, sr);
+    const size_t b = backward_image_bytes(p, in[i].width, in[i].height, ns);
+    if (i > g.back() && used + b > kBwdGroupBytes) {
+      g.push_back(i);
+      used = 0;
+    }
+    used += b;
+  }
+  g.push_back(n);
+  nseg.assign((size_t)n, 0);
+  seg_rows.assign((size_t)n, 0);
+  for (size_t k = 0; k + 1 < g.size(); ++k)
+    for (int i = g[k]; i < g[k + 1]; ++i)
+      fix_layout(in[i].width, in[i].height, (long long)p.n_fields * (g[k + 1] - g[k]), nseg[(size_t)i],
+                 seg_rows[(size_t)i]);
 }
 
 // tm_backward / tm_backward_batch: validate, recompute the forward of every
-// image in one batched pass, then run the adjoint image by image on one
-// shared workspace (the parameter gradients accumulate over the images).
+// image in one batched pass (or take the last forward's intermediates), then
+// run the adjoint over groups of images, each group in one launch per stage
+// (the parameter gradients accumulate over all images).
 tm_status backward_images(tm_ctx *c, int n, const tm_image *in, const tm_image *grad_out,
                           const tm_image *grad_in, float *grad_params, cudaStream_t s) {
   tm_status st;
-  size_t need = 0;
   for (int i = 0; i < n; ++i) {
     char nm[40];
     snprintf(nm, sizeof nm, "in[%d]", i);
@@ -953,13 +992,25 @@ tm_status backward_images(tm_ctx *c, int n, const tm_image *in, const tm_image *
       if (overlap(&grad_in[i], &in[i]) || overlap(&grad_in[i], &grad_out[i]))
         return fail(c, TM_EINVAL, "grad_in[%d] overlaps in[%d] or grad_out[%d]", i, i, i);
     }
-    need = std::max(need, backward_bytes(c->p, in[i].width, in[i].height));
   }
   if (c->p.n_bins < 2 || c->hist_path == 2)
     return fail(c, TM_EUNSUPPORTED, "the backward runs on the fused path (n_bins >= 2)");
   if (c->p.flags & TM_FLAG_VAR_LINEAR)
     return fail(c, TM_EUNSUPPORTED, "the backward covers the log-domain variance (not TM_FLAG_VAR_LINEAR)");
   if ((st = ensure_device_info(c))) return st;
+  std::vector<int> grp, nseg, seg_rows;
+  backward_groups(c->p, n, in, grp, nseg, seg_rows);
+  int gmax = 0;
+  size_t need = 0;
+  for (size_t k = 0; k + 1 < grp.size(); ++k) {
+    size_t b = 0;
+    for (int i = grp[k]; i < grp[k + 1]; ++i)
+      b += backward_image_bytes(c->p, in[i].width, in[i].height, nseg[(size_t)i]);
+    need = std::max(need, b);
+    gmax = std::max(gmax, grp[k + 1] - grp[k]);
+  }
+  const size_t head = backward_header_bytes(gmax);
+  need += head;
   std::vector<Job> jobs;
   int64_t launches = 0;
   if (c->bwd_reuse && c->fwd_valid && (int)c->fwd_in.size() == n && same_images(c->fwd_in, in, n)) {
@@ -971,10 +1022,69 @@ tm_status backward_images(tm_ctx *c, int n, const tm_image *in, const tm_image *
     launches = c->launches;
   }
   if ((st = grow_device(c, &c->bws, &c->bws_bytes, need))) return st;
-  for (int i = 0; i < n; ++i)
-    if ((st = backward_image(c, jobs[(size_t)i], &grad_out[i], grad_in ? &grad_in[i] : nullptr,
-                             i == n - 1 ? grad_params : nullptr, i == 0, s, launches)))
-      return st;
+  char *b = static_cast<char *>(c->bws);
+  BwdAcc *accs = reinterpret_cast<BwdAcc *>(b);
+  double *gsum = reinterpret_cast<double *>(b + align256(sizeof(BwdAcc) * gmax));
+  BwdJob *dbj = reinterpret_cast<BwdJob *>(reinterpret_cast<char *>(gsum) + align256(sizeof(double) * kBwdParams));
+  FixJob *dfj = reinterpret_cast<FixJob *>(reinterpret_cast<char *>(dbj) + align256(sizeof(BwdJob) * gmax));
+  const int nf = c->p.n_fields;
+  for (size_t k = 0; k + 1 < grp.size(); ++k) {
+    const int i0 = grp[k], m = grp[k + 1] - i0;
+    std::vector<BwdJob> bj((size_t)m);
+    std::vector<FixJob> fj((size_t)m);
+    char *o = b + head;
+    int pix = 0, tiles = 0, cols = 0;
+    for (int r = 0; r < m; ++r) {
+      const int i = i0 + r;
+      const Job &J = jobs[(size_t)i];
+      const int W = J.in.W, H = J.in.H;
+      const size_t N = (size_t)W * H, plane = (size_t)(W + 1) * (H + 1);
+      BwdJob &B = bj[(size_t)r];
+      B = BwdJob{};
+      B.in = J.in;
+      B.grad_out = to_image(&grad_out[i]);
+      if (grad_in) B.grad_in = to_image(&grad_in[i]);
+      B.st = J.st;
+      B.q = J.q;
+      B.s12 = reinterpret_cast<const longlong2 *>(J.s1);
+      B.cnt = J.cnt;
+      for (int f = 0; f < kMaxFields; ++f) B.cnt_off[f] = J.cnt_off[f];
+      B.cnt_wide = J.cnt_wide;
+      B.qbits = J.qbits;
+      B.U = reinterpret_cast<float *>(o);
+      B.V = reinterpret_cast<float *>(o + align256(4 * N * nf));
+      B.gi_direct = reinterpret_cast<float *>(o + 2 * align256(4 * N * nf));
+      char *iuv = o + 2 * align256(4 * N * nf) + align256(4 * N);
+      B.IUV = reinterpret_cast<const longlong2 *>(iuv);
+      B.acc = accs + r;
+      B.b0 = pix;
+      pix += bwd_pixel_blocks(W, H);
+      FixJob &F = fj[(size_t)r];
+      F = FixJob{};
+      F.u = B.U;
+      F.v = B.V;
+      F.amax = B.acc->amax;
+      F.dst = reinterpret_cast<unsigned long long *>(iuv);
+      F.scratch = reinterpret_cast<long long *>(iuv + align256(16 * plane * nf));
+      F.scratch_stride = (long long)fix_integral_scratch_elems(W, H, 1, nseg[(size_t)i]);
+      F.W = W;
+      F.H = H;
+      F.nseg = nseg[(size_t)i];
+      F.seg_rows = seg_rows[(size_t)i];
+      F.np = nf;
+      F.b0_tile = tiles;
+      F.b0_col = cols;
+      tiles += fix_tile_blocks(W, F.nseg, nf);
+      cols += fix_col_blocks(W, nf);
+      for (int f = 0; f < nf; ++f) F.nmax[f] = window_max(dev_params(c->p, J.qbits), f, W, H);
+      o += backward_image_bytes(c->p, W, H, nseg[(size_t)i]);
+    }
+    launches += put_words(bj.data(), sizeof(BwdJob) * (size_t)m, dbj, s);
+    launches += put_words(fj.data(), sizeof(FixJob) * (size_t)m, dfj, s);
+    const DevParams P = dev_params(c->p, jobs[(size_t)i0].qbits);
+    launches += launch_backward(P, dbj, dfj, m, pix, tiles, cols, accs, gsum, k == 0,
+                                k + 2 == grp.size() ? grad_params : nullptr, s);
+  }
   mark(c, s, ST_BWD_ADJOINT);
   if ((st = check_launch(c, "backward launch"))) return st;
   c->launches = launches;

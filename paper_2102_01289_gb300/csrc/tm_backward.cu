@@ -24,6 +24,8 @@
 //           through ln imin and ln imax, routed to the first pixel (raster
 //           order) holding imin / imax.
 //   Eq. 11  i = 0.2126 R + 0.7152 G + 0.0722 B (no gradient where floored).
+// Every stage runs once over the whole batch (block -> image through
+// BwdJob::b0), so a batch of small images fills the GPU as one large one.
 // Per-pixel arithmetic is FP32 (FP64 throughput is a small fraction of FP32
 // on this part). Parameter gradients are summed per block in FP32 and the
 // block sums added into FP64 accumulators with one atomic each.
@@ -32,122 +34,147 @@
 namespace tmk {
 namespace {
 
+// Per-pixel launches: 32 x 8 threads, each thread kRowsPer rows 8 apart, so
+// a block covers a 32 x 32 tile (the block's reductions are paid once per
+// four pixels of a thread).
 constexpr int kBT = 256;
 constexpr int kWarpsB = kBT / 32;
+constexpr int kRowsPer = 4;
+constexpr int kTileH = 8 * kRowsPer;
 
 __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
+__device__ __forceinline__ int find_bwd(const BwdJob *jobs, int n, int blk) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].b0 <= blk) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Clears the per-image accumulators and (first) the parameter sums.
+__global__ void k_bwd_init(BwdAcc *accs, int n, double *gsum, int first) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    BwdAcc &a = accs[i];
+    a.lmin = a.lmax = 0.0;
+    for (int k = 0; k < 2 * kMaxFields; ++k) a.amax[k] = 0u;
+    a.argmin = a.argmax = ~0ull;
+  }
+  if (first && threadIdx.x < kBwdParams) gsum[threadIdx.x] = 0.0;
+}
+
 // Per pixel: forward recomputation, Eq. 12/3/2/4 adjoints, u_f and v_f,
 // direct gradients of the colour restoration, parameter partial sums and the
 // largest |u_f|, |v_f| (for the fixed-point scales). NF = number of fields
-// (so every per-field array lives in registers). Six blocks per SM (40
-// registers at three fields, a few spilled): 2% faster per batch adjoint than
-// the unbounded 61 registers at four blocks.
+// (so every per-field array lives in registers).
 template <int NF>
-__global__ void __launch_bounds__(kBT, 6) k_bwd_pixel(DevParams P, Job J, BwdJob B) {
-  constexpr int kA = 3 + 2 * NF;  // [ld_min, ld_max, sat, eps[NF], alpha[NF]], the layout of BwdAcc::g
+__global__ void __launch_bounds__(kBT) k_bwd_pixel(DevParams P, const BwdJob *__restrict__ jobs, int njobs,
+                                                   double *__restrict__ gsum) {
+  constexpr int kA = 3 + 2 * NF;  // [ld_min, ld_max, sat, eps[NF], alpha[NF]], the layout of gsum
   __shared__ float sh[kA][kWarpsB];
   __shared__ unsigned shm[2 * NF][kWarpsB];
+  const BwdJob &J = jobs[find_bwd(jobs, njobs, blockIdx.x)];
   const int W = J.in.W, H = J.in.H;
-  const long long N = (long long)W * H;
-  const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lb = blockIdx.x - J.b0, bx = (W + 31) / 32;
+  const int x = (lb % bx) * 32 + (threadIdx.x & 31);
+  const int ybase = (lb / bx) * kTileH + (threadIdx.x >> 5);
+  const size_t N = (size_t)W * H;
+  const float inv_scale = ldexpf(1.f, -J.qbits);
+  const float inv_scale2 = inv_scale * inv_scale;
+  const float imin = J.st->imin, imax = J.st->imax;
+  const float span = P.ld_max - P.ld_min;
   float acc[kA];
   unsigned amax[2 * NF];
 #pragma unroll
   for (int k = 0; k < kA; ++k) acc[k] = 0.f;
 #pragma unroll
   for (int k = 0; k < 2 * NF; ++k) amax[k] = 0u;
-  if (pix < N) {
-    const int y = (int)(pix / W), x = (int)(pix - (long long)y * W);
-    const float inv_scale = ldexpf(1.f, -J.qbits);
-    const float inv_scale2 = inv_scale * inv_scale;
-    const long long W1 = (long long)W + 1;
-    float Pf[NF], rarea[NF], var[NF], mu[NF], wv[NF], lf[NF];
-    float wsum = 0.f, accL = 0.f, meanL = 0.f;
+  if (x < W) {
+#pragma unroll 1
+    for (int r = 0; r < kRowsPer; ++r) {
+      const int y = ybase + 8 * r;
+      if (y >= H) break;
+      const unsigned pix = (unsigned)y * (unsigned)W + (unsigned)x;
+      float Pf[NF], rarea[NF], var[NF], mu[NF], wv[NF], lf[NF];
+      float wsum = 0.f, accL = 0.f, meanL = 0.f;
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      const unsigned cnt = load_count(J, f, pix);
-      Win w = window_of(P, f, x, y, W, H);
-      const long long iA = (long long)w.y0 * W1 + w.x0, iB = (long long)w.y0 * W1 + w.x1 + 1;
-      const long long iC = (long long)(w.y1 + 1) * W1 + w.x1 + 1, iD = (long long)(w.y1 + 1) * W1 + w.x0;
-      unsigned long long Nw = (unsigned long long)(w.x1 - w.x0 + 1) * (w.y1 - w.y0 + 1);
-      const longlong2 *s12 = reinterpret_cast<const longlong2 *>(J.s1);  // interleaved (q, q^2) sums
-      const longlong2 a = s12[iA], b = s12[iB], c = s12[iC], d = s12[iD];
-      long long q1 = (long long)((unsigned long long)c.x - (unsigned long long)d.x - (unsigned long long)b.x +
-                                 (unsigned long long)a.x);
-      long long q2 = (long long)((unsigned long long)c.y - (unsigned long long)d.y - (unsigned long long)b.y +
-                                 (unsigned long long)a.y);
-      literal_area(P, f, J.qbits, q1, q2, Nw);  // Algorithm 1's area: zero padding
-      rarea[f] = __frcp_rn((float)Nw);
-      var[f] = window_variance(q1, q2, Nw, rarea[f], inv_scale2);
-      mu[f] = (float)q1 * rarea[f] * inv_scale + 0.5f;  // mean of lhat
-      // Eq. 1, 2, 4 and the sums of Eq. 3, as in the forward
-      Pf[f] = (float)cnt * rarea[f];
-      lf[f] = fmaf(P.ld_max - P.ld_min, Pf[f], P.ld_min);
-      wv[f] = __fdividef(P.alpha[f] * var[f], var[f] + P.eps[f]);
-      wsum += wv[f];
-      accL = fmaf(wv[f], lf[f], accL);
-      meanL += lf[f];
-    }
-    const float L = wsum > 0.f ? __fdividef(accL, wsum) : __fdividef(meanL, (float)NF);
-    // Eq. 12
-    float rgb[3];
-    load_rgb(J.in, x, y, rgb[0], rgb[1], rgb[2]);
-    const float pr = __fmul_rn(0.2126f, rgb[0]), pg = __fmul_rn(0.7152f, rgb[1]), pb = __fmul_rn(0.0722f, rgb[2]);
-    const float raw = __fadd_rn(__fadd_rn(pr, pg), pb);
-    const float i = fmaxf(raw, kLumFloor);
-    const float inv_i = __frcp_rn(i);
-    const float *go = static_cast<const float *>(B.grad_out.p) + (long long)y * B.grad_out.pitch + 3LL * x;
-    float gL = 0.f, gi_direct = 0.f, gC[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const float g = go[c];
-      const float rho = rgb[c] * inv_i;
-      gC[c] = 0.f;
-      if (!(rho > 0.f)) {
-        if (P.sat == 0.f) gL += g;
-        continue;
+      for (int f = 0; f < NF; ++f) {
+        const unsigned cnt = load_count(J, f, pix);
+        const WinMoments m = window_moments(P, f, x, y, W, H, J.s12, J.qbits, inv_scale2);
+        rarea[f] = m.rarea;
+        var[f] = m.var;
+        mu[f] = __ll2float_rn(m.q1) * m.rarea * inv_scale + 0.5f;  // mean of lhat
+        // Eq. 1, 2, 4 and the sums of Eq. 3, as in the forward
+        Pf[f] = (float)cnt * m.rarea;
+        lf[f] = fmaf(span, Pf[f], P.ld_min);
+        wv[f] = __fdividef(P.alpha[f] * m.var, m.var + P.eps[f]);
+        wsum += wv[f];
+        accL = fmaf(wv[f], lf[f], accL);
+        meanL += lf[f];
       }
-      const float rs = exp2f(P.sat * __log2f(rho));
-      gL += g * rs;
-      acc[2] += g * rs * __logf(rho) * L;
-      gC[c] = g * P.sat * rs * L * inv_i / rho;
-      gi_direct -= g * P.sat * rs * L * inv_i;
-    }
-    // Eq. 3, 2, 4
-    const float rws = wsum > 0.f ? 1.f / wsum : 0.f;
+      const float L = wsum > 0.f ? __fdividef(accL, wsum) : __fdividef(meanL, (float)NF);
+      // Eq. 12
+      float rgb[3];
+      load_rgb(J.in, x, y, rgb[0], rgb[1], rgb[2]);
+      const float raw =
+          __fadd_rn(__fadd_rn(__fmul_rn(0.2126f, rgb[0]), __fmul_rn(0.7152f, rgb[1])), __fmul_rn(0.0722f, rgb[2]));
+      const float i = fmaxf(raw, kLumFloor);
+      const float inv_i = __fdividef(1.f, i);
+      const float *go = static_cast<const float *>(J.grad_out.p) + (long long)y * J.grad_out.pitch + 3LL * x;
+      float gL = 0.f, gi_direct = 0.f, gC[3];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      const float dLdLf = wsum > 0.f ? wv[f] * rws : 1.f / (float)NF;
-      const float dLdW = (lf[f] - L) * rws;
-      acc[0] += gL * dLdLf * (1.f - Pf[f]);
-      acc[1] += gL * dLdLf * Pf[f];
-      const float gW = gL * dLdW;
-      const float v = var[f], e = P.eps[f], a = P.alpha[f];
-      const float den = (v + e) * (v + e);
-      acc[3 + f] += gW * (-a * v / den);
-      acc[3 + NF + f] += gW * (v / (v + e));
-      const float gv = gW * a * e / den;
-      const float u = 2.f * gv * rarea[f];
-      const float vv = u * mu[f];
-      B.U[f * N + pix] = u;
-      B.V[f * N + pix] = vv;
-      amax[f] = max(amax[f], __float_as_uint(fabsf(u)));
-      amax[NF + f] = max(amax[NF + f], __float_as_uint(fabsf(vv)));
+      for (int c = 0; c < 3; ++c) {
+        const float g = __ldg(go + c);
+        const float rho = rgb[c] * inv_i;
+        gC[c] = 0.f;
+        if (!(rho > 0.f)) {
+          if (P.sat == 0.f) gL += g;
+          continue;
+        }
+        const float lg = __log2f(rho);
+        const float grs = g * exp2f(P.sat * lg);  // g rho^sat
+        gL += grs;
+        acc[2] += grs * lg * (0.69314718f * L);  // d/dsat: g rho^sat ln(rho) L
+        const float t = grs * P.sat * L;         // g sat rho^sat L = dLoss/d ln rho
+        gC[c] = __fdividef(t, rgb[c]);
+        gi_direct -= t * inv_i;
+      }
+      // Eq. 3, 2, 4
+      const float rws = wsum > 0.f ? __fdividef(1.f, wsum) : 0.f;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const float dLdLf = wsum > 0.f ? wv[f] * rws : 1.f / (float)NF;
+        const float gLf = gL * dLdLf;
+        acc[0] += gLf * (1.f - Pf[f]);
+        acc[1] += gLf * Pf[f];
+        const float gW = gL * (lf[f] - L) * rws;
+        const float v = var[f], e = P.eps[f], a = P.alpha[f];
+        const float ve = v + e;
+        const float rden = __fdividef(1.f, ve * ve);
+        acc[3 + f] -= gW * a * v * rden;
+        acc[3 + NF + f] += gW * v * ve * rden;
+        const float u = 2.f * (gW * a * e * rden) * rarea[f];
+        const float vv = u * mu[f];
+        J.U[f * N + pix] = u;
+        J.V[f * N + pix] = vv;
+        amax[f] = max(amax[f], __float_as_uint(fabsf(u)));
+        amax[NF + f] = max(amax[NF + f], __float_as_uint(fabsf(vv)));
+      }
+      J.gi_direct[pix] = gi_direct;
+      if (J.grad_in.p) {
+        float *gin = static_cast<float *>(J.grad_in.p) + (long long)y * J.grad_in.pitch + 3LL * x;
+        gin[0] = gC[0];
+        gin[1] = gC[1];
+        gin[2] = gC[2];
+      }
+      // first pixel (raster order) holding the range extremes
+      if (i == imin) atomicMin(&J.acc->argmin, (unsigned long long)pix);
+      if (i == imax) atomicMin(&J.acc->argmax, (unsigned long long)pix);
     }
-    B.gi_direct[pix] = gi_direct;
-    float *gin = static_cast<float *>(B.grad_in.p) + (long long)y * B.grad_in.pitch + 3LL * x;
-    if (B.grad_in.p) {
-      gin[0] = gC[0];
-      gin[1] = gC[1];
-      gin[2] = gC[2];
-    }
-    // first pixel (raster order) holding the range extremes
-    if (i == J.st->imin) atomicMin(&B.acc->argmin, (unsigned long long)pix);
-    if (i == J.st->imax) atomicMin(&B.acc->argmax, (unsigned long long)pix);
   }
   // block sums of the parameter partials and block maxima of |u|, |v|
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -166,61 +193,85 @@ __global__ void __launch_bounds__(kBT, 6) k_bwd_pixel(DevParams P, Job J, BwdJob
   if (t < kA) {
     float sum = 0.f;
     for (int w = 0; w < kWarpsB; ++w) sum += sh[t][w];
-    atomicAdd(&B.acc->g[t], (double)sum);
+    atomicAdd(&gsum[t < 3 + NF ? t : kMaxFields + t - NF], (double)sum);  // gsum: eps[kMaxFields], alpha[...]
   } else if (t >= 32 && t < 32 + 2 * NF) {
     const int k = t - 32;
     unsigned m = 0u;
     for (int w = 0; w < kWarpsB; ++w) m = max(m, shm[k][w]);
-    if (m) atomicMax(&B.acc->amax[k < NF ? k : kMaxFields + (k - NF)], m);
+    if (m) atomicMax(&J.acc->amax[k < NF ? k : kMaxFields + (k - NF)], m);
   }
 }
 
 // Per pixel: the adjoint of the window variances, through the normalised log,
 // into the luminance and Eq. 11; range-term partial sums.
 template <int NF>
-__global__ void __launch_bounds__(kBT) k_bwd_input(DevParams P, Job J, BwdJob B) {
+__global__ void __launch_bounds__(kBT) k_bwd_input(DevParams P, const BwdJob *__restrict__ jobs, int njobs) {
   __shared__ float sh[2][kWarpsB];
+  __shared__ float scale[2 * NF][2];  // 2^-shift of each fixed-point plane, as two factors
+  const BwdJob &J = jobs[find_bwd(jobs, njobs, blockIdx.x)];
   const int W = J.in.W, H = J.in.H;
-  const long long N = (long long)W * H;
-  const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (threadIdx.x < 2 * NF) {
+    const int k = threadIdx.x, f = k < NF ? k : k - NF;
+    // 2^-shift (shift in [-67, 209]) as two normal factors, so that
+    // float(sum) x hi x lo rounds once, like ldexpf(float(sum), -shift)
+    const int sh_ = fix_shift(J.acc->amax[k < NF ? k : kMaxFields + f], window_max(P, f, W, H));
+    const int h = sh_ / 2;
+    scale[k][0] = ldexpf(1.f, -h);
+    scale[k][1] = ldexpf(1.f, h - sh_);
+  }
+  __syncthreads();
+  const int lb = blockIdx.x - J.b0, bx = (W + 31) / 32;
+  const int x = (lb % bx) * 32 + (threadIdx.x & 31);
+  const int ybase = (lb / bx) * kTileH + (threadIdx.x >> 5);
   // D = ln imax - ln imin = ln 2 x 2^Q / log2_scale (log2_scale = 2^Q / log2(imax / imin))
   const float l2s = J.st->log2_scale;
   const float D = J.st->imax > J.st->imin && l2s > 0.f ? 0.69314718f * ldexpf(1.f, J.qbits) / l2s : 0.f;
+  const float rD = D > 0.f ? 1.f / D : 0.f;
+  const float inv_scale = ldexpf(1.f, -J.qbits);
+  const unsigned W1 = (unsigned)W + 1u;
+  const size_t plane = (size_t)W1 * ((size_t)H + 1);
   float acc_lmin = 0.f, acc_lmax = 0.f;
-  if (pix < N) {
-    const int y = (int)(pix / W), x = (int)(pix - (long long)y * W);
-    float r, g, b;
-    load_rgb(J.in, x, y, r, g, b);
-    const float raw = __fadd_rn(__fadd_rn(__fmul_rn(0.2126f, r), __fmul_rn(0.7152f, g)), __fmul_rn(0.0722f, b));
-    float gi = B.gi_direct[pix];
-    if (D > 0.f) {
-      const long long W1 = (long long)W + 1, plane = W1 * ((long long)H + 1);
-      const float lh = (float)J.q[pix] * ldexpf(1.f, -J.qbits) + 0.5f;
-      float gl = 0.f;
+  if (x < W) {
+#pragma unroll 1
+    for (int r = 0; r < kRowsPer; ++r) {
+      const int y = ybase + 8 * r;
+      if (y >= H) break;
+      const unsigned pix = (unsigned)y * (unsigned)W + (unsigned)x;
+      float rc, gc, bc;
+      load_rgb(J.in, x, y, rc, gc, bc);
+      const float raw = __fadd_rn(__fadd_rn(__fmul_rn(0.2126f, rc), __fmul_rn(0.7152f, gc)), __fmul_rn(0.0722f, bc));
+      float gi = J.gi_direct[pix];
+      if (D > 0.f) {
+        const float lh = (float)J.q[pix] * inv_scale + 0.5f;
+        float gl = 0.f;
 #pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        Win w = window_of(P, f, x, y, W, H);
-        const long long iA = (long long)w.y0 * W1 + w.x0, iB = (long long)w.y0 * W1 + w.x1 + 1;
-        const long long iC = (long long)(w.y1 + 1) * W1 + w.x1 + 1, iD = (long long)(w.y1 + 1) * W1 + w.x0;
-        const unsigned long long *IU = B.IU + (long long)f * plane, *IV = B.IV + (long long)f * plane;
-        const long long bu = (long long)(IU[iC] - IU[iD] - IU[iB] + IU[iA]);
-        const long long bv = (long long)(IV[iC] - IV[iD] - IV[iB] + IV[iA]);
-        const float nmax = window_max(P, f, W, H);
-        const float fu = ldexpf(__ll2float_rn(bu), -fix_shift(B.acc->amax[f], nmax));
-        const float fv = ldexpf(__ll2float_rn(bv), -fix_shift(B.acc->amax[kMaxFields + f], nmax));
-        gl += lh * fu - fv;
+        for (int f = 0; f < NF; ++f) {
+          const int x0 = max(x - P.rx[f], 0), x1 = min(x + P.rx[f], W - 1);
+          const int y0 = max(y - P.ry[f], 0), y1 = min(y + P.ry[f], H - 1);
+          const unsigned rt = (unsigned)y0 * W1, rb = (unsigned)(y1 + 1) * W1;
+          const longlong2 *I = J.IUV + f * plane;
+          const longlong2 a = __ldg(I + (rt + (unsigned)x0)), b = __ldg(I + (rt + (unsigned)x1 + 1u));
+          const longlong2 c = __ldg(I + (rb + (unsigned)x1 + 1u)), d = __ldg(I + (rb + (unsigned)x0));
+          const long long bu = (long long)((unsigned long long)c.x - (unsigned long long)d.x -
+                                           (unsigned long long)b.x + (unsigned long long)a.x);
+          const long long bv = (long long)((unsigned long long)c.y - (unsigned long long)d.y -
+                                           (unsigned long long)b.y + (unsigned long long)a.y);
+          const float fu = __ll2float_rn(bu) * scale[f][0] * scale[f][1];
+          const float fv = __ll2float_rn(bv) * scale[NF + f][0] * scale[NF + f][1];
+          gl += lh * fu - fv;
+        }
+        const float i = fmaxf(raw, kLumFloor);
+        gi += __fdividef(gl * rD, i);
+        acc_lmin += gl * (lh - 1.f) * rD;
+        acc_lmax -= gl * lh * rD;
       }
-      const float i = fmaxf(raw, kLumFloor);
-      gi += gl / (i * D);
-      acc_lmin = gl * (lh - 1.f) / D;
-      acc_lmax = -gl * lh / D;
-    }
-    // degenerate range: only the direct colour-restoration term reaches i
-    if (B.grad_in.p && raw > kLumFloor) {
-      float *gin = static_cast<float *>(B.grad_in.p) + (long long)y * B.grad_in.pitch + 3LL * x;
-      gin[0] += 0.2126f * gi;
-      gin[1] += 0.7152f * gi;
-      gin[2] += 0.0722f * gi;
+      // degenerate range: only the direct colour-restoration term reaches i
+      if (J.grad_in.p && raw > kLumFloor) {
+        float *gin = static_cast<float *>(J.grad_in.p) + (long long)y * J.grad_in.pitch + 3LL * x;
+        gin[0] += 0.2126f * gi;
+        gin[1] += 0.7152f * gi;
+        gin[2] += 0.0722f * gi;
+      }
     }
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -234,61 +285,68 @@ __global__ void __launch_bounds__(kBT) k_bwd_input(DevParams P, Job J, BwdJob B)
   if (threadIdx.x < 2) {
     float sum = 0.f;
     for (int w = 0; w < kWarpsB; ++w) sum += sh[threadIdx.x][w];
-    atomicAdd(threadIdx.x == 0 ? &B.acc->lmin : &B.acc->lmax, (double)sum);
+    atomicAdd(threadIdx.x == 0 ? &J.acc->lmin : &J.acc->lmax, (double)sum);
   }
 }
 
-// Range terms at the argmin / argmax pixels, and the parameter gradients.
-__global__ void k_bwd_finish(DevParams P, Job J, BwdJob B) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const int W = J.in.W;
-  const float imin = J.st->imin, imax = J.st->imax;
-  if (imax > imin && B.grad_in.p) {
-    const unsigned long long idx[2] = {B.acc->argmin, B.acc->argmax};
-    const double gterm[2] = {B.acc->lmin / (double)imin, B.acc->lmax / (double)imax};
+// Range terms at each image's argmin / argmax pixels, and the parameter
+// gradients.
+__global__ void k_bwd_finish(DevParams P, const BwdJob *__restrict__ jobs, int njobs, const double *gsum,
+                             float *grad_params) {
+  for (int j = threadIdx.x; j < njobs; j += blockDim.x) {
+    const BwdJob &J = jobs[j];
+    const int W = J.in.W;
+    const float imin = J.st->imin, imax = J.st->imax;
+    if (!(imax > imin) || !J.grad_in.p) continue;
+    const unsigned long long idx[2] = {J.acc->argmin, J.acc->argmax};
+    const double gterm[2] = {J.acc->lmin / (double)imin, J.acc->lmax / (double)imax};
     for (int k = 0; k < 2; ++k) {
+      if (idx[k] >= (unsigned long long)W * (unsigned long long)J.in.H) continue;  // no pixel held it
       const long long pix = (long long)idx[k];
       const int y = (int)(pix / W), x = (int)(pix - (long long)y * W);
       float r, g, b;
       load_rgb(J.in, x, y, r, g, b);
       const float raw = __fadd_rn(__fadd_rn(__fmul_rn(0.2126f, r), __fmul_rn(0.7152f, g)), __fmul_rn(0.0722f, b));
       if (!(raw > kLumFloor)) continue;
-      float *gin = static_cast<float *>(B.grad_in.p) + (long long)y * B.grad_in.pitch + 3LL * x;
+      float *gin = static_cast<float *>(J.grad_in.p) + (long long)y * J.grad_in.pitch + 3LL * x;
       gin[0] += (float)(0.2126 * gterm[k]);
       gin[1] += (float)(0.7152 * gterm[k]);
       gin[2] += (float)(0.0722 * gterm[k]);
     }
   }
-  if (B.grad_params)
-    for (int k = 0; k < 3 + 2 * P.n_fields; ++k) B.grad_params[k] = (float)B.acc->g[k];
+  if (grad_params && threadIdx.x == 0) {
+    const int nf = P.n_fields;
+    for (int k = 0; k < 3; ++k) grad_params[k] = (float)gsum[k];
+    for (int f = 0; f < nf; ++f) {
+      grad_params[3 + f] = (float)gsum[3 + f];
+      grad_params[3 + nf + f] = (float)gsum[3 + kMaxFields + f];
+    }
+  }
 }
 
 }  // namespace
 
-int launch_backward(const DevParams &P, const Job &J, const BwdJob &B, cudaStream_t s) {
-  const long long N = (long long)J.in.W * J.in.H;
-  const int blocks = (int)((N + kBT - 1) / kBT);
+int bwd_pixel_blocks(int W, int H) { return ((W + 31) / 32) * ((H + kTileH - 1) / kTileH); }
+
+int launch_backward(const DevParams &P, const BwdJob *jobs, const FixJob *fix, int n, int pix_blocks,
+                    int tile_blocks, int col_blocks, BwdAcc *accs, double *gsum, bool first,
+                    float *grad_params, cudaStream_t s) {
+  k_bwd_init<<<1, 256, 0, s>>>(accs, n, gsum, first ? 1 : 0);
   switch (P.n_fields) {
-#define TM_BWD_PIXEL(nf) case nf: k_bwd_pixel<nf><<<blocks, kBT, 0, s>>>(P, J, B); break;
+#define TM_BWD_PIXEL(nf) case nf: k_bwd_pixel<nf><<<pix_blocks, kBT, 0, s>>>(P, jobs, n, gsum); break;
     TM_BWD_PIXEL(1) TM_BWD_PIXEL(2) TM_BWD_PIXEL(3) TM_BWD_PIXEL(4) TM_BWD_PIXEL(5) TM_BWD_PIXEL(6)
-    TM_BWD_PIXEL(7) default: k_bwd_pixel<8><<<blocks, kBT, 0, s>>>(P, J, B); break;
+    TM_BWD_PIXEL(7) default: k_bwd_pixel<8><<<pix_blocks, kBT, 0, s>>>(P, jobs, n, gsum); break;
 #undef TM_BWD_PIXEL
   }
-  const int W = J.in.W, H = J.in.H;
-  // the integral planes of u_f and v_f in fixed point (IV = IU + s planes),
-  // over tiles, one (u_f, v_f) pair per grid row
-  float nmax[kMaxFields];
-  for (int f = 0; f < P.n_fields; ++f) nmax[f] = window_max(P, f, W, H);
-  const int nc = launch_fix_integrals(B.U, B.V, W, H, P.n_fields, B.acc->amax, nmax, B.IU,
-                                      reinterpret_cast<long long *>(B.colscr), s);
+  const int nc = launch_fix_integrals(fix, n, tile_blocks, col_blocks, s);
   switch (P.n_fields) {
-#define TM_BWD_INPUT(nf) case nf: k_bwd_input<nf><<<blocks, kBT, 0, s>>>(P, J, B); break;
+#define TM_BWD_INPUT(nf) case nf: k_bwd_input<nf><<<pix_blocks, kBT, 0, s>>>(P, jobs, n); break;
     TM_BWD_INPUT(1) TM_BWD_INPUT(2) TM_BWD_INPUT(3) TM_BWD_INPUT(4) TM_BWD_INPUT(5) TM_BWD_INPUT(6)
-    TM_BWD_INPUT(7) default: k_bwd_input<8><<<blocks, kBT, 0, s>>>(P, J, B); break;
+    TM_BWD_INPUT(7) default: k_bwd_input<8><<<pix_blocks, kBT, 0, s>>>(P, jobs, n); break;
 #undef TM_BWD_INPUT
   }
-  k_bwd_finish<<<1, 32, 0, s>>>(P, J, B);
-  return 3 + nc;
+  k_bwd_finish<<<1, 32, 0, s>>>(P, jobs, n, gsum, grad_params);
+  return 4 + nc;
 }
 
 }  // namespace tmk

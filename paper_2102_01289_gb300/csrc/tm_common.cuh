@@ -293,6 +293,37 @@ __device__ __forceinline__ float window_variance(long long s1, long long s2, uns
   return fmaxf(v, 0.f) * inv_scale2;
 }
 
+// Window moments of field f at (x, y) from the interleaved integral images
+// of q and q^2 (Eq. 6, one 16-byte load per corner): the fast reciprocal of
+// the area (within 1 ulp), the variance (Eq. 10) and the window sum of q.
+// Positions fit 32 bits: the image holds fewer than 2^31 pixels, so
+// (W + 1)(H + 1) <= 2^32.
+struct WinMoments {
+  float rarea, var;
+  long long q1;
+};
+__device__ __forceinline__ WinMoments window_moments(const DevParams &P, int f, int x, int y, int W, int H,
+                                                     const longlong2 *__restrict__ s12, int qbits,
+                                                     float inv_scale2) {
+  const unsigned W1 = (unsigned)W + 1u;
+  const int x0 = max(x - P.rx[f], 0), x1 = min(x + P.rx[f], W - 1);
+  const int y0 = max(y - P.ry[f], 0), y1 = min(y + P.ry[f], H - 1);
+  const unsigned rt = (unsigned)y0 * W1, rb = (unsigned)(y1 + 1) * W1;
+  const longlong2 a = __ldg(s12 + (rt + (unsigned)x0)), b = __ldg(s12 + (rt + (unsigned)x1 + 1u));
+  const longlong2 c = __ldg(s12 + (rb + (unsigned)x1 + 1u)), d = __ldg(s12 + (rb + (unsigned)x0));
+  unsigned long long N = (unsigned long long)((unsigned)(x1 - x0 + 1) * (unsigned)(y1 - y0 + 1));
+  long long q1 = (long long)((unsigned long long)c.x - (unsigned long long)d.x - (unsigned long long)b.x +
+                             (unsigned long long)a.x);
+  long long q2 = (long long)((unsigned long long)c.y - (unsigned long long)d.y - (unsigned long long)b.y +
+                             (unsigned long long)a.y);
+  literal_area(P, f, qbits, q1, q2, N);
+  WinMoments m;
+  m.rarea = __fdividef(1.f, (float)N);
+  m.var = window_variance(q1, q2, N, m.rarea, inv_scale2);
+  m.q1 = q1;
+  return m;
+}
+
 // Eq. 2, Eq. 4, Eq. 3 from per-field counts, reciprocal areas and variances.
 // The Eq. 1 quotient is count x (1/N); the Eq. 4 and Eq. 3 quotients use the
 // fast division (about 2 ulp).
@@ -316,8 +347,10 @@ __device__ __forceinline__ float fuse_fields(const DevParams &P, const unsigned 
   return wsum > 0.f ? __fdividef(acc, wsum) : __fdividef(mean, (float)P.n_fields);  // Eq. 3
 }
 
-// Eq. 1 numerator of field f at pixel index pix from the sweep's count planes.
-__device__ __forceinline__ unsigned load_count(const Job &J, int f, long long pix) {
+// Eq. 1 numerator of field f at pixel index pix from the sweep's count planes
+// (J: a job holding cnt, cnt_off and cnt_wide).
+template <class JobT>
+__device__ __forceinline__ unsigned load_count(const JobT &J, int f, long long pix) {
   const unsigned char *pl = J.cnt + J.cnt_off[f];
   return ((J.cnt_wide >> f) & 1) ? __ldg(reinterpret_cast<const unsigned *>(pl) + pix)
                                  : (unsigned)__ldg(reinterpret_cast<const uint16_t *>(pl) + pix);

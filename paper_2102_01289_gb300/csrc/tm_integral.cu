@@ -432,54 +432,61 @@ __global__ void __launch_bounds__(kINT, 4) k_int_write(const Job *__restrict__ j
     int_write_tile(X, src, J.s1, J.s2, lb / X.nchunk, lb % X.nchunk, tile, out1, out2, wt);
 }
 
-// The fixed-point integral planes of float plane pairs (u_p, v_p), p =
-// blockIdx.y: plane p of `u` and of `v` (each W x H), scaled by
-// 2^fix_shift(amax[p], nmax[p]) and 2^fix_shift(amax[kMaxFields + p], nmax[p])
-// (the scales the backward converts back with), into planes p and np + p of
-// `dst`; scratch per pair.
-struct FixPairs {
-  const float *u, *v;
-  const unsigned *amax;  // device: float bits of the largest |u_p| (p) and |v_p| (kMaxFields + p)
-  unsigned long long *dst;
-  long long *scratch;
-  size_t scratch_stride;
-  int W, H, nseg, seg_rows, np;
-  float nmax[kMaxFields];
-};
+// The backward's fixed-point integral planes of a batch of images: block ->
+// image through FixJob::b0_tile / b0_col, then (pair p, tile) or (pair p,
+// column block). Pair p of an image: planes u_p and v_p (each W x H), scaled
+// by 2^fix_shift(amax[p], nmax[p]) and 2^fix_shift(amax[kMaxFields + p],
+// nmax[p]) (the scales the backward converts back with), interleaved into
+// the p-th pair plane of dst (two int64 per position); scratch per pair.
+__device__ __forceinline__ int find_fix(const FixJob *jobs, int n, bool tiles, int blk) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((tiles ? jobs[mid].b0_tile : jobs[mid].b0_col) <= blk) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
 
-__device__ __forceinline__ IntTask fix_task(const FixPairs &F, int p) {
+__device__ __forceinline__ IntTask fix_task(const FixJob &F, int p) {
   return int_task(F.W, F.H, F.nseg, F.seg_rows, F.scratch + (long long)p * F.scratch_stride);
 }
 
-__device__ __forceinline__ FixSource fix_source(const FixPairs &F, int p) {
+__device__ __forceinline__ FixSource fix_source(const FixJob &F, int p) {
   const long long N = (long long)F.W * F.H;
   return FixSource{F.u + p * N, F.v + p * N, F.W, fix_shift(__ldg(F.amax + p), F.nmax[p]),
                    fix_shift(__ldg(F.amax + kMaxFields + p), F.nmax[p])};
 }
 
-__global__ void __launch_bounds__(kINT, 4) k_fix_stats(FixPairs F) {
+__global__ void __launch_bounds__(kINT, 4) k_fix_stats(const FixJob *__restrict__ jobs, int n) {
   __shared__ StatsSmem sm;
-  const int p = blockIdx.y;
+  const FixJob &F = jobs[find_fix(jobs, n, true, blockIdx.x)];
+  const int per = F.nseg * ((F.W + kIC - 1) / kIC), lb = blockIdx.x - F.b0_tile;
+  const int p = lb / per, t = lb - p * per;
   const IntTask X = fix_task(F, p);
-  int_stats_tile(X, fix_source(F, p), blockIdx.x / X.nchunk, blockIdx.x % X.nchunk, sm);
+  int_stats_tile(X, fix_source(F, p), t / X.nchunk, t % X.nchunk, sm);
 }
 
-__global__ void __launch_bounds__(kMidCols * kMidGroups) k_fix_mid(FixPairs F) {
+__global__ void __launch_bounds__(kMidCols * kMidGroups) k_fix_mid(const FixJob *__restrict__ jobs, int n) {
   __shared__ long long part[2][kMidGroups][kMidCols];
   __shared__ long long leftT[2][kMidBatch];
-  int_mid_cols(fix_task(F, blockIdx.y), blockIdx.x * kMidCols, part, leftT);
+  const FixJob &F = jobs[find_fix(jobs, n, false, blockIdx.x)];
+  const int per = (F.W + kMidCols - 1) / kMidCols, lb = blockIdx.x - F.b0_col;
+  const int p = lb / per;
+  int_mid_cols(fix_task(F, p), (lb - p * per) * kMidCols, part, leftT);
 }
 
-__global__ void __launch_bounds__(kINT, 4) k_fix_write(FixPairs F) {
+__global__ void __launch_bounds__(kINT, 4) k_fix_write(const FixJob *__restrict__ jobs, int n) {
   __shared__ float2 tile[kIC / 8 * 9];
   __shared__ long long out1[kIC / 8 * 9], out2[kIC / 8 * 9];
   __shared__ long long wt[2][kINT / 32];
-  const int p = blockIdx.y;
+  const FixJob &F = jobs[find_fix(jobs, n, true, blockIdx.x)];
+  const int per = F.nseg * ((F.W + kIC - 1) / kIC), lb = blockIdx.x - F.b0_tile;
+  const int p = lb / per, t = lb - p * per;
   const IntTask X = fix_task(F, p);
   const long long plane = ((long long)F.W + 1) * ((long long)F.H + 1);
-  long long *d = reinterpret_cast<long long *>(F.dst);
-  int_write_tile(X, fix_source(F, p), d + p * plane, d + (F.np + p) * plane, blockIdx.x / X.nchunk,
-                 blockIdx.x % X.nchunk, tile, out1, out2, wt);
+  long long *d = reinterpret_cast<long long *>(F.dst) + 2 * p * plane;
+  int_write_tile<FixSource, long long, true>(X, fix_source(F, p), d, d + 1, t / X.nchunk, t % X.nchunk, tile,
+                                             out1, out2, wt);
 }
 
 // Integral histogram planes (uint32, modulo 2^32) of a bin map over the same
@@ -547,38 +554,27 @@ int integral_tile_blocks(int W, int nseg) { return nseg * ((W + kIC - 1) / kIC);
 
 int integral_col_blocks(int W) { return (W + kMidCols - 1) / kMidCols; }
 
-// Row segments of the fixed-point pairs: short enough for about 2048 tiles
-// over all pairs (the planes of a backward image are small), 4 to kIR rows.
-static void fix_layout(int W, int H, int pairs, int &nseg, int &seg_rows) {
-  const long long tiles_per_row = (long long)pairs * ((W + kIC - 1) / kIC);
+// Row segments of an image's fixed-point pairs in a batch whose pairs, over
+// all images, number `batch_pairs`: short enough for about 2048 tiles over
+// the batch, 4 to kIR rows.
+void fix_layout(int W, int H, long long batch_pairs, int &nseg, int &seg_rows) {
+  const long long tiles_per_row = batch_pairs * ((W + kIC - 1) / kIC);
   seg_rows = (int)std::min<long long>(kIR, std::max<long long>(4, H * tiles_per_row / 2048));
   nseg = (H + seg_rows - 1) / seg_rows;
 }
 
-size_t fix_integral_scratch_elems(int W, int H, int pairs) {
-  int nseg, seg_rows;
-  fix_layout(W, H, pairs, nseg, seg_rows);
+size_t fix_integral_scratch_elems(int W, int H, int pairs, int nseg) {
   return (size_t)pairs * integral_scratch_elems(W, H, nseg);
 }
 
-int launch_fix_integrals(const float *u, const float *v, int W, int H, int pairs, const unsigned *amax,
-                         const float *nmax, unsigned long long *dst, long long *scratch, cudaStream_t s) {
-  FixPairs F{};
-  F.u = u;
-  F.v = v;
-  F.amax = amax;
-  F.dst = dst;
-  F.W = W;
-  F.H = H;
-  F.np = pairs;
-  fix_layout(W, H, pairs, F.nseg, F.seg_rows);
-  F.scratch = scratch;
-  F.scratch_stride = integral_scratch_elems(W, H, F.nseg);
-  for (int i = 0; i < pairs; ++i) F.nmax[i] = nmax[i];
-  const dim3 tiles(integral_tile_blocks(W, F.nseg), pairs), cols(integral_col_blocks(W), pairs);
-  k_fix_stats<<<tiles, kINT, 0, s>>>(F);
-  k_fix_mid<<<cols, kMidCols * kMidGroups, 0, s>>>(F);
-  k_fix_write<<<tiles, kINT, 0, s>>>(F);
+int fix_tile_blocks(int W, int nseg, int pairs) { return pairs * integral_tile_blocks(W, nseg); }
+
+int fix_col_blocks(int W, int pairs) { return pairs * integral_col_blocks(W); }
+
+int launch_fix_integrals(const FixJob *jobs, int n, int tile_blocks, int col_blocks, cudaStream_t s) {
+  k_fix_stats<<<tile_blocks, kINT, 0, s>>>(jobs, n);
+  k_fix_mid<<<col_blocks, kMidCols * kMidGroups, 0, s>>>(jobs, n);
+  k_fix_write<<<tile_blocks, kINT, 0, s>>>(jobs, n);
   return 3;
 }
 

@@ -33,14 +33,32 @@ int integral_tile_blocks(int W, int nseg);
 int integral_col_blocks(int W);
 int launch_integral_jobs(const Job *jobs, int njobs, int tile_blocks, int col_blocks, cudaStream_t s);
 
-// Integral planes (64-bit fixed point) of `pairs` float plane pairs (u_p,
-// v_p), each W x H, over the same tiles: u_p scaled by 2^fix_shift(amax[p],
-// nmax[p]) into plane p of dst, v_p by 2^fix_shift(amax[kMaxFields + p],
-// nmax[p]) into plane pairs + p; amax on the device, nmax on the host.
-// scratch: fix_integral_scratch_elems(W, H, pairs) int64. Returns launches.
-size_t fix_integral_scratch_elems(int W, int H, int pairs);
-int launch_fix_integrals(const float *u, const float *v, int W, int H, int pairs, const unsigned *amax,
-                         const float *nmax, unsigned long long *dst, long long *scratch, cudaStream_t s);
+// The backward's integral planes (64-bit fixed point) of one image's `np`
+// float plane pairs (u_p, v_p), each W x H: u_p scaled by 2^fix_shift(amax[p],
+// nmax[p]) and v_p by 2^fix_shift(amax[kMaxFields + p], nmax[p]) (amax on the
+// device), interleaved into pair plane p of dst ((H+1) x (W+1) positions of
+// two int64). Over a batch: the image's first blocks in the tile and column
+// launches are b0_tile and b0_col.
+struct alignas(16) FixJob {
+  const float *u, *v;
+  const unsigned *amax;
+  unsigned long long *dst;
+  long long *scratch;        // fix_integral_scratch_elems(W, H, np, nseg) int64
+  long long scratch_stride;  // per pair
+  int W, H, nseg, seg_rows, np;
+  int b0_tile, b0_col;
+  float nmax[kMaxFields];
+};
+static_assert(sizeof(FixJob) % 16 == 0, "jobs are copied in 16-byte words");
+
+// Row segments of an image in a batch of batch_pairs pairs in all; the scratch,
+// tile blocks and column blocks of its np pairs; the three launches over a
+// batch (returns 3).
+void fix_layout(int W, int H, long long batch_pairs, int &nseg, int &seg_rows);
+size_t fix_integral_scratch_elems(int W, int H, int pairs, int nseg);
+int fix_tile_blocks(int W, int nseg, int pairs);
+int fix_col_blocks(int W, int pairs);
+int launch_fix_integrals(const FixJob *jobs, int n, int tile_blocks, int col_blocks, cudaStream_t s);
 
 // Stage a3 (Eq. 7-8), materialised: integral histogram planes,
 // (H+1) x (W+1) uint32 each (modulo 2^32, zero first row and column), over

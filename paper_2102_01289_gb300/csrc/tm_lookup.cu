@@ -13,29 +13,6 @@
 namespace tmk {
 namespace {
 
-// Window statistics of field f at (x, y): reciprocal area and variance
-// (Eq. 6, Eq. 10). s12: the integral images of q and q^2 interleaved, one
-// 16-byte load per corner; positions fit 32 bits (the image holds fewer than
-// 2^31 pixels). The reciprocal is the fast one (within 1 ulp).
-__device__ __forceinline__ void window_stats(const DevParams &P, int f, int x, int y, int W, int H,
-                                             const longlong2 *__restrict__ s12, int qbits,
-                                             float inv_scale2, float &rarea, float &var) {
-  const unsigned W1 = (unsigned)W + 1u;
-  const int x0 = max(x - P.rx[f], 0), x1 = min(x + P.rx[f], W - 1);
-  const int y0 = max(y - P.ry[f], 0), y1 = min(y + P.ry[f], H - 1);
-  const unsigned rt = (unsigned)y0 * W1, rb = (unsigned)(y1 + 1) * W1;
-  const longlong2 a = __ldg(s12 + (rt + (unsigned)x0)), b = __ldg(s12 + (rt + (unsigned)x1 + 1u));
-  const longlong2 c = __ldg(s12 + (rb + (unsigned)x1 + 1u)), d = __ldg(s12 + (rb + (unsigned)x0));
-  unsigned long long N = (unsigned long long)((unsigned)(x1 - x0 + 1) * (unsigned)(y1 - y0 + 1));
-  long long q1 = (long long)((unsigned long long)c.x - (unsigned long long)d.x - (unsigned long long)b.x +
-                             (unsigned long long)a.x);
-  long long q2 = (long long)((unsigned long long)c.y - (unsigned long long)d.y - (unsigned long long)b.y +
-                             (unsigned long long)a.y);
-  literal_area(P, f, qbits, q1, q2, N);
-  rarea = __fdividef(1.f, (float)N);
-  var = window_variance(q1, q2, N, rarea, inv_scale2);
-}
-
 // Running sums of the fusion of Eq. 3 over the fields.
 struct Fusion {
   float wsum = 0.f, acc = 0.f, mean = 0.f;
@@ -47,8 +24,8 @@ struct Fusion {
 __device__ __forceinline__ void fold_field(const DevParams &P, int f, int x, int y, int W, int H,
                                            unsigned cnt, const longlong2 *__restrict__ s12, int qbits,
                                            float inv_scale2, Fusion &fu, const DebugPlanes &dbg) {
-  float rarea, var;
-  window_stats(P, f, x, y, W, H, s12, qbits, inv_scale2, rarea, var);
+  const WinMoments m = window_moments(P, f, x, y, W, H, s12, qbits, inv_scale2);
+  const float rarea = m.rarea, var = m.var;
   const float Pf = (float)cnt * rarea;                                  // Eq. 1
   const float Lf = fmaf(P.ld_max - P.ld_min, Pf, P.ld_min);             // Eq. 2
   const float Wf = __fdividef(P.alpha[f] * var, var + P.eps[f]);       // Eq. 4
