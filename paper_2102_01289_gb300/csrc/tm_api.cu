@@ -27,7 +27,7 @@ namespace {
 // kernel, not through a host-to-device copy: such a copy waits on the copy
 // engine behind any large upload in flight on another stream (the next image
 // of tm_forward_host_async), which would stall the forward it starts.
-constexpr int kPutJobs = 32;  // 32 x 672-byte jobs fit the 32 KB parameter space
+constexpr int kPutJobs = 32;  // 32 jobs of under 700 bytes fit the 32 KB parameter space
 template <int N>
 struct JobPack {
   Job j[N];
@@ -453,12 +453,13 @@ bool same_images(const std::vector<tm_image> &a, const tm_image *b, int n) {
 
 // Per-image sizes of the forward workspace.
 struct JobLayout {
-  size_t bins, q, s12, segtot, cnt, grp, dcnt, dvar, dw, dlf, dl, total;
+  size_t bins, q, s12, segtot, cnt, grp, mom, dcnt, dvar, dw, dlf, dl, total;
 };
 
 // Workspace of one image. cnt_bytes: the sweep's count planes (0 on the
-// materialised path); grp: per row and 32-column group, the bin range.
-JobLayout job_layout(const tm_params &p, int W, int H, int nseg, size_t cnt_bytes, bool debug) {
+// materialised path); grp: per row and 32-column group, the bin range; mom:
+// the window moments kept for the backward.
+JobLayout job_layout(const tm_params &p, int W, int H, int nseg, size_t cnt_bytes, bool debug, bool mom = false) {
   // nseg: row segments of the integral images (integral_layout)
   JobLayout L{};
   const size_t N = (size_t)W * H;
@@ -472,6 +473,7 @@ JobLayout job_layout(const tm_params &p, int W, int H, int nseg, size_t cnt_byte
   L.segtot = take(8 * integral_scratch_elems(W, H, nseg));
   L.cnt = take(cnt_bytes);
   L.grp = take(2 * (size_t)((W + 31) / 32) * H);
+  if (mom) L.mom = take(8 * N * s);
   if (debug) {
     L.dcnt = take(4 * N * s);
     L.dvar = take(4 * N * s);
@@ -583,6 +585,8 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   }
   c->fwd_valid = false;  // the workspace is rewritten below
   const bool debug = c->debug != 0 && nimg == 1 && !graph;
+  // under TM_OPT_BACKWARD_REUSE the lookup also keeps the window moments
+  const bool keep_mom = c->bwd_reuse != 0 && do_lookup;
   double total_px = 0;
   for (int i = 0; i < nimg; ++i) total_px += (double)in[i].width * in[i].height;
   std::vector<Job> jobs((size_t)nimg);
@@ -613,7 +617,7 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
     integral_layout(W, H, SIZE_MAX, J.nseg, J.seg_rows);
     const size_t cnt_bytes = sweep_count_bytes(P0, J.plan, J.cnt_off);
     J.cnt_wide = J.plan.cnt_wide;
-    lays[(size_t)i] = job_layout(c->p, W, H, J.nseg, cnt_bytes, debug);
+    lays[(size_t)i] = job_layout(c->p, W, H, J.nseg, cnt_bytes, debug, keep_mom);
     offs[(size_t)i] = ws_total;
     ws_total += lays[(size_t)i].total;
     J.b0[kStRange] = b_range;
@@ -666,6 +670,7 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
     J.segtot = reinterpret_cast<long long *>(b + L.segtot);
     J.cnt = reinterpret_cast<unsigned char *>(b + L.cnt);
     J.grp = reinterpret_cast<uint16_t *>(b + L.grp);
+    J.mom = keep_mom ? reinterpret_cast<float2 *>(b + L.mom) : nullptr;
     if (debug) {
       J.dbg.cnt = reinterpret_cast<unsigned *>(b + L.dcnt);
       J.dbg.sigma2 = reinterpret_cast<float *>(b + L.dvar);
@@ -1028,12 +1033,13 @@ tm_status backward_images(tm_ctx *c, int n, const tm_image *in, const tm_image *
   BwdJob *dbj = reinterpret_cast<BwdJob *>(reinterpret_cast<char *>(gsum) + align256(sizeof(double) * kBwdParams));
   FixJob *dfj = reinterpret_cast<FixJob *>(reinterpret_cast<char *>(dbj) + align256(sizeof(BwdJob) * gmax));
   const int nf = c->p.n_fields;
+  mark(c, s, -1);
   for (size_t k = 0; k + 1 < grp.size(); ++k) {
     const int i0 = grp[k], m = grp[k + 1] - i0;
     std::vector<BwdJob> bj((size_t)m);
     std::vector<FixJob> fj((size_t)m);
     char *o = b + head;
-    int pix = 0, tiles = 0, cols = 0;
+    int pix = 0, inb = 0, tiles = 0, cols = 0;
     for (int r = 0; r < m; ++r) {
       const int i = i0 + r;
       const Job &J = jobs[(size_t)i];
@@ -1047,6 +1053,7 @@ tm_status backward_images(tm_ctx *c, int n, const tm_image *in, const tm_image *
       B.st = J.st;
       B.q = J.q;
       B.s12 = reinterpret_cast<const longlong2 *>(J.s1);
+      B.mom = J.mom;
       B.cnt = J.cnt;
       for (int f = 0; f < kMaxFields; ++f) B.cnt_off[f] = J.cnt_off[f];
       B.cnt_wide = J.cnt_wide;
@@ -1058,7 +1065,9 @@ tm_status backward_images(tm_ctx *c, int n, const tm_image *in, const tm_image *
       B.IUV = reinterpret_cast<const longlong2 *>(iuv);
       B.acc = accs + r;
       B.b0 = pix;
+      B.b0_in = inb;
       pix += bwd_pixel_blocks(W, H);
+      inb += bwd_input_blocks(W, H);
       FixJob &F = fj[(size_t)r];
       F = FixJob{};
       F.u = B.U;
@@ -1082,10 +1091,13 @@ tm_status backward_images(tm_ctx *c, int n, const tm_image *in, const tm_image *
     launches += put_words(bj.data(), sizeof(BwdJob) * (size_t)m, dbj, s);
     launches += put_words(fj.data(), sizeof(FixJob) * (size_t)m, dfj, s);
     const DevParams P = dev_params(c->p, jobs[(size_t)i0].qbits);
-    launches += launch_backward(P, dbj, dfj, m, pix, tiles, cols, accs, gsum, k == 0,
-                                k + 2 == grp.size() ? grad_params : nullptr, s);
+    launches += launch_backward_pixel(P, dbj, m, pix, jobs[(size_t)i0].mom != nullptr, accs, gsum, k == 0, s);
+    mark(c, s, ST_BWD_PIXEL);
+    launches += launch_fix_integrals(dfj, m, tiles, cols, s);
+    mark(c, s, ST_BWD_ADJOINT);
+    launches += launch_backward_input(P, dbj, m, inb, gsum, k + 2 == grp.size() ? grad_params : nullptr, s);
+    mark(c, s, ST_BWD_INPUT);
   }
-  mark(c, s, ST_BWD_ADJOINT);
   if ((st = check_launch(c, "backward launch"))) return st;
   c->launches = launches;
   return TM_OK;
@@ -1626,6 +1638,10 @@ tm_status tm_set_option(tm_ctx *c, int32_t key, int64_t value) {
     return TM_OK;
   }
   if (key == TM_OPT_BACKWARD_REUSE) {
+    if (c->bwd_reuse != (value ? 1 : 0)) {
+      drop_graph(c);  // the cached batch graph keeps (or not) the window moments
+      c->fwd_valid = false;
+    }
     c->bwd_reuse = value ? 1 : 0;
     return TM_OK;
   }

@@ -34,24 +34,24 @@
 namespace tmk {
 namespace {
 
-// Per-pixel launches: 32 x 8 threads, each thread kRowsPer rows 8 apart, so
-// a block covers a 32 x 32 tile (the block's reductions are paid once per
-// four pixels of a thread).
+// Per-pixel launches: 32 x 8 threads, each thread kRowsPix (kRowsIn) rows 8
+// apart, so a block covers a 32 x (8 kRowsPix) tile (the block's reductions
+// are paid once per kRowsPix pixels of a thread).
 constexpr int kBT = 256;
 constexpr int kWarpsB = kBT / 32;
-constexpr int kRowsPer = 4;
-constexpr int kTileH = 8 * kRowsPer;
+constexpr int kRowsPix = 4, kRowsIn = 4;
+constexpr int kMinBlocksPix = 4, kMinBlocksIn = 5;
 
 __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-__device__ __forceinline__ int find_bwd(const BwdJob *jobs, int n, int blk) {
+__device__ __forceinline__ int find_bwd(const BwdJob *jobs, int n, bool input, int blk) {
   int lo = 0, hi = n - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (jobs[mid].b0 <= blk) lo = mid; else hi = mid - 1;
+    if ((input ? jobs[mid].b0_in : jobs[mid].b0) <= blk) lo = mid; else hi = mid - 1;
   }
   return lo;
 }
@@ -71,17 +71,18 @@ __global__ void k_bwd_init(BwdAcc *accs, int n, double *gsum, int first) {
 // direct gradients of the colour restoration, parameter partial sums and the
 // largest |u_f|, |v_f| (for the fixed-point scales). NF = number of fields
 // (so every per-field array lives in registers).
-template <int NF>
-__global__ void __launch_bounds__(kBT) k_bwd_pixel(DevParams P, const BwdJob *__restrict__ jobs, int njobs,
+// MOM: the window variances and means come from the forward's planes.
+template <int NF, bool MOM>
+__global__ void __launch_bounds__(kBT, kMinBlocksPix) k_bwd_pixel(DevParams P, const BwdJob *__restrict__ jobs, int njobs,
                                                    double *__restrict__ gsum) {
   constexpr int kA = 3 + 2 * NF;  // [ld_min, ld_max, sat, eps[NF], alpha[NF]], the layout of gsum
   __shared__ float sh[kA][kWarpsB];
   __shared__ unsigned shm[2 * NF][kWarpsB];
-  const BwdJob &J = jobs[find_bwd(jobs, njobs, blockIdx.x)];
+  const BwdJob &J = jobs[find_bwd(jobs, njobs, false, blockIdx.x)];
   const int W = J.in.W, H = J.in.H;
   const int lb = blockIdx.x - J.b0, bx = (W + 31) / 32;
   const int x = (lb % bx) * 32 + (threadIdx.x & 31);
-  const int ybase = (lb / bx) * kTileH + (threadIdx.x >> 5);
+  const int ybase = (lb / bx) * (8 * kRowsPix) + (threadIdx.x >> 5);
   const size_t N = (size_t)W * H;
   const float inv_scale = ldexpf(1.f, -J.qbits);
   const float inv_scale2 = inv_scale * inv_scale;
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(kBT) k_bwd_pixel(DevParams P, const BwdJob *__
   for (int k = 0; k < 2 * NF; ++k) amax[k] = 0u;
   if (x < W) {
 #pragma unroll 1
-    for (int r = 0; r < kRowsPer; ++r) {
+    for (int r = 0; r < kRowsPix; ++r) {
       const int y = ybase + 8 * r;
       if (y >= H) break;
       const unsigned pix = (unsigned)y * (unsigned)W + (unsigned)x;
@@ -104,14 +105,21 @@ __global__ void __launch_bounds__(kBT) k_bwd_pixel(DevParams P, const BwdJob *__
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         const unsigned cnt = load_count(J, f, pix);
-        const WinMoments m = window_moments(P, f, x, y, W, H, J.s12, J.qbits, inv_scale2);
-        rarea[f] = m.rarea;
-        var[f] = m.var;
-        mu[f] = __ll2float_rn(m.q1) * m.rarea * inv_scale + 0.5f;  // mean of lhat
+        if (MOM) {
+          const float2 vm = __ldg(J.mom + f * N + pix);
+          var[f] = vm.x;
+          mu[f] = vm.y;
+          rarea[f] = __fdividef(1.f, window_area(P, f, x, y, W, H));
+        } else {
+          const WinMoments m = window_moments(P, f, x, y, W, H, J.s12, J.qbits, inv_scale2);
+          rarea[f] = m.rarea;
+          var[f] = m.var;
+          mu[f] = window_mean(m.q1, m.rarea, inv_scale);
+        }
         // Eq. 1, 2, 4 and the sums of Eq. 3, as in the forward
-        Pf[f] = (float)cnt * m.rarea;
+        Pf[f] = (float)cnt * rarea[f];
         lf[f] = fmaf(span, Pf[f], P.ld_min);
-        wv[f] = __fdividef(P.alpha[f] * m.var, m.var + P.eps[f]);
+        wv[f] = __fdividef(P.alpha[f] * var[f], var[f] + P.eps[f]);
         wsum += wv[f];
         accL = fmaf(wv[f], lf[f], accL);
         meanL += lf[f];
@@ -205,10 +213,10 @@ __global__ void __launch_bounds__(kBT) k_bwd_pixel(DevParams P, const BwdJob *__
 // Per pixel: the adjoint of the window variances, through the normalised log,
 // into the luminance and Eq. 11; range-term partial sums.
 template <int NF>
-__global__ void __launch_bounds__(kBT) k_bwd_input(DevParams P, const BwdJob *__restrict__ jobs, int njobs) {
+__global__ void __launch_bounds__(kBT, kMinBlocksIn) k_bwd_input(DevParams P, const BwdJob *__restrict__ jobs, int njobs) {
   __shared__ float sh[2][kWarpsB];
   __shared__ float scale[2 * NF][2];  // 2^-shift of each fixed-point plane, as two factors
-  const BwdJob &J = jobs[find_bwd(jobs, njobs, blockIdx.x)];
+  const BwdJob &J = jobs[find_bwd(jobs, njobs, true, blockIdx.x)];
   const int W = J.in.W, H = J.in.H;
   if (threadIdx.x < 2 * NF) {
     const int k = threadIdx.x, f = k < NF ? k : k - NF;
@@ -220,9 +228,9 @@ __global__ void __launch_bounds__(kBT) k_bwd_input(DevParams P, const BwdJob *__
     scale[k][1] = ldexpf(1.f, h - sh_);
   }
   __syncthreads();
-  const int lb = blockIdx.x - J.b0, bx = (W + 31) / 32;
+  const int lb = blockIdx.x - J.b0_in, bx = (W + 31) / 32;
   const int x = (lb % bx) * 32 + (threadIdx.x & 31);
-  const int ybase = (lb / bx) * kTileH + (threadIdx.x >> 5);
+  const int ybase = (lb / bx) * (8 * kRowsIn) + (threadIdx.x >> 5);
   // D = ln imax - ln imin = ln 2 x 2^Q / log2_scale (log2_scale = 2^Q / log2(imax / imin))
   const float l2s = J.st->log2_scale;
   const float D = J.st->imax > J.st->imin && l2s > 0.f ? 0.69314718f * ldexpf(1.f, J.qbits) / l2s : 0.f;
@@ -233,7 +241,7 @@ __global__ void __launch_bounds__(kBT) k_bwd_input(DevParams P, const BwdJob *__
   float acc_lmin = 0.f, acc_lmax = 0.f;
   if (x < W) {
 #pragma unroll 1
-    for (int r = 0; r < kRowsPer; ++r) {
+    for (int r = 0; r < kRowsIn; ++r) {
       const int y = ybase + 8 * r;
       if (y >= H) break;
       const unsigned pix = (unsigned)y * (unsigned)W + (unsigned)x;
@@ -256,8 +264,8 @@ __global__ void __launch_bounds__(kBT) k_bwd_input(DevParams P, const BwdJob *__
                                            (unsigned long long)b.x + (unsigned long long)a.x);
           const long long bv = (long long)((unsigned long long)c.y - (unsigned long long)d.y -
                                            (unsigned long long)b.y + (unsigned long long)a.y);
-          const float fu = __ll2float_rn(bu) * scale[f][0] * scale[f][1];
-          const float fv = __ll2float_rn(bv) * scale[NF + f][0] * scale[NF + f][1];
+          const float fu = i64_to_float(bu) * scale[f][0] * scale[f][1];
+          const float fv = i64_to_float(bv) * scale[NF + f][0] * scale[NF + f][1];
           gl += lh * fu - fv;
         }
         const float i = fmaxf(raw, kLumFloor);
@@ -326,27 +334,36 @@ __global__ void k_bwd_finish(DevParams P, const BwdJob *__restrict__ jobs, int n
 
 }  // namespace
 
-int bwd_pixel_blocks(int W, int H) { return ((W + 31) / 32) * ((H + kTileH - 1) / kTileH); }
+int bwd_pixel_blocks(int W, int H) { return ((W + 31) / 32) * ((H + 8 * kRowsPix - 1) / (8 * kRowsPix)); }
 
-int launch_backward(const DevParams &P, const BwdJob *jobs, const FixJob *fix, int n, int pix_blocks,
-                    int tile_blocks, int col_blocks, BwdAcc *accs, double *gsum, bool first,
-                    float *grad_params, cudaStream_t s) {
+int bwd_input_blocks(int W, int H) { return ((W + 31) / 32) * ((H + 8 * kRowsIn - 1) / (8 * kRowsIn)); }
+
+int launch_backward_pixel(const DevParams &P, const BwdJob *jobs, int n, int pix_blocks, bool mom, BwdAcc *accs,
+                          double *gsum, bool first, cudaStream_t s) {
   k_bwd_init<<<1, 256, 0, s>>>(accs, n, gsum, first ? 1 : 0);
   switch (P.n_fields) {
-#define TM_BWD_PIXEL(nf) case nf: k_bwd_pixel<nf><<<pix_blocks, kBT, 0, s>>>(P, jobs, n, gsum); break;
+#define TM_BWD_PIXEL(nf)                                                                      \
+  case nf:                                                                                   \
+    if (mom) k_bwd_pixel<nf, true><<<pix_blocks, kBT, 0, s>>>(P, jobs, n, gsum);             \
+    else k_bwd_pixel<nf, false><<<pix_blocks, kBT, 0, s>>>(P, jobs, n, gsum);                \
+    break;
     TM_BWD_PIXEL(1) TM_BWD_PIXEL(2) TM_BWD_PIXEL(3) TM_BWD_PIXEL(4) TM_BWD_PIXEL(5) TM_BWD_PIXEL(6)
-    TM_BWD_PIXEL(7) default: k_bwd_pixel<8><<<pix_blocks, kBT, 0, s>>>(P, jobs, n, gsum); break;
+    TM_BWD_PIXEL(7) TM_BWD_PIXEL(8)
 #undef TM_BWD_PIXEL
   }
-  const int nc = launch_fix_integrals(fix, n, tile_blocks, col_blocks, s);
+  return 2;
+}
+
+int launch_backward_input(const DevParams &P, const BwdJob *jobs, int n, int in_blocks, const double *gsum,
+                          float *grad_params, cudaStream_t s) {
   switch (P.n_fields) {
-#define TM_BWD_INPUT(nf) case nf: k_bwd_input<nf><<<pix_blocks, kBT, 0, s>>>(P, jobs, n); break;
+#define TM_BWD_INPUT(nf) case nf: k_bwd_input<nf><<<in_blocks, kBT, 0, s>>>(P, jobs, n); break;
     TM_BWD_INPUT(1) TM_BWD_INPUT(2) TM_BWD_INPUT(3) TM_BWD_INPUT(4) TM_BWD_INPUT(5) TM_BWD_INPUT(6)
-    TM_BWD_INPUT(7) default: k_bwd_input<8><<<pix_blocks, kBT, 0, s>>>(P, jobs, n); break;
+    TM_BWD_INPUT(7) default: k_bwd_input<8><<<in_blocks, kBT, 0, s>>>(P, jobs, n); break;
 #undef TM_BWD_INPUT
   }
   k_bwd_finish<<<1, 32, 0, s>>>(P, jobs, n, gsum, grad_params);
-  return 4 + nc;
+  return 2;
 }
 
 }  // namespace tmk

@@ -26,6 +26,8 @@ struct alignas(16) BwdJob {
   const Stats *st;              // the range state of the forward
   const int32_t *q;             // H*W quantised normalised log
   const longlong2 *s12;         // (H+1)*(W+1) integral images of q and q^2, interleaved
+  const float2 *mom;            // the forward's window (variance, mean of lhat) per field, or
+                                //   null: recomputed from s12
   const unsigned char *cnt;     // Eq. 1 numerators: plane f at cnt + cnt_off[f]
   long long cnt_off[kMaxFields];
   int cnt_wide;                 // bit f: plane f is uint32 (else uint16)
@@ -35,21 +37,26 @@ struct alignas(16) BwdJob {
   const longlong2 *IUV;         // s pair planes of (H+1)*(W+1) positions: the fixed-point
                                 //   integrals of u_f and v_f, interleaved
   BwdAcc *acc;
-  int b0;                       // first block of this image in the per-pixel launches
-  int pad_;
+  int b0, b0_in;                // first block of this image in the two per-pixel launches
 };
 static_assert(sizeof(BwdJob) % 16 == 0, "jobs are copied in 16-byte words");
 
-// Blocks of the per-pixel launches for one image.
+// Blocks of the two per-pixel launches for one image.
 int bwd_pixel_blocks(int W, int H);
+int bwd_input_blocks(int W, int H);
 
-// The adjoint of a batch of images given their forward intermediates:
-// `jobs` / `fix` (device, n each; the FixJob of image i reads U / V of job i
-// and writes its IUV), `accs` (device, n), `gsum` (device, kBwdParams).
-// first: clear gsum; grad_params (device float[3 + 2s]) or null: written
-// from gsum at the end. Returns the number of launches.
-int launch_backward(const DevParams &P, const BwdJob *jobs, const FixJob *fix, int n, int pix_blocks,
-                    int tile_blocks, int col_blocks, BwdAcc *accs, double *gsum, bool first,
-                    float *grad_params, cudaStream_t s);
+// The adjoint of a batch of images given their forward intermediates, in
+// three steps on one stream: launch_backward_pixel (per pixel: u_f, v_f, the
+// direct gradients, the parameter sums), launch_fix_integrals over `fix` (the
+// FixJob of image i reads U / V of job i and writes its IUV), then
+// launch_backward_input (the box sums back into the input, the range terms,
+// the parameter gradients). mom: every job's BwdJob::mom is set (else none
+// is). jobs / fix / accs: device arrays of n; gsum:
+// device, kBwdParams. first: clear gsum; grad_params (device float[3 + 2s])
+// or null: written from gsum at the end. Each returns its launches.
+int launch_backward_pixel(const DevParams &P, const BwdJob *jobs, int n, int pix_blocks, bool mom, BwdAcc *accs,
+                          double *gsum, bool first, cudaStream_t s);
+int launch_backward_input(const DevParams &P, const BwdJob *jobs, int n, int in_blocks, const double *gsum,
+                          float *grad_params, cudaStream_t s);
 
 }  // namespace tmk

@@ -107,6 +107,8 @@ struct alignas(16) Job {
   long long cnt_off[kMaxFields];
   int cnt_wide;
   uint16_t *grp;            // per row and 32-column group: smallest | largest << 8 bin
+  float2 *mom;              // kept for the backward (else null): (variance, mean of lhat)
+                            //   of field f's windows, plane f of H*W at mom + f*H*W
   DebugPlanes dbg;
   int qbits;
   int s_pair;               // 1: s1 and s2 interleaved (the forward's workspace)
@@ -273,6 +275,47 @@ __device__ __forceinline__ Win window_of(const DevParams &P, int f, int x, int y
   return w;
 }
 
+// Integer <-> float conversions from 32-bit integer and FP32 operations. The
+// 64-bit conversion instructions execute on the FP64 pipe, a small fraction
+// of the FP32 rate on this part (about two results per clock per SM), and
+// bounded the per-pixel kernels that used them.
+//
+// uint32 -> float, correctly rounded: each 16-bit half h is the exact float
+// (2^23 + h) - 2^23, and one FMA joins them with a single rounding.
+__device__ __forceinline__ float u32_to_float(unsigned x) {
+  const float h = __uint_as_float(0x4B000000u | (x >> 16)) - 8388608.f;
+  const float l = __uint_as_float(0x4B000000u | (x & 0xffffu)) - 8388608.f;
+  return __fmaf_rn(h, 65536.f, l);
+}
+
+// uint64 -> float within one ulp (exact below 2^24, correctly rounded below
+// 2^32): the 32-bit halves converted as above and joined by one FMA; the low
+// half's rounding error is at most a quarter ulp of the result when the high
+// half is nonzero.
+__device__ __forceinline__ float u64_to_float(unsigned long long a) {
+  const unsigned hi = (unsigned)(a >> 32);
+  const float lo = u32_to_float((unsigned)a);
+  return hi ? __fmaf_rn(u32_to_float(hi), 4294967296.f, lo) : lo;
+}
+
+// int64 -> float within one ulp (the magnitude as above, then the sign).
+__device__ __forceinline__ float i64_to_float(long long s) {
+  const float f = u64_to_float(s < 0 ? 0ull - (unsigned long long)s : (unsigned long long)s);
+  return s < 0 ? -f : f;
+}
+
+// float -> int64, rounded to nearest with ties to even, for |y| < 2^62: at or
+// above 2^23 a float is an integer (its significand shifted up); below,
+// 2^23 + |y| rounds |y| to an integer in the last place.
+__device__ __forceinline__ long long float_to_i64_rn(float y) {
+  const unsigned bits = __float_as_uint(y);
+  const int ex = (int)((bits >> 23) & 0xffu);
+  const unsigned long long mag =
+      ex >= 150 ? (unsigned long long)((bits & 0x7fffffu) | 0x800000u) << min(ex - 150, 40)
+                : (unsigned long long)(__float_as_uint(fabsf(y) + 8388608.f) - 0x4B000000u);
+  return (bits >> 31) ? -(long long)mag : (long long)mag;
+}
+
 // Window variance of q from its exact window sums s1 = sum q and s2 = sum q^2
 // (modulo 2^64) over N pixels. With m the integer nearest a float estimate of
 // the mean (within a few units of it) and d = s1 - m N,
@@ -291,6 +334,22 @@ __device__ __forceinline__ float window_variance(long long s1, long long s2, uns
   const float df = __ll2float_rn(d);
   const float v = fmaf(-df * rN, df, __ull2float_rn(T)) * rN;
   return fmaxf(v, 0.f) * inv_scale2;
+}
+
+// Area of field f's window at (x, y) as a float: clipped to the image, or
+// under TM_FLAG_AREA_LITERAL the unclipped (2 rx + 1)(2 ry + 1).
+__device__ __forceinline__ float window_area(const DevParams &P, int f, int x, int y, int W, int H) {
+  if (P.flags & kFlagAreaLit) return (float)((unsigned)(2 * P.rx[f] + 1) * (unsigned)(2 * P.ry[f] + 1));
+  const int x0 = max(x - P.rx[f], 0), x1 = min(x + P.rx[f], W - 1);
+  const int y0 = max(y - P.ry[f], 0), y1 = min(y + P.ry[f], H - 1);
+  return (float)((unsigned)(x1 - x0 + 1) * (unsigned)(y1 - y0 + 1));
+}
+
+// Window mean of lhat from the window sum of q (q = 2^Q lhat - 2^(Q-1), up
+// to rounding), with explicit roundings so that every kernel gets the same
+// bits.
+__device__ __forceinline__ float window_mean(long long q1, float rarea, float inv_scale) {
+  return __fmaf_rn(__fmul_rn(__ll2float_rn(q1), rarea), inv_scale, 0.5f);
 }
 
 // Window moments of field f at (x, y) from the interleaved integral images
@@ -318,7 +377,7 @@ __device__ __forceinline__ WinMoments window_moments(const DevParams &P, int f, 
                              (unsigned long long)a.y);
   literal_area(P, f, qbits, q1, q2, N);
   WinMoments m;
-  m.rarea = __fdividef(1.f, (float)N);
+  m.rarea = __fdividef(1.f, (float)(unsigned)N);  // N <= 65535^2 < 2^32
   m.var = window_variance(q1, q2, N, m.rarea, inv_scale2);
   m.q1 = q1;
   return m;

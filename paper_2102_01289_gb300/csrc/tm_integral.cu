@@ -75,21 +75,31 @@ struct QSource {
 };
 
 // Values of the planes: two float planes in 64-bit fixed point, u x 2^sa and
-// v x 2^sb rounded to nearest.
+// v x 2^sb rounded to nearest. Each power of two is applied as two float
+// factors 2^h and 2^(s - h), h = s / 2 (s in [-67, 209], so both are normal):
+// for s >= 0 no product leaves the normal range; for s < 0 only values that
+// end below 2^-126 can round twice, and those convert to 0 either way, so
+// the integers equal those of a single scaling.
 struct FixSource {
   using Raw = float2;
   const float *u, *v;
-  int W, sa, sb;
+  int W;
+  float a_hi, a_lo, b_hi, b_lo;
   __device__ __forceinline__ Raw load(int r, int c) const {
     const long long o = (long long)r * W + c;
     return make_float2(__ldg(u + o), __ldg(v + o));
   }
   __device__ __forceinline__ Raw zero() const { return make_float2(0.f, 0.f); }
   __device__ __forceinline__ void values(Raw x, long long &a, long long &b) const {
-    a = __float2ll_rn(ldexpf(x.x, sa));
-    b = __float2ll_rn(ldexpf(x.y, sb));
+    a = float_to_i64_rn(x.x * a_hi * a_lo);
+    b = float_to_i64_rn(x.y * b_hi * b_lo);
   }
 };
+
+__device__ __forceinline__ FixSource fix_source_of(const float *u, const float *v, int W, int sa, int sb) {
+  return FixSource{u, v, W, ldexpf(1.f, sa / 2), ldexpf(1.f, sa - sa / 2), ldexpf(1.f, sb / 2),
+                   ldexpf(1.f, sb - sb / 2)};
+}
 
 // Values of the planes: indicators of a bin map for thresholds k0 and k0 + 1,
 // [b < k] (cumulative) or [b == k]; raw -1 stands for no pixel.
@@ -174,7 +184,9 @@ __device__ __forceinline__ void chunk_row_prefix(const Src &src, const typename 
 // row prefixes at column c is the prefix, up to c, of the plain column sums
 // (both are the sum of the values above and left of c in the tile), so the
 // rows are only summed down each column and across each row (warp sums, no
-// barrier per row); one block scan over the columns ends the tile.
+// barrier per row); one block scan over the columns ends the tile. The row
+// and tile totals of the last chunk column are read by no later launch (they
+// only offset the chunks to their right), so its tiles skip them.
 constexpr int kRowGroup = 16;  // rows whose warp partial sums are combined together
 struct StatsSmem {
   long long col[2][kIC / 8 * 9];            // the tile's column sums, padded for the scan
@@ -187,6 +199,7 @@ __device__ __forceinline__ void int_stats_tile(const IntTask &X, const Src &src,
   const int W = X.W, H = X.H;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int R0 = seg * X.seg_rows, R1 = min(R0 + X.seg_rows, H), C0 = k * kIC, nc = min(kIC, W - C0);
+  const bool totals = k + 1 < X.nchunk;  // block-uniform
   long long c1[kItems], c2[kItems];  // sums down the thread's strided columns threadIdx.x + m kINT
 #pragma unroll
   for (int m = 0; m < kItems; ++m) c1[m] = c2[m] = 0;
@@ -205,6 +218,7 @@ __device__ __forceinline__ void int_stats_tile(const IntTask &X, const Src &src,
       s2 += x2;
       cur[m] = nxt[m];
     }
+    if (!totals) continue;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       s1 += __shfl_xor_sync(0xffffffffu, s1, o);
@@ -253,7 +267,7 @@ __device__ __forceinline__ void int_stats_tile(const IntTask &X, const Src &src,
       X.colsum[((long long)X.nseg + seg) * W + c] = e2 + l2[i];
     }
   }
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && totals) {
     X.tiletot[(long long)seg * X.nchunk + k] = t1;
     X.tiletot[((long long)X.nseg + seg) * X.nchunk + k] = t2;
   }
@@ -453,17 +467,134 @@ __device__ __forceinline__ IntTask fix_task(const FixJob &F, int p) {
 
 __device__ __forceinline__ FixSource fix_source(const FixJob &F, int p) {
   const long long N = (long long)F.W * F.H;
-  return FixSource{F.u + p * N, F.v + p * N, F.W, fix_shift(__ldg(F.amax + p), F.nmax[p]),
-                   fix_shift(__ldg(F.amax + kMaxFields + p), F.nmax[p])};
+  return fix_source_of(F.u + p * N, F.v + p * N, F.W, fix_shift(__ldg(F.amax + p), F.nmax[p]),
+                       fix_shift(__ldg(F.amax + kMaxFields + p), F.nmax[p]));
 }
 
-__global__ void __launch_bounds__(kINT, 4) k_fix_stats(const FixJob *__restrict__ jobs, int n) {
-  __shared__ StatsSmem sm;
+// Launch 1 for the fixed-point planes (the outputs of int_stats_tile): each
+// thread owns four consecutive columns of the chunk and keeps kFSRows rows of
+// loads in flight, 16 bytes at a time where the rows are 16-byte aligned;
+// plain column sums down the segment, then one block scan over the columns.
+constexpr int kFS = 256;    // threads of a fixed-point stats block
+constexpr int kFSRows = 4;  // rows in flight per thread
+static_assert(kFS * 4 == kIC, "a fixed-point stats block spans one chunk");
+
+__device__ __forceinline__ void fix_load4(const FixSource &src, int r, int c, bool vec, float4 &a, float4 &b) {
+  const int W = src.W;
+  const size_t o = (size_t)r * W + c;
+  if (vec && c + 3 < W) {
+    a = __ldg(reinterpret_cast<const float4 *>(src.u + o));
+    b = __ldg(reinterpret_cast<const float4 *>(src.v + o));
+  } else {
+    a.x = c < W ? __ldg(src.u + o) : 0.f;
+    a.y = c + 1 < W ? __ldg(src.u + o + 1) : 0.f;
+    a.z = c + 2 < W ? __ldg(src.u + o + 2) : 0.f;
+    a.w = c + 3 < W ? __ldg(src.u + o + 3) : 0.f;
+    b.x = c < W ? __ldg(src.v + o) : 0.f;
+    b.y = c + 1 < W ? __ldg(src.v + o + 1) : 0.f;
+    b.z = c + 2 < W ? __ldg(src.v + o + 2) : 0.f;
+    b.w = c + 3 < W ? __ldg(src.v + o + 3) : 0.f;
+  }
+}
+
+__global__ void __launch_bounds__(kFS, 3) k_fix_stats(const FixJob *__restrict__ jobs, int n) {
+  __shared__ long long rowp[kRowGroup][2][kFS / 32];
+  __shared__ long long wt[2][kFS / 32];
   const FixJob &F = jobs[find_fix(jobs, n, true, blockIdx.x)];
   const int per = F.nseg * ((F.W + kIC - 1) / kIC), lb = blockIdx.x - F.b0_tile;
   const int p = lb / per, t = lb - p * per;
   const IntTask X = fix_task(F, p);
-  int_stats_tile(X, fix_source(F, p), t / X.nchunk, t % X.nchunk, sm);
+  const FixSource src = fix_source(F, p);
+  const int W = X.W, H = X.H;
+  const int seg = t / X.nchunk, k = t % X.nchunk;
+  const int R0 = seg * X.seg_rows, R1 = min(R0 + X.seg_rows, H);
+  const int c = k * kIC + 4 * (int)threadIdx.x;
+  const bool vec = (W & 3) == 0;         // rows start 16-byte aligned (the planes are 256-byte aligned)
+  const bool totals = k + 1 < X.nchunk;  // block-uniform; see int_stats_tile
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  long long cu[4] = {0, 0, 0, 0}, cv[4] = {0, 0, 0, 0};
+  for (int r0 = R0; r0 < R1; r0 += kFSRows) {
+    float4 a[kFSRows], b[kFSRows];
+#pragma unroll
+    for (int i = 0; i < kFSRows; ++i) {
+      if (r0 + i < R1) {
+        fix_load4(src, r0 + i, c, vec, a[i], b[i]);
+      } else {
+        a[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        b[i] = a[i];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kFSRows; ++i) {
+      const float ua[4] = {a[i].x, a[i].y, a[i].z, a[i].w}, va[4] = {b[i].x, b[i].y, b[i].z, b[i].w};
+      long long su = 0, sv = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        long long x1, x2;
+        src.values(make_float2(ua[j], va[j]), x1, x2);
+        cu[j] += x1;
+        cv[j] += x2;
+        su += x1;
+        sv += x2;
+      }
+      const int r = r0 + i;
+      if (!totals || r >= R1) continue;  // block-uniform
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        su += __shfl_xor_sync(0xffffffffu, su, o);
+        sv += __shfl_xor_sync(0xffffffffu, sv, o);
+      }
+      const int g = (r - R0) % kRowGroup;
+      if (lane == 0) {
+        rowp[g][0][wid] = su;
+        rowp[g][1][wid] = sv;
+      }
+      if (g == kRowGroup - 1 || r == R1 - 1) {  // the group's row totals
+        __syncthreads();
+        if ((int)threadIdx.x <= g) {
+          const int rr = r - g + (int)threadIdx.x;
+          long long t1 = 0, t2 = 0;
+#pragma unroll
+          for (int w = 0; w < kFS / 32; ++w) t1 += rowp[threadIdx.x][0][w], t2 += rowp[threadIdx.x][1][w];
+          X.rowsum[(long long)rr * X.nchunk + k] = t1;
+          X.rowsum[((long long)H + rr) * X.nchunk + k] = t2;
+        }
+        __syncthreads();  // rowp is rewritten by the next group
+      }
+    }
+  }
+  // chunk-local column prefixes of the column sums: the thread's four
+  // columns, then an exclusive block scan over the threads
+#pragma unroll
+  for (int j = 1; j < 4; ++j) {
+    cu[j] += cu[j - 1];
+    cv[j] += cv[j - 1];
+  }
+  long long x1 = cu[3], x2 = cv[3];
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y1 = __shfl_up_sync(0xffffffffu, x1, o), y2 = __shfl_up_sync(0xffffffffu, x2, o);
+    if (lane >= o) x1 += y1, x2 += y2;
+  }
+  if (lane == 31) wt[0][wid] = x1, wt[1][wid] = x2;
+  __syncthreads();
+  long long e1 = x1 - cu[3], e2 = x2 - cv[3], t1 = 0, t2 = 0;
+#pragma unroll
+  for (int w = 0; w < kFS / 32; ++w) {
+    if (w < wid) e1 += wt[0][w], e2 += wt[1][w];
+    t1 += wt[0][w];
+    t2 += wt[1][w];
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (c + j < W) {
+      X.colsum[(long long)seg * W + c + j] = e1 + cu[j];
+      X.colsum[((long long)X.nseg + seg) * W + c + j] = e2 + cv[j];
+    }
+  if (threadIdx.x == 0 && totals) {
+    X.tiletot[(long long)seg * X.nchunk + k] = t1;
+    X.tiletot[((long long)X.nseg + seg) * X.nchunk + k] = t2;
+  }
 }
 
 __global__ void __launch_bounds__(kMidCols * kMidGroups) k_fix_mid(const FixJob *__restrict__ jobs, int n) {
@@ -572,7 +703,7 @@ int fix_tile_blocks(int W, int nseg, int pairs) { return pairs * integral_tile_b
 int fix_col_blocks(int W, int pairs) { return pairs * integral_col_blocks(W); }
 
 int launch_fix_integrals(const FixJob *jobs, int n, int tile_blocks, int col_blocks, cudaStream_t s) {
-  k_fix_stats<<<tile_blocks, kINT, 0, s>>>(jobs, n);
+  k_fix_stats<<<tile_blocks, kFS, 0, s>>>(jobs, n);
   k_fix_mid<<<col_blocks, kMidCols * kMidGroups, 0, s>>>(jobs, n);
   k_fix_write<<<tile_blocks, kINT, 0, s>>>(jobs, n);
   return 3;

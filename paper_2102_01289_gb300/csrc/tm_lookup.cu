@@ -21,11 +21,16 @@ struct Fusion {
 // Field f of pixel (x, y) with Eq. 1 numerator cnt: Eq. 2 and Eq. 4 folded
 // into the Eq. 3 sums (the same arithmetic as fuse_fields, one field at a
 // time, so no per-field state is kept).
+// mom (or null): receives the window's variance and mean of lhat for the
+// backward (inv_scale = 2^-Q).
 __device__ __forceinline__ void fold_field(const DevParams &P, int f, int x, int y, int W, int H,
                                            unsigned cnt, const longlong2 *__restrict__ s12, int qbits,
-                                           float inv_scale2, Fusion &fu, const DebugPlanes &dbg) {
+                                           float inv_scale2, Fusion &fu, const DebugPlanes &dbg,
+                                           float2 *mom = nullptr, float inv_scale = 0.f) {
   const WinMoments m = window_moments(P, f, x, y, W, H, s12, qbits, inv_scale2);
   const float rarea = m.rarea, var = m.var;
+  if (mom)
+    mom[(size_t)f * W * H + (size_t)y * W + x] = make_float2(var, window_mean(m.q1, rarea, inv_scale));
   const float Pf = (float)cnt * rarea;                                  // Eq. 1
   const float Lf = fmaf(P.ld_max - P.ld_min, Pf, P.ld_min);             // Eq. 2
   const float Wf = __fdividef(P.alpha[f] * var, var + P.eps[f]);       // Eq. 4
@@ -103,13 +108,14 @@ __global__ void __launch_bounds__(256, 8) k_lookup_counts(DevParams P, const Job
   const int y = (lb / bx) * 8 + (threadIdx.x >> 5);
   if (x >= W || y >= H) return;
   const long long pix = (long long)y * W + x;
-  const float inv_scale2 = ldexpf(1.f, -2 * J.qbits);  // Q is per image
+  const float inv_scale = ldexpf(1.f, -J.qbits);  // Q is per image
+  const float inv_scale2 = inv_scale * inv_scale;
   Fusion fu;
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
     const unsigned cnt = load_count(J, f, pix);
     fold_field(P, f, x, y, W, H, cnt, reinterpret_cast<const longlong2 *>(J.s1), J.qbits, inv_scale2, fu,
-               J.dbg);
+               J.dbg, J.mom, inv_scale);
   }
   finish_pixel(J.in, J.out, P, x, y, fu, J.dbg);
 }

@@ -47,9 +47,10 @@ def _gpu_backward(img, gp, gout):
     return gin.cpu().numpy().astype(np.float64), gpar.cpu().numpy().astype(np.float64)
 
 
-# The last case (added below) is 300 x 320 with the C5 radii 8/32/128: r = 128
-# windows lie wholly inside the image and the adjoint's fixed-point integral
-# pass spans several tiles.
+# The last two cases (added below): 300 x 320 with the radii 8/32/128 (r = 128
+# windows lie wholly inside the image; the fixed-point integral pass spans
+# several row segments), and 40 x 2200, whose rows span three 1024-column
+# chunks of the integral tiles (row and tile totals carried across chunks).
 CASES = [
     (40, 56, 16, [2, 7, 30]),
     (33, 47, 32, [(3, 1), 9]),
@@ -59,7 +60,7 @@ CASES = [
 
 
 @pytest.mark.parametrize("flags", [0, 3])  # defaults; inclusive CDF + Algorithm 1's area
-@pytest.mark.parametrize("H,W,n,radii", CASES + [(300, 320, 32, [8, 32, 128])])
+@pytest.mark.parametrize("H,W,n,radii", CASES + [(300, 320, 32, [8, 32, 128]), (40, 2200, 16, [3, 12, 40])])
 def test_backward_matches_oracle_adjoint(orc, H, W, n, radii, flags):
     rng = np.random.default_rng(H + W)
     img = synth.wdr_image(H, W, seed=H * 7 + W)
