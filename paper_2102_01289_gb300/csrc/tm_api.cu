@@ -42,38 +42,6 @@ __global__ void k_put_jobs(const __grid_constant__ JobPack<N> p, Job *dst, int n
 }
 static_assert(sizeof(Job) % 4 == 0, "jobs are copied as words");
 
-// Other descriptor arrays, the same way: up to 24 KB of words per launch.
-constexpr int kPutWordsSmall = 256, kPutWordsLarge = 6144;
-template <int N>
-struct WordPack {
-  unsigned w[N];
-};
-template <int N>
-__global__ void k_put_words(const __grid_constant__ WordPack<N> p, unsigned *dst, int n) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = p.w[i];
-}
-
-// Writes `bytes` (a multiple of 4) from h to device memory d on stream s;
-// returns the launches made.
-int put_words(const void *h, size_t bytes, void *d, cudaStream_t s) {
-  const unsigned *src = static_cast<const unsigned *>(h);
-  unsigned *dst = static_cast<unsigned *>(d);
-  const size_t words = bytes / 4;
-  int launches = 0;
-  for (size_t i = 0; i < words; i += kPutWordsLarge, ++launches) {
-    const int m = (int)std::min<size_t>(kPutWordsLarge, words - i);
-    if (m <= kPutWordsSmall) {
-      WordPack<kPutWordsSmall> p;
-      std::memcpy(p.w, src + i, 4 * (size_t)m);
-      k_put_words<kPutWordsSmall><<<1, 256, 0, s>>>(p, dst + i, m);
-    } else {
-      WordPack<kPutWordsLarge> p;
-      std::memcpy(p.w, src + i, 4 * (size_t)m);
-      k_put_words<kPutWordsLarge><<<1, 256, 0, s>>>(p, dst + i, m);
-    }
-  }
-  return launches;
-}
 }  // namespace
 
 namespace tmk {
@@ -938,13 +906,17 @@ size_t backward_image_bytes(const tm_params &p, int W, int H, int nseg) {
          align256(8 * fix_integral_scratch_elems(W, H, nf, nseg));
 }
 
+// Header: accumulators, parameter sums, then the descriptors (BwdJob[n],
+// FixJob[n]).
 size_t backward_header_bytes(int n) {
-  return align256(sizeof(BwdAcc) * n) + align256(sizeof(double) * kBwdParams) + align256(sizeof(BwdJob) * n) +
-         align256(sizeof(FixJob) * n);
+  return align256(sizeof(BwdAcc) * n) + align256(sizeof(double) * kBwdParams) +
+         align256((sizeof(BwdJob) + sizeof(FixJob)) * n);
 }
 
 // Images of a backward group: the workspace of one group stays below this
-// (or holds one image); the groups run one after another on the stream.
+// (or holds one image), and a group has at most kBwdGroupMax images (its
+// descriptors travel as kernel parameters); the groups run one after
+// another on the stream.
 constexpr size_t kBwdGroupBytes = size_t(4) << 30;
 
 // Groups [g[k], g[k + 1]) of the images and each image's row segments of the
@@ -957,7 +929,7 @@ void backward_groups(const tm_params &p, int n, const tm_image *in, std::vector<
     int ns, sr;
     fix_layout(in[i].width, in[i].height, 1, ns, sr);
     const size_t b = backward_image_bytes(p, in[i].width, in[i].height, ns);
-    if (i > g.back() && used + b > kBwdGroupBytes) {
+    if (i > g.back() && (used + b > kBwdGroupBytes || i - g.back() >= kBwdGroupMax)) {
       g.push_back(i);
       used = 0;
     }
@@ -1030,14 +1002,18 @@ tm_status backward_images(tm_ctx *c, int n, const tm_image *in, const tm_image *
   char *b = static_cast<char *>(c->bws);
   BwdAcc *accs = reinterpret_cast<BwdAcc *>(b);
   double *gsum = reinterpret_cast<double *>(b + align256(sizeof(BwdAcc) * gmax));
-  BwdJob *dbj = reinterpret_cast<BwdJob *>(reinterpret_cast<char *>(gsum) + align256(sizeof(double) * kBwdParams));
-  FixJob *dfj = reinterpret_cast<FixJob *>(reinterpret_cast<char *>(dbj) + align256(sizeof(BwdJob) * gmax));
+  char *desc = reinterpret_cast<char *>(gsum) + align256(sizeof(double) * kBwdParams);
   const int nf = c->p.n_fields;
   mark(c, s, -1);
   for (size_t k = 0; k + 1 < grp.size(); ++k) {
     const int i0 = grp[k], m = grp[k + 1] - i0;
-    std::vector<BwdJob> bj((size_t)m);
-    std::vector<FixJob> fj((size_t)m);
+    // the group's descriptors as one host block: BwdJob[m] then FixJob[m]
+    std::vector<uint4> hdesc((sizeof(BwdJob) + sizeof(FixJob)) * (size_t)m / sizeof(uint4));  // 16-byte aligned
+    unsigned char *hd = reinterpret_cast<unsigned char *>(hdesc.data());
+    BwdJob *bj = reinterpret_cast<BwdJob *>(hd);
+    FixJob *fj = reinterpret_cast<FixJob *>(hd + sizeof(BwdJob) * (size_t)m);
+    BwdJob *dbj = reinterpret_cast<BwdJob *>(desc);
+    FixJob *dfj = reinterpret_cast<FixJob *>(desc + sizeof(BwdJob) * (size_t)m);
     char *o = b + head;
     int pix = 0, inb = 0, tiles = 0, cols = 0;
     for (int r = 0; r < m; ++r) {
@@ -1088,10 +1064,10 @@ tm_status backward_images(tm_ctx *c, int n, const tm_image *in, const tm_image *
       for (int f = 0; f < nf; ++f) F.nmax[f] = window_max(dev_params(c->p, J.qbits), f, W, H);
       o += backward_image_bytes(c->p, W, H, nseg[(size_t)i]);
     }
-    launches += put_words(bj.data(), sizeof(BwdJob) * (size_t)m, dbj, s);
-    launches += put_words(fj.data(), sizeof(FixJob) * (size_t)m, dfj, s);
+    if (launch_backward_setup(hd, hdesc.size() * sizeof(uint4), desc, accs, m, gsum, k == 0, s) < 0)
+      return fail(c, TM_EINVAL, "backward group descriptors exceed %d bytes", kBwdDescBytes);
     const DevParams P = dev_params(c->p, jobs[(size_t)i0].qbits);
-    launches += launch_backward_pixel(P, dbj, m, pix, jobs[(size_t)i0].mom != nullptr, accs, gsum, k == 0, s);
+    launches += 1 + launch_backward_pixel(P, dbj, m, pix, jobs[(size_t)i0].mom != nullptr, gsum, s);
     mark(c, s, ST_BWD_PIXEL);
     launches += launch_fix_integrals(dfj, m, tiles, cols, s);
     mark(c, s, ST_BWD_ADJOINT);

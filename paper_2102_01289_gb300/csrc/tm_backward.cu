@@ -29,6 +29,9 @@
 // Per-pixel arithmetic is FP32 (FP64 throughput is a small fraction of FP32
 // on this part). Parameter gradients are summed per block in FP32 and the
 // block sums added into FP64 accumulators with one atomic each.
+#include <algorithm>
+#include <cstring>
+
 #include "tm_backward.cuh"
 
 namespace tmk {
@@ -56,8 +59,19 @@ __device__ __forceinline__ int find_bwd(const BwdJob *jobs, int n, bool input, i
   return lo;
 }
 
-// Clears the per-image accumulators and (first) the parameter sums.
-__global__ void k_bwd_init(BwdAcc *accs, int n, double *gsum, int first) {
+// The group's descriptors from the kernel parameters, cleared accumulators
+// and block counter, and (first) cleared parameter sums.
+struct DescPack {
+  unsigned w[kBwdDescBytes / 4];
+};
+template <int Words>
+struct SmallPack {
+  unsigned w[Words];
+};
+template <class Pack>
+__global__ void k_bwd_setup(const __grid_constant__ Pack p, int words, unsigned *dst, BwdAcc *accs, int n,
+                            double *gsum, int first) {
+  for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = p.w[i];
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     BwdAcc &a = accs[i];
     a.lmin = a.lmax = 0.0;
@@ -210,6 +224,41 @@ __global__ void __launch_bounds__(kBT, kMinBlocksPix) k_bwd_pixel(DevParams P, c
   }
 }
 
+// Range terms at each image's argmin / argmax pixels (block j: image j), and
+// the parameter gradients (block 0).
+__global__ void k_bwd_finish(DevParams P, const BwdJob *__restrict__ jobs, const double *gsum,
+                             float *grad_params) {
+  if (threadIdx.x == 0) {
+    const BwdJob &J = jobs[blockIdx.x];
+    const int W = J.in.W;
+    const float imin = J.st->imin, imax = J.st->imax;
+    const bool range = imax > imin && J.grad_in.p;
+    const unsigned long long idx[2] = {J.acc->argmin, J.acc->argmax};
+    const double gterm[2] = {J.acc->lmin / (double)imin, J.acc->lmax / (double)imax};
+    for (int k = 0; k < 2 && range; ++k) {
+      if (idx[k] >= (unsigned long long)W * (unsigned long long)J.in.H) continue;  // no pixel held it
+      const long long pix = (long long)idx[k];
+      const int y = (int)(pix / W), x = (int)(pix - (long long)y * W);
+      float r, g, b;
+      load_rgb(J.in, x, y, r, g, b);
+      const float raw = __fadd_rn(__fadd_rn(__fmul_rn(0.2126f, r), __fmul_rn(0.7152f, g)), __fmul_rn(0.0722f, b));
+      if (!(raw > kLumFloor)) continue;
+      float *gin = static_cast<float *>(J.grad_in.p) + (long long)y * J.grad_in.pitch + 3LL * x;
+      gin[0] += (float)(0.2126 * gterm[k]);
+      gin[1] += (float)(0.7152 * gterm[k]);
+      gin[2] += (float)(0.0722 * gterm[k]);
+    }
+  }
+  if (grad_params && blockIdx.x == 0 && threadIdx.x == 0) {
+    const int nf = P.n_fields;
+    for (int k = 0; k < 3; ++k) grad_params[k] = (float)gsum[k];
+    for (int f = 0; f < nf; ++f) {
+      grad_params[3 + f] = (float)gsum[3 + f];
+      grad_params[3 + nf + f] = (float)gsum[3 + kMaxFields + f];
+    }
+  }
+}
+
 // Per pixel: the adjoint of the window variances, through the normalised log,
 // into the luminance and Eq. 11; range-term partial sums.
 template <int NF>
@@ -297,61 +346,41 @@ __global__ void __launch_bounds__(kBT, kMinBlocksIn) k_bwd_input(DevParams P, co
   }
 }
 
-// Range terms at each image's argmin / argmax pixels, and the parameter
-// gradients.
-__global__ void k_bwd_finish(DevParams P, const BwdJob *__restrict__ jobs, int njobs, const double *gsum,
-                             float *grad_params) {
-  for (int j = threadIdx.x; j < njobs; j += blockDim.x) {
-    const BwdJob &J = jobs[j];
-    const int W = J.in.W;
-    const float imin = J.st->imin, imax = J.st->imax;
-    if (!(imax > imin) || !J.grad_in.p) continue;
-    const unsigned long long idx[2] = {J.acc->argmin, J.acc->argmax};
-    const double gterm[2] = {J.acc->lmin / (double)imin, J.acc->lmax / (double)imax};
-    for (int k = 0; k < 2; ++k) {
-      if (idx[k] >= (unsigned long long)W * (unsigned long long)J.in.H) continue;  // no pixel held it
-      const long long pix = (long long)idx[k];
-      const int y = (int)(pix / W), x = (int)(pix - (long long)y * W);
-      float r, g, b;
-      load_rgb(J.in, x, y, r, g, b);
-      const float raw = __fadd_rn(__fadd_rn(__fmul_rn(0.2126f, r), __fmul_rn(0.7152f, g)), __fmul_rn(0.0722f, b));
-      if (!(raw > kLumFloor)) continue;
-      float *gin = static_cast<float *>(J.grad_in.p) + (long long)y * J.grad_in.pitch + 3LL * x;
-      gin[0] += (float)(0.2126 * gterm[k]);
-      gin[1] += (float)(0.7152 * gterm[k]);
-      gin[2] += (float)(0.0722 * gterm[k]);
-    }
-  }
-  if (grad_params && threadIdx.x == 0) {
-    const int nf = P.n_fields;
-    for (int k = 0; k < 3; ++k) grad_params[k] = (float)gsum[k];
-    for (int f = 0; f < nf; ++f) {
-      grad_params[3 + f] = (float)gsum[3 + f];
-      grad_params[3 + nf + f] = (float)gsum[3 + kMaxFields + f];
-    }
-  }
-}
-
 }  // namespace
 
 int bwd_pixel_blocks(int W, int H) { return ((W + 31) / 32) * ((H + 8 * kRowsPix - 1) / (8 * kRowsPix)); }
 
 int bwd_input_blocks(int W, int H) { return ((W + 31) / 32) * ((H + 8 * kRowsIn - 1) / (8 * kRowsIn)); }
 
-int launch_backward_pixel(const DevParams &P, const BwdJob *jobs, int n, int pix_blocks, bool mom, BwdAcc *accs,
-                          double *gsum, bool first, cudaStream_t s) {
-  k_bwd_init<<<1, 256, 0, s>>>(accs, n, gsum, first ? 1 : 0);
+int launch_backward_setup(const void *desc, size_t bytes, void *dst, BwdAcc *accs, int n, double *gsum, bool first,
+                          cudaStream_t s) {
+  const int words = (int)(bytes / 4);
+  if (bytes > kBwdDescBytes || bytes % 4) return -1;
+  if (bytes <= 4096) {
+    SmallPack<1024> p;
+    std::memcpy(p.w, desc, bytes);
+    k_bwd_setup<<<1, 256, 0, s>>>(p, words, static_cast<unsigned *>(dst), accs, n, gsum, first ? 1 : 0);
+  } else {
+    DescPack p;
+    std::memcpy(p.w, desc, bytes);
+    k_bwd_setup<<<1, 256, 0, s>>>(p, words, static_cast<unsigned *>(dst), accs, n, gsum, first ? 1 : 0);
+  }
+  return 1;
+}
+
+int launch_backward_pixel(const DevParams &P, const BwdJob *jobs, int n, int pix_blocks, bool mom, double *gsum,
+                          cudaStream_t s) {
   switch (P.n_fields) {
-#define TM_BWD_PIXEL(nf)                                                                      \
-  case nf:                                                                                   \
-    if (mom) k_bwd_pixel<nf, true><<<pix_blocks, kBT, 0, s>>>(P, jobs, n, gsum);             \
-    else k_bwd_pixel<nf, false><<<pix_blocks, kBT, 0, s>>>(P, jobs, n, gsum);                \
+#define TM_BWD_PIXEL(nf)                                                          \
+  case nf:                                                                       \
+    if (mom) k_bwd_pixel<nf, true><<<pix_blocks, kBT, 0, s>>>(P, jobs, n, gsum); \
+    else k_bwd_pixel<nf, false><<<pix_blocks, kBT, 0, s>>>(P, jobs, n, gsum);    \
     break;
     TM_BWD_PIXEL(1) TM_BWD_PIXEL(2) TM_BWD_PIXEL(3) TM_BWD_PIXEL(4) TM_BWD_PIXEL(5) TM_BWD_PIXEL(6)
     TM_BWD_PIXEL(7) TM_BWD_PIXEL(8)
 #undef TM_BWD_PIXEL
   }
-  return 2;
+  return 1;
 }
 
 int launch_backward_input(const DevParams &P, const BwdJob *jobs, int n, int in_blocks, const double *gsum,
@@ -359,10 +388,10 @@ int launch_backward_input(const DevParams &P, const BwdJob *jobs, int n, int in_
   switch (P.n_fields) {
 #define TM_BWD_INPUT(nf) case nf: k_bwd_input<nf><<<in_blocks, kBT, 0, s>>>(P, jobs, n); break;
     TM_BWD_INPUT(1) TM_BWD_INPUT(2) TM_BWD_INPUT(3) TM_BWD_INPUT(4) TM_BWD_INPUT(5) TM_BWD_INPUT(6)
-    TM_BWD_INPUT(7) default: k_bwd_input<8><<<in_blocks, kBT, 0, s>>>(P, jobs, n); break;
+    TM_BWD_INPUT(7) TM_BWD_INPUT(8)
 #undef TM_BWD_INPUT
   }
-  k_bwd_finish<<<1, 32, 0, s>>>(P, jobs, n, gsum, grad_params);
+  k_bwd_finish<<<n, 32, 0, s>>>(P, jobs, gsum, grad_params);
   return 2;
 }
 

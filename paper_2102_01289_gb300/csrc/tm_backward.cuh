@@ -41,21 +41,30 @@ struct alignas(16) BwdJob {
 };
 static_assert(sizeof(BwdJob) % 16 == 0, "jobs are copied in 16-byte words");
 
+// Descriptors of a group: BwdJob[n] followed by FixJob[n], written by the
+// setup launch from its kernel parameters (at most kBwdDescBytes per group).
+constexpr int kBwdDescBytes = 24576;
+constexpr int kBwdGroupMax = kBwdDescBytes / (int)(sizeof(BwdJob) + sizeof(FixJob));
+
 // Blocks of the two per-pixel launches for one image.
 int bwd_pixel_blocks(int W, int H);
 int bwd_input_blocks(int W, int H);
 
-// The adjoint of a batch of images given their forward intermediates, in
-// three steps on one stream: launch_backward_pixel (per pixel: u_f, v_f, the
-// direct gradients, the parameter sums), launch_fix_integrals over `fix` (the
-// FixJob of image i reads U / V of job i and writes its IUV), then
-// launch_backward_input (the box sums back into the input, the range terms,
-// the parameter gradients). mom: every job's BwdJob::mom is set (else none
-// is). jobs / fix / accs: device arrays of n; gsum:
-// device, kBwdParams. first: clear gsum; grad_params (device float[3 + 2s])
-// or null: written from gsum at the end. Each returns its launches.
-int launch_backward_pixel(const DevParams &P, const BwdJob *jobs, int n, int pix_blocks, bool mom, BwdAcc *accs,
-                          double *gsum, bool first, cudaStream_t s);
+// The adjoint of a group of n images given their forward intermediates, on
+// one stream: launch_backward_setup (writes the group's descriptors `desc`,
+// `bytes` of BwdJob[n] then FixJob[n], to device memory `dst`, clears the
+// accumulators accs[n] and, first, the parameter sums gsum[kBwdParams]; -1
+// if `bytes` exceeds kBwdDescBytes); launch_backward_pixel (per pixel: u_f,
+// v_f, the direct gradients, the parameter sums; mom: every job's
+// BwdJob::mom is set, else none is); launch_fix_integrals over the FixJobs
+// (image i's reads U / V of job i and writes its IUV); launch_backward_input
+// (the box sums back into the input, then the range terms and, when
+// grad_params, device float[3 + 2s], is not null, the parameter gradients
+// from gsum). Each returns its launches.
+int launch_backward_setup(const void *desc, size_t bytes, void *dst, BwdAcc *accs, int n, double *gsum, bool first,
+                          cudaStream_t s);
+int launch_backward_pixel(const DevParams &P, const BwdJob *jobs, int n, int pix_blocks, bool mom, double *gsum,
+                          cudaStream_t s);
 int launch_backward_input(const DevParams &P, const BwdJob *jobs, int n, int in_blocks, const double *gsum,
                           float *grad_params, cudaStream_t s);
 
