@@ -580,7 +580,12 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
     const double share = nimg == 1 ? 1.0 : std::max(1.0 / c->num_sms, W * (double)H / total_px);
     Job &J = jobs[(size_t)i];
     J.qbits = choose_qbits(c->p, W, H);
-    const int target = c->sweep_tiles > 0 ? c->sweep_tiles : std::max(1, (int)std::lround(wave * share));
+    // one wave of tiles for a single image; two for a batch, whose images
+    // differ in cost, so that the queue can even out the CTAs' work
+    // (16 x 1 MP: 1.46 -> 1.39 ms; 12 MP alone was fastest at one wave)
+    const double waves = nimg == 1 ? 1.0 : 2.0;
+    const int target =
+        c->sweep_tiles > 0 ? c->sweep_tiles : std::max(1, (int)std::lround(waves * wave * share));
     plan_sweep(P0, W, H, target, smem_limit, J.plan);
     integral_layout(W, H, SIZE_MAX, J.nseg, J.seg_rows);
     const size_t cnt_bytes = sweep_count_bytes(P0, J.plan, J.cnt_off);
