@@ -656,7 +656,8 @@ def kernel_source_hash(kernel):
 
     import paper_2102_01289_gb300 as tm
 
-    srcs = {"fused_sweep": "tm_sweep.cu", "lookup": "tm_lookup.cu",
+    srcs = {"fused_sweep": "tm_sweep.cu", "lookup": "tm_lookup.cu", "bwd_pixel": "tm_backward.cu",
+            "bwd_input": "tm_backward.cu", "fix_stats": "tm_integral.cu", "fix_write": "tm_integral.cu",
             "integral_histogram": "tm_integral.cu", "integral_image": "tm_integral.cu",
             "prep": "tm_prepass.cu", "range": "tm_prepass.cu"}
     f = os.path.join(tm.PKG, "csrc", srcs.get(kernel, ""))
