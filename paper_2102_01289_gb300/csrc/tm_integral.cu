@@ -90,8 +90,11 @@ struct FixSource {
     return make_float2(__ldg(u + o), __ldg(v + o));
   }
   __device__ __forceinline__ Raw zero() const { return make_float2(0.f, 0.f); }
+  // u through the hardware conversion (the FP64 pipe), v through the 32-bit
+  // integer sequence (the ALU pipe): both give round-to-nearest-even, and the
+  // split keeps either pipe from limiting the tile kernels
   __device__ __forceinline__ void values(Raw x, long long &a, long long &b) const {
-    a = float_to_i64_rn(x.x * a_hi * a_lo);
+    a = __float2ll_rn(x.x * a_hi * a_lo);
     b = float_to_i64_rn(x.y * b_hi * b_lo);
   }
 };

@@ -307,34 +307,27 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const Job &J, int
       gcur = gnxt;
     }
     // the band's last row: every window that reaches it and closes on it or
-    // below it adds E(Y1 - 1); every thread takes (row, column) pairs of them,
-    // four at a time
-    const int TXc = X1 - X0, vlast = Y1 - 1;
+    // below it adds E(Y1 - 1). Each thread walks its event column (the corner
+    // columns are the ones its events use) over every other row, four rows at
+    // a time
+    const int vlast = Y1 - 1, par = tid >> 8;
+    if (col_ok) {
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      const int ybeg = max(vlast - ry[f], 0), yend = min(vlast + ry[f], H - 1);
-      const int total = (yend - ybeg + 1) * TXc;
-      const int rx = min(P.rx[f], W - 1);
-      for (int i0 = tid; i0 < total; i0 += 4 * kNT) {
-        int bb[4], xx[4];
-        long long px[4];
+      for (int f = 0; f < NF; ++f) {
+        const int ybeg = max(vlast - ry[f], 0), yend = min(vlast + ry[f], H - 1);
+        for (int y0 = ybeg + par; y0 <= yend; y0 += 8) {
+          int bb[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int i = i0 + u * kNT;
-          bb[u] = -1;
-          if (i < total) {
-            const int yy = i / TXc;
-            xx[u] = X0 + (i - yy * TXc);
-            px[u] = (long long)(ybeg + yy) * W + xx[u];
-            bb[u] = (int)__ldg(bins + px[u]);
+          for (int u = 0; u < 4; ++u) {
+            const int y = y0 + 2 * u;
+            bb[u] = y <= yend ? (int)__ldg(bins + (long long)y * W + x) : -1;
           }
-        }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if (bb[u] < 0) continue;
-          unsigned E;
-          if (event_value(bb[u], min(xx[u] + rx, W - 1) - 32 * g0, max(xx[u] - rx, 0) - 1 - 32 * g0, vlast, E))
-            slot_add(pl[f], px[u], E);
+          for (int u = 0; u < 4; ++u) {
+            if (bb[u] < 0) continue;
+            unsigned E;
+            if (event_value(bb[u], jr[f], jl[f], vlast, E)) slot_add(pl[f], (long long)(y0 + 2 * u) * W + x, E);
+          }
         }
       }
     }
