@@ -344,12 +344,11 @@ tm_status tm_debug_export(tm_ctx *ctx, int32_t what, void *dst, size_t bytes,
  *                        not changed since that forward (an autograd function
  *                        holding its saved input does). Results are those of
  *                        the recomputation. 0 = always recompute (default).
- *   TM_OPT_SWEEP_TILES   tuning: tiles of 256 columns x TY rows that the fused
- *                        sweep cuts each image into (the rows rounded to whole
- *                        strips); 0 = automatic (default: one wave of the
- *                        sweep's resident CTAs for a single image, two for a
- *                        batch, shared among its images by pixel count).
- *                        Results do not depend on it.
+ *   TM_OPT_SWEEP_TILES   tuning: segments (groups of bands of 256 columns)
+ *                        that the fused sweep cuts each image into, rounded
+ *                        to whole strips; 0 = automatic (one wave of the
+ *                        sweep's resident CTAs, shared among a batch's images
+ *                        by pixel count). Results do not depend on it.
  */
 enum {
   TM_OPT_HIST_PATH = 1,

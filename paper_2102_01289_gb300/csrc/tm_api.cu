@@ -421,13 +421,14 @@ bool same_images(const std::vector<tm_image> &a, const tm_image *b, int n) {
 
 // Per-image sizes of the forward workspace.
 struct JobLayout {
-  size_t bins, q, s12, segtot, cnt, grp, mom, dcnt, dvar, dw, dlf, dl, total;
+  size_t bins, q, s12, segtot, cnt, grp, claim, mom, dcnt, dvar, dw, dlf, dl, total;
 };
 
 // Workspace of one image. cnt_bytes: the sweep's count planes (0 on the
 // materialised path); grp: per row and 32-column group, the bin range; mom:
 // the window moments kept for the backward.
-JobLayout job_layout(const tm_params &p, int W, int H, int nseg, size_t cnt_bytes, bool debug, bool mom = false) {
+JobLayout job_layout(const tm_params &p, int W, int H, int nseg, size_t cnt_bytes, bool debug, bool mom = false,
+                     int bands = 0) {
   // nseg: row segments of the integral images (integral_layout)
   JobLayout L{};
   const size_t N = (size_t)W * H;
@@ -441,6 +442,7 @@ JobLayout job_layout(const tm_params &p, int W, int H, int nseg, size_t cnt_byte
   L.segtot = take(8 * integral_scratch_elems(W, H, nseg));
   L.cnt = take(cnt_bytes);
   L.grp = take(2 * (size_t)((W + 31) / 32) * H);
+  L.claim = take(4 * (size_t)bands);  // the sweep's band claims
   if (mom) L.mom = take(8 * N * s);
   if (debug) {
     L.dcnt = take(4 * N * s);
@@ -580,17 +582,15 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
     const double share = nimg == 1 ? 1.0 : std::max(1.0 / c->num_sms, W * (double)H / total_px);
     Job &J = jobs[(size_t)i];
     J.qbits = choose_qbits(c->p, W, H);
-    // one wave of tiles for a single image; two for a batch, whose images
-    // differ in cost, so that the queue can even out the CTAs' work
-    // (16 x 1 MP: 1.46 -> 1.39 ms; 12 MP alone was fastest at one wave)
-    const double waves = nimg == 1 ? 1.0 : 2.0;
-    const int target =
-        c->sweep_tiles > 0 ? c->sweep_tiles : std::max(1, (int)std::lround(waves * wave * share));
+    // one wave of segments, shared among a batch's images by pixel count (the
+    // segments' band claims even out the CTAs' work; two waves of them were
+    // slower on 16 x 1 MP: 1.33 against 1.28 ms)
+    const int target = c->sweep_tiles > 0 ? c->sweep_tiles : std::max(1, (int)std::lround(wave * share));
     plan_sweep(P0, W, H, target, smem_limit, J.plan);
     integral_layout(W, H, SIZE_MAX, J.nseg, J.seg_rows);
     const size_t cnt_bytes = sweep_count_bytes(P0, J.plan, J.cnt_off);
     J.cnt_wide = J.plan.cnt_wide;
-    lays[(size_t)i] = job_layout(c->p, W, H, J.nseg, cnt_bytes, debug, keep_mom);
+    lays[(size_t)i] = job_layout(c->p, W, H, J.nseg, cnt_bytes, debug, keep_mom, J.plan.tiles_x * J.plan.tiles_y);
     offs[(size_t)i] = ws_total;
     ws_total += lays[(size_t)i].total;
     J.b0[kStRange] = b_range;
@@ -603,19 +603,25 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
     b_cols += integral_col_blocks(W);
     J.b0[kStLook] = b_look;
     b_look += lookup_blocks(W, H);
-    J.nitem = J.plan.tiles_x * J.plan.tiles_y;
-    const double rows = std::min(J.plan.TY + 2.0 * J.plan.Ry + 1, H + 1.0);
+    J.nitemA = J.plan.tiles_x * ((J.plan.tiles_y + J.plan.K - 1) / J.plan.K);
+    J.nitemB = J.plan.tiles_x * J.plan.tiles_y - J.nitemA;
+    const double seg = (double)J.plan.K * J.plan.TY;  // rows of a segment
+    const double rows = std::min(seg + 2.0 * J.plan.Ry + 1, H + 1.0);
     const double cols = std::min(J.plan.TX + 2.0 * J.plan.Rx + 2, W + 1.0);
-    order.push_back({rows * (cols * 0.05 + 100.0) + 6.0 * J.plan.TX * J.plan.TY, i});
+    order.push_back({rows * (cols * 0.05 + 100.0) + 6.0 * J.plan.TX * seg, i});
   }
   // the queue holds each image's tiles together, the images with the
   // costliest tiles first
   std::stable_sort(order.begin(), order.end(),
                    [](const std::pair<double, int> &a, const std::pair<double, int> &b) { return a.first > b.first; });
   int nitems = 0;
-  for (const auto &o : order) {
-    jobs[(size_t)o.second].item0 = nitems;
-    nitems += jobs[(size_t)o.second].nitem;
+  for (const auto &o : order) {  // first phase: every job's group starts
+    jobs[(size_t)o.second].itemA0 = nitems;
+    nitems += jobs[(size_t)o.second].nitemA;
+  }
+  for (const auto &o : order) {  // second phase: the groups' other bands
+    jobs[(size_t)o.second].itemB0 = nitems;
+    nitems += jobs[(size_t)o.second].nitemB;
   }
   if ((st = ensure_stats(c, nimg))) return st;
   if ((st = grow_device(c, &c->ws, &c->ws_bytes, ws_total))) return st;
@@ -643,6 +649,7 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
     J.segtot = reinterpret_cast<long long *>(b + L.segtot);
     J.cnt = reinterpret_cast<unsigned char *>(b + L.cnt);
     J.grp = reinterpret_cast<uint16_t *>(b + L.grp);
+    J.claim = reinterpret_cast<int *>(b + L.claim);
     J.mom = keep_mom ? reinterpret_cast<float2 *>(b + L.mom) : nullptr;
     if (debug) {
       J.dbg.cnt = reinterpret_cast<unsigned *>(b + L.dcnt);

@@ -75,10 +75,13 @@ struct DebugPlanes {
 };
 
 // Tiling and shared-memory layout of the fused sweep over one image
-// (host-computed). Tiles are 256-column strips cut into bands of TY rows.
+// (host-computed). Tiles are 256-column strips cut into bands of TY rows;
+// the bands of a strip form groups of K consecutive bands, each group one
+// segment that a CTA sweeps while it can claim its next band.
 struct SweepPlan {
   int W, H;
-  int TX, TY, tiles_x, tiles_y;   // own tile size and grid
+  int TX, TY, tiles_x, tiles_y;   // own tile size and grid of bands
+  int K;                          // bands per group
   int Rx, Ry;                     // largest half-width / half-height (clipped to W-1 / H-1)
   int nch_max;                    // 32-column chunks of the widest swept row
   int bstride;                    // uint16 entries per threshold row of the in-chunk counts
@@ -114,7 +117,9 @@ struct alignas(16) Job {
   int s_pair;               // 1: s1 and s2 interleaved (the forward's workspace)
   int nseg, seg_rows;       // integral images: row segments of the tiles
   int b0[kNumStages];       // first block of this job in each batched stage
-  int item0, nitem;         // this job's slots in the sweep queue (uniform tiles, row-major)
+  int itemA0, nitemA;       // the sweep queue's slots of this job's group starts (first phase)
+  int itemB0, nitemB;       // and of its other bands (second phase)
+  int *claim;               // tiles_x x tiles_y band claims (cleared by the prep stage)
   SweepPlan plan;           // sweep tiling of this image
 };
 

@@ -75,7 +75,8 @@ int launch_integral_histogram(const uint8_t *bins, int W, int H, int n_bins, boo
 // tiles_target: tiles wanted for the image (a whole number of waves). Count
 // plane bytes of the plan (off[f]: byte offset of field f's plane). CTAs of
 // the sweep that fit one SM at `smem` bytes of dynamic shared memory. The
-// persistent launch over items [0, nitems) of the jobs' uniform tilings.
+// persistent launch over queue slots [0, nitems): every job's group starts
+// (slots itemA0 ..), then the groups' other bands (itemB0 ..).
 bool plan_sweep(const DevParams &P, int W, int H, int tiles_target, size_t smem_limit, SweepPlan &S);
 size_t sweep_count_bytes(const DevParams &P, const SweepPlan &S, long long *off);
 int sweep_ctas_per_sm(int n_fields, size_t smem);

@@ -254,6 +254,10 @@ __global__ void __launch_bounds__(256) k_prep(const Job *__restrict__ jobs, int 
     }
     if (J.grp && (lane & 7) == 0 && kmax >= 0) J.grp[(long long)y * G + (x >> 5)] = (uint16_t)(kmin | (kmax << 8));
   }
+  // the sweep's band claims start cleared
+  if (J.claim)
+    for (int i = lb * blockDim.x + threadIdx.x; i < J.plan.tiles_x * J.plan.tiles_y; i += nb * blockDim.x)
+      J.claim[i] = 0;
   // streaming reuse: the bins above used an earlier frame's range; this
   // frame's own range goes to st_next for the frame after
   if (J.st_next) commit_range(J.st_next, bmin, bmax, nb, n_bins, qbits);

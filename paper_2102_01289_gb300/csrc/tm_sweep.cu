@@ -3,43 +3,49 @@
 //
 // For a threshold k, let C_k(u, v) be the integral histogram in cumulative
 // form (Eq. 7-8 summed over the bins below k): the number of pixels (u', v')
-// with u0 <= u' <= u, v0 < v' <= v and b(u', v') < k, over a tile-local
+// with u0 <= u' <= u, v0 < v' <= v and b(u', v') < k, over a segment-local
 // origin (u0 - 1, v0). A pixel p = (x, y) with threshold k = b(p) (b(p) + 1
 // under TM_FLAG_CDF_INCLUSIVE) needs, per field with half-sizes (rx, ry),
 // the box sum of Eq. 9 over its clipped window [xl, xr] x [yt, yb]:
 //     cnt = E(yb) - E(yt - 1),   E(v) = C_k(xr, v) - C_k(xl - 1, v).
-// Each CTA owns a tile of 256 columns x TY rows and sweeps the rows of the
-// tile widened by the largest half-height above and below it, over its
-// columns widened by the largest half-width on both sides. When the sweep
-// has taken row v in, every pixel whose window starts at row v + 1 takes
-// E(v) (a "top" event, parked in the pixel's count slot) and every pixel
-// whose window ends at row v takes E(v) and subtracts the parked value (a
-// "bottom" event, which leaves the count in the slot).
+// Each image is cut into strips of 256 columns and bands of TY rows; K
+// consecutive bands of a strip form a group. A CTA sweeps a segment: it
+// starts on a band and runs on into the group's next bands while it claims
+// them first. The sweep covers the strip's columns widened by the largest
+// half-width on both sides, and only the segment's own rows, from an origin
+// just above its first row. A window reaching above or below the segment
+// takes its rows there from the other segments: each segment adds
+// E(last row of the window in it) - E(row above the first) to the pixel's
+// count, with 32-bit reductions into count planes cleared beforehand. After
+// row v is taken in, windows opening at v + 1 subtract E(v) and windows
+// closing on v add E(v); at the segment's last row every window reaching it
+// and closing on it or below adds E(last row).
 //
 // The swept columns are cut into 32-column chunks aligned to the image, one
-// warp lane per column. For every threshold k of the tile the shared-memory
-// state is
-//     C_k(u) = PT_k(c) + B_k(u) + (o + 1) m_k(c)        (c = chunk of u, o = u - 32 c)
+// warp lane per chunk. For every threshold k of the segment the
+// shared-memory state is
+//     C_k(u) = PT_k(c) + B_k(u) + (o + 1) m_k(c) + M_k (u - u0 + 1)
+//                                                   (c = chunk of u, o = u - 32 c)
 // where, over the rows swept so far,
 //     m_k(c)  counts the rows in which all of chunk c lies below k,
 //     B_k(u)  sums the in-chunk prefix counts #{u' in c, u' <= u : b < k} of
-//             the rows in which chunk c holds bins on both sides of k, and
-//     PT_k(c) sums the counts below k of all chunks left of c.
+//             the rows in which chunk c holds bins on both sides of k,
+//     PT_k(c) sums the counts below k of all chunks left of c, and
+//     M_k     counts the rows whose every bin lies below k (applied lazily).
 // So a row costs per-column work only where a bin edge crosses a chunk (one
 // ballot and popcount per such threshold), plus one prefix over the chunks
-// per threshold inside the row's bin range and one add per chunk for the
-// thresholds above it. PT and m share one word (21 + 11 bits: at most 2047
-// swept rows and 32 chunks, so neither field overflows), B fits 16 bits (32
+// per threshold inside the row's bin range. PT and m share one word
+// (21 + 11 bits: at most 2047 swept rows and 32 chunks), B fits 16 bits (32
 // columns x 2047 rows), and every E is exact below 2^21.
 //
 // Per row the CTA runs two phases separated by barriers:
 //   1. the corner events of the previous row (reading the state) and the
-//      chunk summaries of this row (bin range per chunk, mixed counts);
-//   2. the state update of this row (B of the mixed chunks, PT and m).
-// The count slots are the count planes handed to the lookup: a field whose
-// window can hold 2^16 pixels or more gets uint32 slots, the others uint16
-// (whose counts are exact modulo 2^16). A tile whose own pixels use more
-// thresholds than the shared memory holds is swept once per group of them.
+//      bins of this row into shared memory;
+//   2. the state update of this row (B of the mixed chunks, PT and m), a warp
+//      per threshold; the chunks' bin ranges come from the per-row group
+//      summary of the bin pass.
+// A segment whose own pixels use more thresholds than the shared memory
+// holds is swept once per group of them (and then does not run on).
 #include <algorithm>
 
 #include "tm_kernels.cuh"
@@ -55,6 +61,12 @@ constexpr int kChunksPerWarp = kMaxChunks / kWarps;
 constexpr int kMaxRows = 2047;      // swept rows of a tile
 constexpr unsigned kPTMask = (1u << 21) - 1;
 constexpr int kPStride = 33;        // words per threshold row of PT | m << 21
+// Bands per group: a segment starts on a group's first band and runs on into
+// its next bands while no other CTA has taken them, so CTAs that finish early
+// take the last bands of slow segments. Measured at 12 MP (one wave of 304
+// groups) with 1, 3, 4, 6, 8 and 12 bands per group: the sweep took 0.480,
+// 0.486, 0.469, 0.463, 0.453 and 0.466 ms (uniform tiles: 0.467).
+constexpr int kBandsPerGroup = 8;
 
 static_assert(2 * kTX == kNT, "one top and one bottom event thread per own column");
 
@@ -100,25 +112,26 @@ __device__ __forceinline__ unsigned pair_value(const unsigned *PT, const unsigne
   return e;
 }
 
-// Adds v to a count slot (a reduction: the value left there is the sum of
-// every band's contributions, modulo 2^32).
-__device__ __forceinline__ void slot_add(unsigned char *pl, long long pix, unsigned v) {
-  atomicAdd(reinterpret_cast<unsigned *>(pl) + pix, v);
-}
-
-// One tile: rows [Y0, Y1) of strip `strip` of job J. The band's sweep starts
-// at its own first row (origin row Y0 - 1, where C = 0): a window reaching
-// above or below the band takes its rows there from the other bands, each
-// band adding E(last row of the window in the band) - E(row above the first)
-// to the pixel's count.
+// One segment: band `band` of strip `strip` of job J, extended over the next
+// bands of its group for as long as the CTA claims them first (a claim is
+// one atomic exchange; a band taken by another CTA ends the segment). The
+// sweep starts at the segment's first row (origin row Y0 - 1, where C = 0):
+// a window reaching above or below the segment takes its rows there from
+// the other segments, each adding E(last row of the window in the segment) -
+// E(row above the first) to the pixel's count.
 template <int NF>
-__device__ __forceinline__ void sweep_tile(const DevParams &P, const Job &J, int strip, int Y0, int Y1) {
+__device__ __forceinline__ void sweep_tile(const DevParams &P, const Job &J, int strip, int band) {
+  __shared__ int ext_sh, next_sh, ext_end_sh;  // the claim state lives in shared memory, off the registers
   unsigned char *const smem = g_smem;
   const SweepPlan &S = J.plan;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int W = S.W, H = S.H;
   const int X0 = strip * kTX, X1 = min(X0 + kTX, W);
-  Y1 = min(Y1, H);
+  const int Y0 = band * S.TY;
+  int Y1 = min(Y0 + S.TY, H);
+  // the group's bands from this one on; the rows the segment can reach
+  const int gend = min((band / S.K + 1) * S.K, S.tiles_y);
+  const int Yg = min(gend * S.TY, H);
   const int cL = max(X0 - S.Rx - 1, -1);
   const int cR = min(X1 - 1 + S.Rx, W - 1);
   const int g0 = (cL + 1) >> 5;
@@ -135,15 +148,15 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const Job &J, int
   const uint8_t *__restrict__ bins = J.bins;
   const uint16_t *__restrict__ grp = J.grp;
   const int G = (W + 31) >> 5;
-  unsigned char *pl[NF];
-#pragma unroll
-  for (int f = 0; f < NF; ++f) pl[f] = J.cnt + J.cnt_off[f];
+  // the count planes' bases, in shared memory (read per event, off the registers)
+  __shared__ unsigned *pl[kMaxFields];
+  if (tid < NF) pl[tid] = reinterpret_cast<unsigned *>(J.cnt + J.cnt_off[tid]);
 
-  // ---- bin range of the pixels whose windows meet the band (its own
-  // columns, the rows the largest half-height reaches), from the per-row
-  // group summary of the bin pass ----
+  // ---- bin range of the pixels whose windows meet the segment (its own
+  // columns, the rows the largest half-height reaches from the rows it can
+  // extend over), from the per-row group summary of the bin pass ----
   {
-    const int ya = max(Y0 - S.Ry, 0), yb = min(Y1 + S.Ry, H);
+    const int ya = max(Y0 - S.Ry, 0), yb = min(Yg + S.Ry, H);
     const int gx0 = X0 >> 5, ngx = ((X1 - 1) >> 5) - gx0 + 1;
     int bmin = 255, bmax = 0;
     for (int i = tid; i < (yb - ya) * ngx; i += kNT) {
@@ -169,6 +182,19 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const Job &J, int
   const int klo = max(1, bmin + incl), khi = min(n - 1, bmax + incl);
   const int nK = max(0, khi - klo + 1);
   const int npass = max(1, (nK + kcap - 1) / kcap);
+  // one pass: the segment may run on into its group's bands before gend as
+  // it reaches them. Several passes each sweep the same rows, so the segment
+  // claims the group's next bands (up to one taken by another CTA) now.
+  if (tid == 0) {
+    int nx = band + 1;
+    if (npass > 1)
+      while (nx < gend && atomicExch(J.claim + nx * S.tiles_x + strip, 1) == 0) ++nx;
+    ext_sh = nx;
+    next_sh = nx;
+    ext_end_sh = npass == 1 ? gend : 0;
+  }
+  __syncthreads();
+  Y1 = min(ext_sh * S.TY, H);
 
   // ---- the thread's event column: windows opening below a swept row
   // (tid < 256: subtract E) or closing on it (add E) ----
@@ -232,6 +258,17 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const Job &J, int
 #pragma unroll
     for (int f = 0; f < NF; ++f) ebin[f] = 0;
     for (int v = Y0; v <= Y1; ++v) {
+      // at the current band's last row, claim the group's next band: if it
+      // is ours, the segment runs on and this row takes regular events
+      if (v == Y1 - 1) {  // block-uniform
+        if (tid == 0) {
+          const int nx = next_sh;
+          ext_sh = nx < ext_end_sh && atomicExch(J.claim + nx * S.tiles_x + strip, 1) == 0;
+          next_sh = nx + 1;
+        }
+        __syncthreads();
+        if (ext_sh) Y1 = min(Y1 + J.plan.TY, H);
+      }
       // ---- phase 1: events of row v - 1; bins of row v into shared memory ----
       const bool last = v >= Y1;
       // rows Y0 .. Y1 - 2 take the windows opening below them and those
@@ -258,7 +295,7 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const Job &J, int
         if (!((act >> f) & 1u)) continue;
         unsigned E;
         if (event_value(ebin[f], jr[f], jl[f], v - 1, E))
-          slot_add(pl[f], (long long)(v - 1 + eoff[f]) * W + x, is_close ? E : 0u - E);
+          atomicAdd(pl[f] + ((long long)(v - 1 + eoff[f]) * W + x), is_close ? E : 0u - E);
       }
       if (last) break;
 #pragma unroll
@@ -326,7 +363,7 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const Job &J, int
           for (int u = 0; u < 4; ++u) {
             if (bb[u] < 0) continue;
             unsigned E;
-            if (event_value(bb[u], jr[f], jl[f], vlast, E)) slot_add(pl[f], (long long)(y0 + 2 * u) * W + x, E);
+            if (event_value(bb[u], jr[f], jl[f], vlast, E)) atomicAdd(pl[f] + ((long long)(y0 + 2 * u) * W + x), E);
           }
         }
       }
@@ -334,13 +371,30 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const Job &J, int
   }
 }
 
-// Persistent sweep over the tiles of a batch. Item i belongs to the job whose
-// slots [item0, item0 + nitem) hold it (any order of the jobs); its tile is
-// (strip, row band) in row-major order of the job's uniform tiling.
+// The persistent sweep: CTAs pop queue slots until the queue runs dry. The
+// first phase of the queue holds every job's group starts (band K g of each
+// strip, jobs in their slot order), the second the groups' other bands, last
+// bands first. A slot's band is swept unless a CTA running on from the band
+// before has claimed it.
+__device__ __forceinline__ void second_phase_band(const SweepPlan &S, int local, int &strip, int &band) {
+  // bands with band % K == r, for r = K - 1 down to 1, each residue row-major
+  for (int r = S.K - 1; r >= 1; --r) {
+    const int nb = r < S.tiles_y ? (S.tiles_y - r + S.K - 1) / S.K : 0;
+    const int cnt = nb * S.tiles_x;
+    if (local < cnt) {
+      strip = local % S.tiles_x;
+      band = (local / S.tiles_x) * S.K + r;
+      return;
+    }
+    local -= cnt;
+  }
+  strip = band = -1;
+}
+
 template <int NF>
 __global__ void __launch_bounds__(kNT, 2) k_sweep(DevParams P, const Job *__restrict__ jobs, int njobs,
                                                   int nitems, int *queue) {
-  __shared__ int item_sh, job_sh;
+  __shared__ int item_sh, job_sh, strip_sh, band_sh, won_sh;
   for (;;) {
     if (threadIdx.x == 0) {
       item_sh = atomicAdd(queue, 1);
@@ -350,16 +404,28 @@ __global__ void __launch_bounds__(kNT, 2) k_sweep(DevParams P, const Job *__rest
     const int it = item_sh;
     if (it >= nitems) break;
     for (int j = threadIdx.x; j < njobs; j += kNT)
-      if (jobs[j].item0 <= it && it < jobs[j].item0 + jobs[j].nitem) job_sh = j;
+      if ((jobs[j].itemA0 <= it && it < jobs[j].itemA0 + jobs[j].nitemA) ||
+          (jobs[j].itemB0 <= it && it < jobs[j].itemB0 + jobs[j].nitemB))
+        job_sh = j;
     __syncthreads();
     const int jb = job_sh;
-    if (jb >= 0) {
+    if (jb >= 0 && threadIdx.x == 0) {
       const Job &J = jobs[jb];
-      const int local = it - J.item0;
-      const int strip = local % J.plan.tiles_x, band = local / J.plan.tiles_x;
-      sweep_tile<NF>(P, J, strip, band * J.plan.TY, (band + 1) * J.plan.TY);
+      int strip, band;
+      if (it < J.itemA0 + J.nitemA && it >= J.itemA0) {
+        const int local = it - J.itemA0;
+        strip = local % J.plan.tiles_x;
+        band = (local / J.plan.tiles_x) * J.plan.K;
+      } else {
+        second_phase_band(J.plan, it - J.itemB0, strip, band);
+      }
+      strip_sh = strip;
+      band_sh = band;
+      won_sh = band >= 0 && atomicExch(J.claim + band * J.plan.tiles_x + strip, 1) == 0;
     }
-    __syncthreads();  // item_sh and job_sh are rewritten for the next item
+    __syncthreads();
+    if (jb >= 0 && won_sh) sweep_tile<NF>(P, jobs[jb], strip_sh, band_sh);
+    __syncthreads();  // the shared slot fields are rewritten for the next item
   }
 }
 
@@ -397,13 +463,13 @@ bool plan_sweep(const DevParams &P, int W, int H, int tiles_target, size_t smem_
   if (smem_for(kcap, s.bstride) > smem_limit) return false;
   s.kcap = kcap;
   s.smem = smem_for(kcap, s.bstride);
-  // bands: enough tiles for the target (a whole number of waves), each at most
-  // 2047 rows (a band sweeps its own rows only)
-  const int max_ty = kMaxRows;
-  int bands = max(1, (tiles_target + s.tiles_x - 1) / s.tiles_x);
+  // bands: kBandsPerGroup per segment of the target, each group of them at
+  // most 2047 rows (a segment sweeps its own rows only)
+  s.K = kBandsPerGroup;
+  int bands = max(1, (s.K * tiles_target + s.tiles_x - 1) / s.tiles_x);
   bands = min(bands, H);
   int TY = (H + bands - 1) / bands;
-  if (TY > max_ty) TY = max_ty;
+  if (TY > kMaxRows / s.K) TY = kMaxRows / s.K;
   s.TY = TY;
   s.tiles_y = (H + TY - 1) / TY;
   // count planes: uint32, the bands' contributions added into them
