@@ -67,6 +67,30 @@ struct QSource {
   const int32_t *q;
   int W;
   __device__ __forceinline__ Raw load(int r, int c) const { return __ldg(q + (long long)r * W + c); }
+  // columns c .. c + 3 of row r (zero past W); vec: rows are 16-byte aligned
+  __device__ __forceinline__ void load4(int r, int c, bool vec, Raw *x) const {
+    const int32_t *p = q + (size_t)r * W + c;
+    if (vec && c + 3 < W) {
+      const int4 v = __ldg(reinterpret_cast<const int4 *>(p));
+      x[0] = v.x, x[1] = v.y, x[2] = v.z, x[3] = v.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) x[j] = c + j < W ? __ldg(p + j) : 0;
+    }
+  }
+  __device__ __forceinline__ bool vec_ok() const {
+    return (W & 3) == 0 && (reinterpret_cast<uintptr_t>(q) & 15) == 0;
+  }
+  // warp sums of a thread's four-element partial row sums: |q| <= 2^23, so a
+  // partial sum of q fits 26 bits and one of q^2 splits into two 24-bit
+  // parts, each summed exactly in 32 bits by the warp reduction
+  __device__ __forceinline__ void warp_sums(long long &su, long long &sv) const {
+    su = (long long)__reduce_add_sync(0xffffffffu, (int)su);
+    const unsigned long long v = (unsigned long long)sv;
+    const unsigned hi = __reduce_add_sync(0xffffffffu, (unsigned)(v >> 24));
+    const unsigned lo = __reduce_add_sync(0xffffffffu, (unsigned)(v & 0xffffffu));
+    sv = (long long)(((unsigned long long)hi << 24) + lo);
+  }
   __device__ __forceinline__ Raw zero() const { return 0; }
   __device__ __forceinline__ void values(Raw x, long long &a, long long &b) const {
     a = x;
@@ -90,6 +114,28 @@ struct FixSource {
     return make_float2(__ldg(u + o), __ldg(v + o));
   }
   __device__ __forceinline__ Raw zero() const { return make_float2(0.f, 0.f); }
+  __device__ __forceinline__ void load4(int r, int c, bool vec, Raw *x) const {
+    const size_t o = (size_t)r * W + c;
+    if (vec && c + 3 < W) {
+      const float4 a = __ldg(reinterpret_cast<const float4 *>(u + o));
+      const float4 b = __ldg(reinterpret_cast<const float4 *>(v + o));
+      x[0] = make_float2(a.x, b.x), x[1] = make_float2(a.y, b.y);
+      x[2] = make_float2(a.z, b.z), x[3] = make_float2(a.w, b.w);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) x[j] = c + j < W ? make_float2(__ldg(u + o + j), __ldg(v + o + j)) : zero();
+    }
+  }
+  __device__ __forceinline__ bool vec_ok() const {
+    return (W & 3) == 0 && ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(v)) & 15) == 0;
+  }
+  __device__ __forceinline__ void warp_sums(long long &su, long long &sv) const {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      su += __shfl_xor_sync(0xffffffffu, su, o);
+      sv += __shfl_xor_sync(0xffffffffu, sv, o);
+    }
+  }
   // u through the hardware conversion (the FP64 pipe), v through the 32-bit
   // integer sequence (the ALU pipe): both give round-to-nearest-even, and the
   // split keeps either pipe from limiting the tile kernels
@@ -413,128 +459,42 @@ __device__ __forceinline__ void int_write_tile(const IntTask &X, const Src &src,
   }
 }
 
-// The q integrals of a batch of jobs: block -> job through the batched stage
-// offsets, then the job's tile or column block.
-__device__ __forceinline__ IntTask job_task(const Job &J) {
-  return int_task(J.in.W, J.in.H, J.nseg, J.seg_rows, J.segtot);
-}
-
-__global__ void __launch_bounds__(kINT, 4) k_int_stats(const Job *__restrict__ jobs, int njobs) {
-  __shared__ StatsSmem sm;
-  const Job &J = jobs[find_job(jobs, njobs, kStRows, blockIdx.x)];
-  const IntTask X = job_task(J);
-  const int lb = blockIdx.x - J.b0[kStRows];
-  const QSource src{J.q, J.in.W};
-  int_stats_tile(X, src, lb / X.nchunk, lb % X.nchunk, sm);
-}
-
-__global__ void __launch_bounds__(kMidCols * kMidGroups) k_int_mid(const Job *__restrict__ jobs, int njobs) {
-  __shared__ long long part[2][kMidGroups][kMidCols];
-  __shared__ long long leftT[2][kMidBatch];
-  const Job &J = jobs[find_job(jobs, njobs, kStCols, blockIdx.x)];
-  int_mid_cols(job_task(J), (blockIdx.x - J.b0[kStCols]) * kMidCols, part, leftT);
-}
-
-__global__ void __launch_bounds__(kINT, 4) k_int_write(const Job *__restrict__ jobs, int njobs) {
-  __shared__ int32_t tile[kIC / 8 * 9];
-  __shared__ long long out1[kIC / 8 * 9], out2[kIC / 8 * 9];
-  __shared__ long long wt[2][kINT / 32];
-  const Job &J = jobs[find_job(jobs, njobs, kStRows, blockIdx.x)];
-  const IntTask X = job_task(J);
-  const int lb = blockIdx.x - J.b0[kStRows];
-  const QSource src{J.q, J.in.W};
-  if (J.s_pair)
-    int_write_tile<QSource, long long, true>(X, src, J.s1, J.s2, lb / X.nchunk, lb % X.nchunk, tile, out1, out2, wt);
-  else
-    int_write_tile(X, src, J.s1, J.s2, lb / X.nchunk, lb % X.nchunk, tile, out1, out2, wt);
-}
-
-// The backward's fixed-point integral planes of a batch of images: block ->
-// image through FixJob::b0_tile / b0_col, then (pair p, tile) or (pair p,
-// column block). Pair p of an image: planes u_p and v_p (each W x H), scaled
-// by 2^fix_shift(amax[p], nmax[p]) and 2^fix_shift(amax[kMaxFields + p],
-// nmax[p]) (the scales the backward converts back with), interleaved into
-// the p-th pair plane of dst (two int64 per position); scratch per pair.
-__device__ __forceinline__ int find_fix(const FixJob *jobs, int n, bool tiles, int blk) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if ((tiles ? jobs[mid].b0_tile : jobs[mid].b0_col) <= blk) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-__device__ __forceinline__ IntTask fix_task(const FixJob &F, int p) {
-  return int_task(F.W, F.H, F.nseg, F.seg_rows, F.scratch + (long long)p * F.scratch_stride);
-}
-
-__device__ __forceinline__ FixSource fix_source(const FixJob &F, int p) {
-  const long long N = (long long)F.W * F.H;
-  return fix_source_of(F.u + p * N, F.v + p * N, F.W, fix_shift(__ldg(F.amax + p), F.nmax[p]),
-                       fix_shift(__ldg(F.amax + kMaxFields + p), F.nmax[p]));
-}
-
-// Launch 1 for the fixed-point planes (the outputs of int_stats_tile): each
-// thread owns four consecutive columns of the chunk and keeps kFSRows rows of
-// loads in flight, 16 bytes at a time where the rows are 16-byte aligned;
-// plain column sums down the segment, then one block scan over the columns.
-constexpr int kFS = 256;    // threads of a fixed-point stats block
+// Launch 1 with each thread owning four consecutive columns of the chunk and
+// kFSRows rows of loads in flight, 16 bytes at a time where the rows are
+// 16-byte aligned: plain column sums down the segment, then one block scan
+// over the columns; the same outputs as int_stats_tile.
+constexpr int kFS = 256;    // threads of a four-column stats block
 constexpr int kFSRows = 4;  // rows in flight per thread
-static_assert(kFS * 4 == kIC, "a fixed-point stats block spans one chunk");
+static_assert(kFS * 4 == kIC, "a four-column stats block spans one chunk");
 
-__device__ __forceinline__ void fix_load4(const FixSource &src, int r, int c, bool vec, float4 &a, float4 &b) {
-  const int W = src.W;
-  const size_t o = (size_t)r * W + c;
-  if (vec && c + 3 < W) {
-    a = __ldg(reinterpret_cast<const float4 *>(src.u + o));
-    b = __ldg(reinterpret_cast<const float4 *>(src.v + o));
-  } else {
-    a.x = c < W ? __ldg(src.u + o) : 0.f;
-    a.y = c + 1 < W ? __ldg(src.u + o + 1) : 0.f;
-    a.z = c + 2 < W ? __ldg(src.u + o + 2) : 0.f;
-    a.w = c + 3 < W ? __ldg(src.u + o + 3) : 0.f;
-    b.x = c < W ? __ldg(src.v + o) : 0.f;
-    b.y = c + 1 < W ? __ldg(src.v + o + 1) : 0.f;
-    b.z = c + 2 < W ? __ldg(src.v + o + 2) : 0.f;
-    b.w = c + 3 < W ? __ldg(src.v + o + 3) : 0.f;
-  }
-}
-
-__global__ void __launch_bounds__(kFS, 3) k_fix_stats(const FixJob *__restrict__ jobs, int n) {
-  __shared__ long long rowp[kRowGroup][2][kFS / 32];
-  __shared__ long long wt[2][kFS / 32];
-  const FixJob &F = jobs[find_fix(jobs, n, true, blockIdx.x)];
-  const int per = F.nseg * ((F.W + kIC - 1) / kIC), lb = blockIdx.x - F.b0_tile;
-  const int p = lb / per, t = lb - p * per;
-  const IntTask X = fix_task(F, p);
-  const FixSource src = fix_source(F, p);
+template <class Src>
+__device__ __forceinline__ void int_stats4_tile(const IntTask &X, const Src &src, int seg, int k,
+                                                long long (*rowp)[2][kFS / 32], long long (*wt)[kFS / 32]) {
   const int W = X.W, H = X.H;
-  const int seg = t / X.nchunk, k = t % X.nchunk;
   const int R0 = seg * X.seg_rows, R1 = min(R0 + X.seg_rows, H);
   const int c = k * kIC + 4 * (int)threadIdx.x;
-  const bool vec = (W & 3) == 0;         // rows start 16-byte aligned (the planes are 256-byte aligned)
+  const bool vec = src.vec_ok();
   const bool totals = k + 1 < X.nchunk;  // block-uniform; see int_stats_tile
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   long long cu[4] = {0, 0, 0, 0}, cv[4] = {0, 0, 0, 0};
   for (int r0 = R0; r0 < R1; r0 += kFSRows) {
-    float4 a[kFSRows], b[kFSRows];
+    typename Src::Raw raw[kFSRows][4];
 #pragma unroll
     for (int i = 0; i < kFSRows; ++i) {
       if (r0 + i < R1) {
-        fix_load4(src, r0 + i, c, vec, a[i], b[i]);
+        src.load4(r0 + i, c, vec, raw[i]);
       } else {
-        a[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        b[i] = a[i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) raw[i][j] = src.zero();
       }
     }
 #pragma unroll
     for (int i = 0; i < kFSRows; ++i) {
-      const float ua[4] = {a[i].x, a[i].y, a[i].z, a[i].w}, va[4] = {b[i].x, b[i].y, b[i].z, b[i].w};
       long long su = 0, sv = 0;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         long long x1, x2;
-        src.values(make_float2(ua[j], va[j]), x1, x2);
+        src.values(raw[i][j], x1, x2);
         cu[j] += x1;
         cv[j] += x2;
         su += x1;
@@ -542,11 +502,7 @@ __global__ void __launch_bounds__(kFS, 3) k_fix_stats(const FixJob *__restrict__
       }
       const int r = r0 + i;
       if (!totals || r >= R1) continue;  // block-uniform
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        su += __shfl_xor_sync(0xffffffffu, su, o);
-        sv += __shfl_xor_sync(0xffffffffu, sv, o);
-      }
+      src.warp_sums(su, sv);
       const int g = (r - R0) % kRowGroup;
       if (lane == 0) {
         rowp[g][0][wid] = su;
@@ -598,6 +554,78 @@ __global__ void __launch_bounds__(kFS, 3) k_fix_stats(const FixJob *__restrict__
     X.tiletot[(long long)seg * X.nchunk + k] = t1;
     X.tiletot[((long long)X.nseg + seg) * X.nchunk + k] = t2;
   }
+}
+
+// The q integrals of a batch of jobs: block -> job through the batched stage
+// offsets, then the job's tile or column block.
+__device__ __forceinline__ IntTask job_task(const Job &J) {
+  return int_task(J.in.W, J.in.H, J.nseg, J.seg_rows, J.segtot);
+}
+
+__global__ void __launch_bounds__(kFS, 3) k_int_stats(const Job *__restrict__ jobs, int njobs) {
+  __shared__ long long rowp[kRowGroup][2][kFS / 32];
+  __shared__ long long wt[2][kFS / 32];
+  const Job &J = jobs[find_job(jobs, njobs, kStRows, blockIdx.x)];
+  const IntTask X = job_task(J);
+  const int lb = blockIdx.x - J.b0[kStRows];
+  const QSource src{J.q, J.in.W};
+  int_stats4_tile(X, src, lb / X.nchunk, lb % X.nchunk, rowp, wt);
+}
+
+__global__ void __launch_bounds__(kMidCols * kMidGroups) k_int_mid(const Job *__restrict__ jobs, int njobs) {
+  __shared__ long long part[2][kMidGroups][kMidCols];
+  __shared__ long long leftT[2][kMidBatch];
+  const Job &J = jobs[find_job(jobs, njobs, kStCols, blockIdx.x)];
+  int_mid_cols(job_task(J), (blockIdx.x - J.b0[kStCols]) * kMidCols, part, leftT);
+}
+
+__global__ void __launch_bounds__(kINT, 4) k_int_write(const Job *__restrict__ jobs, int njobs) {
+  __shared__ int32_t tile[kIC / 8 * 9];
+  __shared__ long long out1[kIC / 8 * 9], out2[kIC / 8 * 9];
+  __shared__ long long wt[2][kINT / 32];
+  const Job &J = jobs[find_job(jobs, njobs, kStRows, blockIdx.x)];
+  const IntTask X = job_task(J);
+  const int lb = blockIdx.x - J.b0[kStRows];
+  const QSource src{J.q, J.in.W};
+  if (J.s_pair)
+    int_write_tile<QSource, long long, true>(X, src, J.s1, J.s2, lb / X.nchunk, lb % X.nchunk, tile, out1, out2, wt);
+  else
+    int_write_tile(X, src, J.s1, J.s2, lb / X.nchunk, lb % X.nchunk, tile, out1, out2, wt);
+}
+
+// The backward's fixed-point integral planes of a batch of images: block ->
+// image through FixJob::b0_tile / b0_col, then (pair p, tile) or (pair p,
+// column block). Pair p of an image: planes u_p and v_p (each W x H), scaled
+// by 2^fix_shift(amax[p], nmax[p]) and 2^fix_shift(amax[kMaxFields + p],
+// nmax[p]) (the scales the backward converts back with), interleaved into
+// the p-th pair plane of dst (two int64 per position); scratch per pair.
+__device__ __forceinline__ int find_fix(const FixJob *jobs, int n, bool tiles, int blk) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((tiles ? jobs[mid].b0_tile : jobs[mid].b0_col) <= blk) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ IntTask fix_task(const FixJob &F, int p) {
+  return int_task(F.W, F.H, F.nseg, F.seg_rows, F.scratch + (long long)p * F.scratch_stride);
+}
+
+__device__ __forceinline__ FixSource fix_source(const FixJob &F, int p) {
+  const long long N = (long long)F.W * F.H;
+  return fix_source_of(F.u + p * N, F.v + p * N, F.W, fix_shift(__ldg(F.amax + p), F.nmax[p]),
+                       fix_shift(__ldg(F.amax + kMaxFields + p), F.nmax[p]));
+}
+
+__global__ void __launch_bounds__(kFS, 3) k_fix_stats(const FixJob *__restrict__ jobs, int n) {
+  __shared__ long long rowp[kRowGroup][2][kFS / 32];
+  __shared__ long long wt[2][kFS / 32];
+  const FixJob &F = jobs[find_fix(jobs, n, true, blockIdx.x)];
+  const int per = F.nseg * ((F.W + kIC - 1) / kIC), lb = blockIdx.x - F.b0_tile;
+  const int p = lb / per, t = lb - p * per;
+  const IntTask X = fix_task(F, p);
+  int_stats4_tile(X, fix_source(F, p), t / X.nchunk, t % X.nchunk, rowp, wt);
 }
 
 __global__ void __launch_bounds__(kMidCols * kMidGroups) k_fix_mid(const FixJob *__restrict__ jobs, int n) {
@@ -713,7 +741,7 @@ int launch_fix_integrals(const FixJob *jobs, int n, int tile_blocks, int col_blo
 }
 
 int launch_integral_jobs(const Job *jobs, int njobs, int tile_blocks, int col_blocks, cudaStream_t s) {
-  k_int_stats<<<tile_blocks, kINT, 0, s>>>(jobs, njobs);
+  k_int_stats<<<tile_blocks, kFS, 0, s>>>(jobs, njobs);
   k_int_mid<<<col_blocks, kMidCols * kMidGroups, 0, s>>>(jobs, njobs);
   k_int_write<<<tile_blocks, kINT, 0, s>>>(jobs, njobs);
   return 3;
