@@ -105,7 +105,22 @@ __device__ void commit_range(Stats *st, unsigned bmin, unsigned bmax, int nb, in
   const float imin = __uint_as_float(vs->min_bits);
   const float imax = __uint_as_float(vs->max_bits);
   const bool degenerate = !(imax > imin);
-  const double lmin = log((double)imin), lmax = log((double)imax);
+  // the FP64 logarithms, one warp each, so that their latencies overlap (the
+  // FP64 pipe is slow on this part and this block is the kernel's tail)
+  __shared__ double lg[5];
+  const unsigned bits = __float_as_uint(imin);
+  if ((threadIdx.x & 31) == 0) {
+    switch (threadIdx.x >> 5) {
+      case 0: lg[0] = log((double)imin); break;
+      case 1: lg[1] = log((double)imax); break;
+      case 2: lg[2] = log2((double)imin); break;
+      case 3: lg[3] = log2((double)imax); break;
+      case 4: lg[4] = log2((double)__uint_as_float((bits & 0x7fffffu) | 0x3f800000u)); break;
+      default: break;
+    }
+  }
+  __syncthreads();
+  const double lmin = lg[0], lmax = lg[1];
   for (int k = 1 + threadIdx.x; k < n_bins; k += blockDim.x) {
     float edge = __int_as_float(0x7f800000);
     if (!degenerate) {
@@ -115,15 +130,13 @@ __device__ void commit_range(Stats *st, unsigned bmin, unsigned bmax, int nb, in
     st->thr[k - 1] = edge;
   }
   if (threadIdx.x == 0) {
-    const unsigned bits = __float_as_uint(imin);
+    const double l2min = lg[2], l2max = lg[3];
     st->e0 = (int)(bits >> 23) - 127;
-    const double m0 = (double)__uint_as_float((bits & 0x7fffffu) | 0x3f800000u);
-    st->c0 = (float)log2(m0);
-    st->log2_scale =
-        degenerate ? 0.f : (float)(ldexp(1.0, qbits) / (log2((double)imax) - log2((double)imin)));
+    st->c0 = (float)lg[4];
+    st->log2_scale = degenerate ? 0.f : (float)(ldexp(1.0, qbits) / (l2max - l2min));
     st->lin_scale = (float)(ldexp(1.0, qbits) / (double)imax);
-    st->lg_min = (float)log2((double)imin);
-    st->bin_scale = degenerate ? 0.f : (float)((double)n_bins / (log2((double)imax) - log2((double)imin)));
+    st->lg_min = (float)l2min;
+    st->bin_scale = degenerate ? 0.f : (float)((double)n_bins / (l2max - l2min));
     st->imin = imin;
     st->imax = imax;
     st->degenerate = degenerate ? 1 : 0;
