@@ -460,6 +460,34 @@ def test_inclusive_cdf_on_the_sweep_at_full_bin_range(orc):
     assert_out_close(out, ref)
 
 
+@pytest.mark.parametrize("segments", [0, 12, 200])
+def test_sweep_segments_and_threshold_passes(orc, segments):
+    """The sweep's segments run on over the bands they claim; CTAs that finish
+    early take the rest. A 1500-column image with 256 bins over ten decades
+    has tiles whose bins span more thresholds than the shared memory holds
+    (several passes: such a segment claims its group's bands up front).
+    Counts bit-exact and output within tolerance at every tiling (0: the
+    automatic one; 12 and 200 segments: long and short bands)."""
+    img = synth.wdr_image(240, 1500, seed=7, decades=(-4.0, 6.0))
+    gp, op = params_pair(orc, 256, [3, 20])
+    x = torch.from_numpy(np.ascontiguousarray(img)).cuda()
+    ctx = tm.tm_create(gp)
+    try:
+        tm.tm_set_debug(ctx, 1)
+        tm.tm_set_option(ctx, tm.TM_OPT_HIST_PATH, 1)
+        tm.tm_set_option(ctx, tm.TM_OPT_SWEEP_TILES, segments)
+        out = torch.empty_like(x)
+        for _ in range(2):  # the claims are cleared for every call
+            tm.tm_forward(ctx, x, out)
+        cnt = tm.tm_debug_export(ctx, tm.TM_DBG_COUNTS).cpu().numpy().view(np.uint32).reshape(2, 240, 1500)
+        torch.cuda.synchronize()
+    finally:
+        tm.tm_destroy(ctx)
+    ref, fl = orc.forward(img, op)
+    assert np.array_equal(cnt, fl.cnt)
+    assert_out_close(out.cpu().numpy(), ref)
+
+
 def test_srgb_uint8_output(orc):
     """TM_FLAG_SRGB_U8: uint8 output is floor(255 srgb(clamp(c)) + 0.5) of
     the oracle's float result, within 1 LSB on at most 0.01% of the values."""
