@@ -335,7 +335,7 @@ tm_status tm_debug_export(tm_ctx *ctx, int32_t what, void *dst, size_t bytes,
  *                        range.
  *   TM_OPT_BACKWARD_REUSE 1 = tm_backward / tm_backward_batch take the forward
  *                        intermediates (bin map, quantised log, integral
- *                        images, slab counts) from the context's workspace
+ *                        images, count planes) from the context's workspace
  *                        instead of recomputing them, when the last forward
  *                        call on the context ran the fused path, each image
  *                        over its own range, on the same image descriptors

@@ -137,7 +137,7 @@ struct tm_ctx {
   int rr_cur = 0, rr_valid = 0, rr_W = 0, rr_H = 0, rr_q = 0;
   const Stats *last_stats = nullptr;  // range state of the last single-image forward
   // TM_OPT_BACKWARD_REUSE: the job descriptors of the last fused forward that
-  // left its intermediates (bins, q, integral images, slab counts) in the
+  // left its intermediates (bins, q, integral images, count planes) in the
   // workspace, the images it ran on, and those of the cached batch graph
   int bwd_reuse = 0;
   bool fwd_valid = false;
@@ -459,7 +459,7 @@ JobLayout job_layout(const tm_params &p, int W, int H, int nseg, size_t cnt_byte
 // bin-major cumulative integral histogram, lookup. Used when the fused sweep
 // does not fit the fields, or on request (TM_OPT_HIST_PATH = 2).
 tm_status forward_materialised(tm_ctx *c, const tm_image *in, const tm_image *out, cudaStream_t s) {
-  c->fwd_valid = false;  // its workspace layout holds no slab counts
+  c->fwd_valid = false;  // its workspace layout holds no count planes
   const int W = in->width, H = in->height;
   const int qbits = choose_qbits(c->p, W, H);
   DevParams P = dev_params(c->p, qbits);

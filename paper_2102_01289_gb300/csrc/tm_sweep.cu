@@ -433,7 +433,7 @@ size_t smem_for(int kcap, int bstride) { return layout(kcap).B + (size_t)kcap * 
 
 }  // namespace
 
-bool plan_sweep(const DevParams &P, int W, int H, int tiles_target, size_t smem_limit, SweepPlan &S) {
+bool plan_sweep(const DevParams &P, int W, int H, int segments, size_t smem_limit, SweepPlan &S) {
   SweepPlan s{};
   s.W = W;
   s.H = H;
@@ -466,7 +466,7 @@ bool plan_sweep(const DevParams &P, int W, int H, int tiles_target, size_t smem_
   // bands: kBandsPerGroup per segment of the target, each group of them at
   // most 2047 rows (a segment sweeps its own rows only)
   s.K = kBandsPerGroup;
-  int bands = max(1, (s.K * tiles_target + s.tiles_x - 1) / s.tiles_x);
+  int bands = max(1, (s.K * segments + s.tiles_x - 1) / s.tiles_x);
   bands = min(bands, H);
   int TY = (H + bands - 1) / bands;
   if (TY > kMaxRows / s.K) TY = kMaxRows / s.K;
