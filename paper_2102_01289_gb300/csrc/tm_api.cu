@@ -129,6 +129,13 @@ struct tm_ctx {
   Job *mdjobs = nullptr;
   size_t mdjobs_bytes = 0;
   cudaStream_t graph_stream = nullptr;
+  // The fused forward runs the sweep on sweep_stream (high priority) beside
+  // the integral images on int_stream (low priority): the integral images
+  // only need q, the sweep only the bins, and the integral tiles fill the
+  // SMs that the sweep's last segments leave idle. ov_fork / ov_sweep /
+  // ov_int order the two streams after the prep stage and before the lookup.
+  cudaStream_t sweep_stream = nullptr, int_stream = nullptr;
+  cudaEvent_t ov_fork = nullptr, ov_sweep = nullptr, ov_int = nullptr;
   int64_t graph_launches = 0;
   // streaming range reuse (TM_OPT_REUSE_RANGE): two range states; a forward
   // bins with rr_stats[rr_cur] and leaves its own range in the other
@@ -149,7 +156,13 @@ struct tm_ctx {
   std::map<std::vector<std::tuple<int, int, int, int>>, int> batch_choice;
   // stage timing: events recorded on the call's stream after each stage
   int stage_timing = 0;
-  std::vector<std::vector<std::pair<cudaEvent_t, int>>> marks;
+  // per call, its stage marks: the event, the stage it ends (or kNoStage),
+  // and the index of the mark it is timed from (-1: the one before)
+  struct Mark {
+    cudaEvent_t e;
+    int stage, from;
+  };
+  std::vector<std::vector<Mark>> marks;
   std::vector<cudaEvent_t> event_pool;
   double stage_ms[16] = {};
 };
@@ -228,20 +241,26 @@ const char *const kStageNames[ST_COUNT] = {"range", "prep", "integral_image", "i
                                           "bwd_adjoint", "bwd_input", "batch_materialised"};
 
 // Record a stage boundary on stream s (stage < 0 opens a new call).
-void mark(tm_ctx *c, cudaStream_t s, int stage) {
-  if (!c->stage_timing) return;
+// Record a stage boundary on stream s (stage -1 opens a new call; kNoStage
+// marks a point that ends no stage). The stage is timed from mark `from` of
+// the call (-1: the mark before). Returns this mark's index in the call (-1
+// without stage timing).
+constexpr int kNoStage = -2;
+int mark(tm_ctx *c, cudaStream_t s, int stage, int from = -1) {
+  if (!c->stage_timing) return -1;
   cudaEvent_t e;
   if (!c->event_pool.empty()) {
     e = c->event_pool.back();
     c->event_pool.pop_back();
   } else if (cudaEventCreate(&e) != cudaSuccess) {
     cudaGetLastError();
-    return;
+    return -1;
   }
-  if (stage < 0) c->marks.emplace_back();
+  if (stage == -1) c->marks.emplace_back();
   if (c->marks.empty()) c->marks.emplace_back();
   cudaEventRecord(e, s);
-  c->marks.back().emplace_back(e, stage);
+  c->marks.back().push_back({e, stage, from});
+  return (int)c->marks.back().size() - 1;
 }
 
 size_t elem_size(int dt) { return dt == TM_F32 ? 4 : dt == TM_F16 ? 2 : 1; }
@@ -318,6 +337,18 @@ tm_status ensure_device_info(tm_ctx *c) {
   c->num_sms = v;
   TM_CUDA(c, cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   c->smem_optin = (size_t)v;
+  return TM_OK;
+}
+
+// The side streams and events of the overlapped sweep (created once).
+tm_status ensure_side_streams(tm_ctx *c) {
+  if (c->sweep_stream) return TM_OK;
+  int least = 0, greatest = 0;
+  TM_CUDA(c, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  TM_CUDA(c, cudaStreamCreateWithPriority(&c->sweep_stream, cudaStreamNonBlocking, greatest));
+  TM_CUDA(c, cudaStreamCreateWithPriority(&c->int_stream, cudaStreamNonBlocking, least));
+  for (cudaEvent_t *e : {&c->ov_fork, &c->ov_sweep, &c->ov_int})
+    TM_CUDA(c, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   return TM_OK;
 }
 
@@ -673,6 +704,7 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   // a batch is captured on the context's own stream (capture is not allowed on
   // the legacy default stream) and the graph is then launched on the caller's
   const cudaStream_t caller = s;
+  if ((st = ensure_side_streams(c))) return st;  // before any capture begins
   if (graph) {
     if (!c->graph_stream) TM_CUDA(c, cudaStreamCreateWithFlags(&c->graph_stream, cudaStreamNonBlocking));
     s = c->graph_stream;
@@ -683,12 +715,23 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   if (run_range) launch_range(dj, nimg, b_range, c->p.n_bins, s);
   if (!graph) mark(c, s, ST_RANGE);
   launch_prep(dj, nimg, b_prep, c->p.n_bins, c->p.flags, c->p.n_fields, s);
-  if (!graph) mark(c, s, ST_PREP);
-  n += (run_range ? 2 : 1) + launch_integral_jobs(dj, nimg, b_rows, b_cols, s);
-  if (!graph) mark(c, s, ST_INTEGRAL);
-  const int ls = launch_sweep(P, dj, nimg, nitems, queue, smem, ctas, s);
-  n += 1;
-  if (!graph) mark(c, s, ST_SWEEP);
+  const int m_prep = graph ? -1 : mark(c, s, ST_PREP);
+  // the sweep (high priority, launched first, so its CTAs take the SMs) and
+  // the integral images (low priority) side by side, each timed from the end
+  // of the prep stage, joined before the lookup
+  TM_CUDA(c, cudaEventRecord(c->ov_fork, s));
+  TM_CUDA(c, cudaStreamWaitEvent(c->sweep_stream, c->ov_fork, 0));
+  TM_CUDA(c, cudaStreamWaitEvent(c->int_stream, c->ov_fork, 0));
+  const int ls = launch_sweep(P, dj, nimg, nitems, queue, smem, ctas, c->sweep_stream);
+  if (!graph) mark(c, c->sweep_stream, ST_SWEEP, m_prep);
+  n += 1 + launch_integral_jobs(dj, nimg, b_rows, b_cols, c->int_stream);
+  if (!graph) mark(c, c->int_stream, ST_INTEGRAL, m_prep);
+  n += run_range ? 2 : 1;
+  TM_CUDA(c, cudaEventRecord(c->ov_sweep, c->sweep_stream));
+  TM_CUDA(c, cudaEventRecord(c->ov_int, c->int_stream));
+  TM_CUDA(c, cudaStreamWaitEvent(s, c->ov_sweep, 0));
+  TM_CUDA(c, cudaStreamWaitEvent(s, c->ov_int, 0));
+  if (!graph) mark(c, s, kNoStage);  // the join: the lookup is timed from here
   if (do_lookup) {
     n += launch_lookup_counts(P, dj, nimg, b_look, s);
     if (!graph) mark(c, s, ST_LOOKUP);
@@ -1261,7 +1304,7 @@ void tm_destroy(tm_ctx *c) {
     cudaDeviceSynchronize();
   drop_graph(c);
   for (auto &call : c->marks)
-    for (auto &m : call) cudaEventDestroy(m.first);
+    for (auto &m : call) cudaEventDestroy(m.e);
   for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
   if (c->ws) cudaFree(c->ws);
   if (c->bws) cudaFree(c->bws);
@@ -1281,6 +1324,10 @@ void tm_destroy(tm_ctx *c) {
   if (c->djobs) cudaFree(c->djobs);
   if (c->ditems) cudaFree(c->ditems);
   if (c->graph_stream) cudaStreamDestroy(c->graph_stream);
+  for (cudaStream_t q : {c->sweep_stream, c->int_stream})
+    if (q) cudaStreamDestroy(q);
+  for (cudaEvent_t e : {c->ov_fork, c->ov_sweep, c->ov_int})
+    if (e) cudaEventDestroy(e);
   if (c->gdjobs) cudaFree(c->gdjobs);
   if (c->gditems) cudaFree(c->gditems);
   if (c->mws) cudaFree(c->mws);
@@ -1658,17 +1705,20 @@ int32_t tm_stage_times(tm_ctx *c, float *ms, const char **names, int32_t cap) {
   }
   for (auto &call : c->marks) {
     if (call.empty()) continue;
-    if (cudaEventSynchronize(call.back().first) != cudaSuccess) {
+    bool ok = true;
+    for (auto &m : call) ok = ok && cudaEventSynchronize(m.e) == cudaSuccess;  // marks on several streams
+    if (!ok) {
       cudaGetLastError();
       fail(c, TM_ECUDA, "tm_stage_times: event synchronisation failed");
       return -1;
     }
     for (size_t i = 1; i < call.size(); ++i) {
       float t = 0.f;
-      if (call[i].second >= 0 && cudaEventElapsedTime(&t, call[i - 1].first, call[i].first) == cudaSuccess)
-        c->stage_ms[call[i].second] += t;
+      const size_t from = call[i].from >= 0 ? (size_t)call[i].from : i - 1;
+      if (call[i].stage >= 0 && cudaEventElapsedTime(&t, call[from].e, call[i].e) == cudaSuccess)
+        c->stage_ms[call[i].stage] += t;
     }
-    for (auto &m : call) c->event_pool.push_back(m.first);
+    for (auto &m : call) c->event_pool.push_back(m.e);
   }
   c->marks.clear();
   int32_t n = 0;
