@@ -205,7 +205,9 @@ tm_status tm_backward(tm_ctx *ctx, const tm_image *in, const tm_image *grad_out,
 
 /* tm_backward over n images of possibly different sizes: the forward
  * intermediates of all images are recomputed in one batched pass (as in
- * tm_forward_batch), then the adjoint runs image by image.
+ * tm_forward_batch), then the adjoint runs one launch per stage over a group
+ * of images at a time (up to 66 images, and a workspace under 4 GiB, per
+ * group).
  *   in[i], grad_out[i]  host arrays of n device-image descriptors.
  *   grad_in             host array of n descriptors, or NULL to skip.
  *   grad_params         device float[3 + 2*s] receiving the SUM over the n
@@ -343,7 +345,11 @@ tm_status tm_debug_export(tm_ctx *ctx, int32_t what, void *dst, size_t bytes,
  *                        The caller guarantees that the pixels of `in` have
  *                        not changed since that forward (an autograd function
  *                        holding its saved input does). Results are those of
- *                        the recomputation. 0 = always recompute (default).
+ *                        the recomputation. While the option is on, the
+ *                        forward's lookup also keeps each field's window
+ *                        variance and mean of the normalised log (8 bytes per
+ *                        field and pixel) for the backward to read.
+ *                        0 = always recompute (default).
  *   TM_OPT_SWEEP_TILES   tuning: segments (groups of bands of 256 columns)
  *                        that the fused sweep cuts each image into, rounded
  *                        to whole strips; 0 = automatic (one wave of the
