@@ -350,18 +350,24 @@ tm_status tm_debug_export(tm_ctx *ctx, int32_t what, void *dst, size_t bytes,
  *                        variance and mean of the normalised log (8 bytes per
  *                        field and pixel) for the backward to read.
  *                        0 = always recompute (default).
- *   TM_OPT_SWEEP_TILES   tuning: segments (groups of bands of 256 columns)
+ *   TM_OPT_SWEEP_TILES   tuning: segments (groups of bands of one strip)
  *                        that the fused sweep cuts each image into, rounded
  *                        to whole strips; 0 = automatic (one wave of the
  *                        sweep's resident CTAs, shared among a batch's images
  *                        by pixel count). Results do not depend on it.
+ *   TM_OPT_SWEEP_WIDTH   tuning: own columns of the fused sweep's strips,
+ *                        256 (two CTAs of 512 threads per SM) or 512 (one
+ *                        CTA of 1024 threads per SM; taken only where every
+ *                        image of the call fits it, else 256); 0 = automatic.
+ *                        Results do not depend on it.
  */
 enum {
   TM_OPT_HIST_PATH = 1,
   TM_OPT_STAGE_TIMING = 2,
   TM_OPT_REUSE_RANGE = 3,
   TM_OPT_BACKWARD_REUSE = 4,
-  TM_OPT_SWEEP_TILES = 5
+  TM_OPT_SWEEP_TILES = 5,
+  TM_OPT_SWEEP_WIDTH = 6
 };
 tm_status tm_set_option(tm_ctx *ctx, int32_t key, int64_t value);
 

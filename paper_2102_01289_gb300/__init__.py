@@ -27,6 +27,7 @@ TM_OPT_STAGE_TIMING = 2
 TM_OPT_REUSE_RANGE = 3
 TM_OPT_BACKWARD_REUSE = 4
 TM_OPT_SWEEP_TILES = 5
+TM_OPT_SWEEP_WIDTH = 6
 # reading variants (tm_params.flags)
 TM_FLAG_CDF_INCLUSIVE, TM_FLAG_AREA_LITERAL, TM_FLAG_VAR_LINEAR, TM_FLAG_SRGB_U8 = 1, 2, 4, 8
 

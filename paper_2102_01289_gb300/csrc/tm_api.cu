@@ -71,6 +71,7 @@ struct tm_ctx {
   int debug = 0;
   int hist_path = 0;
   int sweep_tiles = 0;  // TM_OPT_SWEEP_TILES (0: one wave of the sweep's CTAs per image share)
+  int sweep_width = 0;  // TM_OPT_SWEEP_WIDTH (0: automatic)
   int64_t launches = 0;
   int num_sms = 0;
   size_t smem_optin = 0;
@@ -593,17 +594,26 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   std::vector<Job> jobs((size_t)nimg);
   std::vector<JobLayout> lays((size_t)nimg);
   std::vector<size_t> offs((size_t)nimg);
-  // two sweep CTAs per SM when the shared memory allows it
-  const size_t smem_limit = std::min(c->smem_optin - 2048, (size_t)110 * 1024);
+  // strips of 512 own columns (one CTA per SM, with all of its shared memory)
+  // where every image fits them, else 256 (two CTAs per SM)
   const DevParams P0 = dev_params(c->p, 0);
-  size_t smem = 0;
-  for (int i = 0; i < nimg; ++i) {
-    Job &J = jobs[(size_t)i];
-    memset(&J, 0, sizeof J);
-    if (!plan_sweep(P0, in[i].width, in[i].height, 1, smem_limit, J.plan)) return TM_EUNSUPPORTED;
-    smem = std::max(smem, J.plan.smem);
+  int width = c->sweep_width == 256 ? 256 : 512;
+  size_t smem_limit = 0, smem = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    smem_limit = width == 512 ? c->smem_optin - 2048 : std::min(c->smem_optin - 2048, (size_t)110 * 1024);
+    smem = 0;
+    bool ok = true;
+    for (int i = 0; i < nimg && ok; ++i) {
+      Job &J = jobs[(size_t)i];
+      memset(&J, 0, sizeof J);
+      ok = plan_sweep(P0, in[i].width, in[i].height, 1, smem_limit, width, J.plan);
+      smem = std::max(smem, J.plan.smem);
+    }
+    if (ok) break;
+    if (width == 256) return TM_EUNSUPPORTED;
+    width = 256;
   }
-  const int cps = std::max(1, sweep_ctas_per_sm(c->p.n_fields, smem));
+  const int cps = std::max(1, sweep_ctas_per_sm(c->p.n_fields, smem, width));
   const int wave = c->num_sms * cps;
   size_t ws_total = 0;
   int b_range = 0, b_prep = 0, b_rows = 0, b_cols = 0, b_look = 0;
@@ -617,7 +627,7 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
     // segments' band claims even out the CTAs' work; two waves of them were
     // slower on 16 x 1 MP: 1.33 against 1.28 ms)
     const int target = c->sweep_tiles > 0 ? c->sweep_tiles : std::max(1, (int)std::lround(wave * share));
-    plan_sweep(P0, W, H, target, smem_limit, J.plan);
+    plan_sweep(P0, W, H, target, smem_limit, width, J.plan);
     integral_layout(W, H, SIZE_MAX, J.nseg, J.seg_rows);
     const size_t cnt_bytes = sweep_count_bytes(P0, J.plan, J.cnt_off);
     J.cnt_wide = J.plan.cnt_wide;
@@ -722,7 +732,7 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   TM_CUDA(c, cudaEventRecord(c->ov_fork, s));
   TM_CUDA(c, cudaStreamWaitEvent(c->sweep_stream, c->ov_fork, 0));
   TM_CUDA(c, cudaStreamWaitEvent(c->int_stream, c->ov_fork, 0));
-  const int ls = launch_sweep(P, dj, nimg, nitems, queue, smem, ctas, c->sweep_stream);
+  const int ls = launch_sweep(P, dj, nimg, nitems, queue, smem, ctas, width, c->sweep_stream);
   if (!graph) mark(c, c->sweep_stream, ST_SWEEP, m_prep);
   n += 1 + launch_integral_jobs(dj, nimg, b_rows, b_cols, c->int_stream);
   if (!graph) mark(c, c->int_stream, ST_INTEGRAL, m_prep);
@@ -1159,7 +1169,7 @@ tm_status leave_caller(tm_ctx *c, cudaStream_t s, tm_status st) {
 bool sweep_fits(tm_ctx *c, const tm_image *in) {
   SweepPlan plan;
   return plan_sweep(dev_params(c->p, 0), in->width, in->height, 1,
-                    std::min(c->smem_optin - 2048, (size_t)110 * 1024), plan);
+                    std::min(c->smem_optin - 2048, (size_t)110 * 1024), 256, plan);
 }
 
 // Automatic path of a batch's images that fit the sweep: run the batched
@@ -1684,6 +1694,17 @@ tm_status tm_set_option(tm_ctx *c, int32_t key, int64_t value) {
     if (value < 0 || value > (1 << 20)) return fail(c, TM_EINVAL, "TM_OPT_SWEEP_TILES value %lld", (long long)value);
     c->sweep_tiles = (int)value;
     drop_graph(c);
+    return TM_OK;
+  }
+  if (key == TM_OPT_SWEEP_WIDTH) {
+    if (value != 0 && value != 256 && value != 512)
+      return fail(c, TM_EINVAL, "TM_OPT_SWEEP_WIDTH value %lld (0, 256 or 512)", (long long)value);
+    if (c->sweep_width != (int)value) {
+      drop_graph(c);
+      c->path_choice.clear();  // the timed path choices saw the other width
+      c->batch_choice.clear();
+    }
+    c->sweep_width = (int)value;
     return TM_OK;
   }
   if (key == TM_OPT_HIST_PATH) {

@@ -70,18 +70,19 @@ size_t hist_scratch_bytes(int W, int H, int planes);
 int launch_integral_histogram(const uint8_t *bins, int W, int H, int n_bins, bool cumulative,
                               uint32_t *planes, void *scratch, cudaStream_t s);
 
-// Stage a3', fused: plan of one image's sweep (false if the fields do not
-// fit: a swept row over 32 chunks of 32 columns);
-// segments: the groups of bands wanted for the image (its share of a wave). Count
-// plane bytes of the plan (off[f]: byte offset of field f's plane). CTAs of
-// the sweep that fit one SM at `smem` bytes of dynamic shared memory. The
-// persistent launch over queue slots [0, nitems): every job's group starts
-// (slots itemA0 ..), then the groups' other bands (itemB0 ..).
-bool plan_sweep(const DevParams &P, int W, int H, int segments, size_t smem_limit, SweepPlan &S);
+// Stage a3', fused: plan of one image's sweep over strips of `width` (256 or
+// 512) own columns (false if the fields do not fit: a swept row over 32
+// chunks of 32 columns); segments: the groups of bands wanted for the image
+// (its share of a wave). Count plane bytes of the plan (off[f]: byte offset
+// of field f's plane). CTAs of the sweep that fit one SM at `smem` bytes of
+// dynamic shared memory. The persistent launch over queue slots [0, nitems):
+// every job's group starts (slots itemA0 ..), then the groups' other bands
+// (itemB0 ..); every job's plan has the launch's width.
+bool plan_sweep(const DevParams &P, int W, int H, int segments, size_t smem_limit, int width, SweepPlan &S);
 size_t sweep_count_bytes(const DevParams &P, const SweepPlan &S, long long *off);
-int sweep_ctas_per_sm(int n_fields, size_t smem);
+int sweep_ctas_per_sm(int n_fields, size_t smem, int width);
 int launch_sweep(const DevParams &P, const Job *jobs, int njobs, int nitems, int *queue, size_t smem, int ctas,
-                 cudaStream_t s);
+                 int width, cudaStream_t s);
 
 // Stage a4: per-pixel lookup, tone curve, fusion and colour restoration.
 int lookup_blocks(int W, int H);

@@ -53,11 +53,7 @@
 namespace tmk {
 namespace {
 
-constexpr int kNT = 512;
-constexpr int kWarps = kNT / 32;
-constexpr int kTX = 256;            // own columns of a tile; threads t and t + 256 share column t
 constexpr int kMaxChunks = 32;      // 32-column chunks of a swept row
-constexpr int kChunksPerWarp = kMaxChunks / kWarps;
 constexpr int kMaxRows = 2047;      // swept rows of a tile
 constexpr unsigned kPTMask = (1u << 21) - 1;
 constexpr int kPStride = 33;        // words per threshold row of PT | m << 21
@@ -68,7 +64,15 @@ constexpr int kPStride = 33;        // words per threshold row of PT | m << 21
 // 0.486, 0.469, 0.463, 0.453 and 0.466 ms (uniform tiles: 0.467).
 constexpr int kBandsPerGroup = 8;
 
-static_assert(2 * kTX == kNT, "one top and one bottom event thread per own column");
+// A strip has TX own columns (256 or 512) and its CTA 2 TX threads: threads
+// t and t + TX take the top and bottom events of column t.
+template <int TX>
+struct Shape {
+  static constexpr int NT = 2 * TX, Warps = NT / 32, ChunksPerWarp = kMaxChunks / Warps;
+  // 256: two 512-thread CTAs per SM; 512: one 1024-thread CTA
+  static constexpr int MinBlocks = TX == 256 ? 2 : 1;
+  static_assert(ChunksPerWarp * Warps == kMaxChunks, "every chunk has a warp");
+};
 
 // The sweep's dynamic shared memory (named at file scope so that every access
 // compiles to a shared-memory load or store).
@@ -119,14 +123,15 @@ __device__ __forceinline__ unsigned pair_value(const unsigned *PT, const unsigne
 // a window reaching above or below the segment takes its rows there from
 // the other segments, each adding E(last row of the window in the segment) -
 // E(row above the first) to the pixel's count.
-template <int NF>
+template <int NF, int TX>
 __device__ __forceinline__ void sweep_tile(const DevParams &P, const Job &J, int strip, int band) {
   __shared__ int ext_sh, next_sh, ext_end_sh;  // the claim state lives in shared memory, off the registers
   unsigned char *const smem = g_smem;
   const SweepPlan &S = J.plan;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int W = S.W, H = S.H;
-  const int X0 = strip * kTX, X1 = min(X0 + kTX, W);
+  constexpr int kNT = Shape<TX>::NT, kWarps = Shape<TX>::Warps, kChunksPerWarp = Shape<TX>::ChunksPerWarp;
+  const int X0 = strip * TX, X1 = min(X0 + TX, W);
   const int Y0 = band * S.TY;
   int Y1 = min(Y0 + S.TY, H);
   // the group's bands from this one on; the rows the segment can reach
@@ -198,8 +203,8 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const Job &J, int
 
   // ---- the thread's event column: windows opening below a swept row
   // (tid < 256: subtract E) or closing on it (add E) ----
-  const int xo = tid & (kTX - 1);
-  const bool is_close = tid >= kTX;
+  const int xo = tid & (TX - 1);
+  const bool is_close = tid >= TX;
   const int x = X0 + xo;
   const bool col_ok = x < X1;
   // per field: half-height, corner columns (relative to 32 g0; jl = -1 is the
@@ -347,7 +352,7 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const Job &J, int
     // below it adds E(Y1 - 1). Each thread walks its event column (the corner
     // columns are the ones its events use) over every other row, four rows at
     // a time
-    const int vlast = Y1 - 1, par = tid >> 8;
+    const int vlast = Y1 - 1, par = is_close ? 1 : 0;
     if (col_ok) {
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
@@ -391,9 +396,9 @@ __device__ __forceinline__ void second_phase_band(const SweepPlan &S, int local,
   strip = band = -1;
 }
 
-template <int NF>
-__global__ void __launch_bounds__(kNT, 2) k_sweep(DevParams P, const Job *__restrict__ jobs, int njobs,
-                                                  int nitems, int *queue) {
+template <int NF, int TX>
+__global__ void __launch_bounds__(Shape<TX>::NT, Shape<TX>::MinBlocks)
+    k_sweep(DevParams P, const Job *__restrict__ jobs, int njobs, int nitems, int *queue) {
   __shared__ int item_sh, job_sh, strip_sh, band_sh, won_sh;
   for (;;) {
     if (threadIdx.x == 0) {
@@ -403,7 +408,7 @@ __global__ void __launch_bounds__(kNT, 2) k_sweep(DevParams P, const Job *__rest
     __syncthreads();
     const int it = item_sh;
     if (it >= nitems) break;
-    for (int j = threadIdx.x; j < njobs; j += kNT)
+    for (int j = threadIdx.x; j < njobs; j += Shape<TX>::NT)
       if ((jobs[j].itemA0 <= it && it < jobs[j].itemA0 + jobs[j].nitemA) ||
           (jobs[j].itemB0 <= it && it < jobs[j].itemB0 + jobs[j].nitemB))
         job_sh = j;
@@ -424,7 +429,7 @@ __global__ void __launch_bounds__(kNT, 2) k_sweep(DevParams P, const Job *__rest
       won_sh = band >= 0 && atomicExch(J.claim + band * J.plan.tiles_x + strip, 1) == 0;
     }
     __syncthreads();
-    if (jb >= 0 && won_sh) sweep_tile<NF>(P, jobs[jb], strip_sh, band_sh);
+    if (jb >= 0 && won_sh) sweep_tile<NF, TX>(P, jobs[jb], strip_sh, band_sh);
     __syncthreads();  // the shared slot fields are rewritten for the next item
   }
 }
@@ -433,7 +438,8 @@ size_t smem_for(int kcap, int bstride) { return layout(kcap).B + (size_t)kcap * 
 
 }  // namespace
 
-bool plan_sweep(const DevParams &P, int W, int H, int segments, size_t smem_limit, SweepPlan &S) {
+bool plan_sweep(const DevParams &P, int W, int H, int segments, size_t smem_limit, int width, SweepPlan &S) {
+  if (width != 256 && width != 512) return false;
   SweepPlan s{};
   s.W = W;
   s.H = H;
@@ -444,13 +450,13 @@ bool plan_sweep(const DevParams &P, int W, int H, int segments, size_t smem_limi
   }
   s.Rx = Rx;
   s.Ry = Ry;
-  s.TX = kTX;
-  s.tiles_x = (W + kTX - 1) / kTX;
-  // widest swept row: a strip of 256 columns widened by Rx + 1 on the left and
+  s.TX = width;
+  s.tiles_x = (W + width - 1) / width;
+  // widest swept row: a strip of `width` columns widened by Rx + 1 on the left and
   // Rx on the right, rounded out to 32-column chunks
   int nch_max = 0;
   for (int strip = 0; strip < s.tiles_x; ++strip) {
-    const int X0 = strip * kTX, X1 = min(X0 + kTX, W);
+    const int X0 = strip * width, X1 = min(X0 + width, W);
     const int cL = max(X0 - Rx - 1, -1), cR = min(X1 - 1 + Rx, W - 1);
     nch_max = max(nch_max, (cR >> 5) - ((cL + 1) >> 5) + 1);
   }
@@ -489,23 +495,25 @@ size_t sweep_count_bytes(const DevParams &P, const SweepPlan &S, long long *off)
   return o;
 }
 
-template <int NF>
+template <int NF, int TX>
 static int launch_nf(const DevParams &P, const Job *jobs, int njobs, int nitems, int *queue, size_t smem,
                      int ctas, cudaStream_t s) {
-  if (cudaFuncSetAttribute(k_sweep<NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (cudaFuncSetAttribute(k_sweep<NF, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return -1;
-  k_sweep<NF><<<ctas, kNT, smem, s>>>(P, jobs, njobs, nitems, queue);
+  k_sweep<NF, TX><<<ctas, Shape<TX>::NT, smem, s>>>(P, jobs, njobs, nitems, queue);
   return 1;
 }
 
-int sweep_ctas_per_sm(int n_fields, size_t smem) {
+template <int TX>
+static int ctas_per_sm(int n_fields, size_t smem) {
   int per = 0;
   cudaError_t e;
   switch (n_fields) {
-#define TM_OCC(nf)                                                                                    \
-  case nf:                                                                                            \
-    e = cudaFuncSetAttribute(k_sweep<nf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep<nf>, kNT, smem); \
+#define TM_OCC(nf)                                                                                          \
+  case nf:                                                                                                  \
+    e = cudaFuncSetAttribute(k_sweep<nf, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
+    if (e == cudaSuccess)                                                                                   \
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep<nf, TX>, Shape<TX>::NT, smem);      \
     break;
     TM_OCC(1) TM_OCC(2) TM_OCC(3) TM_OCC(4) TM_OCC(5) TM_OCC(6) TM_OCC(7) TM_OCC(8)
 #undef TM_OCC
@@ -518,19 +526,30 @@ int sweep_ctas_per_sm(int n_fields, size_t smem) {
   return per;
 }
 
-int launch_sweep(const DevParams &P, const Job *jobs, int njobs, int nitems, int *queue, size_t smem, int ctas,
-                 cudaStream_t s) {
-  cudaMemsetAsync(queue, 0, sizeof(int), s);
+template <int TX>
+static int launch_width(const DevParams &P, const Job *jobs, int njobs, int nitems, int *queue, size_t smem,
+                        int ctas, cudaStream_t s) {
   switch (P.n_fields) {
-    case 1: return launch_nf<1>(P, jobs, njobs, nitems, queue, smem, ctas, s);
-    case 2: return launch_nf<2>(P, jobs, njobs, nitems, queue, smem, ctas, s);
-    case 3: return launch_nf<3>(P, jobs, njobs, nitems, queue, smem, ctas, s);
-    case 4: return launch_nf<4>(P, jobs, njobs, nitems, queue, smem, ctas, s);
-    case 5: return launch_nf<5>(P, jobs, njobs, nitems, queue, smem, ctas, s);
-    case 6: return launch_nf<6>(P, jobs, njobs, nitems, queue, smem, ctas, s);
-    case 7: return launch_nf<7>(P, jobs, njobs, nitems, queue, smem, ctas, s);
-    default: return launch_nf<8>(P, jobs, njobs, nitems, queue, smem, ctas, s);
+    case 1: return launch_nf<1, TX>(P, jobs, njobs, nitems, queue, smem, ctas, s);
+    case 2: return launch_nf<2, TX>(P, jobs, njobs, nitems, queue, smem, ctas, s);
+    case 3: return launch_nf<3, TX>(P, jobs, njobs, nitems, queue, smem, ctas, s);
+    case 4: return launch_nf<4, TX>(P, jobs, njobs, nitems, queue, smem, ctas, s);
+    case 5: return launch_nf<5, TX>(P, jobs, njobs, nitems, queue, smem, ctas, s);
+    case 6: return launch_nf<6, TX>(P, jobs, njobs, nitems, queue, smem, ctas, s);
+    case 7: return launch_nf<7, TX>(P, jobs, njobs, nitems, queue, smem, ctas, s);
+    default: return launch_nf<8, TX>(P, jobs, njobs, nitems, queue, smem, ctas, s);
   }
+}
+
+int sweep_ctas_per_sm(int n_fields, size_t smem, int width) {
+  return width == 512 ? ctas_per_sm<512>(n_fields, smem) : ctas_per_sm<256>(n_fields, smem);
+}
+
+int launch_sweep(const DevParams &P, const Job *jobs, int njobs, int nitems, int *queue, size_t smem, int ctas,
+                 int width, cudaStream_t s) {
+  cudaMemsetAsync(queue, 0, sizeof(int), s);
+  return width == 512 ? launch_width<512>(P, jobs, njobs, nitems, queue, smem, ctas, s)
+                      : launch_width<256>(P, jobs, njobs, nitems, queue, smem, ctas, s);
 }
 
 }  // namespace tmk

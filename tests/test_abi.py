@@ -108,6 +108,8 @@ def test_forward_rejects_bad_descriptors_without_launch(built):
         assert L.tm_integral_histogram(None, 4, 4, 8, None, None) == tm.TM_EINVAL
         assert L.tm_integral_image(None, 4, 4, None, None, None) == tm.TM_EINVAL
         assert L.tm_set_option(ctx, tm.TM_OPT_HIST_PATH, 9) == tm.TM_EINVAL
+        assert L.tm_set_option(ctx, tm.TM_OPT_SWEEP_WIDTH, 300) == tm.TM_EINVAL
+        assert L.tm_set_option(ctx, tm.TM_OPT_SWEEP_WIDTH, 512) == tm.TM_OK
         n = ctypes.c_size_t()
         assert L.tm_debug_size(ctx, tm.TM_DBG_BINS, ctypes.byref(n)) == tm.TM_ESTATE
     finally:

@@ -460,14 +460,16 @@ def test_inclusive_cdf_on_the_sweep_at_full_bin_range(orc):
     assert_out_close(out, ref)
 
 
+@pytest.mark.parametrize("width", [256, 512])
 @pytest.mark.parametrize("segments", [0, 12, 200])
-def test_sweep_segments_and_threshold_passes(orc, segments):
+def test_sweep_segments_and_threshold_passes(orc, segments, width):
     """The sweep's segments run on over the bands they claim; CTAs that finish
     early take the rest. A 1500-column image with 256 bins over ten decades
     has tiles whose bins span more thresholds than the shared memory holds
     (several passes: such a segment claims its group's bands up front).
     Counts bit-exact and output within tolerance at every tiling (0: the
-    automatic one; 12 and 200 segments: long and short bands)."""
+    automatic one; 12 and 200 segments: long and short bands) and at both
+    strip widths (256: six strips, the last ragged; 512: three)."""
     img = synth.wdr_image(240, 1500, seed=7, decades=(-4.0, 6.0))
     gp, op = params_pair(orc, 256, [3, 20])
     x = torch.from_numpy(np.ascontiguousarray(img)).cuda()
@@ -476,10 +478,35 @@ def test_sweep_segments_and_threshold_passes(orc, segments):
         tm.tm_set_debug(ctx, 1)
         tm.tm_set_option(ctx, tm.TM_OPT_HIST_PATH, 1)
         tm.tm_set_option(ctx, tm.TM_OPT_SWEEP_TILES, segments)
+        tm.tm_set_option(ctx, tm.TM_OPT_SWEEP_WIDTH, width)
         out = torch.empty_like(x)
         for _ in range(2):  # the claims are cleared for every call
             tm.tm_forward(ctx, x, out)
         cnt = tm.tm_debug_export(ctx, tm.TM_DBG_COUNTS).cpu().numpy().view(np.uint32).reshape(2, 240, 1500)
+        torch.cuda.synchronize()
+    finally:
+        tm.tm_destroy(ctx)
+    ref, fl = orc.forward(img, op)
+    assert np.array_equal(cnt, fl.cnt)
+    assert_out_close(out.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("width", [0, 512])
+def test_sweep_wide_fields_take_narrow_strips(orc, width):
+    """A half-width of 300 does not fit a 512-column strip's swept row (32
+    chunks of 32 columns), so the sweep runs on 256-column strips whatever
+    width is asked for; counts bit-exact, output within tolerance."""
+    img = synth.wdr_image(200, 1400, seed=71)
+    gp, op = params_pair(orc, 32, [5, 300])
+    x = torch.from_numpy(np.ascontiguousarray(img)).cuda()
+    ctx = tm.tm_create(gp)
+    try:
+        tm.tm_set_debug(ctx, 1)
+        tm.tm_set_option(ctx, tm.TM_OPT_HIST_PATH, 1)
+        tm.tm_set_option(ctx, tm.TM_OPT_SWEEP_WIDTH, width)
+        out = torch.empty_like(x)
+        tm.tm_forward(ctx, x, out)
+        cnt = tm.tm_debug_export(ctx, tm.TM_DBG_COUNTS).cpu().numpy().view(np.uint32).reshape(2, 200, 1400)
         torch.cuda.synchronize()
     finally:
         tm.tm_destroy(ctx)
