@@ -743,7 +743,15 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   TM_CUDA(c, cudaStreamWaitEvent(s, c->ov_int, 0));
   if (!graph) mark(c, s, kNoStage);  // the join: the lookup is timed from here
   if (do_lookup) {
-    n += launch_lookup_counts(P, dj, nimg, b_look, s);
+    // the lookup variant: without debug planes and moments, and for one dtype
+    // of every input and output when they share it
+    bool wide = true;
+    int dt = jobs[0].in.dtype;
+    for (const Job &J : jobs) {
+      wide = wide && J.cnt_wide == (1 << c->p.n_fields) - 1;
+      if (J.in.dtype != dt || J.out.dtype != dt) dt = -1;
+    }
+    n += launch_lookup_counts(P, dj, nimg, b_look, !debug && !keep_mom && wide, dt, s);
     if (!graph) mark(c, s, ST_LOOKUP);
   }
   if (graph) {

@@ -158,10 +158,12 @@ __device__ __forceinline__ float luminance(float r, float g, float b) {
   return fmaxf(i, kLumFloor);
 }
 
+// kDt: the image's dtype when known at compile time (-1: read from im).
+template <int kDt = -1>
 __device__ __forceinline__ void load_rgb(const Image &im, int x, int y, float &r,
                                          float &g, float &b) {
   long long o = (long long)y * im.pitch + 3LL * x;
-  if (im.dtype == kF16) {
+  if ((kDt >= 0 ? kDt : im.dtype) == kF16) {
     const __half *p = static_cast<const __half *>(im.p) + o;
     r = __half2float(p[0]);
     g = __half2float(p[1]);
@@ -180,15 +182,17 @@ __device__ __forceinline__ float srgb_encode(float c) {
   return c <= 0.0031308f ? 12.92f * c : 1.055f * powf(c, 1.f / 2.4f) - 0.055f;
 }
 
+template <int kDt = -1>
 __device__ __forceinline__ void store_rgb(const Image &im, int x, int y, float r,
                                           float g, float b, bool srgb = false) {
   long long o = (long long)y * im.pitch + 3LL * x;
-  if (im.dtype == kF32) {
+  const int dt = kDt >= 0 ? kDt : im.dtype;
+  if (dt == kF32) {
     float *p = static_cast<float *>(im.p) + o;
     p[0] = r;
     p[1] = g;
     p[2] = b;
-  } else if (im.dtype == kF16) {
+  } else if (dt == kF16) {
     __half *p = static_cast<__half *>(im.p) + o;
     p[0] = __float2half_rn(r);
     p[1] = __float2half_rn(g);
@@ -366,6 +370,9 @@ struct WinMoments {
   float rarea, var;
   long long q1;
 };
+// kLit = false: the caller guarantees TM_FLAG_AREA_LITERAL is off (the
+// padding terms are then not compiled in).
+template <bool kLit = true>
 __device__ __forceinline__ WinMoments window_moments(const DevParams &P, int f, int x, int y, int W, int H,
                                                      const longlong2 *__restrict__ s12, int qbits,
                                                      float inv_scale2) {
@@ -380,7 +387,7 @@ __device__ __forceinline__ WinMoments window_moments(const DevParams &P, int f, 
                              (unsigned long long)a.x);
   long long q2 = (long long)((unsigned long long)c.y - (unsigned long long)d.y - (unsigned long long)b.y +
                              (unsigned long long)a.y);
-  literal_area(P, f, qbits, q1, q2, N);
+  if (kLit) literal_area(P, f, qbits, q1, q2, N);
   WinMoments m;
   m.rarea = __fdividef(1.f, (float)(unsigned)N);  // N <= 65535^2 < 2^32
   m.var = window_variance(q1, q2, N, m.rarea, inv_scale2);

@@ -22,14 +22,16 @@ struct Fusion {
 // into the Eq. 3 sums (the same arithmetic as fuse_fields, one field at a
 // time, so no per-field state is kept).
 // mom (or null): receives the window's variance and mean of lhat for the
-// backward (inv_scale = 2^-Q).
+// backward (inv_scale = 2^-Q). kPlain: no debug planes, no moments and no
+// literal area (those paths are then not compiled in).
+template <bool kPlain = false>
 __device__ __forceinline__ void fold_field(const DevParams &P, int f, int x, int y, int W, int H,
                                            unsigned cnt, const longlong2 *__restrict__ s12, int qbits,
                                            float inv_scale2, Fusion &fu, const DebugPlanes &dbg,
                                            float2 *mom = nullptr, float inv_scale = 0.f) {
-  const WinMoments m = window_moments(P, f, x, y, W, H, s12, qbits, inv_scale2);
+  const WinMoments m = window_moments<!kPlain>(P, f, x, y, W, H, s12, qbits, inv_scale2);
   const float rarea = m.rarea, var = m.var;
-  if (mom)
+  if (!kPlain && mom)
     mom[(size_t)f * W * H + (size_t)y * W + x] = make_float2(var, window_mean(m.q1, rarea, inv_scale));
   const float Pf = (float)cnt * rarea;                                  // Eq. 1
   const float Lf = fmaf(P.ld_max - P.ld_min, Pf, P.ld_min);             // Eq. 2
@@ -37,7 +39,7 @@ __device__ __forceinline__ void fold_field(const DevParams &P, int f, int x, int
   fu.wsum += Wf;
   fu.acc = fmaf(Wf, Lf, fu.acc);
   fu.mean += Lf;
-  if (dbg.l) {
+  if (!kPlain && dbg.l) {
     const long long N = (long long)W * H, pix = (long long)y * W + x;
     dbg.cnt[f * N + pix] = cnt;
     dbg.sigma2[f * N + pix] = var;
@@ -46,17 +48,19 @@ __device__ __forceinline__ void fold_field(const DevParams &P, int f, int x, int
   }
 }
 
-// Eq. 3 and Eq. 12 for one pixel from the folded sums.
+// Eq. 3 and Eq. 12 for one pixel from the folded sums. kDt: the dtype of
+// both images when known at compile time (-1: read from the descriptors).
+template <bool kPlain = false, int kDt = -1>
 __device__ __forceinline__ void finish_pixel(const Image &in, const Image &out, const DevParams &P,
                                              int x, int y, const Fusion &fu, const DebugPlanes &dbg) {
   const float L = fu.wsum > 0.f ? __fdividef(fu.acc, fu.wsum)
                                 : __fdividef(fu.mean, (float)P.n_fields);  // Eq. 3
   float r, g, b;
-  load_rgb(in, x, y, r, g, b);
+  load_rgb<kDt>(in, x, y, r, g, b);
   const float inv_i = __fdividef(1.f, luminance(r, g, b));
-  store_rgb(out, x, y, restore_channel(r, inv_i, P.sat, L), restore_channel(g, inv_i, P.sat, L),
-            restore_channel(b, inv_i, P.sat, L), (P.flags & kFlagSrgb) != 0);
-  if (dbg.l) dbg.l[(long long)y * in.W + x] = L;
+  store_rgb<kDt>(out, x, y, restore_channel(r, inv_i, P.sat, L), restore_channel(g, inv_i, P.sat, L),
+                 restore_channel(b, inv_i, P.sat, L), (P.flags & kFlagSrgb) != 0);
+  if (!kPlain && dbg.l) dbg.l[(long long)y * in.W + x] = L;
 }
 
 // Eight blocks per SM (32 registers, a few spilled at five fields and more)
@@ -97,7 +101,13 @@ __global__ void __launch_bounds__(256, 8)
 // (image, 32 x 8 pixel tile). NF = number of fields, so the field loop is
 // straight-line code and the loads of all fields can be issued together.
 // Eight blocks per SM (32 registers) keep more of those loads in flight.
-template <int NF>
+// kPlain: no job has debug planes or window moments, every count plane is
+// uint32 and the literal area is off; kDt: the dtype of every job's input
+// and output when they all share one (-1: read from the descriptors).
+// Specialising drops the paths a launch does not take: the compiler would
+// otherwise predicate some of them into every pixel (at 12 MP the plain
+// float32 variant took 0.211 ms against 0.247).
+template <int NF, bool kPlain, int kDt>
 __global__ void __launch_bounds__(256, 8) k_lookup_counts(DevParams P, const Job *__restrict__ jobs, int njobs) {
   const int j = find_job(jobs, njobs, kStLook, blockIdx.x);
   const Job &J = jobs[j];
@@ -113,11 +123,12 @@ __global__ void __launch_bounds__(256, 8) k_lookup_counts(DevParams P, const Job
   Fusion fu;
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
-    const unsigned cnt = load_count(J, f, pix);
-    fold_field(P, f, x, y, W, H, cnt, reinterpret_cast<const longlong2 *>(J.s1), J.qbits, inv_scale2, fu,
-               J.dbg, J.mom, inv_scale);
+    const unsigned cnt = kPlain ? __ldg(reinterpret_cast<const unsigned *>(J.cnt + J.cnt_off[f]) + pix)
+                                : load_count(J, f, pix);
+    fold_field<kPlain>(P, f, x, y, W, H, cnt, reinterpret_cast<const longlong2 *>(J.s1), J.qbits, inv_scale2,
+                       fu, J.dbg, J.mom, inv_scale);
   }
-  finish_pixel(J.in, J.out, P, x, y, fu, J.dbg);
+  finish_pixel<kPlain, kDt>(J.in, J.out, P, x, y, fu, J.dbg);
 }
 
 }  // namespace
@@ -140,17 +151,30 @@ int launch_lookup_materialised(const Image &in, const Image &out, const DevParam
 
 int lookup_blocks(int W, int H) { return ((W + 31) / 32) * ((H + 7) / 8); }
 
-int launch_lookup_counts(const DevParams &P, const Job *jobs, int njobs, int blocks, cudaStream_t s) {
+template <bool kPlain, int kDt>
+static void launch_counts(const DevParams &P, const Job *jobs, int njobs, int blocks, cudaStream_t s) {
   switch (P.n_fields) {
-    case 1: k_lookup_counts<1><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
-    case 2: k_lookup_counts<2><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
-    case 3: k_lookup_counts<3><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
-    case 4: k_lookup_counts<4><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
-    case 5: k_lookup_counts<5><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
-    case 6: k_lookup_counts<6><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
-    case 7: k_lookup_counts<7><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
-    default: k_lookup_counts<8><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
+    case 1: k_lookup_counts<1, kPlain, kDt><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
+    case 2: k_lookup_counts<2, kPlain, kDt><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
+    case 3: k_lookup_counts<3, kPlain, kDt><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
+    case 4: k_lookup_counts<4, kPlain, kDt><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
+    case 5: k_lookup_counts<5, kPlain, kDt><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
+    case 6: k_lookup_counts<6, kPlain, kDt><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
+    case 7: k_lookup_counts<7, kPlain, kDt><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
+    default: k_lookup_counts<8, kPlain, kDt><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
   }
+}
+
+int launch_lookup_counts(const DevParams &P, const Job *jobs, int njobs, int blocks, bool plain, int dtype,
+                         cudaStream_t s) {
+  if (!plain || (P.flags & kFlagAreaLit))
+    launch_counts<false, -1>(P, jobs, njobs, blocks, s);
+  else if (dtype == kF32)
+    launch_counts<true, kF32>(P, jobs, njobs, blocks, s);
+  else if (dtype == kF16)
+    launch_counts<true, kF16>(P, jobs, njobs, blocks, s);
+  else
+    launch_counts<true, -1>(P, jobs, njobs, blocks, s);
   return 1;
 }
 

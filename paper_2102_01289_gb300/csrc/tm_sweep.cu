@@ -123,7 +123,8 @@ __device__ __forceinline__ unsigned pair_value(const unsigned *PT, const unsigne
 // a window reaching above or below the segment takes its rows there from
 // the other segments, each adding E(last row of the window in the segment) -
 // E(row above the first) to the pixel's count.
-template <int NF, int TX>
+// kIncl: TM_FLAG_CDF_INCLUSIVE (the threshold is b + 1 instead of b).
+template <int NF, int TX, bool kIncl>
 __device__ __forceinline__ void sweep_tile(const DevParams &P, const Job &J, int strip, int band) {
   __shared__ int ext_sh, next_sh, ext_end_sh;  // the claim state lives in shared memory, off the registers
   unsigned char *const smem = g_smem;
@@ -142,7 +143,8 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const Job &J, int
   const int g0 = (cL + 1) >> 5;
   const int nch = (cR >> 5) - g0 + 1;
   const int rL = Y0 - 1;  // origin row
-  const int n = P.n_bins, incl = (P.flags & kFlagCdfIncl) ? 1 : 0;
+  const int n = P.n_bins;
+  constexpr int incl = kIncl ? 1 : 0;
   const int kcap = S.kcap, bstride = S.bstride;
   const Lay L = layout(kcap);
   unsigned *const sPT = reinterpret_cast<unsigned *>(smem + L.PT);
@@ -233,16 +235,18 @@ __device__ __forceinline__ void sweep_tile(const DevParams &P, const Job &J, int
       for (int i = tid; i < words; i += kNT) b32[i] = 0u;
     }
     // E at swept row v for threshold k = b + incl (corner columns cjr, cjl);
-    // false when the threshold belongs to another pass
+    // false when there is nothing to add: the threshold belongs to another
+    // pass, or it is 0 (nothing lies below it)
     auto event_value = [&](int b, int cjr, int cjl, int v, unsigned &E) -> bool {
       const int k = b + incl, kk = k - kp0;
       if ((unsigned)kk < (unsigned)nKp) {
         E = pair_value(sPT, sM, sB, bstride, kk, cjr, cjl);
         return true;
       }
-      // thresholds 0 (nothing below) and n (the whole window) in the first pass
-      E = k <= 0 ? 0u : (unsigned)(cjr - cjl) * (unsigned)(v - rL);
-      return specials && (k <= 0 || k >= n);
+      if (!kIncl) return false;  // k <= n - 1 here: only k = 0 is left, or another pass
+      // threshold n (the whole window) in the first pass
+      E = (unsigned)(cjr - cjl) * (unsigned)(v - rL);
+      return specials && k >= n;
     };
     // bins of a swept row, a warp per chunk (wid, wid + 16; 256 marks columns
     // past the image), and the chunks' bin ranges (lanes = chunks) from the
@@ -396,7 +400,7 @@ __device__ __forceinline__ void second_phase_band(const SweepPlan &S, int local,
   strip = band = -1;
 }
 
-template <int NF, int TX>
+template <int NF, int TX, bool kIncl>
 __global__ void __launch_bounds__(Shape<TX>::NT, Shape<TX>::MinBlocks)
     k_sweep(DevParams P, const Job *__restrict__ jobs, int njobs, int nitems, int *queue) {
   __shared__ int item_sh, job_sh, strip_sh, band_sh, won_sh;
@@ -429,7 +433,7 @@ __global__ void __launch_bounds__(Shape<TX>::NT, Shape<TX>::MinBlocks)
       won_sh = band >= 0 && atomicExch(J.claim + band * J.plan.tiles_x + strip, 1) == 0;
     }
     __syncthreads();
-    if (jb >= 0 && won_sh) sweep_tile<NF, TX>(P, jobs[jb], strip_sh, band_sh);
+    if (jb >= 0 && won_sh) sweep_tile<NF, TX, kIncl>(P, jobs[jb], strip_sh, band_sh);
     __syncthreads();  // the shared slot fields are rewritten for the next item
   }
 }
@@ -498,9 +502,10 @@ size_t sweep_count_bytes(const DevParams &P, const SweepPlan &S, long long *off)
 template <int NF, int TX>
 static int launch_nf(const DevParams &P, const Job *jobs, int njobs, int nitems, int *queue, size_t smem,
                      int ctas, cudaStream_t s) {
-  if (cudaFuncSetAttribute(k_sweep<NF, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return -1;
-  k_sweep<NF, TX><<<ctas, Shape<TX>::NT, smem, s>>>(P, jobs, njobs, nitems, queue);
+  const bool incl = (P.flags & kFlagCdfIncl) != 0;
+  auto *k = incl ? k_sweep<NF, TX, true> : k_sweep<NF, TX, false>;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
+  k<<<ctas, Shape<TX>::NT, smem, s>>>(P, jobs, njobs, nitems, queue);
   return 1;
 }
 
@@ -511,9 +516,9 @@ static int ctas_per_sm(int n_fields, size_t smem) {
   switch (n_fields) {
 #define TM_OCC(nf)                                                                                          \
   case nf:                                                                                                  \
-    e = cudaFuncSetAttribute(k_sweep<nf, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
+    e = cudaFuncSetAttribute(k_sweep<nf, TX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
     if (e == cudaSuccess)                                                                                   \
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep<nf, TX>, Shape<TX>::NT, smem);      \
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep<nf, TX, false>, Shape<TX>::NT, smem); \
     break;
     TM_OCC(1) TM_OCC(2) TM_OCC(3) TM_OCC(4) TM_OCC(5) TM_OCC(6) TM_OCC(7) TM_OCC(8)
 #undef TM_OCC
