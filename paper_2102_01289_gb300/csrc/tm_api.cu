@@ -743,15 +743,15 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   TM_CUDA(c, cudaStreamWaitEvent(s, c->ov_int, 0));
   if (!graph) mark(c, s, kNoStage);  // the join: the lookup is timed from here
   if (do_lookup) {
-    // the lookup variant: without debug planes and moments, and for one dtype
-    // of every input and output when they share it
+    // the lookup variant: without debug planes, with or without the moments,
+    // and for one dtype of every input and output when they share it
     bool wide = true;
     int dt = jobs[0].in.dtype;
     for (const Job &J : jobs) {
       wide = wide && J.cnt_wide == (1 << c->p.n_fields) - 1;
       if (J.in.dtype != dt || J.out.dtype != dt) dt = -1;
     }
-    n += launch_lookup_counts(P, dj, nimg, b_look, !debug && !keep_mom && wide, dt, s);
+    n += launch_lookup_counts(P, dj, nimg, b_look, !debug && wide, keep_mom, dt, s);
     if (!graph) mark(c, s, ST_LOOKUP);
   }
   if (graph) {
@@ -1089,10 +1089,12 @@ tm_status backward_images(tm_ctx *c, int n, const tm_image *in, const tm_image *
     FixJob *dfj = reinterpret_cast<FixJob *>(desc + sizeof(BwdJob) * (size_t)m);
     char *o = b + head;
     int pix = 0, inb = 0, tiles = 0, cols = 0;
+    bool plain = true;  // float32 inputs and uint32 count planes throughout the group
     for (int r = 0; r < m; ++r) {
       const int i = i0 + r;
       const Job &J = jobs[(size_t)i];
       const int W = J.in.W, H = J.in.H;
+      plain = plain && J.in.dtype == kF32 && J.cnt_wide == (1 << nf) - 1;
       const size_t N = (size_t)W * H, plane = (size_t)(W + 1) * (H + 1);
       BwdJob &B = bj[(size_t)r];
       B = BwdJob{};
@@ -1140,11 +1142,11 @@ tm_status backward_images(tm_ctx *c, int n, const tm_image *in, const tm_image *
     if (launch_backward_setup(hd, hdesc.size() * sizeof(uint4), desc, accs, m, gsum, k == 0, s) < 0)
       return fail(c, TM_EINVAL, "backward group descriptors exceed %d bytes", kBwdDescBytes);
     const DevParams P = dev_params(c->p, jobs[(size_t)i0].qbits);
-    launches += 1 + launch_backward_pixel(P, dbj, m, pix, jobs[(size_t)i0].mom != nullptr, gsum, s);
+    launches += 1 + launch_backward_pixel(P, dbj, m, pix, jobs[(size_t)i0].mom != nullptr, plain, gsum, s);
     mark(c, s, ST_BWD_PIXEL);
     launches += launch_fix_integrals(dfj, m, tiles, cols, s);
     mark(c, s, ST_BWD_ADJOINT);
-    launches += launch_backward_input(P, dbj, m, inb, gsum, k + 2 == grp.size() ? grad_params : nullptr, s);
+    launches += launch_backward_input(P, dbj, m, inb, plain, gsum, k + 2 == grp.size() ? grad_params : nullptr, s);
     mark(c, s, ST_BWD_INPUT);
   }
   if ((st = check_launch(c, "backward launch"))) return st;

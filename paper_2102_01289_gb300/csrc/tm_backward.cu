@@ -86,7 +86,9 @@ __global__ void k_bwd_setup(const __grid_constant__ Pack p, int words, unsigned 
 // largest |u_f|, |v_f| (for the fixed-point scales). NF = number of fields
 // (so every per-field array lives in registers).
 // MOM: the window variances and means come from the forward's planes.
-template <int NF, bool MOM>
+// kPlain: the literal area is off, every count plane is uint32 and every
+// input is float32 (the other paths are then not compiled in).
+template <int NF, bool MOM, bool kPlain>
 __global__ void __launch_bounds__(kBT, kMinBlocksPix) k_bwd_pixel(DevParams P, const BwdJob *__restrict__ jobs, int njobs,
                                                    double *__restrict__ gsum) {
   constexpr int kA = 3 + 2 * NF;  // [ld_min, ld_max, sat, eps[NF], alpha[NF]], the layout of gsum
@@ -118,14 +120,15 @@ __global__ void __launch_bounds__(kBT, kMinBlocksPix) k_bwd_pixel(DevParams P, c
       float wsum = 0.f, accL = 0.f, meanL = 0.f;
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
-        const unsigned cnt = load_count(J, f, pix);
+        const unsigned cnt = kPlain ? __ldg(reinterpret_cast<const unsigned *>(J.cnt + J.cnt_off[f]) + pix)
+                                    : load_count(J, f, pix);
         if (MOM) {
           const float2 vm = __ldg(J.mom + f * N + pix);
           var[f] = vm.x;
           mu[f] = vm.y;
-          rarea[f] = __fdividef(1.f, window_area(P, f, x, y, W, H));
+          rarea[f] = __fdividef(1.f, window_area<!kPlain>(P, f, x, y, W, H));
         } else {
-          const WinMoments m = window_moments(P, f, x, y, W, H, J.s12, J.qbits, inv_scale2);
+          const WinMoments m = window_moments<!kPlain>(P, f, x, y, W, H, J.s12, J.qbits, inv_scale2);
           rarea[f] = m.rarea;
           var[f] = m.var;
           mu[f] = window_mean(m.q1, m.rarea, inv_scale);
@@ -141,7 +144,7 @@ __global__ void __launch_bounds__(kBT, kMinBlocksPix) k_bwd_pixel(DevParams P, c
       const float L = wsum > 0.f ? __fdividef(accL, wsum) : __fdividef(meanL, (float)NF);
       // Eq. 12
       float rgb[3];
-      load_rgb(J.in, x, y, rgb[0], rgb[1], rgb[2]);
+      load_rgb<kPlain ? kF32 : -1>(J.in, x, y, rgb[0], rgb[1], rgb[2]);
       const float raw =
           __fadd_rn(__fadd_rn(__fmul_rn(0.2126f, rgb[0]), __fmul_rn(0.7152f, rgb[1])), __fmul_rn(0.0722f, rgb[2]));
       const float i = fmaxf(raw, kLumFloor);
@@ -260,8 +263,9 @@ __global__ void k_bwd_finish(DevParams P, const BwdJob *__restrict__ jobs, const
 }
 
 // Per pixel: the adjoint of the window variances, through the normalised log,
-// into the luminance and Eq. 11; range-term partial sums.
-template <int NF>
+// into the luminance and Eq. 11; range-term partial sums. kDt: the dtype of
+// every input when known at compile time (-1: read from the descriptors).
+template <int NF, int kDt>
 __global__ void __launch_bounds__(kBT, kMinBlocksIn) k_bwd_input(DevParams P, const BwdJob *__restrict__ jobs, int njobs) {
   __shared__ float sh[2][kWarpsB];
   __shared__ float scale[2 * NF][2];  // 2^-shift of each fixed-point plane, as two factors
@@ -295,7 +299,7 @@ __global__ void __launch_bounds__(kBT, kMinBlocksIn) k_bwd_input(DevParams P, co
       if (y >= H) break;
       const unsigned pix = (unsigned)y * (unsigned)W + (unsigned)x;
       float rc, gc, bc;
-      load_rgb(J.in, x, y, rc, gc, bc);
+      load_rgb<kDt>(J.in, x, y, rc, gc, bc);
       const float raw = __fadd_rn(__fadd_rn(__fmul_rn(0.2126f, rc), __fmul_rn(0.7152f, gc)), __fmul_rn(0.0722f, bc));
       float gi = J.gi_direct[pix];
       if (D > 0.f) {
@@ -368,29 +372,45 @@ int launch_backward_setup(const void *desc, size_t bytes, void *dst, BwdAcc *acc
   return 1;
 }
 
-int launch_backward_pixel(const DevParams &P, const BwdJob *jobs, int n, int pix_blocks, bool mom, double *gsum,
-                          cudaStream_t s) {
+template <bool MOM, bool kPlain>
+static void launch_pixel(const DevParams &P, const BwdJob *jobs, int n, int pix_blocks, double *gsum,
+                         cudaStream_t s) {
   switch (P.n_fields) {
-#define TM_BWD_PIXEL(nf)                                                          \
-  case nf:                                                                       \
-    if (mom) k_bwd_pixel<nf, true><<<pix_blocks, kBT, 0, s>>>(P, jobs, n, gsum); \
-    else k_bwd_pixel<nf, false><<<pix_blocks, kBT, 0, s>>>(P, jobs, n, gsum);    \
-    break;
+#define TM_BWD_PIXEL(nf) \
+  case nf: k_bwd_pixel<nf, MOM, kPlain><<<pix_blocks, kBT, 0, s>>>(P, jobs, n, gsum); break;
     TM_BWD_PIXEL(1) TM_BWD_PIXEL(2) TM_BWD_PIXEL(3) TM_BWD_PIXEL(4) TM_BWD_PIXEL(5) TM_BWD_PIXEL(6)
     TM_BWD_PIXEL(7) TM_BWD_PIXEL(8)
 #undef TM_BWD_PIXEL
   }
+}
+
+int launch_backward_pixel(const DevParams &P, const BwdJob *jobs, int n, int pix_blocks, bool mom, bool plain,
+                          double *gsum, cudaStream_t s) {
+  plain = plain && !(P.flags & kFlagAreaLit);
+  if (mom) {
+    if (plain) launch_pixel<true, true>(P, jobs, n, pix_blocks, gsum, s);
+    else launch_pixel<true, false>(P, jobs, n, pix_blocks, gsum, s);
+  } else {
+    if (plain) launch_pixel<false, true>(P, jobs, n, pix_blocks, gsum, s);
+    else launch_pixel<false, false>(P, jobs, n, pix_blocks, gsum, s);
+  }
   return 1;
 }
 
-int launch_backward_input(const DevParams &P, const BwdJob *jobs, int n, int in_blocks, const double *gsum,
-                          float *grad_params, cudaStream_t s) {
+template <int kDt>
+static void launch_input(const DevParams &P, const BwdJob *jobs, int n, int in_blocks, cudaStream_t s) {
   switch (P.n_fields) {
-#define TM_BWD_INPUT(nf) case nf: k_bwd_input<nf><<<in_blocks, kBT, 0, s>>>(P, jobs, n); break;
+#define TM_BWD_INPUT(nf) case nf: k_bwd_input<nf, kDt><<<in_blocks, kBT, 0, s>>>(P, jobs, n); break;
     TM_BWD_INPUT(1) TM_BWD_INPUT(2) TM_BWD_INPUT(3) TM_BWD_INPUT(4) TM_BWD_INPUT(5) TM_BWD_INPUT(6)
     TM_BWD_INPUT(7) TM_BWD_INPUT(8)
 #undef TM_BWD_INPUT
   }
+}
+
+int launch_backward_input(const DevParams &P, const BwdJob *jobs, int n, int in_blocks, bool plain,
+                          const double *gsum, float *grad_params, cudaStream_t s) {
+  if (plain) launch_input<kF32>(P, jobs, n, in_blocks, s);
+  else launch_input<-1>(P, jobs, n, in_blocks, s);
   k_bwd_finish<<<n, 32, 0, s>>>(P, jobs, gsum, grad_params);
   return 2;
 }

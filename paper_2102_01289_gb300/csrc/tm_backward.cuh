@@ -56,16 +56,17 @@ int bwd_input_blocks(int W, int H);
 // accumulators accs[n] and, first, the parameter sums gsum[kBwdParams]; -1
 // if `bytes` exceeds kBwdDescBytes); launch_backward_pixel (per pixel: u_f,
 // v_f, the direct gradients, the parameter sums; mom: every job's
-// BwdJob::mom is set, else none is); launch_fix_integrals over the FixJobs
+// BwdJob::mom is set, else none is; plain: every job's input is float32 and
+// its count planes uint32); launch_fix_integrals over the FixJobs
 // (image i's reads U / V of job i and writes its IUV); launch_backward_input
 // (the box sums back into the input, then the range terms and, when
 // grad_params, device float[3 + 2s], is not null, the parameter gradients
 // from gsum). Each returns its launches.
 int launch_backward_setup(const void *desc, size_t bytes, void *dst, BwdAcc *accs, int n, double *gsum, bool first,
                           cudaStream_t s);
-int launch_backward_pixel(const DevParams &P, const BwdJob *jobs, int n, int pix_blocks, bool mom, double *gsum,
-                          cudaStream_t s);
-int launch_backward_input(const DevParams &P, const BwdJob *jobs, int n, int in_blocks, const double *gsum,
-                          float *grad_params, cudaStream_t s);
+int launch_backward_pixel(const DevParams &P, const BwdJob *jobs, int n, int pix_blocks, bool mom, bool plain,
+                          double *gsum, cudaStream_t s);
+int launch_backward_input(const DevParams &P, const BwdJob *jobs, int n, int in_blocks, bool plain,
+                          const double *gsum, float *grad_params, cudaStream_t s);
 
 }  // namespace tmk

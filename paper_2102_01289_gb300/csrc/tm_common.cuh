@@ -346,9 +346,11 @@ __device__ __forceinline__ float window_variance(long long s1, long long s2, uns
 }
 
 // Area of field f's window at (x, y) as a float: clipped to the image, or
-// under TM_FLAG_AREA_LITERAL the unclipped (2 rx + 1)(2 ry + 1).
+// under TM_FLAG_AREA_LITERAL the unclipped (2 rx + 1)(2 ry + 1) (kLit =
+// false: the caller guarantees that flag is off).
+template <bool kLit = true>
 __device__ __forceinline__ float window_area(const DevParams &P, int f, int x, int y, int W, int H) {
-  if (P.flags & kFlagAreaLit) return (float)((unsigned)(2 * P.rx[f] + 1) * (unsigned)(2 * P.ry[f] + 1));
+  if (kLit && (P.flags & kFlagAreaLit)) return (float)((unsigned)(2 * P.rx[f] + 1) * (unsigned)(2 * P.ry[f] + 1));
   const int x0 = max(x - P.rx[f], 0), x1 = min(x + P.rx[f], W - 1);
   const int y0 = max(y - P.ry[f], 0), y1 = min(y + P.ry[f], H - 1);
   return (float)((unsigned)(x1 - x0 + 1) * (unsigned)(y1 - y0 + 1));

@@ -86,11 +86,11 @@ int launch_sweep(const DevParams &P, const Job *jobs, int njobs, int nitems, int
 
 // Stage a4: per-pixel lookup, tone curve, fusion and colour restoration.
 int lookup_blocks(int W, int H);
-// plain: no job has debug planes or window moments to write and every job's
-// count planes are uint32; dtype: the dtype of every job's input and output
-// when they all share one, else -1.
-int launch_lookup_counts(const DevParams &P, const Job *jobs, int njobs, int blocks, bool plain, int dtype,
-                         cudaStream_t s);
+// plain: no job has debug planes to write and every job's count planes are
+// uint32; mom: every job keeps its window moments (else none does); dtype:
+// the dtype of every job's input and output when they all share one, else -1.
+int launch_lookup_counts(const DevParams &P, const Job *jobs, int njobs, int blocks, bool plain, bool mom,
+                         int dtype, cudaStream_t s);
 int launch_lookup_materialised(const Image &in, const Image &out, const DevParams &P,
                                const uint8_t *bins, const uint32_t *cplanes, const int64_t *s12,
                                const DebugPlanes &dbg, cudaStream_t s);

@@ -22,16 +22,16 @@ struct Fusion {
 // into the Eq. 3 sums (the same arithmetic as fuse_fields, one field at a
 // time, so no per-field state is kept).
 // mom (or null): receives the window's variance and mean of lhat for the
-// backward (inv_scale = 2^-Q). kPlain: no debug planes, no moments and no
-// literal area (those paths are then not compiled in).
-template <bool kPlain = false>
+// backward (inv_scale = 2^-Q). kPlain: no debug planes and no literal area,
+// and moments only under kMom (the other paths are then not compiled in).
+template <bool kPlain = false, bool kMom = false>
 __device__ __forceinline__ void fold_field(const DevParams &P, int f, int x, int y, int W, int H,
                                            unsigned cnt, const longlong2 *__restrict__ s12, int qbits,
                                            float inv_scale2, Fusion &fu, const DebugPlanes &dbg,
                                            float2 *mom = nullptr, float inv_scale = 0.f) {
   const WinMoments m = window_moments<!kPlain>(P, f, x, y, W, H, s12, qbits, inv_scale2);
   const float rarea = m.rarea, var = m.var;
-  if (!kPlain && mom)
+  if (kPlain ? kMom : mom != nullptr)
     mom[(size_t)f * W * H + (size_t)y * W + x] = make_float2(var, window_mean(m.q1, rarea, inv_scale));
   const float Pf = (float)cnt * rarea;                                  // Eq. 1
   const float Lf = fmaf(P.ld_max - P.ld_min, Pf, P.ld_min);             // Eq. 2
@@ -65,8 +65,10 @@ __device__ __forceinline__ void finish_pixel(const Image &in, const Image &out, 
 
 // Eight blocks per SM (32 registers, a few spilled at five fields and more)
 // keep more corner loads in flight: at 12 MP with the five-field pyramid this
-// ran 0.48 ms against 0.60 ms at five blocks per SM.
-template <int NF>
+// ran 0.48 ms against 0.60 ms at five blocks per SM. kPlain: no debug planes
+// and no literal area; kDt: the dtype of both images when they share it (-1:
+// read from the descriptors).
+template <int NF, bool kPlain, int kDt>
 __global__ void __launch_bounds__(256, 8)
     k_lookup_materialised(Image in, Image out, DevParams P, const uint8_t *__restrict__ bins,
                           const unsigned *__restrict__ cplanes, const longlong2 *__restrict__ s12,
@@ -92,22 +94,23 @@ __global__ void __launch_bounds__(256, 8)
             __ldg(C + (long long)w.y0 * W1 + w.x1 + 1) + __ldg(C + (long long)w.y0 * W1 + w.x0);
     else if (t >= P.n_bins)
       cnt = (unsigned)((w.x1 - w.x0 + 1) * (w.y1 - w.y0 + 1));
-    fold_field(P, f, x, y, W, H, cnt, s12, P.qbits, inv_scale2, fu, dbg);
+    fold_field<kPlain>(P, f, x, y, W, H, cnt, s12, P.qbits, inv_scale2, fu, dbg);
   }
-  finish_pixel(in, out, P, x, y, fu, dbg);
+  finish_pixel<kPlain, kDt>(in, out, P, x, y, fu, dbg);
 }
 
 // Lookup from the sweep's count planes, over a batch of jobs: block ->
 // (image, 32 x 8 pixel tile). NF = number of fields, so the field loop is
 // straight-line code and the loads of all fields can be issued together.
 // Eight blocks per SM (32 registers) keep more of those loads in flight.
-// kPlain: no job has debug planes or window moments, every count plane is
-// uint32 and the literal area is off; kDt: the dtype of every job's input
-// and output when they all share one (-1: read from the descriptors).
-// Specialising drops the paths a launch does not take: the compiler would
-// otherwise predicate some of them into every pixel (at 12 MP the plain
-// float32 variant took 0.211 ms against 0.247).
-template <int NF, bool kPlain, int kDt>
+// kPlain: no job has debug planes, every count plane is uint32 and the
+// literal area is off; then kMom: every job keeps its window moments (else
+// none does). kDt: the dtype of every job's input and output when they all
+// share one (-1: read from the descriptors). Specialising drops the paths a
+// launch does not take: the compiler would otherwise predicate some of them
+// into every pixel (at 12 MP the plain float32 variant took 0.191 ms against
+// 0.247).
+template <int NF, bool kPlain, int kDt, bool kMom = false>
 __global__ void __launch_bounds__(256, 8) k_lookup_counts(DevParams P, const Job *__restrict__ jobs, int njobs) {
   const int j = find_job(jobs, njobs, kStLook, blockIdx.x);
   const Job &J = jobs[j];
@@ -125,50 +128,68 @@ __global__ void __launch_bounds__(256, 8) k_lookup_counts(DevParams P, const Job
   for (int f = 0; f < NF; ++f) {
     const unsigned cnt = kPlain ? __ldg(reinterpret_cast<const unsigned *>(J.cnt + J.cnt_off[f]) + pix)
                                 : load_count(J, f, pix);
-    fold_field<kPlain>(P, f, x, y, W, H, cnt, reinterpret_cast<const longlong2 *>(J.s1), J.qbits, inv_scale2,
-                       fu, J.dbg, J.mom, inv_scale);
+    fold_field<kPlain, kMom>(P, f, x, y, W, H, cnt, reinterpret_cast<const longlong2 *>(J.s1), J.qbits,
+                             inv_scale2, fu, J.dbg, J.mom, inv_scale);
   }
   finish_pixel<kPlain, kDt>(J.in, J.out, P, x, y, fu, J.dbg);
 }
 
 }  // namespace
 
+template <bool kPlain, int kDt>
+static void launch_mat(const Image &in, const Image &out, const DevParams &P, const uint8_t *bins,
+                       const uint32_t *cplanes, const longlong2 *S12, const DebugPlanes &dbg, cudaStream_t s) {
+  dim3 block(32, 8), grid((in.W + 31) / 32, (in.H + 7) / 8);
+  switch (P.n_fields) {
+#define TM_LOOKUP_MAT(nf)                                                                                       \
+  case nf:                                                                                                      \
+    k_lookup_materialised<nf, kPlain, kDt><<<grid, block, 0, s>>>(in, out, P, bins, cplanes, S12, dbg);        \
+    break;
+    TM_LOOKUP_MAT(1) TM_LOOKUP_MAT(2) TM_LOOKUP_MAT(3) TM_LOOKUP_MAT(4) TM_LOOKUP_MAT(5) TM_LOOKUP_MAT(6)
+    TM_LOOKUP_MAT(7)
+    default: k_lookup_materialised<8, kPlain, kDt><<<grid, block, 0, s>>>(in, out, P, bins, cplanes, S12, dbg); break;
+#undef TM_LOOKUP_MAT
+  }
+}
+
 int launch_lookup_materialised(const Image &in, const Image &out, const DevParams &P,
                                const uint8_t *bins, const uint32_t *cplanes, const int64_t *s12,
                                const DebugPlanes &dbg, cudaStream_t s) {
-  dim3 block(32, 8), grid((in.W + 31) / 32, (in.H + 7) / 8);
   const longlong2 *S12 = reinterpret_cast<const longlong2 *>(s12);
-  switch (P.n_fields) {
-#define TM_LOOKUP_MAT(nf) \
-  case nf: k_lookup_materialised<nf><<<grid, block, 0, s>>>(in, out, P, bins, cplanes, S12, dbg); break;
-    TM_LOOKUP_MAT(1) TM_LOOKUP_MAT(2) TM_LOOKUP_MAT(3) TM_LOOKUP_MAT(4) TM_LOOKUP_MAT(5) TM_LOOKUP_MAT(6)
-    TM_LOOKUP_MAT(7)
-    default: k_lookup_materialised<8><<<grid, block, 0, s>>>(in, out, P, bins, cplanes, S12, dbg); break;
-#undef TM_LOOKUP_MAT
-  }
+  const int dt = in.dtype == out.dtype ? in.dtype : -1;
+  if (dbg.l || (P.flags & kFlagAreaLit))
+    launch_mat<false, -1>(in, out, P, bins, cplanes, S12, dbg, s);
+  else if (dt == kF32)
+    launch_mat<true, kF32>(in, out, P, bins, cplanes, S12, dbg, s);
+  else if (dt == kF16)
+    launch_mat<true, kF16>(in, out, P, bins, cplanes, S12, dbg, s);
+  else
+    launch_mat<true, -1>(in, out, P, bins, cplanes, S12, dbg, s);
   return 1;
 }
 
 int lookup_blocks(int W, int H) { return ((W + 31) / 32) * ((H + 7) / 8); }
 
-template <bool kPlain, int kDt>
+template <bool kPlain, int kDt, bool kMom = false>
 static void launch_counts(const DevParams &P, const Job *jobs, int njobs, int blocks, cudaStream_t s) {
   switch (P.n_fields) {
-    case 1: k_lookup_counts<1, kPlain, kDt><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
-    case 2: k_lookup_counts<2, kPlain, kDt><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
-    case 3: k_lookup_counts<3, kPlain, kDt><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
-    case 4: k_lookup_counts<4, kPlain, kDt><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
-    case 5: k_lookup_counts<5, kPlain, kDt><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
-    case 6: k_lookup_counts<6, kPlain, kDt><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
-    case 7: k_lookup_counts<7, kPlain, kDt><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
-    default: k_lookup_counts<8, kPlain, kDt><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
+    case 1: k_lookup_counts<1, kPlain, kDt, kMom><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
+    case 2: k_lookup_counts<2, kPlain, kDt, kMom><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
+    case 3: k_lookup_counts<3, kPlain, kDt, kMom><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
+    case 4: k_lookup_counts<4, kPlain, kDt, kMom><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
+    case 5: k_lookup_counts<5, kPlain, kDt, kMom><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
+    case 6: k_lookup_counts<6, kPlain, kDt, kMom><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
+    case 7: k_lookup_counts<7, kPlain, kDt, kMom><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
+    default: k_lookup_counts<8, kPlain, kDt, kMom><<<blocks, 256, 0, s>>>(P, jobs, njobs); break;
   }
 }
 
-int launch_lookup_counts(const DevParams &P, const Job *jobs, int njobs, int blocks, bool plain, int dtype,
-                         cudaStream_t s) {
-  if (!plain || (P.flags & kFlagAreaLit))
+int launch_lookup_counts(const DevParams &P, const Job *jobs, int njobs, int blocks, bool plain, bool mom,
+                         int dtype, cudaStream_t s) {
+  if (!plain || (P.flags & kFlagAreaLit) || (mom && dtype != kF32))
     launch_counts<false, -1>(P, jobs, njobs, blocks, s);
+  else if (mom)
+    launch_counts<true, kF32, true>(P, jobs, njobs, blocks, s);
   else if (dtype == kF32)
     launch_counts<true, kF32>(P, jobs, njobs, blocks, s);
   else if (dtype == kF16)
