@@ -540,9 +540,9 @@ tm_status forward_materialised(tm_ctx *c, const tm_image *in, const tm_image *ou
   J.b0[kStRange] = J.b0[kStPrep] = J.b0[kStRows] = J.b0[kStCols] = J.b0[kStLook] = 0;
   int64_t n = put_jobs(&J, 1, c->djobs, s);
   mark(c, s, -1);
-  if (run_range) launch_range(c->djobs, 1, rb, c->p.n_bins, s);
+  if (run_range) launch_range(c->djobs, 1, rb, c->p.n_bins, J.in.dtype, s);
   mark(c, s, ST_RANGE);
-  launch_prep(c->djobs, 1, pb, c->p.n_bins, c->p.flags, c->p.n_fields, s);
+  launch_prep(c->djobs, 1, pb, c->p.n_bins, c->p.flags, c->p.n_fields, J.in.dtype, s);
   mark(c, s, ST_PREP);
   n += (run_range ? 2 : 1) +
        launch_integral_jobs(c->djobs, 1, integral_tile_blocks(W, nseg), integral_col_blocks(W), s);
@@ -722,9 +722,10 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   }
   int64_t n = put_jobs(jobs.data(), nimg, dj, s);
   if (!graph) mark(c, s, -1);
-  if (run_range) launch_range(dj, nimg, b_range, c->p.n_bins, s);
+  const int in_dt = input_dtype(jobs.data(), nimg);
+  if (run_range) launch_range(dj, nimg, b_range, c->p.n_bins, in_dt, s);
   if (!graph) mark(c, s, ST_RANGE);
-  launch_prep(dj, nimg, b_prep, c->p.n_bins, c->p.flags, c->p.n_fields, s);
+  launch_prep(dj, nimg, b_prep, c->p.n_bins, c->p.flags, c->p.n_fields, in_dt, s);
   const int m_prep = graph ? -1 : mark(c, s, ST_PREP);
   // the sweep (high priority, launched first, so its CTAs take the SMs) and
   // the integral images (low priority) side by side, each timed from the end
@@ -874,8 +875,9 @@ tm_status forward_materialised_batch(tm_ctx *c, int nimg, const tm_image *in, co
     TM_CUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   }
   int64_t n = put_jobs(jobs.data(), nimg, c->mdjobs, s);
-  launch_range(c->mdjobs, nimg, b_range, c->p.n_bins, s);
-  launch_prep(c->mdjobs, nimg, b_prep, c->p.n_bins, c->p.flags, c->p.n_fields, s);
+  const int in_dt = input_dtype(jobs.data(), nimg);
+  launch_range(c->mdjobs, nimg, b_range, c->p.n_bins, in_dt, s);
+  launch_prep(c->mdjobs, nimg, b_prep, c->p.n_bins, c->p.flags, c->p.n_fields, in_dt, s);
   n += 2 + launch_integral_jobs(c->mdjobs, nimg, b_rows, b_cols, s);
   for (int i = 0; i < nimg; ++i) {
     const Job &J = jobs[(size_t)i];

@@ -10,11 +10,15 @@
 namespace tmk {
 
 // Stage a0: range of Eq. 11 luminance, bin edges, quantisation constants.
-void launch_range(const Job *jobs, int njobs, int blocks, int n_bins, cudaStream_t s);
+// dtype: the dtype every job's input shares, else -1.
+void launch_range(const Job *jobs, int njobs, int blocks, int n_bins, int dtype, cudaStream_t s);
 // Stage a1: bin map (uint8), quantised normalised log (int32), the per-row
 // 32-column bin ranges (J.grp, when set) and zeroed count planes (J.cnt,
-// when set: n_fields uint32 planes).
-void launch_prep(const Job *jobs, int njobs, int blocks, int n_bins, int flags, int n_fields, cudaStream_t s);
+// when set: n_fields uint32 planes). dtype as for launch_range.
+void launch_prep(const Job *jobs, int njobs, int blocks, int n_bins, int flags, int n_fields, int dtype,
+                 cudaStream_t s);
+// The dtype every job's input shares, else -1 (host).
+int input_dtype(const Job *jobs, int njobs);
 // Blocks of the range / prep stages for one image.
 int range_blocks(int W, int H, int num_sms, double share);
 int prep_blocks(int W, int H, int num_sms, double share);

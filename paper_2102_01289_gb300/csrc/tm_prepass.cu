@@ -14,11 +14,13 @@ namespace tmk {
 namespace {
 
 // Four consecutive pixels of row y starting at x (x + 3 < W), vector loads.
+// kDt: the image's dtype when known at compile time (-1: read from im).
+template <int kDt>
 __device__ __forceinline__ void load4_vec(const Image &im, int x, int y, float r[4], float g[4],
                                           float b[4]) {
   const long long o = (long long)y * im.pitch + 3LL * x;
   float v[12];
-  if (im.dtype == kF16) {
+  if ((kDt >= 0 ? kDt : im.dtype) == kF16) {
     const uint2 *p = reinterpret_cast<const uint2 *>(static_cast<const __half *>(im.p) + o);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -50,19 +52,21 @@ __device__ __forceinline__ void load4_vec(const Image &im, int x, int y, float r
 }
 
 // Up to four pixels of row y from x (n of them), scalar loads.
+template <int kDt>
 __device__ __forceinline__ void load4_scalar(const Image &im, int x, int y, int n, float r[4],
                                              float g[4], float b[4]) {
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    if (i < n) load_rgb(im, x + i, y, r[i], g[i], b[i]);
+    if (i < n) load_rgb<kDt>(im, x + i, y, r[i], g[i], b[i]);
     else r[i] = g[i] = b[i] = 1.f;
   }
 }
 
+template <int kDt>
 __device__ __forceinline__ void load4(const Image &im, bool vec, int x, int y, int n, float r[4],
                                       float g[4], float b[4]) {
-  if (vec && n == 4) load4_vec(im, x, y, r, g, b);
-  else load4_scalar(im, x, y, n, r, g, b);
+  if (vec && n == 4) load4_vec<kDt>(im, x, y, r, g, b);
+  else load4_scalar<kDt>(im, x, y, n, r, g, b);
 }
 
 }  // namespace
@@ -147,7 +151,9 @@ __device__ void commit_range(Stats *st, unsigned bmin, unsigned bmax, int nb, in
 }
 
 // Range of Eq. 11 luminance, per image of the batch: block min/max folded
-// into the image's Stats by commit_range.
+// into the image's Stats by commit_range. kDt: the dtype of every input when
+// they share one (-1: read from the descriptors).
+template <int kDt>
 __global__ void __launch_bounds__(256) k_range(const Job *__restrict__ jobs, int njobs, int n_bins) {
   const int j = find_job(jobs, njobs, kStRange, blockIdx.x);
   const Job &J = jobs[j];
@@ -171,7 +177,7 @@ __global__ void __launch_bounds__(256) k_range(const Job *__restrict__ jobs, int
       if (g < ng) {
         const int y = g / gpr, x = (g - y * gpr) * 4;
         n[u] = min(4, W - x);
-        load4(in, vec, x, y, n[u], r[u], gg[u], b[u]);
+        load4<kDt>(in, vec, x, y, n[u], r[u], gg[u], b[u]);
       }
     }
 #pragma unroll
@@ -192,8 +198,9 @@ __global__ void __launch_bounds__(256) k_range(const Job *__restrict__ jobs, int
 // TM_FLAG_VAR_LINEAR. One thread per group of four pixels; rows are padded to
 // whole 32-pixel groups so that eight consecutive lanes share one group,
 // whose bin range (smallest | largest << 8) goes to J.grp for the sweep.
-__global__ void __launch_bounds__(256) k_prep(const Job *__restrict__ jobs, int njobs, int n_bins,
-                                              int flags, int n_fields) {
+// kLin: TM_FLAG_VAR_LINEAR; kDt as in k_range.
+template <bool kLin, int kDt>
+__global__ void __launch_bounds__(256) k_prep(const Job *__restrict__ jobs, int njobs, int n_bins, int n_fields) {
   __shared__ float thr[kMaxBins];
   const int j = find_job(jobs, njobs, kStPrep, blockIdx.x);
   const Job &J = jobs[j];
@@ -209,7 +216,6 @@ __global__ void __launch_bounds__(256) k_prep(const Job *__restrict__ jobs, int 
   sst.log2_scale = __ldg(&st->log2_scale);
   sst.lin_scale = __ldg(&st->lin_scale);
   const float lg_min = __ldg(&st->lg_min), bin_scale = __ldg(&st->bin_scale);
-  const bool lin = (flags & kFlagVarLin) != 0;
   __syncthreads();
   const int W = in.W, H = in.H, qbits = J.qbits;
   uint8_t *bins = J.bins;
@@ -227,7 +233,7 @@ __global__ void __launch_bounds__(256) k_prep(const Job *__restrict__ jobs, int 
     int kmin = 256, kmax = -1;
     if (n > 0) {
       float r[4], g[4], b[4];
-      load4(in, vec, x, y, n, r, g, b);
+      load4<kDt>(in, vec, x, y, n, r, g, b);
       unsigned bq = 0;
       int qq[4];
 #pragma unroll
@@ -235,7 +241,7 @@ __global__ void __launch_bounds__(256) k_prep(const Job *__restrict__ jobs, int 
         const float l = luminance(r[i], g[i], b[i]);
         const int bi = bin_of(l, thr, n_bins, lg_min, bin_scale);
         bq |= (unsigned)bi << (8 * i);
-        qq[i] = lin ? quantise_lin(l, sst, qbits) : quantise_log(l, sst, qbits);
+        qq[i] = kLin ? quantise_lin(l, sst, qbits) : quantise_log(l, sst, qbits);
         if (i < n) {
           bmin = min(bmin, __float_as_uint(l));
           bmax = max(bmax, __float_as_uint(l));
@@ -292,12 +298,31 @@ int prep_blocks(int W, int H, int num_sms, double share) {
   return (int)(b < 1 ? 1 : b);
 }
 
-void launch_range(const Job *jobs, int njobs, int blocks, int n_bins, cudaStream_t s) {
-  k_range<<<blocks, 256, 0, s>>>(jobs, njobs, n_bins);
+int input_dtype(const Job *jobs, int njobs) {
+  int dt = njobs > 0 ? jobs[0].in.dtype : -1;
+  for (int i = 1; i < njobs; ++i)
+    if (jobs[i].in.dtype != dt) return -1;
+  return dt;
 }
 
-void launch_prep(const Job *jobs, int njobs, int blocks, int n_bins, int flags, int n_fields, cudaStream_t s) {
-  k_prep<<<blocks, 256, 0, s>>>(jobs, njobs, n_bins, flags, n_fields);
+void launch_range(const Job *jobs, int njobs, int blocks, int n_bins, int dtype, cudaStream_t s) {
+  if (dtype == kF32) k_range<kF32><<<blocks, 256, 0, s>>>(jobs, njobs, n_bins);
+  else if (dtype == kF16) k_range<kF16><<<blocks, 256, 0, s>>>(jobs, njobs, n_bins);
+  else k_range<-1><<<blocks, 256, 0, s>>>(jobs, njobs, n_bins);
+}
+
+template <bool kLin>
+static void launch_prep_lin(const Job *jobs, int njobs, int blocks, int n_bins, int n_fields, int dtype,
+                            cudaStream_t s) {
+  if (dtype == kF32) k_prep<kLin, kF32><<<blocks, 256, 0, s>>>(jobs, njobs, n_bins, n_fields);
+  else if (dtype == kF16) k_prep<kLin, kF16><<<blocks, 256, 0, s>>>(jobs, njobs, n_bins, n_fields);
+  else k_prep<kLin, -1><<<blocks, 256, 0, s>>>(jobs, njobs, n_bins, n_fields);
+}
+
+void launch_prep(const Job *jobs, int njobs, int blocks, int n_bins, int flags, int n_fields, int dtype,
+                 cudaStream_t s) {
+  if (flags & kFlagVarLin) launch_prep_lin<true>(jobs, njobs, blocks, n_bins, n_fields, dtype, s);
+  else launch_prep_lin<false>(jobs, njobs, blocks, n_bins, n_fields, dtype, s);
 }
 
 }  // namespace tmk
