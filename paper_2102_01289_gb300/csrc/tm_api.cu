@@ -325,6 +325,9 @@ DevParams dev_params(const tm_params &p, int qbits) {
   d.sat = p.sat;
   d.qbits = qbits;
   d.flags = p.flags;
+  bool small = true;  // every unclipped window below 2^18 pixels
+  for (int f = 0; f < p.n_fields; ++f) small = small && (2LL * p.rx[f] + 1) * (2LL * p.ry[f] + 1) < (1LL << 18);
+  d.small_win = small ? 1 : 0;
   return d;
 }
 

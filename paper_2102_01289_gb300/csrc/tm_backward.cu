@@ -86,8 +86,9 @@ __global__ void k_bwd_setup(const __grid_constant__ Pack p, int words, unsigned 
 // largest |u_f|, |v_f| (for the fixed-point scales). NF = number of fields
 // (so every per-field array lives in registers).
 // MOM: the window variances and means come from the forward's planes.
-// kPlain: the literal area is off, every count plane is uint32 and every
-// input is float32 (the other paths are then not compiled in).
+// kPlain: the literal area is off, every window is small (P.small_win),
+// every count plane is uint32 and every input is float32 (the other paths are
+// then not compiled in).
 template <int NF, bool MOM, bool kPlain>
 __global__ void __launch_bounds__(kBT, kMinBlocksPix) k_bwd_pixel(DevParams P, const BwdJob *__restrict__ jobs, int njobs,
                                                    double *__restrict__ gsum) {
@@ -128,7 +129,8 @@ __global__ void __launch_bounds__(kBT, kMinBlocksPix) k_bwd_pixel(DevParams P, c
           mu[f] = vm.y;
           rarea[f] = __fdividef(1.f, window_area<!kPlain>(P, f, x, y, W, H));
         } else {
-          const WinMoments m = window_moments<!kPlain>(P, f, x, y, W, H, J.s12, J.qbits, inv_scale2);
+          const WinMoments m = window_moments<!kPlain, kPlain ? 1 : -1>(P, f, x, y, W, H, J.s12, J.qbits,
+                                                                        inv_scale2);
           rarea[f] = m.rarea;
           var[f] = m.var;
           mu[f] = window_mean(m.q1, m.rarea, inv_scale);
@@ -386,7 +388,7 @@ static void launch_pixel(const DevParams &P, const BwdJob *jobs, int n, int pix_
 
 int launch_backward_pixel(const DevParams &P, const BwdJob *jobs, int n, int pix_blocks, bool mom, bool plain,
                           double *gsum, cudaStream_t s) {
-  plain = plain && !(P.flags & kFlagAreaLit);
+  plain = plain && P.small_win && !(P.flags & kFlagAreaLit);
   if (mom) {
     if (plain) launch_pixel<true, true>(P, jobs, n, pix_blocks, gsum, s);
     else launch_pixel<true, false>(P, jobs, n, pix_blocks, gsum, s);

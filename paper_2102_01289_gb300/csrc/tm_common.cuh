@@ -31,6 +31,7 @@ struct DevParams {
   float sat;                // Eq. 12
   int qbits;                // Q: q = round(2^Q lhat) - 2^(Q-1)
   int flags;                // TM_FLAG_* reading variants
+  int small_win;            // 1: every unclipped window holds fewer than 2^18 pixels
 };
 
 // Reading variants (the TM_FLAG_* bits of tm_params.flags).
@@ -334,13 +335,23 @@ __device__ __forceinline__ long long float_to_i64_rn(float y) {
 // so the one float subtraction loses at most a few bits whenever var >= 1
 // unit^2, and far less than the quantisation step below that. rN = rounded
 // 1/N; inv_scale2 = 2^-2Q converts to lhat units.
+// Small windows (kSmall = 1, or small at run time with kSmall = -1: every
+// window under 2^18 pixels) take the two 64-bit conversions that run on the
+// slow FP64 pipe through 32-bit ones: |s1| <= 2^23 N < 2^41, so s1 / 2^10
+// (rounded down) fits 31 bits and its float estimate of the mean is within
+// 2^10 / N + 4 of it; then |d| <= 4.5 N + 2^10 < 2^31. The float error of
+// T - d^2 / N grows to about 2^-24 (var + (m - mean)^2) unit^2, at most
+// 2^-4 unit^2 (one-pixel windows), below the quantisation step.
+template <int kSmall = -1>
 __device__ __forceinline__ float window_variance(long long s1, long long s2, unsigned long long N,
-                                                 float rN, float inv_scale2) {
+                                                 float rN, float inv_scale2, bool small = false) {
+  const bool sm = kSmall >= 0 ? kSmall != 0 : small;
   // |mean| <= 2^(Q-1) <= 2^23: the nearest integer fits 32 bits
-  const int m = __float2int_rn(__ll2float_rn(s1) * rN);
+  const int m = sm ? __float2int_rn(__int2float_rn((int)(s1 >> 10)) * (rN * 1024.f))
+                   : __float2int_rn(__ll2float_rn(s1) * rN);
   const long long d = s1 - (long long)m * (long long)N;
   const unsigned long long T = (unsigned long long)s2 - (unsigned long long)((long long)m * (s1 + d));
-  const float df = __ll2float_rn(d);
+  const float df = sm ? __int2float_rn((int)d) : __ll2float_rn(d);
   const float v = fmaf(-df * rN, df, __ull2float_rn(T)) * rN;
   return fmaxf(v, 0.f) * inv_scale2;
 }
@@ -373,8 +384,9 @@ struct WinMoments {
   long long q1;
 };
 // kLit = false: the caller guarantees TM_FLAG_AREA_LITERAL is off (the
-// padding terms are then not compiled in).
-template <bool kLit = true>
+// padding terms are then not compiled in); kSmall as for window_variance
+// (-1: P.small_win).
+template <bool kLit = true, int kSmall = -1>
 __device__ __forceinline__ WinMoments window_moments(const DevParams &P, int f, int x, int y, int W, int H,
                                                      const longlong2 *__restrict__ s12, int qbits,
                                                      float inv_scale2) {
@@ -392,7 +404,7 @@ __device__ __forceinline__ WinMoments window_moments(const DevParams &P, int f, 
   if (kLit) literal_area(P, f, qbits, q1, q2, N);
   WinMoments m;
   m.rarea = __fdividef(1.f, (float)(unsigned)N);  // N <= 65535^2 < 2^32
-  m.var = window_variance(q1, q2, N, m.rarea, inv_scale2);
+  m.var = window_variance<kSmall>(q1, q2, N, m.rarea, inv_scale2, P.small_win != 0);
   m.q1 = q1;
   return m;
 }

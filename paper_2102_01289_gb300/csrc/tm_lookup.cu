@@ -23,13 +23,14 @@ struct Fusion {
 // time, so no per-field state is kept).
 // mom (or null): receives the window's variance and mean of lhat for the
 // backward (inv_scale = 2^-Q). kPlain: no debug planes and no literal area,
-// and moments only under kMom (the other paths are then not compiled in).
-template <bool kPlain = false, bool kMom = false>
+// and moments only under kMom (the other paths are then not compiled in);
+// kSmall as for window_variance.
+template <bool kPlain = false, bool kMom = false, int kSmall = -1>
 __device__ __forceinline__ void fold_field(const DevParams &P, int f, int x, int y, int W, int H,
                                            unsigned cnt, const longlong2 *__restrict__ s12, int qbits,
                                            float inv_scale2, Fusion &fu, const DebugPlanes &dbg,
                                            float2 *mom = nullptr, float inv_scale = 0.f) {
-  const WinMoments m = window_moments<!kPlain>(P, f, x, y, W, H, s12, qbits, inv_scale2);
+  const WinMoments m = window_moments<!kPlain, kSmall>(P, f, x, y, W, H, s12, qbits, inv_scale2);
   const float rarea = m.rarea, var = m.var;
   if (kPlain ? kMom : mom != nullptr)
     mom[(size_t)f * W * H + (size_t)y * W + x] = make_float2(var, window_mean(m.q1, rarea, inv_scale));
@@ -103,8 +104,10 @@ __global__ void __launch_bounds__(256, 8)
 // (image, 32 x 8 pixel tile). NF = number of fields, so the field loop is
 // straight-line code and the loads of all fields can be issued together.
 // Eight blocks per SM (32 registers) keep more of those loads in flight.
-// kPlain: no job has debug planes, every count plane is uint32 and the
-// literal area is off; then kMom: every job keeps its window moments (else
+// kPlain: no job has debug planes, every count plane is uint32, the literal
+// area is off and every window is small (P.small_win; the window variance
+// then takes its 32-bit conversions); then kMom: every job keeps its window
+// moments (else
 // none does). kDt: the dtype of every job's input and output when they all
 // share one (-1: read from the descriptors). Specialising drops the paths a
 // launch does not take: the compiler would otherwise predicate some of them
@@ -128,8 +131,8 @@ __global__ void __launch_bounds__(256, 8) k_lookup_counts(DevParams P, const Job
   for (int f = 0; f < NF; ++f) {
     const unsigned cnt = kPlain ? __ldg(reinterpret_cast<const unsigned *>(J.cnt + J.cnt_off[f]) + pix)
                                 : load_count(J, f, pix);
-    fold_field<kPlain, kMom>(P, f, x, y, W, H, cnt, reinterpret_cast<const longlong2 *>(J.s1), J.qbits,
-                             inv_scale2, fu, J.dbg, J.mom, inv_scale);
+    fold_field<kPlain, kMom, kPlain ? 1 : -1>(P, f, x, y, W, H, cnt, reinterpret_cast<const longlong2 *>(J.s1),
+                                              J.qbits, inv_scale2, fu, J.dbg, J.mom, inv_scale);
   }
   finish_pixel<kPlain, kDt>(J.in, J.out, P, x, y, fu, J.dbg);
 }
@@ -186,7 +189,7 @@ static void launch_counts(const DevParams &P, const Job *jobs, int njobs, int bl
 
 int launch_lookup_counts(const DevParams &P, const Job *jobs, int njobs, int blocks, bool plain, bool mom,
                          int dtype, cudaStream_t s) {
-  if (!plain || (P.flags & kFlagAreaLit) || (mom && dtype != kF32))
+  if (!plain || !P.small_win || (P.flags & kFlagAreaLit) || (mom && dtype != kF32))
     launch_counts<false, -1>(P, jobs, njobs, blocks, s);
   else if (mom)
     launch_counts<true, kF32, true>(P, jobs, njobs, blocks, s);
