@@ -117,11 +117,21 @@ struct tm_ctx {
   uint8_t *bins = nullptr;
   int32_t *q = nullptr;
   DebugPlanes dbg{};
-  // CUDA graph of the last batch, replayed while the batch is unchanged (the
-  // images taking the fused path), and of the last batch's images taking the
-  // materialised path, with that pass's own workspace and descriptors
-  cudaGraphExec_t graph = nullptr;
-  std::vector<tm_image> graph_in, graph_out;
+  // CUDA graphs of the last fused forwards (batches, or the images of a batch
+  // taking the fused path, and single images), each replayed while its images
+  // are unchanged; the least recently used is replaced. They share the
+  // workspace and gdjobs / gditems, which each replay rewrites first. And the
+  // graph of the last batch's images taking the materialised path, with that
+  // pass's own workspace and descriptors.
+  struct FusedGraph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<tm_image> in, out;
+    int64_t launches = 0;
+    std::vector<Job> jobs;
+    uint64_t used = 0;
+  };
+  std::vector<FusedGraph> graphs;
+  uint64_t graph_clock = 0;
   cudaGraphExec_t mgraph = nullptr;
   std::vector<tm_image> mgraph_in, mgraph_out;
   int64_t mgraph_launches = 0;
@@ -137,7 +147,6 @@ struct tm_ctx {
   // ov_int order the two streams after the prep stage and before the lookup.
   cudaStream_t sweep_stream = nullptr, int_stream = nullptr;
   cudaEvent_t ov_fork = nullptr, ov_sweep = nullptr, ov_int = nullptr;
-  int64_t graph_launches = 0;
   // streaming range reuse (TM_OPT_REUSE_RANGE): two range states; a forward
   // bins with rr_stats[rr_cur] and leaves its own range in the other
   int reuse_range = 0;
@@ -146,10 +155,10 @@ struct tm_ctx {
   const Stats *last_stats = nullptr;  // range state of the last single-image forward
   // TM_OPT_BACKWARD_REUSE: the job descriptors of the last fused forward that
   // left its intermediates (bins, q, integral images, count planes) in the
-  // workspace, the images it ran on, and those of the cached batch graph
+  // workspace and the images it ran on
   int bwd_reuse = 0;
   bool fwd_valid = false;
-  std::vector<Job> fwd_jobs, graph_jobs;
+  std::vector<Job> fwd_jobs;
   std::vector<tm_image> fwd_in;
   // automatic histogram path: the measured choice per (width, height, in dtype, out dtype),
   // and per batch of images that fit the sweep (their sizes and dtype pairs)
@@ -356,11 +365,14 @@ tm_status ensure_side_streams(tm_ctx *c) {
   return TM_OK;
 }
 
+// Fused-forward graphs kept at once (two alternating images, each also
+// through the host entry points' two staging slots, fit).
+constexpr size_t kFusedGraphs = 6;
+
 void drop_graph(tm_ctx *c) {
-  if (c->graph) cudaGraphExecDestroy(c->graph);
-  c->graph = nullptr;
-  c->graph_in.clear();
-  c->graph_out.clear();
+  for (auto &g : c->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
   if (c->mgraph) cudaGraphExecDestroy(c->mgraph);
   c->mgraph = nullptr;
   c->mgraph_in.clear();
@@ -573,21 +585,23 @@ tm_status forward_materialised(tm_ctx *c, const tm_image *in, const tm_image *ou
 
 // The fused path over a batch of images: one launch per stage for the whole
 // batch, the sweep as a persistent kernel over a queue of (image, strip, row
-// band) tiles. `graph`: capture the batch into a CUDA graph and replay it
-// while the batch is unchanged. Returns TM_EUNSUPPORTED if some image cannot
-// be swept.
+// band) tiles. `graph`: capture the batch into a CUDA graph of the context's
+// cache and replay it while the batch is unchanged. Returns TM_EUNSUPPORTED
+// if some image cannot be swept.
+tm_status finish_fused(tm_ctx *c, int nimg, const tm_image *in, const std::vector<Job> &jobs, int64_t n,
+                       bool run_range, std::vector<Job> *jobs_out);
+
 tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image *out, cudaStream_t s,
                         bool graph, bool do_lookup = true, std::vector<Job> *jobs_out = nullptr) {
   tm_status st;
-  if (graph && c->graph && same_images(c->graph_in, in, nimg) && same_images(c->graph_out, out, nimg)) {
-    c->fwd_valid = false;
-    TM_CUDA(c, cudaGraphLaunch(c->graph, s));
-    c->launches = c->graph_launches;
-    c->fwd_jobs = c->graph_jobs;
-    c->fwd_in.assign(in, in + nimg);
-    c->fwd_valid = true;
-    return TM_OK;
-  }
+  if (graph)
+    for (auto &G : c->graphs) {
+      if (!same_images(G.in, in, nimg) || !same_images(G.out, out, nimg)) continue;
+      c->fwd_valid = false;
+      TM_CUDA(c, cudaGraphLaunch(G.exec, s));
+      G.used = ++c->graph_clock;
+      return finish_fused(c, nimg, in, G.jobs, G.launches, true, jobs_out);
+    }
   c->fwd_valid = false;  // the workspace is rewritten below
   const bool debug = c->debug != 0 && nimg == 1 && !graph;
   // under TM_OPT_BACKWARD_REUSE the lookup also keeps the window moments
@@ -669,7 +683,12 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
   }
   if ((st = ensure_stats(c, nimg))) return st;
   if ((st = grow_device(c, &c->ws, &c->ws_bytes, ws_total))) return st;
-  if (graph) drop_graph(c);  // re-captured below
+  if (graph && c->graphs.size() >= kFusedGraphs) {  // room for the graph captured below
+    auto lru = std::min_element(c->graphs.begin(), c->graphs.end(),
+                                [](const tm_ctx::FusedGraph &a, const tm_ctx::FusedGraph &b) { return a.used < b.used; });
+    cudaGraphExecDestroy(lru->exec);
+    c->graphs.erase(lru);
+  }
   Job **djobs = graph ? &c->gdjobs : &c->djobs;
   int4 **ditems = graph ? &c->gditems : &c->ditems;
   if ((st = grow_device(c, (void **)djobs, graph ? &c->gdjobs_bytes : &c->djobs_bytes, sizeof(Job) * nimg)))
@@ -766,21 +785,29 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
       cudaGetLastError();
       return fail(c, TM_ECUDA, "batch capture failed: %s", cudaGetErrorString(e));
     }
-    e = cudaGraphInstantiate(&c->graph, g, 0);
+    tm_ctx::FusedGraph G;
+    e = cudaGraphInstantiate(&G.exec, g, 0);
     cudaGraphDestroy(g);
-    if (e != cudaSuccess) {
-      c->graph = nullptr;
-      return cuda_fail(c, e, "cudaGraphInstantiate");
-    }
-    c->graph_in.assign(in, in + nimg);
-    c->graph_out.assign(out, out + nimg);
-    c->graph_launches = n;
-    c->graph_jobs = jobs;
-    TM_CUDA(c, cudaGraphLaunch(c->graph, caller));
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+    G.in.assign(in, in + nimg);
+    G.out.assign(out, out + nimg);
+    G.launches = n;
+    G.jobs = jobs;
+    G.used = ++c->graph_clock;
+    c->graphs.push_back(std::move(G));
+    TM_CUDA(c, cudaGraphLaunch(c->graphs.back().exec, caller));
   } else if (ls < 0) {
     return check_launch(c, "sweep shared-memory attribute");
   }
   if ((st = check_launch(c, "forward launch"))) return st;
+  return finish_fused(c, nimg, in, jobs, n, run_range, jobs_out);
+}
+
+// Bookkeeping after a fused forward over `jobs` (n launches), launched or
+// replayed: the intermediates the backward may reuse and, for one image, the
+// layout the debug exports read.
+tm_status finish_fused(tm_ctx *c, int nimg, const tm_image *in, const std::vector<Job> &jobs, int64_t n,
+                       bool run_range, std::vector<Job> *jobs_out) {
   c->launches = n;
   if (jobs_out) *jobs_out = jobs;
   if (run_range) {  // each image binned over its own range, as a recomputation would
@@ -965,7 +992,9 @@ tm_status forward_device(tm_ctx *c, const tm_image *in, const tm_image *out, cud
     path = it->second;
   }
   if (path == 1) {
-    st = forward_fused(c, 1, in, out, s, false);
+    // a cached CUDA graph per image pair unless a per-call feature is on
+    const bool graph = !c->stage_timing && !c->debug && !c->reuse_range;
+    st = forward_fused(c, 1, in, out, s, graph);
     if (st != TM_EUNSUPPORTED) return st;
     if (c->hist_path == 1)
       return fail(c, TM_EUNSUPPORTED, "fused sweep does not fit these fields (use the materialised path)");
@@ -1324,7 +1353,7 @@ tm_status tm_create(const tm_params *params, tm_ctx **out) {
 
 void tm_destroy(tm_ctx *c) {
   if (!c) return;
-  if (c->ws || c->mws || c->stats || c->rr_stats || c->stage || c->djobs || c->gdjobs || c->graph || c->mgraph ||
+  if (c->ws || c->mws || c->stats || c->rr_stats || c->stage || c->djobs || c->gdjobs || !c->graphs.empty() || c->mgraph ||
       c->hslot[0])
     cudaDeviceSynchronize();
   drop_graph(c);

@@ -104,6 +104,50 @@ def test_graph_replay_tracks_inputs():
         tm.tm_destroy(ctx)
 
 
+def test_single_image_graph_cache():
+    """Single-image forwards replay a cached CUDA graph per (input, output)
+    pair, the least recently used replaced beyond six: eight images of
+    several sizes cycled twice (the workspace grows on the way, which drops
+    the cache), a batch in between and new contents in a cached input. Every
+    output equals the same forward without graphs (stage timing on), bit for
+    bit."""
+    p = tm.make_params(16, [2, 9, 40])
+    sizes = [(300, 200), (128, 96), (257, 255), (64, 64), (520, 130), (96, 300), (200, 200), (33, 47)]
+    xs = [torch.from_numpy(synth.wdr_image(h, w, seed=20 + i)).cuda() for i, (w, h) in enumerate(sizes)]
+    ys = [torch.empty_like(x) for x in xs]
+    ref_ctx = tm.tm_create(p)
+    ctx = tm.tm_create(p)
+    try:
+        tm.tm_set_option(ref_ctx, tm.TM_OPT_HIST_PATH, 1)
+        tm.tm_set_option(ref_ctx, tm.TM_OPT_STAGE_TIMING, 1)  # no graphs
+        tm.tm_set_option(ctx, tm.TM_OPT_HIST_PATH, 1)
+
+        def ref(x):
+            y = torch.empty_like(x)
+            tm.tm_forward(ref_ctx, x, y)
+            return y
+
+        for rnd in range(2):
+            for x, y in zip(xs, ys):
+                tm.tm_forward(ctx, x, y)
+                torch.cuda.synchronize()
+                assert torch.equal(y, ref(x)), (rnd, tuple(x.shape))
+            if rnd == 0:
+                zs = [torch.empty_like(x) for x in xs[:3]]
+                tm.tm_forward_batch(ctx, xs[:3], zs)
+                torch.cuda.synchronize()
+                for x, z in zip(xs[:3], zs):
+                    assert torch.equal(z, ref(x))
+        # new contents in a cached input: the replay sees them
+        xs[-1].copy_(torch.from_numpy(synth.wdr_image(47, 33, seed=99)).cuda())
+        tm.tm_forward(ctx, xs[-1], ys[-1])
+        torch.cuda.synchronize()
+        assert torch.equal(ys[-1], ref(xs[-1]))
+    finally:
+        tm.tm_destroy(ctx)
+        tm.tm_destroy(ref_ctx)
+
+
 def test_batch_image_matches_oracle(orc):
     p = tm.make_params(32, [4, 16, 64])
     op = orc.make_params(32, [4, 16, 64], eps=float(np.float32(0.1)), sat=float(np.float32(0.6)))
