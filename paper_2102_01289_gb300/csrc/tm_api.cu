@@ -131,7 +131,10 @@ struct tm_ctx {
     uint64_t used = 0;
   };
   std::vector<FusedGraph> graphs;
-  uint64_t graph_clock = 0;
+  uint64_t calls = 0;  // forward calls so far (FusedGraph::used counts in them)
+  // single-image (input, output) pairs seen lately without a graph, with the
+  // call that saw them: a pair gets its graph when it comes back
+  std::vector<std::pair<std::vector<tm_image>, uint64_t>> graph_seen;
   cudaGraphExec_t mgraph = nullptr;
   std::vector<tm_image> mgraph_in, mgraph_out;
   int64_t mgraph_launches = 0;
@@ -599,7 +602,7 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
       if (!same_images(G.in, in, nimg) || !same_images(G.out, out, nimg)) continue;
       c->fwd_valid = false;
       TM_CUDA(c, cudaGraphLaunch(G.exec, s));
-      G.used = ++c->graph_clock;
+      G.used = c->calls;
       return finish_fused(c, nimg, in, G.jobs, G.launches, true, jobs_out);
     }
   c->fwd_valid = false;  // the workspace is rewritten below
@@ -793,7 +796,7 @@ tm_status forward_fused(tm_ctx *c, int nimg, const tm_image *in, const tm_image 
     G.out.assign(out, out + nimg);
     G.launches = n;
     G.jobs = jobs;
-    G.used = ++c->graph_clock;
+    G.used = c->calls;
     c->graphs.push_back(std::move(G));
     TM_CUDA(c, cudaGraphLaunch(c->graphs.back().exec, caller));
   } else if (ls < 0) {
@@ -977,9 +980,42 @@ tm_status choose_path(tm_ctx *c, const tm_image *in, const tm_image *out, cudaSt
 }
 
 // The forward launch sequence on one image (device buffers already checked).
+// Whether a single-image forward on (in, out) runs from a CUDA graph: yes
+// when one is cached; else it is captured when the pair came in one of the
+// recent calls and a graph slot is free, or the least recently used graph
+// has not run for kGraphStale calls. A pair seen for the first time runs its
+// launches directly, so a stream of ever-new buffers never pays for a
+// capture, and pairs cycling through more slots than there are do not
+// replace one another's graphs on every call.
+constexpr uint64_t kGraphStale = 64;
+constexpr size_t kGraphSeen = 16;
+
+bool single_graph_ok(tm_ctx *c, const tm_image *in, const tm_image *out) {
+  const std::vector<tm_image> pair{*in, *out};
+  for (const auto &G : c->graphs)
+    if (same_images(G.in, in, 1) && same_images(G.out, out, 1)) return true;
+  auto seen = std::find_if(c->graph_seen.begin(), c->graph_seen.end(), [&](const auto &e) {
+    return same_images(e.first, pair.data(), 2);
+  });
+  if (seen != c->graph_seen.end()) {
+    seen->second = c->calls;
+    bool room = c->graphs.size() < kFusedGraphs;
+    for (const auto &G : c->graphs) room = room || G.used + kGraphStale < c->calls;
+    if (!room) return false;
+    c->graph_seen.erase(seen);
+    return true;
+  }
+  if (c->graph_seen.size() >= kGraphSeen)
+    c->graph_seen.erase(std::min_element(c->graph_seen.begin(), c->graph_seen.end(),
+                                         [](const auto &a, const auto &b) { return a.second < b.second; }));
+  c->graph_seen.emplace_back(pair, c->calls);
+  return false;
+}
+
 tm_status forward_device(tm_ctx *c, const tm_image *in, const tm_image *out, cudaStream_t s) {
   tm_status st = ensure_device_info(c);
   if (st) return st;
+  ++c->calls;
   int path = c->hist_path;
   if (c->p.n_bins < 2) path = 2;  // no thresholds: nothing to sweep
   if (path == 0) {
@@ -993,7 +1029,7 @@ tm_status forward_device(tm_ctx *c, const tm_image *in, const tm_image *out, cud
   }
   if (path == 1) {
     // a cached CUDA graph per image pair unless a per-call feature is on
-    const bool graph = !c->stage_timing && !c->debug && !c->reuse_range;
+    const bool graph = !c->stage_timing && !c->debug && !c->reuse_range && single_graph_ok(c, in, out);
     st = forward_fused(c, 1, in, out, s, graph);
     if (st != TM_EUNSUPPORTED) return st;
     if (c->hist_path == 1)
@@ -1286,6 +1322,7 @@ tm_status forward_batch(tm_ctx *c, int n, const tm_image *in, const tm_image *ou
     }
   }
   int64_t total = 0;
+  ++c->calls;
   if (!fin.empty()) {
     mark(c, st, -1);
     s = forward_fused(c, (int)fin.size(), fin.data(), fout.data(), st, true);

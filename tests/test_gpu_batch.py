@@ -106,11 +106,13 @@ def test_graph_replay_tracks_inputs():
 
 def test_single_image_graph_cache():
     """Single-image forwards replay a cached CUDA graph per (input, output)
-    pair, the least recently used replaced beyond six: eight images of
-    several sizes cycled twice (the workspace grows on the way, which drops
-    the cache), a batch in between and new contents in a cached input. Every
-    output equals the same forward without graphs (stage timing on), bit for
-    bit."""
+    pair once the pair comes back (a pair seen once runs its launches
+    directly). Three images cycled three times (captured on their second
+    call, replayed on the third), then eight images of several sizes cycled
+    twice (more pairs than graph slots; the workspace grows on the way, which
+    drops the cache), a batch in between and new contents in a cached input.
+    Every output equals the same forward without graphs (stage timing on),
+    bit for bit."""
     p = tm.make_params(16, [2, 9, 40])
     sizes = [(300, 200), (128, 96), (257, 255), (64, 64), (520, 130), (96, 300), (200, 200), (33, 47)]
     xs = [torch.from_numpy(synth.wdr_image(h, w, seed=20 + i)).cuda() for i, (w, h) in enumerate(sizes)]
@@ -127,11 +129,17 @@ def test_single_image_graph_cache():
             tm.tm_forward(ref_ctx, x, y)
             return y
 
+        def check(k, tag):
+            tm.tm_forward(ctx, xs[k], ys[k])
+            torch.cuda.synchronize()
+            assert torch.equal(ys[k], ref(xs[k])), (tag, k)
+
+        for rnd in range(3):
+            for k in range(3):
+                check(k, ("three", rnd))
         for rnd in range(2):
-            for x, y in zip(xs, ys):
-                tm.tm_forward(ctx, x, y)
-                torch.cuda.synchronize()
-                assert torch.equal(y, ref(x)), (rnd, tuple(x.shape))
+            for k in range(len(xs)):
+                check(k, ("eight", rnd))
             if rnd == 0:
                 zs = [torch.empty_like(x) for x in xs[:3]]
                 tm.tm_forward_batch(ctx, xs[:3], zs)
@@ -139,10 +147,9 @@ def test_single_image_graph_cache():
                 for x, z in zip(xs[:3], zs):
                     assert torch.equal(z, ref(x))
         # new contents in a cached input: the replay sees them
-        xs[-1].copy_(torch.from_numpy(synth.wdr_image(47, 33, seed=99)).cuda())
-        tm.tm_forward(ctx, xs[-1], ys[-1])
-        torch.cuda.synchronize()
-        assert torch.equal(ys[-1], ref(xs[-1]))
+        xs[0].copy_(torch.from_numpy(synth.wdr_image(200, 300, seed=99)).cuda())
+        check(0, "new contents")
+        check(0, "new contents, again")
     finally:
         tm.tm_destroy(ctx)
         tm.tm_destroy(ref_ctx)
