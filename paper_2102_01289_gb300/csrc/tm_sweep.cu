@@ -59,10 +59,13 @@ constexpr unsigned kPTMask = (1u << 21) - 1;
 constexpr int kPStride = 33;        // words per threshold row of PT | m << 21
 // Bands per group: a segment starts on a group's first band and runs on into
 // its next bands while no other CTA has taken them, so CTAs that finish early
-// take the last bands of slow segments. Measured at 12 MP (one wave of 304
-// groups) with 1, 3, 4, 6, 8 and 12 bands per group: the sweep took 0.480,
-// 0.486, 0.469, 0.463, 0.453 and 0.466 ms (uniform tiles: 0.467).
-constexpr int kBandsPerGroup = 8;
+// take the last bands of slow segments. Measured at 12 MP on 256-column strips
+// (one wave of 304 groups) with 1, 3, 4, 6, 8 and 12 bands per group: the sweep
+// took 0.480, 0.486, 0.469, 0.463, 0.453 and 0.466 ms (uniform tiles: 0.467).
+// On 512-column strips (152 groups) the forward took 0.762, 0.749, 0.755 and
+// 0.791 ms with 4, 6, 8 and 12: the integral images beside the sweep, which
+// start as its CTAs run dry, end first with 6.
+constexpr int kBandsPerGroup = 6;
 
 // A strip has TX own columns (256 or 512) and its CTA 2 TX threads: threads
 // t and t + TX take the top and bottom events of column t.
