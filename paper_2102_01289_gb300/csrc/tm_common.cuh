@@ -75,10 +75,10 @@ struct DebugPlanes {
   float *l;        // H * W
 };
 
-// Tiling and shared-memory layout of the fused sweep over one image
-// (host-computed). Tiles are 256-column strips cut into bands of TY rows;
-// the bands of a strip form groups of K consecutive bands, each group one
-// segment that a CTA sweeps while it can claim its next band.
+// Tiling and shared-memory layout of the fused sweep over one image (host-
+// computed). Tiles are strips of TX (512 or 256) columns cut into bands of TY
+// rows; the bands of a strip form groups of K consecutive bands, each group
+// one segment that a CTA sweeps while it can claim its next band.
 struct SweepPlan {
   int W, H;
   int TX, TY, tiles_x, tiles_y;   // own tile size and grid of bands

@@ -8,8 +8,8 @@
 // under TM_FLAG_CDF_INCLUSIVE) needs, per field with half-sizes (rx, ry),
 // the box sum of Eq. 9 over its clipped window [xl, xr] x [yt, yb]:
 //     cnt = E(yb) - E(yt - 1),   E(v) = C_k(xr, v) - C_k(xl - 1, v).
-// Each image is cut into strips of 256 columns and bands of TY rows; K
-// consecutive bands of a strip form a group. A CTA sweeps a segment: it
+// Each image is cut into strips of 512 (or 256) columns and bands of TY rows;
+// K consecutive bands of a strip form a group. A CTA sweeps a segment: it
 // starts on a band and runs on into the group's next bands while it claims
 // them first. The sweep covers the strip's columns widened by the largest
 // half-width on both sides, and only the segment's own rows, from an origin
