@@ -979,7 +979,6 @@ tm_status choose_path(tm_ctx *c, const tm_image *in, const tm_image *out, cudaSt
   return TM_OK;
 }
 
-// The forward launch sequence on one image (device buffers already checked).
 // Whether a single-image forward on (in, out) runs from a CUDA graph: yes
 // when one is cached; else it is captured when the pair came in one of the
 // recent calls and a graph slot is free, or the least recently used graph
@@ -1012,6 +1011,7 @@ bool single_graph_ok(tm_ctx *c, const tm_image *in, const tm_image *out) {
   return false;
 }
 
+// The forward launch sequence on one image (device buffers already checked).
 tm_status forward_device(tm_ctx *c, const tm_image *in, const tm_image *out, cudaStream_t s) {
   tm_status st = ensure_device_info(c);
   if (st) return st;
