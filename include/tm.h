@@ -145,7 +145,11 @@ const char *tm_status_string(tm_status s);
  * (TM_OPT_HIST_PATH = 0, the default) the first call for an image size and
  * dtype pair times both paths and synchronises `stream` once. The context's
  * workspace is reused, so calls on one context must be ordered (same stream,
- * or synchronised). */
+ * or synchronised). On the fused path, an (in, out) pair of descriptors that
+ * comes back is captured in a CUDA graph of the context and replayed while
+ * the same descriptors are passed (a replay reads the current pixel
+ * contents); not with debug exports, stage timing or streaming range reuse
+ * on. The context keeps six such graphs (batches' included). */
 tm_status tm_forward(tm_ctx *ctx, const tm_image *in, const tm_image *out,
                      void *stream);
 
@@ -358,8 +362,9 @@ tm_status tm_debug_export(tm_ctx *ctx, int32_t what, void *dst, size_t bytes,
  *   TM_OPT_SWEEP_WIDTH   tuning: own columns of the fused sweep's strips,
  *                        256 (two CTAs of 512 threads per SM) or 512 (one
  *                        CTA of 1024 threads per SM; taken only where every
- *                        image of the call fits it, else 256); 0 = automatic.
- *                        Results do not depend on it.
+ *                        image of the call fits it, else 256); 0 = automatic
+ *                        (512 where every image fits it). Other values are
+ *                        TM_EINVAL. Results do not depend on it.
  */
 enum {
   TM_OPT_HIST_PATH = 1,
